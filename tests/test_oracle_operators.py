@@ -1,0 +1,166 @@
+"""Pins of the oracle's Galerkin operators: brute-force quadrature of singular
+pairs, closed-form zeros, symmetries, Gram identities and the Calderon
+projector identity of Eq. (10)."""
+import warnings
+
+import numpy as np
+import pytest
+
+import mtf_inputs as mi
+from oracle.quadrature import sauter_schwab, ss_map
+from oracle.operators import (pair_integrals, assemble_block, classify_pairs, identity_gram,
+                              transmission_gram, paired_trace, plane_wave, l2_trace_projection,
+                              ss_vertex_order)
+from oracle.brute import brute_pair
+from tests.oracle_helpers import skeleton_of, sphere_system
+
+A = np.array([0.0, 0.0, 0.0])
+B = np.array([1.0, 0.1, 0.0])
+C = np.array([0.3, 0.9, 0.1])
+D = np.array([0.5, -0.7, 0.6])
+E = np.array([-0.8, -0.2, 0.4])
+F = np.array([-0.3, 0.6, -0.5])
+
+
+def _rwg(P, s=(1, -1, 1)):
+    area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+    L = np.array([np.linalg.norm(P[2] - P[1]), np.linalg.norm(P[0] - P[2]), np.linalg.norm(P[1] - P[0])])
+    return np.array(s) * L / (2 * area), P.copy(), area
+
+
+def _ss(kind, Pt, Ps, k, n):
+    ca, pa, At = _rwg(Pt)
+    cb, qb, As = _rwg(Ps, (-1, 1, 1))
+    xh, yh, w = sauter_schwab(kind, n)
+    X, Y = ss_map(Pt[None], xh), ss_map(Ps[None], yh)
+    T, K = pair_integrals(k, X, Y, (4 * At * As * w)[None], ca[None], pa[None], cb[None], qb[None])
+    return T[0], K[0], (ca, pa, cb, qb)
+
+
+@pytest.mark.parametrize("kind,Pt,Ps,no,ni,tolT,tolK", [
+    ("coincident", np.array([A, B, C]), np.array([A, B, C]), 16, 16, 2e-7, None),
+    ("edge", np.array([A, B, C]), np.array([A, B, D]), 32, 24, 1e-8, 1e-6),
+    ("vertex", np.array([A, B, C]), np.array([A, E, F]), 16, 20, 1e-8, 1e-6),
+])
+def test_sauter_schwab_matches_brute_force(kind, Pt, Ps, no, ni, tolT, tolK):
+    """P6: every 3x3 local EFIO/MFIO entry of a singular pair agrees with an
+    independent nested polar quadrature (no Sauter-Schwab map)."""
+    k = 2.0 + 0.0j
+    T, K, (ca, pa, cb, qb) = _ss(kind, Pt, Ps, k, 10)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        Tb, Kb = brute_pair(k, Pt, Ps, ca, pa, cb, qb, kind, n_outer=no, n_inner=ni)
+    assert np.abs(T - Tb).max() / np.abs(Tb).max() < tolT
+    if tolK is None:   # flat coincident pair: K vanishes identically
+        assert np.abs(K).max() < 1e-14 * np.abs(T).max()
+        assert np.abs(Kb).max() < 1e-5 * np.abs(Tb).max()   # brute force: zero to its accuracy
+    else:
+        assert np.abs(K - Kb).max() / np.abs(Kb).max() < tolK
+    # the default rule (n = 4) is within its expected accuracy
+    T4, K4, _ = _ss(kind, Pt, Ps, k, 4)
+    assert np.abs(T4 - Tb).max() / np.abs(Tb).max() < 1e-4
+
+
+def test_mfio_vanishes_on_coplanar_pairs():
+    """K integrand (x - y) . (g x f) is zero when both triangles lie in one
+    plane: coincident and coplanar edge-adjacent pairs give exactly 0."""
+    k = 1.3
+    P1 = np.array([A, B, np.array([0.2, 0.8, 0.0])])
+    P2 = np.array([A, B, np.array([0.6, -0.9, 0.0])])
+    for kind, Ps in (("coincident", P1), ("edge", P2)):
+        _, K, _ = _ss(kind, P1, Ps, k, 4)
+        assert np.abs(K).max() < 1e-15
+
+
+def test_efio_symmetric_and_swap_consistent(oracle_cache):
+    """T_i is complex symmetric up to quadrature error (P4), and blocks 0 and
+    1 of the sphere, assembled at the same k on the same triangles with
+    opposite normals and RWG signs, are identical (P8)."""
+    cfg, sk, sysm = sphere_system(oracle_cache, 1)
+    T0, K0 = assemble_block(sk, 0, 1.7)
+    T1, K1 = assemble_block(sk, 1, 1.7)
+    assert np.abs(T0 - T1).max() <= 1e-13 * np.abs(T0).max()
+    assert np.abs(K0 - K1).max() <= 1e-13 * np.abs(K0).max()
+    T = sysm.T[1]
+    assert np.abs(T - T.T).max() / np.abs(T).max() < 5e-5
+
+
+def test_transmission_grams(oracle_cache):
+    """G^{ji} = (G^{ij})^T (skew pairing with opposite normals), and on the
+    single sphere (Gamma_0 = Gamma_1, RWG_1 = -RWG_0 on every triangle)
+    G^{01} = -Id_0; the 6-point rule integrates these quadratics exactly."""
+    cfg, sk, sysm = sphere_system(oracle_cache, 1)
+    G01, G10 = transmission_gram(sk, 0, 1), transmission_gram(sk, 1, 0)
+    assert np.allclose(G10, G01.T, atol=1e-15)
+    Id0 = identity_gram(sk, 0)
+    assert np.allclose(G01, -Id0, atol=1e-15)
+    assert np.allclose(Id0, -Id0.T, atol=1e-15)   # antisymmetric x-pairing
+    # split sphere: rows of all Grams into Gamma_1 sum to -Id_1 on the
+    # non-junction dofs' restriction of the same field (check on a field)
+    sk2 = skeleton_of(mi.split_sphere(3))
+    assert np.allclose(transmission_gram(sk2, 1, 2), transmission_gram(sk2, 2, 1).T, atol=1e-15)
+
+
+def _fields_radiating(k, x0, m):
+    """E = curl(m G(., x0)) (a magnetic dipole, radiating), and curl E / (i k)."""
+    def parts(X):
+        R = X - x0
+        r = np.linalg.norm(R, axis=-1)[..., None]
+        G = np.exp(1j * k * r) / (4 * np.pi * r)
+        Gp = G * (1j * k - 1.0 / r)
+        Gpp = G * (1j * k - 1.0 / r) ** 2 + G / r ** 2
+        return R, r, G, Gp, Gpp
+
+    def Ef(X):
+        R, r, G, Gp, Gpp = parts(X)
+        return np.cross(Gp * R / r, np.broadcast_to(m, R.shape))
+
+    def Nf(X):
+        R, r, G, Gp, Gpp = parts(X)
+        Rm = (R @ m)[..., None]
+        Hm = (Gp / r) * m + (Gpp - Gp / r) * R * Rm / r ** 2
+        return (Hm + k * k * G * m) / (1j * k)
+    return Ef, Nf
+
+
+def _projector_residual(sk, sysm, i, k, rho, fields, sign):
+    Ef, Nf = fields
+    cD, cN = l2_trace_projection(sk, i, Ef, Nf)
+    bD, bN = paired_trace(sk, i, Ef, Nf)
+    u = np.concatenate([cD, rho * cN])
+    b = np.concatenate([bD, rho * bN])
+    Au = sysm.calderon_block(i) @ u
+    return np.linalg.norm(Au - sign * 0.5 * b) / np.linalg.norm(0.5 * b)
+
+
+def test_calderon_projector_identity(oracle_cache):
+    """P2, Eq. (10): A_i u = u/2 for Cauchy data of fields solving Maxwell in
+    Omega_i (interior block: plane wave at k_1; exterior block: radiating
+    dipole inside the sphere), and A_0 u = -u/2 for the incident plane wave
+    (regular inside the scatterer), which fixes the sign of the right-hand
+    side.  Residuals shrink under refinement; flipping the sign of K or T
+    breaks them (checked on the mutated operator)."""
+    res = {}
+    for lvl in (1, 2):
+        cfg, sk, sysm = sphere_system(oracle_cache, lvl)
+        k0, k1, rho1 = sysm.k[0], sysm.k[1], sysm.rho[1]
+        d, p = np.array([0.3, -0.4, np.sqrt(0.75)]), np.array([1.0, 0.5j, 0.0])
+        p = p - (p @ d) * d
+        r_int = _projector_residual(sk, sysm, 1, k1, rho1, plane_wave(k1, d, p), +1)
+        r_ext = _projector_residual(sk, sysm, 0, k0, 1.0,
+                                    _fields_radiating(k0, np.array([0.1, -0.2, 0.05]),
+                                                      np.array([0.3, 1.0, -0.5])), +1)
+        r_inc = _projector_residual(sk, sysm, 0, k0, 1.0, plane_wave(k0, d, p), -1)
+        r_wrong = _projector_residual(sk, sysm, 0, k0, 1.0, plane_wave(k0, d, p), +1)
+        r_ext_wrong = _projector_residual(sk, sysm, 0, k0, 1.0,
+                                          _fields_radiating(k0, np.array([0.1, -0.2, 0.05]),
+                                                            np.array([0.3, 1.0, -0.5])), -1)
+        res[lvl] = (r_int, r_inc, r_ext, r_wrong, r_ext_wrong)
+    for lvl, (r_int, r_inc, r_ext, r_wrong, r_ext_wrong) in res.items():
+        assert r_wrong > 1.5 and r_ext_wrong > 1.5      # the other sign is far off
+        assert max(r_int, r_inc) < (0.08 if lvl == 1 else 0.05), res
+        # the radiating field converges slowly in this (l2 of tested values)
+        # norm; the bound only has to separate the two signs
+        assert r_ext < 0.15, res
+    for q in range(2):
+        assert res[2][q] < 0.75 * res[1][q], res   # plane-wave cases converge
