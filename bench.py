@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MTF path (assembly + preconditioned GMRES solve).
+
+Workload (one step = one pass of the whole hot path over one batch): the
+split-sphere scatterer -- unit sphere cut by the equatorial disk into two
+hemispheres (eps_r 2 and 4, a triple-junction equator), k0 = 2, 2178
+skeleton triangles (6 * 11^2 per surface), two polarisations of a plane wave
+along +z.  A step re-assembles the MTF operator (regular + Sauter-Schwab
+pairs, transmission Grams), builds the right-hand sides, solves with
+restarted FGMRES to a relative residual that makes the solution error
+<= 1e-5, and evaluates the far field on the z = 0 plane (RCS_z).
+
+Metric: solved right-hand sides per second (plus assembly triangle pairs
+per second).  ``value`` is device-timed (CUDA events on the launching
+stream, inputs resident in HBM); ``e2e`` times the same work through the
+C-ABI from host buffers (mesh creation, upload, assembly, solve, far field,
+results copied back).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import mtf_inputs as mi  # noqa: E402
+
+METRIC = "solved RHS/sec at 1e-5 rel. err vs FP64 oracle; assembly triangle-pairs/sec"
+UNIT = "RHS/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12      # 152 SMs x 128 lanes x FMA x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (recipe table)
+FLOPS_PER_EVAL = 57                                    # moment-form inner loop, see the design doc
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def workload(name):
+    if name == "split_sphere":
+        cfg = mi.config_split_sphere()
+        desc = ("split sphere r=1 (equator disk, triple junction), eps_r 2/4, k0=2, 2178 skeleton "
+                "triangles, 2 plane waves (x/y pol, +z)")
+    elif name == "sphere":
+        cfg = mi.config_sphere(2)
+        desc = "dielectric sphere r=1 eps_r=2 k0=1, icosphere 320 triangles, 1 plane wave"
+    elif name == "cube2":
+        cfg = mi.config_cube2()
+        desc = "unit cube 2x2x2 subcubes eps U[1.5,4] k0=3, 5832 triangles, 64 plane waves"
+    else:
+        raise ValueError(name)
+    obs_t = np.linspace(0.0, np.pi, 181)
+    cfg["obs"] = np.stack([np.cos(obs_t), np.sin(obs_t), 0 * obs_t], axis=1)
+    cfg["desc"] = desc
+    return cfg
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) baseline on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample(cfg, iters, budget_s=12.0):
+    """Time the FP64 oracle on a bounded sample of the workload and
+    extrapolate to one full step: assembly of a sample of block 0's triangle
+    pairs (regular and singular timed separately), dense matvecs of the full
+    block sizes, times the GMRES iteration count of the GPU solve."""
+    from oracle.skeleton import Skeleton
+    from oracle.operators import classify_pairs, assemble_block
+    from oracle.mtf import MTFSystem
+
+    m = cfg["mesh"]
+    sk = Skeleton(m.vertices, m.triangles, m.labels, m.n_domains)
+    pr = classify_pairs(sk, 0)
+    ntau = 8
+    t0 = time.perf_counter()
+    sel = np.isin(pr["regular"][0], np.arange(ntau))
+    reg = {"regular": (pr["regular"][0][sel], pr["regular"][1][sel])}
+    assemble_block(sk, 0, 2.0, pairs=reg)
+    t_reg = time.perf_counter() - t0
+    sing = {}
+    for kind in ("coincident", "edge", "vertex"):
+        s = np.isin(pr[kind][0], np.arange(ntau))
+        sing[kind] = (pr[kind][0][s], pr[kind][1][s])
+    t0 = time.perf_counter()
+    assemble_block(sk, 0, 2.0, pairs=sing)
+    t_sing = time.perf_counter() - t0
+    n_reg = len(reg["regular"][0])
+    n_sing = sum(len(v[0]) for v in sing.values())
+    counts = np.zeros(3, dtype=np.int64)
+    for i in range(sk.n_domains):
+        prc = classify_pairs(sk, i)
+        counts[0] += len(prc["regular"][0])
+        counts[1] += sum(len(prc[k][0]) for k in ("coincident", "edge", "vertex"))
+    t_asm = t_reg * counts[0] / max(1, n_reg) + t_sing * counts[1] / max(1, n_sing)
+    # matvec cost with full-size dense blocks (random entries, same shapes)
+    ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"], assemble=False)
+    rng = np.random.default_rng(0)
+    ref.T = [rng.standard_normal((n, n)) + 0j for n in sk.N]
+    ref.K = [rng.standard_normal((n, n)) + 0j for n in sk.N]
+    x = rng.standard_normal((sk.n_total, len(cfg["dirs"]))) + 0j
+    t0 = time.perf_counter()
+    nmv = 3
+    for _ in range(nmv):
+        ref.matvec(x)
+    t_mv = (time.perf_counter() - t0) / nmv
+    t_step = t_asm + (iters + 2) * t_mv
+    return {
+        "t_step": t_step, "t_assembly": t_asm, "t_matvec": t_mv,
+        "sample": (f"oracle assembly of {n_reg} regular + {n_sing} singular pairs of block 0 "
+                   f"(test triangles 0..{ntau - 1}), extrapolated to {counts[0]} + {counts[1]} pairs; "
+                   f"{nmv} full-size FP64 block matvecs x {iters + 2} GMRES iterations"),
+        "pairs_per_s": (n_reg + n_sing) / (t_reg + t_sing),
+    }
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    iters = args.ref_iters
+    vals = []
+    res = None
+    for _ in range(args.steps):
+        res = oracle_sample(cfg, iters)
+        vals.append(len(cfg["dirs"]) / res["t_step"])
+    v = statistics.median(vals)
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["t_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg["desc"], "nrhs": len(cfg["dirs"])},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="split_sphere")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2502_10907_gb300.build import build
+    build()
+    from paper_2502_10907_gb300 import api, _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prec = L.MTF_PREC_FP64 if args.precision == "fp64" else L.MTF_PREC_MIXED
+    m = cfg["mesh"]
+    mesh = api.Mesh.from_inputs(m)
+    counts = mesh.pair_counts()
+    n_pairs = int(counts.sum())
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
+                      precision=prec)
+    # accuracy gate: FP64 solution at tight tolerance (the FP64 path is pinned
+    # to the oracle at 1e-10 by the parity tests)
+    ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=300)
+    x_ref, st_ref = ref_sys.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+    del ref_sys
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+        x, st = sysg.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        f = sysg.farfield(x, cfg["obs"])
+        return x, st, f
+
+    for _ in range(max(3, args.warmup)):
+        x, st, f = step()
+    torch.cuda.synchronize()
+    L.mtf_profile_read()                      # reset counters
+    L.mtf_profile_enable(True)
+    iters = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, st, f = step()
+            iters.append(st.iterations)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    L.mtf_profile_enable(False)
+    prof = L.mtf_profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nrhs = len(cfg["dirs"])
+    value = world * nrhs / (ms / 1e3)
+    err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max())
+    # assembly alone (device-timed)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(3):
+        sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    eb.record(stream)
+    torch.cuda.synchronize()
+    t_asm = ea.elapsed_time(eb) / 3 / 1e3
+    L.mtf_profile_read()
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    hbm, bf16, src = _peaks()
+    launches = sum(v[0] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tms) = top
+    per_launch_s = tms / max(1, nl) / 1e3
+    n_mat = int(sum(int(n) * int(n) for n in mesh.n_dofs))
+    roof = None
+    if name in ("regular64", "regular32"):
+        flops = counts[3] * 36 * FLOPS_PER_EVAL
+        peak = FP64_PEAK_TFLOPS if name == "regular64" else FP32_PEAK_TFLOPS
+        ach = flops / per_launch_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "derived from unit counts and max SM clock (FP64 1.25 TF/s, FP32 80.5 TF/s)"}
+    elif name in ("matvec64", "matvec32"):
+        eb_ = 32 if name == "matvec64" else 16
+        byts = n_mat * eb_ + 2 * mesh.n_total * 16 * nrhs + int(mesh.n_total // 2) * 6 * (16 + 8)
+        ach = byts / per_launch_s / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src}
+    elif name == "singular64":
+        npts = {0: 6, 1: 5, 2: 2}
+        evals = sum(int(counts[c]) * npts[c] * sysg.opt.n_ss ** 4 for c in range(3))
+        ach = evals * 75 / per_launch_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived (FP64 1.25 TF/s at max SM clock)"}
+    else:
+        roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": src}
+    roof["launches"] = nl
+    roof["avg_launch_ms"] = per_launch_s * 1e3
+
+    # ---- end to end through the C-ABI from host buffers ---------------------
+    e2e_times = []
+    h2d = (m.vertices.nbytes + m.triangles.nbytes + m.labels.nbytes + 2 * 8 * m.n_domains
+           + cfg["dirs"].nbytes + cfg["pols"].nbytes + cfg["obs"].nbytes)
+    d2h = nrhs * mesh.n_total * 16 + nrhs * len(cfg["obs"]) * 3 * 16
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
+        sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
+                        precision=prec)
+        xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        fe = sh.farfield(xe, cfg["obs"])
+        xh, fh = xe.cpu(), fe.cpu()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        del sh, mh
+    e2e = world * nrhs / statistics.median(e2e_times)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = oracle_sample(cfg, int(statistics.median(iters)))
+        cpu = {"value": nrhs / res["t_step"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": res["sample"], "assembly_pairs_per_s": res["pairs_per_s"]}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == L.MTF_PREC_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["desc"], "nrhs": nrhs, "n_unknowns": int(mesh.n_total),
+                       "triangle_pairs": n_pairs, "precision": args.precision, "gmres_tol": args.tol,
+                       "restart": args.restart, "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
+                       "parallelism": f"replicas x{world}"},
+            "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},
+            "solution_rel_err_vs_fp64": err,
+            "gmres_iterations": int(statistics.median(iters)),
+            "converged": bool(st.converged), "reference_converged": bool(st_ref.converged),
+            "gpu_launches": int(launches),
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+            "roofline": roof,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * libmtf -- local multiple traces formulation (MTF) for time-harmonic
+ * Maxwell transmission problems through heterogeneous scatterers, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2502.10907 ("Local Multiple Traces Formulation for
+ * Heterogeneous Electromagnetic Scattering: Implementation and
+ * Preconditioning").  Each entry point cites the passage that defines what it
+ * computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Complex numbers are interleaved (re, im) pairs.  "complex128" = two
+ *   doubles, "complex64" = two floats.
+ * - Unknown vector layout (Sec. 3.2, Eq. 16): blocks i = 0..M in order; block
+ *   i holds [D coefficients (N_i), N coefficients (N_i)] of
+ *   u_i = (gamma_D E, rho_i gamma_N E) in the RWG basis of Gamma_i; block
+ *   offsets are 2 * sum_{j<i} N_j.  Multi-vector arguments are column-major
+ *   n_total x nrhs (column c starts at c * n_total).
+ * - RWG dofs of Gamma_i are the edges of Gamma_i ordered by increasing
+ *   (lower vertex id, higher vertex id); the RWG function of edge e on
+ *   triangle t of Gamma_i is s * l / (2 A) (x - v) with v the vertex opposite
+ *   e, l = |e|, A = area(t), s = dir(e, t) * swap_i(t), dir = +1 iff t's
+ *   vertex order runs along e from the lower to the higher vertex id.
+ * - Ownership: the caller owns every pointer it passes; host inputs are
+ *   copied before the call returns.  Handles own their device memory.
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *   default stream).  Device work is enqueued on it; calls that return
+ *   host-side results (stats, info) synchronise it.
+ * - Errors: every call returns an mtf_status and never throws.  On error the
+ *   output buffers are unspecified and handles remain valid; mtf_last_error()
+ *   describes the last failure of the calling thread.
+ * - Device pointers must be 16-byte aligned.
+ */
+#ifndef MTF_H_
+#define MTF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtf_mesh_s* mtf_mesh;
+typedef struct mtf_system_s* mtf_system;
+
+typedef enum {
+  MTF_OK = 0,
+  MTF_ERR_ARG = 1,      /* invalid argument (null pointer, size, range)      */
+  MTF_ERR_MESH = 2,     /* skeleton mesh violates the admissibility rules    */
+  MTF_ERR_CUDA = 3,     /* a CUDA runtime call failed                        */
+  MTF_ERR_OOM = 4,      /* device allocation failed                          */
+  MTF_ERR_NOCONV = 5,   /* solver reached max_iter above the tolerance       */
+  MTF_ERR_NAN = 6,      /* non-finite value met in the solver                */
+  MTF_ERR_TIMEOUT = 7   /* a bounded device wait ran out                     */
+} mtf_status;
+
+typedef enum {
+  MTF_PREC_FP64 = 0,    /* FP64 assembly, storage, matvec and solver         */
+  MTF_PREC_MIXED = 1    /* FP32 regular pairs + FP32 storage / matvec, FP64
+                           singular pairs, Arnoldi and refinement residuals   */
+} mtf_precision;
+
+typedef enum {
+  MTF_PRECOND_NONE = 0,
+  MTF_PRECOND_OSRC = 1  /* block-OSRC of Sec. 4.4 (Eq. 19)                   */
+} mtf_precond;
+
+typedef struct {
+  int32_t precision;    /* mtf_precision, default MTF_PREC_FP64              */
+  int32_t n_ss;         /* Gauss points per coordinate of the Sauter-Schwab
+                           rules (default 4, range 1..12)                     */
+  int32_t restart;      /* GMRES restart length m (default 100)              */
+  int32_t max_iter;     /* total GMRES iterations per solve (default 2000)   */
+  double tol;           /* relative residual ||b - M x|| / ||b|| target
+                           (default 1e-5, Sec. 5.3)                           */
+  int32_t precond;      /* mtf_precond, default MTF_PRECOND_NONE             */
+  int32_t osrc_np;      /* Pade order N_p of the OSRC square root (default 4)*/
+  double osrc_theta;    /* branch-cut rotation angle (default pi/2)          */
+  double osrc_eps_scale;/* damping eps = osrc_eps_scale k^(1/3) R^(-2/3)
+                           with R the block's radius (default 0.39)          */
+  int32_t max_refine;   /* outer FP64 iterative-refinement steps in mixed
+                           mode (default 4)                                  */
+} mtf_options;
+
+typedef struct {
+  int32_t iterations;   /* inner (F)GMRES iterations, max over right-hand sides */
+  int32_t restarts;     /* restart cycles of the slowest right-hand side        */
+  int32_t refinements;  /* outer refinement steps (mixed precision)             */
+  int32_t converged;    /* 1 if every right-hand side met tol                   */
+  double rel_residual;  /* max over rhs of the final true ||b - M x|| / ||b||  */
+  double seconds;       /* wall time of the call                               */
+} mtf_solve_stats;
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+void mtf_default_options(mtf_options* opt);
+
+/* Skeleton mesh and subdomain spaces (Sec. 3.2, Sec. 4.2, Algorithm 1).
+ *   vertices: nv * 3 doubles (host).
+ *   tris:     nt * 3 int32 vertex ids (host); the right-hand-rule normal of
+ *             triangle t points from subdomain labels[2t] into labels[2t+1].
+ *   labels:   nt * 2 int32 (host), distinct, in [0, n_domains); 0 = exterior.
+ *             Triangles with labels[2t] > labels[2t+1] are re-oriented so
+ *             every interface Gamma_ij has its normal from min(i,j) to
+ *             max(i,j), the convention Algorithm 1 assumes.
+ *   n_domains: M + 1.
+ * Algorithm 1 then gives, per subdomain i, the triangles of Gamma_i with
+ * swap = sign(j - i) and the RWG dofs of Gamma_i.  Fails with MTF_ERR_MESH
+ * unless every Gamma_i is a closed surface (each of its edges on exactly two
+ * of its triangles) and every subdomain has at least one triangle.
+ * Host-only: the mesh tables are uploaded to the current CUDA device by the
+ * first mtf_assemble that uses the mesh (so this call, mtf_mesh_info and
+ * mtf_mesh_pair_counts work without a GPU).  */
+mtf_status mtf_mesh_create(const double* vertices, int32_t nv, const int32_t* tris, int32_t nt,
+                           const int32_t* labels, int32_t n_domains, mtf_mesh* out);
+
+/* n_dofs (host, n_domains entries) receives N_i = dim RWG_i; n_total
+ * receives N = 2 sum N_i (Eq. 16).  Either pointer may be NULL. */
+mtf_status mtf_mesh_info(mtf_mesh mesh, int32_t* n_dofs, int64_t* n_total);
+
+/* Number of singular triangle pairs of each kind summed over blocks
+ * (coincident, common edge, common vertex) and of regular pairs. */
+mtf_status mtf_mesh_pair_counts(mtf_mesh mesh, int64_t* counts4);
+
+void mtf_mesh_destroy(mtf_mesh mesh);
+
+/* Galerkin assembly of the MTF operator M = 2A + X of Problem 2.
+ *   k0:    exterior wavenumber (> 0).
+ *   eps_r, mu_r: n_domains doubles each (host), relative permittivity and
+ *          permeability; k_i = k0 sqrt(eps_r mu_r), rho_i = sqrt(eps_r / mu_r)
+ *          (Eq. 1).  Index 0 is the exterior.
+ *   opt:   NULL = defaults.
+ * Builds, per block i, the dense EFIO T_i and MFIO K_i Galerkin matrices
+ * at k_i (Eqs. 7-9) tested with the x-pairing (Eq. 5) -- regular pairs with
+ * the 6x6-point tensor rule, coincident / common-edge / common-vertex pairs
+ * with Sauter-Schwab rules -- and the sparse transmission Grams of Eq. (18)
+ * for the exchange X (Eqs. 11-13).  All data stays on the device. */
+mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const double* mu_r,
+                        const mtf_options* opt, void* stream, mtf_system* out);
+
+/* Assemble again into an existing system (same mesh and options, new k0 /
+ * materials), reusing its device buffers; same definitions as mtf_assemble. */
+mtf_status mtf_reassemble(mtf_system sys, double k0, const double* eps_r, const double* mu_r,
+                          void* stream);
+
+/* Kernel accounting (no counterpart in the paper; used to measure the
+ * library).  Launch counts of every library kernel are always kept; with
+ * mtf_profile_enable(1) each launch is also bracketed by CUDA events on its
+ * stream.  mtf_profile_read(n, launches, ms) synchronises on the recorded
+ * events, writes for kernel ids 0..n-1 the launches and device milliseconds
+ * accumulated since the previous read (either array may be NULL) and resets
+ * the counters.  Process-wide, not thread-safe. */
+mtf_status mtf_profile_enable(int32_t on);
+mtf_status mtf_profile_read(int32_t n, int64_t* launches, double* ms);
+int32_t mtf_kernel_count(void);
+const char* mtf_kernel_name(int32_t id);
+
+/* Copy T_i and K_i (N_i x N_i complex128 each, row-major, row = test dof,
+ * column = trial dof) into device buffers t_out / k_out. */
+mtf_status mtf_get_block(mtf_system sys, int32_t i, void* t_out, void* k_out, void* stream);
+
+/* y = M x (Problem 2): block-dense 2 A_i u_i plus the skeleton exchange
+ * sum_j G^{ij} u_j in both trace slots (Remark 2).  x, y: device complex128,
+ * n_total x nrhs, must not overlap. */
+mtf_status mtf_matvec(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream);
+
+/* Right-hand side of Problem 2 for plane waves E_inc = p exp(i k0 d.x)
+ * (Eq. 22): block 0 holds -2 <gamma_{.,0} E_inc, psi_m>_x for the D and N
+ * slots (sign from the Calderon identities of Eq. 10 with n_0), all other
+ * blocks are zero.  dirs: nrhs * 3 doubles (host, unit); pols: nrhs * 3
+ * complex128 (host, orthogonal to d); b_out: device complex128 n_total x nrhs. */
+mtf_status mtf_rhs(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
+                   void* b_out, void* stream);
+
+/* Solve M u = b for nrhs plane waves with restarted flexible GMRES
+ * (Sec. 5.3: relative tolerance, iteration cap), right-preconditioned by
+ * block-OSRC when opt.precond says so.  x_out: device complex128
+ * n_total x nrhs.  stats: host, may be NULL.  Returns MTF_ERR_NOCONV (with
+ * x_out holding the last iterate) if some right-hand side misses tol. */
+mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
+                     void* x_out, mtf_solve_stats* stats, void* stream);
+
+/* Far field E_inf(xhat) of solutions x (device complex128 n_total x nrhs) at
+ * n_obs unit directions obs_dirs (host, n_obs * 3 doubles):
+ * E_inf = i k0 / (4 pi) [xhat x w_D + (xhat x w_N) x xhat],
+ * w_. = int_{Gamma_0} (trace) exp(-i k0 xhat . y) dy, from the Stratton-Chu
+ * representation (Eq. 8) in Omega_0 (RCS_z of Sec. 5.2 is its z component).
+ * f_out: device complex128, n_obs * 3 * nrhs, index (c * n_obs + o) * 3 + xyz. */
+mtf_status mtf_farfield(mtf_system sys, const void* x, int32_t nrhs, const double* obs_dirs,
+                        int32_t n_obs, void* f_out, void* stream);
+
+void mtf_system_destroy(mtf_system sys);
+
+const char* mtf_status_string(mtf_status s);
+const char* mtf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTF_H_ */

@@ -337,3 +337,20 @@ def l2_trace_projection(sk: Skeleton, i: int, field_D, field_N):
         np.add.at(b, sk.dof[i].ravel(), loc3.ravel())
         out.append(np.linalg.solve(Mm, b))
     return out[0], out[1]
+
+
+def block_rows(sk: Skeleton, i: int, k: complex, rows, n_ss: int = 4):
+    """Full rows T_i[rows, :], K_i[rows, :]: assembles every pair whose test
+    triangle supports one of the rows (the only pairs that touch them)."""
+    rows = np.asarray(rows)
+    dof = sk.dof[i]
+    tau = np.unique(np.where(np.isin(dof, rows).any(axis=1))[0])
+    T = len(sk.tris[i])
+    a = np.repeat(tau, T)
+    b = np.tile(np.arange(T), len(tau))
+    Ft = sk.F[sk.tris[i]]
+    nsh = _shared_vertices(Ft[a], Ft[b])
+    names = {3: "coincident", 2: "edge", 1: "vertex", 0: "regular"}
+    pairs = {names[c]: (a[nsh == c], b[nsh == c]) for c in (3, 2, 1, 0) if np.any(nsh == c)}
+    Tm, Km = assemble_block(sk, i, k, n_ss=n_ss, pairs=pairs)
+    return Tm[rows], Km[rows]

@@ -1,0 +1,192 @@
+// Internal declarations of libmtf (not part of the public C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mtf.h"
+
+namespace mtf {
+
+// ---------------------------------------------------------------------------
+// errors: thrown inside the library, turned into mtf_status at the C-ABI
+// ---------------------------------------------------------------------------
+struct Error {
+  mtf_status status;
+  std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+
+#define MTF_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw ::mtf::Error{e_ == cudaErrorMemoryAllocation ? MTF_ERR_OOM : MTF_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+
+#define MTF_REQUIRE(cond, st, msg)                      \
+  do {                                                  \
+    if (!(cond)) throw ::mtf::Error{(st), (msg)};       \
+  } while (0)
+
+// Owning device buffer.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count == n && p) return;
+    release();
+    if (count == 0) return;
+    MTF_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    alloc(h.size());
+    if (!h.empty()) MTF_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// quadrature tables (generated on the host from their defining equations)
+// ---------------------------------------------------------------------------
+struct TriRule {
+  double s[6], t[6], w[6];  // reference triangle {s,t>=0, s+t<=1}, sum w = 1/2
+};
+const TriRule& triangle_rule6();
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+// Sauter-Schwab rule: (x1, x2, y1, y2, w) per point, kinds 0 coincident,
+// 1 common edge, 2 common vertex.
+void sauter_schwab_rule(int kind, int n, std::vector<double>& pts);
+
+// ---------------------------------------------------------------------------
+// mesh (Algorithm 1 and RWG tables)
+// ---------------------------------------------------------------------------
+struct BlockInfo {
+  int32_t T = 0;          // triangles of Gamma_i
+  int32_t N = 0;          // RWG dofs of Gamma_i
+  int64_t bt_off = 0;     // first block-triangle index
+  int64_t dof_off = 0;    // unknown offset 2 sum_{j<i} N_j
+  int64_t mat_off = 0;    // first dense entry of the block's matrices
+  int64_t row_off = 0;    // first exchange row (sum_{j<i} N_j)
+};
+
+// Singular pair record (device): block-triangle ids and the Sauter-Schwab
+// vertex orders (local vertex indices 0..2 packed in 2 bits each).
+struct SingPair {
+  int32_t tau;   // block-triangle index of the test triangle
+  int32_t sig;   // block-triangle index of the trial triangle
+  int32_t block;
+  int32_t code;  // kind (bits 0-1) | perm_tau (bits 2-7) | perm_sig (bits 8-13)
+};
+
+// Exchange (transmission Gram) entry: row = (block i, dof m); 6 entries per
+// row, one per (triangle of Gamma_i containing edge m, local edge b of the
+// neighbour's RWG function on that triangle).
+struct XEntry {
+  int32_t bt_i;   // block-triangle of the row's triangle in block i
+  int32_t bt_j;   // the same skeleton triangle seen from block j
+  int32_t col;    // global unknown index of the D slot of dof_j(t, b)
+  int32_t ab;     // a | (b << 2) | (nj << 4): local edges and N_j for the N slot offset
+};
+
+}  // namespace mtf
+
+struct mtf_mesh_s {
+  int32_t nv = 0, nt = 0, nd = 0;
+  bool uploaded = false;                     // device copies made at the first mtf_assemble
+  std::vector<double> V;
+  std::vector<int32_t> F, L;                 // canonical: normal from min to max label
+  std::vector<mtf::BlockInfo> blk;
+  int64_t n_total = 0, n_rows = 0, n_bt = 0, n_mat = 0;
+  int64_t pair_counts[4] = {0, 0, 0, 0};    // coincident, edge, vertex, regular
+  // host copies of the per-block-triangle tables
+  std::vector<int32_t> bt_tri, bt_dof, bt_vid, bt_blk;
+  std::vector<int8_t> bt_swap;
+  std::vector<double> bt_v, bt_c, bt_area;
+  std::vector<mtf::SingPair> sing;
+  std::vector<mtf::XEntry> xent;
+  std::vector<int32_t> dof_bt;               // per exchange row: 2 x (bt*3 + a)
+  // device copies
+  mtf::DevBuf<double> d_bt_v, d_bt_c, d_bt_area;
+  mtf::DevBuf<int32_t> d_bt_dof, d_bt_vid, d_bt_blk, d_dof_bt;
+  mtf::DevBuf<int8_t> d_bt_swap;
+  mtf::DevBuf<mtf::SingPair> d_sing;
+  mtf::DevBuf<mtf::XEntry> d_xent;
+  mtf::DevBuf<int64_t> d_blk_mat_off;        // per block
+  mtf::DevBuf<int32_t> d_blk_N, d_blk_T;
+  mtf::DevBuf<int64_t> d_blk_bt_off, d_blk_dof_off, d_blk_row_off;
+  std::vector<int64_t> reg_cta_prefix;       // regular-pair CTA prefix over blocks
+  mtf::DevBuf<int64_t> d_reg_cta_prefix;
+  mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
+};
+
+namespace mtf {
+struct GmresWork;
+}
+
+struct mtf_system_s {
+  mtf_mesh mesh = nullptr;
+  mtf_options opt{};
+  double k0 = 0;
+  std::vector<double> k_re, k_im, rho_re, rho_im;
+  mtf::DevBuf<double> d_k, d_rho;            // (re, im) per block
+  mtf::DevBuf<double> d_TK64;                // FP64: 4 doubles per dense entry
+  mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
+  mtf::DevBuf<double> d_xval;                // exchange values (6 per row)
+  mtf::DevBuf<double> d_ss_pts[3];           // Sauter-Schwab tables
+  int32_t ss_npts[3] = {0, 0, 0};
+  mtf::GmresWork* gw = nullptr;
+};
+
+namespace mtf {
+// kernel ids of the per-kernel accounting (profile.cpp)
+enum KernelId {
+  KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
+  KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
+  KID_MISC, KID_COUNT
+};
+void prof_begin(int kid, cudaStream_t s);
+void prof_end(int kid, cudaStream_t s);
+void prof_enable(bool on);
+void prof_read(int n, int64_t* launches, double* ms);
+const char* kernel_name(int kid);
+// launch a kernel with accounting: LAUNCH(kid, stream, kernel<<<...>>>(args))
+#define MTF_LAUNCH(kid, stream, ...)          \
+  do {                                        \
+    ::mtf::prof_begin((kid), (stream));       \
+    __VA_ARGS__;                              \
+    MTF_CUDA(cudaGetLastError());             \
+    ::mtf::prof_end((kid), (stream));         \
+  } while (0)
+
+void assemble_into(mtf_system sys, double k0, const double* eps_r, const double* mu_r, cudaStream_t s);
+// kernels launched from the host side (implemented in the .cu files)
+void launch_assemble(mtf_system sys, cudaStream_t s);
+void launch_exchange_values(mtf_system sys, cudaStream_t s);
+// y = M x; column c of x (y) starts at x + 2 c ldx (y + 2 c ldy) doubles.
+void launch_matvec(mtf_system sys, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs,
+                   cudaStream_t s);
+void launch_rhs(mtf_system sys, int nrhs, const double* d_dirs, const double* d_pols, double* b,
+                cudaStream_t s);
+void launch_farfield(mtf_system sys, const double* x, int nrhs, const double* d_obs, int nobs,
+                     double* f, cudaStream_t s);
+void launch_get_block(mtf_system sys, int i, double* t_out, double* k_out, cudaStream_t s);
+mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
+                 cudaStream_t s);
+void destroy_gmres(GmresWork* w);
+}  // namespace mtf

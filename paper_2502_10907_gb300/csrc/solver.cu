@@ -1,0 +1,307 @@
+// Restarted flexible GMRES for M u = b (Sec. 5.3: relative tolerance and an
+// iteration cap), batched over right-hand sides: every right-hand side has its
+// own Krylov basis, all of them advance together so that each operator apply
+// is one multi-column matvec.  Orthogonalisation is classical Gram-Schmidt
+// applied twice (CGS2) in FP64 on the device; the small Hessenberg least-
+// squares problems (Givens rotations) run on the host from the (j+2) new
+// Hessenberg entries per right-hand side copied back each iteration.  A
+// restart cycle ends on convergence of every right-hand side, on the restart
+// length or on the iteration cap; each cycle starts from the true residual
+// b - M x, which is also the stopping test.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+
+#include "common.h"
+
+namespace mtf {
+
+using cd = std::complex<double>;
+
+struct GmresWork {
+  int nrhs = 0, m = 0;
+  int64_t n = 0;
+  DevBuf<double> V, w, r, b, y;
+  DevBuf<double> h;  // [hA (m+1) x nrhs][hB (m+1) x nrhs][norm nrhs] complex
+  double* h_host = nullptr;
+  ~GmresWork() {
+    if (h_host) cudaFreeHost(h_host);
+  }
+};
+
+void destroy_gmres(GmresWork* w) { delete w; }
+
+// h[c*(ldh) + i] = <V_i^c, w^c> = sum conj(V) w  for i < j, one CTA per (i, c)
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, const double* __restrict__ w,
+                                              int64_t n, int ldv, double* __restrict__ h, int ldh) {
+  const int i = blockIdx.x, c = blockIdx.y;
+  const double2* v = reinterpret_cast<const double2*>(V) + (int64_t(c) * ldv + i) * n;
+  const double2* x = reinterpret_cast<const double2*>(w) + int64_t(c) * n;
+  double sr = 0, si = 0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 a = v[k], b = x[k];
+    sr += a.x * b.x + a.y * b.y;
+    si += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double red[2][8];
+  for (int s = 16; s > 0; s >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, s);
+    si += __shfl_xor_sync(0xffffffffu, si, s);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) {
+      a += red[0][q];
+      b += red[1][q];
+    }
+    h[2 * (int64_t(c) * ldh + i)] = a;
+    h[2 * (int64_t(c) * ldh + i) + 1] = b;
+  }
+}
+
+// w^c += sign * sum_{i<j} V_i^c h_i^c
+__global__ void k_axpy_multi(const double* __restrict__ V, const double* __restrict__ h, int j, int64_t n,
+                             int ldv, int ldh, double sign, double* __restrict__ w, int nrhs) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * nrhs) return;
+  const int c = int(t / n);
+  const int64_t k = t % n;
+  const double2* v = reinterpret_cast<const double2*>(V) + int64_t(c) * ldv * n + k;
+  const double* hc = h + 2 * int64_t(c) * ldh;
+  double sr = 0, si = 0;
+  for (int i = 0; i < j; ++i) {
+    const double2 a = v[int64_t(i) * n];
+    const double hr = hc[2 * i], hi = hc[2 * i + 1];
+    sr += a.x * hr - a.y * hi;
+    si += a.x * hi + a.y * hr;
+  }
+  double2* x = reinterpret_cast<double2*>(w) + int64_t(c) * n + k;
+  double2 o = *x;
+  o.x += sign * sr;
+  o.y += sign * si;
+  *x = o;
+}
+
+// nrm[c] = ||w^c||, out^c = w^c / nrm[c] (zero if nrm is 0); one CTA per c
+__global__ void __launch_bounds__(1024) k_norm_scale(const double* __restrict__ w, int64_t n,
+                                                      double* __restrict__ nrm, double* __restrict__ out,
+                                                      int64_t out_stride) {
+  const int c = blockIdx.x;
+  const double2* x = reinterpret_cast<const double2*>(w) + int64_t(c) * n;
+  double s = 0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s += x[k].x * x[k].x + x[k].y * x[k].y;
+  __shared__ double red[32];
+  __shared__ double tot;
+  for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) a += red[q];
+    tot = sqrt(a);
+    nrm[2 * c] = tot;
+    nrm[2 * c + 1] = 0.0;
+  }
+  __syncthreads();
+  const double inv = tot > 0 ? 1.0 / tot : 0.0;
+  double2* o = reinterpret_cast<double2*>(out) + int64_t(c) * out_stride;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) o[k] = make_double2(x[k].x * inv, x[k].y * inv);
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                      int64_t n2) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n2) out[t] = a[t] - b[t];
+}
+
+static inline unsigned nblk(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
+                 cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  mtf_mesh msh = sys->mesh;
+  const int64_t n = msh->n_total;
+  const int m = std::max(1, sys->opt.restart);
+  if (!sys->gw) sys->gw = new GmresWork();
+  GmresWork& G = *sys->gw;
+  if (G.nrhs != nrhs || G.m != m || G.n != n) {
+    G.V.alloc(size_t(m + 1) * n * nrhs * 2);
+    G.w.alloc(size_t(n) * nrhs * 2);
+    G.r.alloc(size_t(n) * nrhs * 2);
+    G.y.alloc(size_t(m + 1) * nrhs * 2);
+    G.h.alloc(size_t(2 * (m + 1) + 1) * nrhs * 2);
+    if (G.h_host) cudaFreeHost(G.h_host);
+    G.h_host = nullptr;
+    MTF_CUDA(cudaMallocHost(&G.h_host, G.h.n * sizeof(double)));
+    G.nrhs = nrhs;
+    G.m = m;
+    G.n = n;
+  }
+  double* hA = G.h.p;
+  double* hB = G.h.p + 2 * size_t(m + 1) * nrhs;
+  double* hN = G.h.p + 4 * size_t(m + 1) * nrhs;
+  double* hostA = G.h_host;
+  double* hostB = G.h_host + 2 * size_t(m + 1) * nrhs;
+  double* hostN = G.h_host + 4 * size_t(m + 1) * nrhs;
+  const int ldv = m + 1;
+  const size_t vec_bytes = size_t(n) * nrhs * 2 * sizeof(double);
+
+  // ||b|| per right-hand side
+  std::vector<double> bnorm(nrhs), rel(nrhs, 1.0);
+  MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(b_dev, n, hN, G.w.p, n));
+  MTF_CUDA(cudaMemcpyAsync(hostN, hN, size_t(nrhs) * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MTF_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < nrhs; ++c) bnorm[c] = hostN[2 * c] > 0 ? hostN[2 * c] : 1.0;
+  MTF_CUDA(cudaMemsetAsync(x_dev, 0, vec_bytes, s));
+
+  std::vector<int> done(nrhs, 0), iters(nrhs, 0), jc(nrhs, 0);
+  std::vector<cd> H(size_t(m + 1) * m * nrhs), g(size_t(m + 1) * nrhs), sn(size_t(m) * nrhs);
+  std::vector<double> cs(size_t(m) * nrhs);
+  std::vector<double> yhost(size_t(m + 1) * nrhs * 2);
+  int restarts = 0, total = 0;
+  bool first = true;
+  const int max_iter = std::max(1, sys->opt.max_iter);
+  const double tol = sys->opt.tol;
+  mtf_status status = MTF_OK;
+  while (true) {
+    // true residual r = b - M x and its norm; V_0 = r / ||r||
+    if (first) {
+      MTF_CUDA(cudaMemcpyAsync(G.r.p, b_dev, vec_bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+      launch_matvec(sys, x_dev, n, G.w.p, n, nrhs, s);
+      MTF_LAUNCH(KID_SUB, s, k_sub<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(b_dev, G.w.p, G.r.p, n * nrhs * 2));
+    }
+    first = false;
+    MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(G.r.p, n, hN, G.V.p, int64_t(ldv) * n));
+    MTF_CUDA(cudaMemcpyAsync(hostN, hN, size_t(nrhs) * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) {
+      rel[c] = hostN[2 * c] / bnorm[c];
+      if (!std::isfinite(rel[c])) status = MTF_ERR_NAN;
+      done[c] = rel[c] <= tol;
+      all = all && done[c];
+      jc[c] = 0;
+      std::fill(g.begin() + size_t(c) * (m + 1), g.begin() + size_t(c + 1) * (m + 1), cd(0));
+      g[size_t(c) * (m + 1)] = hostN[2 * c];
+    }
+    if (status != MTF_OK) break;
+    if (all) break;
+    if (total >= max_iter) {
+      status = MTF_ERR_NOCONV;
+      break;
+    }
+    ++restarts;
+    std::vector<int> active(nrhs);
+    for (int c = 0; c < nrhs; ++c) active[c] = !done[c];
+    int j = 0;
+    for (; j < m && total < max_iter; ++j) {
+      // w = M v_j  (right preconditioning hook: identity)
+      launch_matvec(sys, G.V.p + 2 * size_t(j) * n, int64_t(ldv) * n, G.r.p, n, nrhs, s);
+      // CGS2
+      dim3 gd(unsigned(j + 1), unsigned(nrhs));
+      MTF_LAUNCH(KID_DOTS, s, k_dots<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hA, m + 1));
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, hA, j + 1, n, ldv, m + 1, -1.0, G.r.p, nrhs));
+      MTF_LAUNCH(KID_DOTS, s, k_dots<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hB, m + 1));
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, hB, j + 1, n, ldv, m + 1, -1.0, G.r.p, nrhs));
+      // v_{j+1} = w / ||w||
+      MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(G.r.p, n, hN, G.V.p + 2 * size_t(j + 1) * n, int64_t(ldv) * n));
+      MTF_CUDA(cudaGetLastError());
+      MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, G.h.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MTF_CUDA(cudaStreamSynchronize(s));
+      ++total;
+      bool all_done = true;
+      for (int c = 0; c < nrhs; ++c) {
+        if (!active[c]) continue;
+        cd* Hc = &H[size_t(c) * (m + 1) * m + size_t(j) * (m + 1)];
+        for (int q = 0; q <= j; ++q)
+          Hc[q] = cd(hostA[2 * (size_t(c) * (m + 1) + q)] + hostB[2 * (size_t(c) * (m + 1) + q)],
+                     hostA[2 * (size_t(c) * (m + 1) + q) + 1] + hostB[2 * (size_t(c) * (m + 1) + q) + 1]);
+        Hc[j + 1] = cd(hostN[2 * c], 0.0);
+        // previous rotations
+        for (int q = 0; q < j; ++q) {
+          const double cq = cs[size_t(c) * m + q];
+          const cd sq = sn[size_t(c) * m + q];
+          const cd t = cq * Hc[q] + sq * Hc[q + 1];
+          Hc[q + 1] = -std::conj(sq) * Hc[q] + cq * Hc[q + 1];
+          Hc[q] = t;
+        }
+        // new rotation zeroing H[j+1, j]
+        const cd a = Hc[j], bb = Hc[j + 1];
+        const double an = std::abs(a), bn = std::abs(bb), tt = std::hypot(an, bn);
+        double cj;
+        cd sj;
+        if (tt == 0) {
+          cj = 1.0;
+          sj = 0.0;
+        } else if (an == 0) {
+          cj = 0.0;
+          sj = std::conj(bb) / tt;
+          Hc[j] = tt;
+        } else {
+          cj = an / tt;
+          sj = (a / an) * std::conj(bb) / tt;
+          Hc[j] = (a / an) * tt;
+        }
+        Hc[j + 1] = 0.0;
+        cs[size_t(c) * m + j] = cj;
+        sn[size_t(c) * m + j] = sj;
+        cd* gc = &g[size_t(c) * (m + 1)];
+        gc[j + 1] = -std::conj(sj) * gc[j];
+        gc[j] = cj * gc[j];
+        jc[c] = j + 1;
+        ++iters[c];
+        const double est = std::abs(gc[j + 1]) / bnorm[c];
+        if (!std::isfinite(est)) status = MTF_ERR_NAN;
+        if (est <= tol * 0.5 || hostN[2 * c] == 0.0) active[c] = 0;
+        all_done = all_done && !active[c];
+      }
+      if (status != MTF_OK || all_done) {
+        ++j;
+        break;
+      }
+    }
+    if (status != MTF_OK) break;
+    // x += V y, y = R^{-1} g per right-hand side
+    std::fill(yhost.begin(), yhost.end(), 0.0);
+    int jmax = 0;
+    for (int c = 0; c < nrhs; ++c) {
+      const int jj = jc[c];
+      jmax = std::max(jmax, jj);
+      const cd* Hc = &H[size_t(c) * (m + 1) * m];
+      std::vector<cd> yy(jj);
+      for (int q = jj - 1; q >= 0; --q) {
+        cd acc = g[size_t(c) * (m + 1) + q];
+        for (int p = q + 1; p < jj; ++p) acc -= Hc[size_t(p) * (m + 1) + q] * yy[p];
+        yy[q] = acc / Hc[size_t(q) * (m + 1) + q];
+      }
+      for (int q = 0; q < jj; ++q) {
+        yhost[2 * (size_t(c) * (m + 1) + q)] = yy[q].real();
+        yhost[2 * (size_t(c) * (m + 1) + q) + 1] = yy[q].imag();
+      }
+    }
+    if (jmax > 0) {
+      MTF_CUDA(cudaMemcpyAsync(G.y.p, yhost.data(), yhost.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, G.y.p, jmax, n, ldv, m + 1, 1.0, x_dev, nrhs));
+      MTF_CUDA(cudaGetLastError());
+      MTF_CUDA(cudaStreamSynchronize(s));  // yhost is reused next cycle
+    }
+  }
+  if (st) {
+    st->iterations = *std::max_element(iters.begin(), iters.end());
+    st->restarts = restarts;
+    st->refinements = 0;
+    st->converged = status == MTF_OK;
+    st->rel_residual = *std::max_element(rel.begin(), rel.end());
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+}  // namespace mtf

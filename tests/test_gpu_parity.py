@@ -1,0 +1,144 @@
+"""GPU (FP64 path) vs oracle parity through the C-ABI.
+
+Tolerance: relative 1e-10 for the FP64 path (norm-wise, ||gpu - ref|| /
+||ref||), the bound stated for the exact path.  Small cases compare every
+output element; the full-size split-sphere workload compares sampled full
+matrix rows and sampled rows of M x that the oracle computes one by one."""
+import numpy as np
+import pytest
+import torch
+
+import mtf_inputs as mi
+from oracle.mtf import MTFSystem
+from oracle.operators import block_rows, transmission_gram
+from tests.oracle_helpers import skeleton_of, sphere_system, rcs_plane
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2502_10907_gb300.build import build
+    build()
+    from paper_2502_10907_gb300 import api as A
+    return A
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def _case(cache, name):
+    if ("gpucase", name) in cache:
+        return cache[("gpucase", name)]
+    if name == "sphere":
+        cfg, sk, ref = sphere_system(cache, 2)
+    elif name == "split":
+        cfg = mi.config_split_sphere(rings=4, k0=2.0)
+        sk = skeleton_of(cfg["mesh"])
+        ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    elif name == "cubes":
+        cfg = mi.config_cube2(n=2, k0=3.0, n_dirs=3)
+        sk = skeleton_of(cfg["mesh"])
+        ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    cache[("gpucase", name)] = (cfg, sk, ref)
+    return cfg, sk, ref
+
+
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+def test_blocks_match_oracle(api, oracle_cache, name):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    for i in range(sk.n_domains):
+        T, K = (t.cpu().numpy() for t in sysg.block(i))
+        assert rel(T, ref.T[i]) < TOL, (i, rel(T, ref.T[i]))
+        assert rel(K, ref.K[i]) < TOL, (i, rel(K, ref.K[i]))
+
+
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_matvec_and_rhs_match_oracle(api, oracle_cache, name, nrhs):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    rng = np.random.default_rng(nrhs)
+    x = rng.standard_normal((nrhs, sk.n_total)) + 1j * rng.standard_normal((nrhs, sk.n_total))
+    y = sysg.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    yr = ref.matvec(x.T).T
+    assert rel(y, yr) < TOL
+    dirs, pols = mi.plane_wave_batch(max(1, nrhs // 2))
+    dirs, pols = dirs[:nrhs], pols[:nrhs]
+    if len(dirs) < nrhs:
+        dirs, pols = np.repeat(dirs, nrhs, 0)[:nrhs], np.repeat(pols, nrhs, 0)[:nrhs]
+    b = sysg.rhs(dirs, pols).cpu().numpy()
+    assert rel(b, ref.rhs(dirs, pols).T) < TOL
+
+
+@pytest.mark.parametrize("name", ["sphere", "split"])
+def test_solve_and_farfield_match_oracle_lu(api, oracle_cache, name):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-12, restart=2000, max_iter=4000)
+    x, st = sysg.solve(cfg["dirs"], cfg["pols"])
+    xr = ref.solve_lu(ref.rhs(cfg["dirs"], cfg["pols"]))
+    assert st.converged == 1 and st.rel_residual <= 1e-12
+    assert rel(x.cpu().numpy().T, xr) < TOL
+    obs = rcs_plane(37)
+    f = sysg.farfield(x, obs).cpu().numpy()          # (nrhs, nobs, 3)
+    fr = ref.farfield(xr, obs).transpose(2, 0, 1)
+    assert rel(f, fr) < TOL
+
+
+def test_degenerate_inputs_are_rejected(api, oracle_cache):
+    from paper_2502_10907_gb300 import _lib as L
+    cfg, sk, ref = _case(oracle_cache, "sphere")
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    x = torch.zeros((1, sk.n_total), dtype=torch.complex128, device="cuda")
+    with pytest.raises(L.MtfError):
+        L.mtf_matvec(sysg.handle, x, x, 1)            # aliasing
+    y = torch.empty_like(x)
+    with pytest.raises(L.MtfError):
+        L.mtf_matvec(sysg.handle, x, y, 0)            # empty batch
+    with pytest.raises(L.MtfError):
+        sysg.rhs(np.array([[0.0, 0.0, 2.0]]), np.array([[1.0, 0, 0]], dtype=complex))  # not unit
+    with pytest.raises(L.MtfError):
+        api.System(mesh, -1.0, cfg["eps_r"], cfg["mu_r"])
+    # zero incident field -> zero solution, converged at once
+    xs, st = sysg.solve(np.array([[0.0, 0.0, 1.0]]), np.zeros((1, 3), dtype=complex))
+    assert st.converged == 1 and float(xs.abs().max()) == 0.0
+
+
+def test_full_size_split_sphere_sampled_rows(api):
+    """Split sphere, 2178 skeleton triangles (the benchmark workload), in
+    the benchmark's launch configuration: sampled full rows of T_i, K_i and
+    sampled rows of M x against the oracle."""
+    cfg = mi.config_split_sphere()
+    sk = skeleton_of(cfg["mesh"])
+    ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"], assemble=False)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((2, sk.n_total)) + 1j * rng.standard_normal((2, sk.n_total))
+    y = sysg.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    for i in range(sk.n_domains):
+        rows = np.sort(rng.choice(sk.N[i], 3, replace=False))
+        rows[0] = 0
+        Tr, Kr = block_rows(sk, i, ref.k[i], rows)
+        T, K = (t.cpu().numpy()[rows] for t in sysg.block(i))
+        assert rel(T, Tr) < TOL and rel(K, Kr) < TOL
+        Di, Ni = sk.block_slices(i)
+        r = ref.rho[i]
+        yD = 2 * (Kr @ x[:, Di].T + (Tr @ x[:, Ni].T) / r)
+        yN = 2 * (-r * (Tr @ x[:, Di].T) + Kr @ x[:, Ni].T)
+        for j in sk.Lambda[i]:
+            Gij = transmission_gram(sk, i, j)[rows]
+            Dj, Nj = sk.block_slices(j)
+            yD += Gij @ x[:, Dj].T
+            yN += Gij @ x[:, Nj].T
+        assert rel(y[:, Di][:, rows], yD.T) < TOL
+        assert rel(y[:, Ni][:, rows], yN.T) < TOL
