@@ -217,6 +217,9 @@ def main():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--no-accuracy-gate", action="store_true",
+                    help="skip the tight-tolerance FP64 reference solve (profiling runs)")
     args = ap.parse_args()
     cfg = workload(args.workload)
     if args.impl == "reference":
@@ -245,12 +248,14 @@ def main():
     counts = mesh.pair_counts()
     n_pairs = int(counts.sum())
     sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                      precision=prec)
+                      precision=prec, max_iter=args.max_iter)
     # accuracy gate: FP64 solution at tight tolerance (the FP64 path is pinned
     # to the oracle at 1e-10 by the parity tests)
-    ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=300)
-    x_ref, st_ref = ref_sys.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
-    del ref_sys
+    x_ref, st_ref = None, None
+    if not args.no_accuracy_gate:
+        ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=300, max_iter=4000)
+        x_ref, st_ref = ref_sys.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        del ref_sys
     stream = torch.cuda.current_stream()
 
     def step():
@@ -285,7 +290,7 @@ def main():
         ms = float(t.item())
     nrhs = len(cfg["dirs"])
     value = world * nrhs / (ms / 1e3)
-    err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max())
+    err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
     # assembly alone (device-timed)
     torch.cuda.synchronize()
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -341,7 +346,7 @@ def main():
         t0 = time.perf_counter()
         mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
         sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                        precision=prec)
+                        precision=prec, max_iter=args.max_iter)
         xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
         fe = sh.farfield(xe, cfg["obs"])
         xh, fh = xe.cpu(), fe.cpu()
@@ -368,7 +373,8 @@ def main():
             "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},
             "solution_rel_err_vs_fp64": err,
             "gmres_iterations": int(statistics.median(iters)),
-            "converged": bool(st.converged), "reference_converged": bool(st_ref.converged),
+            "converged": bool(st.converged),
+            "reference_converged": bool(st_ref.converged) if st_ref is not None else None,
             "gpu_launches": int(launches),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
             "roofline": roof,
