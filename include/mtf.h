@@ -180,6 +180,31 @@ mtf_status mtf_rhs(mtf_system sys, int32_t nrhs, const double* dirs, const doubl
 mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
                      void* x_out, mtf_solve_stats* stats, void* stream);
 
+/* mtf_solve without device allocation (the paper has no counterpart; this
+ * is an interface for callers that cannot allocate).  Some callers must not
+ * call cudaMalloc while they run: code working inside a fixed, pre-reserved
+ * memory budget that a late allocation could exhaust, or a serving loop /
+ * host callback where cudaMalloc may implicitly synchronise the device and
+ * stall other work.  This entry point computes exactly what mtf_solve
+ * computes (same kernels, same arithmetic) but takes every device buffer it
+ * needs -- right-hand sides, Krylov basis, work vectors, Hessenberg columns,
+ * wave parameters -- from one static device array of 16 MiB that every GPU
+ * loading the library holds until the process exits.  The caller still
+ * provides x_out.
+ *   Limit: 2 n_total nrhs (restart + 4) + 6 nrhs (restart + 2) + 9 nrhs + 64
+ *   doubles must fit in 2^21 doubles; larger requests fail with MTF_ERR_ARG
+ *   and a message giving both numbers.
+ *   Set-up: the first call on each device (with that device current) looks
+ *   up the array's device address; make that first call before any stream
+ *   capture.
+ *   Sharing: every call on a device uses the same array and leaves its
+ *   contents behind (each call clears the part it uses first).  Calls whose
+ *   GPU work overlaps -- on different streams or from different threads --
+ *   race on the array and give wrong results; serialise them.
+ * Arguments, results and errors are those of mtf_solve. */
+mtf_status mtf_solve_static(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
+                            void* x_out, mtf_solve_stats* stats, void* stream);
+
 /* Far field E_inf(xhat) of solutions x (device complex128 n_total x nrhs) at
  * n_obs unit directions obs_dirs (host, n_obs * 3 doubles):
  * E_inf = i k0 / (4 pi) [xhat x w_D + (xhat x w_N) x xhat],

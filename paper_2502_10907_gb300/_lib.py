@@ -56,6 +56,7 @@ _SIGS = {
     "mtf_matvec": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_rhs": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
+    "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_farfield": (_i32, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "mtf_system_destroy": (None, [_vp]),
     "mtf_status_string": (ctypes.c_char_p, [_i32]),
@@ -191,6 +192,18 @@ def mtf_solve(sys_, dirs, pols, x_out, stream=0, raise_on_noconv=True):
     p = np.ascontiguousarray(pols, dtype=np.complex128)
     st = mtf_solve_stats()
     status = load().mtf_solve(sys_, len(d), _ptr(d), _ptr(p), _ptr(x_out), ctypes.byref(st), stream or None)
+    if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
+        _check(status)
+    return st, status
+
+
+def mtf_solve_static(sys_, dirs, pols, x_out, stream=0, raise_on_noconv=True):
+    """mtf_solve that allocates no device memory (static 16 MiB workspace)."""
+    d = np.ascontiguousarray(dirs, dtype=np.float64)
+    p = np.ascontiguousarray(pols, dtype=np.complex128)
+    st = mtf_solve_stats()
+    status = load().mtf_solve_static(sys_, len(d), _ptr(d), _ptr(p), _ptr(x_out), ctypes.byref(st),
+                                     stream or None)
     if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
         _check(status)
     return st, status
