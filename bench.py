@@ -212,9 +212,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="split_sphere")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="osrc", choices=["none", "osrc"])
     ap.add_argument("--tol", type=float, default=1e-7)
-    ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--restart", type=int, default=500)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=2000)
@@ -243,17 +244,19 @@ def main():
             dist.barrier()
 
     prec = L.MTF_PREC_FP64 if args.precision == "fp64" else L.MTF_PREC_MIXED
+    pc = L.MTF_PRECOND_OSRC if args.precond == "osrc" else L.MTF_PRECOND_NONE
     m = cfg["mesh"]
     mesh = api.Mesh.from_inputs(m)
     counts = mesh.pair_counts()
     n_pairs = int(counts.sum())
     sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                      precision=prec, max_iter=args.max_iter)
+                      precision=prec, max_iter=args.max_iter, precond=pc)
     # accuracy gate: FP64 solution at tight tolerance (the FP64 path is pinned
     # to the oracle at 1e-10 by the parity tests)
     x_ref, st_ref = None, None
     if not args.no_accuracy_gate:
-        ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=300, max_iter=4000)
+        ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=args.restart,
+                             max_iter=4000, precond=L.MTF_PRECOND_OSRC)
         x_ref, st_ref = ref_sys.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
         del ref_sys
     stream = torch.cuda.current_stream()
@@ -346,7 +349,7 @@ def main():
         t0 = time.perf_counter()
         mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
         sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                        precision=prec, max_iter=args.max_iter)
+                        precision=prec, max_iter=args.max_iter, precond=pc)
         xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
         fe = sh.farfield(xe, cfg["obs"])
         xh, fh = xe.cpu(), fe.cpu()
@@ -367,7 +370,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if prec == L.MTF_PREC_FP64 else "f32+f64",
             "data": "synthetic",
             "config": {"workload": cfg["desc"], "nrhs": nrhs, "n_unknowns": int(mesh.n_total),
-                       "triangle_pairs": n_pairs, "precision": args.precision, "gmres_tol": args.tol,
+                       "triangle_pairs": n_pairs, "precision": args.precision, "preconditioner": args.precond, "gmres_tol": args.tol,
                        "restart": args.restart, "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
                        "parallelism": f"replicas x{world}"},
             "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},

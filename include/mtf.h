@@ -164,6 +164,16 @@ mtf_status mtf_get_block(mtf_system sys, int32_t i, void* t_out, void* k_out, vo
  * n_total x nrhs, must not overlap. */
 mtf_status mtf_matvec(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream);
 
+/* z = A~ r: the block-OSRC preconditioner of Sec. 4.4 (Eq. 19),
+ * A~_i = [[0, rho_i^-1 T~], [-rho_i T~, 0]] per block, with T~ the Pade
+ * OSRC approximation of the EtM map (order opt.osrc_np, branch-cut angle
+ * opt.osrc_theta, damped wavenumber k_i + i eps_i) evaluated on the
+ * spectral decomposition of the block's RWG div-div / mass pencil.  Maps
+ * tested residual vectors to coefficient vectors.  r, z: device complex128
+ * n_total x nrhs, must not overlap.  Requires opt.precond == MTF_PRECOND_OSRC
+ * at assembly (MTF_ERR_ARG otherwise). */
+mtf_status mtf_precond_apply(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream);
+
 /* Right-hand side of Problem 2 for plane waves E_inc = p exp(i k0 d.x)
  * (Eq. 22): block 0 holds -2 <gamma_{.,0} E_inc, psi_m>_x for the D and N
  * slots (sign from the Calderon identities of Eq. 10 with n_0), all other
@@ -201,7 +211,8 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
  *   contents behind (each call clears the part it uses first).  Calls whose
  *   GPU work overlaps -- on different streams or from different threads --
  *   race on the array and give wrong results; serialise them.
- * Arguments, results and errors are those of mtf_solve. */
+ * Only systems assembled with MTF_PREC_FP64 are accepted (MTF_ERR_ARG
+ * otherwise).  Arguments, results and errors are those of mtf_solve. */
 mtf_status mtf_solve_static(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
                             void* x_out, mtf_solve_stats* stats, void* stream);
 

@@ -54,6 +54,7 @@ _SIGS = {
     "mtf_kernel_name": (ctypes.c_char_p, [_i32]),
     "mtf_get_block": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "mtf_matvec": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "mtf_precond_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_rhs": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
@@ -179,6 +180,10 @@ def mtf_get_block(sys_, i, t_out, k_out, stream=0):
 
 def mtf_matvec(sys_, x, y, nrhs, stream=0):
     _check(load().mtf_matvec(sys_, _ptr(x), _ptr(y), int(nrhs), stream or None))
+
+
+def mtf_precond_apply(sys_, r, z, nrhs, stream=0):
+    _check(load().mtf_precond_apply(sys_, _ptr(r), _ptr(z), int(nrhs), stream or None))
 
 
 def mtf_rhs(sys_, dirs, pols, b_out, stream=0):

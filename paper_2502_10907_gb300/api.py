@@ -63,6 +63,12 @@ class System:
         L.mtf_matvec(self.handle, x, y, x.shape[0], _stream())
         return y
 
+    def precond(self, r):
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        L.mtf_precond_apply(self.handle, r, z, r.shape[0], _stream())
+        return z
+
     def rhs(self, dirs, pols):
         b = torch.empty((len(dirs), self.mesh.n_total), dtype=torch.complex128, device="cuda")
         L.mtf_rhs(self.handle, dirs, pols, b, _stream())

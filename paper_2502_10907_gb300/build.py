@@ -64,7 +64,9 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
             if p.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
     if jobs or not os.path.exists(LIB):
-        cmd = [nv, *ARCH, "-shared", "-o", LIB, *objs]
+        libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
+        cmd = [nv, *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver", "-L", libdir,
+               "-Xlinker", "-rpath", "-Xlinker", libdir]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             sys.stderr.write(p.stdout + p.stderr)

@@ -12,16 +12,50 @@
 
 namespace mtf {
 
-struct C2m {
-  double re, im;
+template <class MatT>
+struct Entry;
+template <>
+struct Entry<double> {
+  // (T.re, T.im, K.re, K.im) as two 16-byte loads
+  static __device__ __forceinline__ void load(const double* row, int n, double& tr, double& ti, double& kr,
+                                              double& ki) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(row) + 2 * n);
+    const double2 b = __ldg(reinterpret_cast<const double2*>(row) + 2 * n + 1);
+    tr = a.x; ti = a.y; kr = b.x; ki = b.y;
+  }
+};
+template <>
+struct Entry<float> {
+  static __device__ __forceinline__ void load(const float* row, int n, float& tr, float& ti, float& kr,
+                                              float& ki) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(row) + n);
+    tr = a.x; ti = a.y; kr = a.z; ki = a.w;
+  }
 };
 
-__global__ void __launch_bounds__(256) k_matvec64(
-    const double* __restrict__ TK, const XEntry* __restrict__ xe, const double* __restrict__ xval,
+template <class VecT>
+struct VecLoad;
+template <>
+struct VecLoad<double> {
+  static __device__ __forceinline__ double2 ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
+};
+template <>
+struct VecLoad<float> {
+  static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+};
+
+// MatT: storage precision of the (T, K) blocks; AccT: arithmetic and
+// accumulation precision; VecT: precision of the dense-part input vector xv
+// (an FP32 copy of x on the FP32 path, so that no FP64 conversion sits in the
+// inner loop).  The exchange part and the output are FP64.
+template <class MatT, class AccT, class VecT>
+__global__ void __launch_bounds__(256) k_matvec(
+    const MatT* __restrict__ TK, const XEntry* __restrict__ xe, const double* __restrict__ xval,
     const int32_t* __restrict__ row_blk, const int64_t* __restrict__ blk_row_off,
     const int32_t* __restrict__ blk_N, const int64_t* __restrict__ blk_dof_off,
     const int64_t* __restrict__ blk_mat_off, const double* __restrict__ rho, const double* __restrict__ x,
-    int64_t ldx, double* __restrict__ y, int64_t ldy, int nrhs, int64_t n_rows) {
+    int64_t ldx, const VecT* __restrict__ xv, int64_t ldxv, double* __restrict__ y, int64_t ldy, int nrhs,
+    int64_t n_rows) {
   const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= n_rows) return;
@@ -29,35 +63,49 @@ __global__ void __launch_bounds__(256) k_matvec64(
   const int64_t m = r - blk_row_off[i];
   const int N = blk_N[i];
   const int64_t off = blk_dof_off[i];
-  const double2* row = reinterpret_cast<const double2*>(TK + 4 * (blk_mat_off[i] + m * N));
+  const MatT* row = TK + 4 * (blk_mat_off[i] + m * N);
   const double rr = rho[2 * i], ri = rho[2 * i + 1];
   const double rn = rr * rr + ri * ri;
   const double ir = rr / rn, ii = -ri / rn;  // 1 / rho
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     const int nc = min(4, nrhs - c0);
-    double acc[4][8];
+    AccT acc[4][8];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[c][q] = 0.0;
-    for (int n = lane; n < N; n += 32) {
-      const double2 t2 = __ldg(row + 2 * n), k2 = __ldg(row + 2 * n + 1);
-      const double4 tk = make_double4(t2.x, t2.y, k2.x, k2.y);
+      for (int q = 0; q < 8; ++q) acc[c][q] = AccT(0);
+    // U row entries per lane in flight: the loads of a group are issued
+    // before any of their arithmetic (latency hiding for the HBM stream)
+    constexpr int U = sizeof(MatT) == 4 ? 4 : 2;
+    for (int n0 = lane; n0 < N; n0 += 32 * U) {
+      MatT e[U][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c < nc) {
-          const double* xc = x + 2 * (int64_t(c0 + c) * ldx + off);
-          const double2 xd = *reinterpret_cast<const double2*>(xc + 2 * n);
-          const double2 xn = *reinterpret_cast<const double2*>(xc + 2 * (N + n));
-          // T xd, T xn, K xd, K xn
-          acc[c][0] += tk.x * xd.x - tk.y * xd.y;
-          acc[c][1] += tk.x * xd.y + tk.y * xd.x;
-          acc[c][2] += tk.x * xn.x - tk.y * xn.y;
-          acc[c][3] += tk.x * xn.y + tk.y * xn.x;
-          acc[c][4] += tk.z * xd.x - tk.w * xd.y;
-          acc[c][5] += tk.z * xd.y + tk.w * xd.x;
-          acc[c][6] += tk.z * xn.x - tk.w * xn.y;
-          acc[c][7] += tk.z * xn.y + tk.w * xn.x;
+      for (int u = 0; u < U; ++u) {
+        const int n = n0 + 32 * u;
+        if (n < N) Entry<MatT>::load(row, n, e[u][0], e[u][1], e[u][2], e[u][3]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int n = n0 + 32 * u;
+        if (n >= N) break;
+        const AccT Tr = AccT(e[u][0]), Ti = AccT(e[u][1]), Kr = AccT(e[u][2]), Ki = AccT(e[u][3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < nc) {
+            const VecT* xc = xv + 2 * (int64_t(c0 + c) * ldxv + off);
+            const auto xd2 = VecLoad<VecT>::ld(xc + 2 * n);
+            const auto xn2 = VecLoad<VecT>::ld(xc + 2 * (N + n));
+            const AccT xdr = AccT(xd2.x), xdi = AccT(xd2.y), xnr = AccT(xn2.x), xni = AccT(xn2.y);
+            // T xd, T xn, K xd, K xn
+            acc[c][0] += Tr * xdr - Ti * xdi;
+            acc[c][1] += Tr * xdi + Ti * xdr;
+            acc[c][2] += Tr * xnr - Ti * xni;
+            acc[c][3] += Tr * xni + Ti * xnr;
+            acc[c][4] += Kr * xdr - Ki * xdi;
+            acc[c][5] += Kr * xdi + Ki * xdr;
+            acc[c][6] += Kr * xnr - Ki * xni;
+            acc[c][7] += Kr * xni + Ki * xnr;
+          }
         }
       }
     }
@@ -65,20 +113,20 @@ __global__ void __launch_bounds__(256) k_matvec64(
     for (int c = 0; c < 4; ++c)
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        double v = acc[c][q];
+        AccT v = acc[c][q];
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
         acc[c][q] = v;
       }
     if (lane < nc) {
-      // each of the first nc lanes finishes one right-hand side
+      // each of the first nc lanes finishes one right-hand side (in FP64)
       double a[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        a[q] = acc[0][q];
+        a[q] = double(acc[0][q]);
 #pragma unroll
         for (int c = 1; c < 4; ++c)
-          if (lane == c) a[q] = acc[c][q];
+          if (lane == c) a[q] = double(acc[c][q]);
       }
       const int col = c0 + lane;
       const double* xc = x + 2 * int64_t(col) * ldx;
@@ -106,14 +154,44 @@ __global__ void __launch_bounds__(256) k_matvec64(
   }
 }
 
+__global__ void k_to_f32(const double* __restrict__ x, int64_t ldx, int64_t n2, int nrhs, float* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n2 * nrhs) return;
+  const int64_t c = t / n2, k = t % n2;
+  out[t] = float(x[2 * c * ldx + k]);
+}
+
+void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, double* y, int64_t ldy,
+                        int nrhs, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  const unsigned blocks = unsigned((m->n_rows * 32 + 255) / 256);
+  if (kind == MV_AUTO) kind = sys->opt.precision == MTF_PREC_FP64 ? MV_FP64 : MV_FP32;
+  if (kind == MV_FP64) {
+    MTF_LAUNCH(KID_MATVEC64, s, k_matvec<double, double, double><<<blocks, 256, 0, s>>>(
+        sys->d_TK64.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
+        m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, x, ldx, y, ldy, nrhs, m->n_rows));
+  } else if (kind == MV_FP32) {
+    const int64_t n2 = 2 * m->n_total;
+    if (sys->d_x32.n < size_t(n2) * nrhs) sys->d_x32.alloc(size_t(n2) * nrhs);
+    MTF_LAUNCH(KID_MISC, s, k_to_f32<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(x, ldx, n2, nrhs, sys->d_x32.p));
+    MTF_LAUNCH(KID_MATVEC32, s, k_matvec<float, float, float><<<blocks, 256, 0, s>>>(
+        sys->d_TK32.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
+        m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, sys->d_x32.p, m->n_total, y, ldy, nrhs,
+        m->n_rows));
+  } else {
+    MTF_LAUNCH(KID_MATVEC64, s, k_matvec<float, double, double><<<blocks, 256, 0, s>>>(
+        sys->d_TK32.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
+        m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, x, ldx, y, ldy, nrhs, m->n_rows));
+  }
+}
+
+// y = M x with the operator as stored: FP64 storage and arithmetic on the FP64
+// path; FP32 storage with FP64 accumulation (the refinement residual) on the
+// mixed path.
 void launch_matvec(mtf_system sys, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs,
                    cudaStream_t s) {
-  mtf_mesh m = sys->mesh;
-  const int64_t threads = m->n_rows * 32;
-  MTF_LAUNCH(KID_MATVEC64, s, k_matvec64<<<unsigned((threads + 255) / 256), 256, 0, s>>>(
-      sys->d_TK64.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
-      m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, y, ldy, nrhs, m->n_rows));
-  MTF_CUDA(cudaGetLastError());
+  launch_matvec_kind(sys, sys->opt.precision == MTF_PREC_FP64 ? MV_FP64 : MV_FP32_ACC64, x, ldx, y, ldy,
+                     nrhs, s);
 }
 
 }  // namespace mtf

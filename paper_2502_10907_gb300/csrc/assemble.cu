@@ -25,7 +25,7 @@
 
 namespace mtf {
 
-__constant__ double c_tri_s[6], c_tri_t[6], c_tri_w[6];
+__constant__ double c_tri_s[6], c_tri_t[6], c_tri_w[6];  // 6-point rule
 
 #define INV_FOUR_PI 0.079577471545947667884
 
@@ -111,6 +111,9 @@ __device__ __forceinline__ void add_entry(double* TK, int64_t idx, C2 T, C2 K) {
   atomicAdd(e + 1, T.im);
   atomicAdd(e + 2, K.re);
   atomicAdd(e + 3, K.im);
+}
+__device__ __forceinline__ void add_entry(float* TK, int64_t idx, C2 T, C2 K) {
+  atomicAdd(reinterpret_cast<float4*>(TK) + idx, make_float4(float(T.re), float(T.im), float(K.re), float(K.im)));
 }
 
 // ---------------------------------------------------------------------------
@@ -248,11 +251,12 @@ __global__ void __launch_bounds__(128) k_regular64(BlockArgs A, const int64_t* _
 // ---------------------------------------------------------------------------
 // singular pairs (Sauter-Schwab), FP64: one warp per pair
 // ---------------------------------------------------------------------------
+template <class OutT>
 __global__ void __launch_bounds__(256) k_singular64(BlockArgs A, const SingPair* __restrict__ sp,
                                                     int64_t npairs, const double* __restrict__ ss0,
                                                     const double* __restrict__ ss1,
                                                     const double* __restrict__ ss2, int n0, int n1,
-                                                    int n2, double* __restrict__ TK) {
+                                                    int n2, OutT* __restrict__ TK) {
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= npairs) return;
@@ -502,7 +506,8 @@ __global__ void __launch_bounds__(256) k_farfield(const double* __restrict__ x, 
   }
 }
 
-__global__ void k_split_block(const double* __restrict__ TK, int64_t n, double* __restrict__ T,
+template <class MatT>
+__global__ void k_split_block(const MatT* __restrict__ TK, int64_t n, double* __restrict__ T,
                               double* __restrict__ K) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -552,19 +557,28 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
       sys->ss_npts[kind] = int(pts.size() / 5);
     }
   }
-  sys->d_TK64.alloc(size_t(m->n_mat) * 4);
-  MTF_CUDA(cudaMemsetAsync(sys->d_TK64.p, 0, size_t(m->n_mat) * 4 * sizeof(double), s));
   BlockArgs A = block_args(sys);
-  const int64_t nct = m->reg_cta_prefix.back();
-  if (nct > 0) MTF_LAUNCH(KID_REGULAR64, s, k_regular64<<<unsigned(nct), 128, 0, s>>>(A, m->d_reg_cta_prefix.p, sys->d_TK64.p));
-  MTF_CUDA(cudaGetLastError());
   const int64_t np = int64_t(m->sing.size());
-  if (np > 0) {
-    const int64_t threads = np * 32;
-    MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<<<unsigned((threads + 255) / 256), 256, 0, s>>>(
-        A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
-        sys->ss_npts[1], sys->ss_npts[2], sys->d_TK64.p));
-    MTF_CUDA(cudaGetLastError());
+  const unsigned sblocks = unsigned((np * 32 + 255) / 256);
+  if (sys->opt.precision == MTF_PREC_FP64) {
+    sys->d_TK64.alloc(size_t(m->n_mat) * 4);
+    MTF_CUDA(cudaMemsetAsync(sys->d_TK64.p, 0, size_t(m->n_mat) * 4 * sizeof(double), s));
+    const int64_t nct = m->reg_cta_prefix.back();
+    if (nct > 0)
+      MTF_LAUNCH(KID_REGULAR64, s, k_regular64<<<unsigned(nct), 128, 0, s>>>(A, m->d_reg_cta_prefix.p, sys->d_TK64.p));
+    if (np > 0)
+      MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<double><<<sblocks, 256, 0, s>>>(
+          A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
+          sys->ss_npts[1], sys->ss_npts[2], sys->d_TK64.p));
+  } else {
+    // mixed: FP32 storage; regular pairs in FP32, singular pairs in FP64
+    sys->d_TK32.alloc(size_t(m->n_mat) * 4);
+    MTF_CUDA(cudaMemsetAsync(sys->d_TK32.p, 0, size_t(m->n_mat) * 4 * sizeof(float), s));
+    launch_assemble_regular32(sys, s);
+    if (np > 0)
+      MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<float><<<sblocks, 256, 0, s>>>(
+          A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
+          sys->ss_npts[1], sys->ss_npts[2], sys->d_TK32.p));
   }
   launch_exchange_values(sys, s);
 }
@@ -603,8 +617,13 @@ void launch_farfield(mtf_system sys, const double* x, int nrhs, const double* d_
 void launch_get_block(mtf_system sys, int i, double* t_out, double* k_out, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   const int64_t n = int64_t(m->blk[i].N) * m->blk[i].N;
-  const double* src = sys->d_TK64.p + 4 * m->blk[i].mat_off;
-  MTF_LAUNCH(KID_SPLIT, s, k_split_block<<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, t_out, k_out));
+  if (sys->opt.precision == MTF_PREC_FP64) {
+    const double* src = sys->d_TK64.p + 4 * m->blk[i].mat_off;
+    MTF_LAUNCH(KID_SPLIT, s, k_split_block<double><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, t_out, k_out));
+  } else {
+    const float* src = sys->d_TK32.p + 4 * m->blk[i].mat_off;
+    MTF_LAUNCH(KID_SPLIT, s, k_split_block<float><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, n, t_out, k_out));
+  }
   MTF_CUDA(cudaGetLastError());
 }
 

@@ -66,6 +66,7 @@ void assemble_into(mtf_system sys, double k0, const double* eps_r, const double*
   upload_small(sys->d_k, kk.data(), kk.size(), s);
   upload_small(sys->d_rho, rr.data(), rr.size(), s);
   launch_assemble(sys, s);
+  if (sys->opt.precond == MTF_PRECOND_OSRC) osrc_setup(sys, s);
 }
 }  // namespace mtf
 
@@ -134,6 +135,9 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
       MTF_REQUIRE(sys->opt.n_ss >= 1 && sys->opt.n_ss <= 12, MTF_ERR_ARG, "n_ss out of range 1..12");
       MTF_REQUIRE(sys->opt.precision == MTF_PREC_FP64 || sys->opt.precision == MTF_PREC_MIXED, MTF_ERR_ARG,
                   "unknown precision");
+      MTF_REQUIRE(sys->opt.precond == MTF_PRECOND_NONE || sys->opt.precond == MTF_PRECOND_OSRC, MTF_ERR_ARG,
+                  "unknown preconditioner");
+      MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {
       delete sys;
@@ -183,6 +187,19 @@ mtf_status mtf_matvec(mtf_system sys, const void* x, void* y, int32_t nrhs, void
     const int64_t n = sys->mesh->n_total;
     launch_matvec(sys, static_cast<const double*>(x), n, static_cast<double*>(y), n, nrhs,
                   static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_precond_apply(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && r && z, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1, MTF_ERR_ARG, "nrhs must be >= 1");
+    MTF_REQUIRE(r != z, MTF_ERR_ARG, "r and z must not overlap");
+    MTF_REQUIRE(sys->opt.precond == MTF_PRECOND_OSRC, MTF_ERR_ARG,
+                "the system was assembled without the OSRC preconditioner");
+    const int64_t n = sys->mesh->n_total;
+    launch_osrc_apply(sys, static_cast<const double*>(r), n, static_cast<double*>(z), n, nrhs,
+                      static_cast<cudaStream_t>(stream));
   });
 }
 

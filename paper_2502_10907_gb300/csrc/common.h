@@ -133,6 +133,10 @@ struct mtf_mesh_s {
   std::vector<int64_t> reg_cta_prefix;       // regular-pair CTA prefix over blocks
   mtf::DevBuf<int64_t> d_reg_cta_prefix;
   mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
+  // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
+  bool osrc_ready = false;
+  mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;
+  std::vector<double> osrc_area;
 };
 
 namespace mtf {
@@ -149,6 +153,11 @@ struct mtf_system_s {
   mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
   mtf::DevBuf<double> d_xval;                // exchange values (6 per row)
   mtf::DevBuf<double> d_ss_pts[3];           // Sauter-Schwab tables
+  // FP32 geometry of the mixed regular-pair kernel (per block-triangle)
+  mtf::DevBuf<float> d_x32;                  // FP32 copy of the matvec input (mixed path)
+  mtf::DevBuf<float> d_osrc_f, d_osrc_r32, d_osrc_t;  // OSRC symbol (complex) and apply scratch
+  mtf::DevBuf<double> d_cen;
+  mtf::DevBuf<float> d_qx, d_qw, d_pv, d_cc;
   int32_t ss_npts[3] = {0, 0, 0};
   mtf::GmresWork* gw = nullptr;
 };
@@ -177,6 +186,15 @@ const char* kernel_name(int kid);
 void assemble_into(mtf_system sys, double k0, const double* eps_r, const double* mu_r, cudaStream_t s);
 // kernels launched from the host side (implemented in the .cu files)
 void launch_assemble(mtf_system sys, cudaStream_t s);
+void launch_assemble_regular32(mtf_system sys, cudaStream_t s);
+void osrc_setup(mtf_system sys, cudaStream_t s);
+// z = A~ r (block-OSRC, Eq. 19); column c of r (z) at r + 2 c ldr (z + 2 c ldz)
+void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
+                       cudaStream_t s);
+// matvec flavours: storage / accumulation precision
+enum MatvecKind { MV_AUTO = 0, MV_FP64 = 1, MV_FP32 = 2, MV_FP32_ACC64 = 3 };
+void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, double* y, int64_t ldy,
+                        int nrhs, cudaStream_t s);
 void launch_exchange_values(mtf_system sys, cudaStream_t s);
 // y = M x; column c of x (y) starts at x + 2 c ldx (y + 2 c ldy) doubles.
 void launch_matvec(mtf_system sys, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs,

@@ -1,0 +1,333 @@
+// Block-OSRC preconditioner of Sec. 4.4 (Eq. 19):
+//   A~_i = [[0, rho_i^-1 T~], [-rho_i T~, 0]],  T~ ~ EtM ~ T^-1.
+// Discretisation (the paper leaves it to the cited OSRC work): with the RWG
+// mass G and div-div matrix D of Gamma_i and the generalised eigenpairs
+// D v = lambda G v, V^T G V = I,
+//   T~ = V diag(f) V^T,  f(lambda) = 2k / (k_eps P(-lambda / k_eps^2)),
+// where P is the rotating-branch-cut Pade approximant of sqrt(1 + z) of order
+// N_p and angle theta (Milinazzo, Zala & Brooke 1997) and k_eps = k + i eps,
+// eps = c k^{1/3} R^{-2/3}, R the radius of the sphere with Gamma_i's area.
+// The eigenpairs depend on the mesh only and are computed once (FP32 dense
+// symmetric-definite eigensolver); f depends on k and is recomputed at every
+// assembly.  The apply is two dense FP32 passes per block, t = V^T r and
+// z = V (f t), HBM-bound like the block matvec.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <mutex>
+
+#include "common.h"
+
+namespace mtf {
+
+__constant__ double c_os_s[6], c_os_t[6], c_os_w[6];
+
+// dense G and D of every block (FP32, column-major = row-major, symmetric)
+__global__ void k_gram_divdiv(const double* __restrict__ bt_v, const double* __restrict__ bt_c,
+                              const double* __restrict__ bt_area, const int32_t* __restrict__ bt_dof,
+                              const int32_t* __restrict__ bt_blk, const int64_t* __restrict__ blk_mat_off,
+                              const int32_t* __restrict__ blk_N, int64_t n_bt, float* __restrict__ G,
+                              float* __restrict__ D) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n_bt) return;
+  const int i = bt_blk[q];
+  const int N = blk_N[i];
+  const int64_t base = blk_mat_off[i];
+  const double* v = bt_v + 9 * q;
+  const double A2 = 2.0 * bt_area[q];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double g = 0.0;
+      for (int p = 0; p < 6; ++p) {
+        double dot = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const double x = v[c] + c_os_s[p] * (v[3 + c] - v[c]) + c_os_t[p] * (v[6 + c] - v[c]);
+          dot += (x - v[3 * a + c]) * (x - v[3 * b + c]);
+        }
+        g += c_os_w[p] * dot;
+      }
+      const double ca = bt_c[3 * q + a], cb = bt_c[3 * q + b];
+      const int64_t e = base + int64_t(bt_dof[3 * q + a]) * N + bt_dof[3 * q + b];
+      atomicAdd(G + e, float(A2 * g * ca * cb));
+      atomicAdd(D + e, float(0.5 * A2 * (2.0 * ca) * (2.0 * cb)));
+    }
+}
+
+// VR (row-major V) from the eigensolver output (column-major V = row-major V^T)
+__global__ void k_transpose_block(const float* __restrict__ Vt, int N, float* __restrict__ VR) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int row = by + r, col = bx + threadIdx.x;
+    if (row < N && col < N) tile[r][threadIdx.x] = Vt[int64_t(row) * N + col];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int row = bx + r, col = by + threadIdx.x;
+    if (row < N && col < N) VR[int64_t(row) * N + col] = tile[threadIdx.x][r];
+  }
+}
+
+// f_j = 2k / (k_eps P(-lambda_j / k_eps^2)) per (block, j); Pade data in pd
+__global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __restrict__ row_blk, int64_t n_rows,
+                              const double* __restrict__ kk, const double* __restrict__ keps,
+                              const double* __restrict__ pd, int np, float2* __restrict__ f) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int i = row_blk[r];
+  // complex arithmetic written out: (re, im) pairs
+  const double kr = keps[2 * i], ki = keps[2 * i + 1];
+  const double k2r = kr * kr - ki * ki, k2i = 2 * kr * ki;          // k_eps^2
+  const double k2n = k2r * k2r + k2i * k2i;
+  const double l = double(lam[r]);
+  const double zr = -l * k2r / k2n, zi = l * k2i / k2n;            // -lambda / k_eps^2
+  double Pr = pd[0], Pi = pd[1];
+  for (int j = 0; j < np; ++j) {
+    const double Ar = pd[2 + 4 * j], Ai = pd[3 + 4 * j], Br = pd[4 + 4 * j], Bi = pd[5 + 4 * j];
+    const double nr = Ar * zr - Ai * zi, ni = Ar * zi + Ai * zr;   // A z
+    const double dr = 1.0 + Br * zr - Bi * zi, di = Br * zi + Bi * zr;  // 1 + B z
+    const double dn = dr * dr + di * di;
+    Pr += (nr * dr + ni * di) / dn;
+    Pi += (ni * dr - nr * di) / dn;
+  }
+  const double er = kr * Pr - ki * Pi, ei = kr * Pi + ki * Pr;     // k_eps P
+  const double en = er * er + ei * ei;
+  const double num = 2.0 * kk[2 * i];
+  f[r] = make_float2(float(num * er / en), float(-num * ei / en));
+}
+
+// pass 1: t[c][slot][row] = f_row * sum_m Vt[row][m] r32[c][slot block][m]; warp per (row, c)
+__global__ void __launch_bounds__(256) k_osrc_pass1(const float* __restrict__ Vt, const float* __restrict__ r32,
+                                                    const float2* __restrict__ f, const int32_t* __restrict__ row_blk,
+                                                    const int64_t* __restrict__ blk_row_off,
+                                                    const int32_t* __restrict__ blk_N,
+                                                    const int64_t* __restrict__ blk_dof_off,
+                                                    const int64_t* __restrict__ blk_mat_off, int64_t n_rows,
+                                                    int64_t n_total, int nrhs, float2* __restrict__ t) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rows * nrhs) return;
+  const int64_t r = w % n_rows;
+  const int c = int(w / n_rows);
+  const int i = row_blk[r];
+  const int N = blk_N[i];
+  const int64_t j = r - blk_row_off[i];
+  const float* row = Vt + blk_mat_off[i] + j * N;
+  const float* rv = r32 + 2 * (int64_t(c) * n_total + blk_dof_off[i]);
+  float dr = 0, di = 0, nr = 0, ni = 0;
+  for (int m0 = lane; m0 < N; m0 += 32 * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (m0 + 32 * u < N) ? row[m0 + 32 * u] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int m = m0 + 32 * u;
+      if (m >= N) break;
+      const float2 a = *reinterpret_cast<const float2*>(rv + 2 * m);
+      const float2 b = *reinterpret_cast<const float2*>(rv + 2 * (N + m));
+      dr = fmaf(v[u], a.x, dr);
+      di = fmaf(v[u], a.y, di);
+      nr = fmaf(v[u], b.x, nr);
+      ni = fmaf(v[u], b.y, ni);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    dr += __shfl_xor_sync(0xffffffffu, dr, s);
+    di += __shfl_xor_sync(0xffffffffu, di, s);
+    nr += __shfl_xor_sync(0xffffffffu, nr, s);
+    ni += __shfl_xor_sync(0xffffffffu, ni, s);
+  }
+  if (lane == 0) {
+    const float2 fr = f[r];
+    float2* tc = t + 2 * (int64_t(c) * n_rows + blk_row_off[i]);
+    tc[j] = make_float2(fr.x * dr - fr.y * di, fr.x * di + fr.y * dr);          // f V^T r_D
+    tc[N + j] = make_float2(fr.x * nr - fr.y * ni, fr.x * ni + fr.y * nr);      // f V^T r_N
+  }
+}
+
+// pass 2: z_D = rho^-1 V (f V^T r_N), z_N = -rho V (f V^T r_D); warp per (row, c)
+__global__ void __launch_bounds__(256) k_osrc_pass2(const float* __restrict__ VR, const float2* __restrict__ t,
+                                                    const double* __restrict__ rho,
+                                                    const int32_t* __restrict__ row_blk,
+                                                    const int64_t* __restrict__ blk_row_off,
+                                                    const int32_t* __restrict__ blk_N,
+                                                    const int64_t* __restrict__ blk_dof_off,
+                                                    const int64_t* __restrict__ blk_mat_off, int64_t n_rows,
+                                                    int nrhs, double* __restrict__ z, int64_t ldz) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rows * nrhs) return;
+  const int64_t r = w % n_rows;
+  const int c = int(w / n_rows);
+  const int i = row_blk[r];
+  const int N = blk_N[i];
+  const int64_t m = r - blk_row_off[i];
+  const float* row = VR + blk_mat_off[i] + m * N;
+  const float2* tc = t + 2 * (int64_t(c) * n_rows + blk_row_off[i]);
+  float dr = 0, di = 0, nr = 0, ni = 0;
+  for (int j0 = lane; j0 < N; j0 += 32 * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (j0 + 32 * u < N) ? row[j0 + 32 * u] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 32 * u;
+      if (j >= N) break;
+      const float2 a = tc[j], b = tc[N + j];
+      dr = fmaf(v[u], a.x, dr);
+      di = fmaf(v[u], a.y, di);
+      nr = fmaf(v[u], b.x, nr);
+      ni = fmaf(v[u], b.y, ni);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    dr += __shfl_xor_sync(0xffffffffu, dr, s);
+    di += __shfl_xor_sync(0xffffffffu, di, s);
+    nr += __shfl_xor_sync(0xffffffffu, nr, s);
+    ni += __shfl_xor_sync(0xffffffffu, ni, s);
+  }
+  if (lane == 0) {
+    const double rr = rho[2 * i], ri = rho[2 * i + 1];
+    const double rn = rr * rr + ri * ri;
+    const double ir = rr / rn, ii = -ri / rn;
+    double* zc = z + 2 * (int64_t(c) * ldz + blk_dof_off[i]);
+    // z_D = rho^-1 (V t_N), z_N = -rho (V t_D)
+    zc[2 * m] = ir * nr - ii * ni;
+    zc[2 * m + 1] = ir * ni + ii * nr;
+    zc[2 * (N + m)] = -(rr * dr - ri * di);
+    zc[2 * (N + m) + 1] = -(rr * di + ri * dr);
+  }
+}
+
+__global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t n2, int nrhs, float* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n2 * nrhs) return;
+  const int64_t c = t / n2, k = t % n2;
+  out[t] = float(x[2 * c * ldx + k]);
+}
+
+static cusolverDnHandle_t solver_handle() {
+  static cusolverDnHandle_t h = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!h) {
+    MTF_REQUIRE(cusolverDnCreate(&h) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnCreate failed");
+  }
+  return h;
+}
+
+// mesh-level eigenpairs of (D, G) for every block (once per mesh)
+static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
+  if (m->osrc_ready) return;
+  const TriRule& rule = triangle_rule6();
+  MTF_CUDA(cudaMemcpyToSymbolAsync(c_os_s, rule.s, sizeof(rule.s), 0, cudaMemcpyHostToDevice, s));
+  MTF_CUDA(cudaMemcpyToSymbolAsync(c_os_t, rule.t, sizeof(rule.t), 0, cudaMemcpyHostToDevice, s));
+  MTF_CUDA(cudaMemcpyToSymbolAsync(c_os_w, rule.w, sizeof(rule.w), 0, cudaMemcpyHostToDevice, s));
+  DevBuf<float> G;
+  m->d_osrc_Vt.alloc(size_t(m->n_mat));
+  m->d_osrc_VR.alloc(size_t(m->n_mat));
+  m->d_osrc_lam.alloc(size_t(m->n_rows));
+  G.alloc(size_t(m->n_mat));
+  MTF_CUDA(cudaMemsetAsync(G.p, 0, size_t(m->n_mat) * sizeof(float), s));
+  MTF_CUDA(cudaMemsetAsync(m->d_osrc_Vt.p, 0, size_t(m->n_mat) * sizeof(float), s));
+  MTF_LAUNCH(KID_MISC, s, k_gram_divdiv<<<unsigned((m->n_bt + 127) / 128), 128, 0, s>>>(
+      m->d_bt_v.p, m->d_bt_c.p, m->d_bt_area.p, m->d_bt_dof.p, m->d_bt_blk.p, m->d_blk_mat_off.p, m->d_blk_N.p,
+      m->n_bt, G.p, m->d_osrc_Vt.p));
+  cusolverDnHandle_t h = solver_handle();
+  MTF_REQUIRE(cusolverDnSetStream(h, s) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnSetStream failed");
+  DevBuf<int> info;
+  info.alloc(1);
+  for (int i = 0; i < m->nd; ++i) {
+    const int N = m->blk[i].N;
+    float* A = m->d_osrc_Vt.p + m->blk[i].mat_off;
+    float* B = G.p + m->blk[i].mat_off;
+    float* W = m->d_osrc_lam.p + m->blk[i].row_off;
+    int lwork = 0;
+    MTF_REQUIRE(cusolverDnSsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                            N, A, N, B, N, W, &lwork) == CUSOLVER_STATUS_SUCCESS,
+                MTF_ERR_CUDA, "cusolverDnSsygvd_bufferSize failed");
+    DevBuf<float> work;
+    work.alloc(size_t(std::max(lwork, 1)));
+    MTF_REQUIRE(cusolverDnSsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, A, N, B,
+                                 N, W, work.p, lwork, info.p) == CUSOLVER_STATUS_SUCCESS,
+                MTF_ERR_CUDA, "cusolverDnSsygvd failed");
+    int hinfo = 0;
+    MTF_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
+    MTF_REQUIRE(hinfo == 0, MTF_ERR_CUDA, "OSRC eigensolver failed for block " + std::to_string(i) +
+                                              " (info " + std::to_string(hinfo) + ")");
+    dim3 tg{unsigned((N + 31) / 32), unsigned((N + 31) / 32), 1u};
+    MTF_LAUNCH(KID_MISC, s, k_transpose_block<<<tg, dim3(32, 8), 0, s>>>(A, N, m->d_osrc_VR.p + m->blk[i].mat_off));
+  }
+  // areas of Gamma_i for the damping parameter
+  m->osrc_area.assign(m->nd, 0.0);
+  for (int64_t q = 0; q < m->n_bt; ++q) m->osrc_area[m->bt_blk[q]] += m->bt_area[q];
+  MTF_CUDA(cudaStreamSynchronize(s));
+  m->osrc_ready = true;
+}
+
+void osrc_setup(mtf_system sys, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  osrc_mesh_setup(m, s);
+  const int np = std::max(1, sys->opt.osrc_np);
+  const double th = sys->opt.osrc_theta;
+  using cd = std::complex<double>;
+  // rotated-branch-cut Pade coefficients
+  std::vector<double> pd(2 + 4 * np);
+  const cd e = std::exp(cd(0, -th));
+  cd R = 1.0;
+  std::vector<double> a(np), b(np);
+  for (int j = 1; j <= np; ++j) {
+    a[j - 1] = 2.0 / (2 * np + 1) * std::pow(std::sin(j * M_PI / (2 * np + 1)), 2);
+    b[j - 1] = std::pow(std::cos(j * M_PI / (2 * np + 1)), 2);
+    R += a[j - 1] * (e - 1.0) / (1.0 + b[j - 1] * (e - 1.0));
+  }
+  const cd C0 = std::exp(cd(0, th / 2)) * R;
+  pd[0] = C0.real();
+  pd[1] = C0.imag();
+  for (int j = 0; j < np; ++j) {
+    const cd den = 1.0 + b[j] * (e - 1.0);
+    const cd A = std::exp(cd(0, -th / 2)) * a[j] / (den * den);
+    const cd B = e * b[j] / den;
+    pd[2 + 4 * j] = A.real();
+    pd[3 + 4 * j] = A.imag();
+    pd[4 + 4 * j] = B.real();
+    pd[5 + 4 * j] = B.imag();
+  }
+  std::vector<double> keps(2 * m->nd);
+  for (int i = 0; i < m->nd; ++i) {
+    const double k = sys->k_re[i];
+    const double R = std::sqrt(m->osrc_area[i] / (4 * M_PI));
+    keps[2 * i] = k;
+    keps[2 * i + 1] = sys->opt.osrc_eps_scale * std::cbrt(k) * std::pow(R, -2.0 / 3.0);
+  }
+  DevBuf<double> d_pd, d_keps;
+  d_pd.upload(pd, s);
+  d_keps.upload(keps, s);
+  sys->d_osrc_f.alloc(size_t(m->n_rows) * 2);
+  MTF_LAUNCH(KID_MISC, s, k_osrc_symbol<<<unsigned((m->n_rows + 127) / 128), 128, 0, s>>>(
+      m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, sys->d_k.p, d_keps.p, d_pd.p, np,
+      reinterpret_cast<float2*>(sys->d_osrc_f.p)));
+  MTF_CUDA(cudaStreamSynchronize(s));  // d_pd / d_keps are freed on return
+}
+
+void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
+                       cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  const int64_t n2 = 2 * m->n_total;
+  if (sys->d_osrc_r32.n < size_t(n2) * nrhs) sys->d_osrc_r32.alloc(size_t(n2) * nrhs);
+  if (sys->d_osrc_t.n < size_t(n2) * nrhs) sys->d_osrc_t.alloc(size_t(n2) * nrhs);
+  MTF_LAUNCH(KID_OSRC, s, k_to_f32_cols<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(r, ldr, n2, nrhs, sys->d_osrc_r32.p));
+  const unsigned blocks = unsigned((m->n_rows * nrhs * 32 + 255) / 256);
+  MTF_LAUNCH(KID_OSRC, s, k_osrc_pass1<<<blocks, 256, 0, s>>>(
+      m->d_osrc_Vt.p, sys->d_osrc_r32.p, reinterpret_cast<const float2*>(sys->d_osrc_f.p), m->d_row_blk.p,
+      m->d_blk_row_off.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->n_rows, m->n_total, nrhs,
+      reinterpret_cast<float2*>(sys->d_osrc_t.p)));
+  MTF_LAUNCH(KID_OSRC, s, k_osrc_pass2<<<blocks, 256, 0, s>>>(
+      m->d_osrc_VR.p, reinterpret_cast<const float2*>(sys->d_osrc_t.p), sys->d_rho.p, m->d_row_blk.p,
+      m->d_blk_row_off.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->n_rows, nrhs, z, ldz));
+}
+
+}  // namespace mtf

@@ -66,6 +66,8 @@ mtf_status solve_static(mtf_system sys, int nrhs, const double* dirs, const doub
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = sys->mesh->n_total;
   const int m = std::max(1, sys->opt.restart);
+  MTF_REQUIRE(sys->opt.precision == MTF_PREC_FP64, MTF_ERR_ARG,
+              "mtf_solve_static supports systems assembled with MTF_PREC_FP64 only");
   const size_t need = static_solve_need(n, nrhs, m);
   MTF_REQUIRE(need <= kStaticScratchDoubles, MTF_ERR_ARG,
               "mtf_solve_static: the solve needs " + std::to_string(need) +

@@ -22,7 +22,7 @@ using cd = std::complex<double>;
 struct GmresWork {
   int nrhs = 0, m = 0;
   int64_t n = 0;
-  DevBuf<double> V, w, r, b, y;
+  DevBuf<double> V, Z, w, r, b, y;
   DevBuf<double> h;  // [hA (m+1) x nrhs][hB (m+1) x nrhs][norm nrhs] complex
   double* h_host = nullptr;
   ~GmresWork() {
@@ -122,27 +122,171 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
 
 static inline unsigned nblk(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
-mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
-                 cudaStream_t s) {
-  const auto t0 = std::chrono::steady_clock::now();
+// Segmented kernels of the batched Arnoldi step: the row range is cut into
+// segments of kSeg entries so that every step keeps the whole GPU busy;
+// per-segment partial sums are accumulated with FP64 atomics (the
+// accumulators are cleared before each use).
+constexpr int kSeg = 2048;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(0xffffffffu, t, s);
+  }
+  return t;  // valid in thread 0
+}
+
+// h[c*ldh + i] += sum_k conj(V_i^c[k]) w^c[k] over one segment of length seg;
+// grid (segments, i, c)
+__global__ void __launch_bounds__(256) k_dots_seg(const double* __restrict__ V, const double* __restrict__ w,
+                                                  int64_t n, int ldv, double* __restrict__ h, int ldh, int64_t seg) {
+  const int i = blockIdx.y, c = blockIdx.z;
+  const int64_t k0 = int64_t(blockIdx.x) * seg;
+  const int64_t k1 = min(n, k0 + seg);
+  const double2* v = reinterpret_cast<const double2*>(V) + (int64_t(c) * ldv + i) * n;
+  const double2* x = reinterpret_cast<const double2*>(w) + int64_t(c) * n;
+  double sr = 0, si = 0;
+#pragma unroll 8
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double2 a = v[k], b = x[k];
+    sr += a.x * b.x + a.y * b.y;
+    si += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double red[32];
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(h + 2 * (int64_t(c) * ldh + i), sr);
+    atomicAdd(h + 2 * (int64_t(c) * ldh + i) + 1, si);
+  }
+}
+
+// w^c -= sum_{i<j} V_i^c h_i^c ; optionally ss[c] += ||w^c||^2 (after update).
+// CTA = 32 consecutive rows x 8 groups of basis vectors (i = g mod 8), the
+// group partial sums combined in shared memory; grid (ceil(n/32), c).
+__global__ void __launch_bounds__(256) k_axpy_grp(const double* __restrict__ V, const double* __restrict__ h, int j,
+                                                  int64_t n, int ldv, int ldh, double sign, double* __restrict__ w,
+                                                  double* __restrict__ ss) {
+  const int c = blockIdx.y;
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t k = int64_t(blockIdx.x) * 32 + lane;
+  __shared__ double2 part[8][32];
+  __shared__ double red[32];
+  double sr = 0, si = 0;
+  if (k < n) {
+    const double2* v = reinterpret_cast<const double2*>(V) + int64_t(c) * ldv * n + k;
+    const double* hc = h + 2 * int64_t(c) * ldh;
+#pragma unroll 4
+    for (int i = grp; i < j; i += 8) {
+      const double2 a = v[int64_t(i) * n];
+      const double hr = hc[2 * i], hi = hc[2 * i + 1];
+      sr += a.x * hr - a.y * hi;
+      si += a.x * hi + a.y * hr;
+    }
+  }
+  part[grp][lane] = make_double2(sr, si);
+  __syncthreads();
+  double sq = 0;
+  if (grp == 0 && k < n) {
+    double tr = 0, ti = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      tr += part[g][lane].x;
+      ti += part[g][lane].y;
+    }
+    double2* x = reinterpret_cast<double2*>(w) + int64_t(c) * n + k;
+    double2 o = *x;
+    o.x += sign * tr;
+    o.y += sign * ti;
+    *x = o;
+    sq = o.x * o.x + o.y * o.y;
+  }
+  if (ss) {
+    if (grp == 0) {
+      for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
+      if (lane == 0) atomicAdd(ss + c, sq);
+    }
+  }
+  (void)red;
+}
+
+__global__ void __launch_bounds__(256) k_axpy_sq(const double* __restrict__ V, const double* __restrict__ h, int j,
+                                                 int64_t n, int ldv, int ldh, double sign, double* __restrict__ w,
+                                                 double* __restrict__ ss) {
+  const int c = blockIdx.y;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double sq = 0;
+  if (k < n) {
+    const double2* v = reinterpret_cast<const double2*>(V) + int64_t(c) * ldv * n + k;
+    const double* hc = h + 2 * int64_t(c) * ldh;
+    double sr = 0, si = 0;
+#pragma unroll 8
+    for (int i = 0; i < j; ++i) {
+      const double2 a = v[int64_t(i) * n];
+      const double hr = hc[2 * i], hi = hc[2 * i + 1];
+      sr += a.x * hr - a.y * hi;
+      si += a.x * hi + a.y * hr;
+    }
+    double2* x = reinterpret_cast<double2*>(w) + int64_t(c) * n + k;
+    double2 o = *x;
+    o.x += sign * sr;
+    o.y += sign * si;
+    *x = o;
+    sq = o.x * o.x + o.y * o.y;
+  }
+  if (ss) {
+    __shared__ double red[32];
+    sq = block_sum(sq, red);
+    if (threadIdx.x == 0) atomicAdd(ss + c, sq);
+  }
+}
+
+// ss[c] += ||w^c||^2
+__global__ void __launch_bounds__(256) k_sqnorm(const double* __restrict__ w, int64_t n, double* __restrict__ ss) {
+  const int c = blockIdx.y;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double sq = 0;
+  if (k < n) {
+    const double2 a = reinterpret_cast<const double2*>(w)[int64_t(c) * n + k];
+    sq = a.x * a.x + a.y * a.y;
+  }
+  __shared__ double red[32];
+  sq = block_sum(sq, red);
+  if (threadIdx.x == 0) atomicAdd(ss + c, sq);
+}
+
+// out^c = w^c / sqrt(ss[c]) (zero if 0); nrm[c] = (sqrt(ss[c]), 0)
+__global__ void __launch_bounds__(256) k_scale(const double* __restrict__ w, int64_t n, const double* __restrict__ ss,
+                                               double* __restrict__ nrm, double* __restrict__ out,
+                                               int64_t out_stride) {
+  const int c = blockIdx.y;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const double t = sqrt(ss[c]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    nrm[2 * c] = t;
+    nrm[2 * c + 1] = 0.0;
+  }
+  if (k >= n) return;
+  const double inv = t > 0 ? 1.0 / t : 0.0;
+  const double2 a = reinterpret_cast<const double2*>(w)[int64_t(c) * n + k];
+  reinterpret_cast<double2*>(out)[int64_t(c) * out_stride + k] = make_double2(a.x * inv, a.y * inv);
+}
+
+// One restarted GMRES solve of M x = b (x starts at 0) with the given matvec
+// flavour.  Per right-hand side: iters[c] += inner iterations, rel[c] = final
+// true relative residual (w.r.t. the same flavour).
+static mtf_status gmres_core(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, int mvkind,
+                             double tol, int max_iter, std::vector<int>& iters, int& restarts,
+                             std::vector<double>& rel, cudaStream_t s) {
   mtf_mesh msh = sys->mesh;
   const int64_t n = msh->n_total;
   const int m = std::max(1, sys->opt.restart);
-  if (!sys->gw) sys->gw = new GmresWork();
   GmresWork& G = *sys->gw;
-  if (G.nrhs != nrhs || G.m != m || G.n != n) {
-    G.V.alloc(size_t(m + 1) * n * nrhs * 2);
-    G.w.alloc(size_t(n) * nrhs * 2);
-    G.r.alloc(size_t(n) * nrhs * 2);
-    G.y.alloc(size_t(m + 1) * nrhs * 2);
-    G.h.alloc(size_t(2 * (m + 1) + 1) * nrhs * 2);
-    if (G.h_host) cudaFreeHost(G.h_host);
-    G.h_host = nullptr;
-    MTF_CUDA(cudaMallocHost(&G.h_host, G.h.n * sizeof(double)));
-    G.nrhs = nrhs;
-    G.m = m;
-    G.n = n;
-  }
   double* hA = G.h.p;
   double* hB = G.h.p + 2 * size_t(m + 1) * nrhs;
   double* hN = G.h.p + 4 * size_t(m + 1) * nrhs;
@@ -152,29 +296,28 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
   const int ldv = m + 1;
   const size_t vec_bytes = size_t(n) * nrhs * 2 * sizeof(double);
 
-  // ||b|| per right-hand side
-  std::vector<double> bnorm(nrhs), rel(nrhs, 1.0);
+  std::vector<double> bnorm(nrhs);
   MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(b_dev, n, hN, G.w.p, n));
   MTF_CUDA(cudaMemcpyAsync(hostN, hN, size_t(nrhs) * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   MTF_CUDA(cudaStreamSynchronize(s));
   for (int c = 0; c < nrhs; ++c) bnorm[c] = hostN[2 * c] > 0 ? hostN[2 * c] : 1.0;
   MTF_CUDA(cudaMemsetAsync(x_dev, 0, vec_bytes, s));
 
-  std::vector<int> done(nrhs, 0), iters(nrhs, 0), jc(nrhs, 0);
+  std::vector<int> done(nrhs, 0), jc(nrhs, 0);
   std::vector<cd> H(size_t(m + 1) * m * nrhs), g(size_t(m + 1) * nrhs), sn(size_t(m) * nrhs);
   std::vector<double> cs(size_t(m) * nrhs);
   std::vector<double> yhost(size_t(m + 1) * nrhs * 2);
-  int restarts = 0, total = 0;
+  int total = 0;
   bool first = true;
-  const int max_iter = std::max(1, sys->opt.max_iter);
-  const double tol = sys->opt.tol;
   mtf_status status = MTF_OK;
+  const bool pre = sys->opt.precond == MTF_PRECOND_OSRC;
+  if (pre && G.Z.n != size_t(m) * n * nrhs * 2) G.Z.alloc(size_t(m) * n * nrhs * 2);
   while (true) {
     // true residual r = b - M x and its norm; V_0 = r / ||r||
     if (first) {
       MTF_CUDA(cudaMemcpyAsync(G.r.p, b_dev, vec_bytes, cudaMemcpyDeviceToDevice, s));
     } else {
-      launch_matvec(sys, x_dev, n, G.w.p, n, nrhs, s);
+      launch_matvec_kind(sys, mvkind, x_dev, n, G.w.p, n, nrhs, s);
       MTF_LAUNCH(KID_SUB, s, k_sub<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(b_dev, G.w.p, G.r.p, n * nrhs * 2));
     }
     first = false;
@@ -200,19 +343,31 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
     ++restarts;
     std::vector<int> active(nrhs);
     for (int c = 0; c < nrhs; ++c) active[c] = !done[c];
-    int j = 0;
-    for (; j < m && total < max_iter; ++j) {
-      // w = M v_j  (right preconditioning hook: identity)
-      launch_matvec(sys, G.V.p + 2 * size_t(j) * n, int64_t(ldv) * n, G.r.p, n, nrhs, s);
-      // CGS2
-      dim3 gd(unsigned(j + 1), unsigned(nrhs));
-      MTF_LAUNCH(KID_DOTS, s, k_dots<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hA, m + 1));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, hA, j + 1, n, ldv, m + 1, -1.0, G.r.p, nrhs));
-      MTF_LAUNCH(KID_DOTS, s, k_dots<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hB, m + 1));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, hB, j + 1, n, ldv, m + 1, -1.0, G.r.p, nrhs));
+    for (int j = 0; j < m && total < max_iter; ++j) {
+      // flexible right preconditioning: z_j = P v_j, w = M z_j
+      if (pre) {
+        launch_osrc_apply(sys, G.V.p + 2 * size_t(j) * n, int64_t(ldv) * n, G.Z.p + 2 * size_t(j) * n,
+                          int64_t(m) * n, nrhs, s);
+        launch_matvec_kind(sys, mvkind, G.Z.p + 2 * size_t(j) * n, int64_t(m) * n, G.r.p, n, nrhs, s);
+      } else {
+        launch_matvec_kind(sys, mvkind, G.V.p + 2 * size_t(j) * n, int64_t(ldv) * n, G.r.p, n, nrhs, s);
+      }
+      // CGS2: h_A = V^H w, w -= V h_A, h_B = V^H w, w -= V h_B (with ||w||^2)
+      MTF_CUDA(cudaMemsetAsync(G.h.p, 0, G.h.n * sizeof(double), s));
+      // segments per dot so that ~1200 CTAs run whatever j is
+      const int64_t nseg = std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024,
+                                                                  1200 / (int64_t(j + 1) * nrhs)));
+      const int64_t seg = (n + nseg - 1) / nseg;
+      dim3 gd(unsigned(nseg), unsigned(j + 1), unsigned(nrhs));
+      dim3 ga(nblk(n, 256), unsigned(nrhs));
+      dim3 gg(nblk(n, 32), unsigned(nrhs));
+      double* ss = hN + 2 * nrhs;  // sum of squares scratch after the norms
+      MTF_LAUNCH(KID_DOTS, s, k_dots_seg<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hA, m + 1, seg));
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, 0, s>>>(G.V.p, hA, j + 1, n, ldv, m + 1, -1.0, G.r.p, nullptr));
+      MTF_LAUNCH(KID_DOTS, s, k_dots_seg<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hB, m + 1, seg));
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, 0, s>>>(G.V.p, hB, j + 1, n, ldv, m + 1, -1.0, G.r.p, ss));
       // v_{j+1} = w / ||w||
-      MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(G.r.p, n, hN, G.V.p + 2 * size_t(j + 1) * n, int64_t(ldv) * n));
-      MTF_CUDA(cudaGetLastError());
+      MTF_LAUNCH(KID_NORM, s, k_scale<<<ga, 256, 0, s>>>(G.r.p, n, ss, hN, G.V.p + 2 * size_t(j + 1) * n, int64_t(ldv) * n));
       MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, G.h.n * sizeof(double), cudaMemcpyDeviceToHost, s));
       MTF_CUDA(cudaStreamSynchronize(s));
       ++total;
@@ -262,10 +417,7 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
         if (est <= tol * 0.5 || hostN[2 * c] == 0.0) active[c] = 0;
         all_done = all_done && !active[c];
       }
-      if (status != MTF_OK || all_done) {
-        ++j;
-        break;
-      }
+      if (status != MTF_OK || all_done) break;
     }
     if (status != MTF_OK) break;
     // x += V y, y = R^{-1} g per right-hand side
@@ -288,15 +440,116 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
     }
     if (jmax > 0) {
       MTF_CUDA(cudaMemcpyAsync(G.y.p, yhost.data(), yhost.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nblk(n * nrhs, 256), 256, 0, s>>>(G.V.p, G.y.p, jmax, n, ldv, m + 1, 1.0, x_dev, nrhs));
-      MTF_CUDA(cudaGetLastError());
+      // x += Z y (flexible) or V y
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<dim3(nblk(n, 32), unsigned(nrhs)), 256, 0, s>>>(
+          pre ? G.Z.p : G.V.p, G.y.p, jmax, n, pre ? m : ldv, m + 1, 1.0, x_dev, nullptr));
       MTF_CUDA(cudaStreamSynchronize(s));  // yhost is reused next cycle
     }
+  }
+  return status;
+}
+
+__global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int64_t n2) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n2) x[t] += d[t];
+}
+
+mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
+                 cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  mtf_mesh msh = sys->mesh;
+  const int64_t n = msh->n_total;
+  const int m = std::max(1, sys->opt.restart);
+  if (!sys->gw) sys->gw = new GmresWork();
+  GmresWork& G = *sys->gw;
+  const bool mixed = sys->opt.precision != MTF_PREC_FP64;
+  if (G.nrhs != nrhs || G.m != m || G.n != n) {
+    G.V.alloc(size_t(m + 1) * n * nrhs * 2);
+    G.w.alloc(size_t(n) * nrhs * 2);
+    G.r.alloc(size_t(n) * nrhs * 2);
+    G.y.alloc(size_t(m + 1) * nrhs * 2);
+    G.h.alloc(size_t(2 * (m + 1) + 2) * nrhs * 2);
+    if (G.h_host) cudaFreeHost(G.h_host);
+    G.h_host = nullptr;
+    MTF_CUDA(cudaMallocHost(&G.h_host, G.h.n * sizeof(double)));
+    G.nrhs = nrhs;
+    G.m = m;
+    G.n = n;
+  }
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> rel(nrhs, 1.0);
+  int restarts = 0, refinements = 0;
+  const int max_iter = std::max(1, sys->opt.max_iter);
+  mtf_status status = MTF_OK;
+  if (!mixed) {
+    status = gmres_core(sys, nrhs, b_dev, x_dev, MV_FP64, sys->opt.tol, max_iter, iters, restarts, rel, s);
+  } else {
+    // FP64 iterative refinement: r = b - M x with FP64 accumulation over the
+    // FP32-stored operator; inner FGMRES on M d = r with the FP32 matvec.
+    if (G.b.n != size_t(n) * nrhs * 2) G.b.alloc(size_t(n) * nrhs * 2);  // residual
+    DevBuf<double> dx;
+    dx.alloc(size_t(n) * nrhs * 2);
+    const size_t vec_bytes = size_t(n) * nrhs * 2 * sizeof(double);
+    double* hN = G.h.p + 4 * size_t(m + 1) * nrhs;
+    double* hostN = G.h_host + 4 * size_t(m + 1) * nrhs;
+    std::vector<double> bnorm(nrhs);
+    MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(b_dev, n, hN, G.w.p, n));
+    MTF_CUDA(cudaMemcpyAsync(hostN, hN, size_t(nrhs) * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < nrhs; ++c) bnorm[c] = hostN[2 * c] > 0 ? hostN[2 * c] : 1.0;
+    MTF_CUDA(cudaMemsetAsync(x_dev, 0, vec_bytes, s));
+    const int max_ref = std::max(1, sys->opt.max_refine);
+    int total = 0;
+    for (int it = 0;; ++it) {
+      if (it == 0) {
+        MTF_CUDA(cudaMemcpyAsync(G.b.p, b_dev, vec_bytes, cudaMemcpyDeviceToDevice, s));
+      } else {
+        launch_matvec_kind(sys, MV_FP32_ACC64, x_dev, n, G.w.p, n, nrhs, s);
+        MTF_LAUNCH(KID_SUB, s, k_sub<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(b_dev, G.w.p, G.b.p, n * nrhs * 2));
+      }
+      MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(G.b.p, n, hN, G.w.p, n));
+      MTF_CUDA(cudaMemcpyAsync(hostN, hN, size_t(nrhs) * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MTF_CUDA(cudaStreamSynchronize(s));
+      double rmax = 0;
+      for (int c = 0; c < nrhs; ++c) {
+        rel[c] = hostN[2 * c] / bnorm[c];
+        if (!std::isfinite(rel[c])) status = MTF_ERR_NAN;
+        rmax = std::max(rmax, rel[c]);
+      }
+      if (status != MTF_OK) break;
+      if (rmax <= sys->opt.tol) break;
+      if (it >= max_ref || total >= max_iter) {
+        status = MTF_ERR_NOCONV;
+        break;
+      }
+      // right-hand sides already converged get a zero residual
+      for (int c = 0; c < nrhs; ++c)
+        if (rel[c] <= sys->opt.tol)
+          MTF_CUDA(cudaMemsetAsync(G.b.p + 2 * size_t(c) * n, 0, size_t(n) * 2 * sizeof(double), s));
+      const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
+      std::vector<int> it_in(nrhs, 0);
+      std::vector<double> rel_in(nrhs, 1.0);
+      const mtf_status si = gmres_core(sys, nrhs, G.b.p, dx.p, MV_FP32, inner_tol, max_iter - total, it_in,
+                                       restarts, rel_in, s);
+      if (si == MTF_ERR_NAN) {
+        status = si;
+        break;
+      }
+      int mx = 0;
+      for (int c = 0; c < nrhs; ++c) {
+        iters[c] += it_in[c];
+        mx = std::max(mx, it_in[c]);
+      }
+      total += mx;
+      ++refinements;
+      MTF_LAUNCH(KID_MISC, s, k_add<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(x_dev, dx.p, n * nrhs * 2));
+    }
+    MTF_CUDA(cudaStreamSynchronize(s));
   }
   if (st) {
     st->iterations = *std::max_element(iters.begin(), iters.end());
     st->restarts = restarts;
-    st->refinements = 0;
+    st->refinements = refinements;
     st->converged = status == MTF_OK;
     st->rel_residual = *std::max_element(rel.begin(), rel.end());
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -142,3 +142,81 @@ def test_full_size_split_sphere_sampled_rows(api):
             yN += Gij @ x[:, Nj].T
         assert rel(y[:, Di][:, rows], yD.T) < TOL
         assert rel(y[:, Ni][:, rows], yN.T) < TOL
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 regular pairs and storage, FP64 singular pairs,
+# FP32-matvec FGMRES inside FP64 iterative refinement.  Stated bound: 1e-5
+# relative error of solutions and far fields vs the FP64 oracle; the
+# assembled blocks carry FP32 rounding (bound 2e-6 norm-wise).
+# ---------------------------------------------------------------------------
+MIXED_TOL = 1e-5
+
+
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+def test_mixed_blocks_match_oracle(api, oracle_cache, name):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    for i in range(sk.n_domains):
+        T, K = (t.cpu().numpy() for t in sysg.block(i))
+        assert rel(T, ref.T[i]) < 2e-6, (i, rel(T, ref.T[i]))
+        assert rel(K, ref.K[i]) < 2e-6, (i, rel(K, ref.K[i]))
+
+
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+def test_mixed_solve_and_farfield_within_1e5_of_oracle(api, oracle_cache, name):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, tol=1e-8, restart=2000,
+                      max_iter=6000, max_refine=6)
+    x, st = sysg.solve(cfg["dirs"], cfg["pols"])
+    xr = ref.solve_lu(ref.rhs(cfg["dirs"], cfg["pols"]))
+    assert st.converged == 1
+    errs = np.linalg.norm(x.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
+    assert errs.max() < MIXED_TOL, errs
+    obs = rcs_plane(37)
+    f = sysg.farfield(x, obs).cpu().numpy()
+    fr = ref.farfield(xr, obs).transpose(2, 0, 1)
+    assert rel(f, fr) < MIXED_TOL
+
+
+# ---------------------------------------------------------------------------
+# block-OSRC preconditioner (Eq. 19).  The apply uses an FP32 eigensolver and
+# FP32 passes: bound 1e-4 against the FP64 oracle operator.  Preconditioned
+# solves converge to the same solution (1e-10 FP64, 1e-5 mixed).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["sphere", "split"])
+def test_osrc_apply_matches_oracle(api, oracle_cache, name):
+    from oracle.osrc import BlockOSRC
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1)
+    P = BlockOSRC(sk, ref.k, ref.rho)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal((3, sk.n_total)) + 1j * rng.standard_normal((3, sk.n_total))
+    z = sysg.precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    zr = np.stack([P.apply(rr) for rr in r])
+    assert rel(z, zr) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["sphere", "split"])
+def test_osrc_preconditioned_solves(api, oracle_cache, name):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    xr = ref.solve_lu(ref.rhs(cfg["dirs"], cfg["pols"]))
+    plain = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-6, restart=2000, max_iter=4000)
+    _, st0 = plain.solve(cfg["dirs"], cfg["pols"])
+    pre = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-6, restart=2000, max_iter=4000,
+                     precond=1)
+    _, st1 = pre.solve(cfg["dirs"], cfg["pols"])
+    assert st1.iterations * 2 < st0.iterations, (st0.iterations, st1.iterations)
+    exact = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-12, restart=2000, max_iter=4000,
+                       precond=1)
+    x, st = exact.solve(cfg["dirs"], cfg["pols"])
+    assert rel(x.cpu().numpy().T, xr) < TOL
+    mixed = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-8, restart=500, max_iter=4000,
+                       precond=1, precision=1, max_refine=6)
+    xm, stm = mixed.solve(cfg["dirs"], cfg["pols"])
+    errs = np.linalg.norm(xm.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
+    assert stm.converged == 1 and errs.max() < MIXED_TOL, errs

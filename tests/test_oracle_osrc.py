@@ -1,0 +1,55 @@
+"""Pins of the oracle's block-OSRC preconditioner (Sec. 4.4, Eq. 19).
+
+The OSRC operator only changes iteration counts, never the solution; its
+pins are the Pade approximation of the square root (against the principal
+square root away from the rotated branch cut), the structure of the RWG
+div-div matrix, and the effect the paper reports: block-OSRC speeds up GMRES
+by more than 3x (Sec. 5.3)."""
+import numpy as np
+import pytest
+
+import mtf_inputs as mi
+from oracle.osrc import (pade_sqrt, pade_coefficients, divdiv_matrix, BlockOSRC, gmres_iterations)
+from oracle.operators import mass_matrix
+from tests.oracle_helpers import sphere_system, skeleton_of
+
+
+def test_pade_sqrt_converges_to_principal_root():
+    z = np.concatenate([np.linspace(-0.9, 4.0, 40), np.linspace(-0.9, 4.0, 40) + 0.3j])
+    e4 = np.abs(pade_sqrt(z, 4) - np.sqrt(1 + z)).max()
+    e8 = np.abs(pade_sqrt(z, 8) - np.sqrt(1 + z)).max()
+    assert e4 < 3e-2 and e8 < 1e-3 and e8 < e4 / 20
+    assert np.abs(pade_sqrt(z, 16) - np.sqrt(1 + z)).max() < 1e-6   # exponential in N_p
+    C0, A, B = pade_coefficients(4, np.pi / 2)
+    assert abs(C0 + A.sum() * 0 - pade_sqrt(0.0, 4)) < 1e-15     # P(0) = C0
+    assert abs(C0 - 1.0) < 1e-3
+    # evanescent side (rotated cut): finite, follows i sqrt(|z| - 1)
+    z = -np.linspace(2.0, 6.0, 9) + 1e-3j
+    assert np.abs(pade_sqrt(z, 8) - np.sqrt(1 + z)).max() < 5e-2
+
+
+def test_divdiv_matrix_rank_and_symmetry():
+    sk = skeleton_of(mi.icosphere(1))
+    D = divdiv_matrix(sk, 0)
+    G = mass_matrix(sk, 0)
+    assert np.allclose(D, D.T) and np.allclose(G, G.T)
+    ev = np.linalg.eigvalsh(D)
+    T = len(sk.tris[0])
+    # div maps RWG onto zero-mean piecewise constants: rank T - 1
+    assert np.sum(ev > 1e-10 * ev.max()) == T - 1
+    assert np.all(np.linalg.eigvalsh(G) > 0)
+
+
+def test_block_osrc_speeds_up_gmres(oracle_cache):
+    cfg, sk, ref = sphere_system(oracle_cache, 2)
+    M = ref.matrix()
+    b = ref.rhs(cfg["dirs"], cfg["pols"])[:, 0]
+    xs = np.linalg.solve(M, b)
+    P = BlockOSRC(sk, ref.k, ref.rho)
+    x0, it0, c0 = gmres_iterations(M, b, 1e-5, 100, 1500)
+    x1, it1, c1 = gmres_iterations(M, b, 1e-5, 100, 1500, P=P.matrix())
+    assert c1 and it1 * 3 < it0, (it0, it1)
+    # the preconditioner changes the iterations, not the solution
+    assert np.linalg.norm(x1 - xs) / np.linalg.norm(xs) < 1e-3
+    r = np.random.default_rng(0).standard_normal(sk.n_total) + 0j
+    assert np.allclose(P.apply(r), P.matrix() @ r)
