@@ -8,14 +8,15 @@ wavenumber k_eps = k + i eps) of a square-root surface operator, and leaves
 its discretisation to the cited OSRC work.  Reading taken here (stated in
 the design notes; the CUDA library implements the same operator):
 
-* Principal symbols of the Galerkin EFIO on a flat patch: on irrotational
-  currents with div-div / mass eigenvalue lambda (= |xi|^2) the EFIO acts as
-  i q / (2k), q = sqrt(lambda - k^2) (outgoing branch), on solenoidal ones as
-  -i k / (2q); both inverses equal 2k / sqrt(k^2 - lambda) at lambda = 0 and
-  the first is the OSRC square-root symbol
-      T^{-1} ~ 2k / (k_eps sqrt(1 + Z)),   Z = -lambda / k_eps^2,
-  i.e. sqrt(1 + X / k_eps^2) with X = grad_G div_G (the curl-curl part of the
-  Hodge Laplacian, which RWG cannot represent conformingly, is dropped).
+* Principal symbols of the Galerkin EFIO on a flat patch (outgoing branch
+  q = sqrt(|xi|^2 - k^2)): on irrotational currents (grad phi) the EFIO acts
+  as i q / (2k), on solenoidal currents (n x grad phi) as -i k / (2q).  With
+  k_eps = k + i eps and Z = -|xi|^2 / k_eps^2 their inverses are
+      irrotational:  2k / (k_eps sqrt(1 + Z)),
+      solenoidal:    (2 k_eps / k) sqrt(1 + Z),
+  the two factors of the OSRC magnetic-to-electric operator
+  (1 + X/k_eps^2)^{-1/2} (1 - curl curl / k_eps^2), X the surface Hodge
+  Laplacian; both tend to 2 as |xi| -> 0.
 * sqrt(1 + Z) is replaced by the rotating-branch-cut Pade approximant of
   order N_p and angle theta (Milinazzo, Zala & Brooke 1997):
       a_j = 2/(2N_p+1) sin^2(j pi/(2N_p+1)), b_j = cos^2(j pi/(2N_p+1)),
@@ -26,12 +27,18 @@ the design notes; the CUDA library implements the same operator):
       B_j = e^{-i theta} b_j / (1 + b_j (e^{-i theta} - 1)).
 * Damping eps = c k^{1/3} R^{-2/3} (c = 0.39, R the radius of the sphere with
   the area of Gamma_i), the curvature-based choice of the OSRC literature.
-* Discretisation: with the RWG mass G and div-div matrix D of Gamma_i and the
-  generalised eigenpairs D v = lambda G v, V^T G V = I, the operator is
-      T~ = V diag(f(lambda)) V^T,  f = 2k / (k_eps P(-lambda / k_eps^2)),
-  which maps tested vectors to coefficients (V V^T = G^{-1}); the Pade
-  approximant is applied exactly on each eigenvalue instead of through
-  auxiliary sparse solves.
+* Discretisation on RWG_i (closed, genus-0 Gamma_i): the RWG space splits
+  G-orthogonally into the irrotational part (generalised eigenpairs
+  D v = lambda G v with lambda > 0, D the div-div and G the mass matrix;
+  |xi|^2 = lambda) and the loop part, the RWG images u = L phi of nodal P1
+  functions (u = n x grad phi exactly, L[e, lo] = 1/l_e, L[e, hi] = -1/l_e),
+  whose eigenpairs S phi = mu M phi (P1 stiffness S, mass M; |xi|^2 = mu)
+  give G-orthonormal loop modes L phi / sqrt(mu) (L^T G L = S).  With W the
+  G-orthonormal basis of both parts and f the matching symbols,
+      T~ = W diag(f) W^T,
+  which maps tested vectors to coefficients (W W^T = G^{-1}); the Pade
+  approximant is applied exactly on every mode instead of through auxiliary
+  sparse solves.
 """
 from __future__ import annotations
 
@@ -77,6 +84,39 @@ def damping(k, area, scale=0.39):
     return scale * np.real(k) ** (1.0 / 3.0) * R ** (-2.0 / 3.0)
 
 
+def p1_matrices(sk: Skeleton, i: int):
+    """Vertices of Gamma_i and the P1 Laplace-Beltrami stiffness S and mass M."""
+    tris = sk.tris[i]
+    F = sk.F[tris]
+    verts = np.unique(F)
+    pos = {v: q for q, v in enumerate(verts)}
+    nv = len(verts)
+    S = np.zeros((nv, nv))
+    M = np.zeros((nv, nv))
+    for t in range(len(tris)):
+        f = F[t]
+        P = sk.V[f]
+        A = sk.area[tris[t]]
+        n = np.cross(P[1] - P[0], P[2] - P[0])
+        g = [np.cross(n, P[(a + 2) % 3] - P[(a + 1) % 3]) / (n @ n) for a in range(3)]
+        for a in range(3):
+            for b in range(3):
+                S[pos[f[a]], pos[f[b]]] += A * (g[a] @ g[b])
+                M[pos[f[a]], pos[f[b]]] += A * (2.0 if a == b else 1.0) / 12.0
+    return verts, pos, S, M
+
+
+def loop_map(sk: Skeleton, i: int, pos):
+    """L[e, v]: RWG coefficients of n_i x grad(phi_v), L[e, lo] = 1/l, L[e, hi] = -1/l."""
+    E = sk.edges[i]
+    L = np.zeros((len(E), len(pos)))
+    le = np.linalg.norm(sk.V[E[:, 1]] - sk.V[E[:, 0]], axis=1)
+    for e, (lo, hi) in enumerate(E):
+        L[e, pos[lo]] = 1.0 / le[e]
+        L[e, pos[hi]] = -1.0 / le[e]
+    return L
+
+
 class BlockOSRC:
     """Block-OSRC preconditioner of an MTF system (Eq. 19)."""
 
@@ -88,10 +128,19 @@ class BlockOSRC:
             G = mass_matrix(sk, i)
             D = divdiv_matrix(sk, i)
             lam, V = scipy.linalg.eigh(D, G)
+            nirr = len(sk.tris[i]) - 1                 # rank of div on RWG_i
+            verts, pos, S, M = p1_matrices(sk, i)
+            mu, Phi = scipy.linalg.eigh(S, M)
+            if nirr + len(verts) - 1 != sk.N[i]:
+                raise ValueError("block-OSRC needs genus-0 subdomain boundaries")
+            U = loop_map(sk, i, pos) @ Phi[:, 1:] / np.sqrt(mu[1:])[None, :]
             area = float(np.sum(sk.area[sk.tris[i]]))
             keps = k[i] + 1j * damping(k[i], area, eps_scale)
-            f = 2 * k[i] / (keps * pade_sqrt(-lam / keps ** 2, Np, theta))
-            self.Ttil.append((V * f[None, :]) @ V.T)
+            f_irr = 2 * k[i] / (keps * pade_sqrt(-lam[-nirr:] / keps ** 2, Np, theta))
+            f_sol = (2 * keps / k[i]) * pade_sqrt(-mu[1:] / keps ** 2, Np, theta)
+            W = np.concatenate([V[:, -nirr:], U], axis=1)
+            f = np.concatenate([f_irr, f_sol])
+            self.Ttil.append((W * f[None, :]) @ W.T)
 
     def apply(self, r):
         """z = A~ r blockwise: z_D = rho^-1 T~ r_N, z_N = -rho T~ r_D."""

@@ -135,8 +135,19 @@ struct mtf_mesh_s {
   mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
   // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
   bool osrc_ready = false;
-  mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;
+  mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;   // W^T, W (per block), |xi|^2 per mode
+  mtf::DevBuf<int32_t> d_osrc_nirr;                      // irrotational modes per block
   std::vector<double> osrc_area;
+  // P1 (vertex) tables of every Gamma_i for the loop modes
+  std::vector<int32_t> p1_n;                             // vertices of Gamma_i
+  std::vector<int64_t> p1_off_h, p1_row_h;               // dense (V_i^2) and row offsets
+  int64_t p1_nmat = 0, p1_nrow = 0;
+  std::vector<int32_t> bt_lv;                            // local vertex index per triangle corner
+  std::vector<int32_t> edge_lohi;                        // per exchange row: local (lo, hi) vertex
+  std::vector<double> edge_len;                          // per exchange row: edge length
+  mtf::DevBuf<int32_t> d_bt_lv, d_p1_n, d_edge_lohi;
+  mtf::DevBuf<int64_t> d_p1_off;
+  mtf::DevBuf<double> d_edge_len;
 };
 
 namespace mtf {

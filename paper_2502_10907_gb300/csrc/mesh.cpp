@@ -122,6 +122,31 @@ mtf_mesh build_mesh(const double* V, int32_t nv, const int32_t* F, int32_t nt, c
         for (int a = 0; a < 3; ++a)
           for (int c = 0; c < 3; ++c) m->bt_v.push_back(m->V[3 * f[a] + c]);
       }
+      // P1 (vertex) tables of Gamma_i: local vertex ids, per-dof (lo, hi) and length
+      {
+        std::vector<int32_t> verts;
+        for (int64_t q = B.bt_off; q < bt; ++q)
+          for (int a = 0; a < 3; ++a) verts.push_back(m->F[3 * m->bt_tri[q] + a]);
+        std::sort(verts.begin(), verts.end());
+        verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+        m->p1_n.push_back(int32_t(verts.size()));
+        auto loc = [&](int32_t v) { return int32_t(std::lower_bound(verts.begin(), verts.end(), v) - verts.begin()); };
+        for (int64_t q = B.bt_off; q < bt; ++q)
+          for (int a = 0; a < 3; ++a) m->bt_lv.push_back(loc(m->F[3 * m->bt_tri[q] + a]));
+        for (size_t d = 0; d < uk.size(); ++d) {
+          const int32_t lo = int32_t(uk[d] / (int64_t(nv) + 1)), hi = int32_t(uk[d] % (int64_t(nv) + 1));
+          m->edge_lohi.push_back(loc(lo));
+          m->edge_lohi.push_back(loc(hi));
+          const double* pl = &m->V[3 * lo];
+          const double* ph = &m->V[3 * hi];
+          m->edge_len.push_back(std::sqrt((pl[0] - ph[0]) * (pl[0] - ph[0]) + (pl[1] - ph[1]) * (pl[1] - ph[1]) +
+                                          (pl[2] - ph[2]) * (pl[2] - ph[2])));
+        }
+        m->p1_off_h.push_back(m->p1_nmat);
+        m->p1_row_h.push_back(m->p1_nrow);
+        m->p1_nmat += int64_t(verts.size()) * int64_t(verts.size());
+        m->p1_nrow += int64_t(verts.size());
+      }
       B.dof_off = dofo;
       B.mat_off = mato;
       B.row_off = rowo;
@@ -246,6 +271,11 @@ void upload_mesh(mtf_mesh m, cudaStream_t s) {
   m->d_sing.upload(m->sing, s);
   m->d_xent.upload(m->xent, s);
   m->d_dof_bt.upload(m->dof_bt, s);
+  m->d_bt_lv.upload(m->bt_lv, s);
+  m->d_p1_n.upload(m->p1_n, s);
+  m->d_p1_off.upload(m->p1_off_h, s);
+  m->d_edge_lohi.upload(m->edge_lohi, s);
+  m->d_edge_len.upload(m->edge_len, s);
   std::vector<int64_t> mo, bo, dofo, rowo;
   std::vector<int32_t> N, T, row_blk;
   m->reg_cta_prefix.assign(1, 0);

@@ -1,16 +1,21 @@
 // Block-OSRC preconditioner of Sec. 4.4 (Eq. 19):
 //   A~_i = [[0, rho_i^-1 T~], [-rho_i T~, 0]],  T~ ~ EtM ~ T^-1.
-// Discretisation (the paper leaves it to the cited OSRC work): with the RWG
-// mass G and div-div matrix D of Gamma_i and the generalised eigenpairs
-// D v = lambda G v, V^T G V = I,
-//   T~ = V diag(f) V^T,  f(lambda) = 2k / (k_eps P(-lambda / k_eps^2)),
+// Discretisation (the paper leaves it to the cited OSRC work): RWG_i splits
+// G-orthogonally (G the RWG mass) into irrotational modes, eigenpairs
+// D v = lambda G v (lambda > 0, D the div-div matrix, |xi|^2 = lambda), and
+// loop modes L phi / sqrt(mu) from the P1 Laplace-Beltrami eigenpairs
+// S phi = mu M phi (L phi = RWG coefficients of n x grad phi, |xi|^2 = mu).
+// With W the G-orthonormal basis of both and Z = -|xi|^2 / k_eps^2,
+//   T~ = W diag(f) W^T,  f = 2k / (k_eps P(Z)) (irrotational),
+//                        f = (2 k_eps / k) P(Z) (loops),
 // where P is the rotating-branch-cut Pade approximant of sqrt(1 + z) of order
 // N_p and angle theta (Milinazzo, Zala & Brooke 1997) and k_eps = k + i eps,
 // eps = c k^{1/3} R^{-2/3}, R the radius of the sphere with Gamma_i's area.
-// The eigenpairs depend on the mesh only and are computed once (FP32 dense
-// symmetric-definite eigensolver); f depends on k and is recomputed at every
-// assembly.  The apply is two dense FP32 passes per block, t = V^T r and
-// z = V (f t), HBM-bound like the block matvec.
+// the two factors of the OSRC magnetic-to-electric operator.  The eigenpairs
+// depend on the mesh only and are computed once (FP32 dense symmetric-
+// definite eigensolver); f depends on k and is recomputed at every assembly.
+// The apply is two dense FP32 passes per block, t = W^T r and z = W (f t),
+// HBM-bound like the block matvec.
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -55,6 +60,67 @@ __global__ void k_gram_divdiv(const double* __restrict__ bt_v, const double* __r
     }
 }
 
+// dense P1 Laplace-Beltrami stiffness S and mass M of every block
+__global__ void k_p1_matrices(const double* __restrict__ bt_v, const double* __restrict__ bt_area,
+                              const int32_t* __restrict__ bt_lv, const int32_t* __restrict__ bt_blk,
+                              const int64_t* __restrict__ p1_off, const int32_t* __restrict__ p1_n, int64_t n_bt,
+                              float* __restrict__ S, float* __restrict__ M) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n_bt) return;
+  const int i = bt_blk[q];
+  const int nv = p1_n[i];
+  const double* P = bt_v + 9 * q;
+  const double A = bt_area[q];
+  double e1[3], e2[3], n[3];
+  for (int c = 0; c < 3; ++c) {
+    e1[c] = P[3 + c] - P[c];
+    e2[c] = P[6 + c] - P[c];
+  }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  double g[3][3];  // grad of barycentric a = n x (P_{a+2} - P_{a+1}) / |n|^2
+  for (int a = 0; a < 3; ++a) {
+    double t[3];
+    for (int c = 0; c < 3; ++c) t[c] = P[3 * ((a + 2) % 3) + c] - P[3 * ((a + 1) % 3) + c];
+    g[a][0] = (n[1] * t[2] - n[2] * t[1]) / nn;
+    g[a][1] = (n[2] * t[0] - n[0] * t[2]) / nn;
+    g[a][2] = (n[0] * t[1] - n[1] * t[0]) / nn;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const int64_t e = p1_off[i] + int64_t(bt_lv[3 * q + a]) * nv + bt_lv[3 * q + b];
+      atomicAdd(S + e, float(A * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2])));
+      atomicAdd(M + e, float(A * (a == b ? 2.0 : 1.0) / 12.0));
+    }
+}
+
+// W (column-major, N x N per block): columns j < nirr the irrotational
+// eigenvectors V[:, N - nirr + j]; columns nirr + k the loop modes
+// L Phi[:, k+1] / sqrt(mu_{k+1}), L[e, lo] = 1/l_e, L[e, hi] = -1/l_e.
+// eig[row_off + j] receives the matching |xi|^2.
+__global__ void k_build_w(const float* __restrict__ V, const float* __restrict__ lam, const float* __restrict__ Phi,
+                          const float* __restrict__ mu, const int32_t* __restrict__ edge_lohi,
+                          const double* __restrict__ edge_len, int N, int nirr, int nv, float* __restrict__ W,
+                          float* __restrict__ eig) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(N) * N) return;
+  const int j = int(t / N), e = int(t % N);  // column j, row e
+  float v;
+  if (j < nirr) {
+    v = V[int64_t(N - nirr + j) * N + e];
+    if (e == 0) eig[j] = lam[N - nirr + j];
+  } else {
+    const int k = j - nirr + 1;
+    const float* ph = Phi + int64_t(k) * nv;
+    const float sm = sqrtf(fmaxf(mu[k], 1e-30f));
+    v = float((ph[edge_lohi[2 * e]] - ph[edge_lohi[2 * e + 1]]) / (edge_len[e] * sm));
+    if (e == 0) eig[j] = mu[k];
+  }
+  W[t] = v;
+}
+
 // VR (row-major V) from the eigensolver output (column-major V = row-major V^T)
 __global__ void k_transpose_block(const float* __restrict__ Vt, int N, float* __restrict__ VR) {
   __shared__ float tile[32][33];
@@ -70,13 +136,16 @@ __global__ void k_transpose_block(const float* __restrict__ Vt, int N, float* __
   }
 }
 
-// f_j = 2k / (k_eps P(-lambda_j / k_eps^2)) per (block, j); Pade data in pd
+// symbol per (block, mode j) with Z = -|xi|^2 / k_eps^2:
+//   irrotational (j < nirr): f = 2k / (k_eps P(Z)),  loop: f = (2 k_eps / k) P(Z)
 __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __restrict__ row_blk, int64_t n_rows,
+                              const int64_t* __restrict__ blk_row_off, const int32_t* __restrict__ nirr_blk,
                               const double* __restrict__ kk, const double* __restrict__ keps,
                               const double* __restrict__ pd, int np, float2* __restrict__ f) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
   const int i = row_blk[r];
+  const bool irr = (r - blk_row_off[i]) < nirr_blk[i];
   // complex arithmetic written out: (re, im) pairs
   const double kr = keps[2 * i], ki = keps[2 * i + 1];
   const double k2r = kr * kr - ki * ki, k2i = 2 * kr * ki;          // k_eps^2
@@ -93,9 +162,13 @@ __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __re
     Pi += (ni * dr - nr * di) / dn;
   }
   const double er = kr * Pr - ki * Pi, ei = kr * Pi + ki * Pr;     // k_eps P
-  const double en = er * er + ei * ei;
-  const double num = 2.0 * kk[2 * i];
-  f[r] = make_float2(float(num * er / en), float(-num * ei / en));
+  const double k0 = kk[2 * i];
+  if (irr) {
+    const double en = er * er + ei * ei;
+    f[r] = make_float2(float(2.0 * k0 * er / en), float(-2.0 * k0 * ei / en));
+  } else {
+    f[r] = make_float2(float(2.0 * er / k0), float(2.0 * ei / k0));
+  }
 }
 
 // pass 1: t[c][slot][row] = f_row * sum_m Vt[row][m] r32[c][slot block][m]; warp per (row, c)
@@ -239,11 +312,7 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   MTF_REQUIRE(cusolverDnSetStream(h, s) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnSetStream failed");
   DevBuf<int> info;
   info.alloc(1);
-  for (int i = 0; i < m->nd; ++i) {
-    const int N = m->blk[i].N;
-    float* A = m->d_osrc_Vt.p + m->blk[i].mat_off;
-    float* B = G.p + m->blk[i].mat_off;
-    float* W = m->d_osrc_lam.p + m->blk[i].row_off;
+  auto sygvd = [&](int N, float* A, float* B, float* W, const std::string& what) {
     int lwork = 0;
     MTF_REQUIRE(cusolverDnSsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
                                             N, A, N, B, N, W, &lwork) == CUSOLVER_STATUS_SUCCESS,
@@ -256,11 +325,42 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
     int hinfo = 0;
     MTF_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     MTF_CUDA(cudaStreamSynchronize(s));
-    MTF_REQUIRE(hinfo == 0, MTF_ERR_CUDA, "OSRC eigensolver failed for block " + std::to_string(i) +
-                                              " (info " + std::to_string(hinfo) + ")");
+    MTF_REQUIRE(hinfo == 0, MTF_ERR_CUDA, "OSRC eigensolver failed for " + what + " (info " + std::to_string(hinfo) + ")");
+  };
+  // P1 Laplace-Beltrami pencils (S, M) per block
+  DevBuf<float> S1, M1, mu, lam_tmp;
+  S1.alloc(size_t(m->p1_nmat));
+  M1.alloc(size_t(m->p1_nmat));
+  mu.alloc(size_t(m->p1_nrow));
+  lam_tmp.alloc(size_t(m->n_rows));
+  MTF_CUDA(cudaMemsetAsync(S1.p, 0, S1.n * sizeof(float), s));
+  MTF_CUDA(cudaMemsetAsync(M1.p, 0, M1.n * sizeof(float), s));
+  MTF_LAUNCH(KID_MISC, s, k_p1_matrices<<<unsigned((m->n_bt + 127) / 128), 128, 0, s>>>(
+      m->d_bt_v.p, m->d_bt_area.p, m->d_bt_lv.p, m->d_bt_blk.p, m->d_p1_off.p, m->d_p1_n.p, m->n_bt, S1.p, M1.p));
+  DevBuf<float> Wtmp;
+  for (int i = 0; i < m->nd; ++i) {
+    const int N = m->blk[i].N, nv = m->p1_n[i];
+    const int nirr = m->blk[i].T - 1;
+    MTF_REQUIRE(nirr + nv - 1 == N, MTF_ERR_MESH,
+                "block-OSRC needs genus-0 subdomain boundaries (Gamma_" + std::to_string(i) + ")");
+    float* A = m->d_osrc_Vt.p + m->blk[i].mat_off;
+    sygvd(N, A, G.p + m->blk[i].mat_off, lam_tmp.p + m->blk[i].row_off, "the div-div pencil of block " + std::to_string(i));
+    sygvd(nv, S1.p + m->p1_off_h[i], M1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
+          "the Laplace-Beltrami pencil of block " + std::to_string(i));
+    // W = [irrotational eigenvectors, loop modes] -> Wtmp, then back into Vt
+    Wtmp.alloc(size_t(N) * N);
+    MTF_LAUNCH(KID_MISC, s, k_build_w<<<unsigned((int64_t(N) * N + 255) / 256), 256, 0, s>>>(
+        A, lam_tmp.p + m->blk[i].row_off, S1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
+        m->d_edge_lohi.p + 2 * m->blk[i].row_off, m->d_edge_len.p + m->blk[i].row_off, N, nirr, nv, Wtmp.p,
+        m->d_osrc_lam.p + m->blk[i].row_off));
+    MTF_CUDA(cudaMemcpyAsync(A, Wtmp.p, size_t(N) * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
     dim3 tg{unsigned((N + 31) / 32), unsigned((N + 31) / 32), 1u};
     MTF_LAUNCH(KID_MISC, s, k_transpose_block<<<tg, dim3(32, 8), 0, s>>>(A, N, m->d_osrc_VR.p + m->blk[i].mat_off));
   }
+  std::vector<int32_t> nirr_h(m->nd);
+  for (int i = 0; i < m->nd; ++i) nirr_h[i] = m->blk[i].T - 1;
+  m->d_osrc_nirr.upload(nirr_h, s);
   // areas of Gamma_i for the damping parameter
   m->osrc_area.assign(m->nd, 0.0);
   for (int64_t q = 0; q < m->n_bt; ++q) m->osrc_area[m->bt_blk[q]] += m->bt_area[q];
@@ -308,8 +408,8 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   d_keps.upload(keps, s);
   sys->d_osrc_f.alloc(size_t(m->n_rows) * 2);
   MTF_LAUNCH(KID_MISC, s, k_osrc_symbol<<<unsigned((m->n_rows + 127) / 128), 128, 0, s>>>(
-      m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, sys->d_k.p, d_keps.p, d_pd.p, np,
-      reinterpret_cast<float2*>(sys->d_osrc_f.p)));
+      m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, m->d_blk_row_off.p, m->d_osrc_nirr.p, sys->d_k.p, d_keps.p,
+      d_pd.p, np, reinterpret_cast<float2*>(sys->d_osrc_f.p)));
   MTF_CUDA(cudaStreamSynchronize(s));  // d_pd / d_keps are freed on return
 }
 

@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 import mtf_inputs as mi
-from oracle.osrc import (pade_sqrt, pade_coefficients, divdiv_matrix, BlockOSRC, gmres_iterations)
+from oracle.osrc import (pade_sqrt, pade_coefficients, divdiv_matrix, BlockOSRC, gmres_iterations,
+                         p1_matrices, loop_map)
 from oracle.operators import mass_matrix
 from tests.oracle_helpers import sphere_system, skeleton_of
 
@@ -38,6 +39,22 @@ def test_divdiv_matrix_rank_and_symmetry():
     # div maps RWG onto zero-mean piecewise constants: rank T - 1
     assert np.sum(ev > 1e-10 * ev.max()) == T - 1
     assert np.all(np.linalg.eigvalsh(G) > 0)
+
+
+def test_loop_map_is_divergence_free_and_isometric():
+    """L maps nodal P1 values to the RWG coefficients of n x grad(phi):
+    div L phi = 0 exactly (D L = 0) and ||L phi||_G^2 = phi^T S phi."""
+    sk = skeleton_of(mi.split_sphere(3))
+    for i in range(sk.n_domains):
+        verts, pos, S, M = p1_matrices(sk, i)
+        L = loop_map(sk, i, pos)
+        D = divdiv_matrix(sk, i)
+        G = mass_matrix(sk, i)
+        assert np.abs(D @ L).max() < 1e-12 * np.abs(D).max()
+        assert np.abs(L.T @ G @ L - S).max() < 1e-12 * np.abs(S).max()
+        # P1 Laplace-Beltrami: constants in the kernel, M symmetric positive definite
+        assert np.abs(S @ np.ones(len(verts))).max() < 1e-12
+        assert np.all(np.linalg.eigvalsh(M) > 0)
 
 
 def test_block_osrc_speeds_up_gmres(oracle_cache):
