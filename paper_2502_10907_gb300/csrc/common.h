@@ -133,10 +133,14 @@ struct mtf_mesh_s {
   std::vector<int64_t> reg_cta_prefix;       // regular-pair CTA prefix over blocks
   mtf::DevBuf<int64_t> d_reg_cta_prefix;
   mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
+  int64_t n_tiles8 = 0, n_tiles32 = 0;       // 8- and 32-row tiles over all blocks (streaming kernels)
+  mtf::DevBuf<int32_t> d_tile_blk, d_tile_row0, d_tile32_blk, d_tile32_row0;
   // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
   bool osrc_ready = false;
   mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;   // W^T, W (per block), |xi|^2 per mode
   mtf::DevBuf<int32_t> d_osrc_nirr;                      // irrotational modes per block
+  std::vector<int64_t> osrc_off_h;                       // padded W offsets per block
+  mtf::DevBuf<int64_t> d_osrc_off;
   std::vector<double> osrc_area;
   // P1 (vertex) tables of every Gamma_i for the loop modes
   std::vector<int32_t> p1_n;                             // vertices of Gamma_i
@@ -202,6 +206,15 @@ void osrc_setup(mtf_system sys, cudaStream_t s);
 // z = A~ r (block-OSRC, Eq. 19); column c of r (z) at r + 2 c ldr (z + 2 c ldz)
 void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
                        cudaStream_t s);
+void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
+                           cudaStream_t s);
+// FP32 complex in / out matvec of the FP32-stored operator (column strides in complex units)
+void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
+                       cudaStream_t s);
+// inner solve of the mixed path: FP32 Krylov basis, FP64 reductions; solves
+// M d = r (d starts at 0) to the relative tolerance tol
+mtf_status gmres_core32(mtf_system sys, int nrhs, const double* r_dev, double* d_dev, double tol, int max_iter,
+                        std::vector<int>& iters, int& restarts, std::vector<double>& rel, cudaStream_t s);
 // matvec flavours: storage / accumulation precision
 enum MatvecKind { MV_AUTO = 0, MV_FP64 = 1, MV_FP32 = 2, MV_FP32_ACC64 = 3 };
 void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, double* y, int64_t ldy,

@@ -121,8 +121,8 @@ __global__ void k_build_w(const float* __restrict__ V, const float* __restrict__
   W[t] = v;
 }
 
-// VR (row-major V) from the eigensolver output (column-major V = row-major V^T)
-__global__ void k_transpose_block(const float* __restrict__ Vt, int N, float* __restrict__ VR) {
+// W row-major padded (ld) from column-major W (= row-major W^T, N x N)
+__global__ void k_transpose_block(const float* __restrict__ Vt, int N, int ld, float* __restrict__ VR) {
   __shared__ float tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -132,8 +132,16 @@ __global__ void k_transpose_block(const float* __restrict__ Vt, int N, float* __
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int row = bx + r, col = by + threadIdx.x;
-    if (row < N && col < N) VR[int64_t(row) * N + col] = tile[threadIdx.x][r];
+    if (row < N && col < N) VR[int64_t(row) * ld + col] = tile[threadIdx.x][r];
   }
+}
+
+// W^T row-major padded (ld): row j = column j of W; pad entries are zero
+__global__ void k_pad_copy(const float* __restrict__ W, int N, int ld, float* __restrict__ Wt) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(N) * ld) return;
+  const int j = int(t / ld), e = int(t % ld);
+  Wt[t] = e < N ? W[int64_t(j) * N + e] : 0.0f;
 }
 
 // symbol per (block, mode j) with Z = -|xi|^2 / k_eps^2:
@@ -171,106 +179,124 @@ __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __re
   }
 }
 
-// pass 1: t[c][slot][row] = f_row * sum_m Vt[row][m] r32[c][slot block][m]; warp per (row, c)
-__global__ void __launch_bounds__(256) k_osrc_pass1(const float* __restrict__ Vt, const float* __restrict__ r32,
-                                                    const float2* __restrict__ f, const int32_t* __restrict__ row_blk,
-                                                    const int64_t* __restrict__ blk_row_off,
-                                                    const int32_t* __restrict__ blk_N,
-                                                    const int64_t* __restrict__ blk_dof_off,
-                                                    const int64_t* __restrict__ blk_mat_off, int64_t n_rows,
-                                                    int64_t n_total, int nrhs, float2* __restrict__ t) {
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= n_rows * nrhs) return;
-  const int64_t r = w % n_rows;
-  const int c = int(w / n_rows);
-  const int i = row_blk[r];
-  const int N = blk_N[i];
-  const int64_t j = r - blk_row_off[i];
-  const float* row = Vt + blk_mat_off[i] + j * N;
-  const float* rv = r32 + 2 * (int64_t(c) * n_total + blk_dof_off[i]);
-  float dr = 0, di = 0, nr = 0, ni = 0;
-  for (int m0 = lane; m0 < N; m0 += 32 * 8) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (m0 + 32 * u < N) ? row[m0 + 32 * u] : 0.0f;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int m = m0 + 32 * u;
-      if (m >= N) break;
-      const float2 a = *reinterpret_cast<const float2*>(rv + 2 * m);
-      const float2 b = *reinterpret_cast<const float2*>(rv + 2 * (N + m));
-      dr = fmaf(v[u], a.x, dr);
-      di = fmaf(v[u], a.y, di);
-      nr = fmaf(v[u], b.x, nr);
-      ni = fmaf(v[u], b.y, ni);
-    }
-  }
-  for (int s = 16; s > 0; s >>= 1) {
-    dr += __shfl_xor_sync(0xffffffffu, dr, s);
-    di += __shfl_xor_sync(0xffffffffu, di, s);
-    nr += __shfl_xor_sync(0xffffffffu, nr, s);
-    ni += __shfl_xor_sync(0xffffffffu, ni, s);
-  }
-  if (lane == 0) {
-    const float2 fr = f[r];
-    float2* tc = t + 2 * (int64_t(c) * n_rows + blk_row_off[i]);
-    tc[j] = make_float2(fr.x * dr - fr.y * di, fr.x * di + fr.y * dr);          // f V^T r_D
-    tc[N + j] = make_float2(fr.x * nr - fr.y * ni, fr.x * ni + fr.y * nr);      // f V^T r_N
-  }
-}
+// Streaming passes (same pattern as the FP32 matvec): CTA = 8 rows of one
+// block, one warp per row streaming a padded FP32 row with float4 loads, the
+// block's complex input pair (slot D, slot N; NC right-hand sides) staged in
+// shared memory in chunks.
+//   PASS 1: rows of W^T (modes j), input r (tested residual), output
+//           t_D[j] = f_j (W^T r_D)_j, t_N[j] = f_j (W^T r_N)_j (FP32).
+//   PASS 2: rows of W (dofs e), input t, output z_D = rho^-1 (W t_N)_e,
+//           z_N = -rho (W t_D)_e (FP64).
+constexpr int kOsChunk = 1024;
 
-// pass 2: z_D = rho^-1 V (f V^T r_N), z_N = -rho V (f V^T r_D); warp per (row, c)
-__global__ void __launch_bounds__(256) k_osrc_pass2(const float* __restrict__ VR, const float2* __restrict__ t,
-                                                    const double* __restrict__ rho,
-                                                    const int32_t* __restrict__ row_blk,
-                                                    const int64_t* __restrict__ blk_row_off,
-                                                    const int32_t* __restrict__ blk_N,
-                                                    const int64_t* __restrict__ blk_dof_off,
-                                                    const int64_t* __restrict__ blk_mat_off, int64_t n_rows,
-                                                    int nrhs, double* __restrict__ z, int64_t ldz) {
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= n_rows * nrhs) return;
-  const int64_t r = w % n_rows;
-  const int c = int(w / n_rows);
-  const int i = row_blk[r];
+constexpr int kOsRowsPerWarp = 4;  // a CTA covers 32 rows, amortising one staging
+constexpr int kOsRowsPerCta = 8 * kOsRowsPerWarp;
+
+template <int PASS, int NC, class ZT>
+__global__ void __launch_bounds__(256) k_osrc_stream(
+    const float* __restrict__ Wm, const int64_t* __restrict__ osrc_off, const float* __restrict__ vin,
+    int64_t ldin, const float2* __restrict__ f, const double* __restrict__ rho,
+    const int32_t* __restrict__ tile_blk, const int32_t* __restrict__ tile_row0,
+    const int32_t* __restrict__ blk_N, const int64_t* __restrict__ blk_dof_off,
+    const int64_t* __restrict__ blk_row_off, int64_t n_total, int c0, float2* __restrict__ tout,
+    ZT* __restrict__ zout, int64_t ldz) {
+  constexpr int RW = kOsRowsPerWarp;
+  extern __shared__ float2 vs[];  // [NC][2][kOsChunk]
+  const int i = tile_blk[blockIdx.x];
+  const int r0 = tile_row0[blockIdx.x];
   const int N = blk_N[i];
-  const int64_t m = r - blk_row_off[i];
-  const float* row = VR + blk_mat_off[i] + m * N;
-  const float2* tc = t + 2 * (int64_t(c) * n_rows + blk_row_off[i]);
-  float dr = 0, di = 0, nr = 0, ni = 0;
-  for (int j0 = lane; j0 < N; j0 += 32 * 8) {
-    float v[8];
+  const int ld = (N + 3) & ~3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // input vectors: complex FP32, per rhs c at vin + 2 (c * n_total + dof_off_i), slots at +0 / +N
+  const int64_t base = blk_dof_off[i];
+  const float4* wr[RW];
+  bool act[RW];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (j0 + 32 * u < N) ? row[j0 + 32 * u] : 0.0f;
+  for (int q = 0; q < RW; ++q) {
+    const int row = r0 + q * 8 + warp;
+    act[q] = row < N;
+    wr[q] = reinterpret_cast<const float4*>(Wm + osrc_off[i] + int64_t(act[q] ? row : 0) * ld);
+  }
+  float acc[RW][NC][4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int j = j0 + 32 * u;
-      if (j >= N) break;
-      const float2 a = tc[j], b = tc[N + j];
-      dr = fmaf(v[u], a.x, dr);
-      di = fmaf(v[u], a.y, di);
-      nr = fmaf(v[u], b.x, nr);
-      ni = fmaf(v[u], b.y, ni);
+  for (int q = 0; q < RW; ++q)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[q][c][t] = 0.f;
+  for (int cb = 0; cb < N; cb += kOsChunk) {
+    const int clen = min(kOsChunk, N - cb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < NC * 2 * kOsChunk; t += blockDim.x) {
+      const int c = t / (2 * kOsChunk), rem = t % (2 * kOsChunk), slot = rem / kOsChunk, e = rem % kOsChunk;
+      vs[t] = e < clen ? *reinterpret_cast<const float2*>(vin + 2 * ((c0 + c) * ldin + base + slot * N + cb + e))
+                       : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int nq = (clen + 3) >> 2;  // float4 groups in this chunk (row padding is zero)
+    for (int g = lane; g < nq; g += 32) {
+      float4 w4[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) w4[q] = act[q] ? __ldg(wr[q] + (cb >> 2) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 a = vs[(c * 2) * kOsChunk + 4 * g + e];
+          const float2 b = vs[(c * 2 + 1) * kOsChunk + 4 * g + e];
+#pragma unroll
+          for (int q = 0; q < RW; ++q) {
+            const float wv = e == 0 ? w4[q].x : (e == 1 ? w4[q].y : (e == 2 ? w4[q].z : w4[q].w));
+            acc[q][c][0] = fmaf(wv, a.x, acc[q][c][0]);
+            acc[q][c][1] = fmaf(wv, a.y, acc[q][c][1]);
+            acc[q][c][2] = fmaf(wv, b.x, acc[q][c][2]);
+            acc[q][c][3] = fmaf(wv, b.y, acc[q][c][3]);
+          }
+        }
+      }
     }
   }
-  for (int s = 16; s > 0; s >>= 1) {
-    dr += __shfl_xor_sync(0xffffffffu, dr, s);
-    di += __shfl_xor_sync(0xffffffffu, di, s);
-    nr += __shfl_xor_sync(0xffffffffu, nr, s);
-    ni += __shfl_xor_sync(0xffffffffu, ni, s);
-  }
-  if (lane == 0) {
-    const double rr = rho[2 * i], ri = rho[2 * i + 1];
-    const double rn = rr * rr + ri * ri;
-    const double ir = rr / rn, ii = -ri / rn;
-    double* zc = z + 2 * (int64_t(c) * ldz + blk_dof_off[i]);
-    // z_D = rho^-1 (V t_N), z_N = -rho (V t_D)
-    zc[2 * m] = ir * nr - ii * ni;
-    zc[2 * m + 1] = ir * ni + ii * nr;
-    zc[2 * (N + m)] = -(rr * dr - ri * di);
-    zc[2 * (N + m) + 1] = -(rr * di + ri * dr);
+#pragma unroll
+  for (int q = 0; q < RW; ++q)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float v = acc[q][c][t];
+#pragma unroll
+        for (int s2 = 16; s2 > 0; s2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s2);
+        acc[q][c][t] = v;
+      }
+  if (lane >= NC) return;
+  const int col = c0 + lane;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
+    if (!act[q]) continue;
+    const int row = r0 + q * 8 + warp;
+    float a0 = acc[q][0][0], a1 = acc[q][0][1], a2 = acc[q][0][2], a3 = acc[q][0][3];
+#pragma unroll
+    for (int c = 1; c < NC; ++c)
+      if (lane == c) {
+        a0 = acc[q][c][0];
+        a1 = acc[q][c][1];
+        a2 = acc[q][c][2];
+        a3 = acc[q][c][3];
+      }
+    if (PASS == 1) {
+      const float2 fr = f[blk_row_off[i] + row];
+      float2* tc = tout + (int64_t(col) * n_total + base);
+      tc[row] = make_float2(fr.x * a0 - fr.y * a1, fr.x * a1 + fr.y * a0);
+      tc[N + row] = make_float2(fr.x * a2 - fr.y * a3, fr.x * a3 + fr.y * a2);
+    } else {
+      const double rr = rho[2 * i], ri = rho[2 * i + 1];
+      const double rn = rr * rr + ri * ri;
+      const double ir = rr / rn, ii = -ri / rn;
+      ZT* zc = zout + 2 * (int64_t(col) * ldz + base);
+      zc[2 * row] = ZT(ir * a2 - ii * a3);
+      zc[2 * row + 1] = ZT(ir * a3 + ii * a2);
+      zc[2 * (N + row)] = ZT(-(rr * a0 - ri * a1));
+      zc[2 * (N + row) + 1] = ZT(-(rr * a1 + ri * a0));
+    }
   }
 }
 
@@ -299,15 +325,26 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   MTF_CUDA(cudaMemcpyToSymbolAsync(c_os_t, rule.t, sizeof(rule.t), 0, cudaMemcpyHostToDevice, s));
   MTF_CUDA(cudaMemcpyToSymbolAsync(c_os_w, rule.w, sizeof(rule.w), 0, cudaMemcpyHostToDevice, s));
   DevBuf<float> G;
-  m->d_osrc_Vt.alloc(size_t(m->n_mat));
-  m->d_osrc_VR.alloc(size_t(m->n_mat));
+  // padded offsets of the per-block W matrices
+  m->osrc_off_h.assign(m->nd, 0);
+  int64_t po = 0;
+  for (int i = 0; i < m->nd; ++i) {
+    m->osrc_off_h[i] = po;
+    po += int64_t((m->blk[i].N + 3) & ~3) * m->blk[i].N;
+  }
+  m->d_osrc_off.upload(m->osrc_off_h, s);
+  m->d_osrc_Vt.alloc(size_t(po));
+  m->d_osrc_VR.alloc(size_t(po));
   m->d_osrc_lam.alloc(size_t(m->n_rows));
+  MTF_CUDA(cudaMemsetAsync(m->d_osrc_VR.p, 0, size_t(po) * sizeof(float), s));
+  DevBuf<float> Dd;
+  Dd.alloc(size_t(m->n_mat));
   G.alloc(size_t(m->n_mat));
   MTF_CUDA(cudaMemsetAsync(G.p, 0, size_t(m->n_mat) * sizeof(float), s));
-  MTF_CUDA(cudaMemsetAsync(m->d_osrc_Vt.p, 0, size_t(m->n_mat) * sizeof(float), s));
+  MTF_CUDA(cudaMemsetAsync(Dd.p, 0, size_t(m->n_mat) * sizeof(float), s));
   MTF_LAUNCH(KID_MISC, s, k_gram_divdiv<<<unsigned((m->n_bt + 127) / 128), 128, 0, s>>>(
       m->d_bt_v.p, m->d_bt_c.p, m->d_bt_area.p, m->d_bt_dof.p, m->d_bt_blk.p, m->d_blk_mat_off.p, m->d_blk_N.p,
-      m->n_bt, G.p, m->d_osrc_Vt.p));
+      m->n_bt, G.p, Dd.p));
   cusolverDnHandle_t h = solver_handle();
   MTF_REQUIRE(cusolverDnSetStream(h, s) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnSetStream failed");
   DevBuf<int> info;
@@ -343,7 +380,7 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
     const int nirr = m->blk[i].T - 1;
     MTF_REQUIRE(nirr + nv - 1 == N, MTF_ERR_MESH,
                 "block-OSRC needs genus-0 subdomain boundaries (Gamma_" + std::to_string(i) + ")");
-    float* A = m->d_osrc_Vt.p + m->blk[i].mat_off;
+    float* A = Dd.p + m->blk[i].mat_off;
     sygvd(N, A, G.p + m->blk[i].mat_off, lam_tmp.p + m->blk[i].row_off, "the div-div pencil of block " + std::to_string(i));
     sygvd(nv, S1.p + m->p1_off_h[i], M1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
           "the Laplace-Beltrami pencil of block " + std::to_string(i));
@@ -353,10 +390,14 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
         A, lam_tmp.p + m->blk[i].row_off, S1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
         m->d_edge_lohi.p + 2 * m->blk[i].row_off, m->d_edge_len.p + m->blk[i].row_off, N, nirr, nv, Wtmp.p,
         m->d_osrc_lam.p + m->blk[i].row_off));
-    MTF_CUDA(cudaMemcpyAsync(A, Wtmp.p, size_t(N) * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    MTF_CUDA(cudaStreamSynchronize(s));
+    // padded row-major W^T (rows = modes) and W (rows = RWG dofs), ld = N rounded up to 4
+    const int ld = (N + 3) & ~3;
     dim3 tg{unsigned((N + 31) / 32), unsigned((N + 31) / 32), 1u};
-    MTF_LAUNCH(KID_MISC, s, k_transpose_block<<<tg, dim3(32, 8), 0, s>>>(A, N, m->d_osrc_VR.p + m->blk[i].mat_off));
+    MTF_LAUNCH(KID_MISC, s, k_pad_copy<<<unsigned((int64_t(N) * ld + 255) / 256), 256, 0, s>>>(
+        Wtmp.p, N, ld, m->d_osrc_Vt.p + m->osrc_off_h[i]));
+    MTF_LAUNCH(KID_MISC, s, k_transpose_block<<<tg, dim3(32, 8), 0, s>>>(Wtmp.p, N, ld,
+                                                                         m->d_osrc_VR.p + m->osrc_off_h[i]));
+    MTF_CUDA(cudaStreamSynchronize(s));
   }
   std::vector<int32_t> nirr_h(m->nd);
   for (int i = 0; i < m->nd; ++i) nirr_h[i] = m->blk[i].T - 1;
@@ -413,21 +454,53 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   MTF_CUDA(cudaStreamSynchronize(s));  // d_pd / d_keps are freed on return
 }
 
+template <class ZT>
+static void osrc_passes(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  const int64_t n2 = 2 * m->n_total;
+  if (sys->d_osrc_t.n < size_t(n2) * nrhs) sys->d_osrc_t.alloc(size_t(n2) * nrhs);
+  const unsigned tiles = unsigned(m->n_tiles32);
+  const float2* f = reinterpret_cast<const float2*>(sys->d_osrc_f.p);
+  float2* t = reinterpret_cast<float2*>(sys->d_osrc_t.p);
+  for (int c0 = 0; c0 < nrhs; c0 += 4) {
+    const int nc = std::min(4, nrhs - c0);
+    const size_t smem = size_t(nc) * 2 * kOsChunk * sizeof(float2);
+#define OS_PASS(P, NC, W, VIN, LDIN)                                                                            \
+  do {                                                                                                         \
+    auto kfn = k_osrc_stream<P, NC, ZT>;                                                                       \
+    MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));               \
+    MTF_LAUNCH(KID_OSRC, s, kfn<<<tiles, 256, smem, s>>>(W, m->d_osrc_off.p, VIN, LDIN, f, sys->d_rho.p,       \
+                                                         m->d_tile32_blk.p, m->d_tile32_row0.p, m->d_blk_N.p,  \
+                                                         m->d_blk_dof_off.p, m->d_blk_row_off.p, m->n_total,   \
+                                                         c0, t, z, ldz));                                       \
+  } while (0)
+#define OS_BOTH(NC)                                                                                  \
+  do {                                                                                               \
+    OS_PASS(1, NC, m->d_osrc_Vt.p, r32, ldr);                                                        \
+    OS_PASS(2, NC, m->d_osrc_VR.p, reinterpret_cast<const float*>(sys->d_osrc_t.p), m->n_total);    \
+  } while (0)
+    if (nc == 1) OS_BOTH(1);
+    else if (nc == 2) OS_BOTH(2);
+    else if (nc == 3) OS_BOTH(3);
+    else OS_BOTH(4);
+#undef OS_BOTH
+#undef OS_PASS
+  }
+}
+
 void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
                        cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   const int64_t n2 = 2 * m->n_total;
   if (sys->d_osrc_r32.n < size_t(n2) * nrhs) sys->d_osrc_r32.alloc(size_t(n2) * nrhs);
-  if (sys->d_osrc_t.n < size_t(n2) * nrhs) sys->d_osrc_t.alloc(size_t(n2) * nrhs);
   MTF_LAUNCH(KID_OSRC, s, k_to_f32_cols<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(r, ldr, n2, nrhs, sys->d_osrc_r32.p));
-  const unsigned blocks = unsigned((m->n_rows * nrhs * 32 + 255) / 256);
-  MTF_LAUNCH(KID_OSRC, s, k_osrc_pass1<<<blocks, 256, 0, s>>>(
-      m->d_osrc_Vt.p, sys->d_osrc_r32.p, reinterpret_cast<const float2*>(sys->d_osrc_f.p), m->d_row_blk.p,
-      m->d_blk_row_off.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->n_rows, m->n_total, nrhs,
-      reinterpret_cast<float2*>(sys->d_osrc_t.p)));
-  MTF_LAUNCH(KID_OSRC, s, k_osrc_pass2<<<blocks, 256, 0, s>>>(
-      m->d_osrc_VR.p, reinterpret_cast<const float2*>(sys->d_osrc_t.p), sys->d_rho.p, m->d_row_blk.p,
-      m->d_blk_row_off.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->n_rows, nrhs, z, ldz));
+  osrc_passes<double>(sys, sys->d_osrc_r32.p, m->n_total, z, ldz, nrhs, s);
+}
+
+// FP32 in, FP32 out (the FP32-basis inner solver)
+void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
+                           cudaStream_t s) {
+  osrc_passes<float>(sys, r, ldr, z, ldz, nrhs, s);
 }
 
 }  // namespace mtf

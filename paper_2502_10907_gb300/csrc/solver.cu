@@ -166,6 +166,62 @@ __global__ void __launch_bounds__(256) k_dots_seg(const double* __restrict__ V, 
   }
 }
 
+// h[c*ldh + i] += sum_{k in segment} conj(V_i^c[k]) w^c[k]: CTA = one column
+// segment (<= 2048 entries of w staged in shared memory) x 16 basis vectors
+// (2 per warp, interleaved for 16 loads in flight); grid (segments,
+// ceil(rows/16), c).
+__global__ void __launch_bounds__(256) k_dots_stage(const double* __restrict__ V, const double* __restrict__ w,
+                                                    int64_t n, int ldv, int rows, double* __restrict__ h, int ldh,
+                                                    int64_t seg) {
+  extern __shared__ double2 ws[];
+  const int c = blockIdx.z;
+  const int64_t k0 = int64_t(blockIdx.x) * seg;
+  const int len = int(min(n, k0 + seg) - k0);
+  const double2* wc = reinterpret_cast<const double2*>(w) + int64_t(c) * n + k0;
+  for (int t = threadIdx.x; t < len; t += blockDim.x) ws[t] = wc[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * 16 + warp * 2;
+  if (i0 >= rows) return;
+  const bool two = i0 + 1 < rows;
+  const double2* v0 = reinterpret_cast<const double2*>(V) + (int64_t(c) * ldv + i0) * n + k0;
+  const double2* v1 = two ? v0 + n : v0;
+  double r0 = 0, q0 = 0, r1 = 0, q1 = 0;
+#pragma unroll 8
+  for (int t = lane; t < len; t += 32) {
+    const double2 a = v0[t], b = v1[t], x = ws[t];
+    r0 += a.x * x.x + a.y * x.y;
+    q0 += a.x * x.y - a.y * x.x;
+    r1 += b.x * x.x + b.y * x.y;
+    q1 += b.x * x.y - b.y * x.x;
+  }
+#pragma unroll
+  for (int s2 = 16; s2 > 0; s2 >>= 1) {
+    r0 += __shfl_xor_sync(0xffffffffu, r0, s2);
+    q0 += __shfl_xor_sync(0xffffffffu, q0, s2);
+    r1 += __shfl_xor_sync(0xffffffffu, r1, s2);
+    q1 += __shfl_xor_sync(0xffffffffu, q1, s2);
+  }
+  if (lane == 0) {
+    atomicAdd(h + 2 * (int64_t(c) * ldh + i0), r0);
+    atomicAdd(h + 2 * (int64_t(c) * ldh + i0) + 1, q0);
+    if (two) {
+      atomicAdd(h + 2 * (int64_t(c) * ldh + i0 + 1), r1);
+      atomicAdd(h + 2 * (int64_t(c) * ldh + i0 + 1) + 1, q1);
+    }
+  }
+}
+
+static void launch_dots(const double* V, const double* w, int64_t n, int ldv, int rows, double* h, int ldh, int nrhs,
+                        cudaStream_t s) {
+  const int64_t rg = (rows + 15) / 16;
+  const int64_t minseg = (n + 2047) / 2048;
+  const int64_t nseg = std::max<int64_t>(minseg, std::min<int64_t>((n + 511) / 512, 1200 / (rg * nrhs)));
+  const int64_t seg = (n + nseg - 1) / nseg;
+  dim3 g{unsigned(nseg), unsigned(rg), unsigned(nrhs)};
+  MTF_LAUNCH(KID_DOTS, s, k_dots_stage<<<g, 256, size_t(seg) * sizeof(double2), s>>>(V, w, n, ldv, rows, h, ldh, seg));
+}
+
 // w^c -= sum_{i<j} V_i^c h_i^c ; optionally ss[c] += ||w^c||^2 (after update).
 // CTA = 32 consecutive rows x 8 groups of basis vectors (i = g mod 8), the
 // group partial sums combined in shared memory; grid (ceil(n/32), c).
@@ -177,16 +233,19 @@ __global__ void __launch_bounds__(256) k_axpy_grp(const double* __restrict__ V, 
   const int64_t k = int64_t(blockIdx.x) * 32 + lane;
   __shared__ double2 part[8][32];
   __shared__ double red[32];
+  extern __shared__ double2 hs[];  // h of this rhs (j entries)
+  const double2* hc = reinterpret_cast<const double2*>(h) + int64_t(c) * ldh;
+  for (int t = threadIdx.x; t < j; t += blockDim.x) hs[t] = hc[t];
+  __syncthreads();
   double sr = 0, si = 0;
   if (k < n) {
     const double2* v = reinterpret_cast<const double2*>(V) + int64_t(c) * ldv * n + k;
-    const double* hc = h + 2 * int64_t(c) * ldh;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = grp; i < j; i += 8) {
       const double2 a = v[int64_t(i) * n];
-      const double hr = hc[2 * i], hi = hc[2 * i + 1];
-      sr += a.x * hr - a.y * hi;
-      si += a.x * hi + a.y * hr;
+      const double2 hv = hs[i];
+      sr += a.x * hv.x - a.y * hv.y;
+      si += a.x * hv.y + a.y * hv.x;
     }
   }
   part[grp][lane] = make_double2(sr, si);
@@ -362,10 +421,12 @@ static mtf_status gmres_core(mtf_system sys, int nrhs, const double* b_dev, doub
       dim3 ga(nblk(n, 256), unsigned(nrhs));
       dim3 gg(nblk(n, 32), unsigned(nrhs));
       double* ss = hN + 2 * nrhs;  // sum of squares scratch after the norms
-      MTF_LAUNCH(KID_DOTS, s, k_dots_seg<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hA, m + 1, seg));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, 0, s>>>(G.V.p, hA, j + 1, n, ldv, m + 1, -1.0, G.r.p, nullptr));
-      MTF_LAUNCH(KID_DOTS, s, k_dots_seg<<<gd, 256, 0, s>>>(G.V.p, G.r.p, n, ldv, hB, m + 1, seg));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, 0, s>>>(G.V.p, hB, j + 1, n, ldv, m + 1, -1.0, G.r.p, ss));
+      const size_t hsm = size_t(j + 1) * sizeof(double2);
+      (void)gd;
+      launch_dots(G.V.p, G.r.p, n, ldv, j + 1, hA, m + 1, nrhs, s);
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, hsm, s>>>(G.V.p, hA, j + 1, n, ldv, m + 1, -1.0, G.r.p, nullptr));
+      launch_dots(G.V.p, G.r.p, n, ldv, j + 1, hB, m + 1, nrhs, s);
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<gg, 256, hsm, s>>>(G.V.p, hB, j + 1, n, ldv, m + 1, -1.0, G.r.p, ss));
       // v_{j+1} = w / ||w||
       MTF_LAUNCH(KID_NORM, s, k_scale<<<ga, 256, 0, s>>>(G.r.p, n, ss, hN, G.V.p + 2 * size_t(j + 1) * n, int64_t(ldv) * n));
       MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, G.h.n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -441,7 +502,7 @@ static mtf_status gmres_core(mtf_system sys, int nrhs, const double* b_dev, doub
     if (jmax > 0) {
       MTF_CUDA(cudaMemcpyAsync(G.y.p, yhost.data(), yhost.size() * sizeof(double), cudaMemcpyHostToDevice, s));
       // x += Z y (flexible) or V y
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<dim3(nblk(n, 32), unsigned(nrhs)), 256, 0, s>>>(
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_grp<<<dim3(nblk(n, 32), unsigned(nrhs)), 256, size_t(jmax) * sizeof(double2), s>>>(
           pre ? G.Z.p : G.V.p, G.y.p, jmax, n, pre ? m : ldv, m + 1, 1.0, x_dev, nullptr));
       MTF_CUDA(cudaStreamSynchronize(s));  // yhost is reused next cycle
     }
