@@ -79,8 +79,10 @@ typedef struct {
   double osrc_theta;    /* branch-cut rotation angle (default pi/2)          */
   double osrc_eps_scale;/* damping eps = osrc_eps_scale k^(1/3) R^(-2/3)
                            with R the block's radius (default 0.39)          */
-  int32_t max_refine;   /* outer FP64 iterative-refinement steps in mixed
-                           mode (default 4)                                  */
+  int32_t max_refine;   /* mixed mode: outer FP64 refinement steps whose
+                           FP32 inner solve reached its tolerance (default 4);
+                           inner cycles that end on the restart length are
+                           restarts and count against max_iter only          */
 } mtf_options;
 
 typedef struct {

@@ -261,6 +261,7 @@ mtf_status mtf_farfield(mtf_system sys, const void* x, int32_t nrhs, const doubl
 void mtf_system_destroy(mtf_system sys) {
   if (!sys) return;
   destroy_gmres(sys->gw);
+  destroy_gmres32(sys->gw32);
   delete sys;
 }
 

@@ -156,6 +156,7 @@ struct mtf_mesh_s {
 
 namespace mtf {
 struct GmresWork;
+struct Gmres32Work;
 }
 
 struct mtf_system_s {
@@ -175,6 +176,7 @@ struct mtf_system_s {
   mtf::DevBuf<float> d_qx, d_qw, d_pv, d_cc;
   int32_t ss_npts[3] = {0, 0, 0};
   mtf::GmresWork* gw = nullptr;
+  mtf::Gmres32Work* gw32 = nullptr;
 };
 
 namespace mtf {
@@ -211,10 +213,12 @@ void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z
 // FP32 complex in / out matvec of the FP32-stored operator (column strides in complex units)
 void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
                        cudaStream_t s);
-// inner solve of the mixed path: FP32 Krylov basis, FP64 reductions; solves
-// M d = r (d starts at 0) to the relative tolerance tol
-mtf_status gmres_core32(mtf_system sys, int nrhs, const double* r_dev, double* d_dev, double tol, int max_iter,
-                        std::vector<int>& iters, int& restarts, std::vector<double>& rel, cudaStream_t s);
+// One FGMRES cycle of the mixed path on M d = r from d = 0 (FP32 Krylov
+// basis, FP64 reductions), then x += d.  Stops when every right-hand side's
+// estimate reaches tol relative to ||r|| (reached = true), after the restart
+// length or after max_iter iterations; iters[c] += iterations of rhs c.
+mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
+                          std::vector<int>& iters, bool& reached, cudaStream_t s);
 // matvec flavours: storage / accumulation precision
 enum MatvecKind { MV_AUTO = 0, MV_FP64 = 1, MV_FP32 = 2, MV_FP32_ACC64 = 3 };
 void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, double* y, int64_t ldy,
@@ -231,4 +235,5 @@ void launch_get_block(mtf_system sys, int i, double* t_out, double* k_out, cudaS
 mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
                  cudaStream_t s);
 void destroy_gmres(GmresWork* w);
+void destroy_gmres32(Gmres32Work* w);
 }  // namespace mtf

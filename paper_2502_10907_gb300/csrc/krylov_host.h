@@ -24,9 +24,10 @@ struct HostArnoldi {
     bnorm.assign(nrhs, 1.0);
     jc.assign(nrhs, 0);
   }
-  // start of a restart cycle for rhs c with ||r||
+  // start of a cycle for rhs c with ||r||; estimates are relative to ||r||
   void start(int c, double rnorm) {
     jc[c] = 0;
+    bnorm[c] = rnorm > 0 ? rnorm : 1.0;
     for (int q = 0; q <= m; ++q) g[size_t(c) * (m + 1) + q] = 0.0;
     g[size_t(c) * (m + 1)] = rnorm;
   }

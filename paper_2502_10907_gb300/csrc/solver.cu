@@ -546,10 +546,11 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
     status = gmres_core(sys, nrhs, b_dev, x_dev, MV_FP64, sys->opt.tol, max_iter, iters, restarts, rel, s);
   } else {
     // FP64 iterative refinement: r = b - M x with FP64 accumulation over the
-    // FP32-stored operator; inner FGMRES on M d = r with the FP32 matvec.
+    // FP32-stored operator; each correction is one FGMRES cycle in FP32
+    // (fgmres_cycle32) that adds its update to x.  A cycle that ends on the
+    // restart length is a restart (the next one starts from the new FP64
+    // residual); one that reaches its tolerance ends a refinement step.
     if (G.b.n != size_t(n) * nrhs * 2) G.b.alloc(size_t(n) * nrhs * 2);  // residual
-    DevBuf<double> dx;
-    dx.alloc(size_t(n) * nrhs * 2);
     const size_t vec_bytes = size_t(n) * nrhs * 2 * sizeof(double);
     double* hN = G.h.p + 4 * size_t(m + 1) * nrhs;
     double* hostN = G.h_host + 4 * size_t(m + 1) * nrhs;
@@ -579,7 +580,7 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       }
       if (status != MTF_OK) break;
       if (rmax <= sys->opt.tol) break;
-      if (it >= max_ref || total >= max_iter) {
+      if (refinements >= max_ref || total >= max_iter) {
         status = MTF_ERR_NOCONV;
         break;
       }
@@ -589,21 +590,17 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
           MTF_CUDA(cudaMemsetAsync(G.b.p + 2 * size_t(c) * n, 0, size_t(n) * 2 * sizeof(double), s));
       const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
-      std::vector<double> rel_in(nrhs, 1.0);
-      const mtf_status si = gmres_core(sys, nrhs, G.b.p, dx.p, MV_FP32, inner_tol, max_iter - total, it_in,
-                                       restarts, rel_in, s);
-      if (si == MTF_ERR_NAN) {
-        status = si;
-        break;
-      }
+      bool reached = false;
+      status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s);
+      if (status != MTF_OK) break;
       int mx = 0;
       for (int c = 0; c < nrhs; ++c) {
         iters[c] += it_in[c];
         mx = std::max(mx, it_in[c]);
       }
       total += mx;
-      ++refinements;
-      MTF_LAUNCH(KID_MISC, s, k_add<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(x_dev, dx.p, n * nrhs * 2));
+      ++restarts;
+      if (reached) ++refinements;
     }
     MTF_CUDA(cudaStreamSynchronize(s));
   }

@@ -220,3 +220,28 @@ def test_osrc_preconditioned_solves(api, oracle_cache, name):
     xm, stm = mixed.solve(cfg["dirs"], cfg["pols"])
     errs = np.linalg.norm(xm.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
     assert stm.converged == 1 and errs.max() < MIXED_TOL, errs
+
+
+# ---------------------------------------------------------------------------
+# mixed precision with restarted inner cycles: the FP32-basis FGMRES cycles
+# end on the restart length or the inner tolerance, and every cycle starts
+# from an FP64 residual; 6 right-hand sides exercise the 4 + 2 column chunks
+# of the FP32 matvec and OSRC passes.  Restart lengths are ones with which
+# restarted GMRES on this system converges in the oracle's own GMRES (the
+# unpreconditioned system needs ~1450 iterations of full GMRES, and restarts
+# of 200 still stagnate in FP64 there, so that case runs one long cycle per
+# refinement step).  Same 1e-5 bound against the oracle LU.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precond,restart", [(0, 2000), (1, 50)])
+def test_mixed_restarted_six_rhs(api, oracle_cache, precond, restart):
+    cfg, sk, ref = _case(oracle_cache, "split")
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    dirs, pols = mi.plane_wave_batch(3)
+    xr = ref.solve_lu(ref.rhs(dirs, pols))
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, tol=1e-8, restart=restart,
+                      max_iter=8000, max_refine=8, precond=precond)
+    x, st = sysg.solve(dirs, pols)
+    assert st.converged == 1
+    assert st.restarts >= 2, st.restarts
+    errs = np.linalg.norm(x.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
+    assert errs.max() < MIXED_TOL, errs
