@@ -176,6 +176,20 @@ mtf_status mtf_matvec(mtf_system sys, const void* x, void* y, int32_t nrhs, void
  * at assembly (MTF_ERR_ARG otherwise). */
 mtf_status mtf_precond_apply(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream);
 
+/* y = M x (Eq. 16) with complex64 vectors: the FP32 streaming matvec run by
+ * the mixed-precision inner solver (FP32 products and sums over the FP32-
+ * stored blocks, the exchange rows X x in FP64, the result rounded to FP32).
+ * Requires opt.precision == MTF_PREC_MIXED at assembly (MTF_ERR_ARG
+ * otherwise).  x, y: device complex64 n_total x nrhs, must not overlap.
+ * Synchronises `stream`; MTF_ERR_TIMEOUT if a bulk copy of the kernel did
+ * not complete within its time limit (the output is then undefined). */
+mtf_status mtf_matvec_f32(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream);
+
+/* z = A~ r (Eq. 19) with complex64 vectors: the FP32 apply the mixed inner
+ * solver runs.  Same operator and requirements as mtf_precond_apply; r, z:
+ * device complex64 n_total x nrhs, must not overlap. */
+mtf_status mtf_precond_apply_f32(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream);
+
 /* Right-hand side of Problem 2 for plane waves E_inc = p exp(i k0 d.x)
  * (Eq. 22): block 0 holds -2 <gamma_{.,0} E_inc, psi_m>_x for the D and N
  * slots (sign from the Calderon identities of Eq. 10 with n_0), all other

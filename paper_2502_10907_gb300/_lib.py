@@ -55,6 +55,8 @@ _SIGS = {
     "mtf_get_block": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "mtf_matvec": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_precond_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "mtf_matvec_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "mtf_precond_apply_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_rhs": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
@@ -184,6 +186,14 @@ def mtf_matvec(sys_, x, y, nrhs, stream=0):
 
 def mtf_precond_apply(sys_, r, z, nrhs, stream=0):
     _check(load().mtf_precond_apply(sys_, _ptr(r), _ptr(z), int(nrhs), stream or None))
+
+
+def mtf_matvec_f32(sys_, x, y, nrhs, stream=0):
+    _check(load().mtf_matvec_f32(sys_, _ptr(x), _ptr(y), int(nrhs), stream or None))
+
+
+def mtf_precond_apply_f32(sys_, r, z, nrhs, stream=0):
+    _check(load().mtf_precond_apply_f32(sys_, _ptr(r), _ptr(z), int(nrhs), stream or None))
 
 
 def mtf_rhs(sys_, dirs, pols, b_out, stream=0):

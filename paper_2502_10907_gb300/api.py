@@ -69,6 +69,20 @@ class System:
         L.mtf_precond_apply(self.handle, r, z, r.shape[0], _stream())
         return z
 
+    def matvec_f32(self, x):
+        """FP32 streaming matvec (mixed-precision systems); x: (nrhs, n_total) complex64."""
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        L.mtf_matvec_f32(self.handle, x, y, x.shape[0], _stream())
+        return y
+
+    def precond_f32(self, r):
+        """FP32 block-OSRC apply; r: (nrhs, n_total) complex64."""
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        L.mtf_precond_apply_f32(self.handle, r, z, r.shape[0], _stream())
+        return z
+
     def rhs(self, dirs, pols):
         b = torch.empty((len(dirs), self.mesh.n_total), dtype=torch.complex128, device="cuda")
         L.mtf_rhs(self.handle, dirs, pols, b, _stream())

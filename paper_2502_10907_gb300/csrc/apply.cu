@@ -156,123 +156,6 @@ __global__ void __launch_bounds__(256) k_matvec(
   }
 }
 
-// ---------------------------------------------------------------------------
-// FP32 streaming matvec: CTA = 8 rows of one block (one warp per row); the
-// block's input vector is staged in shared memory in chunks of kChunk
-// entries (FP32 complex, D and N slots, NC right-hand sides) so that the
-// warps only stream the matrix from HBM, 8 float4 loads per lane in flight.
-// ---------------------------------------------------------------------------
-constexpr int kRowsPerCta = 8;
-constexpr int kChunk = 1024;
-
-// XT: precision of x (read by the exchange epilogue); the dense part always
-// reads the FP32 vector x32 (column stride ld32); YT: output precision.
-template <int NC, class XT, class YT>
-__global__ void __launch_bounds__(256) k_matvec32s(
-    const float4* __restrict__ TK, const XEntry* __restrict__ xe, const double* __restrict__ xval,
-    const int32_t* __restrict__ tile_blk, const int32_t* __restrict__ tile_row0, const int32_t* __restrict__ blk_N,
-    const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_mat_off,
-    const int64_t* __restrict__ blk_row_off, const double* __restrict__ rho, const XT* __restrict__ x,
-    int64_t ldx, const float* __restrict__ x32, int64_t ld32, YT* __restrict__ y, int64_t ldy, int c0) {
-  extern __shared__ float2 xs[];  // [NC][2][kChunk]
-  const int i = tile_blk[blockIdx.x];
-  const int r0 = tile_row0[blockIdx.x];
-  const int N = blk_N[i];
-  const int64_t off = blk_dof_off[i];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = r0 + warp;
-  const bool active = m < N;
-  const float4* row = TK + blk_mat_off[i] + int64_t(active ? m : 0) * N;
-  float acc[NC][8];
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[c][q] = 0.f;
-  for (int cb = 0; cb < N; cb += kChunk) {
-    const int clen = min(kChunk, N - cb);
-    __syncthreads();
-    for (int t = threadIdx.x; t < NC * 2 * clen; t += blockDim.x) {
-      const int c = t / (2 * clen), rem = t % (2 * clen), slot = rem / clen, e = rem % clen;
-      xs[(c * 2 + slot) * kChunk + e] =
-          *reinterpret_cast<const float2*>(x32 + 2 * ((c0 + c) * ld32 + off + slot * N + cb + e));
-    }
-    __syncthreads();
-    if (active) {
-      for (int n0 = lane; n0 < clen; n0 += 32 * 8) {
-        float4 ev[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int n = n0 + 32 * u;
-          ev[u] = n < clen ? __ldg(row + cb + n) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int n = n0 + 32 * u;
-          if (n < clen) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const float2 xd = xs[(c * 2) * kChunk + n], xn = xs[(c * 2 + 1) * kChunk + n];
-              acc[c][0] = fmaf(ev[u].x, xd.x, fmaf(-ev[u].y, xd.y, acc[c][0]));
-              acc[c][1] = fmaf(ev[u].x, xd.y, fmaf(ev[u].y, xd.x, acc[c][1]));
-              acc[c][2] = fmaf(ev[u].x, xn.x, fmaf(-ev[u].y, xn.y, acc[c][2]));
-              acc[c][3] = fmaf(ev[u].x, xn.y, fmaf(ev[u].y, xn.x, acc[c][3]));
-              acc[c][4] = fmaf(ev[u].z, xd.x, fmaf(-ev[u].w, xd.y, acc[c][4]));
-              acc[c][5] = fmaf(ev[u].z, xd.y, fmaf(ev[u].w, xd.x, acc[c][5]));
-              acc[c][6] = fmaf(ev[u].z, xn.x, fmaf(-ev[u].w, xn.y, acc[c][6]));
-              acc[c][7] = fmaf(ev[u].z, xn.y, fmaf(ev[u].w, xn.x, acc[c][7]));
-            }
-          }
-        }
-      }
-    }
-  }
-  if (!active) return;
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float v = acc[c][q];
-#pragma unroll
-      for (int s2 = 16; s2 > 0; s2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s2);
-      acc[c][q] = v;
-    }
-  if (lane < NC) {
-    double a[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      a[q] = double(acc[0][q]);
-#pragma unroll
-      for (int c = 1; c < NC; ++c)
-        if (lane == c) a[q] = double(acc[c][q]);
-    }
-    const double rr = rho[2 * i], ri = rho[2 * i + 1];
-    const double rn = rr * rr + ri * ri;
-    const double ir = rr / rn, ii = -ri / rn;
-    const int col = c0 + lane;
-    const XT* xc = x + 2 * int64_t(col) * ldx;
-    double yDr = 2.0 * (a[4] + (a[2] * ir - a[3] * ii));
-    double yDi = 2.0 * (a[5] + (a[2] * ii + a[3] * ir));
-    double yNr = 2.0 * (a[6] - (a[0] * rr - a[1] * ri));
-    double yNi = 2.0 * (a[7] - (a[0] * ri + a[1] * rr));
-    const int64_t r = blk_row_off[i] + m;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const XEntry X = xe[6 * r + e];
-      const double v = xval[6 * r + e];
-      const int Nj = X.ab >> 4;
-      yDr += v * double(xc[2 * int64_t(X.col)]);
-      yDi += v * double(xc[2 * int64_t(X.col) + 1]);
-      yNr += v * double(xc[2 * (int64_t(X.col) + Nj)]);
-      yNi += v * double(xc[2 * (int64_t(X.col) + Nj) + 1]);
-    }
-    YT* yc = y + 2 * (int64_t(col) * ldy + off);
-    yc[2 * m] = YT(yDr);
-    yc[2 * m + 1] = YT(yDi);
-    yc[2 * (N + m)] = YT(yNr);
-    yc[2 * (N + m) + 1] = YT(yNi);
-  }
-}
-
 __global__ void k_to_f32(const double* __restrict__ x, int64_t ldx, int64_t n2, int nrhs, float* __restrict__ out) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n2 * nrhs) return;
@@ -293,55 +176,11 @@ void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, 
     const int64_t n2 = 2 * m->n_total;
     if (sys->d_x32.n < size_t(n2) * nrhs) sys->d_x32.alloc(size_t(n2) * nrhs);
     MTF_LAUNCH(KID_MISC, s, k_to_f32<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(x, ldx, n2, nrhs, sys->d_x32.p));
-    const unsigned tiles = unsigned(m->n_tiles8);
-    for (int c0 = 0; c0 < nrhs; c0 += 4) {
-      const int nc = std::min(4, nrhs - c0);
-      const size_t smem = size_t(nc) * 2 * kChunk * sizeof(float2);
-#define MV32S(NC)                                                                                             \
-  do {                                                                                                        \
-    auto kfn = k_matvec32s<NC, double, double>;                                                               \
-    MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));              \
-    MTF_LAUNCH(KID_MATVEC32, s, kfn<<<tiles, 256, smem, s>>>(                                                 \
-        reinterpret_cast<const float4*>(sys->d_TK32.p), m->d_xent.p, sys->d_xval.p, m->d_tile_blk.p,          \
-        m->d_tile_row0.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->d_blk_row_off.p,           \
-        sys->d_rho.p, x, ldx, sys->d_x32.p, m->n_total, y, ldy, c0));                                         \
-  } while (0)
-      if (nc == 1) MV32S(1);
-      else if (nc == 2) MV32S(2);
-      else if (nc == 3) MV32S(3);
-      else MV32S(4);
-#undef MV32S
-    }
+    launch_matvec_stream64(sys, x, ldx, sys->d_x32.p, m->n_total, y, ldy, nrhs, s);
   } else {
     MTF_LAUNCH(KID_MATVEC64, s, k_matvec<float, double, double><<<blocks, 256, 0, s>>>(
         sys->d_TK32.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
         m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, x, ldx, y, ldy, nrhs, m->n_rows));
-  }
-}
-
-// FP32 in, FP32 out (the FP32-basis inner solver): x, y complex64 with
-// column strides ldx, ldy (complex units)
-void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
-                       cudaStream_t s) {
-  mtf_mesh m = sys->mesh;
-  const unsigned tiles = unsigned(m->n_tiles8);
-  for (int c0 = 0; c0 < nrhs; c0 += 4) {
-    const int nc = std::min(4, nrhs - c0);
-    const size_t smem = size_t(nc) * 2 * kChunk * sizeof(float2);
-#define MV32F(NC)                                                                                             \
-  do {                                                                                                        \
-    auto kfn = k_matvec32s<NC, float, float>;                                                                 \
-    MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));              \
-    MTF_LAUNCH(KID_MATVEC32, s, kfn<<<tiles, 256, smem, s>>>(                                                 \
-        reinterpret_cast<const float4*>(sys->d_TK32.p), m->d_xent.p, sys->d_xval.p, m->d_tile_blk.p,          \
-        m->d_tile_row0.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, m->d_blk_row_off.p,           \
-        sys->d_rho.p, x, ldx, x, ldx, y, ldy, c0));                                                           \
-  } while (0)
-    if (nc == 1) MV32F(1);
-    else if (nc == 2) MV32F(2);
-    else if (nc == 3) MV32F(3);
-    else MV32F(4);
-#undef MV32F
   }
 }
 

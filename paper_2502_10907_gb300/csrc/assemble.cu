@@ -583,13 +583,20 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
   launch_exchange_values(sys, s);
 }
 
+__global__ void k_d2f(const double* __restrict__ a, int64_t n, float* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = float(a[t]);
+}
+
 void launch_exchange_values(mtf_system sys, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   const int64_t nent = m->n_rows * 6;
   sys->d_xval.alloc(size_t(nent));
   MTF_LAUNCH(KID_XVALUES, s, k_exchange_values<<<unsigned((nent + 255) / 256), 256, 0, s>>>(
       m->d_xent.p, nent, m->d_bt_v.p, m->d_bt_c.p, m->d_bt_area.p, m->d_bt_swap.p, sys->d_xval.p));
-  MTF_CUDA(cudaGetLastError());
+  // FP32 copy for the FP32 epilogues of the mixed inner solver
+  sys->d_xval32.alloc(size_t(nent));
+  MTF_LAUNCH(KID_XVALUES, s, k_d2f<<<unsigned((nent + 255) / 256), 256, 0, s>>>(sys->d_xval.p, nent, sys->d_xval32.p));
 }
 
 void launch_rhs(mtf_system sys, int nrhs, const double* d_dirs, const double* d_pols, double* b,

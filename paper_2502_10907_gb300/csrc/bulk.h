@@ -1,0 +1,99 @@
+// Inline-PTX helpers for the bulk-copy (TMA engine) pipelines: mbarrier
+// setup, transaction-count arrival, bounded parity waits and the untiled
+// global -> shared bulk copy.  Addresses of bulk copies must be 16-byte
+// aligned and sizes multiples of 16 bytes; callers guarantee both.
+#pragma once
+
+#include <cstdint>
+
+namespace mtf {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make the initialised barriers visible to the async proxy
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// one arrival that also expects `bytes` of transactions on this phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity to complete; gives up after
+// limit_ns nanoseconds of wall time and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// bulk copy of `bytes` from global to this CTA's shared memory, completing
+// as transactions on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) accesses to the same memory
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Sum K per-lane values over the warp with recursive halving: at each level
+// a lane keeps one half of its values and trades the other with its partner,
+// so K values cost K - 1 + (5 - log2 K) shuffles.  On return v[0] of every
+// lane holds the warp total of value index (lane >> (5 - log2 K)).
+template <int W>
+struct WarpTransposeSum {
+  __device__ __forceinline__ static void run(float* v, int lane, int o) {
+    constexpr int H = W / 2;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const float send = up ? v[q] : v[q + H];
+      const float keep = up ? v[q + H] : v[q];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    WarpTransposeSum<H>::run(v, lane, o >> 1);
+  }
+};
+template <>
+struct WarpTransposeSum<1> {
+  __device__ __forceinline__ static void run(float* v, int, int o) {
+#pragma unroll
+    for (; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  }
+};
+
+}  // namespace mtf

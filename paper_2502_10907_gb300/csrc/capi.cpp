@@ -65,6 +65,18 @@ void assemble_into(mtf_system sys, double k0, const double* eps_r, const double*
   }
   upload_small(sys->d_k, kk.data(), kk.size(), s);
   upload_small(sys->d_rho, rr.data(), rr.size(), s);
+  // FP32 (rho, 1 / rho) per block for the FP32 epilogues
+  std::vector<float> r32(4 * mesh->nd);
+  for (int i = 0; i < mesh->nd; ++i) {
+    const std::complex<double> r(rr[2 * i], rr[2 * i + 1]), ri = 1.0 / r;
+    r32[4 * i] = float(r.real());
+    r32[4 * i + 1] = float(r.imag());
+    r32[4 * i + 2] = float(ri.real());
+    r32[4 * i + 3] = float(ri.imag());
+  }
+  sys->d_rho32.alloc(r32.size());
+  MTF_CUDA(cudaMemcpyAsync(sys->d_rho32.p, r32.data(), r32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  MTF_CUDA(cudaStreamSynchronize(s));
   launch_assemble(sys, s);
   if (sys->opt.precond == MTF_PRECOND_OSRC) osrc_setup(sys, s);
 }
@@ -200,6 +212,33 @@ mtf_status mtf_precond_apply(mtf_system sys, const void* r, void* z, int32_t nrh
     const int64_t n = sys->mesh->n_total;
     launch_osrc_apply(sys, static_cast<const double*>(r), n, static_cast<double*>(z), n, nrhs,
                       static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_matvec_f32(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && x && y, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1, MTF_ERR_ARG, "nrhs must be >= 1");
+    MTF_REQUIRE(x != y, MTF_ERR_ARG, "x and y must not overlap");
+    MTF_REQUIRE(sys->opt.precision == MTF_PREC_MIXED, MTF_ERR_ARG,
+                "the FP32 matvec needs a system assembled in mixed precision");
+    const int64_t n = sys->mesh->n_total;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_matvec_f32(sys, static_cast<const float*>(x), n, static_cast<float*>(y), n, nrhs, s);
+    check_matvec_stream(sys, s);
+  });
+}
+
+mtf_status mtf_precond_apply_f32(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && r && z, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1, MTF_ERR_ARG, "nrhs must be >= 1");
+    MTF_REQUIRE(r != z, MTF_ERR_ARG, "r and z must not overlap");
+    MTF_REQUIRE(sys->opt.precond == MTF_PRECOND_OSRC, MTF_ERR_ARG,
+                "the system was assembled without the OSRC preconditioner");
+    const int64_t n = sys->mesh->n_total;
+    launch_osrc_apply_f32(sys, static_cast<const float*>(r), n, static_cast<float*>(z), n, nrhs,
+                          static_cast<cudaStream_t>(stream));
   });
 }
 

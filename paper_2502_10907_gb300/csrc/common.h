@@ -135,6 +135,13 @@ struct mtf_mesh_s {
   mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
   int64_t n_tiles8 = 0, n_tiles32 = 0;       // 8- and 32-row tiles over all blocks (streaming kernels)
   mtf::DevBuf<int32_t> d_tile_blk, d_tile_row0, d_tile32_blk, d_tile32_row0;
+  // streaming-matvec work units: (N, global row, first input column, len | piece << 12)
+  // and the float4 offset of each piece in the stored blocks
+  bool mv_units_ready = false;
+  int64_t mv_n_units = 0;
+  int32_t mv_pmax = 1;
+  mtf::DevBuf<int4> d_mv_units;
+  mtf::DevBuf<int64_t> d_mv_src;
   // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
   bool osrc_ready = false;
   mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;   // W^T, W (per block), |xi|^2 per mode
@@ -168,6 +175,8 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_TK64;                // FP64: 4 doubles per dense entry
   mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
   mtf::DevBuf<double> d_xval;                // exchange values (6 per row)
+  mtf::DevBuf<float> d_xval32;               // FP32 copy of the exchange values
+  mtf::DevBuf<float> d_rho32;                // per block: rho (re, im), 1 / rho (re, im)
   mtf::DevBuf<double> d_ss_pts[3];           // Sauter-Schwab tables
   // FP32 geometry of the mixed regular-pair kernel (per block-triangle)
   mtf::DevBuf<float> d_x32;                  // FP32 copy of the matvec input (mixed path)
@@ -175,6 +184,10 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_cen;
   mtf::DevBuf<float> d_qx, d_qw, d_pv, d_cc;
   int32_t ss_npts[3] = {0, 0, 0};
+  // streaming matvec: per-row piece sums and the error word (d_mv_ctl[2])
+  mtf::DevBuf<float> d_mv_part;
+  mtf::DevBuf<unsigned> d_mv_ctl;
+  int32_t mv_grid = 0;
   mtf::GmresWork* gw = nullptr;
   mtf::Gmres32Work* gw32 = nullptr;
 };
@@ -184,7 +197,7 @@ namespace mtf {
 enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
-  KID_MISC, KID_COUNT
+  KID_MISC, KID_MVCOMBINE, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
@@ -210,9 +223,14 @@ void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, 
                        cudaStream_t s);
 void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
                            cudaStream_t s);
-// FP32 complex in / out matvec of the FP32-stored operator (column strides in complex units)
+// Streaming matvec of the FP32-stored operator (matvec32.cu).  The dense
+// part reads the FP32 vector x32 (column stride ld32, complex units); the
+// exchange rows read x.  f32: FP32 in and out.
 void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
                        cudaStream_t s);
+void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const float* x32, int64_t ld32, double* y,
+                            int64_t ldy, int nrhs, cudaStream_t s);
+void check_matvec_stream(mtf_system sys, cudaStream_t s);
 // One FGMRES cycle of the mixed path on M d = r from d = 0 (FP32 Krylov
 // basis, FP64 reductions), then x += d.  Stops when every right-hand side's
 // estimate reaches tol relative to ||r|| (reached = true), after the restart

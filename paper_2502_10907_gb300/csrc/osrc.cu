@@ -195,7 +195,7 @@ constexpr int kOsRowsPerCta = 8 * kOsRowsPerWarp;
 template <int PASS, int NC, class ZT>
 __global__ void __launch_bounds__(256) k_osrc_stream(
     const float* __restrict__ Wm, const int64_t* __restrict__ osrc_off, const float* __restrict__ vin,
-    int64_t ldin, const float2* __restrict__ f, const double* __restrict__ rho,
+    int64_t ldin, const float2* __restrict__ f, const double* __restrict__ rho, const float* __restrict__ rho32,
     const int32_t* __restrict__ tile_blk, const int32_t* __restrict__ tile_row0,
     const int32_t* __restrict__ blk_N, const int64_t* __restrict__ blk_dof_off,
     const int64_t* __restrict__ blk_row_off, int64_t n_total, int c0, float2* __restrict__ tout,
@@ -288,9 +288,20 @@ __global__ void __launch_bounds__(256) k_osrc_stream(
       tc[row] = make_float2(fr.x * a0 - fr.y * a1, fr.x * a1 + fr.y * a0);
       tc[N + row] = make_float2(fr.x * a2 - fr.y * a3, fr.x * a3 + fr.y * a2);
     } else {
-      const double rr = rho[2 * i], ri = rho[2 * i + 1];
-      const double rn = rr * rr + ri * ri;
-      const double ir = rr / rn, ii = -ri / rn;
+      // rho, 1/rho in the output precision (FP32 from the per-block table)
+      ZT rr, ri, ir, ii;
+      if constexpr (sizeof(ZT) == 4) {
+        rr = rho32[4 * i];
+        ri = rho32[4 * i + 1];
+        ir = rho32[4 * i + 2];
+        ii = rho32[4 * i + 3];
+      } else {
+        rr = rho[2 * i];
+        ri = rho[2 * i + 1];
+        const ZT rn = rr * rr + ri * ri;
+        ir = rr / rn;
+        ii = -ri / rn;
+      }
       ZT* zc = zout + 2 * (int64_t(col) * ldz + base);
       zc[2 * row] = ZT(ir * a2 - ii * a3);
       zc[2 * row + 1] = ZT(ir * a3 + ii * a2);
@@ -469,7 +480,7 @@ static void osrc_passes(mtf_system sys, const float* r32, int64_t ldr, ZT* z, in
   do {                                                                                                         \
     auto kfn = k_osrc_stream<P, NC, ZT>;                                                                       \
     MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));               \
-    MTF_LAUNCH(KID_OSRC, s, kfn<<<tiles, 256, smem, s>>>(W, m->d_osrc_off.p, VIN, LDIN, f, sys->d_rho.p,       \
+    MTF_LAUNCH(KID_OSRC, s, kfn<<<tiles, 256, smem, s>>>(W, m->d_osrc_off.p, VIN, LDIN, f, sys->d_rho.p, sys->d_rho32.p, \
                                                          m->d_tile32_blk.p, m->d_tile32_row0.p, m->d_blk_N.p,  \
                                                          m->d_blk_dof_off.p, m->d_blk_row_off.p, m->n_total,   \
                                                          c0, t, z, ldz));                                       \

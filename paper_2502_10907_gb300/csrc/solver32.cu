@@ -26,7 +26,10 @@ struct Gmres32Work {
   int64_t n = 0, ldn = 0;
   bool pre = false;
   DevBuf<float> V, Z, w;
-  DevBuf<double> h, y;  // h: [hA (m+1) x nrhs][hB (m+1) x nrhs][nrm nrhs][ss nrhs] complex
+  // h: kBatch slots, one per Arnoldi column j of a batch; slot layout (complex
+  // entries, index i * nrhs + c): hA (j+1) x nrhs, hB (j+1) x nrhs, ||w|| nrhs,
+  // then nrhs real sums of squares
+  DevBuf<double> h, y;
   double* h_host = nullptr;
   ~Gmres32Work() {
     if (h_host) cudaFreeHost(h_host);
@@ -37,12 +40,12 @@ void destroy_gmres32(Gmres32Work* w) { delete w; }
 
 static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
-// h[c*ldh + i] += sum_{k in segment} conj(V_i^c[k]) w^c[k].  CTA = one segment
+// h[i*hst + c] += sum_{k in segment} conj(V_i^c[k]) w^c[k].  CTA = one segment
 // of w (seg complex entries, staged in shared memory as float4 pairs) x 32
 // basis vectors (4 per warp, 4 float4 loads in flight per step); grid
 // (segments, ceil(rows/32), c).  V_i^c starts at V + 2 (c ldv + i ldn).
 __global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
-                                                int64_t ldv, int rows, double* __restrict__ h, int ldh, int seg) {
+                                                int64_t ldv, int rows, double* __restrict__ h, int hst, int seg) {
   extern __shared__ float4 ws4[];
   constexpr int RW = 4;
   const int c = blockIdx.z;
@@ -71,35 +74,39 @@ __global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, con
       ai[r] += a.x * x.y - a.y * x.x + a.z * x.w - a.w * x.z;
     }
   }
+  // FP32 warp sums (32 lane partials), FP64 accumulation over segments
 #pragma unroll
   for (int r = 0; r < RW; ++r) {
-    double sr = ar[r], si = ai[r];
+    float sr = ar[r], si = ai[r];
 #pragma unroll
     for (int s2 = 16; s2 > 0; s2 >>= 1) {
       sr += __shfl_xor_sync(0xffffffffu, sr, s2);
       si += __shfl_xor_sync(0xffffffffu, si, s2);
     }
     if (lane == 0 && i0 + r < rows) {
-      atomicAdd(h + 2 * (int64_t(c) * ldh + i0 + r), sr);
-      atomicAdd(h + 2 * (int64_t(c) * ldh + i0 + r) + 1, si);
+      atomicAdd(h + 2 * (int64_t(i0 + r) * hst + c), double(sr));
+      atomicAdd(h + 2 * (int64_t(i0 + r) * hst + c) + 1, double(si));
     }
   }
 }
 
-// w^c -= sum_{i<j} V_i^c h_i^c (h FP64, used as FP32); optionally
+// w^c -= sum_{i<j} V_i^c h_i^c (h_i^c at h[i*hst + c], FP64, used as FP32); optionally
 // ss[c] += ||w^c||^2 after the update.  CTA = 64 consecutive entries (a float4
 // pair per lane) x 8 groups of basis vectors (i = grp mod 8), the group sums
 // combined in shared memory; grid (ldn / 64, c).
 __global__ void __launch_bounds__(256) k_axpy32(const float* __restrict__ V, const double* __restrict__ h, int j,
-                                                int64_t ldn, int64_t ldv, int ldh, float* __restrict__ w,
+                                                int64_t ldn, int64_t ldv, int hst, float* __restrict__ w,
                                                 double* __restrict__ ss) {
   const int c = blockIdx.y;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t q = int64_t(blockIdx.x) * 32 + lane;  // float4 index within a vector
   __shared__ float4 part[8][32];
   extern __shared__ float2 hs[];
-  const double2* hc = reinterpret_cast<const double2*>(h) + int64_t(c) * ldh;
-  for (int t = threadIdx.x; t < j; t += blockDim.x) hs[t] = make_float2(float(hc[t].x), float(hc[t].y));
+  const double2* hc = reinterpret_cast<const double2*>(h) + c;
+  for (int t = threadIdx.x; t < j; t += blockDim.x) {
+    const double2 hv = hc[int64_t(t) * hst];
+    hs[t] = make_float2(float(hv.x), float(hv.y));
+  }
   __syncthreads();
   const int64_t ldq = ldn >> 1;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(256) k_axpy32(const float* __restrict__ V, con
   part[grp][lane] = acc;
   __syncthreads();
   if (grp != 0) return;
-  double sq = 0;
+  float sq = 0.f;
   if (q < ldq) {
     float4 t = part[0][lane];
 #pragma unroll
@@ -136,11 +143,11 @@ __global__ void __launch_bounds__(256) k_axpy32(const float* __restrict__ V, con
     o.z -= t.z;
     o.w -= t.w;
     *x = o;
-    sq = double(o.x) * o.x + double(o.y) * o.y + double(o.z) * o.z + double(o.w) * o.w;
+    sq = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
   }
   if (ss) {
     for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
-    if (lane == 0) atomicAdd(ss + c, sq);
+    if (lane == 0) atomicAdd(ss + c, double(sq));
   }
 }
 
@@ -150,13 +157,18 @@ __global__ void __launch_bounds__(256) k_scale32(const float* __restrict__ w, in
                                                  double* __restrict__ nrm, float* __restrict__ out, int64_t ldo) {
   const int c = blockIdx.y;
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const double t = sqrt(ss[c]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    nrm[2 * c] = t;
-    nrm[2 * c + 1] = 0.0;
+  __shared__ float sinv;  // one FP64 square root per CTA, not per thread
+  if (threadIdx.x == 0) {
+    const double t = sqrt(ss[c]);
+    sinv = t > 0 ? float(1.0 / t) : 0.f;
+    if (blockIdx.x == 0) {
+      nrm[2 * c] = t;
+      nrm[2 * c + 1] = 0.0;
+    }
   }
+  __syncthreads();
   if (q >= (ldn >> 1)) return;
-  const float inv = t > 0 ? float(1.0 / t) : 0.f;
+  const float inv = sinv;
   float4 a = reinterpret_cast<const float4*>(w + 2 * int64_t(c) * ldn)[q];
   a.x *= inv;
   a.y *= inv;
@@ -253,8 +265,8 @@ __global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, 
   }
 }
 
-static void launch_dots32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, double* h, int ldh,
-                          int nrhs, cudaStream_t s) {
+static void launch_dots32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, double* h, int nrhs,
+                          cudaStream_t s) {
   const int64_t rg = (rows + 31) / 32;
   // segments of <= 4096 entries (32 KB staged), enough of them for ~2 waves
   const int64_t minseg = (ldn + 4095) / 4096;
@@ -263,8 +275,18 @@ static void launch_dots32(const float* V, const float* w, int64_t ldn, int64_t l
   seg = (seg + 63) & ~int64_t(63);
   const int64_t nsg = (ldn + seg - 1) / seg;
   dim3 g{unsigned(nsg), unsigned(rg), unsigned(nrhs)};
-  MTF_LAUNCH(KID_DOTS, s, k_dots32<<<g, 256, size_t(seg) * sizeof(float2), s>>>(V, w, ldn, ldv, rows, h, ldh, int(seg)));
+  MTF_LAUNCH(KID_DOTS, s, k_dots32<<<g, 256, size_t(seg) * sizeof(float2), s>>>(V, w, ldn, ldv, rows, h, nrhs, int(seg)));
 }
+
+// Arnoldi columns enqueued back to back before the host reads their
+// Hessenberg entries: CGS2 needs no host result, only the stopping test does,
+// so at most kBatch - 1 iterations per cycle are computed beyond the one that
+// meets the tolerance (they are discarded) while kBatch - 1 of every kBatch
+// host round trips disappear.
+constexpr int kBatch = 8;
+
+// doubles of the Hessenberg slot of column j
+static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 4) * nrhs; }
 
 mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
                           std::vector<int>& iters, bool& reached, cudaStream_t s) {
@@ -286,7 +308,7 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     }
     G.w.alloc(size_t(ldn) * nrhs * 2);
     MTF_CUDA(cudaMemsetAsync(G.w.p, 0, G.w.n * sizeof(float), s));
-    G.h.alloc(size_t(2 * (m + 1) + 2) * nrhs * 2);
+    G.h.alloc(size_t(kBatch) * slot_len(m - 1, nrhs));
     G.y.alloc(size_t(m + 1) * nrhs * 2);
     if (G.h_host) cudaFreeHost(G.h_host);
     G.h_host = nullptr;
@@ -299,26 +321,19 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
   }
   const int ldh = m + 1;
   const int64_t ldv = int64_t(m + 1) * ldn, ldz = int64_t(m) * ldn;
-  double* hA = G.h.p;
-  double* hB = G.h.p + 2 * size_t(ldh) * nrhs;
-  double* hN = G.h.p + 4 * size_t(ldh) * nrhs;
-  double* ss = hN + 2 * nrhs;
-  const double* hostA = G.h_host;
-  const double* hostB = G.h_host + 2 * size_t(ldh) * nrhs;
-  const double* hostN = G.h_host + 4 * size_t(ldh) * nrhs;
-  const double* hostS = hostN + 2 * nrhs;
+  const size_t slot = slot_len(m - 1, nrhs);
 
-  // V_0 = r / ||r||
-  MTF_CUDA(cudaMemsetAsync(G.h.p, 0, G.h.n * sizeof(double), s));
-  MTF_LAUNCH(KID_NORM, s, k_sqnorm64<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, ss));
-  MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, ss, G.V.p, ldv));
-  MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, G.h.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // V_0 = r / ||r|| (sums of squares in slot 0)
+  MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nrhs) * sizeof(double), s));
+  MTF_LAUNCH(KID_NORM, s, k_sqnorm64<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p));
+  MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p, G.V.p, ldv));
+  MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, size_t(nrhs) * sizeof(double), cudaMemcpyDeviceToHost, s));
   MTF_CUDA(cudaStreamSynchronize(s));
   HostArnoldi ha(m, nrhs);
   std::vector<int> active(nrhs);
   bool any = false;
   for (int c = 0; c < nrhs; ++c) {
-    const double rn = std::sqrt(hostS[c]);
+    const double rn = std::sqrt(G.h_host[c]);
     if (!std::isfinite(rn)) return MTF_ERR_NAN;
     ha.start(c, rn);
     active[c] = rn > 0;
@@ -337,45 +352,67 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
   }
   const dim3 ga{nb(ldn / 2, 32), unsigned(nrhs)};
   const dim3 gs{nb(ldn / 2, 256), unsigned(nrhs)};
-  for (int j = 0; j < m && j < max_iter; ++j) {
-    const float* vj = G.V.p + 2 * size_t(j) * ldn;
-    if (pre) {
-      float* zj = G.Z.p + 2 * size_t(j) * ldn;
-      launch_osrc_apply_f32(sys, vj, ldv, zj, ldz, nrhs, s);
-      launch_matvec_f32(sys, zj, ldz, G.w.p, ldn, nrhs, s);
-    } else {
-      launch_matvec_f32(sys, vj, ldv, G.w.p, ldn, nrhs, s);
-    }
-    // CGS2 with FP64 reductions of the FP32 data
-    MTF_CUDA(cudaMemsetAsync(G.h.p, 0, G.h.n * sizeof(double), s));
-    launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hA, ldh, nrhs, s);
-    MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hA, j + 1, ldn, ldv, ldh, G.w.p, nullptr));
-    launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hB, ldh, nrhs, s);
-    MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hB, j + 1, ldn, ldv, ldh, G.w.p, ss));
-    MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, ss, hN, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
-    MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, G.h.n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MTF_CUDA(cudaStreamSynchronize(s));
-    bool all_done = true;
-    std::vector<double> hcol(2 * size_t(j + 1));
-    for (int c = 0; c < nrhs; ++c) {
-      if (!active[c]) continue;
-      for (int q = 0; q <= j; ++q) {
-        hcol[2 * q] = hostA[2 * (size_t(c) * ldh + q)] + hostB[2 * (size_t(c) * ldh + q)];
-        hcol[2 * q + 1] = hostA[2 * (size_t(c) * ldh + q) + 1] + hostB[2 * (size_t(c) * ldh + q) + 1];
+  const int jend = std::min(m, std::max(1, max_iter));
+  std::vector<double> hcol;
+  bool stop = false;
+  for (int j0 = 0; j0 < jend && !stop; j0 += kBatch) {
+    const int nbat = std::min(kBatch, jend - j0);
+    for (int b = 0; b < nbat; ++b) {
+      const int j = j0 + b;
+      const float* vj = G.V.p + 2 * size_t(j) * ldn;
+      if (pre) {
+        float* zj = G.Z.p + 2 * size_t(j) * ldn;
+        launch_osrc_apply_f32(sys, vj, ldv, zj, ldz, nrhs, s);
+        launch_matvec_f32(sys, zj, ldz, G.w.p, ldn, nrhs, s);
+      } else {
+        launch_matvec_f32(sys, vj, ldv, G.w.p, ldn, nrhs, s);
       }
-      const double hn = hostN[2 * c];
-      const double est = ha.add_column(c, j, hcol.data(), hn);
-      ++iters[c];
-      if (!std::isfinite(est)) status = MTF_ERR_NAN;
-      if (est <= tol || hn == 0.0) active[c] = 0;
-      all_done = all_done && !active[c];
+      // CGS2 with FP64 accumulation of the FP32 partial sums
+      double* hA = G.h.p + size_t(b) * slot;
+      double* hB = hA + 2 * size_t(j + 1) * nrhs;
+      double* hN = hB + 2 * size_t(j + 1) * nrhs;
+      double* ss = hN + 2 * nrhs;
+      MTF_CUDA(cudaMemsetAsync(hA, 0, slot_len(j, nrhs) * sizeof(double), s));
+      launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hA, nrhs, s);
+      MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hA, j + 1, ldn, ldv, nrhs, G.w.p, nullptr));
+      launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hB, nrhs, s);
+      MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hB, j + 1, ldn, ldv, nrhs, G.w.p, ss));
+      MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, ss, hN, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
+      MTF_CUDA(cudaMemcpyAsync(G.h_host + size_t(b) * slot, hA, slot_len(j, nrhs) * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
     }
-    if (status != MTF_OK) return status;
-    if (all_done) {
-      reached = true;
-      break;
+    MTF_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < nbat && !stop; ++b) {
+      const int j = j0 + b;
+      const double* hostA = G.h_host + size_t(b) * slot;
+      const double* hostB = hostA + 2 * size_t(j + 1) * nrhs;
+      const double* hostN = hostB + 2 * size_t(j + 1) * nrhs;
+      hcol.assign(2 * size_t(j + 1), 0.0);
+      bool all_done = true;
+      for (int c = 0; c < nrhs; ++c) {
+        if (!active[c]) continue;
+        for (int q = 0; q <= j; ++q) {
+          hcol[2 * q] = hostA[2 * (size_t(q) * nrhs + c)] + hostB[2 * (size_t(q) * nrhs + c)];
+          hcol[2 * q + 1] = hostA[2 * (size_t(q) * nrhs + c) + 1] + hostB[2 * (size_t(q) * nrhs + c) + 1];
+        }
+        const double hn = hostN[2 * c];
+        const double est = ha.add_column(c, j, hcol.data(), hn);
+        ++iters[c];
+        if (!std::isfinite(est)) status = MTF_ERR_NAN;
+        if (est <= tol || hn == 0.0) active[c] = 0;
+        all_done = all_done && !active[c];
+      }
+      if (status != MTF_OK) {
+        check_matvec_stream(sys, s);
+        return status;
+      }
+      if (all_done) {
+        reached = true;
+        stop = true;
+      }
     }
   }
+  check_matvec_stream(sys, s);
   // x += Z y (flexible) or V y, y = R^{-1} g per right-hand side
   std::vector<double> yhost(size_t(m + 1) * nrhs * 2);
   const int jmax = ha.solve(yhost);

@@ -245,3 +245,80 @@ def test_mixed_restarted_six_rhs(api, oracle_cache, precond, restart):
     assert st.restarts >= 2, st.restarts
     errs = np.linalg.norm(x.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
     assert errs.max() < MIXED_TOL, errs
+
+
+# ---------------------------------------------------------------------------
+# FP32 entry points of the mixed inner solver: the streaming matvec (rows cut
+# into pieces of <= 512 columns, handed out dynamically) and the FP32 OSRC
+# apply.  Bound: 1e-5 norm-wise against the FP64 oracle for the matvec (FP32
+# storage and sums), 1e-4 for the OSRC apply as for its FP64-vector entry.
+# nrhs 1, 3 and 6 cover every column-chunk width (1..4) of the kernels.
+# ---------------------------------------------------------------------------
+def _rand_c64(rng, shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_matvec_f32_matches_oracle(api, oracle_cache, name, nrhs):
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    x = _rand_c64(np.random.default_rng(nrhs), (nrhs, sk.n_total))
+    y = sysg.matvec_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    yr = np.stack([ref.matvec(xx.astype(np.complex128)) for xx in x])
+    assert rel(y, yr) < 1e-5, rel(y, yr)
+    # repeated launches give identical results (schedule-independent sums)
+    y2 = sysg.matvec_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.array_equal(y, y2)
+
+
+def test_matvec_f32_full_size_sampled_rows(api):
+    """Benchmark workload (rows of ~2200 columns in 5 pieces each), nrhs 2."""
+    cfg = mi.config_split_sphere()
+    sk = skeleton_of(cfg["mesh"])
+    ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"], assemble=False)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    rng = np.random.default_rng(8)
+    x = _rand_c64(rng, (2, sk.n_total))
+    y = sysg.matvec_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    xd = x.astype(np.complex128)
+    for i in range(sk.n_domains):
+        rows = np.sort(rng.choice(sk.N[i], 4, replace=False))
+        Tr, Kr = block_rows(sk, i, ref.k[i], rows)
+        Di, Ni = sk.block_slices(i)
+        r = ref.rho[i]
+        yD = 2 * (Kr @ xd[:, Di].T + (Tr @ xd[:, Ni].T) / r)
+        yN = 2 * (-r * (Tr @ xd[:, Di].T) + Kr @ xd[:, Ni].T)
+        for j in sk.Lambda[i]:
+            Gij = transmission_gram(sk, i, j)[rows]
+            Dj, Nj = sk.block_slices(j)
+            yD += Gij @ xd[:, Dj].T
+            yN += Gij @ xd[:, Nj].T
+        assert rel(y[:, Di][:, rows], yD.T) < 1e-5
+        assert rel(y[:, Ni][:, rows], yN.T) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["sphere", "split"])
+def test_osrc_apply_f32_matches_oracle(api, oracle_cache, name):
+    from oracle.osrc import BlockOSRC
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, precision=1)
+    P = BlockOSRC(sk, ref.k, ref.rho)
+    r = _rand_c64(np.random.default_rng(12), (5, sk.n_total))
+    z = sysg.precond_f32(torch.from_numpy(r).cuda()).cpu().numpy()
+    zr = np.stack([P.apply(rr.astype(np.complex128)) for rr in r])
+    assert rel(z, zr) < 1e-4
+
+
+def test_f32_entries_reject_wrong_systems(api, oracle_cache):
+    cfg, sk, ref = _case(oracle_cache, "sphere")
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sys64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    x = torch.zeros((1, sk.n_total), dtype=torch.complex64, device="cuda")
+    with pytest.raises(api.L.MtfError):
+        sys64.matvec_f32(x)
+    with pytest.raises(api.L.MtfError):
+        sys64.precond_f32(x)
