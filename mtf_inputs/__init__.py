@@ -12,14 +12,14 @@ vertex order) pointing from subdomain ``a`` into subdomain ``b``; subdomain 0
 is the unbounded exterior.  This is the "normal from min(i,j) to max(i,j)"
 orientation of the skeleton mesh described in Sec. 3.2 of the paper.
 """
-from .meshes import (icosphere, split_sphere, cube_partition, two_disjoint_cubes,
+from .meshes import (icosphere, uv_sphere, split_sphere, cube_partition, two_disjoint_cubes,
                      cut_sphere, Mesh)
 from .waves import fibonacci_directions, orthonormal_polarizations, plane_wave_batch
 from .configs import (config_sphere, config_split_sphere, config_cube2,
                       config_cube4, config_batch_instances, CONFIG_NAMES)
 
 __all__ = [
-    "Mesh", "icosphere", "split_sphere", "cube_partition", "two_disjoint_cubes",
+    "Mesh", "icosphere", "uv_sphere", "split_sphere", "cube_partition", "two_disjoint_cubes",
     "cut_sphere", "fibonacci_directions", "orthonormal_polarizations",
     "plane_wave_batch", "config_sphere", "config_split_sphere", "config_cube2",
     "config_cube4", "config_batch_instances", "CONFIG_NAMES",

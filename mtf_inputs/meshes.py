@@ -162,6 +162,37 @@ def icosphere(level: int, radius: float = 1.0, center=(0.0, 0.0, 0.0),
     return Mesh(V, F.astype(np.int32), labels, inside_label + 1, f"icosphere{level}")
 
 
+def uv_sphere(rings: int, segments: int, radius: float = 1.0, inside_label: int = 1) -> Mesh:
+    """Latitude-longitude sphere: two poles and rings - 1 parallels of
+    `segments` points; V = 2 + (rings - 1) segments, so an odd V (and then an
+    odd edge count E = 3V - 6) is available, unlike the icosphere family.
+    Labels and orientation as icosphere (normal into the sphere)."""
+    V = [np.array([0.0, 0.0, 1.0])]
+    for r in range(1, rings):
+        th = np.pi * r / rings
+        for k in range(segments):
+            ph = 2 * np.pi * k / segments + 0.5 * r  # twist rings to avoid slivers
+            V.append(np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)]))
+    V.append(np.array([0.0, 0.0, -1.0]))
+    V = np.array(V) * radius
+    F = []
+    ring = lambda r, k: 1 + (r - 1) * segments + (k % segments)
+    for k in range(segments):
+        F.append((0, ring(1, k), ring(1, k + 1)))
+    for r in range(1, rings - 1):
+        for k in range(segments):
+            a, b, c, d = ring(r, k), ring(r, k + 1), ring(r + 1, k), ring(r + 1, k + 1)
+            F += [(a, c, b), (b, c, d)]
+    south = len(V) - 1
+    for k in range(segments):
+        F.append((south, ring(rings - 1, k + 1), ring(rings - 1, k)))
+    F = np.array(F, dtype=np.int64)
+    cen = V[F].mean(axis=1)
+    F = _orient(V, F, -cen)
+    labels = np.tile(np.array([0, inside_label], dtype=np.int32), (len(F), 1))
+    return Mesh(V, F.astype(np.int32), labels, inside_label + 1, f"uv_sphere{rings}x{segments}")
+
+
 # ----------------------------------------------------------------------------
 # spheres cut by parallel planes (slab subdomains), rotated at random
 # ----------------------------------------------------------------------------

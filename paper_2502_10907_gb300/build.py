@@ -65,7 +65,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
     if jobs or not os.path.exists(LIB):
         libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
-        cmd = [nv, *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver", "-L", libdir,
+        cmd = [nv, *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver", "-lcublas", "-L", libdir,
                "-Xlinker", "-rpath", "-Xlinker", libdir]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:

@@ -104,6 +104,19 @@ struct XEntry {
   int32_t ab;     // a | (b << 2) | (nj << 4): local edges and N_j for the N slot offset
 };
 
+// Work units of a bulk-copy tiled streaming operator apply (stream.cuh):
+// groups of consecutive rows of a block x one column piece, piece-major
+// within a block.  units: {N_i, global row of the first row, first input
+// column, len | piece << 12 | rows << 24 (rows <= 31)}; src: first entry of
+// the first row's piece in the stored operator.
+struct StreamUnits {
+  bool ready = false;
+  int64_t n_units = 0;
+  int32_t pmax = 1;
+  DevBuf<int4> d_units;
+  DevBuf<int64_t> d_src;
+};
+
 }  // namespace mtf
 
 struct mtf_mesh_s {
@@ -133,18 +146,13 @@ struct mtf_mesh_s {
   std::vector<int64_t> reg_cta_prefix;       // regular-pair CTA prefix over blocks
   mtf::DevBuf<int64_t> d_reg_cta_prefix;
   mtf::DevBuf<int32_t> d_row_blk;            // exchange row -> block
-  int64_t n_tiles8 = 0, n_tiles32 = 0;       // 8- and 32-row tiles over all blocks (streaming kernels)
-  mtf::DevBuf<int32_t> d_tile_blk, d_tile_row0, d_tile32_blk, d_tile32_row0;
-  // streaming-matvec work units: (N, global row, first input column, len | piece << 12)
-  // and the float4 offset of each piece in the stored blocks
-  bool mv_units_ready = false;
-  int64_t mv_n_units = 0;
-  int32_t mv_pmax = 1;
-  mtf::DevBuf<int4> d_mv_units;
-  mtf::DevBuf<int64_t> d_mv_src;
+  // streaming work units of the FP32 matvec ({T, K} entries) and of the
+  // OSRC apply (T~ entries)
+  mtf::StreamUnits mv_units, os_units;
+  std::vector<int64_t> os_T_off_h;           // first entry of each block's T~ (rows of even stride)
   // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
   bool osrc_ready = false;
-  mtf::DevBuf<float> d_osrc_Vt, d_osrc_VR, d_osrc_lam;   // W^T, W (per block), |xi|^2 per mode
+  mtf::DevBuf<float> d_osrc_Vt, d_osrc_lam;              // W^T (per block, padded rows), |xi|^2 per mode
   mtf::DevBuf<int32_t> d_osrc_nirr;                      // irrotational modes per block
   std::vector<int64_t> osrc_off_h;                       // padded W offsets per block
   mtf::DevBuf<int64_t> d_osrc_off;
@@ -180,7 +188,9 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_ss_pts[3];           // Sauter-Schwab tables
   // FP32 geometry of the mixed regular-pair kernel (per block-triangle)
   mtf::DevBuf<float> d_x32;                  // FP32 copy of the matvec input (mixed path)
-  mtf::DevBuf<float> d_osrc_f, d_osrc_r32, d_osrc_t;  // OSRC symbol (complex) and apply scratch
+  mtf::DevBuf<float> d_osrc_f, d_osrc_r32;   // OSRC symbol (complex) and apply scratch
+  mtf::DevBuf<float> d_osrc_T;               // complex T~ of every block (rows of N_i, at the blocks' mat_off)
+  mtf::DevBuf<float> d_os_part;              // per-row piece sums of the OSRC apply
   mtf::DevBuf<double> d_cen;
   mtf::DevBuf<float> d_qx, d_qw, d_pv, d_cc;
   int32_t ss_npts[3] = {0, 0, 0};
@@ -197,7 +207,7 @@ namespace mtf {
 enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
-  KID_MISC, KID_MVCOMBINE, KID_COUNT
+  KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
@@ -231,6 +241,15 @@ void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, in
 void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const float* x32, int64_t ld32, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);
 void check_matvec_stream(mtf_system sys, cudaStream_t s);
+// grid size and error word shared by the streaming kernels
+void stream_prepare(mtf_system sys, cudaStream_t s);
+// fill u with the units of the tiled streaming kernel: every block's rows in
+// groups of `rows`, cut into pieces of at most piece_len entries (lengths and
+// starts multiples of 16 / entry_bytes); blk_entry_off[i] = first entry of
+// block i, row_stride[i] = entries between its rows.  Checks that every bulk
+// copy of the units is 16-byte aligned.
+void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, const std::vector<int64_t>& blk_entry_off,
+                        const std::vector<int64_t>& row_stride, StreamUnits& u, cudaStream_t s);
 // One FGMRES cycle of the mixed path on M d = r from d = 0 (FP32 Krylov
 // basis, FP64 reductions), then x += d.  Stops when every right-hand side's
 // estimate reaches tol relative to ||r|| (reached = true), after the restart

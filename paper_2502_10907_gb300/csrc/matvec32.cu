@@ -1,135 +1,12 @@
-// Bulk-copy streaming matvec of the FP32-stored MTF operator (Eq. 16 applied
-// as y = 2 A x + X x, block by block, as in the FP64 kernel).
-//
-// The dense blocks are cut into work units: a unit is one row piece of at
-// most kMvUnit entries (row m of block i, columns [c, c + len)), every row of
-// block i in P_i pieces of near-equal length.  Units are ordered piece-major
-// within a block (all rows of piece 0, then piece 1, ...), and warp g of the
-// grid takes units g, g + W, g + 2W, ... (W warps), so the warps of one SM
-// work on neighbouring rows of the same column piece and share its slice of
-// the input vector in L1.  Each warp owns a private ring of S shared-memory
-// stages; one lane fetches units with the TMA engine (cp.async.bulk, one
-// mbarrier per stage) S units ahead of the one the warp consumes, with the
-// unit records themselves prefetched one unit further ahead, so nothing on
-// a warp's path waits on a global round trip except the matrix data itself.
-//
-// A unit's partial sums (8 per right-hand side: T and K against the D and N
-// slots) are reduced over the warp and stored; k_mv_combine then adds each
-// row's pieces in fixed order (the result does not depend on the schedule)
-// and applies the epilogue: rho coupling, factor 2 and the exchange rows X x.
-//
-// A wait on a bulk copy that does not complete within ~0.5 s sets an error
-// word instead of hanging; the host reports it as MTF_ERR_TIMEOUT.
+// FP32 block matvec of the mixed inner solver (Eq. 16 applied as
+// y = 2 A x + X x, block by block, as in the FP64 kernel): the stored
+// {T, K} entries are streamed by the bulk-copy row kernel of stream.cuh
+// (ENT = 2); k_mv_combine adds each row's pieces and applies the epilogue.
 #include <algorithm>
 
-#include "bulk.h"
-#include "common.h"
+#include "stream.cuh"
 
 namespace mtf {
-
-constexpr int kMvWarps = 8;
-constexpr int kMvUnit = 512;    // float4 entries (8 KB) per unit
-constexpr int kMvStages = 3;
-constexpr uint64_t kMvWaitNs = 500000000ull;
-
-template <int NC>
-struct MvK {
-  static constexpr int K = NC == 1 ? 8 : (NC == 2 ? 16 : 32);  // partial sums per unit, padded to 2^k
-  static constexpr int SH = NC == 1 ? 2 : (NC == 2 ? 1 : 0);  // value index = lane >> SH
-};
-
-// unit record: N of the block, global row, first input column (dof offset of
-// the block + first column of the piece), len | piece << 12; plus the float4
-// offset of the piece in the stored blocks
-template <int NC>
-__global__ void __launch_bounds__(kMvWarps * 32, 1) k_matvec_bulk(const float4* __restrict__ TK,
-                                                                   const int4* __restrict__ units,
-                                                                   const int64_t* __restrict__ usrc, int n_units,
-                                                                   int pmax, const float* __restrict__ x32,
-                                                                   int64_t ld32, int c0, float* __restrict__ part,
-                                                                   unsigned* __restrict__ err) {
-  constexpr int K = MvK<NC>::K, SH = MvK<NC>::SH, S = kMvStages;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* tail = smem_raw + size_t(kMvWarps) * S * kMvUnit * sizeof(float4);
-  float4* ring = reinterpret_cast<float4*>(smem_raw) + size_t(warp) * S * kMvUnit;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tail) + warp * S;
-  int4* meta = reinterpret_cast<int4*>(tail + size_t(kMvWarps) * S * sizeof(uint64_t)) + warp * S;
-  if (lane == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-    mbar_fence_init();
-  }
-  __syncwarp();
-  const int W = int(gridDim.x) * kMvWarps;
-  int u_next = int(blockIdx.x) * kMvWarps + warp;  // next unit to issue
-  int issued = 0, consumed = 0;
-  int4 nrec = make_int4(0, 0, 0, 0);  // lane 0: record of u_next, loaded one issue ahead
-  int64_t nsrc = 0;
-  if (lane == 0 && u_next < n_units) {
-    nrec = units[u_next];
-    nsrc = usrc[u_next];
-  }
-  auto issue = [&]() {
-    if (lane == 0) {
-      const int s = issued % S;
-      meta[s] = nrec;
-      const uint32_t bytes = uint32_t(nrec.w & 0xfff) * uint32_t(sizeof(float4));
-      mbar_arrive_expect_tx(&bar[s], bytes);
-      bulk_g2s(ring + size_t(s) * kMvUnit, TK + nsrc, bytes, &bar[s]);
-      const int un = u_next + W;
-      if (un < n_units) {
-        nrec = units[un];
-        nsrc = usrc[un];
-      }
-    }
-    u_next += W;
-    ++issued;
-  };
-
-  for (int k = 0; k < S && u_next < n_units; ++k) issue();
-  const float2* x2 = reinterpret_cast<const float2*>(x32);
-  while (consumed < issued) {
-    const int s = consumed % S;
-    if (!mbar_wait_bounded(&bar[s], uint32_t(consumed / S) & 1u, kMvWaitNs)) {
-      if (lane == 0) atomicExch(err, 1u);
-      // let the other copies of this warp land (bounded) before leaving
-      for (int q = consumed + 1; q < issued; ++q) mbar_wait_bounded(&bar[q % S], uint32_t(q / S) & 1u, kMvWaitNs);
-      return;
-    }
-    const int4 info = meta[s];
-    const int N = info.x, row = info.y, len = info.w & 0xfff, p = info.w >> 12;
-    const float2* xb = x2 + info.z;
-    float v[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) v[q] = 0.f;
-    const float4* st = ring + size_t(s) * kMvUnit;
-#pragma unroll 4
-    for (int e = lane; e < len; e += 32) {
-      const float4 a = st[e];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float2 xd = __ldg(xb + (c0 + c) * ld32 + e);
-        const float2 xn = __ldg(xb + (c0 + c) * ld32 + e + N);
-        float* w = v + 8 * c;
-        w[0] = fmaf(a.x, xd.x, fmaf(-a.y, xd.y, w[0]));  // T x_D
-        w[1] = fmaf(a.x, xd.y, fmaf(a.y, xd.x, w[1]));
-        w[2] = fmaf(a.x, xn.x, fmaf(-a.y, xn.y, w[2]));  // T x_N
-        w[3] = fmaf(a.x, xn.y, fmaf(a.y, xn.x, w[3]));
-        w[4] = fmaf(a.z, xd.x, fmaf(-a.w, xd.y, w[4]));  // K x_D
-        w[5] = fmaf(a.z, xd.y, fmaf(a.w, xd.x, w[5]));
-        w[6] = fmaf(a.z, xn.x, fmaf(-a.w, xn.y, w[6]));  // K x_N
-        w[7] = fmaf(a.z, xn.y, fmaf(a.w, xn.x, w[7]));
-      }
-    }
-    // stage s has been read: refill it while this unit is reduced
-    fence_proxy_async_smem();
-    __syncwarp();
-    ++consumed;
-    if (u_next < n_units) issue();
-    WarpTransposeSum<K>::run(v, lane, 16);
-    if ((lane & ((1 << SH) - 1)) == 0) part[(int64_t(row) * pmax + p) * K + (lane >> SH)] = v[0];
-  }
-}
 
 // y rows of one block row m (one warp per global row): sum the row's P piece
 // partials in order, then 2 (K x_D + rho^-1 T x_N) + X_D x and
@@ -145,14 +22,14 @@ __global__ void __launch_bounds__(256) k_mv_combine(
     const double* __restrict__ xval, const float* __restrict__ xval32, const double* __restrict__ rho,
     const float* __restrict__ rho32, const XT* __restrict__ x, int64_t ldx, YT* __restrict__ y, int64_t ldy, int c0,
     int64_t n_rows) {
-  constexpr int K = MvK<NC>::K;
+  constexpr int K = StreamK<NC, 2>::K;
   using AT = YT;
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n_rows) return;
   const int i = row_blk[row];
   const int N = blk_N[i];
-  const int P = max(1, (N + kMvUnit - 1) / kMvUnit);
+  const int P = st_pieces<2>(N);
   float tot = 0.f;
   if (lane < K)
     for (int p = 0; p < P; ++p) tot += part[(row * pmax + p) * K + lane];
@@ -204,45 +81,51 @@ __global__ void __launch_bounds__(256) k_mv_combine(
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static void build_units(mtf_mesh m, cudaStream_t s) {
-  if (m->mv_units_ready) return;
+void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, const std::vector<int64_t>& blk_entry_off,
+                        const std::vector<int64_t>& row_stride, StreamUnits& su, cudaStream_t s) {
+  MTF_REQUIRE(entry_bytes == 8 || entry_bytes == 16, MTF_ERR_ARG, "stream entries are 8 or 16 bytes");
+  MTF_REQUIRE(rows >= 1 && rows <= 31, MTF_ERR_ARG, "rows per stream unit out of range");
+  const int q = 16 / entry_bytes;  // entries per 16 bytes
   std::vector<int4> u;
   std::vector<int64_t> src;
   int pmax = 1;
   for (int i = 0; i < m->nd; ++i) {
     const int N = m->blk[i].N;
-    const int P = std::max(1, (N + kMvUnit - 1) / kMvUnit);
-    const int ps = (N + P - 1) / P;
-    MTF_REQUIRE(ps <= kMvUnit, MTF_ERR_MESH, "matvec piece longer than a stage");
+    const int64_t ld = row_stride[i];
+    const int P = std::max(1, (N + piece_len - 1) / piece_len);
+    const int ps = ((N + P - 1) / P + q - 1) / q * q;
+    MTF_REQUIRE(ps <= piece_len && P < 4096 && N < (1 << 30), MTF_ERR_MESH, "stream piece longer than a slot");
+    MTF_REQUIRE((ld * entry_bytes) % 16 == 0 && (blk_entry_off[i] * entry_bytes) % 16 == 0 && ld >= N,
+                MTF_ERR_ARG, "stream operator rows are not 16-byte aligned");
     pmax = std::max(pmax, P);
-    for (int p = 0; p < P; ++p)
-      for (int r = 0; r < N; ++r) {
-        const int c = p * ps, len = std::min(ps, N - c);
-        MTF_REQUIRE(len > 0, MTF_ERR_MESH, "empty matvec piece");
-        u.push_back(make_int4(N, int(m->blk[i].row_off + r), int(m->blk[i].dof_off + c), len | (p << 12)));
-        src.push_back(m->blk[i].mat_off + int64_t(r) * N + c);
+    for (int p = 0; p < P; ++p) {
+      const int c = p * ps, len = std::min(ps, N - c);
+      const int clen = (len + q - 1) / q * q;  // entries the copy moves
+      MTF_REQUIRE(len > 0 && len < 4096 && c + clen <= ld, MTF_ERR_MESH, "stream piece out of its row");
+      for (int r0 = 0; r0 < N; r0 += rows) {
+        const int nr = std::min(rows, N - r0);
+        u.push_back(make_int4(N, int(m->blk[i].row_off + r0), int(m->blk[i].dof_off + c),
+                              len | (p << 12) | (nr << 24)));
+        src.push_back(blk_entry_off[i] + int64_t(r0) * ld + c);
       }
+    }
   }
   MTF_REQUIRE(m->n_total < (int64_t(1) << 31) && int64_t(u.size()) < (int64_t(1) << 31), MTF_ERR_MESH,
-              "mesh too large for the streaming matvec tables");
-  m->mv_n_units = int64_t(u.size());
-  m->mv_pmax = pmax;
-  m->d_mv_units.alloc(u.size());
-  m->d_mv_src.alloc(src.size());
+              "mesh too large for the streaming tables");
+  su.n_units = int64_t(u.size());
+  su.pmax = pmax;
+  su.d_units.alloc(u.size());
+  su.d_src.alloc(src.size());
   if (!u.empty()) {
-    MTF_CUDA(cudaMemcpyAsync(m->d_mv_units.p, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-    MTF_CUDA(cudaMemcpyAsync(m->d_mv_src.p, src.data(), src.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(su.d_units.p, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(su.d_src.p, src.data(), src.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     MTF_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
   }
-  m->mv_units_ready = true;
+  su.ready = true;
 }
 
-static void ensure_mv_scratch(mtf_system sys, cudaStream_t s) {
-  mtf_mesh m = sys->mesh;
-  build_units(m, s);
-  const size_t npart = size_t(m->n_rows) * m->mv_pmax * 32;
-  if (sys->d_mv_part.n != npart) {
-    sys->d_mv_part.alloc(npart);
+void stream_prepare(mtf_system sys, cudaStream_t s) {
+  if (!sys->d_mv_ctl.p) {
     sys->d_mv_ctl.alloc(4);
     MTF_CUDA(cudaMemsetAsync(sys->d_mv_ctl.p, 0, 4 * sizeof(unsigned), s));
   }
@@ -254,21 +137,28 @@ static void ensure_mv_scratch(mtf_system sys, cudaStream_t s) {
   }
 }
 
-static constexpr size_t mv_smem() {
-  return size_t(kMvWarps) * kMvStages * (kMvUnit * sizeof(float4) + sizeof(uint64_t) + sizeof(int4));
+static void ensure_mv_scratch(mtf_system sys, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  stream_prepare(sys, s);
+  if (!m->mv_units.ready) {
+    std::vector<int64_t> off(m->nd), ld(m->nd);
+    for (int i = 0; i < m->nd; ++i) {
+      off[i] = m->blk[i].mat_off;
+      ld[i] = m->blk[i].N;
+    }
+    build_stream_units(m, kStRows, st_piece_len<2>(), 16, off, ld, m->mv_units, s);
+  }
+  const size_t npart = size_t(m->n_rows) * m->mv_units.pmax * 32;
+  if (sys->d_mv_part.n < npart) sys->d_mv_part.alloc(npart);
 }
 
 template <int NC, class XT, class YT>
 static void mv_launch(mtf_system sys, const XT* x, int64_t ldx, const float* x32, int64_t ld32, YT* y, int64_t ldy,
                       int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  auto kfn = k_matvec_bulk<NC>;
-  MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(mv_smem())));
-  MTF_LAUNCH(KID_MATVEC32, s, kfn<<<unsigned(sys->mv_grid), kMvWarps * 32, mv_smem(), s>>>(
-      reinterpret_cast<const float4*>(sys->d_TK32.p), m->d_mv_units.p, m->d_mv_src.p, int(m->mv_n_units),
-      m->mv_pmax, x32, ld32, c0, sys->d_mv_part.p, sys->d_mv_ctl.p + 2));
+  launch_stream_tiles<NC, 2>(sys, sys->d_TK32.p, m->mv_units, x32, ld32, c0, sys->d_mv_part.p, KID_MATVEC32, s);
   MTF_LAUNCH(KID_MVCOMBINE, s, k_mv_combine<NC, XT, YT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
-      sys->d_mv_part.p, m->mv_pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
+      sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
       m->d_xent.p, sys->d_xval.p, sys->d_xval32.p, sys->d_rho.p, sys->d_rho32.p, x, ldx, y, ldy, c0, m->n_rows));
 }
 
@@ -295,9 +185,9 @@ void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, in
   mv_all<float, float>(sys, x, ldx, x, ldx, y, ldy, nrhs, s);
 }
 
-// Throws MTF_ERR_TIMEOUT if a launch of the streaming matvec gave up on a
-// bulk copy since the last check (synchronises the stream) and clears the
-// error word.
+// Throws MTF_ERR_TIMEOUT if a launch of a streaming kernel (matvec or OSRC
+// apply) gave up on a bulk copy since the last check (synchronises the
+// stream) and clears the error word.
 void check_matvec_stream(mtf_system sys, cudaStream_t s) {
   if (!sys->d_mv_ctl.p) return;
   unsigned ctl[4];
@@ -306,7 +196,7 @@ void check_matvec_stream(mtf_system sys, cudaStream_t s) {
   if (ctl[2] == 0) return;
   MTF_CUDA(cudaMemsetAsync(sys->d_mv_ctl.p, 0, 4 * sizeof(unsigned), s));
   MTF_CUDA(cudaStreamSynchronize(s));
-  throw Error{MTF_ERR_TIMEOUT, "a bulk copy of the streaming matvec did not complete in time"};
+  throw Error{MTF_ERR_TIMEOUT, "a bulk copy of a streaming operator apply did not complete in time"};
 }
 
 }  // namespace mtf

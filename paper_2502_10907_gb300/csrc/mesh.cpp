@@ -298,24 +298,6 @@ void upload_mesh(mtf_mesh m, cudaStream_t s) {
   m->d_blk_T.upload(T, s);
   m->d_reg_cta_prefix.upload(m->reg_cta_prefix, s);
   m->d_row_blk.upload(row_blk, s);
-  std::vector<int32_t> tb, tr;
-  for (int i = 0; i < m->nd; ++i)
-    for (int r = 0; r < m->blk[i].N; r += 8) {
-      tb.push_back(i);
-      tr.push_back(r);
-    }
-  m->n_tiles8 = int64_t(tb.size());
-  m->d_tile_blk.upload(tb, s);
-  m->d_tile_row0.upload(tr, s);
-  std::vector<int32_t> tb32, tr32;
-  for (int i = 0; i < m->nd; ++i)
-    for (int r = 0; r < m->blk[i].N; r += 32) {
-      tb32.push_back(i);
-      tr32.push_back(r);
-    }
-  m->n_tiles32 = int64_t(tb32.size());
-  m->d_tile32_blk.upload(tb32, s);
-  m->d_tile32_row0.upload(tr32, s);
   MTF_CUDA(cudaStreamSynchronize(s));
 }
 

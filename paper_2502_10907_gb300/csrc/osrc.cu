@@ -13,9 +13,13 @@
 // eps = c k^{1/3} R^{-2/3}, R the radius of the sphere with Gamma_i's area.
 // the two factors of the OSRC magnetic-to-electric operator.  The eigenpairs
 // depend on the mesh only and are computed once (FP32 dense symmetric-
-// definite eigensolver); f depends on k and is recomputed at every assembly.
-// The apply is two dense FP32 passes per block, t = W^T r and z = W (f t),
-// HBM-bound like the block matvec.
+// definite eigensolver); f depends on k and is recomputed at every assembly,
+// together with the dense complex T~ of every block (two FP32 GEMMs,
+// W diag(Re f) W^T and W diag(Im f) W^T).  The apply streams T~ once per
+// right-hand-side chunk with the bulk-copy row kernel (stream.cuh, ENT = 1),
+// HBM-bound like the block matvec: the same bytes as the two real passes
+// t = W^T r, z = W (f t), in one launch and without the intermediate t.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -23,7 +27,7 @@
 #include <complex>
 #include <mutex>
 
-#include "common.h"
+#include "stream.cuh"
 
 namespace mtf {
 
@@ -121,21 +125,6 @@ __global__ void k_build_w(const float* __restrict__ V, const float* __restrict__
   W[t] = v;
 }
 
-// W row-major padded (ld) from column-major W (= row-major W^T, N x N)
-__global__ void k_transpose_block(const float* __restrict__ Vt, int N, int ld, float* __restrict__ VR) {
-  __shared__ float tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int row = by + r, col = bx + threadIdx.x;
-    if (row < N && col < N) tile[r][threadIdx.x] = Vt[int64_t(row) * N + col];
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int row = bx + r, col = by + threadIdx.x;
-    if (row < N && col < N) VR[int64_t(row) * ld + col] = tile[threadIdx.x][r];
-  }
-}
-
 // W^T row-major padded (ld): row j = column j of W; pad entries are zero
 __global__ void k_pad_copy(const float* __restrict__ W, int N, int ld, float* __restrict__ Wt) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -179,136 +168,73 @@ __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __re
   }
 }
 
-// Streaming passes (same pattern as the FP32 matvec): CTA = 8 rows of one
-// block, one warp per row streaming a padded FP32 row with float4 loads, the
-// block's complex input pair (slot D, slot N; NC right-hand sides) staged in
-// shared memory in chunks.
-//   PASS 1: rows of W^T (modes j), input r (tested residual), output
-//           t_D[j] = f_j (W^T r_D)_j, t_N[j] = f_j (W^T r_N)_j (FP32).
-//   PASS 2: rows of W (dofs e), input t, output z_D = rho^-1 (W t_N)_e,
-//           z_N = -rho (W t_D)_e (FP64).
-constexpr int kOsChunk = 1024;
+// columns j of W (rows e, leading dimension ld) scaled by Re f_j and Im f_j
+__global__ void k_scale_modes(const float* __restrict__ Wc, int N, int ld, const float2* __restrict__ f,
+                              float* __restrict__ Bre, float* __restrict__ Bim) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(N) * ld) return;
+  const int j = int(t / ld);
+  const float w = Wc[t];
+  const float2 fj = f[j];
+  Bre[t] = w * fj.x;
+  Bim[t] = w * fj.y;
+}
 
-constexpr int kOsRowsPerWarp = 4;  // a CTA covers 32 rows, amortising one staging
-constexpr int kOsRowsPerCta = 8 * kOsRowsPerWarp;
+// complex rows of stride ldt (>= N, padding zero) from N x N real and imaginary parts
+__global__ void k_interleave(const float* __restrict__ re, const float* __restrict__ im, int N, int ldt,
+                             float2* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(N) * ldt) return;
+  const int64_t r = t / ldt, c = t % ldt;
+  out[t] = c < N ? make_float2(re[r * N + c], im[r * N + c]) : make_float2(0.f, 0.f);
+}
 
-template <int PASS, int NC, class ZT>
-__global__ void __launch_bounds__(256) k_osrc_stream(
-    const float* __restrict__ Wm, const int64_t* __restrict__ osrc_off, const float* __restrict__ vin,
-    int64_t ldin, const float2* __restrict__ f, const double* __restrict__ rho, const float* __restrict__ rho32,
-    const int32_t* __restrict__ tile_blk, const int32_t* __restrict__ tile_row0,
-    const int32_t* __restrict__ blk_N, const int64_t* __restrict__ blk_dof_off,
-    const int64_t* __restrict__ blk_row_off, int64_t n_total, int c0, float2* __restrict__ tout,
-    ZT* __restrict__ zout, int64_t ldz) {
-  constexpr int RW = kOsRowsPerWarp;
-  extern __shared__ float2 vs[];  // [NC][2][kOsChunk]
-  const int i = tile_blk[blockIdx.x];
-  const int r0 = tile_row0[blockIdx.x];
+// z rows of one block row m (one warp per global row): the row's T~ pieces
+// added in order, then z_D = rho^-1 (T~ r_N), z_N = -rho (T~ r_D) per
+// right-hand side (lane c < NC), in the output precision.
+template <int NC, class ZT>
+__global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ part, int pmax,
+                                                    const int32_t* __restrict__ row_blk,
+                                                    const int32_t* __restrict__ blk_N,
+                                                    const int64_t* __restrict__ blk_dof_off,
+                                                    const int64_t* __restrict__ blk_row_off,
+                                                    const double* __restrict__ rho, const float* __restrict__ rho32,
+                                                    ZT* __restrict__ z, int64_t ldz, int c0, int64_t n_rows) {
+  constexpr int K = StreamK<NC, 1>::K;
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const int i = row_blk[row];
   const int N = blk_N[i];
-  const int ld = (N + 3) & ~3;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // input vectors: complex FP32, per rhs c at vin + 2 (c * n_total + dof_off_i), slots at +0 / +N
-  const int64_t base = blk_dof_off[i];
-  const float4* wr[RW];
-  bool act[RW];
+  const int P = st_pieces<1>(N);
+  float tot = 0.f;
+  if (lane < K)
+    for (int p = 0; p < P; ++p) tot += part[(row * pmax + p) * K + lane];
+  float a[4];
+  const int cl = lane < NC ? lane : 0;
 #pragma unroll
-  for (int q = 0; q < RW; ++q) {
-    const int row = r0 + q * 8 + warp;
-    act[q] = row < N;
-    wr[q] = reinterpret_cast<const float4*>(Wm + osrc_off[i] + int64_t(act[q] ? row : 0) * ld);
-  }
-  float acc[RW][NC][4];
-#pragma unroll
-  for (int q = 0; q < RW; ++q)
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) acc[q][c][t] = 0.f;
-  for (int cb = 0; cb < N; cb += kOsChunk) {
-    const int clen = min(kOsChunk, N - cb);
-    __syncthreads();
-    for (int t = threadIdx.x; t < NC * 2 * kOsChunk; t += blockDim.x) {
-      const int c = t / (2 * kOsChunk), rem = t % (2 * kOsChunk), slot = rem / kOsChunk, e = rem % kOsChunk;
-      vs[t] = e < clen ? *reinterpret_cast<const float2*>(vin + 2 * ((c0 + c) * ldin + base + slot * N + cb + e))
-                       : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int nq = (clen + 3) >> 2;  // float4 groups in this chunk (row padding is zero)
-    for (int g = lane; g < nq; g += 32) {
-      float4 w4[RW];
-#pragma unroll
-      for (int q = 0; q < RW; ++q) w4[q] = act[q] ? __ldg(wr[q] + (cb >> 2) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 a = vs[(c * 2) * kOsChunk + 4 * g + e];
-          const float2 b = vs[(c * 2 + 1) * kOsChunk + 4 * g + e];
-#pragma unroll
-          for (int q = 0; q < RW; ++q) {
-            const float wv = e == 0 ? w4[q].x : (e == 1 ? w4[q].y : (e == 2 ? w4[q].z : w4[q].w));
-            acc[q][c][0] = fmaf(wv, a.x, acc[q][c][0]);
-            acc[q][c][1] = fmaf(wv, a.y, acc[q][c][1]);
-            acc[q][c][2] = fmaf(wv, b.x, acc[q][c][2]);
-            acc[q][c][3] = fmaf(wv, b.y, acc[q][c][3]);
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RW; ++q)
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        float v = acc[q][c][t];
-#pragma unroll
-        for (int s2 = 16; s2 > 0; s2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s2);
-        acc[q][c][t] = v;
-      }
+  for (int q = 0; q < 4; ++q) a[q] = __shfl_sync(0xffffffffu, tot, cl * 4 + q);
   if (lane >= NC) return;
-  const int col = c0 + lane;
-#pragma unroll
-  for (int q = 0; q < RW; ++q) {
-    if (!act[q]) continue;
-    const int row = r0 + q * 8 + warp;
-    float a0 = acc[q][0][0], a1 = acc[q][0][1], a2 = acc[q][0][2], a3 = acc[q][0][3];
-#pragma unroll
-    for (int c = 1; c < NC; ++c)
-      if (lane == c) {
-        a0 = acc[q][c][0];
-        a1 = acc[q][c][1];
-        a2 = acc[q][c][2];
-        a3 = acc[q][c][3];
-      }
-    if (PASS == 1) {
-      const float2 fr = f[blk_row_off[i] + row];
-      float2* tc = tout + (int64_t(col) * n_total + base);
-      tc[row] = make_float2(fr.x * a0 - fr.y * a1, fr.x * a1 + fr.y * a0);
-      tc[N + row] = make_float2(fr.x * a2 - fr.y * a3, fr.x * a3 + fr.y * a2);
-    } else {
-      // rho, 1/rho in the output precision (FP32 from the per-block table)
-      ZT rr, ri, ir, ii;
-      if constexpr (sizeof(ZT) == 4) {
-        rr = rho32[4 * i];
-        ri = rho32[4 * i + 1];
-        ir = rho32[4 * i + 2];
-        ii = rho32[4 * i + 3];
-      } else {
-        rr = rho[2 * i];
-        ri = rho[2 * i + 1];
-        const ZT rn = rr * rr + ri * ri;
-        ir = rr / rn;
-        ii = -ri / rn;
-      }
-      ZT* zc = zout + 2 * (int64_t(col) * ldz + base);
-      zc[2 * row] = ZT(ir * a2 - ii * a3);
-      zc[2 * row + 1] = ZT(ir * a3 + ii * a2);
-      zc[2 * (N + row)] = ZT(-(rr * a0 - ri * a1));
-      zc[2 * (N + row) + 1] = ZT(-(rr * a1 + ri * a0));
-    }
+  ZT rr, ri, ir, ii;
+  if constexpr (sizeof(ZT) == 4) {
+    rr = rho32[4 * i];
+    ri = rho32[4 * i + 1];
+    ir = rho32[4 * i + 2];
+    ii = rho32[4 * i + 3];
+  } else {
+    rr = rho[2 * i];
+    ri = rho[2 * i + 1];
+    const ZT rn = rr * rr + ri * ri;
+    ir = rr / rn;
+    ii = -ri / rn;
   }
+  const int64_t m = row - blk_row_off[i];
+  ZT* zc = z + 2 * (int64_t(c0 + lane) * ldz + blk_dof_off[i]);
+  const ZT a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3];  // T~ r_D, T~ r_N
+  zc[2 * m] = ir * a2 - ii * a3;
+  zc[2 * m + 1] = ir * a3 + ii * a2;
+  zc[2 * (N + m)] = -(rr * a0 - ri * a1);
+  zc[2 * (N + m) + 1] = -(rr * a1 + ri * a0);
 }
 
 __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t n2, int nrhs, float* __restrict__ out) {
@@ -316,6 +242,16 @@ __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t
   if (t >= n2 * nrhs) return;
   const int64_t c = t / n2, k = t % n2;
   out[t] = float(x[2 * c * ldx + k]);
+}
+
+static cublasHandle_t blas_handle() {
+  static cublasHandle_t h = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!h) {
+    MTF_REQUIRE(cublasCreate(&h) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasCreate failed");
+  }
+  return h;
 }
 
 static cusolverDnHandle_t solver_handle() {
@@ -345,9 +281,7 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   }
   m->d_osrc_off.upload(m->osrc_off_h, s);
   m->d_osrc_Vt.alloc(size_t(po));
-  m->d_osrc_VR.alloc(size_t(po));
   m->d_osrc_lam.alloc(size_t(m->n_rows));
-  MTF_CUDA(cudaMemsetAsync(m->d_osrc_VR.p, 0, size_t(po) * sizeof(float), s));
   DevBuf<float> Dd;
   Dd.alloc(size_t(m->n_mat));
   G.alloc(size_t(m->n_mat));
@@ -401,13 +335,11 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
         A, lam_tmp.p + m->blk[i].row_off, S1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
         m->d_edge_lohi.p + 2 * m->blk[i].row_off, m->d_edge_len.p + m->blk[i].row_off, N, nirr, nv, Wtmp.p,
         m->d_osrc_lam.p + m->blk[i].row_off));
-    // padded row-major W^T (rows = modes) and W (rows = RWG dofs), ld = N rounded up to 4
+    // padded row-major W^T (rows = modes), ld = N rounded up to 4: the
+    // column-major W (rows = RWG dofs) with leading dimension ld
     const int ld = (N + 3) & ~3;
-    dim3 tg{unsigned((N + 31) / 32), unsigned((N + 31) / 32), 1u};
     MTF_LAUNCH(KID_MISC, s, k_pad_copy<<<unsigned((int64_t(N) * ld + 255) / 256), 256, 0, s>>>(
         Wtmp.p, N, ld, m->d_osrc_Vt.p + m->osrc_off_h[i]));
-    MTF_LAUNCH(KID_MISC, s, k_transpose_block<<<tg, dim3(32, 8), 0, s>>>(Wtmp.p, N, ld,
-                                                                         m->d_osrc_VR.p + m->osrc_off_h[i]));
     MTF_CUDA(cudaStreamSynchronize(s));
   }
   std::vector<int32_t> nirr_h(m->nd);
@@ -462,40 +394,74 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   MTF_LAUNCH(KID_MISC, s, k_osrc_symbol<<<unsigned((m->n_rows + 127) / 128), 128, 0, s>>>(
       m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, m->d_blk_row_off.p, m->d_osrc_nirr.p, sys->d_k.p, d_keps.p,
       d_pd.p, np, reinterpret_cast<float2*>(sys->d_osrc_f.p)));
-  MTF_CUDA(cudaStreamSynchronize(s));  // d_pd / d_keps are freed on return
+  // T~_i = W diag(f) W^T (column-major GEMMs; T~ is symmetric, so the
+  // column-major result read row by row is T~ itself)
+  cublasHandle_t bh = blas_handle();
+  MTF_REQUIRE(cublasSetStream(bh, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
+  MTF_REQUIRE(cublasSetMathMode(bh, CUBLAS_PEDANTIC_MATH) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
+              "cublasSetMathMode failed");
+  int nmax = 0;
+  for (int i = 0; i < m->nd; ++i) nmax = std::max(nmax, m->blk[i].N);
+  const int ldmax = (nmax + 3) & ~3;
+  DevBuf<float> Bre, Bim, Cre, Cim;
+  Bre.alloc(size_t(nmax) * ldmax);
+  Bim.alloc(size_t(nmax) * ldmax);
+  Cre.alloc(size_t(nmax) * nmax);
+  Cim.alloc(size_t(nmax) * nmax);
+  // T~ rows padded to an even length (8-byte entries: 16-byte aligned rows)
+  m->os_T_off_h.assign(m->nd, 0);
+  int64_t toff = 0;
+  for (int i = 0; i < m->nd; ++i) {
+    m->os_T_off_h[i] = toff;
+    toff += int64_t(m->blk[i].N) * (m->blk[i].N + (m->blk[i].N & 1));
+  }
+  sys->d_osrc_T.alloc(size_t(toff) * 2);
+  const float one = 1.f, zero = 0.f;
+  for (int i = 0; i < m->nd; ++i) {
+    const int N = m->blk[i].N, ld = (N + 3) & ~3;
+    const float* Wc = m->d_osrc_Vt.p + m->osrc_off_h[i];
+    MTF_LAUNCH(KID_MISC, s, k_scale_modes<<<unsigned((int64_t(N) * ld + 255) / 256), 256, 0, s>>>(
+        Wc, N, ld, reinterpret_cast<const float2*>(sys->d_osrc_f.p) + m->blk[i].row_off, Bre.p, Bim.p));
+    MTF_REQUIRE(cublasSgemm(bh, CUBLAS_OP_N, CUBLAS_OP_T, N, N, N, &one, Bre.p, ld, Wc, ld, &zero, Cre.p, N) ==
+                    CUBLAS_STATUS_SUCCESS,
+                MTF_ERR_CUDA, "cublasSgemm failed");
+    MTF_REQUIRE(cublasSgemm(bh, CUBLAS_OP_N, CUBLAS_OP_T, N, N, N, &one, Bim.p, ld, Wc, ld, &zero, Cim.p, N) ==
+                    CUBLAS_STATUS_SUCCESS,
+                MTF_ERR_CUDA, "cublasSgemm failed");
+    const int ldt = N + (N & 1);
+    const int64_t nn = int64_t(N) * ldt;
+    MTF_LAUNCH(KID_MISC, s, k_interleave<<<unsigned((nn + 255) / 256), 256, 0, s>>>(
+        Cre.p, Cim.p, N, ldt, reinterpret_cast<float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i]));
+  }
+  MTF_CUDA(cudaStreamSynchronize(s));  // scratch and d_pd / d_keps are freed on return
+}
+
+template <int NC, class ZT>
+static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int c0, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  launch_stream_tiles<NC, 1>(sys, sys->d_osrc_T.p, m->os_units, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
+  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+      sys->d_os_part.p, m->os_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
+      sys->d_rho.p, sys->d_rho32.p, z, ldz, c0, m->n_rows));
 }
 
 template <class ZT>
-static void osrc_passes(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
+static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  const int64_t n2 = 2 * m->n_total;
-  if (sys->d_osrc_t.n < size_t(n2) * nrhs) sys->d_osrc_t.alloc(size_t(n2) * nrhs);
-  const unsigned tiles = unsigned(m->n_tiles32);
-  const float2* f = reinterpret_cast<const float2*>(sys->d_osrc_f.p);
-  float2* t = reinterpret_cast<float2*>(sys->d_osrc_t.p);
+  stream_prepare(sys, s);
+  if (!m->os_units.ready) {
+    std::vector<int64_t> ld(m->nd);
+    for (int i = 0; i < m->nd; ++i) ld[i] = m->blk[i].N + (m->blk[i].N & 1);
+    build_stream_units(m, kStRows, st_piece_len<1>(), 8, m->os_T_off_h, ld, m->os_units, s);
+  }
+  const size_t npart = size_t(m->n_rows) * m->os_units.pmax * 16;
+  if (sys->d_os_part.n < npart) sys->d_os_part.alloc(npart);
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     const int nc = std::min(4, nrhs - c0);
-    const size_t smem = size_t(nc) * 2 * kOsChunk * sizeof(float2);
-#define OS_PASS(P, NC, W, VIN, LDIN)                                                                            \
-  do {                                                                                                         \
-    auto kfn = k_osrc_stream<P, NC, ZT>;                                                                       \
-    MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));               \
-    MTF_LAUNCH(KID_OSRC, s, kfn<<<tiles, 256, smem, s>>>(W, m->d_osrc_off.p, VIN, LDIN, f, sys->d_rho.p, sys->d_rho32.p, \
-                                                         m->d_tile32_blk.p, m->d_tile32_row0.p, m->d_blk_N.p,  \
-                                                         m->d_blk_dof_off.p, m->d_blk_row_off.p, m->n_total,   \
-                                                         c0, t, z, ldz));                                       \
-  } while (0)
-#define OS_BOTH(NC)                                                                                  \
-  do {                                                                                               \
-    OS_PASS(1, NC, m->d_osrc_Vt.p, r32, ldr);                                                        \
-    OS_PASS(2, NC, m->d_osrc_VR.p, reinterpret_cast<const float*>(sys->d_osrc_t.p), m->n_total);    \
-  } while (0)
-    if (nc == 1) OS_BOTH(1);
-    else if (nc == 2) OS_BOTH(2);
-    else if (nc == 3) OS_BOTH(3);
-    else OS_BOTH(4);
-#undef OS_BOTH
-#undef OS_PASS
+    if (nc == 1) os_launch<1>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 2) os_launch<2>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 3) os_launch<3>(sys, r32, ldr, z, ldz, c0, s);
+    else os_launch<4>(sys, r32, ldr, z, ldz, c0, s);
   }
 }
 
@@ -505,13 +471,13 @@ void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, 
   const int64_t n2 = 2 * m->n_total;
   if (sys->d_osrc_r32.n < size_t(n2) * nrhs) sys->d_osrc_r32.alloc(size_t(n2) * nrhs);
   MTF_LAUNCH(KID_OSRC, s, k_to_f32_cols<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(r, ldr, n2, nrhs, sys->d_osrc_r32.p));
-  osrc_passes<double>(sys, sys->d_osrc_r32.p, m->n_total, z, ldz, nrhs, s);
+  osrc_stream<double>(sys, sys->d_osrc_r32.p, m->n_total, z, ldz, nrhs, s);
 }
 
 // FP32 in, FP32 out (the FP32-basis inner solver)
 void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
                            cudaStream_t s) {
-  osrc_passes<float>(sys, r, ldr, z, ldz, nrhs, s);
+  osrc_stream<float>(sys, r, ldr, z, ldz, nrhs, s);
 }
 
 }  // namespace mtf

@@ -1,0 +1,248 @@
+// Bulk-copy tiled streaming kernel of the FP32 operator applies: the block
+// matvec (entries {T, K}: two complex FP32 values, ENT = 2) and the
+// block-OSRC apply (entries T~: one complex FP32 value, ENT = 1).
+//
+// A dense block is cut into work units of kStRows consecutive rows x one
+// column piece of at most st_piece_len<ENT>() entries (every row of block i
+// in P_i pieces of near-equal length).  One persistent CTA per SM takes units
+// blockIdx.x, blockIdx.x + gridDim.x, ...  A producer warp fetches, with the
+// TMA engine (cp.async.bulk, one "full" mbarrier per stage), the unit's row
+// pieces and the matching slices of the input vectors (D and N slots of
+// every right-hand side) into a ring of S shared-memory stages; kStConsumers
+// consumer warps, two rows each, read both from shared memory, so the input
+// slice is fetched once per unit instead of once per row, each value of it
+// read from shared memory serves two rows, and no consumer waits on a global
+// load.  Consumers release a stage through an "empty" mbarrier.
+//
+// Per row and right-hand side a consumer forms the partial sums
+//   ENT = 2:  T x_D, T x_N, K x_D, K x_N    (8 floats)
+//   ENT = 1:  T~ x_D, T~ x_N                (4 floats)
+// reduces them over the warp (recursive halving) and stores them at
+// part[(row * pmax + piece) * K + value]; a per-operator combine kernel adds
+// each row's pieces in fixed order and applies the epilogue.
+//
+// Bulk copies need 16-byte aligned addresses and sizes: rows of ENT = 1
+// operators are stored with an even row stride and pieces start at even
+// columns (the host checks every unit), and input slices are widened to the
+// enclosing 16-byte boundaries, which stay inside the vector because vectors
+// start at even complex offsets (ld32 even, 16-byte aligned base: checked by
+// the host).  Every wait is bounded (~0.5 s): on timeout the kernel sets *err
+// and its warps leave.
+#pragma once
+
+#include "bulk.h"
+#include "common.h"
+
+namespace mtf {
+
+// tuning (compile-time overridable): bytes of one row piece, shared-memory
+// budget of the stage ring
+#ifndef MTF_ST_PIECE_BYTES
+#define MTF_ST_PIECE_BYTES 4096
+#endif
+#ifndef MTF_ST_SMEM_BUDGET
+#define MTF_ST_SMEM_BUDGET (220 * 1024)
+#endif
+constexpr int kStConsumers = 8;          // consumer warps per CTA
+constexpr int kStRows = 2 * kStConsumers;  // rows per unit: two per consumer warp
+constexpr int kStMaxStages = 8;
+constexpr int kStSmemBudget = MTF_ST_SMEM_BUDGET;
+constexpr uint64_t kStWaitNs = 500000000ull;
+
+// entries per piece (one row's slot in a stage)
+template <int ENT>
+__host__ __device__ constexpr int st_piece_len() {
+  return MTF_ST_PIECE_BYTES / (8 * ENT);
+}
+
+template <int NC, int ENT>
+struct StreamK {
+  static constexpr int raw = 4 * ENT * NC;  // partial sums per row piece
+  static constexpr int K = raw <= 4 ? 4 : (raw <= 8 ? 8 : (raw <= 16 ? 16 : 32));
+  static constexpr int SH = K == 4 ? 3 : (K == 8 ? 2 : (K == 16 ? 1 : 0));  // value index = lane >> SH
+  static constexpr int L = st_piece_len<ENT>();
+  static constexpr int RB = L * 8 * ENT;                                       // bytes of a row slot
+  static constexpr int XB = (L + 2) * 8;                                       // bytes of an input-slice slot
+  static constexpr int SB = ((kStRows * RB + 2 * NC * XB) + 127) / 128 * 128;  // bytes of a stage
+  static constexpr int S = (kStSmemBudget / SB) < kStMaxStages ? (kStSmemBudget / SB) : kStMaxStages;
+  static constexpr size_t smem = size_t(S) * SB + size_t(S) * (2 * sizeof(uint64_t) + sizeof(int4));
+  static_assert(S >= 2, "the stage ring needs at least two stages");
+  static_assert(smem <= 232448, "shared memory above the per-CTA limit");
+};
+
+// partial sums of one row piece against NC right-hand sides, accumulated into v
+template <int NC, int ENT>
+__device__ __forceinline__ void st_row_fma(float* v, const unsigned char* rowp, const float2* const* xs, int e) {
+  if constexpr (ENT == 2) {
+    const float4 a = reinterpret_cast<const float4*>(rowp)[e];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float2 xd = xs[2 * c][e], xn = xs[2 * c + 1][e];
+      float* w = v + 8 * c;
+      w[0] = fmaf(a.x, xd.x, fmaf(-a.y, xd.y, w[0]));  // T x_D
+      w[1] = fmaf(a.x, xd.y, fmaf(a.y, xd.x, w[1]));
+      w[2] = fmaf(a.x, xn.x, fmaf(-a.y, xn.y, w[2]));  // T x_N
+      w[3] = fmaf(a.x, xn.y, fmaf(a.y, xn.x, w[3]));
+      w[4] = fmaf(a.z, xd.x, fmaf(-a.w, xd.y, w[4]));  // K x_D
+      w[5] = fmaf(a.z, xd.y, fmaf(a.w, xd.x, w[5]));
+      w[6] = fmaf(a.z, xn.x, fmaf(-a.w, xn.y, w[6]));  // K x_N
+      w[7] = fmaf(a.z, xn.y, fmaf(a.w, xn.x, w[7]));
+    }
+  } else {
+    const float2 a = reinterpret_cast<const float2*>(rowp)[e];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float2 xd = xs[2 * c][e], xn = xs[2 * c + 1][e];
+      float* w = v + 4 * c;
+      w[0] = fmaf(a.x, xd.x, fmaf(-a.y, xd.y, w[0]));  // T~ x_D
+      w[1] = fmaf(a.x, xd.y, fmaf(a.y, xd.x, w[1]));
+      w[2] = fmaf(a.x, xn.x, fmaf(-a.y, xn.y, w[2]));  // T~ x_N
+      w[3] = fmaf(a.x, xn.y, fmaf(a.y, xn.x, w[3]));
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// unit record: {N of the block, global row of the unit's first row, first
+// input column (dof offset of the block + first column of the piece),
+// len | piece << 12 | rows << 24 (rows <= 31)}; usrc: entry offset of the
+// first row's piece
+template <int NC, int ENT>
+__global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
+    const void* __restrict__ entries, const int4* __restrict__ units, const int64_t* __restrict__ usrc, int n_units,
+    int pmax, const float* __restrict__ x32, int64_t ld32, int c0, float* __restrict__ part,
+    unsigned* __restrict__ err) {
+  using SK = StreamK<NC, ENT>;
+  constexpr int EB = 8 * ENT, Q = 16 / EB, K = SK::K, SH = SK::SH, RB = SK::RB, XB = SK::XB, SB = SK::SB, S = SK::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(S) * SB);
+  uint64_t* empty = full + S;
+  int4* meta = reinterpret_cast<int4*>(empty + S);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kStConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == kStConsumers) {
+    // producer: one lane issues every copy
+    if (lane != 0) return;
+    const unsigned char* ent = static_cast<const unsigned char*>(entries);
+    // unit records are loaded one unit ahead so that their global round trip
+    // overlaps the wait for a free stage
+    int4 nrec = make_int4(0, 0, 0, 0);
+    int64_t nsrc = 0;
+    if (int(blockIdx.x) < n_units) {
+      nrec = units[blockIdx.x];
+      nsrc = usrc[blockIdx.x];
+    }
+    int k = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
+      const int4 rec = nrec;
+      const int64_t src = nsrc;
+      if (u + int(gridDim.x) < n_units) {
+        nrec = units[u + gridDim.x];
+        nsrc = usrc[u + gridDim.x];
+      }
+      const int s = k % S;
+      if (!mbar_wait_bounded(&empty[s], (uint32_t(k / S) & 1u) ^ 1u, kStWaitNs)) {
+        atomicExch(err, 1u);
+        return;
+      }
+      const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0x1f;
+      const int64_t stride = ENT == 1 ? N + (N & 1) : N;
+      const uint32_t rb = uint32_t((len + Q - 1) / Q * Q) * EB;
+      uint32_t total = uint32_t(nrows) * rb;
+      int64_t xa[2 * NC];
+      uint32_t xbytes[2 * NC];
+#pragma unroll
+      for (int q = 0; q < 2 * NC; ++q) {
+        const int64_t a = int64_t(c0 + (q >> 1)) * ld32 + rec.z + (q & 1) * N;
+        xa[q] = a & ~int64_t(1);
+        xbytes[q] = uint32_t((((a + len + 1) & ~int64_t(1)) - xa[q]) * 8);
+        total += xbytes[q];
+      }
+      meta[s] = rec;
+      mbar_arrive_expect_tx(&full[s], total);
+      unsigned char* st = smem + size_t(s) * SB;
+      for (int r = 0; r < nrows; ++r) bulk_g2s(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s]);
+#pragma unroll
+      for (int q = 0; q < 2 * NC; ++q)
+        bulk_g2s(st + kStRows * RB + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
+    }
+    return;
+  }
+
+  // consumers: warp w owns rows 2w and 2w + 1 of every unit; each input
+  // value read from shared memory feeds both rows
+  int k = 0;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
+    const int s = k % S;
+    if (!mbar_wait_bounded(&full[s], uint32_t(k / S) & 1u, kStWaitNs)) {
+      if (lane == 0) atomicExch(err, 1u);
+      return;
+    }
+    const int4 rec = meta[s];
+    const int N = rec.x, len = rec.w & 0xfff, p = (rec.w >> 12) & 0xfff, nrows = (rec.w >> 24) & 0x1f;
+    const unsigned char* st = smem + size_t(s) * SB;
+    const int r0 = 2 * warp;
+    if (r0 < nrows) {
+      const bool two = r0 + 1 < nrows;
+      const float2* xs[2 * NC];
+#pragma unroll
+      for (int q = 0; q < 2 * NC; ++q) {
+        const int64_t a = int64_t(c0 + (q >> 1)) * ld32 + rec.z + (q & 1) * N;
+        xs[q] = reinterpret_cast<const float2*>(st + kStRows * RB + q * XB) + (a & 1);
+      }
+      float v0[K], v1[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) v0[q] = v1[q] = 0.f;
+      const unsigned char* row0 = st + r0 * RB;
+      const unsigned char* row1 = st + (two ? r0 + 1 : r0) * RB;  // a repeat of row 0 is discarded
+#pragma unroll 2
+      for (int e = lane; e < len; e += 32) {
+        st_row_fma<NC, ENT>(v0, row0, xs, e);
+        st_row_fma<NC, ENT>(v1, row1, xs, e);
+      }
+      WarpTransposeSum<K>::run(v0, lane, 16);
+      WarpTransposeSum<K>::run(v1, lane, 16);
+      if ((lane & ((1 << SH) - 1)) == 0) {
+        part[(int64_t(rec.y + r0) * pmax + p) * K + (lane >> SH)] = v0[0];
+        if (two) part[(int64_t(rec.y + r0 + 1) * pmax + p) * K + (lane >> SH)] = v1[0];
+      }
+    }
+    // release the stage: order this warp's shared reads before the next bulk write
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+// one launch of the tiled streaming kernel for right-hand sides c0 .. c0+NC-1
+template <int NC, int ENT>
+void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits& su, const float* x32, int64_t ld32,
+                         int c0, float* part, int kid, cudaStream_t s) {
+  using SK = StreamK<NC, ENT>;
+  MTF_REQUIRE(ld32 % 2 == 0 && (reinterpret_cast<uintptr_t>(x32) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(entries) & 15) == 0,
+              MTF_ERR_ARG, "streamed vectors and operators must be 16-byte aligned with an even column stride");
+  auto kfn = k_stream_tiles<NC, ENT>;
+  MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SK::smem)));
+  MTF_LAUNCH(kid, s, kfn<<<unsigned(sys->mv_grid), (kStConsumers + 1) * 32, SK::smem, s>>>(
+      entries, su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
+}
+
+// pieces of a row of N entries (the combine kernels use the same count)
+template <int ENT>
+__host__ __device__ inline int st_pieces(int N) {
+  return N <= 0 ? 1 : (N + st_piece_len<ENT>() - 1) / st_piece_len<ENT>();
+}
+
+}  // namespace mtf

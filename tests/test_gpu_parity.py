@@ -44,6 +44,13 @@ def _case(cache, name):
         cfg = mi.config_cube2(n=2, k0=3.0, n_dirs=3)
         sk = skeleton_of(cfg["mesh"])
         ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    elif name == "uvodd":
+        # odd block size (N = 567): odd piece lengths and padded rows in the
+        # streaming kernels
+        cfg = dict(mesh=mi.uv_sphere(10, 21), k0=1.5, eps_r=np.array([1.0, 2.5]), mu_r=np.array([1.0, 1.0]),
+                   dirs=np.array([[0.0, 0.0, 1.0]]), pols=np.array([[1.0, 0.0, 0.0]], dtype=np.complex128))
+        sk = skeleton_of(cfg["mesh"])
+        ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
     cache[("gpucase", name)] = (cfg, sk, ref)
     return cfg, sk, ref
 
@@ -186,7 +193,7 @@ def test_mixed_solve_and_farfield_within_1e5_of_oracle(api, oracle_cache, name):
 # FP32 passes: bound 1e-4 against the FP64 oracle operator.  Preconditioned
 # solves converge to the same solution (1e-10 FP64, 1e-5 mixed).
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["sphere", "split"])
+@pytest.mark.parametrize("name", ["sphere", "split", "uvodd"])
 def test_osrc_apply_matches_oracle(api, oracle_cache, name):
     from oracle.osrc import BlockOSRC
     cfg, sk, ref = _case(oracle_cache, name)
@@ -258,7 +265,7 @@ def _rand_c64(rng, shape):
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("name", ["sphere", "split", "cubes"])
+@pytest.mark.parametrize("name", ["sphere", "split", "cubes", "uvodd"])
 @pytest.mark.parametrize("nrhs", [1, 3, 6])
 def test_matvec_f32_matches_oracle(api, oracle_cache, name, nrhs):
     cfg, sk, ref = _case(oracle_cache, name)
@@ -300,7 +307,7 @@ def test_matvec_f32_full_size_sampled_rows(api):
         assert rel(y[:, Ni][:, rows], yN.T) < 1e-5
 
 
-@pytest.mark.parametrize("name", ["sphere", "split"])
+@pytest.mark.parametrize("name", ["sphere", "split", "uvodd"])
 def test_osrc_apply_f32_matches_oracle(api, oracle_cache, name):
     from oracle.osrc import BlockOSRC
     cfg, sk, ref = _case(oracle_cache, name)
