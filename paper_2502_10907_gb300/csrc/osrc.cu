@@ -207,9 +207,7 @@ __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ pa
   const int i = row_blk[row];
   const int N = blk_N[i];
   const int P = st_pieces<1>(N);
-  float tot = 0.f;
-  if (lane < K)
-    for (int p = 0; p < P; ++p) tot += part[(row * pmax + p) * K + lane];
+  const float tot = st_row_total<K>(part + row * pmax * K, P, lane);
   float a[4];
   const int cl = lane < NC ? lane : 0;
 #pragma unroll

@@ -40,19 +40,22 @@ void destroy_gmres32(Gmres32Work* w) { delete w; }
 
 static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
-// h[i*hst + c] += sum_{k in segment} conj(V_i^c[k]) w^c[k].  CTA = one segment
-// of w (seg complex entries, staged in shared memory as float4 pairs) x 32
-// basis vectors (4 per warp, 4 float4 loads in flight per step); grid
-// (segments, ceil(rows/32), c).  V_i^c starts at V + 2 (c ldv + i ldn).
+// h[i*hst + c] += sum_{k in segment} conj(V_i^c[k]) w^c[k].  CTA = one
+// segment of kDotSeg entries of w (staged in shared memory as float4 pairs)
+// x 32 basis vectors (4 per warp); every lane keeps all 16 of its float4
+// loads in flight at once.  Grid (segments, ceil(rows/32), c); V_i^c starts at
+// V + 2 (c ldv + i ldn).
+constexpr int kDotSeg = 256;
+
 __global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
-                                                int64_t ldv, int rows, double* __restrict__ h, int hst, int seg) {
-  extern __shared__ float4 ws4[];
-  constexpr int RW = 4;
+                                                int64_t ldv, int rows, double* __restrict__ h, int hst) {
+  __shared__ float4 ws4[kDotSeg / 2];
+  constexpr int RW = 4, NQ = kDotSeg / 64;  // float4 per lane
   const int c = blockIdx.z;
-  const int64_t k0 = int64_t(blockIdx.x) * seg;
-  const int nq = int((min(ldn, k0 + seg) - k0) >> 1);
+  const int64_t k0 = int64_t(blockIdx.x) * kDotSeg;
+  const int nq = int(min(ldn - k0, int64_t(kDotSeg)) >> 1);
   const float4* wc = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0));
-  for (int t = threadIdx.x; t < nq; t += blockDim.x) ws4[t] = wc[t];
+  if (threadIdx.x < nq) ws4[threadIdx.x] = wc[threadIdx.x];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * (8 * RW) + warp * RW;
@@ -61,17 +64,22 @@ __global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, con
 #pragma unroll
   for (int r = 0; r < RW; ++r)
     v[r] = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(min(i0 + r, rows - 1)) * ldn + k0));
+  float4 a[NQ][RW];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u)
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+      a[u][r] = lane + 32 * u < nq ? v[r][lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
   float ar[RW], ai[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) ar[r] = ai[r] = 0.f;
-#pragma unroll 2
-  for (int t = lane; t < nq; t += 32) {
-    const float4 x = ws4[t];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
+    const float4 x = lane + 32 * u < nq ? ws4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
-      const float4 a = v[r][t];
-      ar[r] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
-      ai[r] += a.x * x.y - a.y * x.x + a.z * x.w - a.w * x.z;
+      ar[r] += a[u][r].x * x.x + a[u][r].y * x.y + a[u][r].z * x.z + a[u][r].w * x.w;
+      ai[r] += a[u][r].x * x.y - a[u][r].y * x.x + a[u][r].z * x.w - a[u][r].w * x.z;
     }
   }
   // FP32 warp sums (32 lane partials), FP64 accumulation over segments
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(256) k_axpy32(const float* __restrict__ V, con
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (q < ldq) {
     const float4* v = reinterpret_cast<const float4*>(V + 2 * int64_t(c) * ldv) + q;
-#pragma unroll 8
+#pragma unroll 16
     for (int i = grp; i < j; i += 8) {
       const float4 a = v[int64_t(i) * ldq];
       const float2 hv = hs[i];
@@ -267,15 +275,8 @@ __global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, 
 
 static void launch_dots32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, double* h, int nrhs,
                           cudaStream_t s) {
-  const int64_t rg = (rows + 31) / 32;
-  // segments of <= 4096 entries (32 KB staged), enough of them for ~2 waves
-  const int64_t minseg = (ldn + 4095) / 4096;
-  const int64_t nseg = std::max<int64_t>(minseg, std::min<int64_t>((ldn + 1023) / 1024, 1200 / (rg * nrhs)));
-  int64_t seg = (ldn + nseg - 1) / nseg;
-  seg = (seg + 63) & ~int64_t(63);
-  const int64_t nsg = (ldn + seg - 1) / seg;
-  dim3 g{unsigned(nsg), unsigned(rg), unsigned(nrhs)};
-  MTF_LAUNCH(KID_DOTS, s, k_dots32<<<g, 256, size_t(seg) * sizeof(float2), s>>>(V, w, ldn, ldv, rows, h, nrhs, int(seg)));
+  dim3 g{nb(ldn, kDotSeg), nb(rows, 32), unsigned(nrhs)};
+  MTF_LAUNCH(KID_DOTS, s, k_dots32<<<g, 256, 0, s>>>(V, w, ldn, ldv, rows, h, nrhs));
 }
 
 // Arnoldi columns enqueued back to back before the host reads their
@@ -357,6 +358,8 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
   bool stop = false;
   for (int j0 = 0; j0 < jend && !stop; j0 += kBatch) {
     const int nbat = std::min(kBatch, jend - j0);
+    // the batch's Hessenberg slots are cleared once and copied back once
+    MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nbat) * slot * sizeof(double), s));
     for (int b = 0; b < nbat; ++b) {
       const int j = j0 + b;
       const float* vj = G.V.p + 2 * size_t(j) * ldn;
@@ -372,15 +375,14 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       double* hB = hA + 2 * size_t(j + 1) * nrhs;
       double* hN = hB + 2 * size_t(j + 1) * nrhs;
       double* ss = hN + 2 * nrhs;
-      MTF_CUDA(cudaMemsetAsync(hA, 0, slot_len(j, nrhs) * sizeof(double), s));
       launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hA, nrhs, s);
       MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hA, j + 1, ldn, ldv, nrhs, G.w.p, nullptr));
       launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hB, nrhs, s);
       MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hB, j + 1, ldn, ldv, nrhs, G.w.p, ss));
       MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, ss, hN, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
-      MTF_CUDA(cudaMemcpyAsync(G.h_host + size_t(b) * slot, hA, slot_len(j, nrhs) * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
     }
+    MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, (size_t(nbat - 1) * slot + slot_len(j0 + nbat - 1, nrhs)) * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
     MTF_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nbat && !stop; ++b) {
       const int j = j0 + b;

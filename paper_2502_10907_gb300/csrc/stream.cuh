@@ -30,6 +30,8 @@
 // and its warps leave.
 #pragma once
 
+#include <atomic>
+
 #include "bulk.h"
 #include "common.h"
 
@@ -234,9 +236,30 @@ void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits&
                   (reinterpret_cast<uintptr_t>(entries) & 15) == 0,
               MTF_ERR_ARG, "streamed vectors and operators must be 16-byte aligned with an even column stride");
   auto kfn = k_stream_tiles<NC, ENT>;
-  MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SK::smem)));
+  // the shared-memory opt-in is set once per device, not on every launch
+  static std::atomic<uint64_t> opted{0};
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(opted.load(std::memory_order_relaxed) & bit)) {
+    MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SK::smem)));
+    opted.fetch_or(bit);
+  }
   MTF_LAUNCH(kid, s, kfn<<<unsigned(sys->mv_grid), (kStConsumers + 1) * 32, SK::smem, s>>>(
       entries, su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
+}
+
+// Sum of the P piece partials of one row (stored contiguously, K per piece)
+// for value index lane % K: every lane loads its share independently and the
+// lanes holding the same value index are combined in a fixed order.
+template <int K>
+__device__ __forceinline__ float st_row_total(const float* __restrict__ prow, int P, int lane) {
+  float acc = 0.f;
+  const int n = P * K;
+  for (int j = lane; j < n; j += 32) acc += prow[j];
+#pragma unroll
+  for (int o = K; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
 }
 
 // pieces of a row of N entries (the combine kernels use the same count)
