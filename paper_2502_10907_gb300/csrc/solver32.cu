@@ -27,8 +27,8 @@ struct Gmres32Work {
   bool pre = false;
   DevBuf<float> V, Z, w;
   // h: kBatch slots, one per Arnoldi column j of a batch; slot layout (complex
-  // entries, index i * nrhs + c): hA (j+1) x nrhs, hB (j+1) x nrhs, ||w|| nrhs,
-  // then nrhs real sums of squares
+  // entries, index i * nrhs + c): t (j+1) x nrhs, s (j+1) x nrhs, coef 2 nrhs
+  // (alpha, h_j), ||w|| nrhs, then nrhs real sums of squares
   DevBuf<double> h, y;
   double* h_host = nullptr;
   ~Gmres32Work() {
@@ -40,22 +40,27 @@ void destroy_gmres32(Gmres32Work* w) { delete w; }
 
 static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
-// h[i*hst + c] += sum_{k in segment} conj(V_i^c[k]) w^c[k].  CTA = one
-// segment of kDotSeg entries of w (staged in shared memory as float4 pairs)
-// x 32 basis vectors (4 per warp); every lane keeps all 16 of its float4
-// loads in flight at once.  Grid (segments, ceil(rows/32), c); V_i^c starts at
-// V + 2 (c ldv + i ldn).
+// Fused reduction of the delayed CGS2 step (one pass over the basis):
+//   t[i*hst + c] += sum_k conj(V_i^c[k]) w^c[k]   and
+//   s[i*hst + c] += sum_k conj(V_i^c[k]) V_jq^c[k]   for i < rows,
+// over one segment of kDotSeg entries of w and of V_jq (both staged in
+// shared memory as float4 pairs) x 32 basis vectors per CTA (4 per warp,
+// every lane's 16 loads in flight at once).  Grid (segments, ceil(rows/32), c);
+// V_i^c starts at V + 2 (c ldv + i ldn).
 constexpr int kDotSeg = 256;
 
-__global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
-                                                int64_t ldv, int rows, double* __restrict__ h, int hst) {
-  __shared__ float4 ws4[kDotSeg / 2];
+__global__ void __launch_bounds__(256) k_dots2_32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
+                                                  int64_t ldv, int rows, int jq, double* __restrict__ t,
+                                                  double* __restrict__ sq, int hst) {
+  __shared__ float4 ws4[kDotSeg / 2], qs4[kDotSeg / 2];
   constexpr int RW = 4, NQ = kDotSeg / 64;  // float4 per lane
   const int c = blockIdx.z;
   const int64_t k0 = int64_t(blockIdx.x) * kDotSeg;
   const int nq = int(min(ldn - k0, int64_t(kDotSeg)) >> 1);
-  const float4* wc = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0));
-  if (threadIdx.x < nq) ws4[threadIdx.x] = wc[threadIdx.x];
+  if (threadIdx.x < nq) {
+    ws4[threadIdx.x] = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0))[threadIdx.x];
+    qs4[threadIdx.x] = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(jq) * ldn + k0))[threadIdx.x];
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * (8 * RW) + warp * RW;
@@ -70,93 +75,209 @@ __global__ void __launch_bounds__(256) k_dots32(const float* __restrict__ V, con
 #pragma unroll
     for (int r = 0; r < RW; ++r)
       a[u][r] = lane + 32 * u < nq ? v[r][lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float ar[RW], ai[RW];
+  float tr[RW], ti[RW], sr[RW], si[RW];
 #pragma unroll
-  for (int r = 0; r < RW; ++r) ar[r] = ai[r] = 0.f;
+  for (int r = 0; r < RW; ++r) tr[r] = ti[r] = sr[r] = si[r] = 0.f;
 #pragma unroll
   for (int u = 0; u < NQ; ++u) {
-    const float4 x = lane + 32 * u < nq ? ws4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool ok = lane + 32 * u < nq;
+    const float4 x = ok ? ws4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 y = ok ? qs4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
-      ar[r] += a[u][r].x * x.x + a[u][r].y * x.y + a[u][r].z * x.z + a[u][r].w * x.w;
-      ai[r] += a[u][r].x * x.y - a[u][r].y * x.x + a[u][r].z * x.w - a[u][r].w * x.z;
+      const float4 e = a[u][r];
+      tr[r] += e.x * x.x + e.y * x.y + e.z * x.z + e.w * x.w;
+      ti[r] += e.x * x.y - e.y * x.x + e.z * x.w - e.w * x.z;
+      sr[r] += e.x * y.x + e.y * y.y + e.z * y.z + e.w * y.w;
+      si[r] += e.x * y.y - e.y * y.x + e.z * y.w - e.w * y.z;
     }
   }
   // FP32 warp sums (32 lane partials), FP64 accumulation over segments
 #pragma unroll
   for (int r = 0; r < RW; ++r) {
-    float sr = ar[r], si = ai[r];
 #pragma unroll
     for (int s2 = 16; s2 > 0; s2 >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, s2);
-      si += __shfl_xor_sync(0xffffffffu, si, s2);
+      tr[r] += __shfl_xor_sync(0xffffffffu, tr[r], s2);
+      ti[r] += __shfl_xor_sync(0xffffffffu, ti[r], s2);
+      sr[r] += __shfl_xor_sync(0xffffffffu, sr[r], s2);
+      si[r] += __shfl_xor_sync(0xffffffffu, si[r], s2);
     }
     if (lane == 0 && i0 + r < rows) {
-      atomicAdd(h + 2 * (int64_t(i0 + r) * hst + c), double(sr));
-      atomicAdd(h + 2 * (int64_t(i0 + r) * hst + c) + 1, double(si));
+      const int64_t o = 2 * (int64_t(i0 + r) * hst + c);
+      atomicAdd(t + o, double(tr[r]));
+      atomicAdd(t + o + 1, double(ti[r]));
+      atomicAdd(sq + o, double(sr[r]));
+      atomicAdd(sq + o + 1, double(si[r]));
     }
   }
 }
 
-// w^c -= sum_{i<j} V_i^c h_i^c (h_i^c at h[i*hst + c], FP64, used as FP32); optionally
-// ss[c] += ||w^c||^2 after the update.  CTA = 64 consecutive entries (a float4
-// pair per lane) x 8 groups of basis vectors (i = grp mod 8), the group sums
-// combined in shared memory; grid (ldn / 64, c).
-__global__ void __launch_bounds__(256) k_axpy32(const float* __restrict__ V, const double* __restrict__ h, int j,
-                                                int64_t ldn, int64_t ldv, int hst, float* __restrict__ w,
-                                                double* __restrict__ ss) {
+// Coefficients of the delayed CGS2 step for column j (j > 0) from
+// s_i = <V_i, q~_j> (i < j), sigma = <q~_j, q~_j> and t_i = <V_i, w>:
+//   alpha = sqrt(sigma - sum |s_i|^2)   (norm of q~_j - sum V_i s_i),
+//   h_j   = (t_j - sum conj(s_i) t_i) / alpha   (= <q_j, w>);
+// for j = 0 the start vector is final: alpha = 1, h_0 = t_0.  A vanishing
+// q~_j (a right-hand side with zero residual, or an exhausted Krylov space)
+// keeps alpha = 1: nothing is divided by zero and the subdiagonal beta alpha
+// reports the breakdown through beta.
+template <class R>
+__device__ __forceinline__ void dcgs_coef(R sigma, R s2, R pr, R pi, R tjr, R tji, bool first, R& alpha, R& hr,
+                                          R& hi) {
+  alpha = R(1);
+  const R d = sigma - s2;
+  if (!first && sigma > R(0) && d > R(1e-12) * sigma) alpha = sqrt(d);
+  hr = (tjr - pr) / alpha;
+  hi = (tji - pi) / alpha;
+}
+
+// Update of the delayed CGS2 step, one pass over V_0 .. V_{j-1}:
+//   q_j = (q~_j - sum_{i<j} V_i s_i) / alpha        (written over V_j = q~_j)
+//   w  <- w - sum_{i<j} V_i t_i - h_j q_j            (in place)
+// and ss[c] += ||w||^2 after the update.  t, s at [i*hst + c] (FP64, used as
+// FP32).  Every CTA forms alpha and h_j itself in FP32 from the staged t, s;
+// CTA 0 of each right-hand side also forms them in FP64 and stores
+// coef[c] = (alpha, 0), coef[nrhs + c] = h_j for the Hessenberg matrix.
+// CTA = 64 consecutive entries (a float4 pair per lane) x 8 groups of basis
+// vectors (i = grp mod 8), the group sums combined in shared memory; grid
+// (ldn / 64, c).
+__global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const double* __restrict__ t,
+                                                  const double* __restrict__ sq, double* __restrict__ coef,
+                                                  int j, int nrhs, int64_t ldn, int64_t ldv, float* __restrict__ w,
+                                                  double* __restrict__ ss) {
   const int c = blockIdx.y;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t q = int64_t(blockIdx.x) * 32 + lane;  // float4 index within a vector
-  __shared__ float4 part[8][32];
-  extern __shared__ float2 hs[];
-  const double2* hc = reinterpret_cast<const double2*>(h) + c;
-  for (int t = threadIdx.x; t < j; t += blockDim.x) {
-    const double2 hv = hc[int64_t(t) * hst];
-    hs[t] = make_float2(float(hv.x), float(hv.y));
+  __shared__ float4 part_t[8][32], part_s[8][32];
+  __shared__ float red[3][8];
+  __shared__ double redd[3][8];
+  __shared__ float cf[3];
+  extern __shared__ float2 hs[];  // t_i at hs[i], s_i at hs[j + i]
+  const bool lead = blockIdx.x == 0;
+  float s2 = 0.f, pr = 0.f, pi = 0.f;
+  double s2d = 0, prd = 0, pid = 0;
+  for (int u = threadIdx.x; u < j; u += blockDim.x) {
+    const int64_t o = 2 * (int64_t(u) * nrhs + c);
+    const double tr = t[o], ti = t[o + 1], sr = sq[o], si = sq[o + 1];
+    const float2 tv = make_float2(float(tr), float(ti)), sv = make_float2(float(sr), float(si));
+    hs[u] = tv;
+    hs[j + u] = sv;
+    s2 += sv.x * sv.x + sv.y * sv.y;
+    pr += sv.x * tv.x + sv.y * tv.y;  // conj(s) t
+    pi += sv.x * tv.y - sv.y * tv.x;
+    if (lead) {
+      s2d += sr * sr + si * si;
+      prd += sr * tr + si * ti;
+      pid += sr * ti - si * tr;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    pi += __shfl_xor_sync(0xffffffffu, pi, o);
+  }
+  if (lane == 0) {
+    red[0][grp] = s2;
+    red[1][grp] = pr;
+    red[2][grp] = pi;
+  }
+  if (lead) {
+    for (int o = 16; o > 0; o >>= 1) {
+      s2d += __shfl_xor_sync(0xffffffffu, s2d, o);
+      prd += __shfl_xor_sync(0xffffffffu, prd, o);
+      pid += __shfl_xor_sync(0xffffffffu, pid, o);
+    }
+    if (lane == 0) {
+      redd[0][grp] = s2d;
+      redd[1][grp] = prd;
+      redd[2][grp] = pid;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f, e = 0.f;
+    for (int g = 0; g < 8; ++g) {
+      a += red[0][g];
+      b += red[1][g];
+      e += red[2][g];
+    }
+    const int64_t oj = 2 * (int64_t(j) * nrhs + c);
+    float alpha, hr, hi;
+    dcgs_coef<float>(float(sq[oj]), a, b, e, float(t[oj]), float(t[oj + 1]), j == 0, alpha, hr, hi);
+    cf[0] = 1.f / alpha;
+    cf[1] = hr;
+    cf[2] = hi;
+    if (lead) {
+      double ad = 0, bd = 0, ed = 0;
+      for (int g = 0; g < 8; ++g) {
+        ad += redd[0][g];
+        bd += redd[1][g];
+        ed += redd[2][g];
+      }
+      double alphad, hrd, hid;
+      dcgs_coef<double>(sq[oj], ad, bd, ed, t[oj], t[oj + 1], j == 0, alphad, hrd, hid);
+      coef[2 * c] = alphad;
+      coef[2 * c + 1] = 0.0;
+      coef[2 * (nrhs + c)] = hrd;
+      coef[2 * (nrhs + c) + 1] = hid;
+    }
   }
   __syncthreads();
   const int64_t ldq = ldn >> 1;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 at = make_float4(0.f, 0.f, 0.f, 0.f), as = at;
+  float4* vb = reinterpret_cast<float4*>(V + 2 * int64_t(c) * ldv) + q;
   if (q < ldq) {
-    const float4* v = reinterpret_cast<const float4*>(V + 2 * int64_t(c) * ldv) + q;
 #pragma unroll 16
     for (int i = grp; i < j; i += 8) {
-      const float4 a = v[int64_t(i) * ldq];
-      const float2 hv = hs[i];
-      acc.x += a.x * hv.x - a.y * hv.y;
-      acc.y += a.x * hv.y + a.y * hv.x;
-      acc.z += a.z * hv.x - a.w * hv.y;
-      acc.w += a.z * hv.y + a.w * hv.x;
+      const float4 a = vb[int64_t(i) * ldq];
+      const float2 hv = hs[i], sv = hs[j + i];
+      at.x += a.x * hv.x - a.y * hv.y;
+      at.y += a.x * hv.y + a.y * hv.x;
+      at.z += a.z * hv.x - a.w * hv.y;
+      at.w += a.z * hv.y + a.w * hv.x;
+      as.x += a.x * sv.x - a.y * sv.y;
+      as.y += a.x * sv.y + a.y * sv.x;
+      as.z += a.z * sv.x - a.w * sv.y;
+      as.w += a.z * sv.y + a.w * sv.x;
     }
   }
-  part[grp][lane] = acc;
+  part_t[grp][lane] = at;
+  part_s[grp][lane] = as;
   __syncthreads();
   if (grp != 0) return;
-  float sq = 0.f;
+  float sqn = 0.f;
   if (q < ldq) {
-    float4 t = part[0][lane];
+    float4 st = part_t[0][lane], ssum = part_s[0][lane];
 #pragma unroll
     for (int g = 1; g < 8; ++g) {
-      const float4 p = part[g][lane];
-      t.x += p.x;
-      t.y += p.y;
-      t.z += p.z;
-      t.w += p.w;
+      const float4 p1 = part_t[g][lane], p2 = part_s[g][lane];
+      st.x += p1.x;
+      st.y += p1.y;
+      st.z += p1.z;
+      st.w += p1.w;
+      ssum.x += p2.x;
+      ssum.y += p2.y;
+      ssum.z += p2.z;
+      ssum.w += p2.w;
     }
+    const float ia = cf[0], hr = cf[1], hi = cf[2];
+    float4* qv = vb + int64_t(j) * ldq;
+    float4 qj = *qv;
+    qj.x = (qj.x - ssum.x) * ia;
+    qj.y = (qj.y - ssum.y) * ia;
+    qj.z = (qj.z - ssum.z) * ia;
+    qj.w = (qj.w - ssum.w) * ia;
+    *qv = qj;
     float4* x = reinterpret_cast<float4*>(w + 2 * int64_t(c) * ldn) + q;
     float4 o = *x;
-    o.x -= t.x;
-    o.y -= t.y;
-    o.z -= t.z;
-    o.w -= t.w;
+    o.x -= st.x + (hr * qj.x - hi * qj.y);
+    o.y -= st.y + (hr * qj.y + hi * qj.x);
+    o.z -= st.z + (hr * qj.z - hi * qj.w);
+    o.w -= st.w + (hr * qj.w + hi * qj.z);
     *x = o;
-    sq = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+    sqn = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
   }
-  if (ss) {
-    for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
-    if (lane == 0) atomicAdd(ss + c, double(sq));
-  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) sqn += __shfl_xor_sync(0xffffffffu, sqn, s2);
+  if (lane == 0) atomicAdd(ss + c, double(sqn));
 }
 
 // out^c = w^c / sqrt(ss[c]) over the padded length (zero if ss is 0);
@@ -217,13 +338,14 @@ __global__ void __launch_bounds__(256) k_start32(const double* __restrict__ r, i
   reinterpret_cast<float2*>(V + 2 * int64_t(c) * ldv)[k] = make_float2(float(a.x * inv), float(a.y * inv));
 }
 
-// x^c += sum_{i<j} Z_i^c y_i^c: FP32 basis, FP64 coefficients and FP64
+// x^c += sum_{i<jc[c]} Z_i^c y_i^c: FP32 basis, FP64 coefficients and FP64
 // accumulation of the group sums into the FP64 iterate (column stride n).
-// Same CTA shape as k_axpy32.
-__global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, const double* __restrict__ y, int j,
-                                                   int64_t ldn, int64_t ldz, int ldy, int64_t n,
-                                                   double* __restrict__ x) {
+// Same CTA shape as k_axpy2_32.
+__global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, const double* __restrict__ y,
+                                                   const int* __restrict__ jc, int64_t ldn, int64_t ldz, int ldy,
+                                                   int64_t n, double* __restrict__ x) {
   const int c = blockIdx.y;
+  const int j = jc[c];  // columns of this right-hand side (others may hold anything)
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t q = int64_t(blockIdx.x) * 32 + lane;
   __shared__ double2 part[8][2][32];
@@ -273,21 +395,36 @@ __global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, 
   }
 }
 
-static void launch_dots32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, double* h, int nrhs,
-                          cudaStream_t s) {
+static void launch_dots2_32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, int jq, double* t,
+                            double* sq, int nrhs, cudaStream_t s) {
   dim3 g{nb(ldn, kDotSeg), nb(rows, 32), unsigned(nrhs)};
-  MTF_LAUNCH(KID_DOTS, s, k_dots32<<<g, 256, 0, s>>>(V, w, ldn, ldv, rows, h, nrhs));
+  MTF_LAUNCH(KID_DOTS, s, k_dots2_32<<<g, 256, 0, s>>>(V, w, ldn, ldv, rows, jq, t, sq, nrhs));
 }
 
 // Arnoldi columns enqueued back to back before the host reads their
-// Hessenberg entries: CGS2 needs no host result, only the stopping test does,
-// so at most kBatch - 1 iterations per cycle are computed beyond the one that
-// meets the tolerance (they are discarded) while kBatch - 1 of every kBatch
-// host round trips disappear.
+// Hessenberg entries: the orthogonalisation needs no host result, only the
+// stopping test does, so at most kBatch iterations per cycle are computed
+// beyond the one that meets the tolerance (they are discarded) while
+// kBatch - 1 of every kBatch host round trips disappear.
+//
+// Orthogonalisation: CGS2 with delayed re-orthogonalisation (the DCGS2
+// variant of low-synchronisation Gram-Schmidt; Swirydowicz, Langou,
+// Ananthan, Yang and Thomas, 2020).  Step j receives q~_j = V_j, once
+// orthogonalised against q_0 .. q_{j-1}, applies the operator to it
+// (z_j = P q~_j, w = M z_j), and in one pass over the basis both finishes
+// q~_j (its second projection, q_j = (q~_j - sum V_i s_i) / alpha) and
+// projects w once against q_0 .. q_j; the result w / ||w|| is q~_{j+1}.  Two
+// passes over the basis per iteration instead of CGS2's four.  Finishing
+// q~_j changes the previous Hessenberg column: with beta = ||w_{j-1}||,
+// H[i, j-1] += beta s_i (i < j) and H[j, j-1] = beta alpha, so column j - 1 is
+// final once step j's reduction is known and the host applies its Givens
+// rotation then; the last column of a cycle keeps its once-projected
+// values.  Since w was computed from q~_j, the solution update uses the
+// vectors actually multiplied (z_j; without a preconditioner a copy of q~_j).
 constexpr int kBatch = 8;
 
 // doubles of the Hessenberg slot of column j
-static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 4) * nrhs; }
+static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 8) * nrhs; }
 
 mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
                           std::vector<int>& iters, bool& reached, cudaStream_t s) {
@@ -301,12 +438,8 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
   if (G.nrhs != nrhs || G.m != m || G.n != n || G.pre != pre) {
     G.V.alloc(size_t(m + 1) * ldn * nrhs * 2);
     MTF_CUDA(cudaMemsetAsync(G.V.p, 0, G.V.n * sizeof(float), s));
-    if (pre) {
-      G.Z.alloc(size_t(m) * ldn * nrhs * 2);
-      MTF_CUDA(cudaMemsetAsync(G.Z.p, 0, G.Z.n * sizeof(float), s));
-    } else {
-      G.Z.release();
-    }
+    G.Z.alloc(size_t(m) * ldn * nrhs * 2);
+    MTF_CUDA(cudaMemsetAsync(G.Z.p, 0, G.Z.n * sizeof(float), s));
     G.w.alloc(size_t(ldn) * nrhs * 2);
     MTF_CUDA(cudaMemsetAsync(G.w.p, 0, G.w.n * sizeof(float), s));
     G.h.alloc(size_t(kBatch) * slot_len(m - 1, nrhs));
@@ -344,64 +477,90 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
   if (!any) return MTF_OK;
 
   mtf_status status = MTF_OK;
-  const size_t hsm = size_t(m + 1) * sizeof(float2);
+  const size_t hsm = size_t(2 * m) * sizeof(float2);
   const size_t ysm = size_t(m + 1) * sizeof(double2);
-  if (hsm > 48 * 1024 || ysm > 40 * 1024) {
-    MTF_REQUIRE(ysm <= 200 * 1024, MTF_ERR_ARG, "restart length too large for the FP32 inner solver");
-    MTF_CUDA(cudaFuncSetAttribute(k_axpy32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hsm)));
+  if (hsm > 40 * 1024 || ysm > 40 * 1024) {
+    MTF_REQUIRE(ysm <= 200 * 1024 && hsm <= 200 * 1024, MTF_ERR_ARG,
+                "restart length too large for the FP32 inner solver");
+    MTF_CUDA(cudaFuncSetAttribute(k_axpy2_32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hsm) + 8192));
     MTF_CUDA(cudaFuncSetAttribute(k_xupdate32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ysm)));
   }
   const dim3 ga{nb(ldn / 2, 32), unsigned(nrhs)};
   const dim3 gs{nb(ldn / 2, 256), unsigned(nrhs)};
   const int jend = std::min(m, std::max(1, max_iter));
+  // provisional (once-projected) column of every right-hand side, finished
+  // when the next step's reduction arrives
+  std::vector<std::vector<double>> rawcol(nrhs);
+  std::vector<double> rawbeta(nrhs, 0.0);
   std::vector<double> hcol;
   bool stop = false;
+  auto finish_column = [&](int c, int jc, const double* sv, double alpha) -> double {
+    // column jc with H[i, jc] += beta s_i (i <= jc) and H[jc+1, jc] = beta alpha
+    hcol.assign(rawcol[c].begin(), rawcol[c].end());
+    const double beta = rawbeta[c];
+    if (sv)
+      for (int i = 0; i <= jc; ++i) {
+        hcol[2 * i] += beta * sv[2 * (size_t(i) * nrhs + c)];
+        hcol[2 * i + 1] += beta * sv[2 * (size_t(i) * nrhs + c) + 1];
+      }
+    ++iters[c];
+    return ha.add_column(c, jc, hcol.data(), beta * alpha);
+  };
   for (int j0 = 0; j0 < jend && !stop; j0 += kBatch) {
     const int nbat = std::min(kBatch, jend - j0);
     // the batch's Hessenberg slots are cleared once and copied back once
     MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nbat) * slot * sizeof(double), s));
     for (int b = 0; b < nbat; ++b) {
       const int j = j0 + b;
-      const float* vj = G.V.p + 2 * size_t(j) * ldn;
+      float* vj = G.V.p + 2 * size_t(j) * ldn;
+      float* zj = G.Z.p + 2 * size_t(j) * ldn;
       if (pre) {
-        float* zj = G.Z.p + 2 * size_t(j) * ldn;
         launch_osrc_apply_f32(sys, vj, ldv, zj, ldz, nrhs, s);
-        launch_matvec_f32(sys, zj, ldz, G.w.p, ldn, nrhs, s);
       } else {
-        launch_matvec_f32(sys, vj, ldv, G.w.p, ldn, nrhs, s);
+        MTF_CUDA(cudaMemcpy2DAsync(zj, size_t(ldz) * 8, vj, size_t(ldv) * 8, size_t(ldn) * 8, size_t(nrhs),
+                                   cudaMemcpyDeviceToDevice, s));
       }
-      // CGS2 with FP64 accumulation of the FP32 partial sums
-      double* hA = G.h.p + size_t(b) * slot;
-      double* hB = hA + 2 * size_t(j + 1) * nrhs;
-      double* hN = hB + 2 * size_t(j + 1) * nrhs;
-      double* ss = hN + 2 * nrhs;
-      launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hA, nrhs, s);
-      MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hA, j + 1, ldn, ldv, nrhs, G.w.p, nullptr));
-      launch_dots32(G.V.p, G.w.p, ldn, ldv, j + 1, hB, nrhs, s);
-      MTF_LAUNCH(KID_AXPY, s, k_axpy32<<<ga, 256, hsm, s>>>(G.V.p, hB, j + 1, ldn, ldv, nrhs, G.w.p, ss));
-      MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, ss, hN, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
+      launch_matvec_f32(sys, zj, ldz, G.w.p, ldn, nrhs, s);
+      // delayed CGS2: one fused reduction, coefficients, one fused update
+      double* T = G.h.p + size_t(b) * slot;
+      double* S = T + 2 * size_t(j + 1) * nrhs;
+      double* C = S + 2 * size_t(j + 1) * nrhs;
+      double* NRM = C + 4 * size_t(nrhs);
+      double* SS = NRM + 2 * size_t(nrhs);
+      launch_dots2_32(G.V.p, G.w.p, ldn, ldv, j + 1, j, T, S, nrhs, s);
+      MTF_LAUNCH(KID_AXPY, s, k_axpy2_32<<<ga, 256, size_t(2 * j) * sizeof(float2), s>>>(
+          G.V.p, T, S, C, j, nrhs, ldn, ldv, G.w.p, SS));
+      MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, SS, NRM, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
     }
     MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, (size_t(nbat - 1) * slot + slot_len(j0 + nbat - 1, nrhs)) * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
     MTF_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nbat && !stop; ++b) {
       const int j = j0 + b;
-      const double* hostA = G.h_host + size_t(b) * slot;
-      const double* hostB = hostA + 2 * size_t(j + 1) * nrhs;
-      const double* hostN = hostB + 2 * size_t(j + 1) * nrhs;
-      hcol.assign(2 * size_t(j + 1), 0.0);
+      const double* T = G.h_host + size_t(b) * slot;
+      const double* S = T + 2 * size_t(j + 1) * nrhs;
+      const double* C = S + 2 * size_t(j + 1) * nrhs;
+      const double* NRM = C + 4 * size_t(nrhs);
       bool all_done = true;
       for (int c = 0; c < nrhs; ++c) {
         if (!active[c]) continue;
-        for (int q = 0; q <= j; ++q) {
-          hcol[2 * q] = hostA[2 * (size_t(q) * nrhs + c)] + hostB[2 * (size_t(q) * nrhs + c)];
-          hcol[2 * q + 1] = hostA[2 * (size_t(q) * nrhs + c) + 1] + hostB[2 * (size_t(q) * nrhs + c) + 1];
+        if (j >= 1) {
+          const double alpha = C[2 * c];
+          const double est = finish_column(c, j - 1, S, alpha);
+          if (!std::isfinite(est)) status = MTF_ERR_NAN;
+          if (est <= tol || rawbeta[c] * alpha == 0.0) active[c] = 0;
         }
-        const double hn = hostN[2 * c];
-        const double est = ha.add_column(c, j, hcol.data(), hn);
-        ++iters[c];
-        if (!std::isfinite(est)) status = MTF_ERR_NAN;
-        if (est <= tol || hn == 0.0) active[c] = 0;
+        if (active[c]) {
+          // provisional column j: t_0 .. t_{j-1}, h_j; subdiagonal ||w||
+          rawcol[c].assign(2 * size_t(j + 1), 0.0);
+          for (int i = 0; i < j; ++i) {
+            rawcol[c][2 * i] = T[2 * (size_t(i) * nrhs + c)];
+            rawcol[c][2 * i + 1] = T[2 * (size_t(i) * nrhs + c) + 1];
+          }
+          rawcol[c][2 * j] = C[2 * (nrhs + c)];
+          rawcol[c][2 * j + 1] = C[2 * (nrhs + c) + 1];
+          rawbeta[c] = NRM[2 * c];
+        }
         all_done = all_done && !active[c];
       }
       if (status != MTF_OK) {
@@ -414,17 +573,40 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       }
     }
   }
+  if (!stop) {
+    // cycle ended on its length: the last columns keep their once-projected values
+    bool all_done = true;
+    for (int c = 0; c < nrhs; ++c) {
+      if (!active[c]) continue;
+      const double est = finish_column(c, jend - 1, nullptr, 1.0);
+      if (!std::isfinite(est)) status = MTF_ERR_NAN;
+      if (est <= tol) active[c] = 0;
+      all_done = all_done && !active[c];
+    }
+    if (all_done) reached = true;
+    if (status != MTF_OK) {
+      check_matvec_stream(sys, s);
+      return status;
+    }
+  }
   check_matvec_stream(sys, s);
-  // x += Z y (flexible) or V y, y = R^{-1} g per right-hand side
+  // x += Z y, y = R^{-1} g per right-hand side
   std::vector<double> yhost(size_t(m + 1) * nrhs * 2);
   const int jmax = ha.solve(yhost);
   for (double v : yhost)
     if (!std::isfinite(v)) return MTF_ERR_NAN;
   if (jmax > 0) {
-    MTF_CUDA(cudaMemcpyAsync(G.y.p, yhost.data(), yhost.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    // y followed by the per-rhs column counts
+    const size_t ny = yhost.size();
+    std::vector<double> ybuf(ny + size_t(nrhs));
+    std::copy(yhost.begin(), yhost.end(), ybuf.begin());
+    int* jcs = reinterpret_cast<int*>(ybuf.data() + ny);
+    for (int c = 0; c < nrhs; ++c) jcs[c] = ha.jc[c];
+    if (G.y.n < ybuf.size()) G.y.alloc(ybuf.size());
+    MTF_CUDA(cudaMemcpyAsync(G.y.p, ybuf.data(), ybuf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     MTF_LAUNCH(KID_AXPY, s, k_xupdate32<<<ga, 256, size_t(jmax) * sizeof(double2), s>>>(
-        pre ? G.Z.p : G.V.p, G.y.p, jmax, ldn, pre ? ldz : ldv, ldh, n, x_dev));
-    MTF_CUDA(cudaStreamSynchronize(s));  // yhost is released on return
+        G.Z.p, G.y.p, reinterpret_cast<const int*>(G.y.p + ny), ldn, ldz, ldh, n, x_dev));
+    MTF_CUDA(cudaStreamSynchronize(s));  // ybuf is released on return
   }
   return status;
 }

@@ -137,6 +137,9 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
     // producer: one lane issues every copy
     if (lane != 0) return;
     const unsigned char* ent = static_cast<const unsigned char*>(entries);
+    // the operator is read once per apply: its lines go first out of L2, so
+    // the reused vectors and the Krylov basis stay resident
+    const uint64_t stream_pol = l2_policy_evict_first();
     // unit records are loaded one unit ahead so that their global round trip
     // overlaps the wait for a free stage
     int4 nrec = make_int4(0, 0, 0, 0);
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
       meta[s] = rec;
       mbar_arrive_expect_tx(&full[s], total);
       unsigned char* st = smem + size_t(s) * SB;
-      for (int r = 0; r < nrows; ++r) bulk_g2s(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s]);
+      for (int r = 0; r < nrows; ++r)
+        bulk_g2s_hint(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s], stream_pol);
 #pragma unroll
       for (int q = 0; q < 2 * NC; ++q)
         bulk_g2s(st + kStRows * RB + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
