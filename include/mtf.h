@@ -83,6 +83,10 @@ typedef struct {
                            FP32 inner solve reached its tolerance (default 4);
                            inner cycles that end on the restart length are
                            restarts and count against max_iter only          */
+  int32_t learned;      /* 1: mtf_solve adds the trained learned correction
+                           to block-OSRC (mixed precision with
+                           MTF_PRECOND_OSRC only; see mtf_learned_init);
+                           default 0                                         */
 } mtf_options;
 
 typedef struct {
@@ -185,6 +189,14 @@ mtf_status mtf_precond_apply(mtf_system sys, const void* r, void* z, int32_t nrh
  * not complete within its time limit (the output is then undefined). */
 mtf_status mtf_matvec_f32(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream);
 
+/* y = M^H v with complex64 vectors (mixed precision): the conjugate
+ * transpose of mtf_matvec_f32, evaluated with T_i and K_i taken as complex
+ * symmetric (their Galerkin forms are; the quadrature's asymmetry, ~1e-5 to
+ * 1e-4 relative, is the approximation) and the real symmetric exchange
+ * matrix.  Used for gradients of the learned correction.  Synchronises
+ * `stream`; MTF_ERR_TIMEOUT as mtf_matvec_f32. */
+mtf_status mtf_matvec_adjoint_f32(mtf_system sys, const void* v, void* y, int32_t nrhs, void* stream);
+
 /* z = A~ r (Eq. 19) with complex64 vectors: the FP32 apply the mixed inner
  * solver runs.  Same operator and requirements as mtf_precond_apply; r, z:
  * device complex64 n_total x nrhs, must not overlap. */
@@ -231,6 +243,115 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
  * otherwise).  Arguments, results and errors are those of mtf_solve. */
 mtf_status mtf_solve_static(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
                             void* x_out, mtf_solve_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned correction of the block-OSRC preconditioner (no counterpart in the
+ * paper).  The preconditioner stays linear: z = P r + C r, P the block-OSRC
+ * operator of Eq. 19 and C a local stencil.  For dof m of block i and its 4
+ * RWG neighbours (the other edges of its two triangles on Gamma_i, ascending
+ * local dof index) -- stencil slots q = 0 (m) .. 4 -- and sources s in
+ * {r, P r}:
+ *   (C r)_D[m] = sum_{q,s} a[q,s,DD] s_D[q] + a[q,s,DN] s_N[q]
+ *   (C r)_N[m] = sum_{q,s} a[q,s,ND] s_D[q] + a[q,s,NN] s_N[q],
+ * 80 reals per dof, the (re, im) of a ordered [q][s][DD, DN, ND, NN].
+ * Parametrisations (mtf_learned_kind):
+ *  - MTF_LEARNED_TABLE: the coefficients are the parameters, float
+ *    80 x n_dofs feature-major (coefficient o of dof row g at [o n_dofs + g]);
+ *  - MTF_LEARNED_NETWORK: a = g(x) per dof, g a network of 10 geometric
+ *    features (k_i l_m, rho_i, 1 for block 0, k_i l of the 4 neighbours,
+ *    k_i^2 (A_1 + A_2) of its triangles, cosine between their normals, 1 for
+ *    a junction edge) -> 64 -> 64 (ReLU) -> 80; parameters augmented
+ *    row-major matrices [W | b] layer after layer (64 x 11, 64 x 65, 80 x 65).
+ * Both start at zero output (plain block-OSRC).  Training minimises the
+ * power loss
+ *   L = mean_z ||E^K z||^2 / ||z||^2,   E = I - M (P + C) / c0,
+ * over complex Rademacher vectors z, c0 the mean Rayleigh quotient
+ * <z, M P z> / <z, z> of the plain preconditioned operator: a stochastic
+ * estimate of sum_i |1 - lambda_i / c0|^(2K) over the eigenvalues of
+ * M (P + C), dominated by the outliers that slow restarted GMRES.  Inside
+ * flexible GMRES the correction changes only the iteration count.  Rows are
+ * the global dof rows, n_dofs = n_total / 2.  All entry points need a system
+ * assembled with MTF_PRECOND_OSRC (training: also MTF_PREC_MIXED); device
+ * arrays must not overlap.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  MTF_LEARNED_TABLE = 0,
+  MTF_LEARNED_NETWORK = 1
+} mtf_learned_kind;
+
+/* Number of float parameters (0 before mtf_learned_init). */
+int64_t mtf_learned_param_count(mtf_system sys);
+
+/* Create the correction: `kind` (mtf_learned_kind); the network's hidden
+ * layers He-uniform from `seed`, every output zero; resets Adam. */
+mtf_status mtf_learned_init(mtf_system sys, int32_t kind, uint64_t seed);
+
+/* Copy the parameters to / from host memory (mtf_learned_param_count floats). */
+mtf_status mtf_learned_get_params(mtf_system sys, float* host_params);
+mtf_status mtf_learned_set_params(mtf_system sys, const float* host_params);
+
+/* Geometric features of every dof: x_out device float 10 x n_dofs,
+ * feature-major.  Synchronises `stream`. */
+mtf_status mtf_learned_features(mtf_system sys, void* x_out, void* stream);
+
+/* Network only: loss sum_q w_q |g(x_q) - t_q|^2 and its gradient; x device
+ * float 10 x rows, t device float 80 x rows (feature-major, leading
+ * dimension rows), w device float rows; grad_out device float (param
+ * count); *loss on host.  Synchronises `stream`. */
+mtf_status mtf_learned_loss_grad(mtf_system sys, const void* x, const void* t, const void* w, int64_t rows,
+                                 void* grad_out, double* loss, void* stream);
+
+/* Power loss of K steps (1..16) on given vectors z (device complex64
+ * n_total x ncols, ncols <= 32) with centre c0 = c0_re + i c0_im, and its
+ * gradient with respect to the parameters (grad_out device float, param
+ * count); *loss on host.  Synchronises `stream`. */
+mtf_status mtf_learned_power_grad(mtf_system sys, const void* z, int32_t ncols, double c0_re, double c0_im,
+                                  int32_t K, void* grad_out, double* loss, void* stream);
+
+/* Adjoint of the stencil: out_r = C_r^H w and out_p = C_P^H w, with C r =
+ * C_r r + C_P (P r); w, out_r, out_p device complex64 n_total x nrhs. */
+mtf_status mtf_learned_stencil_adjoint(mtf_system sys, const void* w, void* out_r, void* out_p, int32_t nrhs,
+                                       void* stream);
+
+/* Adjoint of block-OSRC: z = P^H w (complex64 device n_total x nrhs). */
+mtf_status mtf_precond_adjoint_f32(mtf_system sys, const void* w, void* z, int32_t nrhs, void* stream);
+
+/* Centre c0 of the power loss (real part returned, imaginary part in *im if
+ * not NULL), estimated over 64 random vectors on first use. */
+double mtf_learned_centre(mtf_system sys, double* im);
+
+/* `steps` Adam steps (learning rate lr) of the power loss with K steps on
+ * `batch` (<= 32) fresh random vectors each, drawn from `seed`; the loss of
+ * the first and of the last step on host.  Synchronises `stream`. */
+mtf_status mtf_learned_train(mtf_system sys, int32_t steps, double lr, int32_t batch, int32_t K, uint64_t seed,
+                             double* loss_first, double* loss_last, void* stream);
+
+typedef struct {
+  int32_t plain_iterations;  /* validation solve with plain block-OSRC        */
+  int32_t best_iterations;   /* best validation solve (plain if not improved) */
+  int32_t best_round;        /* round of the kept parameters, 0 = none        */
+  int32_t rounds;            /* training rounds run                           */
+  double loss_first;         /* power loss of the first training step         */
+  double loss_last;          /* power loss of the last training step          */
+  int32_t enabled;           /* 1 if the correction is switched on            */
+} mtf_learned_report;
+
+/* Train in `rounds` rounds of steps_per_round mtf_learned_train steps and,
+ * after each, solve the n_val plane waves (host dirs / pols as in mtf_rhs)
+ * with the correction; keep the parameters of the round with the fewest
+ * iterations and switch the correction on if that beats plain block-OSRC,
+ * else switch it off.  Needs a mixed-precision system.  Synchronises
+ * `stream`. */
+mtf_status mtf_learned_fit(mtf_system sys, int32_t n_val, const double* dirs, const double* pols, int32_t rounds,
+                           int32_t steps_per_round, double lr, int32_t batch, int32_t K, uint64_t seed,
+                           mtf_learned_report* report, void* stream);
+
+/* Switch the correction on (1) or off (0) for later mtf_solve calls of this
+ * system (the assembly option `learned` sets the initial state). */
+mtf_status mtf_learned_enable(mtf_system sys, int32_t on);
+
+/* z = P r + C r for nrhs columns, complex64 device n_total x nrhs. */
+mtf_status mtf_learned_apply(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream);
 
 /* Far field E_inf(xhat) of solutions x (device complex128 n_total x nrhs) at
  * n_obs unit directions obs_dirs (host, n_obs * 3 doubles):

@@ -30,7 +30,7 @@ class mtf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_ss", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("precond", ctypes.c_int32),
                 ("osrc_np", ctypes.c_int32), ("osrc_theta", ctypes.c_double),
-                ("osrc_eps_scale", ctypes.c_double), ("max_refine", ctypes.c_int32)]
+                ("osrc_eps_scale", ctypes.c_double), ("max_refine", ctypes.c_int32), ("learned", ctypes.c_int32)]
 
 
 class mtf_solve_stats(ctypes.Structure):
@@ -56,12 +56,28 @@ _SIGS = {
     "mtf_matvec": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_precond_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_matvec_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "mtf_matvec_adjoint_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_precond_apply_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_rhs": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_farfield": (_i32, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "mtf_system_destroy": (None, [_vp]),
+    "mtf_learned_param_count": (_i64, [_vp]),
+    "mtf_learned_init": (_i32, [_vp, _i32, ctypes.c_uint64]),
+    "mtf_learned_get_params": (_i32, [_vp, _vp]),
+    "mtf_learned_set_params": (_i32, [_vp, _vp]),
+    "mtf_learned_features": (_i32, [_vp, _vp, _vp]),
+    "mtf_learned_loss_grad": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(_dbl), _vp]),
+    "mtf_learned_power_grad": (_i32, [_vp, _vp, _i32, _dbl, _dbl, _i32, _vp, ctypes.POINTER(_dbl), _vp]),
+    "mtf_learned_stencil_adjoint": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "mtf_precond_adjoint_f32": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "mtf_learned_centre": (_dbl, [_vp, ctypes.POINTER(_dbl)]),
+    "mtf_learned_train": (_i32, [_vp, _i32, _dbl, _i32, _i32, ctypes.c_uint64, ctypes.POINTER(_dbl),
+                                 ctypes.POINTER(_dbl), _vp]),
+    "mtf_learned_fit": (_i32, [_vp, _i32, _vp, _vp, _i32, _i32, _dbl, _i32, _i32, ctypes.c_uint64, _vp, _vp]),
+    "mtf_learned_enable": (_i32, [_vp, _i32]),
+    "mtf_learned_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "mtf_status_string": (ctypes.c_char_p, [_i32]),
     "mtf_last_error": (ctypes.c_char_p, []),
 }
@@ -192,6 +208,10 @@ def mtf_matvec_f32(sys_, x, y, nrhs, stream=0):
     _check(load().mtf_matvec_f32(sys_, _ptr(x), _ptr(y), int(nrhs), stream or None))
 
 
+def mtf_matvec_adjoint_f32(sys_, v, y, nrhs, stream=0):
+    _check(load().mtf_matvec_adjoint_f32(sys_, _ptr(v), _ptr(y), int(nrhs), stream or None))
+
+
 def mtf_precond_apply_f32(sys_, r, z, nrhs, stream=0):
     _check(load().mtf_precond_apply_f32(sys_, _ptr(r), _ptr(z), int(nrhs), stream or None))
 
@@ -231,3 +251,90 @@ def mtf_farfield(sys_, x, nrhs, obs_dirs, f_out, stream=0):
 
 def mtf_system_destroy(sys_):
     load().mtf_system_destroy(sys_)
+
+
+# --- learned correction of block-OSRC ---------------------------------------
+LEARNED_KINDS = {"table": 0, "network": 1}
+
+
+class mtf_learned_report(ctypes.Structure):
+    _fields_ = [("plain_iterations", ctypes.c_int32), ("best_iterations", ctypes.c_int32),
+                ("best_round", ctypes.c_int32), ("rounds", ctypes.c_int32), ("loss_first", ctypes.c_double),
+                ("loss_last", ctypes.c_double), ("enabled", ctypes.c_int32)]
+
+
+def mtf_learned_param_count(sys_):
+    return int(load().mtf_learned_param_count(sys_))
+
+
+def mtf_learned_init(sys_, kind="table", seed=0):
+    _check(load().mtf_learned_init(sys_, LEARNED_KINDS[kind], int(seed)))
+
+
+def mtf_learned_get_params(sys_):
+    out = np.zeros(mtf_learned_param_count(sys_), dtype=np.float32)
+    _check(load().mtf_learned_get_params(sys_, _ptr(out)))
+    return out
+
+
+def mtf_learned_set_params(sys_, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != mtf_learned_param_count(sys_):
+        raise ValueError("wrong number of parameters")
+    _check(load().mtf_learned_set_params(sys_, _ptr(p)))
+
+
+def mtf_learned_features(sys_, x_out, stream=0):
+    _check(load().mtf_learned_features(sys_, _ptr(x_out), stream or None))
+
+
+def mtf_learned_loss_grad(sys_, x, t, w, rows, grad_out, stream=0):
+    loss = _dbl()
+    _check(load().mtf_learned_loss_grad(sys_, _ptr(x), _ptr(t), _ptr(w), int(rows), _ptr(grad_out),
+                                        ctypes.byref(loss), stream or None))
+    return loss.value
+
+
+def mtf_learned_power_grad(sys_, z, ncols, c0, K, grad_out, stream=0):
+    loss = _dbl()
+    _check(load().mtf_learned_power_grad(sys_, _ptr(z), int(ncols), float(np.real(c0)), float(np.imag(c0)), int(K),
+                                         _ptr(grad_out), ctypes.byref(loss), stream or None))
+    return loss.value
+
+
+def mtf_learned_stencil_adjoint(sys_, w, out_r, out_p, nrhs, stream=0):
+    _check(load().mtf_learned_stencil_adjoint(sys_, _ptr(w), _ptr(out_r), _ptr(out_p), int(nrhs), stream or None))
+
+
+def mtf_precond_adjoint_f32(sys_, w, z, nrhs, stream=0):
+    _check(load().mtf_precond_adjoint_f32(sys_, _ptr(w), _ptr(z), int(nrhs), stream or None))
+
+
+def mtf_learned_centre(sys_):
+    im = _dbl()
+    re = load().mtf_learned_centre(sys_, ctypes.byref(im))
+    return complex(re, im.value)
+
+
+def mtf_learned_train(sys_, steps, lr, batch, K, seed=0, stream=0):
+    a, b = _dbl(), _dbl()
+    _check(load().mtf_learned_train(sys_, int(steps), float(lr), int(batch), int(K), int(seed), ctypes.byref(a),
+                                    ctypes.byref(b), stream or None))
+    return a.value, b.value
+
+
+def mtf_learned_fit(sys_, dirs, pols, rounds, steps_per_round, lr, batch, K, seed=0, stream=0):
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    p = np.ascontiguousarray(pols, dtype=np.complex128).reshape(len(d), 3)
+    rep = mtf_learned_report()
+    _check(load().mtf_learned_fit(sys_, len(d), _ptr(d), _ptr(p), int(rounds), int(steps_per_round), float(lr),
+                                  int(batch), int(K), int(seed), ctypes.byref(rep), stream or None))
+    return {f: getattr(rep, f) for f, _ in mtf_learned_report._fields_}
+
+
+def mtf_learned_enable(sys_, on):
+    _check(load().mtf_learned_enable(sys_, 1 if on else 0))
+
+
+def mtf_learned_apply(sys_, r, z, nrhs, stream=0):
+    _check(load().mtf_learned_apply(sys_, _ptr(r), _ptr(z), int(nrhs), stream or None))

@@ -69,11 +69,89 @@ class System:
         L.mtf_precond_apply(self.handle, r, z, r.shape[0], _stream())
         return z
 
+    # --- learned correction of block-OSRC (see include/mtf.h) ---------------
+    def learned_init(self, kind="table", seed=0):
+        """kind: "table" (per-dof stencil coefficients) or "network" (geometry network)."""
+        L.mtf_learned_init(self.handle, kind, seed)
+
+    @property
+    def learned_param_count(self):
+        return L.mtf_learned_param_count(self.handle)
+
+    @property
+    def learned_params(self):
+        return L.mtf_learned_get_params(self.handle)
+
+    @learned_params.setter
+    def learned_params(self, p):
+        L.mtf_learned_set_params(self.handle, p)
+
+    def learned_features(self):
+        """Geometric features (10, n_dofs) float32 of every dof."""
+        x = torch.empty((10, self.mesh.n_total // 2), dtype=torch.float32, device="cuda")
+        L.mtf_learned_features(self.handle, x, _stream())
+        return x
+
+    def learned_loss_grad(self, x, t, w):
+        """Network kind: x (10, rows), t (80, rows), w (rows,) float32 -> (loss, grad)."""
+        x, t, w = x.contiguous(), t.contiguous(), w.contiguous()
+        g = torch.empty(self.learned_param_count, dtype=torch.float32, device="cuda")
+        loss = L.mtf_learned_loss_grad(self.handle, x, t, w, x.shape[1], g, _stream())
+        return loss, g
+
+    def learned_power_grad(self, z, c0, K):
+        """z (ncols, n_total) complex64 -> (loss, grad) of the K-step power loss with centre c0."""
+        z = z.contiguous()
+        g = torch.empty(self.learned_param_count, dtype=torch.float32, device="cuda")
+        loss = L.mtf_learned_power_grad(self.handle, z, z.shape[0], c0, K, g, _stream())
+        return loss, g
+
+    def learned_stencil_adjoint(self, w):
+        """w (nrhs, n_total) complex64 -> (C_r^H w, C_P^H w)."""
+        w = w.contiguous()
+        out_r, out_p = torch.empty_like(w), torch.empty_like(w)
+        L.mtf_learned_stencil_adjoint(self.handle, w, out_r, out_p, w.shape[0], _stream())
+        return out_r, out_p
+
+    def precond_adjoint_f32(self, w):
+        """P^H w for complex64 (nrhs, n_total) w (mixed-precision systems)."""
+        w = w.contiguous()
+        z = torch.empty_like(w)
+        L.mtf_precond_adjoint_f32(self.handle, w, z, w.shape[0], _stream())
+        return z
+
+    @property
+    def learned_centre(self):
+        return L.mtf_learned_centre(self.handle)
+
+    def learned_train(self, steps, lr=3e-3, batch=16, K=6, seed=0):
+        return L.mtf_learned_train(self.handle, steps, lr, batch, K, seed, _stream())
+
+    def learned_fit(self, dirs, pols, rounds=4, steps_per_round=150, lr=3e-3, batch=16, K=6, seed=0):
+        """Train with validation on the plane waves (dirs, pols); returns the report as a dict."""
+        return L.mtf_learned_fit(self.handle, dirs, pols, rounds, steps_per_round, lr, batch, K, seed, _stream())
+
+    def learned_enable(self, on=True):
+        L.mtf_learned_enable(self.handle, on)
+
+    def learned_apply(self, r):
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        L.mtf_learned_apply(self.handle, r, z, r.shape[0], _stream())
+        return z
+
     def matvec_f32(self, x):
         """FP32 streaming matvec (mixed-precision systems); x: (nrhs, n_total) complex64."""
         x = x.contiguous()
         y = torch.empty_like(x)
         L.mtf_matvec_f32(self.handle, x, y, x.shape[0], _stream())
+        return y
+
+    def matvec_adjoint_f32(self, v):
+        """M^H v (mixed-precision systems); v: (nrhs, n_total) complex64."""
+        v = v.contiguous()
+        y = torch.empty_like(v)
+        L.mtf_matvec_adjoint_f32(self.handle, v, y, v.shape[0], _stream())
         return y
 
     def precond_f32(self, r):

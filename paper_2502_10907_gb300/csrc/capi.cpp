@@ -229,6 +229,20 @@ mtf_status mtf_matvec_f32(mtf_system sys, const void* x, void* y, int32_t nrhs, 
   });
 }
 
+mtf_status mtf_matvec_adjoint_f32(mtf_system sys, const void* v, void* y, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && v && y, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1, MTF_ERR_ARG, "nrhs must be >= 1");
+    MTF_REQUIRE(v != y, MTF_ERR_ARG, "v and y must not overlap");
+    MTF_REQUIRE(sys->opt.precision == MTF_PREC_MIXED, MTF_ERR_ARG,
+                "the FP32 adjoint matvec needs a system assembled in mixed precision");
+    const int64_t n = sys->mesh->n_total;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_matvec_adj_f32(sys, static_cast<const float*>(v), n, static_cast<float*>(y), n, nrhs, s);
+    check_matvec_stream(sys, s);
+  });
+}
+
 mtf_status mtf_precond_apply_f32(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream) {
   return guarded([&] {
     MTF_REQUIRE(sys && r && z, MTF_ERR_ARG, "null argument");
@@ -284,6 +298,177 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
   return g != MTF_OK ? g : st;
 }
 
+// ---------------------------------------------------------------------------
+// learned correction of block-OSRC
+// ---------------------------------------------------------------------------
+int64_t mtf_learned_param_count(mtf_system sys) { return sys ? learned_param_count(sys) : 0; }
+
+static void require_learned_system(mtf_system sys) {
+  MTF_REQUIRE(sys, MTF_ERR_ARG, "null argument");
+  MTF_REQUIRE(sys->opt.precond == MTF_PRECOND_OSRC, MTF_ERR_ARG,
+              "the learned correction needs a system assembled with MTF_PRECOND_OSRC");
+}
+
+mtf_status mtf_learned_init(mtf_system sys, int32_t kind, uint64_t seed) {
+  return guarded([&] {
+    require_learned_system(sys);
+    learned_init(sys, kind, seed, nullptr);
+  });
+}
+
+mtf_status mtf_learned_get_params(mtf_system sys, float* host_params) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(host_params, MTF_ERR_ARG, "null argument");
+    learned_get_params(sys, host_params, nullptr);
+  });
+}
+
+mtf_status mtf_learned_set_params(mtf_system sys, const float* host_params) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(host_params, MTF_ERR_ARG, "null argument");
+    learned_set_params(sys, host_params, nullptr);
+  });
+}
+
+mtf_status mtf_learned_features(mtf_system sys, void* x_out, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(x_out, MTF_ERR_ARG, "null argument");
+    learned_features(sys, static_cast<float*>(x_out), static_cast<cudaStream_t>(stream));
+    MTF_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  });
+}
+
+mtf_status mtf_learned_loss_grad(mtf_system sys, const void* x, const void* t, const void* w, int64_t rows,
+                                 void* grad_out, double* loss, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(x && t && w && grad_out, MTF_ERR_ARG, "null argument");
+    learned_loss_grad(sys, static_cast<const float*>(x), static_cast<const float*>(t), static_cast<const float*>(w),
+                      rows, static_cast<float*>(grad_out), loss, static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_learned_power_grad(mtf_system sys, const void* z, int32_t ncols, double c0_re, double c0_im, int32_t K,
+                                  void* grad_out, double* loss, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(z && grad_out, MTF_ERR_ARG, "null argument");
+    learned_power_grad(sys, static_cast<const float*>(z), ncols, c0_re, c0_im, K, static_cast<float*>(grad_out), loss,
+                       static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_learned_stencil_adjoint(mtf_system sys, const void* w, void* out_r, void* out_p, int32_t nrhs,
+                                       void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(w && out_r && out_p && nrhs >= 1, MTF_ERR_ARG, "null argument or nrhs < 1");
+    learned_stencil_adjoint(sys, static_cast<const float*>(w), static_cast<float*>(out_r), static_cast<float*>(out_p),
+                            nrhs, static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_precond_adjoint_f32(mtf_system sys, const void* w, void* z, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(w && z && w != z && nrhs >= 1, MTF_ERR_ARG, "null or overlapping argument, or nrhs < 1");
+    MTF_REQUIRE(sys->opt.precision == MTF_PREC_MIXED, MTF_ERR_ARG, "FP32 operators need a mixed-precision system");
+    const int64_t n = sys->mesh->n_total;
+    launch_osrc_apply_adj_f32(sys, static_cast<const float*>(w), n, static_cast<float*>(z), n, nrhs,
+                              static_cast<cudaStream_t>(stream));
+  });
+}
+
+double mtf_learned_centre(mtf_system sys, double* im) {
+  double re = 1.0;
+  if (im) *im = 0.0;
+  guarded([&] {
+    require_learned_system(sys);
+    re = learned_centre(sys, im, nullptr);
+  });
+  return re;
+}
+
+mtf_status mtf_learned_train(mtf_system sys, int32_t steps, double lr, int32_t batch, int32_t K, uint64_t seed,
+                             double* loss_first, double* loss_last, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    learned_train(sys, steps, lr, batch, K, seed, loss_first, loss_last, static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_learned_fit(mtf_system sys, int32_t n_val, const double* dirs, const double* pols, int32_t rounds,
+                           int32_t steps_per_round, double lr, int32_t batch, int32_t K, uint64_t seed,
+                           mtf_learned_report* report, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(sys->learned, MTF_ERR_ARG, "the learned correction has not been initialised");
+    MTF_REQUIRE(n_val >= 1 && dirs && pols && rounds >= 0 && steps_per_round >= 0, MTF_ERR_ARG,
+                "n_val >= 1, rounds >= 0, steps_per_round >= 0 and non-null plane waves");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBuf<double> dd, dp, b, x;
+    upload_waves(dd, dp, n_val, dirs, pols, s);
+    b.alloc(size_t(sys->mesh->n_total) * n_val * 2);
+    x.alloc(b.n);
+    launch_rhs(sys, n_val, dd.p, dp.p, b.p, s);
+    // iterations of a validation solve; a solve that misses the tolerance
+    // counts as no improvement
+    auto validate = [&]() {
+      mtf_solve_stats st{};
+      const mtf_status r = solve(sys, n_val, b.p, x.p, &st, s);
+      MTF_CUDA(cudaStreamSynchronize(s));
+      if (r == MTF_ERR_NOCONV || r == MTF_ERR_NAN || !st.converged) return INT32_MAX;
+      MTF_REQUIRE(r == MTF_OK, r, "validation solve failed");
+      return int(st.iterations);
+    };
+    mtf_learned_report rep{};
+    sys->opt.learned = 0;
+    rep.plain_iterations = validate();
+    rep.best_iterations = rep.plain_iterations;
+    std::vector<float> best(static_cast<size_t>(learned_param_count(sys)));
+    sys->opt.learned = 1;
+    for (int r = 1; r <= rounds; ++r) {
+      double l0 = 0, l1 = 0;
+      learned_train(sys, steps_per_round, lr, batch, K, seed, &l0, &l1, s);
+      if (r == 1) rep.loss_first = l0;
+      rep.loss_last = l1;
+      rep.rounds = r;
+      const int it = validate();
+      if (it < rep.best_iterations) {
+        rep.best_iterations = it;
+        rep.best_round = r;
+        learned_get_params(sys, best.data(), s);
+      }
+    }
+    if (rep.best_round > 0) learned_set_params(sys, best.data(), s);
+    rep.enabled = rep.best_round > 0 ? 1 : 0;
+    sys->opt.learned = rep.enabled;
+    if (report) *report = rep;
+  });
+}
+
+mtf_status mtf_learned_enable(mtf_system sys, int32_t on) {
+  return guarded([&] {
+    require_learned_system(sys);
+    sys->opt.learned = on ? 1 : 0;
+  });
+}
+
+mtf_status mtf_learned_apply(mtf_system sys, const void* r, void* z, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    require_learned_system(sys);
+    MTF_REQUIRE(sys->learned, MTF_ERR_ARG, "the learned correction has not been initialised");
+    MTF_REQUIRE(r && z && r != z && nrhs >= 1, MTF_ERR_ARG, "null or overlapping argument, or nrhs < 1");
+    const int64_t n = sys->mesh->n_total;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_osrc_apply_f32(sys, static_cast<const float*>(r), n, static_cast<float*>(z), n, nrhs, s);
+    learned_apply_inplace(sys, static_cast<const float*>(r), n, static_cast<float*>(z), n, nrhs, s);
+  });
+}
+
 mtf_status mtf_farfield(mtf_system sys, const void* x, int32_t nrhs, const double* obs_dirs, int32_t n_obs,
                         void* f_out, void* stream) {
   return guarded([&] {
@@ -301,6 +486,7 @@ void mtf_system_destroy(mtf_system sys) {
   if (!sys) return;
   destroy_gmres(sys->gw);
   destroy_gmres32(sys->gw32);
+  destroy_learned(sys->learned);
   delete sys;
 }
 

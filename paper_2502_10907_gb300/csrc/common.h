@@ -172,6 +172,7 @@ struct mtf_mesh_s {
 namespace mtf {
 struct GmresWork;
 struct Gmres32Work;
+struct LearnedState;
 }
 
 struct mtf_system_s {
@@ -188,6 +189,8 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_ss_pts[3];           // Sauter-Schwab tables
   // FP32 geometry of the mixed regular-pair kernel (per block-triangle)
   mtf::DevBuf<float> d_x32;                  // FP32 copy of the matvec input (mixed path)
+  mtf::DevBuf<float> d_adj32;                // conjugated input of the adjoint matvec
+  mtf::DevBuf<float> d_os_adj32;             // conjugated input of the adjoint block-OSRC apply
   mtf::DevBuf<float> d_osrc_f, d_osrc_r32;   // OSRC symbol (complex) and apply scratch
   mtf::DevBuf<float> d_osrc_T;               // complex T~ of every block (rows of N_i, at the blocks' mat_off)
   mtf::DevBuf<float> d_os_part;              // per-row piece sums of the OSRC apply
@@ -200,6 +203,8 @@ struct mtf_system_s {
   int32_t mv_grid = 0;
   mtf::GmresWork* gw = nullptr;
   mtf::Gmres32Work* gw32 = nullptr;
+  mtf::LearnedState* learned = nullptr;  // learned OSRC correction (learned.cu)
+  bool learned_active = false;           // used by the current solve (cleared by its fallback)
 };
 
 namespace mtf {
@@ -240,6 +245,15 @@ void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, in
                        cudaStream_t s);
 void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const float* x32, int64_t ld32, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);
+// y = M^H v (FP32), with T and K taken as complex symmetric (their Galerkin
+// forms are; the quadrature's asymmetry is the approximation)
+void launch_matvec_adj_f32(mtf_system sys, const float* v, int64_t ldv, float* y, int64_t ldy, int nrhs,
+                           cudaStream_t s);
+// z = P^H w (FP32), the adjoint of the block-OSRC operator
+void launch_osrc_apply_adj_f32(mtf_system sys, const float* w, int64_t ldw, float* z, int64_t ldz, int nrhs,
+                               cudaStream_t s);
+// out^c = conj(v^c) over n complex entries
+void launch_conj32(const float* v, int64_t ldv, int64_t n, int ncols, float* out, int64_t ldo, cudaStream_t s);
 void check_matvec_stream(mtf_system sys, cudaStream_t s);
 // grid size and error word shared by the streaming kernels
 void stream_prepare(mtf_system sys, cudaStream_t s);
@@ -273,4 +287,22 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
                  cudaStream_t s);
 void destroy_gmres(GmresWork* w);
 void destroy_gmres32(Gmres32Work* w);
+void destroy_learned(LearnedState* l);
+// learned OSRC correction (learned.cu)
+int64_t learned_param_count(mtf_system sys);
+void learned_init(mtf_system sys, int kind, uint64_t seed, cudaStream_t s);
+int learned_kind(mtf_system sys);
+void learned_set_params(mtf_system sys, const float* host, cudaStream_t s);
+void learned_get_params(mtf_system sys, float* host, cudaStream_t s);
+void learned_features(mtf_system sys, float* X, cudaStream_t s);
+void learned_loss_grad(mtf_system sys, const float* X, const float* T, const float* w, int64_t rows, float* grad_out,
+                       double* loss_host, cudaStream_t s);
+void learned_apply_inplace(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
+                           cudaStream_t s);
+void learned_stencil_adjoint(mtf_system sys, const float* w, float* out_r, float* out_p, int nrhs, cudaStream_t s);
+void learned_power_grad(mtf_system sys, const float* Z, int pb, double c0r, double c0i, int K, float* grad_out,
+                        double* loss_host, cudaStream_t s);
+double learned_centre(mtf_system sys, double* im, cudaStream_t s);
+void learned_train(mtf_system sys, int steps, double lr, int batch, int K, uint64_t seed, double* loss_first,
+                   double* loss_last, cudaStream_t s);
 }  // namespace mtf

@@ -76,6 +76,65 @@ __global__ void __launch_bounds__(256) k_mv_combine(
   yc[2 * (N + m) + 1] = yNi;
 }
 
+// Adjoint epilogue (FP32): the streamed partial sums were taken against
+// a = conj(v_D), b = conj(v_N); with T and K complex symmetric (Galerkin
+// forms of symmetric kernels, up to the quadrature's asymmetry) and the
+// exchange matrix X real symmetric,
+//   (M^H v)_D = conj(2 (K a - rho T b)) + X v_D-slots,
+//   (M^H v)_N = conj(2 (T a / rho + K b)) + X v_N-slots.
+template <int NC>
+__global__ void __launch_bounds__(256) k_mv_combine_adj(
+    const float* __restrict__ part, int pmax, const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_N,
+    const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const XEntry* __restrict__ xe,
+    const float* __restrict__ xval32, const float* __restrict__ rho32, const float* __restrict__ v, int64_t ldv,
+    float* __restrict__ y, int64_t ldy, int c0, int64_t n_rows) {
+  constexpr int K = StreamK<NC, 2>::K;
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const int i = row_blk[row];
+  const int N = blk_N[i];
+  const float tot = st_row_total<K>(part + row * pmax * K, st_pieces<2>(N), lane);
+  float a[8];
+  const int cl = lane < NC ? lane : 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = __shfl_sync(0xffffffffu, tot, cl * 8 + q);
+  if (lane >= NC) return;
+  const int64_t m = row - blk_row_off[i];
+  const int64_t off = blk_dof_off[i];
+  const float rr = rho32[4 * i], ri = rho32[4 * i + 1], ir = rho32[4 * i + 2], ii = rho32[4 * i + 3];
+  const int col = c0 + lane;
+  const float* vc = v + 2 * int64_t(col) * ldv;
+  // P_D = K a - rho T b, P_N = T a / rho + K b
+  const float pDr = a[4] - (rr * a[2] - ri * a[3]), pDi = a[5] - (rr * a[3] + ri * a[2]);
+  const float pNr = ir * a[0] - ii * a[1] + a[6], pNi = ir * a[1] + ii * a[0] + a[7];
+  float yDr = 2.f * pDr, yDi = -2.f * pDi, yNr = 2.f * pNr, yNi = -2.f * pNi;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const XEntry X = xe[6 * row + e];
+    const float xv = xval32[6 * row + e];
+    const int Nj = X.ab >> 4;
+    yDr += xv * vc[2 * int64_t(X.col)];
+    yDi += xv * vc[2 * int64_t(X.col) + 1];
+    yNr += xv * vc[2 * (int64_t(X.col) + Nj)];
+    yNi += xv * vc[2 * (int64_t(X.col) + Nj) + 1];
+  }
+  float* yc = y + 2 * (int64_t(col) * ldy + off);
+  yc[2 * m] = yDr;
+  yc[2 * m + 1] = yDi;
+  yc[2 * (N + m)] = yNr;
+  yc[2 * (N + m) + 1] = yNi;
+}
+
+// out^c = conj(v^c) over n complex entries (column strides ldv, ldo)
+__global__ void k_conj32(const float* __restrict__ v, int64_t ldv, int64_t n, float* __restrict__ out, int64_t ldo) {
+  const int c = blockIdx.y;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float2 x = reinterpret_cast<const float2*>(v + 2 * int64_t(c) * ldv)[k];
+  reinterpret_cast<float2*>(out + 2 * int64_t(c) * ldo)[k] = make_float2(x.x, -x.y);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -181,6 +240,37 @@ void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const 
 void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
                        cudaStream_t s) {
   mv_all<float, float>(sys, x, ldx, x, ldx, y, ldy, nrhs, s);
+}
+
+template <int NC>
+static void mv_adj_launch(mtf_system sys, const float* v, int64_t ldv, const float* a32, int64_t lda, float* y,
+                          int64_t ldy, int c0, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  launch_stream_tiles<NC, 2>(sys, sys->d_TK32.p, m->mv_units, a32, lda, c0, sys->d_mv_part.p, KID_MATVEC32, s);
+  MTF_LAUNCH(KID_MVCOMBINE, s, k_mv_combine_adj<NC><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+      sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
+      m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, v, ldv, y, ldy, c0, m->n_rows));
+}
+
+void launch_conj32(const float* v, int64_t ldv, int64_t n, int ncols, float* out, int64_t ldo, cudaStream_t s) {
+  MTF_LAUNCH(KID_MISC, s, k_conj32<<<dim3(unsigned((n + 255) / 256), unsigned(ncols)), 256, 0, s>>>(v, ldv, n, out, ldo));
+}
+
+void launch_matvec_adj_f32(mtf_system sys, const float* v, int64_t ldv, float* y, int64_t ldy, int nrhs,
+                           cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  ensure_mv_scratch(sys, s);
+  const int64_t n = m->n_total;
+  if (sys->d_adj32.n < size_t(2 * n) * nrhs) sys->d_adj32.alloc(size_t(2 * n) * nrhs);
+  MTF_LAUNCH(KID_MISC, s, k_conj32<<<dim3(unsigned((n + 255) / 256), unsigned(nrhs)), 256, 0, s>>>(
+      v, ldv, n, sys->d_adj32.p, n));
+  for (int c0 = 0; c0 < nrhs; c0 += 4) {
+    const int nc = std::min(4, nrhs - c0);
+    if (nc == 1) mv_adj_launch<1>(sys, v, ldv, sys->d_adj32.p, n, y, ldy, c0, s);
+    else if (nc == 2) mv_adj_launch<2>(sys, v, ldv, sys->d_adj32.p, n, y, ldy, c0, s);
+    else if (nc == 3) mv_adj_launch<3>(sys, v, ldv, sys->d_adj32.p, n, y, ldy, c0, s);
+    else mv_adj_launch<4>(sys, v, ldv, sys->d_adj32.p, n, y, ldy, c0, s);
+  }
 }
 
 // Throws MTF_ERR_TIMEOUT if a launch of a streaming kernel (matvec or OSRC

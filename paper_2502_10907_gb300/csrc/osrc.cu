@@ -192,7 +192,10 @@ __global__ void k_interleave(const float* __restrict__ re, const float* __restri
 // z rows of one block row m (one warp per global row): the row's T~ pieces
 // added in order, then z_D = rho^-1 (T~ r_N), z_N = -rho (T~ r_D) per
 // right-hand side (lane c < NC), in the output precision.
-template <int NC, class ZT>
+//
+// ADJ: the input columns were conjugated (w~ = conj(w)); with T~ symmetric,
+// P^H w = conj([-rho T~ w~_N ; rho^-1 T~ w~_D]) is written instead (FP32).
+template <int NC, class ZT, bool ADJ = false>
 __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ part, int pmax,
                                                     const int32_t* __restrict__ row_blk,
                                                     const int32_t* __restrict__ blk_N,
@@ -229,6 +232,13 @@ __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ pa
   const int64_t m = row - blk_row_off[i];
   ZT* zc = z + 2 * (int64_t(c0 + lane) * ldz + blk_dof_off[i]);
   const ZT a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3];  // T~ r_D, T~ r_N
+  if constexpr (ADJ) {
+    zc[2 * m] = -(rr * a2 - ri * a3);
+    zc[2 * m + 1] = rr * a3 + ri * a2;
+    zc[2 * (N + m)] = ir * a0 - ii * a1;
+    zc[2 * (N + m) + 1] = -(ir * a1 + ii * a0);
+    return;
+  }
   zc[2 * m] = ir * a2 - ii * a3;
   zc[2 * m + 1] = ir * a3 + ii * a2;
   zc[2 * (N + m)] = -(rr * a0 - ri * a1);
@@ -434,16 +444,16 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   MTF_CUDA(cudaStreamSynchronize(s));  // scratch and d_pd / d_keps are freed on return
 }
 
-template <int NC, class ZT>
+template <int NC, class ZT, bool ADJ = false>
 static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   launch_stream_tiles<NC, 1>(sys, sys->d_osrc_T.p, m->os_units, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
-  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT, ADJ><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
       sys->d_os_part.p, m->os_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
       sys->d_rho.p, sys->d_rho32.p, z, ldz, c0, m->n_rows));
 }
 
-template <class ZT>
+template <class ZT, bool ADJ = false>
 static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   stream_prepare(sys, s);
@@ -456,10 +466,10 @@ static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, in
   if (sys->d_os_part.n < npart) sys->d_os_part.alloc(npart);
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     const int nc = std::min(4, nrhs - c0);
-    if (nc == 1) os_launch<1>(sys, r32, ldr, z, ldz, c0, s);
-    else if (nc == 2) os_launch<2>(sys, r32, ldr, z, ldz, c0, s);
-    else if (nc == 3) os_launch<3>(sys, r32, ldr, z, ldz, c0, s);
-    else os_launch<4>(sys, r32, ldr, z, ldz, c0, s);
+    if (nc == 1) os_launch<1, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 2) os_launch<2, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 3) os_launch<3, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
+    else os_launch<4, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
   }
 }
 
@@ -476,6 +486,16 @@ void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, 
 void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
                            cudaStream_t s) {
   osrc_stream<float>(sys, r, ldr, z, ldz, nrhs, s);
+}
+
+// w -> P^H w (FP32): the adjoint of the block-OSRC operator, used to
+// back-propagate through preconditioned products
+void launch_osrc_apply_adj_f32(mtf_system sys, const float* w, int64_t ldw, float* z, int64_t ldz, int nrhs,
+                               cudaStream_t s) {
+  const int64_t n = sys->mesh->n_total;
+  if (sys->d_os_adj32.n < size_t(2 * n) * nrhs) sys->d_os_adj32.alloc(size_t(2 * n) * nrhs);
+  launch_conj32(w, ldw, n, nrhs, sys->d_os_adj32.p, n, s);
+  osrc_stream<float, true>(sys, sys->d_os_adj32.p, n, z, ldz, nrhs, s);
 }
 
 }  // namespace mtf

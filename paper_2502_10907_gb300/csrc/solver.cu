@@ -524,6 +524,7 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
   if (!sys->gw) sys->gw = new GmresWork();
   GmresWork& G = *sys->gw;
   const bool mixed = sys->opt.precision != MTF_PREC_FP64;
+  sys->learned_active = false;  // the learned correction runs in the mixed path only
   if (G.nrhs != nrhs || G.m != m || G.n != n) {
     G.V.alloc(size_t(m + 1) * n * nrhs * 2);
     G.w.alloc(size_t(n) * nrhs * 2);
@@ -562,6 +563,10 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
     MTF_CUDA(cudaMemsetAsync(x_dev, 0, vec_bytes, s));
     const int max_ref = std::max(1, sys->opt.max_refine);
     int total = 0;
+    // learned correction: used while it keeps the FP64 residual falling; a
+    // cycle that fails to reduce it by 5% falls back to plain block-OSRC
+    sys->learned_active = sys->opt.learned && sys->learned && sys->opt.precond == MTF_PRECOND_OSRC;
+    double prev_rmax = -1.0;
     for (int it = 0;; ++it) {
       if (it == 0) {
         MTF_CUDA(cudaMemcpyAsync(G.b.p, b_dev, vec_bytes, cudaMemcpyDeviceToDevice, s));
@@ -580,6 +585,8 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       }
       if (status != MTF_OK) break;
       if (rmax <= sys->opt.tol) break;
+      if (sys->learned_active && prev_rmax > 0 && rmax > 0.95 * prev_rmax) sys->learned_active = false;
+      prev_rmax = rmax;
       if (refinements >= max_ref || total >= max_iter) {
         status = MTF_ERR_NOCONV;
         break;

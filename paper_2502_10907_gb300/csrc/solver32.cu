@@ -516,6 +516,7 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       float* zj = G.Z.p + 2 * size_t(j) * ldn;
       if (pre) {
         launch_osrc_apply_f32(sys, vj, ldv, zj, ldz, nrhs, s);
+        if (sys->learned_active) learned_apply_inplace(sys, vj, ldv, zj, ldz, nrhs, s);
       } else {
         MTF_CUDA(cudaMemcpy2DAsync(zj, size_t(ldz) * 8, vj, size_t(ldv) * 8, size_t(ldn) * 8, size_t(nrhs),
                                    cudaMemcpyDeviceToDevice, s));

@@ -37,10 +37,19 @@
 
 namespace mtf {
 
-// tuning (compile-time overridable): bytes of one row piece, shared-memory
-// budget of the stage ring
-#ifndef MTF_ST_PIECE_BYTES
-#define MTF_ST_PIECE_BYTES 4096
+// tuning (compile-time overridable): bytes of one row piece for 16-byte
+// ({T, K}) and 8-byte (T~) entries, shared-memory budget of the stage ring
+#ifndef MTF_ST_PIECE_BYTES2
+#define MTF_ST_PIECE_BYTES2 4096
+#endif
+#ifndef MTF_ST_PIECE_BYTES1
+#define MTF_ST_PIECE_BYTES1 4096
+#endif
+#ifndef MTF_ST_UNROLL2
+#define MTF_ST_UNROLL2 1
+#endif
+#ifndef MTF_ST_UNROLL1
+#define MTF_ST_UNROLL1 8
 #endif
 #ifndef MTF_ST_SMEM_BUDGET
 #define MTF_ST_SMEM_BUDGET (220 * 1024)
@@ -50,11 +59,17 @@ constexpr int kStRows = 2 * kStConsumers;  // rows per unit: two per consumer wa
 constexpr int kStMaxStages = 8;
 constexpr int kStSmemBudget = MTF_ST_SMEM_BUDGET;
 constexpr uint64_t kStWaitNs = 500000000ull;
+// consumer loop unrolling per entry type (measured: the 16-byte entries run
+// fastest unrolled once, the 8-byte ones eight times)
+template <int ENT>
+constexpr int st_unroll() {
+  return ENT == 2 ? MTF_ST_UNROLL2 : MTF_ST_UNROLL1;
+}
 
 // entries per piece (one row's slot in a stage)
 template <int ENT>
 __host__ __device__ constexpr int st_piece_len() {
-  return MTF_ST_PIECE_BYTES / (8 * ENT);
+  return (ENT == 2 ? MTF_ST_PIECE_BYTES2 : MTF_ST_PIECE_BYTES1) / (8 * ENT);
 }
 
 template <int NC, int ENT>
@@ -212,7 +227,7 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
       for (int q = 0; q < K; ++q) v0[q] = v1[q] = 0.f;
       const unsigned char* row0 = st + r0 * RB;
       const unsigned char* row1 = st + (two ? r0 + 1 : r0) * RB;  // a repeat of row 0 is discarded
-#pragma unroll 2
+#pragma unroll st_unroll<ENT>()
       for (int e = lane; e < len; e += 32) {
         st_row_fma<NC, ENT>(v0, row0, xs, e);
         st_row_fma<NC, ENT>(v1, row1, xs, e);
