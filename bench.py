@@ -43,6 +43,13 @@ FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (recipe tabl
 FLOPS_PER_EVAL = 57                                    # moment-form inner loop, see the design doc
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the current streaming kernels (--set full, launches around Arnoldi column
+# 330 of the split-sphere workload, n_total 13,068, 2 right-hand sides); keyed
+# by (kernel, n_total, nrhs), absent for other workloads
+NCU_TRAFFIC = {("matvec32", 13068, 2): 231.80e6, ("osrc_apply", 13068, 2): 117.11e6}
+
+
 def _stream_bytes(name, Ns, n_total, nrhs):
     """Algorithmic bytes of one launch of an operator-apply kernel.
     matvec64: FP64 {T, K} entries (32 B per dense entry) + FP64 x reads and y
@@ -355,7 +362,8 @@ def main():
         byts = _stream_bytes(name, [int(n) for n in mesh.n_dofs], int(mesh.n_total), nrhs)
         ach = byts / per_launch_s / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": src}
+                "frac": ach / hbm, "traffic": NCU_TRAFFIC.get((name, int(mesh.n_total), nrhs)),
+                "algorithmic_bytes": byts, "peak_source": src}
     elif name == "singular64":
         npts = {0: 6, 1: 5, 2: 2}
         evals = sum(int(counts[c]) * npts[c] * sysg.opt.n_ss ** 4 for c in range(3))
