@@ -87,6 +87,12 @@ typedef struct {
                            to block-OSRC (mixed precision with
                            MTF_PRECOND_OSRC only; see mtf_learned_init);
                            default 0                                         */
+  int32_t osrc_half;    /* 1: the FP32 block-OSRC applies (the mixed inner
+                           solver, mtf_precond_apply_f32) stream an FP16 copy
+                           of T~ scaled per block (relative entry error
+                           <= 2^-11 of the block's largest entry; the solution
+                           is unaffected, FGMRES uses the vectors applied);
+                           0: FP32 T~.  Default 1                            */
 } mtf_options;
 
 typedef struct {

@@ -150,6 +150,8 @@ struct mtf_mesh_s {
   // OSRC apply (T~ entries)
   mtf::StreamUnits mv_units, os_units;
   std::vector<int64_t> os_T_off_h;           // first entry of each block's T~ (rows of even stride)
+  std::vector<int64_t> os16_off_h;           // first entry of each block's FP16 T~ (rows padded to 4 entries)
+  mtf::StreamUnits os16_units;               // stream units of the FP16 T~
   // block-OSRC: eigenpairs of (div-div, mass) per block, computed once
   bool osrc_ready = false;
   mtf::DevBuf<float> d_osrc_Vt, d_osrc_lam;              // W^T (per block, padded rows), |xi|^2 per mode
@@ -193,6 +195,8 @@ struct mtf_system_s {
   mtf::DevBuf<float> d_os_adj32;             // conjugated input of the adjoint block-OSRC apply
   mtf::DevBuf<float> d_osrc_f, d_osrc_r32;   // OSRC symbol (complex) and apply scratch
   mtf::DevBuf<float> d_osrc_T;               // complex T~ of every block (rows of N_i, at the blocks' mat_off)
+  mtf::DevBuf<uint32_t> d_osrc_T16;          // FP16 (__half2) copy of T~, scaled per block (osrc_half)
+  mtf::DevBuf<float> d_os_coef16;            // per block: s_i (rho, 1/rho) for the FP16 copy
   mtf::DevBuf<float> d_os_part;              // per-row piece sums of the OSRC apply
   mtf::DevBuf<double> d_cen;
   mtf::DevBuf<float> d_qx, d_qw, d_pv, d_cc;

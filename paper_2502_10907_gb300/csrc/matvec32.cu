@@ -140,8 +140,9 @@ __global__ void k_conj32(const float* __restrict__ v, int64_t ldv, int64_t n, fl
 // ---------------------------------------------------------------------------
 void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, const std::vector<int64_t>& blk_entry_off,
                         const std::vector<int64_t>& row_stride, StreamUnits& su, cudaStream_t s) {
-  MTF_REQUIRE(entry_bytes == 8 || entry_bytes == 16, MTF_ERR_ARG, "stream entries are 8 or 16 bytes");
-  MTF_REQUIRE(rows >= 1 && rows <= 31, MTF_ERR_ARG, "rows per stream unit out of range");
+  MTF_REQUIRE(entry_bytes == 4 || entry_bytes == 8 || entry_bytes == 16, MTF_ERR_ARG,
+              "stream entries are 4, 8 or 16 bytes");
+  MTF_REQUIRE(rows >= 1 && rows <= 64, MTF_ERR_ARG, "rows per stream unit out of range");
   const int q = 16 / entry_bytes;  // entries per 16 bytes
   std::vector<int4> u;
   std::vector<int64_t> src;
@@ -203,7 +204,7 @@ static void ensure_mv_scratch(mtf_system sys, cudaStream_t s) {
       off[i] = m->blk[i].mat_off;
       ld[i] = m->blk[i].N;
     }
-    build_stream_units(m, kStRows, st_piece_len<2>(), 16, off, ld, m->mv_units, s);
+    build_stream_units(m, st_unit_rows<2>(), st_piece_len<2>(), 16, off, ld, m->mv_units, s);
   }
   const size_t npart = size_t(m->n_rows) * m->mv_units.pmax * 32;
   if (sys->d_mv_part.n < npart) sys->d_mv_part.alloc(npart);

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <mutex>
 
 #include "stream.cuh"
@@ -195,7 +196,9 @@ __global__ void k_interleave(const float* __restrict__ re, const float* __restri
 //
 // ADJ: the input columns were conjugated (w~ = conj(w)); with T~ symmetric,
 // P^H w = conj([-rho T~ w~_N ; rho^-1 T~ w~_D]) is written instead (FP32).
-template <int NC, class ZT, bool ADJ = false>
+// ENT: entry type of the streamed T~ (1: FP32, 3: FP16 scaled per block, the
+// scale folded into rho32).
+template <int NC, class ZT, bool ADJ = false, int ENT = 1>
 __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ part, int pmax,
                                                     const int32_t* __restrict__ row_blk,
                                                     const int32_t* __restrict__ blk_N,
@@ -203,13 +206,13 @@ __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ pa
                                                     const int64_t* __restrict__ blk_row_off,
                                                     const double* __restrict__ rho, const float* __restrict__ rho32,
                                                     ZT* __restrict__ z, int64_t ldz, int c0, int64_t n_rows) {
-  constexpr int K = StreamK<NC, 1>::K;
+  constexpr int K = StreamK<NC, ENT>::K;
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n_rows) return;
   const int i = row_blk[row];
   const int N = blk_N[i];
-  const int P = st_pieces<1>(N);
+  const int P = st_pieces<ENT>(N);
   const float tot = st_row_total<K>(part + row * pmax * K, P, lane);
   float a[4];
   const int cl = lane < NC ? lane : 0;
@@ -243,6 +246,30 @@ __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ pa
   zc[2 * m + 1] = ir * a3 + ii * a2;
   zc[2 * (N + m)] = -(rr * a0 - ri * a1);
   zc[2 * (N + m) + 1] = -(rr * a1 + ri * a0);
+}
+
+// mx[i] = max over block i's T~ entries of max(|re|, |im|) (non-negative
+// floats compare as their bit patterns)
+__global__ void k_os_absmax(const float2* __restrict__ T, int64_t n, int blk, unsigned* __restrict__ mx) {
+  float a = 0.f;
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const float2 v = T[k];
+    a = fmaxf(a, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx + blk, __float_as_uint(a));
+}
+
+// FP16 copy of one block of T~: rows of ld16 (multiple of 4) entries,
+// entries scaled by inv, padding zero
+__global__ void k_os_to_half(const float2* __restrict__ T, int N, int ld32, int ld16, float inv,
+                             __half2* __restrict__ out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= int64_t(N) * ld16) return;
+  const int64_t r = k / ld16;
+  const int c = int(k - r * ld16);
+  const float2 v = c < N ? T[r * ld32 + c] : make_float2(0.f, 0.f);
+  out[k] = __floats2half2_rn(v.x * inv, v.y * inv);
 }
 
 __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t n2, int nrhs, float* __restrict__ out) {
@@ -360,6 +387,53 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   m->osrc_ready = true;
 }
 
+// FP16 copy of T~ for the FP32 applies: block i is stored as T~_i / s_i
+// (s_i = largest |re| or |im| of its entries, so every entry lies in
+// [-1, 1] where FP16 keeps 11 significant bits), rows padded to a multiple
+// of 4 entries; the combine's coefficients (rho, 1/rho) carry s_i.
+static void osrc_half_copy(mtf_system sys, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  m->os16_off_h.assign(m->nd, 0);
+  int64_t off = 0;
+  for (int i = 0; i < m->nd; ++i) {
+    m->os16_off_h[i] = off;
+    off += int64_t(m->blk[i].N) * st_row_stride<3>(m->blk[i].N);
+  }
+  sys->d_osrc_T16.alloc(size_t(off));
+  DevBuf<unsigned> mx;
+  mx.alloc(size_t(m->nd));
+  MTF_CUDA(cudaMemsetAsync(mx.p, 0, size_t(m->nd) * sizeof(unsigned), s));
+  for (int i = 0; i < m->nd; ++i) {
+    const int N = m->blk[i].N;
+    const int64_t nn = int64_t(N) * st_row_stride<1>(N);
+    MTF_LAUNCH(KID_MISC, s, k_os_absmax<<<unsigned(std::min<int64_t>(1024, (nn + 255) / 256)), 256, 0, s>>>(
+        reinterpret_cast<const float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i], nn, i, mx.p));
+  }
+  std::vector<unsigned> mh(static_cast<size_t>(m->nd));
+  MTF_CUDA(cudaMemcpyAsync(mh.data(), mx.p, mh.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MTF_CUDA(cudaStreamSynchronize(s));
+  std::vector<float> cf(static_cast<size_t>(4 * m->nd));
+  for (int i = 0; i < m->nd; ++i) {
+    float sc;
+    std::memcpy(&sc, &mh[size_t(i)], sizeof(float));
+    MTF_REQUIRE(std::isfinite(sc), MTF_ERR_NAN, "non-finite block-OSRC entries");
+    if (!(sc > 0.f)) sc = 1.f;
+    const int N = m->blk[i].N;
+    const int ld16 = int(st_row_stride<3>(N));
+    const int64_t nn = int64_t(N) * ld16;
+    MTF_LAUNCH(KID_MISC, s, k_os_to_half<<<unsigned((nn + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i], N, int(st_row_stride<1>(N)), ld16,
+        1.f / sc, reinterpret_cast<__half2*>(sys->d_osrc_T16.p) + m->os16_off_h[i]));
+    const double rr = sys->rho_re[i], ri = sys->rho_im[i], rn = rr * rr + ri * ri;
+    cf[size_t(4 * i)] = float(sc * rr);
+    cf[size_t(4 * i + 1)] = float(sc * ri);
+    cf[size_t(4 * i + 2)] = float(sc * rr / rn);
+    cf[size_t(4 * i + 3)] = float(-sc * ri / rn);
+  }
+  sys->d_os_coef16.upload(cf, s);
+  MTF_CUDA(cudaStreamSynchronize(s));  // mx and the host tables go out of scope
+}
+
 void osrc_setup(mtf_system sys, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   osrc_mesh_setup(m, s);
@@ -441,36 +515,56 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
     MTF_LAUNCH(KID_MISC, s, k_interleave<<<unsigned((nn + 255) / 256), 256, 0, s>>>(
         Cre.p, Cim.p, N, ldt, reinterpret_cast<float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i]));
   }
+  if (sys->opt.osrc_half) osrc_half_copy(sys, s);
   MTF_CUDA(cudaStreamSynchronize(s));  // scratch and d_pd / d_keps are freed on return
 }
 
-template <int NC, class ZT, bool ADJ = false>
+template <int NC, class ZT, bool ADJ = false, int ENT = 1>
 static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  launch_stream_tiles<NC, 1>(sys, sys->d_osrc_T.p, m->os_units, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
-  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT, ADJ><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
-      sys->d_os_part.p, m->os_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
-      sys->d_rho.p, sys->d_rho32.p, z, ldz, c0, m->n_rows));
+  const StreamUnits& su = ENT == 3 ? m->os16_units : m->os_units;
+  const void* ent = ENT == 3 ? static_cast<const void*>(sys->d_osrc_T16.p) : static_cast<const void*>(sys->d_osrc_T.p);
+  const float* cf = ENT == 3 ? sys->d_os_coef16.p : sys->d_rho32.p;
+  launch_stream_tiles<NC, ENT>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
+  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT, ADJ, ENT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+      sys->d_os_part.p, su.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
+      sys->d_rho.p, cf, z, ldz, c0, m->n_rows));
 }
 
-template <class ZT, bool ADJ = false>
-static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
+template <class ZT, bool ADJ, int ENT>
+static void osrc_stream_ent(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs,
+                            cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  stream_prepare(sys, s);
-  if (!m->os_units.ready) {
+  StreamUnits& su = ENT == 3 ? m->os16_units : m->os_units;
+  if (!su.ready) {
     std::vector<int64_t> ld(m->nd);
-    for (int i = 0; i < m->nd; ++i) ld[i] = m->blk[i].N + (m->blk[i].N & 1);
-    build_stream_units(m, kStRows, st_piece_len<1>(), 8, m->os_T_off_h, ld, m->os_units, s);
+    for (int i = 0; i < m->nd; ++i) ld[i] = st_row_stride<ENT>(m->blk[i].N);
+    build_stream_units(m, st_unit_rows<ENT>(), st_piece_len<ENT>(), st_eb<ENT>(), ENT == 3 ? m->os16_off_h : m->os_T_off_h, ld, su,
+                       s);
   }
-  const size_t npart = size_t(m->n_rows) * m->os_units.pmax * 16;
+  const size_t npart = size_t(m->n_rows) * su.pmax * 16;
   if (sys->d_os_part.n < npart) sys->d_os_part.alloc(npart);
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     const int nc = std::min(4, nrhs - c0);
-    if (nc == 1) os_launch<1, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
-    else if (nc == 2) os_launch<2, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
-    else if (nc == 3) os_launch<3, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
-    else os_launch<4, ZT, ADJ>(sys, r32, ldr, z, ldz, c0, s);
+    if (nc == 1) os_launch<1, ZT, ADJ, ENT>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 2) os_launch<2, ZT, ADJ, ENT>(sys, r32, ldr, z, ldz, c0, s);
+    else if (nc == 3) os_launch<3, ZT, ADJ, ENT>(sys, r32, ldr, z, ldz, c0, s);
+    else os_launch<4, ZT, ADJ, ENT>(sys, r32, ldr, z, ldz, c0, s);
   }
+}
+
+// FP32 output follows the system's osrc_half option (FP16 copy of T~);
+// FP64 output always streams the FP32 T~
+template <class ZT, bool ADJ = false>
+static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
+  stream_prepare(sys, s);
+  if constexpr (sizeof(ZT) == 4) {
+    if (sys->opt.osrc_half) {
+      osrc_stream_ent<ZT, ADJ, 3>(sys, r32, ldr, z, ldz, nrhs, s);
+      return;
+    }
+  }
+  osrc_stream_ent<ZT, ADJ, 1>(sys, r32, ldr, z, ldz, nrhs, s);
 }
 
 void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,

@@ -2,21 +2,22 @@
 // matvec (entries {T, K}: two complex FP32 values, ENT = 2) and the
 // block-OSRC apply (entries T~: one complex FP32 value, ENT = 1).
 //
-// A dense block is cut into work units of kStRows consecutive rows x one
-// column piece of at most st_piece_len<ENT>() entries (every row of block i
-// in P_i pieces of near-equal length).  One persistent CTA per SM takes units
-// blockIdx.x, blockIdx.x + gridDim.x, ...  A producer warp fetches, with the
-// TMA engine (cp.async.bulk, one "full" mbarrier per stage), the unit's row
-// pieces and the matching slices of the input vectors (D and N slots of
-// every right-hand side) into a ring of S shared-memory stages; kStConsumers
-// consumer warps, two rows each, read both from shared memory, so the input
-// slice is fetched once per unit instead of once per row, each value of it
-// read from shared memory serves two rows, and no consumer waits on a global
-// load.  Consumers release a stage through an "empty" mbarrier.
+// A dense block is cut into work units of st_unit_rows<ENT>() consecutive
+// rows x one column piece of at most st_piece_len<ENT>() entries (every row
+// of block i in P_i pieces of near-equal length).  One persistent CTA per SM
+// takes units blockIdx.x, blockIdx.x + gridDim.x, ...  A producer warp
+// fetches, with the TMA engine (cp.async.bulk, one "full" mbarrier per
+// stage), the unit's row pieces and the matching slices of the input vectors
+// (D and N slots of every right-hand side) into a ring of S shared-memory
+// stages; st_consumers<ENT>() consumer warps, st_rpw<ENT>() rows each, read both
+// from shared memory, so the input slice is fetched once per unit instead of
+// once per row, each value of it read from shared memory serves every row of
+// the warp, and no consumer waits on a global load.  Consumers release a
+// stage through an "empty" mbarrier.
 //
 // Per row and right-hand side a consumer forms the partial sums
-//   ENT = 2:  T x_D, T x_N, K x_D, K x_N    (8 floats)
-//   ENT = 1:  T~ x_D, T~ x_N                (4 floats)
+//   ENT = 2:      T x_D, T x_N, K x_D, K x_N    (8 floats)
+//   ENT = 1, 3:   T~ x_D, T~ x_N                (4 floats; T~ in FP32 or FP16)
 // reduces them over the warp (recursive halving) and stores them at
 // part[(row * pmax + piece) * K + value]; a per-operator combine kernel adds
 // each row's pieces in fixed order and applies the epilogue.
@@ -32,6 +33,8 @@
 
 #include <atomic>
 
+#include <cuda_fp16.h>
+
 #include "bulk.h"
 #include "common.h"
 
@@ -45,42 +48,93 @@ namespace mtf {
 #ifndef MTF_ST_PIECE_BYTES1
 #define MTF_ST_PIECE_BYTES1 4096
 #endif
+#ifndef MTF_ST_PIECE_BYTES3
+#define MTF_ST_PIECE_BYTES3 3072
+#endif
+// consumer warps and rows per consumer warp for the 8- and 4-byte entry
+// types (the 16-byte {T, K} entries use 8 warps of two rows).  Measured on
+// the split sphere: 8 x 2, 16 x 1 and 8 x 4 run within 4% of each other at
+// these piece sizes; smaller pieces are slower (per-unit costs)
+#ifndef MTF_ST_CONS1
+#define MTF_ST_CONS1 8
+#endif
+#ifndef MTF_ST_RPW1
+#define MTF_ST_RPW1 2
+#endif
 #ifndef MTF_ST_UNROLL2
 #define MTF_ST_UNROLL2 1
 #endif
 #ifndef MTF_ST_UNROLL1
 #define MTF_ST_UNROLL1 8
 #endif
+#ifndef MTF_ST_UNROLL3
+#define MTF_ST_UNROLL3 8
+#endif
 #ifndef MTF_ST_SMEM_BUDGET
 #define MTF_ST_SMEM_BUDGET (220 * 1024)
 #endif
-constexpr int kStConsumers = 8;          // consumer warps per CTA
-constexpr int kStRows = 2 * kStConsumers;  // rows per unit: two per consumer warp
 constexpr int kStMaxStages = 8;
 constexpr int kStSmemBudget = MTF_ST_SMEM_BUDGET;
 constexpr uint64_t kStWaitNs = 500000000ull;
+// Entry types: ENT = 2: {T, K} as two complex FP32 (16 bytes); ENT = 1: one
+// complex FP32 (8 bytes); ENT = 3: one complex FP16 (4 bytes, __half2).
+template <int ENT>
+__host__ __device__ constexpr int st_eb() {
+  return ENT == 2 ? 16 : (ENT == 1 ? 8 : 4);
+}
+// partial sums per right-hand side and row piece: (T, K) x (x_D, x_N) or
+// T x (x_D, x_N), complex
+template <int ENT>
+__host__ __device__ constexpr int st_nv() {
+  return ENT == 2 ? 8 : 4;
+}
+// entries between consecutive rows of an N x N block: 16-byte aligned rows
+template <int ENT>
+__host__ __device__ inline int64_t st_row_stride(int N) {
+  return ENT == 2 ? N : (ENT == 1 ? N + (N & 1) : (N + 3) & ~3);
+}
+
+// consumer warps per CTA, rows per consumer warp and rows per unit
+template <int ENT>
+__host__ __device__ constexpr int st_consumers() {
+  return ENT == 2 ? 8 : MTF_ST_CONS1;
+}
+template <int ENT>
+__host__ __device__ constexpr int st_rpw() {
+  return ENT == 2 ? 2 : MTF_ST_RPW1;
+}
+template <int ENT>
+__host__ __device__ constexpr int st_unit_rows() {
+  return st_consumers<ENT>() * st_rpw<ENT>();
+}
+template <int ENT>
+__host__ __device__ constexpr int st_threads() {
+  return (st_consumers<ENT>() + 1) * 32;
+}
+
 // consumer loop unrolling per entry type (measured: the 16-byte entries run
 // fastest unrolled once, the 8-byte ones eight times)
 template <int ENT>
 constexpr int st_unroll() {
-  return ENT == 2 ? MTF_ST_UNROLL2 : MTF_ST_UNROLL1;
+  return ENT == 2 ? MTF_ST_UNROLL2 : (ENT == 1 ? MTF_ST_UNROLL1 : MTF_ST_UNROLL3);
 }
 
 // entries per piece (one row's slot in a stage)
 template <int ENT>
 __host__ __device__ constexpr int st_piece_len() {
-  return (ENT == 2 ? MTF_ST_PIECE_BYTES2 : MTF_ST_PIECE_BYTES1) / (8 * ENT);
+  return (ENT == 2 ? MTF_ST_PIECE_BYTES2 : (ENT == 1 ? MTF_ST_PIECE_BYTES1 : MTF_ST_PIECE_BYTES3)) / st_eb<ENT>();
 }
 
 template <int NC, int ENT>
 struct StreamK {
-  static constexpr int raw = 4 * ENT * NC;  // partial sums per row piece
+  static constexpr int raw = st_nv<ENT>() * NC;  // partial sums per row piece
   static constexpr int K = raw <= 4 ? 4 : (raw <= 8 ? 8 : (raw <= 16 ? 16 : 32));
   static constexpr int SH = K == 4 ? 3 : (K == 8 ? 2 : (K == 16 ? 1 : 0));  // value index = lane >> SH
   static constexpr int L = st_piece_len<ENT>();
-  static constexpr int RB = L * 8 * ENT;                                       // bytes of a row slot
+  static constexpr int RB = L * st_eb<ENT>();                                  // bytes of a row slot
   static constexpr int XB = (L + 2) * 8;                                       // bytes of an input-slice slot
-  static constexpr int SB = ((kStRows * RB + 2 * NC * XB) + 127) / 128 * 128;  // bytes of a stage
+  static constexpr int ROWS = st_unit_rows<ENT>();
+  static constexpr int SB = ((ROWS * RB + 2 * NC * XB) + 127) / 128 * 128;  // bytes of a stage
   static constexpr int S = (kStSmemBudget / SB) < kStMaxStages ? (kStSmemBudget / SB) : kStMaxStages;
   static constexpr size_t smem = size_t(S) * SB + size_t(S) * (2 * sizeof(uint64_t) + sizeof(int4));
   static_assert(S >= 2, "the stage ring needs at least two stages");
@@ -106,7 +160,9 @@ __device__ __forceinline__ void st_row_fma(float* v, const unsigned char* rowp, 
       w[7] = fmaf(a.z, xn.y, fmaf(a.w, xn.x, w[7]));
     }
   } else {
-    const float2 a = reinterpret_cast<const float2*>(rowp)[e];
+    float2 a;
+    if constexpr (ENT == 1) a = reinterpret_cast<const float2*>(rowp)[e];
+    else a = __half22float2(reinterpret_cast<const __half2*>(rowp)[e]);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const float2 xd = xs[2 * c][e], xn = xs[2 * c + 1][e];
@@ -125,15 +181,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // unit record: {N of the block, global row of the unit's first row, first
 // input column (dof offset of the block + first column of the piece),
-// len | piece << 12 | rows << 24 (rows <= 31)}; usrc: entry offset of the
+// len | piece << 12 | rows << 24 (rows <= 64)}; usrc: entry offset of the
 // first row's piece
 template <int NC, int ENT>
-__global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
+__global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
     const void* __restrict__ entries, const int4* __restrict__ units, const int64_t* __restrict__ usrc, int n_units,
     int pmax, const float* __restrict__ x32, int64_t ld32, int c0, float* __restrict__ part,
     unsigned* __restrict__ err) {
   using SK = StreamK<NC, ENT>;
-  constexpr int EB = 8 * ENT, Q = 16 / EB, K = SK::K, SH = SK::SH, RB = SK::RB, XB = SK::XB, SB = SK::SB, S = SK::S;
+  constexpr int RW = st_rpw<ENT>(), ROWS = SK::ROWS;
+  constexpr int EB = st_eb<ENT>(), Q = 16 / EB, K = SK::K, SH = SK::SH, RB = SK::RB, XB = SK::XB, SB = SK::SB, S = SK::S;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(S) * SB);
   uint64_t* empty = full + S;
@@ -142,13 +199,13 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kStConsumers);
+      mbar_init(&empty[s], st_consumers<ENT>());
     }
     mbar_fence_init();
   }
   __syncthreads();
 
-  if (warp == kStConsumers) {
+  if (warp == st_consumers<ENT>()) {
     // producer: one lane issues every copy
     if (lane != 0) return;
     const unsigned char* ent = static_cast<const unsigned char*>(entries);
@@ -176,8 +233,8 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
         atomicExch(err, 1u);
         return;
       }
-      const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0x1f;
-      const int64_t stride = ENT == 1 ? N + (N & 1) : N;
+      const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0xff;
+      const int64_t stride = st_row_stride<ENT>(N);
       const uint32_t rb = uint32_t((len + Q - 1) / Q * Q) * EB;
       uint32_t total = uint32_t(nrows) * rb;
       int64_t xa[2 * NC];
@@ -196,13 +253,13 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
         bulk_g2s_hint(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s], stream_pol);
 #pragma unroll
       for (int q = 0; q < 2 * NC; ++q)
-        bulk_g2s(st + kStRows * RB + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
+        bulk_g2s(st + ROWS * RB + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
     }
     return;
   }
 
-  // consumers: warp w owns rows 2w and 2w + 1 of every unit; each input
-  // value read from shared memory feeds both rows
+  // consumers: warp w owns rows RW w .. RW w + RW - 1 of every unit; each
+  // input value read from shared memory feeds all of them
   int k = 0;
   for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
     const int s = k % S;
@@ -211,32 +268,35 @@ __global__ void __launch_bounds__((kStConsumers + 1) * 32, 1) k_stream_tiles(
       return;
     }
     const int4 rec = meta[s];
-    const int N = rec.x, len = rec.w & 0xfff, p = (rec.w >> 12) & 0xfff, nrows = (rec.w >> 24) & 0x1f;
+    const int N = rec.x, len = rec.w & 0xfff, p = (rec.w >> 12) & 0xfff, nrows = (rec.w >> 24) & 0xff;
     const unsigned char* st = smem + size_t(s) * SB;
-    const int r0 = 2 * warp;
+    const int r0 = RW * warp;
     if (r0 < nrows) {
-      const bool two = r0 + 1 < nrows;
       const float2* xs[2 * NC];
 #pragma unroll
       for (int q = 0; q < 2 * NC; ++q) {
         const int64_t a = int64_t(c0 + (q >> 1)) * ld32 + rec.z + (q & 1) * N;
-        xs[q] = reinterpret_cast<const float2*>(st + kStRows * RB + q * XB) + (a & 1);
+        xs[q] = reinterpret_cast<const float2*>(st + ROWS * RB + q * XB) + (a & 1);
       }
-      float v0[K], v1[K];
+      float v[RW][K];
+      const unsigned char* rowp[RW];
 #pragma unroll
-      for (int q = 0; q < K; ++q) v0[q] = v1[q] = 0.f;
-      const unsigned char* row0 = st + r0 * RB;
-      const unsigned char* row1 = st + (two ? r0 + 1 : r0) * RB;  // a repeat of row 0 is discarded
+      for (int r = 0; r < RW; ++r) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[r][q] = 0.f;
+        rowp[r] = st + min(r0 + r, nrows - 1) * RB;  // repeats of the unit's last row are discarded
+      }
 #pragma unroll st_unroll<ENT>()
       for (int e = lane; e < len; e += 32) {
-        st_row_fma<NC, ENT>(v0, row0, xs, e);
-        st_row_fma<NC, ENT>(v1, row1, xs, e);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) st_row_fma<NC, ENT>(v[r], rowp[r], xs, e);
       }
-      WarpTransposeSum<K>::run(v0, lane, 16);
-      WarpTransposeSum<K>::run(v1, lane, 16);
+#pragma unroll
+      for (int r = 0; r < RW; ++r) WarpTransposeSum<K>::run(v[r], lane, 16);
       if ((lane & ((1 << SH) - 1)) == 0) {
-        part[(int64_t(rec.y + r0) * pmax + p) * K + (lane >> SH)] = v0[0];
-        if (two) part[(int64_t(rec.y + r0 + 1) * pmax + p) * K + (lane >> SH)] = v1[0];
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+          if (r0 + r < nrows) part[(int64_t(rec.y + r0 + r) * pmax + p) * K + (lane >> SH)] = v[r][0];
       }
     }
     // release the stage: order this warp's shared reads before the next bulk write
@@ -264,7 +324,7 @@ void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits&
     MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SK::smem)));
     opted.fetch_or(bit);
   }
-  MTF_LAUNCH(kid, s, kfn<<<unsigned(sys->mv_grid), (kStConsumers + 1) * 32, SK::smem, s>>>(
+  MTF_LAUNCH(kid, s, kfn<<<unsigned(sys->mv_grid), st_threads<ENT>(), SK::smem, s>>>(
       entries, su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
 }
 

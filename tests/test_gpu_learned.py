@@ -54,7 +54,8 @@ def small(oracle_cache):
 
 def _system(api, cfg, **kw):
     mesh = api.Mesh.from_inputs(cfg["mesh"])
-    opts = dict(precision=1, precond=1, tol=1e-7, restart=200, max_iter=8000, max_refine=8)
+    # FP32 T~ so that the block-OSRC parts match the oracle to FP32 accuracy
+    opts = dict(precision=1, precond=1, tol=1e-7, restart=200, max_iter=8000, max_refine=8, osrc_half=0)
     opts.update(kw)
     return api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **opts)
 
