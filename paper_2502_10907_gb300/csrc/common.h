@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mtf.h"
@@ -231,6 +232,32 @@ const char* kernel_name(int kid);
     MTF_CUDA(cudaGetLastError());             \
     ::mtf::prof_end((kid), (stream));         \
   } while (0)
+
+// Programmatic dependent launch for the chains of short kernels of the
+// inner solver: a kernel launched by launch_pdl may be scheduled before its
+// predecessor on the stream has finished; its first statements must be
+// MTF_PDL_WAIT() (returns once the predecessor grid has completed and its
+// memory is visible, so stream order holds for every access) and
+// MTF_PDL_TRIGGER() (lets the next such kernel be scheduled once all CTAs of
+// this one have started).  Both are no-ops for ordinary launches.
+#define MTF_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define MTF_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  MTF_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 void assemble_into(mtf_system sys, double k0, const double* eps_r, const double* mu_r, cudaStream_t s);
 // kernels launched from the host side (implemented in the .cu files)

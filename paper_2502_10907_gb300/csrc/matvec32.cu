@@ -22,6 +22,8 @@ __global__ void __launch_bounds__(256) k_mv_combine(
     const double* __restrict__ xval, const float* __restrict__ xval32, const double* __restrict__ rho,
     const float* __restrict__ rho32, const XT* __restrict__ x, int64_t ldx, YT* __restrict__ y, int64_t ldy, int c0,
     int64_t n_rows) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   constexpr int K = StreamK<NC, 2>::K;
   using AT = YT;
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -88,6 +90,8 @@ __global__ void __launch_bounds__(256) k_mv_combine_adj(
     const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const XEntry* __restrict__ xe,
     const float* __restrict__ xval32, const float* __restrict__ rho32, const float* __restrict__ v, int64_t ldv,
     float* __restrict__ y, int64_t ldy, int c0, int64_t n_rows) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   constexpr int K = StreamK<NC, 2>::K;
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -215,9 +219,11 @@ static void mv_launch(mtf_system sys, const XT* x, int64_t ldx, const float* x32
                       int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   launch_stream_tiles<NC, 2>(sys, sys->d_TK32.p, m->mv_units, x32, ld32, c0, sys->d_mv_part.p, KID_MATVEC32, s);
-  MTF_LAUNCH(KID_MVCOMBINE, s, k_mv_combine<NC, XT, YT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
-      sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
-      m->d_xent.p, sys->d_xval.p, sys->d_xval32.p, sys->d_rho.p, sys->d_rho32.p, x, ldx, y, ldy, c0, m->n_rows));
+  MTF_LAUNCH(KID_MVCOMBINE, s,
+             launch_pdl(k_mv_combine<NC, XT, YT>, dim3(unsigned((m->n_rows * 32 + 255) / 256)), dim3(256), 0, s,
+                        sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p,
+                        m->d_blk_row_off.p, m->d_xent.p, sys->d_xval.p, sys->d_xval32.p, sys->d_rho.p,
+                        sys->d_rho32.p, x, ldx, y, ldy, c0, m->n_rows));
 }
 
 template <class XT, class YT>

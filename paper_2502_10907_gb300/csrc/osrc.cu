@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(256) k_os_combine(const float* __restrict__ pa
                                                     const int64_t* __restrict__ blk_row_off,
                                                     const double* __restrict__ rho, const float* __restrict__ rho32,
                                                     ZT* __restrict__ z, int64_t ldz, int c0, int64_t n_rows) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   constexpr int K = StreamK<NC, ENT>::K;
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -526,9 +528,10 @@ static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int6
   const void* ent = ENT == 3 ? static_cast<const void*>(sys->d_osrc_T16.p) : static_cast<const void*>(sys->d_osrc_T.p);
   const float* cf = ENT == 3 ? sys->d_os_coef16.p : sys->d_rho32.p;
   launch_stream_tiles<NC, ENT>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
-  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_combine<NC, ZT, ADJ, ENT><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
-      sys->d_os_part.p, su.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
-      sys->d_rho.p, cf, z, ldz, c0, m->n_rows));
+  MTF_LAUNCH(KID_OSCOMBINE, s,
+             launch_pdl(k_os_combine<NC, ZT, ADJ, ENT>, dim3(unsigned((m->n_rows * 32 + 255) / 256)), dim3(256), 0,
+                        s, sys->d_os_part.p, su.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p,
+                        m->d_blk_row_off.p, sys->d_rho.p, cf, z, ldz, c0, m->n_rows));
 }
 
 template <class ZT, bool ADJ, int ENT>

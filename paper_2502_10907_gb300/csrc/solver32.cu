@@ -52,6 +52,8 @@ constexpr int kDotSeg = 256;
 __global__ void __launch_bounds__(256) k_dots2_32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
                                                   int64_t ldv, int rows, int jq, double* __restrict__ t,
                                                   double* __restrict__ sq, int hst) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   __shared__ float4 ws4[kDotSeg / 2], qs4[kDotSeg / 2];
   constexpr int RW = 4, NQ = kDotSeg / 64;  // float4 per lane
   const int c = blockIdx.z;
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
                                                   const double* __restrict__ sq, double* __restrict__ coef,
                                                   int j, int nrhs, int64_t ldn, int64_t ldv, float* __restrict__ w,
                                                   double* __restrict__ ss) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int c = blockIdx.y;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t q = int64_t(blockIdx.x) * 32 + lane;  // float4 index within a vector
@@ -284,6 +288,8 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
 // nrm[c] = (sqrt(ss[c]), 0).  grid (ldn / 512, c), one float4 per thread.
 __global__ void __launch_bounds__(256) k_scale32(const float* __restrict__ w, int64_t ldn, const double* __restrict__ ss,
                                                  double* __restrict__ nrm, float* __restrict__ out, int64_t ldo) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int c = blockIdx.y;
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   __shared__ float sinv;  // one FP64 square root per CTA, not per thread
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, 
 static void launch_dots2_32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, int jq, double* t,
                             double* sq, int nrhs, cudaStream_t s) {
   dim3 g{nb(ldn, kDotSeg), nb(rows, 32), unsigned(nrhs)};
-  MTF_LAUNCH(KID_DOTS, s, k_dots2_32<<<g, 256, 0, s>>>(V, w, ldn, ldv, rows, jq, t, sq, nrhs));
+  MTF_LAUNCH(KID_DOTS, s, launch_pdl(k_dots2_32, g, dim3(256), 0, s, V, w, ldn, ldv, rows, jq, t, sq, nrhs));
 }
 
 // Arnoldi columns enqueued back to back before the host reads their
@@ -529,9 +535,12 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       double* NRM = C + 4 * size_t(nrhs);
       double* SS = NRM + 2 * size_t(nrhs);
       launch_dots2_32(G.V.p, G.w.p, ldn, ldv, j + 1, j, T, S, nrhs, s);
-      MTF_LAUNCH(KID_AXPY, s, k_axpy2_32<<<ga, 256, size_t(2 * j) * sizeof(float2), s>>>(
-          G.V.p, T, S, C, j, nrhs, ldn, ldv, G.w.p, SS));
-      MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, SS, NRM, G.V.p + 2 * size_t(j + 1) * ldn, ldv));
+      MTF_LAUNCH(KID_AXPY, s,
+                 launch_pdl(k_axpy2_32, ga, dim3(256), size_t(2 * j) * sizeof(float2), s, G.V.p, T, S, C, j, nrhs,
+                            ldn, ldv, G.w.p, SS));
+      MTF_LAUNCH(KID_NORM, s,
+                 launch_pdl(k_scale32, gs, dim3(256), 0, s, G.w.p, ldn, SS, NRM, G.V.p + 2 * size_t(j + 1) * ldn,
+                            ldv));
     }
     MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, (size_t(nbat - 1) * slot + slot_len(j0 + nbat - 1, nrhs)) * sizeof(double),
                              cudaMemcpyDeviceToHost, s));

@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
   using SK = StreamK<NC, ENT>;
   constexpr int RW = st_rpw<ENT>(), ROWS = SK::ROWS;
   constexpr int EB = st_eb<ENT>(), Q = 16 / EB, K = SK::K, SH = SK::SH, RB = SK::RB, XB = SK::XB, SB = SK::SB, S = SK::S;
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(S) * SB);
   uint64_t* empty = full + S;
@@ -324,8 +326,9 @@ void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits&
     MTF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SK::smem)));
     opted.fetch_or(bit);
   }
-  MTF_LAUNCH(kid, s, kfn<<<unsigned(sys->mv_grid), st_threads<ENT>(), SK::smem, s>>>(
-      entries, su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
+  MTF_LAUNCH(kid, s,
+             launch_pdl(kfn, dim3(unsigned(sys->mv_grid)), dim3(st_threads<ENT>()), SK::smem, s, entries,
+                        su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
 }
 
 // Sum of the P piece partials of one row (stored contiguously, K per piece)
