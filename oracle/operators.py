@@ -155,6 +155,13 @@ def assemble_block(sk: Skeleton, i: int, k: complex, n_ss: int = 4, chunk: int =
     Regular pairs use the 6x6 tensor rule; singular pairs the Sauter-Schwab
     rules with n_ss Gauss points per coordinate.  ``pairs`` (optional)
     restricts to a dict kind -> (loc_tau, loc_sigma).
+
+    The EFIO and MFIO Galerkin forms are symmetric in test and trial function
+    (G(x, y) = G(y, x); for the MFIO the swap changes the sign of both grad G
+    and the cross product).  An edge- or vertex-adjacent pair is therefore
+    integrated with the lower-indexed triangle as the test triangle, and the
+    pair with the roles swapped takes the transposed local block, so that
+    both orderings of an adjacent pair come from one Sauter-Schwab rule.
     """
     N = sk.N[i]
     Tm = np.zeros((N, N), dtype=np.complex128)
@@ -168,8 +175,12 @@ def assemble_block(sk: Skeleton, i: int, k: complex, n_ss: int = 4, chunk: int =
         npts = 36 if kind == "regular" else len(sauter_schwab(kind, n_ss)[2])
         step = max(1, chunk // npts)
         for s in range(0, len(la), step):
-            a = la[s:s + step]
-            b = lb[s:s + len(a)]
+            a0 = la[s:s + step]
+            b0 = lb[s:s + len(a0)]
+            # adjacent pairs with tau > sigma: integrate (sigma, tau), transpose below
+            flip = (a0 > b0) if kind in ("edge", "vertex") else np.zeros(len(a0), dtype=bool)
+            a = np.where(flip, b0, a0)
+            b = np.where(flip, a0, b0)
             ca, pa = _rwg_data(sk, i, a)
             cb, qb = _rwg_data(sk, i, b)
             if kind == "regular":
@@ -187,8 +198,10 @@ def assemble_block(sk: Skeleton, i: int, k: complex, n_ss: int = 4, chunk: int =
                 area_b = sk.area[sk.tris[i][b]]
                 W = (4.0 * area_a * area_b)[:, None] * w[None, :]
             Tl, Kl = pair_integrals(k, X, Y, W, ca, pa, cb, qb)
-            _scatter(Tm, dof[a], dof[b], Tl)
-            _scatter(Km, dof[a], dof[b], Kl)
+            Tl = np.where(flip[:, None, None], np.swapaxes(Tl, 1, 2), Tl)
+            Kl = np.where(flip[:, None, None], np.swapaxes(Kl, 1, 2), Kl)
+            _scatter(Tm, dof[a0], dof[b0], Tl)
+            _scatter(Km, dof[a0], dof[b0], Kl)
     return Tm, Km
 
 

@@ -340,7 +340,11 @@ __global__ void __launch_bounds__(256) k_singular64(BlockArgs A, const SingPair*
     C2 Tv, Kv;
     local_entry(M, pa, qb, D, A.bt_c[3 * qt + a] * A.bt_c[3 * qs + b], kr, ki, Tv, Kv);
     const int N = A.blk_N[i];
-    add_entry(TK, A.blk_mat_off[i] + int64_t(A.bt_dof[3 * qt + a]) * N + A.bt_dof[3 * qs + b], Tv, Kv);
+    const int64_t ra = A.bt_dof[3 * qt + a], cb = A.bt_dof[3 * qs + b];
+    add_entry(TK, A.blk_mat_off[i] + ra * N + cb, Tv, Kv);
+    // the swapped pair (sigma, tau) of an adjacent pair: the same value at
+    // the transposed position (symmetric Galerkin forms)
+    if (kind != 0) add_entry(TK, A.blk_mat_off[i] + cb * N + ra, Tv, Kv);
   }
 }
 

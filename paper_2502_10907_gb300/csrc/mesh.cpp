@@ -178,6 +178,11 @@ mtf_mesh build_mesh(const double* V, int32_t nv, const int32_t* F, int32_t nt, c
           int shared = 0;
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) shared += ft[a] == fs[b];
+          // T and K are symmetric Galerkin forms: an edge- or vertex-adjacent
+          // pair is integrated once, with the lower-indexed triangle as the
+          // test triangle, and its entries are also added transposed for the
+          // swapped pair (the counts below still count ordered pairs)
+          if (shared < 3 && s < q) continue;
           int kind, pt[3], ps[3];
           if (shared == 3) {
             kind = 0;
@@ -207,7 +212,7 @@ mtf_mesh build_mesh(const double* V, int32_t nv, const int32_t* F, int32_t nt, c
                 if (ft[a] == fs[b]) { sa = a; sb = b; }
             for (int c = 0; c < 3; ++c) { pt[c] = (sa + c) % 3; ps[c] = (sb + c) % 3; }
           }
-          ++cnt[kind];
+          cnt[kind] += kind == 0 ? 1 : 2;
           SingPair sp;
           sp.tau = int32_t(q);
           sp.sig = s;
