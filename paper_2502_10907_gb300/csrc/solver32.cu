@@ -43,9 +43,9 @@ static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); 
 // Fused reduction of the delayed CGS2 step (one pass over the basis):
 //   t[i*hst + c] += sum_k conj(V_i^c[k]) w^c[k]   and
 //   s[i*hst + c] += sum_k conj(V_i^c[k]) V_jq^c[k]   for i < rows,
-// over one segment of kDotSeg entries of w and of V_jq (both staged in
-// shared memory as float4 pairs) x 32 basis vectors per CTA (4 per warp,
-// every lane's 16 loads in flight at once).  Grid (segments, ceil(rows/32), c);
+// over one segment of kDotSeg entries x 32 basis vectors per CTA (4 per
+// warp; every lane loads its 16 basis values and the 8 values of w and q~
+// they multiply at once).  Grid (segments, ceil(rows/32), c);
 // V_i^c starts at V + 2 (c ldv + i ldn).
 constexpr int kDotSeg = 256;
 
@@ -54,37 +54,37 @@ __global__ void __launch_bounds__(256) k_dots2_32(const float* __restrict__ V, c
                                                   double* __restrict__ sq, int hst) {
   MTF_PDL_WAIT();
   MTF_PDL_TRIGGER();
-  __shared__ float4 ws4[kDotSeg / 2], qs4[kDotSeg / 2];
   constexpr int RW = 4, NQ = kDotSeg / 64;  // float4 per lane
   const int c = blockIdx.z;
   const int64_t k0 = int64_t(blockIdx.x) * kDotSeg;
   const int nq = int(min(ldn - k0, int64_t(kDotSeg)) >> 1);
-  if (threadIdx.x < nq) {
-    ws4[threadIdx.x] = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0))[threadIdx.x];
-    qs4[threadIdx.x] = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(jq) * ldn + k0))[threadIdx.x];
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * (8 * RW) + warp * RW;
   if (i0 >= rows) return;
+  // every lane loads the w and q~ values it multiplies itself, together with
+  // its basis values: one memory round trip, no staging barrier
+  const float4* wv = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0));
+  const float4* qv = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(jq) * ldn + k0));
   const float4* v[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r)
     v[r] = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(min(i0 + r, rows - 1)) * ldn + k0));
-  float4 a[NQ][RW];
+  float4 a[NQ][RW], xw[NQ], xq[NQ];
 #pragma unroll
-  for (int u = 0; u < NQ; ++u)
+  for (int u = 0; u < NQ; ++u) {
+    const bool ok = lane + 32 * u < nq;
+    xw[u] = ok ? wv[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xq[u] = ok ? qv[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int r = 0; r < RW; ++r)
-      a[u][r] = lane + 32 * u < nq ? v[r][lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < RW; ++r) a[u][r] = ok ? v[r][lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   float tr[RW], ti[RW], sr[RW], si[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) tr[r] = ti[r] = sr[r] = si[r] = 0.f;
 #pragma unroll
   for (int u = 0; u < NQ; ++u) {
-    const bool ok = lane + 32 * u < nq;
-    const float4 x = ok ? ws4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 y = ok ? qs4[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 x = xw[u];
+    const float4 y = xq[u];
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
       const float4 e = a[u][r];
@@ -157,6 +157,16 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
   __shared__ float cf[3];
   extern __shared__ float2 hs[];  // t_i at hs[i], s_i at hs[j + i]
   const bool lead = blockIdx.x == 0;
+  // the first 8 basis columns of this group are loaded before the
+  // coefficients are formed, so that their latency overlaps the prologue
+  const int64_t ldq = ldn >> 1;
+  float4* vb = reinterpret_cast<float4*>(V + 2 * int64_t(c) * ldv) + q;
+  float4 pre[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int i = grp + 8 * u;
+    pre[u] = (q < ldq && i < j) ? vb[int64_t(i) * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   float s2 = 0.f, pr = 0.f, pi = 0.f;
   double s2d = 0, prd = 0, pid = 0;
   for (int u = threadIdx.x; u < j; u += blockDim.x) {
@@ -226,13 +236,9 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
     }
   }
   __syncthreads();
-  const int64_t ldq = ldn >> 1;
   float4 at = make_float4(0.f, 0.f, 0.f, 0.f), as = at;
-  float4* vb = reinterpret_cast<float4*>(V + 2 * int64_t(c) * ldv) + q;
   if (q < ldq) {
-#pragma unroll 16
-    for (int i = grp; i < j; i += 8) {
-      const float4 a = vb[int64_t(i) * ldq];
+    auto acc = [&](const float4 a, int i) {
       const float2 hv = hs[i], sv = hs[j + i];
       at.x += a.x * hv.x - a.y * hv.y;
       at.y += a.x * hv.y + a.y * hv.x;
@@ -242,7 +248,12 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
       as.y += a.x * sv.y + a.y * sv.x;
       as.z += a.z * sv.x - a.w * sv.y;
       as.w += a.z * sv.y + a.w * sv.x;
-    }
+    };
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (grp + 8 * u < j) acc(pre[u], grp + 8 * u);
+#pragma unroll 16
+    for (int i = grp + 64; i < j; i += 8) acc(vb[int64_t(i) * ldq], i);
   }
   part_t[grp][lane] = at;
   part_s[grp][lane] = as;

@@ -3,10 +3,10 @@
 Parity: features, the network's loss gradient, the stencil, its adjoint, the
 adjoint of block-OSRC and the gradient of the power loss (both
 parametrisations) against the FP64 oracle with dense M and P on the small
-split sphere.  The GPU path computes in FP32 and takes T and K as complex
-symmetric in M^H (the quadrature's asymmetry is ~1e-4 here), hence the
-norm-wise tolerances 1e-5 (stencil), 1e-4 (operators) and 3e-3 (gradients
-through M^H).  Behaviour: an untrained correction is plain block-OSRC
+split sphere.  The GPU path computes in FP32, and its adjoint matvec uses
+that T and K are complex symmetric (both sides assemble them symmetric to
+rounding), hence the norm-wise tolerances 1e-5 (stencil), 1e-4 (operators)
+and 3e-4 (gradients through three adjoint steps).  Behaviour: an untrained correction is plain block-OSRC
 exactly, training lowers the power loss, and a fitted correction is
 measured against plain block-OSRC on plane waves it was not fitted on."""
 import numpy as np
@@ -171,7 +171,7 @@ def test_power_loss_gradient_matches_oracle(api, small, kind):
     else:
         _, acts = Lr.forward(th.astype(np.float64), H, X)
         go = Lr.backward(th.astype(np.float64), H, X, acts, G)
-    assert rel(g.cpu().numpy(), go) < 3e-3
+    assert rel(g.cpu().numpy(), go) < 3e-4, rel(g.cpu().numpy(), go)
 
 
 def test_training_lowers_the_power_loss(api, small):
