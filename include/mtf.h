@@ -197,9 +197,9 @@ mtf_status mtf_matvec_f32(mtf_system sys, const void* x, void* y, int32_t nrhs, 
 
 /* y = M^H v with complex64 vectors (mixed precision): the conjugate
  * transpose of mtf_matvec_f32, evaluated with T_i and K_i taken as complex
- * symmetric (their Galerkin forms are; the quadrature's asymmetry, ~1e-5 to
- * 1e-4 relative, is the approximation) and the real symmetric exchange
- * matrix.  Used for gradients of the learned correction.  Synchronises
+ * symmetric (their Galerkin forms are, and the assembly keeps them so to
+ * rounding: both orderings of a triangle pair come from one rule) and the
+ * real symmetric exchange matrix.  Used for gradients of the learned correction.  Synchronises
  * `stream`; MTF_ERR_TIMEOUT as mtf_matvec_f32. */
 mtf_status mtf_matvec_adjoint_f32(mtf_system sys, const void* v, void* y, int32_t nrhs, void* stream);
 

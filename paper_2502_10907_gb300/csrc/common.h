@@ -277,7 +277,7 @@ void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, in
 void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const float* x32, int64_t ld32, double* y,
                             int64_t ldy, int nrhs, cudaStream_t s);
 // y = M^H v (FP32), with T and K taken as complex symmetric (their Galerkin
-// forms are; the quadrature's asymmetry is the approximation)
+// forms are, and the assembly keeps them so to rounding)
 void launch_matvec_adj_f32(mtf_system sys, const float* v, int64_t ldv, float* y, int64_t ldy, int nrhs,
                            cudaStream_t s);
 // z = P^H w (FP32), the adjoint of the block-OSRC operator

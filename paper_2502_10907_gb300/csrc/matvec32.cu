@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) k_mv_combine(
 
 // Adjoint epilogue (FP32): the streamed partial sums were taken against
 // a = conj(v_D), b = conj(v_N); with T and K complex symmetric (Galerkin
-// forms of symmetric kernels, up to the quadrature's asymmetry) and the
+// forms of symmetric kernels, assembled symmetric to rounding) and the
 // exchange matrix X real symmetric,
 //   (M^H v)_D = conj(2 (K a - rho T b)) + X v_D-slots,
 //   (M^H v)_N = conj(2 (T a / rho + K b)) + X v_N-slots.
