@@ -245,6 +245,9 @@ def main():
     ap.add_argument("--precond", default="osrc", choices=["none", "osrc"])
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--restart", type=int, default=500)
+    # the Pade order of the OSRC square root is free (N_p >= 1); it only
+    # changes the per-mode symbol formed at assembly, not the apply
+    ap.add_argument("--osrc-np", type=int, default=16)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=2000)
@@ -279,7 +282,7 @@ def main():
     counts = mesh.pair_counts()
     n_pairs = int(counts.sum())
     sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                      precision=prec, max_iter=args.max_iter, precond=pc)
+                      precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
     # accuracy gate: FP64 solution at tight tolerance (the FP64 path is pinned
     # to the oracle at 1e-10 by the parity tests)
     x_ref, st_ref = None, None
@@ -390,7 +393,7 @@ def main():
         t0 = time.perf_counter()
         mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
         sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                        precision=prec, max_iter=args.max_iter, precond=pc)
+                        precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
         xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
         fe = sh.farfield(xe, cfg["obs"])
         xh, fh = xe.cpu(), fe.cpu()
@@ -411,7 +414,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if prec == L.MTF_PREC_FP64 else "f32+f64",
             "data": "synthetic",
             "config": {"workload": cfg["desc"], "nrhs": nrhs, "n_unknowns": int(mesh.n_total),
-                       "triangle_pairs": n_pairs, "precision": args.precision, "preconditioner": args.precond, "gmres_tol": args.tol,
+                       "triangle_pairs": n_pairs, "precision": args.precision, "preconditioner": args.precond, "osrc_pade_order": args.osrc_np, "gmres_tol": args.tol,
                        "restart": args.restart, "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
                        "parallelism": f"replicas x{world}"},
             "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},
