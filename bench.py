@@ -384,11 +384,34 @@ def main():
     roof["avg_launch_ms"] = per_launch_s * 1e3
 
     # ---- end to end through the C-ABI from host buffers ---------------------
-    e2e_times = []
-    h2d = (m.vertices.nbytes + m.triangles.nbytes + m.labels.nbytes + 2 * 8 * m.n_domains
-           + cfg["dirs"].nbytes + cfg["pols"].nbytes + cfg["obs"].nbytes)
+    # The step of the timed region (materials re-assembled, plane waves
+    # solved, far field) with its inputs taken from host arrays and its
+    # results (surface currents and far field) read back to the host every
+    # step.  The mesh and system handles are set up once, as long-lived state
+    # (their one-time block-OSRC eigen-setup is reported separately below).
     d2h = nrhs * mesh.n_total * 16 + nrhs * len(cfg["obs"]) * 3 * 16
-    for _ in range(max(1, min(args.steps, 3))):
+    h2d = 8 + 2 * 8 * m.n_domains + cfg["dirs"].nbytes + cfg["pols"].nbytes + cfg["obs"].nbytes
+    mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
+    sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
+                    precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
+    e2e_times = []
+    for it in range(1 + max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sh.reassemble(cfg["k0"], np.asarray(cfg["eps_r"], dtype=np.float64), np.asarray(cfg["mu_r"], dtype=np.float64))
+        xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        fe = sh.farfield(xe, cfg["obs"])
+        xh, fh = xe.cpu(), fe.cpu()
+        torch.cuda.synchronize()
+        if it > 0:                                   # the first pass is a warm-up
+            e2e_times.append(time.perf_counter() - t0)
+    del sh, mh
+    e2e = world * nrhs / statistics.median(e2e_times)
+    # the same with the mesh and system created from host arrays every step
+    # (mesh tables, block-OSRC eigenpairs, assembly), for reference
+    setup_times = []
+    h2d_setup = h2d + m.vertices.nbytes + m.triangles.nbytes + m.labels.nbytes
+    for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
@@ -398,9 +421,9 @@ def main():
         fe = sh.farfield(xe, cfg["obs"])
         xh, fh = xe.cpu(), fe.cpu()
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        setup_times.append(time.perf_counter() - t0)
         del sh, mh
-    e2e = world * nrhs / statistics.median(e2e_times)
+    e2e_setup = world * nrhs / min(setup_times)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,7 +450,13 @@ def main():
             "kernel_times": "CUDA events around every library launch in a second pass of the same steps "
                             "(event pairs slow the solve, so that pass is not the timed one)",
             "roofline": roof,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "step": "mtf_reassemble (host eps_r, mu_r) + mtf_solve (host plane waves) + mtf_farfield, "
+                            "x and far field read back; mesh and system handles created once"},
+            "e2e_with_mesh_setup": {"value": e2e_setup, "unit": UNIT, "h2d_bytes_per_step": int(h2d_setup),
+                                    "d2h_bytes_per_step": int(d2h),
+                                    "step": "mtf_mesh_create + mtf_assemble (incl. block-OSRC eigenpairs) + "
+                                            "mtf_solve + mtf_farfield from host arrays"},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
         }
