@@ -250,6 +250,8 @@ def main():
     ap.add_argument("--osrc-np", type=int, default=16)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the FP64-path and learned-correction lines (rank 0, N=1 only)")
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-accuracy-gate", action="store_true",
                     help="skip the tight-tolerance FP64 reference solve (profiling runs)")
@@ -425,6 +427,50 @@ def main():
         del sh, mh
     e2e_setup = world * nrhs / min(setup_times)
 
+    # ---- the same workload on the plain FP64 path and with the learned ------
+    # correction (rank 0 at N = 1): the comparisons the method is judged by
+    fp64_line, learned_line = None, None
+    if rank == 0 and world == 1 and not args.no_comparisons and prec == L.MTF_PREC_MIXED:
+        s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
+                         max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
+
+        def step64():
+            s64.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+            x6, st6 = s64.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+            return x6, st6, s64.farfield(x6, cfg["obs"])
+
+        step64()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            x6, st6, _f6 = step64()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / 2
+        err64 = (float(((x6 - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None)
+        fp64_line = {"value": nrhs / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                     "gmres_iterations": int(st6.iterations), "converged": bool(st6.converged),
+                     "solution_rel_err_vs_fp64_tight": err64,
+                     "path": "FP64 storage, matvec, Arnoldi; block-OSRC (same tolerance, restart, Pade order)"}
+        del s64
+        # learned correction: fitted on two other plane waves with validation
+        # solves; plain block-OSRC is kept when no round beats it
+        sl = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
+                        precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
+        sl.learned_init("table")
+        d_val = mi.fibonacci_directions(9)[0:2]
+        p_val = mi.orthonormal_polarizations(d_val)[0].astype(np.complex128)
+        t0 = time.perf_counter()
+        rep = sl.learned_fit(d_val, p_val, rounds=4, steps_per_round=150, lr=3e-3, batch=16, K=6, seed=5)
+        t_fit = time.perf_counter() - t0
+        xl, stl = sl.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        errl = float(((xl - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
+        learned_line = {"fit": rep, "fit_seconds": t_fit, "enabled": bool(rep["enabled"]),
+                        "gmres_iterations": int(stl.iterations), "solution_rel_err_vs_fp64": errl,
+                        "note": "table-parametrised stencil, power loss K = 6, validation on 2 other plane waves"}
+        del sl
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(cfg, int(statistics.median(iters)))
@@ -458,6 +504,8 @@ def main():
                                     "step": "mtf_mesh_create + mtf_assemble (incl. block-OSRC eigenpairs) + "
                                             "mtf_solve + mtf_farfield from host arrays"},
             "cpu_baseline": cpu,
+            "fp64_block_osrc": fp64_line,
+            "learned_correction": learned_line,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -93,6 +93,12 @@ typedef struct {
                            <= 2^-11 of the block's largest entry; the solution
                            is unaffected, FGMRES uses the vectors applied);
                            0: FP32 T~.  Default 1                            */
+  int32_t recycle;      /* 1: in the mixed path the second inner FGMRES cycle
+                           of a solve reuses the first cycle's Krylov space
+                           (GCRO-style: the new residual is projected out of
+                           it and new basis vectors are orthogonalised
+                           against it) instead of restarting from scratch;
+                           0: plain restart.  Default 1                      */
 } mtf_options;
 
 typedef struct {

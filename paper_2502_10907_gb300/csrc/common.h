@@ -299,8 +299,13 @@ void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, co
 // basis, FP64 reductions), then x += d.  Stops when every right-hand side's
 // estimate reaches tol relative to ||r|| (reached = true), after the restart
 // length or after max_iter iterations; iters[c] += iterations of rhs c.
+// cycle: index of the cycle within the solve.  With opt.recycle, cycle 0
+// keeps its Krylov space (C = M U) and cycle 1 starts from it (GCRO): the
+// residual is projected out of C and the new basis is orthogonalised
+// against C, so the second cycle does not repeat the first one's slow
+// start.
 mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t s);
+                          std::vector<int>& iters, bool& reached, cudaStream_t s, int cycle);
 // matvec flavours: storage / accumulation precision
 enum MatvecKind { MV_AUTO = 0, MV_FP64 = 1, MV_FP32 = 2, MV_FP32_ACC64 = 3 };
 void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, double* y, int64_t ldy,

@@ -24,12 +24,34 @@ struct HostArnoldi {
     bnorm.assign(nrhs, 1.0);
     jc.assign(nrhs, 0);
   }
-  // start of a cycle for rhs c with ||r||; estimates are relative to ||r||
-  void start(int c, double rnorm) {
+  // start of a cycle for rhs c with first basis vector r / ||r||; estimates
+  // are relative to base (default ||r||)
+  void start(int c, double rnorm, double base = -1.0) {
     jc[c] = 0;
-    bnorm[c] = rnorm > 0 ? rnorm : 1.0;
+    if (base < 0) base = rnorm;
+    bnorm[c] = base > 0 ? base : 1.0;
     for (int q = 0; q <= m; ++q) g[size_t(c) * (m + 1) + q] = 0.0;
     g[size_t(c) * (m + 1)] = rnorm;
+  }
+  // Q (rows x k, column-major, ld = k + 1) and R (k x k upper triangular,
+  // column-major, ld = ldr) of H = Q R for the first k columns of rhs c:
+  // R is the rotated Hessenberg, Q = G_0^H ... G_{k-1}^H [I_k; 0]
+  void qr(int c, int k, std::complex<double>* Q, std::complex<double>* R, int ldr) const {
+    const cd* Hc = &H[size_t(c) * (m + 1) * m];
+    for (int p = 0; p < k; ++p)
+      for (int q = 0; q < k; ++q) R[size_t(p) * ldr + q] = q <= p ? Hc[size_t(p) * (m + 1) + q] : cd(0);
+    const int ld = k + 1;
+    for (int p = 0; p < k; ++p)
+      for (int q = 0; q <= k; ++q) Q[size_t(p) * ld + q] = q == p ? cd(1) : cd(0);
+    for (int j = k - 1; j >= 0; --j) {
+      const double cj = cs[size_t(c) * m + j];
+      const cd sj = sn[size_t(c) * m + j];
+      for (int p = 0; p < k; ++p) {
+        const cd a = Q[size_t(p) * ld + j], b = Q[size_t(p) * ld + j + 1];
+        Q[size_t(p) * ld + j] = cj * a - sj * b;
+        Q[size_t(p) * ld + j + 1] = std::conj(sj) * a + cj * b;
+      }
+    }
   }
   // column j of rhs c from h (interleaved complex, j+1 entries) and ||w||;
   // returns the relative residual estimate |g_{j+1}| / ||b||

@@ -281,7 +281,7 @@ __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t
   out[t] = float(x[2 * c * ldx + k]);
 }
 
-static cublasHandle_t blas_handle() {
+cublasHandle_t blas_handle() {
   static cublasHandle_t h = nullptr;
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cublas_v2.h>
+
 #include "common.h"
 #include "krylov_host.h"
 
@@ -26,6 +28,10 @@ struct Gmres32Work {
   int64_t n = 0, ldn = 0;
   bool pre = false;
   DevBuf<float> V, Z, w;
+  // recycled space of the previous cycle of the same solve: C = V Q in the
+  // first rec_k columns of V, U = Z R^{-1} (M U = C) in those of Z
+  int rec_k = 0;
+  DevBuf<float> RC, RU, RQ;
   // h: kBatch slots, one per Arnoldi column j of a batch; slot layout (complex
   // entries, index i * nrhs + c): t (j+1) x nrhs, s (j+1) x nrhs, coef 2 nrhs
   // (alpha, h_j), ||w|| nrhs, then nrhs real sums of squares
@@ -144,8 +150,8 @@ __device__ __forceinline__ void dcgs_coef(R sigma, R s2, R pr, R pi, R tjr, R tj
 // (ldn / 64, c).
 __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const double* __restrict__ t,
                                                   const double* __restrict__ sq, double* __restrict__ coef,
-                                                  int j, int nrhs, int64_t ldn, int64_t ldv, float* __restrict__ w,
-                                                  double* __restrict__ ss) {
+                                                  int j, int j0, int nrhs, int64_t ldn, int64_t ldv,
+                                                  float* __restrict__ w, double* __restrict__ ss) {
   MTF_PDL_WAIT();
   MTF_PDL_TRIGGER();
   const int c = blockIdx.y;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
     }
     const int64_t oj = 2 * (int64_t(j) * nrhs + c);
     float alpha, hr, hi;
-    dcgs_coef<float>(float(sq[oj]), a, b, e, float(t[oj]), float(t[oj + 1]), j == 0, alpha, hr, hi);
+    dcgs_coef<float>(float(sq[oj]), a, b, e, float(t[oj]), float(t[oj + 1]), j == j0, alpha, hr, hi);
     cf[0] = 1.f / alpha;
     cf[1] = hr;
     cf[2] = hi;
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
         ed += redd[2][g];
       }
       double alphad, hrd, hid;
-      dcgs_coef<double>(sq[oj], ad, bd, ed, t[oj], t[oj + 1], j == 0, alphad, hrd, hid);
+      dcgs_coef<double>(sq[oj], ad, bd, ed, t[oj], t[oj + 1], j == j0, alphad, hrd, hid);
       coef[2 * c] = alphad;
       coef[2 * c + 1] = 0.0;
       coef[2 * (nrhs + c)] = hrd;
@@ -288,6 +294,58 @@ __global__ void __launch_bounds__(256) k_axpy2_32(float* __restrict__ V, const d
     o.y -= st.y + (hr * qj.y + hi * qj.x);
     o.z -= st.z + (hr * qj.z - hi * qj.w);
     o.w -= st.w + (hr * qj.w + hi * qj.z);
+    *x = o;
+    sqn = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) sqn += __shfl_xor_sync(0xffffffffu, sqn, s2);
+  if (lane == 0) atomicAdd(ss + c, double(sqn));
+}
+
+// w^c -= sum_{i<k} V_i^c t_i (t FP64 at [i * nrhs + c], interleaved
+// complex) and ss[c] += ||w^c||^2 after the update: one classical
+// Gram-Schmidt projection against k basis columns.  CTA = 64 entries x 8
+// groups of columns (i = grp mod 8), grid (ldn / 64, c).
+__global__ void __launch_bounds__(256) k_proj32(const float* __restrict__ V, const double* __restrict__ t, int k,
+                                                int nrhs, int64_t ldn, int64_t ldv, float* __restrict__ w,
+                                                double* __restrict__ ss) {
+  const int c = blockIdx.y;
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t q = int64_t(blockIdx.x) * 32 + lane;
+  const int64_t ldq = ldn >> 1;
+  __shared__ float4 part[8][32];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (q < ldq) {
+    const float4* vb = reinterpret_cast<const float4*>(V + 2 * int64_t(c) * ldv) + q;
+#pragma unroll 8
+    for (int i = grp; i < k; i += 8) {
+      const float4 a = vb[int64_t(i) * ldq];
+      const int64_t o = 2 * (int64_t(i) * nrhs + c);
+      const float hr = float(t[o]), hi = float(t[o + 1]);
+      acc.x += a.x * hr - a.y * hi;
+      acc.y += a.x * hi + a.y * hr;
+      acc.z += a.z * hr - a.w * hi;
+      acc.w += a.z * hi + a.w * hr;
+    }
+  }
+  part[grp][lane] = acc;
+  __syncthreads();
+  if (grp != 0) return;
+  float sqn = 0.f;
+  if (q < ldq) {
+    float4 st = part[0][lane];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) {
+      st.x += part[g][lane].x;
+      st.y += part[g][lane].y;
+      st.z += part[g][lane].z;
+      st.w += part[g][lane].w;
+    }
+    float4* x = reinterpret_cast<float4*>(w + 2 * int64_t(c) * ldn) + q;
+    float4 o = *x;
+    o.x -= st.x;
+    o.y -= st.y;
+    o.z -= st.z;
+    o.w -= st.w;
     *x = o;
     sqn = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
   }
@@ -443,8 +501,80 @@ constexpr int kBatch = 8;
 // doubles of the Hessenberg slot of column j
 static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 8) * nrhs; }
 
+cublasHandle_t blas_handle();  // shared cuBLAS handle (osrc.cu)
+
+// Build the recycled space of a finished cycle for the next cycle of the same
+// solve: per rhs c with k_c finished columns, H_c = Q_c R_c (host Givens
+// data), C_c = V_c Q_c (orthonormal, M U_c = C_c) and U_c = Z_c R_c^{-1}, stored
+// in the first k_c columns of V and Z; columns k_c .. kr-1 (kr = max k_c)
+// are zero.  Returns kr.
+static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_t ldv, int64_t ldz, cudaStream_t s) {
+  const int64_t ldn = G.ldn;
+  int kr = 0;
+  for (int c = 0; c < nrhs; ++c) kr = std::max(kr, ha.jc[c]);
+  if (kr <= 0) return 0;
+  using cd = std::complex<double>;
+  const size_t qsz = size_t(kr + 1) * kr, rsz = size_t(kr) * kr;
+  std::vector<cd> Q(qsz), R(rsz);
+  std::vector<float> qr32(size_t(nrhs) * (qsz + rsz) * 2);
+  for (int c = 0; c < nrhs; ++c) {
+    const int kc = ha.jc[c];
+    if (kc <= 0) continue;
+    ha.qr(c, kc, Q.data(), R.data(), kr);
+    float* qc = qr32.data() + size_t(c) * (qsz + rsz) * 2;
+    for (int p = 0; p < kc; ++p)
+      for (int q = 0; q <= kc; ++q) {
+        qc[2 * (size_t(p) * (kr + 1) + q)] = float(Q[size_t(p) * (kc + 1) + q].real());
+        qc[2 * (size_t(p) * (kr + 1) + q) + 1] = float(Q[size_t(p) * (kc + 1) + q].imag());
+      }
+    float* rc = qc + qsz * 2;
+    for (size_t t = 0; t < rsz; ++t) {
+      rc[2 * t] = float(R[t].real());
+      rc[2 * t + 1] = float(R[t].imag());
+    }
+  }
+  const size_t ncols = size_t(kr) * ldn * nrhs * 2;
+  if (G.RC.n < ncols) G.RC.alloc(ncols);
+  if (G.RU.n < ncols) G.RU.alloc(ncols);
+  if (G.RQ.n < qr32.size()) G.RQ.alloc(qr32.size());
+  MTF_CUDA(cudaMemcpyAsync(G.RQ.p, qr32.data(), qr32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  cublasHandle_t h = blas_handle();
+  MTF_REQUIRE(cublasSetStream(h, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
+  MTF_REQUIRE(cublasSetMathMode(h, CUBLAS_PEDANTIC_MATH) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
+              "cublasSetMathMode failed");
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  for (int c = 0; c < nrhs; ++c) {
+    const int kc = ha.jc[c];
+    float* Vc = G.V.p + 2 * size_t(c) * ldv;
+    float* Zc = G.Z.p + 2 * size_t(c) * ldz;
+    float* Cc = G.RC.p + 2 * size_t(c) * kr * ldn;
+    float* Uc = G.RU.p + 2 * size_t(c) * kr * ldn;
+    const cuComplex* Qd = reinterpret_cast<const cuComplex*>(G.RQ.p + size_t(c) * (qsz + rsz) * 2);
+    const cuComplex* Rd = Qd + qsz;
+    if (kc > 0) {
+      MTF_REQUIRE(cublasCgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, int(ldn), kc, kc + 1, &one,
+                              reinterpret_cast<const cuComplex*>(Vc), int(ldn), Qd, kr + 1, &zero,
+                              reinterpret_cast<cuComplex*>(Cc), int(ldn)) == CUBLAS_STATUS_SUCCESS,
+                  MTF_ERR_CUDA, "cublasCgemm failed");
+      MTF_CUDA(cudaMemcpyAsync(Uc, Zc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
+      MTF_REQUIRE(cublasCtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT,
+                              int(ldn), kc, &one, Rd, kr, reinterpret_cast<cuComplex*>(Uc), int(ldn)) ==
+                      CUBLAS_STATUS_SUCCESS,
+                  MTF_ERR_CUDA, "cublasCtrsm failed");
+      MTF_CUDA(cudaMemcpyAsync(Vc, Cc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
+      MTF_CUDA(cudaMemcpyAsync(Zc, Uc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (kc < kr) {
+      MTF_CUDA(cudaMemsetAsync(Vc + 2 * size_t(kc) * ldn, 0, size_t(kr - kc) * ldn * 8, s));
+      MTF_CUDA(cudaMemsetAsync(Zc + 2 * size_t(kc) * ldn, 0, size_t(kr - kc) * ldn * 8, s));
+    }
+  }
+  MTF_CUDA(cudaStreamSynchronize(s));  // qr32 is released on return
+  return kr;
+}
+
 mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t s) {
+                          std::vector<int>& iters, bool& reached, cudaStream_t s, int cycle) {
   mtf_mesh msh = sys->mesh;
   const int64_t n = msh->n_total;
   const int64_t ldn = (n + 63) & ~int64_t(63);
@@ -469,31 +599,16 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     G.n = n;
     G.ldn = ldn;
     G.pre = pre;
+    G.rec_k = 0;
   }
+  if (cycle == 0) G.rec_k = 0;  // a new solve: nothing to recycle
+  const int kr = G.rec_k;       // columns of the recycled space (0: none)
+  G.rec_k = 0;                  // used by this cycle only
   const int ldh = m + 1;
   const int64_t ldv = int64_t(m + 1) * ldn, ldz = int64_t(m) * ldn;
   const size_t slot = slot_len(m - 1, nrhs);
-
-  // V_0 = r / ||r|| (sums of squares in slot 0)
-  MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nrhs) * sizeof(double), s));
-  MTF_LAUNCH(KID_NORM, s, k_sqnorm64<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p));
-  MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p, G.V.p, ldv));
-  MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, size_t(nrhs) * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MTF_CUDA(cudaStreamSynchronize(s));
-  HostArnoldi ha(m, nrhs);
-  std::vector<int> active(nrhs);
-  bool any = false;
-  for (int c = 0; c < nrhs; ++c) {
-    const double rn = std::sqrt(G.h_host[c]);
-    if (!std::isfinite(rn)) return MTF_ERR_NAN;
-    ha.start(c, rn);
-    active[c] = rn > 0;
-    any = any || active[c];
-  }
-  reached = !any;
-  if (!any) return MTF_OK;
-
-  mtf_status status = MTF_OK;
+  const dim3 ga{nb(ldn / 2, 32), unsigned(nrhs)};
+  const dim3 gs{nb(ldn / 2, 256), unsigned(nrhs)};
   const size_t hsm = size_t(2 * m) * sizeof(float2);
   const size_t ysm = size_t(m + 1) * sizeof(double2);
   if (hsm > 40 * 1024 || ysm > 40 * 1024) {
@@ -502,14 +617,98 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     MTF_CUDA(cudaFuncSetAttribute(k_axpy2_32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hsm) + 8192));
     MTF_CUDA(cudaFuncSetAttribute(k_xupdate32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ysm)));
   }
-  const dim3 ga{nb(ldn / 2, 32), unsigned(nrhs)};
-  const dim3 gs{nb(ldn / 2, 256), unsigned(nrhs)};
-  const int jend = std::min(m, std::max(1, max_iter));
+  // x += sum_{i < jc[c]} Z_i y_i for coefficient vectors yc (m+1 complex per rhs)
+  auto x_update = [&](const std::vector<double>& yc, const std::vector<int>& jcs) {
+    int jm = 0;
+    for (int c = 0; c < nrhs; ++c) jm = std::max(jm, jcs[size_t(c)]);
+    if (jm <= 0) return;
+    const size_t ny = yc.size();
+    std::vector<double> ybuf(ny + size_t(nrhs));
+    std::copy(yc.begin(), yc.end(), ybuf.begin());
+    int* jp = reinterpret_cast<int*>(ybuf.data() + ny);
+    for (int c = 0; c < nrhs; ++c) jp[c] = jcs[size_t(c)];
+    if (G.y.n < ybuf.size()) G.y.alloc(ybuf.size());
+    MTF_CUDA(cudaMemcpyAsync(G.y.p, ybuf.data(), ybuf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    MTF_LAUNCH(KID_AXPY, s, k_xupdate32<<<ga, 256, size_t(jm) * sizeof(double2), s>>>(
+        G.Z.p, G.y.p, reinterpret_cast<const int*>(G.y.p + ny), ldn, ldz, ldh, n, x_dev));
+    MTF_CUDA(cudaStreamSynchronize(s));  // ybuf is released on return
+  };
+
+  HostArnoldi ha(m, nrhs);
+  std::vector<int> active(nrhs);
+  bool any = false;
+  MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nrhs) * sizeof(double), s));
+  MTF_LAUNCH(KID_NORM, s, k_sqnorm64<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p));
+  if (kr == 0) {
+    // V_0 = r / ||r|| (sums of squares in slot 0)
+    MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, G.h.p, G.V.p, ldv));
+    MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, size_t(nrhs) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < nrhs; ++c) {
+      const double rn = std::sqrt(G.h_host[c]);
+      if (!std::isfinite(rn)) return MTF_ERR_NAN;
+      ha.start(c, rn);
+      active[c] = rn > 0;
+      any = any || active[c];
+    }
+  } else {
+    // Recycled start (GCRO): the residual is projected out of C = M U twice
+    // (classical Gram-Schmidt), x += U (C^H r), and the new Krylov space
+    // starts at column kr with the projected residual; the columns 0..kr-1
+    // stay in the basis, so every later vector is also orthogonalised
+    // against C.
+    double* SS0 = G.h.p;                            // ||r||^2
+    double* T1 = SS0 + nrhs;                        // C^H w, first pass
+    double* S1 = T1 + 2 * size_t(kr) * nrhs;        // (unused second output of the dot kernel)
+    double* T2 = S1 + 2 * size_t(kr) * nrhs;        // second pass
+    double* SS1 = T2 + 2 * size_t(kr) * nrhs;       // ||w||^2 after pass 1 (unused), pass 2
+    double* SS2 = SS1 + nrhs;
+    double* NRM = SS2 + nrhs;
+    const size_t used = size_t(NRM + 2 * nrhs - G.h.p);
+    MTF_REQUIRE(used <= G.h.n, MTF_ERR_ARG, "recycled space larger than the Hessenberg scratch");
+    MTF_CUDA(cudaMemsetAsync(T1, 0, (used - nrhs) * sizeof(double), s));
+    MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, SS0, G.w.p, ldn));
+    launch_dots2_32(G.V.p, G.w.p, ldn, ldv, kr, 0, T1, S1, nrhs, s);
+    MTF_LAUNCH(KID_AXPY, s, k_proj32<<<ga, 256, 0, s>>>(G.V.p, T1, kr, nrhs, ldn, ldv, G.w.p, SS1));
+    MTF_CUDA(cudaMemsetAsync(S1, 0, 2 * size_t(kr) * nrhs * sizeof(double), s));
+    launch_dots2_32(G.V.p, G.w.p, ldn, ldv, kr, 0, T2, S1, nrhs, s);
+    MTF_LAUNCH(KID_AXPY, s, k_proj32<<<ga, 256, 0, s>>>(G.V.p, T2, kr, nrhs, ldn, ldv, G.w.p, SS2));
+    MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, SS2, NRM, G.V.p + 2 * size_t(kr) * ldn, ldv));
+    MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, used * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MTF_CUDA(cudaStreamSynchronize(s));
+    const double* hT1 = G.h_host + (T1 - G.h.p);
+    const double* hT2 = G.h_host + (T2 - G.h.p);
+    const double* hN = G.h_host + (NRM - G.h.p);
+    std::vector<double> yc(size_t(m + 1) * nrhs * 2, 0.0);
+    std::vector<int> jcs(nrhs, 0);
+    for (int c = 0; c < nrhs; ++c) {
+      const double rn = std::sqrt(G.h_host[c]);
+      if (!std::isfinite(rn) || !std::isfinite(hN[2 * c])) return MTF_ERR_NAN;
+      for (int i = 0; i < kr; ++i) {
+        const size_t o = 2 * (size_t(i) * nrhs + c);
+        yc[2 * (size_t(c) * (m + 1) + i)] = rn * (hT1[o] + hT2[o]);
+        yc[2 * (size_t(c) * (m + 1) + i) + 1] = rn * (hT1[o + 1] + hT2[o + 1]);
+      }
+      jcs[c] = rn > 0 ? kr : 0;
+      const double beta = rn * hN[2 * c];  // norm of the projected residual
+      ha.start(c, beta, rn);
+      active[c] = rn > 0 && beta > 0;
+      any = any || active[c];
+    }
+    x_update(yc, jcs);  // x += U (C^H r)
+  }
+  reached = !any;
+  if (!any) return MTF_OK;
+
+  mtf_status status = MTF_OK;
+  const int jend = std::min(m, kr + std::max(1, max_iter));
   // provisional (once-projected) column of every right-hand side, finished
   // when the next step's reduction arrives
   std::vector<std::vector<double>> rawcol(nrhs);
   std::vector<double> rawbeta(nrhs, 0.0);
   std::vector<double> hcol;
+  // rows 0..kr-1 of the new columns (their components along C), per rhs
+  std::vector<std::vector<double>> Bcol(nrhs);
   bool stop = false;
   auto finish_column = [&](int c, int jc, const double* sv, double alpha) -> double {
     // column jc with H[i, jc] += beta s_i (i <= jc) and H[jc+1, jc] = beta alpha
@@ -521,9 +720,10 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
         hcol[2 * i + 1] += beta * sv[2 * (size_t(i) * nrhs + c) + 1];
       }
     ++iters[c];
-    return ha.add_column(c, jc, hcol.data(), beta * alpha);
+    if (kr > 0) Bcol[c].insert(Bcol[c].end(), hcol.begin(), hcol.begin() + 2 * size_t(kr));
+    return ha.add_column(c, jc - kr, hcol.data() + 2 * size_t(kr), beta * alpha);
   };
-  for (int j0 = 0; j0 < jend && !stop; j0 += kBatch) {
+  for (int j0 = kr; j0 < jend && !stop; j0 += kBatch) {
     const int nbat = std::min(kBatch, jend - j0);
     // the batch's Hessenberg slots are cleared once and copied back once
     MTF_CUDA(cudaMemsetAsync(G.h.p, 0, size_t(nbat) * slot * sizeof(double), s));
@@ -547,8 +747,8 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       double* SS = NRM + 2 * size_t(nrhs);
       launch_dots2_32(G.V.p, G.w.p, ldn, ldv, j + 1, j, T, S, nrhs, s);
       MTF_LAUNCH(KID_AXPY, s,
-                 launch_pdl(k_axpy2_32, ga, dim3(256), size_t(2 * j) * sizeof(float2), s, G.V.p, T, S, C, j, nrhs,
-                            ldn, ldv, G.w.p, SS));
+                 launch_pdl(k_axpy2_32, ga, dim3(256), size_t(2 * j) * sizeof(float2), s, G.V.p, T, S, C, j, kr,
+                            nrhs, ldn, ldv, G.w.p, SS));
       MTF_LAUNCH(KID_NORM, s,
                  launch_pdl(k_scale32, gs, dim3(256), 0, s, G.w.p, ldn, SS, NRM, G.V.p + 2 * size_t(j + 1) * ldn,
                             ldv));
@@ -565,7 +765,7 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       bool all_done = true;
       for (int c = 0; c < nrhs; ++c) {
         if (!active[c]) continue;
-        if (j >= 1) {
+        if (j > kr) {
           const double alpha = C[2 * c];
           const double est = finish_column(c, j - 1, S, alpha);
           if (!std::isfinite(est)) status = MTF_ERR_NAN;
@@ -611,23 +811,42 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     }
   }
   check_matvec_stream(sys, s);
-  // x += Z y, y = R^{-1} g per right-hand side
+  // x += Z y, y = R^{-1} g per right-hand side (new columns); with a recycled
+  // space also x -= U (B y), B the new columns' components along C
   std::vector<double> yhost(size_t(m + 1) * nrhs * 2);
-  const int jmax = ha.solve(yhost);
+  ha.solve(yhost);
   for (double v : yhost)
     if (!std::isfinite(v)) return MTF_ERR_NAN;
-  if (jmax > 0) {
-    // y followed by the per-rhs column counts
-    const size_t ny = yhost.size();
-    std::vector<double> ybuf(ny + size_t(nrhs));
-    std::copy(yhost.begin(), yhost.end(), ybuf.begin());
-    int* jcs = reinterpret_cast<int*>(ybuf.data() + ny);
-    for (int c = 0; c < nrhs; ++c) jcs[c] = ha.jc[c];
-    if (G.y.n < ybuf.size()) G.y.alloc(ybuf.size());
-    MTF_CUDA(cudaMemcpyAsync(G.y.p, ybuf.data(), ybuf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    MTF_LAUNCH(KID_AXPY, s, k_xupdate32<<<ga, 256, size_t(jmax) * sizeof(double2), s>>>(
-        G.Z.p, G.y.p, reinterpret_cast<const int*>(G.y.p + ny), ldn, ldz, ldh, n, x_dev));
-    MTF_CUDA(cudaStreamSynchronize(s));  // ybuf is released on return
+  std::vector<double> yc(size_t(m + 1) * nrhs * 2, 0.0);
+  std::vector<int> jcs(nrhs, 0);
+  for (int c = 0; c < nrhs; ++c) {
+    const int jl = ha.jc[c];
+    if (jl <= 0) continue;
+    const double* yl = yhost.data() + 2 * size_t(c) * (m + 1);
+    double* yo = yc.data() + 2 * size_t(c) * (m + 1);
+    for (int q = 0; q < jl; ++q) {
+      yo[2 * (kr + q)] = yl[2 * q];
+      yo[2 * (kr + q) + 1] = yl[2 * q + 1];
+    }
+    for (int i = 0; i < kr; ++i) {
+      double ur = 0, ui = 0;
+      for (int q = 0; q < jl; ++q) {
+        const double br = Bcol[c][2 * (size_t(q) * kr + i)], bi = Bcol[c][2 * (size_t(q) * kr + i) + 1];
+        ur += br * yl[2 * q] - bi * yl[2 * q + 1];
+        ui += br * yl[2 * q + 1] + bi * yl[2 * q];
+      }
+      yo[2 * i] = -ur;
+      yo[2 * i + 1] = -ui;
+    }
+    jcs[c] = kr + jl;
+  }
+  x_update(yc, jcs);
+  // keep this cycle's space for the next cycle of the solve when there is
+  // room for a useful number of new columns next to it
+  if (cycle == 0 && kr == 0 && sys->opt.recycle) {
+    int kmax = 0;
+    for (int c = 0; c < nrhs; ++c) kmax = std::max(kmax, ha.jc[c]);
+    if (kmax > 0 && kmax + 32 <= m) G.rec_k = build_recycle(G, ha, nrhs, ldv, ldz, s);
   }
   return status;
 }
