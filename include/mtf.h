@@ -374,6 +374,17 @@ mtf_status mtf_learned_apply(mtf_system sys, const void* r, void* z, int32_t nrh
 mtf_status mtf_farfield(mtf_system sys, const void* x, int32_t nrhs, const double* obs_dirs,
                         int32_t n_obs, void* f_out, void* stream);
 
+/* Near field by the representation formula (Eq. 8): for every point x_p
+ * (host, n_pts * 3 doubles) in subdomain domains[p] (host int32, 0..M),
+ *   U(x_p) = H_{k_i}(gamma_D U) + E_{k_i}(gamma_N U)
+ * from block i = domains[p] of the solutions x (device complex128
+ * n_total x nrhs): the scattered field in Omega_0, the total field in
+ * Omega_i (i >= 1).  6-point rule per triangle: points should keep about one
+ * triangle diameter from the skeleton.  f_out: device complex128,
+ * n_pts * 3 * nrhs, index (c * n_pts + p) * 3 + xyz.  Synchronises `stream`. */
+mtf_status mtf_nearfield(mtf_system sys, const void* x, int32_t nrhs, const double* points, const int32_t* domains,
+                         int32_t n_pts, void* f_out, void* stream);
+
 void mtf_system_destroy(mtf_system sys);
 
 const char* mtf_status_string(mtf_status s);

@@ -42,6 +42,7 @@ class mtf_solve_stats(ctypes.Structure):
 _lib = None
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _SIGS = {
+    "mtf_nearfield": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
     "mtf_default_options": (None, [ctypes.POINTER(mtf_options)]),
     "mtf_mesh_create": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(_vp)]),
     "mtf_mesh_info": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
@@ -248,6 +249,15 @@ def mtf_solve_static(sys_, dirs, pols, x_out, stream=0, raise_on_noconv=True):
 def mtf_farfield(sys_, x, nrhs, obs_dirs, f_out, stream=0):
     o = np.ascontiguousarray(obs_dirs, dtype=np.float64)
     _check(load().mtf_farfield(sys_, _ptr(x), int(nrhs), _ptr(o), len(o), _ptr(f_out), stream or None))
+
+
+def mtf_nearfield(sys_, x, nrhs, points, domains, f_out, stream=0):
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    dom = np.ascontiguousarray(domains, dtype=np.int32).reshape(-1)
+    if len(dom) != len(pts):
+        raise ValueError("one subdomain per point")
+    _check(load().mtf_nearfield(sys_, _ptr(x), int(nrhs), _ptr(pts), _ptr(dom), len(pts), _ptr(f_out),
+                                stream or None))
 
 
 def mtf_system_destroy(sys_):

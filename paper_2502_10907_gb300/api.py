@@ -171,6 +171,15 @@ class System:
         st, status = L.mtf_solve(self.handle, dirs, pols, x, _stream(), raise_on_noconv)
         return x, st
 
+    def nearfield(self, x, points, domains):
+        """U at points (P, 3) in subdomains domains (P,) by Eq. 8 -> (nrhs, P, 3) complex128:
+        the scattered field in subdomain 0, the total field in the others."""
+        x = x.contiguous()
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        f = torch.empty((x.shape[0], len(pts), 3), dtype=torch.complex128, device="cuda")
+        L.mtf_nearfield(self.handle, x, x.shape[0], pts, domains, f, _stream())
+        return f
+
     def farfield(self, x, obs):
         nrhs = x.shape[0]
         f = torch.empty((nrhs, len(obs), 3), dtype=torch.complex128, device="cuda")

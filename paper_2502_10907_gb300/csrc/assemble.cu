@@ -615,6 +615,107 @@ void launch_rhs(mtf_system sys, int nrhs, const double* d_dirs, const double* d_
   MTF_CUDA(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// near field (Stratton-Chu, Eq. 8): for a point x in Omega_i,
+//   U(x) = H_k(a)(x) + E_k(b)(x),  a = gamma_D U,  b = gamma_N U (N slot / rho_i),
+//   H_k a = int grad_x G x a,  E_k b = i k int G b - 1/(i k) int grad_x G div b,
+// with k = k_i, the RWG fields of block i's coefficients and div psi_a = 2 c_a.
+// One CTA per (point, rhs); the 6-point rule on every triangle of block i.
+// blk: per block {first block-triangle, triangles, N, dof offset}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_nearfield(const double* __restrict__ x, int64_t n_total,
+                                                   const double* __restrict__ bt_v,
+                                                   const double* __restrict__ bt_c,
+                                                   const double* __restrict__ bt_area,
+                                                   const int32_t* __restrict__ bt_dof,
+                                                   const int64_t* __restrict__ blk, const double* __restrict__ kk,
+                                                   const double* __restrict__ rho, const double* __restrict__ pts,
+                                                   const int32_t* __restrict__ dom, int npts,
+                                                   double* __restrict__ fout) {
+  const int p = blockIdx.x, col = blockIdx.y;
+  const int i = dom[p];
+  const double X[3] = {pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]};
+  const int64_t q0 = blk[4 * i], T = blk[4 * i + 1], N = blk[4 * i + 2], off = blk[4 * i + 3];
+  const double kr = kk[2 * i], ki = kk[2 * i + 1];
+  const double rr = rho[2 * i], ri = rho[2 * i + 1], rn = rr * rr + ri * ri;
+  const C2 irho{rr / rn, -ri / rn};
+  const C2 ik{-ki, kr};
+  const double kn = kr * kr + ki * ki;
+  const C2 minv_ik{ki / kn, kr / kn};  // -1 / (i k)
+  const double* xc = x + 2 * int64_t(col) * n_total;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t it = threadIdx.x; it < T * 6; it += blockDim.x) {
+    const int64_t q = q0 + it / 6;
+    const int qp = int(it % 6);
+    const double* v = bt_v + 9 * q;
+    double y[3], d[3];
+    for (int c = 0; c < 3; ++c) {
+      y[c] = v[c] + c_tri_s[qp] * (v[3 + c] - v[c]) + c_tri_t[qp] * (v[6 + c] - v[c]);
+      d[c] = X[c] - y[c];
+    }
+    const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    C2 G, g;
+    helmholtz(kr, ki, R, G, g);  // grad_x G = g d
+    const double w = 2.0 * bt_area[q] * c_tri_w[qp];
+    C2 av[3] = {{0, 0}, {0, 0}, {0, 0}}, bv[3] = {{0, 0}, {0, 0}, {0, 0}}, divb{0, 0};
+    for (int a = 0; a < 3; ++a) {
+      const int64_t m = bt_dof[3 * q + a];
+      const double ca = bt_c[3 * q + a];
+      const C2 uD{xc[2 * (off + m)], xc[2 * (off + m) + 1]};
+      const C2 uN = cmul(C2{xc[2 * (off + N + m)], xc[2 * (off + N + m) + 1]}, irho);
+      for (int c = 0; c < 3; ++c) {
+        const double f = ca * (y[c] - v[3 * a + c]);
+        av[c] = cadd(av[c], cscale(uD, f));
+        bv[c] = cadd(bv[c], cscale(uN, f));
+      }
+      divb = cadd(divb, cscale(uN, 2.0 * ca));
+    }
+    const C2 ikG = cmul(ik, G);
+    const C2 e2 = cmul(minv_ik, cmul(g, divb));
+    for (int c = 0; c < 3; ++c) {
+      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      const C2 cr = csub(cscale(av[c2], d[c1]), cscale(av[c1], d[c2]));  // (d x a)_c
+      const C2 e = cadd(cadd(cmul(g, cr), cmul(ikG, bv[c])), cscale(e2, d[c]));
+      acc[2 * c] += w * e.re;
+      acc[2 * c + 1] += w * e.im;
+    }
+  }
+  __shared__ double red[8][6];
+  for (int c = 0; c < 6; ++c) {
+    double v = acc[c];
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    acc[c] = v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) red[warp][c] = acc[c];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0;
+    for (int wi = 0; wi < int(blockDim.x >> 5); ++wi) t += red[wi][threadIdx.x];
+    fout[(int64_t(col) * npts + p) * 6 + threadIdx.x] = t;
+  }
+}
+
+void launch_nearfield(mtf_system sys, const double* x, int nrhs, const double* d_pts, const int32_t* d_dom,
+                      int npts, double* f, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  upload_rule_constants(s);
+  std::vector<int64_t> blk(static_cast<size_t>(4 * m->nd));
+  for (int i = 0; i < m->nd; ++i) {
+    blk[size_t(4 * i)] = m->blk[i].bt_off;
+    blk[size_t(4 * i + 1)] = m->blk[i].T;
+    blk[size_t(4 * i + 2)] = m->blk[i].N;
+    blk[size_t(4 * i + 3)] = m->blk[i].dof_off;
+  }
+  DevBuf<int64_t> d_blk;
+  d_blk.upload(blk, s);
+  MTF_LAUNCH(KID_FARFIELD, s, k_nearfield<<<dim3(unsigned(npts), unsigned(nrhs)), 256, 0, s>>>(
+      x, m->n_total, m->d_bt_v.p, m->d_bt_c.p, m->d_bt_area.p, m->d_bt_dof.p, d_blk.p, sys->d_k.p, sys->d_rho.p,
+      d_pts, d_dom, npts, f));
+  MTF_CUDA(cudaStreamSynchronize(s));  // d_blk is released on return
+}
+
 void launch_farfield(mtf_system sys, const double* x, int nrhs, const double* d_obs, int nobs, double* f,
                      cudaStream_t s) {
   mtf_mesh m = sys->mesh;

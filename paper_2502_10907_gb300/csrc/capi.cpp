@@ -473,6 +473,27 @@ mtf_status mtf_learned_apply(mtf_system sys, const void* r, void* z, int32_t nrh
   });
 }
 
+mtf_status mtf_nearfield(mtf_system sys, const void* x, int32_t nrhs, const double* points, const int32_t* domains,
+                         int32_t n_pts, void* f_out, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && x && points && domains && f_out, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1 && n_pts >= 1, MTF_ERR_ARG, "nrhs and n_pts must be >= 1");
+    const int nd = sys->mesh->nd;
+    for (int32_t p = 0; p < n_pts; ++p)
+      MTF_REQUIRE(domains[p] >= 0 && domains[p] < nd && std::isfinite(points[3 * p]) &&
+                      std::isfinite(points[3 * p + 1]) && std::isfinite(points[3 * p + 2]),
+                  MTF_ERR_ARG, "point with a subdomain out of range or a non-finite coordinate");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBuf<double> dp;
+    DevBuf<int32_t> dd;
+    dp.alloc(size_t(3) * n_pts);
+    dd.alloc(size_t(n_pts));
+    MTF_CUDA(cudaMemcpyAsync(dp.p, points, size_t(3) * n_pts * sizeof(double), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(dd.p, domains, size_t(n_pts) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    launch_nearfield(sys, static_cast<const double*>(x), nrhs, dp.p, dd.p, n_pts, static_cast<double*>(f_out), s);
+  });
+}
+
 mtf_status mtf_farfield(mtf_system sys, const void* x, int32_t nrhs, const double* obs_dirs, int32_t n_obs,
                         void* f_out, void* stream) {
   return guarded([&] {

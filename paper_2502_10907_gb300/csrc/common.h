@@ -318,6 +318,11 @@ void launch_rhs(mtf_system sys, int nrhs, const double* d_dirs, const double* d_
                 cudaStream_t s);
 void launch_farfield(mtf_system sys, const double* x, int nrhs, const double* d_obs, int nobs,
                      double* f, cudaStream_t s);
+// U(x) by the representation formula (Eq. 8) at npts points (device, 3 each)
+// in the subdomains d_dom (device), from the solutions x; f: device complex128
+// (nrhs x npts x 3)
+void launch_nearfield(mtf_system sys, const double* x, int nrhs, const double* d_pts, const int32_t* d_dom,
+                      int npts, double* f, cudaStream_t s);
 void launch_get_block(mtf_system sys, int i, double* t_out, double* k_out, cudaStream_t s);
 mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
                  cudaStream_t s);

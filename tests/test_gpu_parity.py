@@ -100,6 +100,28 @@ def test_solve_and_farfield_match_oracle_lu(api, oracle_cache, name):
     assert rel(f, fr) < TOL
 
 
+NEAR_POINTS = {
+    "sphere": (np.array([[0.0, 0.0, 2.0], [1.5, 0.5, 0.0], [0.1, 0.2, -0.1], [0.0, 0.0, 0.4]]), [0, 0, 1, 1]),
+    "split": (np.array([[0.0, 0.0, 2.0], [1.2, 0.9, 0.3], [0.1, 0.2, 0.4], [-0.3, 0.0, 0.5], [0.2, -0.1, -0.4],
+                        [0.0, 0.3, -0.5]]), [0, 0, 1, 1, 2, 2]),
+}
+
+
+@pytest.mark.parametrize("name", ["sphere", "split"])
+def test_nearfield_matches_oracle(api, oracle_cache, name):
+    """U = H(gamma_D U) + E(gamma_N U) (Eq. 8) at points of every subdomain,
+    from the same (oracle LU) solution on both sides."""
+    from oracle.nearfield import representation
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    xr = ref.solve_lu(ref.rhs(cfg["dirs"], cfg["pols"]))
+    pts, dom = NEAR_POINTS[name]
+    f = sysg.nearfield(torch.from_numpy(np.ascontiguousarray(xr.T)).cuda(), pts, dom).cpu().numpy()
+    fr = representation(ref, xr, pts, np.array(dom)).transpose(2, 0, 1)
+    assert rel(f, fr) < TOL, rel(f, fr)
+
+
 def test_degenerate_inputs_are_rejected(api, oracle_cache):
     from paper_2502_10907_gb300 import _lib as L
     cfg, sk, ref = _case(oracle_cache, "sphere")
