@@ -14,10 +14,12 @@
 // streaming kernels read two complex entries per lane as one float4; the
 // padding is zero at allocation and every kernel keeps it zero.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include <cublas_v2.h>
 
+#include "bulk.h"
 #include "common.h"
 #include "krylov_host.h"
 
@@ -49,74 +51,134 @@ static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); 
 // Fused reduction of the delayed CGS2 step (one pass over the basis):
 //   t[i*hst + c] += sum_k conj(V_i^c[k]) w^c[k]   and
 //   s[i*hst + c] += sum_k conj(V_i^c[k]) V_jq^c[k]   for i < rows,
-// over one segment of kDotSeg entries x 32 basis vectors per CTA (4 per
-// warp; every lane loads its 16 basis values and the 8 values of w and q~
-// they multiply at once).  Grid (segments, ceil(rows/32), c);
-// V_i^c starts at V + 2 (c ldv + i ldn).
-constexpr int kDotSeg = 256;
+// V_i^c starting at V + 2 (c ldv + i ldn).  The basis is staged in shared
+// memory by the bulk-copy engine: a persistent CTA per SM takes units
+// (right-hand side c, segment of kDtL entries, group of kDtR basis vectors)
+// in turn.  A producer warp copies
+// the unit's kDtR vector slices and the matching slices of w and q~ into a
+// ring of kDtS stages (one "full" mbarrier per stage); kDtCons consumer warps,
+// kDtRW vectors each, form the four partial sums per vector from shared
+// memory, reduce them over the warp and add them into t and s (FP64), then
+// release the stage ("empty" mbarrier).  The copies of the next units are in
+// flight while a unit is reduced, so the basis streams at a steady rate
+// instead of in one burst per CTA wave (measured on the split sphere: 14 %
+// less time than one register-staged pass per CTA; 4 KB slices of 16
+// vectors beat 2 KB slices and 16 warps of one vector).  Every wait is
+// bounded (~0.5 s): on timeout the kernel sets *err and its warps leave.
+#ifndef MTF_DT_L
+#define MTF_DT_L 512
+#endif
+#ifndef MTF_DT_RW
+#define MTF_DT_RW 2
+#endif
+#ifndef MTF_DT_CONS
+#define MTF_DT_CONS 8
+#endif
+#ifndef MTF_DT_S
+#define MTF_DT_S 3
+#endif
+constexpr int kDtL = MTF_DT_L;            // complex entries per slice (a multiple of 64)
+constexpr int kDtRW = MTF_DT_RW;          // basis vectors per consumer warp
+constexpr int kDtCons = MTF_DT_CONS;      // consumer warps
+constexpr int kDtR = kDtRW * kDtCons;     // basis vectors per unit
+constexpr int kDtSliceB = kDtL * 8;       // bytes of one slice
+constexpr int kDtSB = (kDtR + 2) * kDtSliceB;
+constexpr int kDtS = MTF_DT_S;
+static_assert(kDtL % 64 == 0 && (kDtRW == 1 || kDtRW == 2 || kDtRW == 4), "unsupported dot-kernel tiling");
+constexpr size_t kDtSmem = size_t(kDtS) * kDtSB + size_t(kDtS) * 2 * sizeof(uint64_t);
+static_assert(kDtSmem <= 232448, "stage ring above the per-CTA shared-memory limit");
+constexpr uint64_t kDtWaitNs = 500000000ull;
 
-__global__ void __launch_bounds__(256) k_dots2_32(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn,
-                                                  int64_t ldv, int rows, int jq, double* __restrict__ t,
-                                                  double* __restrict__ sq, int hst) {
+__global__ void __launch_bounds__((kDtCons + 1) * 32, 1)
+    k_dots_tma(const float* __restrict__ V, const float* __restrict__ w, int64_t ldn, int64_t ldv, int rows, int jq,
+               double* __restrict__ t, double* __restrict__ sq, int hst, int nrhs, unsigned* __restrict__ err) {
   MTF_PDL_WAIT();
   MTF_PDL_TRIGGER();
-  constexpr int RW = 4, NQ = kDotSeg / 64;  // float4 per lane
-  const int c = blockIdx.z;
-  const int64_t k0 = int64_t(blockIdx.x) * kDotSeg;
-  const int nq = int(min(ldn - k0, int64_t(kDotSeg)) >> 1);
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(kDtS) * kDtSB);
+  uint64_t* empty = full + kDtS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.y * (8 * RW) + warp * RW;
-  if (i0 >= rows) return;
-  // every lane loads the w and q~ values it multiplies itself, together with
-  // its basis values: one memory round trip, no staging barrier
-  const float4* wv = reinterpret_cast<const float4*>(w + 2 * (int64_t(c) * ldn + k0));
-  const float4* qv = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(jq) * ldn + k0));
-  const float4* v[RW];
-#pragma unroll
-  for (int r = 0; r < RW; ++r)
-    v[r] = reinterpret_cast<const float4*>(V + 2 * (int64_t(c) * ldv + int64_t(min(i0 + r, rows - 1)) * ldn + k0));
-  float4 a[NQ][RW], xw[NQ], xq[NQ];
-#pragma unroll
-  for (int u = 0; u < NQ; ++u) {
-    const bool ok = lane + 32 * u < nq;
-    xw[u] = ok ? wv[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
-    xq[u] = ok ? qv[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int r = 0; r < RW; ++r) a[u][r] = ok ? v[r][lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nseg = int((ldn + kDtL - 1) / kDtL), nrg = (rows + kDtR - 1) / kDtR;
+  const int n_units = nseg * nrg * nrhs;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kDtS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kDtCons);
+    }
+    mbar_fence_init();
   }
-  float tr[RW], ti[RW], sr[RW], si[RW];
-#pragma unroll
-  for (int r = 0; r < RW; ++r) tr[r] = ti[r] = sr[r] = si[r] = 0.f;
-#pragma unroll
-  for (int u = 0; u < NQ; ++u) {
-    const float4 x = xw[u];
-    const float4 y = xq[u];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const float4 e = a[u][r];
-      tr[r] += e.x * x.x + e.y * x.y + e.z * x.z + e.w * x.w;
-      ti[r] += e.x * x.y - e.y * x.x + e.z * x.w - e.w * x.z;
-      sr[r] += e.x * y.x + e.y * y.y + e.z * y.z + e.w * y.w;
-      si[r] += e.x * y.y - e.y * y.x + e.z * y.w - e.w * y.z;
+  __syncthreads();
+  if (warp == kDtCons) {
+    // producer: one lane issues every copy
+    if (lane != 0) return;
+    int k = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
+      const int seg = u % nseg, rg = (u / nseg) % nrg, c = u / (nseg * nrg);
+      const int st = k % kDtS;
+      if (!mbar_wait_bounded(&empty[st], (uint32_t(k / kDtS) & 1u) ^ 1u, kDtWaitNs)) {
+        atomicExch(err, 1u);
+        return;
+      }
+      const int64_t k0 = int64_t(seg) * kDtL;
+      const uint32_t bytes = uint32_t(min(int64_t(kDtL), ldn - k0)) * 8u;
+      const int i0 = rg * kDtR, nr = min(kDtR, rows - i0);
+      mbar_arrive_expect_tx(&full[st], uint32_t(nr + 2) * bytes);
+      unsigned char* sb = smem + size_t(st) * kDtSB;
+      const float* Vc = V + 2 * (int64_t(c) * ldv + k0);
+      for (int r = 0; r < nr; ++r) bulk_g2s(sb + r * kDtSliceB, Vc + 2 * int64_t(i0 + r) * ldn, bytes, &full[st]);
+      bulk_g2s(sb + kDtR * kDtSliceB, w + 2 * (int64_t(c) * ldn + k0), bytes, &full[st]);
+      bulk_g2s(sb + (kDtR + 1) * kDtSliceB, Vc + 2 * int64_t(jq) * ldn, bytes, &full[st]);
     }
+    return;
   }
-  // FP32 warp sums (32 lane partials), FP64 accumulation over segments
-#pragma unroll
-  for (int r = 0; r < RW; ++r) {
-#pragma unroll
-    for (int s2 = 16; s2 > 0; s2 >>= 1) {
-      tr[r] += __shfl_xor_sync(0xffffffffu, tr[r], s2);
-      ti[r] += __shfl_xor_sync(0xffffffffu, ti[r], s2);
-      sr[r] += __shfl_xor_sync(0xffffffffu, sr[r], s2);
-      si[r] += __shfl_xor_sync(0xffffffffu, si[r], s2);
+  int k = 0;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
+    const int st = k % kDtS;
+    if (!mbar_wait_bounded(&full[st], uint32_t(k / kDtS) & 1u, kDtWaitNs)) {
+      if (lane == 0) atomicExch(err, 1u);
+      return;
     }
-    if (lane == 0 && i0 + r < rows) {
-      const int64_t o = 2 * (int64_t(i0 + r) * hst + c);
-      atomicAdd(t + o, double(tr[r]));
-      atomicAdd(t + o + 1, double(ti[r]));
-      atomicAdd(sq + o, double(sr[r]));
-      atomicAdd(sq + o + 1, double(si[r]));
+    const int seg = u % nseg, rg = (u / nseg) % nrg, c = u / (nseg * nrg);
+    const int64_t k0 = int64_t(seg) * kDtL;
+    const int nq = int(min(int64_t(kDtL), ldn - k0) >> 1);  // float4 (two complex) per slice
+    const int i0 = rg * kDtR, nr = min(kDtR, rows - i0);
+    const int r0 = kDtRW * warp;
+    if (r0 < nr) {
+      const unsigned char* sb = smem + size_t(st) * kDtSB;
+      const float4* xw = reinterpret_cast<const float4*>(sb + kDtR * kDtSliceB);
+      const float4* xq = reinterpret_cast<const float4*>(sb + (kDtR + 1) * kDtSliceB);
+      const float4* a[kDtRW];
+#pragma unroll
+      for (int r = 0; r < kDtRW; ++r)
+        a[r] = reinterpret_cast<const float4*>(sb + min(r0 + r, nr - 1) * kDtSliceB);  // repeats are discarded
+      float v[4 * kDtRW];
+#pragma unroll
+      for (int q = 0; q < 4 * kDtRW; ++q) v[q] = 0.f;
+#pragma unroll 4
+      for (int e = lane; e < nq; e += 32) {
+        const float4 x = xw[e], y = xq[e];
+#pragma unroll
+        for (int r = 0; r < kDtRW; ++r) {
+          const float4 b = a[r][e];
+          v[4 * r] += b.x * x.x + b.y * x.y + b.z * x.z + b.w * x.w;  // conj(V) w
+          v[4 * r + 1] += b.x * x.y - b.y * x.x + b.z * x.w - b.w * x.z;
+          v[4 * r + 2] += b.x * y.x + b.y * y.y + b.z * y.z + b.w * y.w;  // conj(V) q~
+          v[4 * r + 3] += b.x * y.y - b.y * y.x + b.z * y.w - b.w * y.z;
+        }
+      }
+      // lane (32 / (4 kDtRW)) q ends with the warp total of value q
+      WarpTransposeSum<4 * kDtRW>::run(v, lane, 16);
+      constexpr int SH = kDtRW == 1 ? 3 : (kDtRW == 2 ? 2 : 1);
+      if ((lane & ((1 << SH) - 1)) == 0) {
+        const int q = lane >> SH, r = q >> 2, kind = q & 3;
+        if (r0 + r < nr)
+          atomicAdd((kind < 2 ? t : sq) + 2 * (int64_t(i0 + r0 + r) * hst + c) + (kind & 1), double(v[0]));
+      }
     }
+    // release the stage: order this warp's shared reads before the next bulk write
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
   }
 }
 
@@ -470,10 +532,27 @@ __global__ void __launch_bounds__(256) k_xupdate32(const float* __restrict__ Z, 
   }
 }
 
-static void launch_dots2_32(const float* V, const float* w, int64_t ldn, int64_t ldv, int rows, int jq, double* t,
-                            double* sq, int nrhs, cudaStream_t s) {
-  dim3 g{nb(ldn, kDotSeg), nb(rows, 32), unsigned(nrhs)};
-  MTF_LAUNCH(KID_DOTS, s, launch_pdl(k_dots2_32, g, dim3(256), 0, s, V, w, ldn, ldv, rows, jq, t, sq, nrhs));
+static void launch_dots2_32(mtf_system sys, const float* V, const float* w, int64_t ldn, int64_t ldv, int rows,
+                            int jq, double* t, double* sq, int nrhs, cudaStream_t s) {
+  MTF_REQUIRE(ldn % 64 == 0 && ldv % 2 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(w) & 15) == 0,
+              MTF_ERR_ARG, "Krylov vectors must be 16-byte aligned with a stride of 64 entries");
+  const int64_t units = ((ldn + kDtL - 1) / kDtL) * ((rows + kDtR - 1) / kDtR) * nrhs;
+  if (units <= 0) return;
+  stream_prepare(sys, s);
+  // the shared-memory opt-in is set once per device, not on every launch
+  static std::atomic<uint64_t> opted{0};
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(opted.load(std::memory_order_relaxed) & bit)) {
+    MTF_CUDA(cudaFuncSetAttribute(k_dots_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kDtSmem)));
+    opted.fetch_or(bit);
+  }
+  const unsigned grid = unsigned(std::min<int64_t>(units, sys->mv_grid));
+  MTF_LAUNCH(KID_DOTS, s,
+             launch_pdl(k_dots_tma, dim3(grid), dim3((kDtCons + 1) * 32), kDtSmem, s, V, w, ldn, ldv, rows, jq, t, sq,
+                        nrhs, nrhs, sys->d_mv_ctl.p + 2));
 }
 
 // Arnoldi columns enqueued back to back before the host reads their
@@ -668,10 +747,10 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     MTF_REQUIRE(used <= G.h.n, MTF_ERR_ARG, "recycled space larger than the Hessenberg scratch");
     MTF_CUDA(cudaMemsetAsync(T1, 0, (used - nrhs) * sizeof(double), s));
     MTF_LAUNCH(KID_NORM, s, k_start32<<<dim3(nb(n, 256), unsigned(nrhs)), 256, 0, s>>>(r_dev, n, SS0, G.w.p, ldn));
-    launch_dots2_32(G.V.p, G.w.p, ldn, ldv, kr, 0, T1, S1, nrhs, s);
+    launch_dots2_32(sys, G.V.p, G.w.p, ldn, ldv, kr, 0, T1, S1, nrhs, s);
     MTF_LAUNCH(KID_AXPY, s, k_proj32<<<ga, 256, 0, s>>>(G.V.p, T1, kr, nrhs, ldn, ldv, G.w.p, SS1));
     MTF_CUDA(cudaMemsetAsync(S1, 0, 2 * size_t(kr) * nrhs * sizeof(double), s));
-    launch_dots2_32(G.V.p, G.w.p, ldn, ldv, kr, 0, T2, S1, nrhs, s);
+    launch_dots2_32(sys, G.V.p, G.w.p, ldn, ldv, kr, 0, T2, S1, nrhs, s);
     MTF_LAUNCH(KID_AXPY, s, k_proj32<<<ga, 256, 0, s>>>(G.V.p, T2, kr, nrhs, ldn, ldv, G.w.p, SS2));
     MTF_LAUNCH(KID_NORM, s, k_scale32<<<gs, 256, 0, s>>>(G.w.p, ldn, SS2, NRM, G.V.p + 2 * size_t(kr) * ldn, ldv));
     MTF_CUDA(cudaMemcpyAsync(G.h_host, G.h.p, used * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -745,7 +824,7 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       double* C = S + 2 * size_t(j + 1) * nrhs;
       double* NRM = C + 4 * size_t(nrhs);
       double* SS = NRM + 2 * size_t(nrhs);
-      launch_dots2_32(G.V.p, G.w.p, ldn, ldv, j + 1, j, T, S, nrhs, s);
+      launch_dots2_32(sys, G.V.p, G.w.p, ldn, ldv, j + 1, j, T, S, nrhs, s);
       MTF_LAUNCH(KID_AXPY, s,
                  launch_pdl(k_axpy2_32, ga, dim3(256), size_t(2 * j) * sizeof(float2), s, G.V.p, T, S, C, j, kr,
                             nrhs, ldn, ldv, G.w.p, SS));

@@ -175,10 +175,6 @@ __device__ __forceinline__ void st_row_fma(float* v, const unsigned char* rowp, 
   }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // unit record: {N of the block, global row of the unit's first row, first
 // input column (dof offset of the block + first column of the piece),
 // len | piece << 12 | rows << 24 (rows <= 64)}; usrc: entry offset of the
