@@ -13,14 +13,16 @@ is the unbounded exterior.  This is the "normal from min(i,j) to max(i,j)"
 orientation of the skeleton mesh described in Sec. 3.2 of the paper.
 """
 from .meshes import (icosphere, uv_sphere, split_sphere, cube_partition, two_disjoint_cubes,
-                     cut_sphere, Mesh)
+                     cut_sphere, grid_partition, concentric_cuboids, Mesh)
 from .waves import fibonacci_directions, orthonormal_polarizations, plane_wave_batch
 from .configs import (config_sphere, config_split_sphere, config_cube2,
-                      config_cube4, config_batch_instances, CONFIG_NAMES)
+                      config_cube4, config_batch_instances, config_concentric_cuboids, cuboid_radii,
+                      CONFIG_NAMES)
 
 __all__ = [
     "Mesh", "icosphere", "uv_sphere", "split_sphere", "cube_partition", "two_disjoint_cubes",
-    "cut_sphere", "fibonacci_directions", "orthonormal_polarizations",
+    "cut_sphere", "grid_partition", "concentric_cuboids", "fibonacci_directions", "orthonormal_polarizations",
     "plane_wave_batch", "config_sphere", "config_split_sphere", "config_cube2",
-    "config_cube4", "config_batch_instances", "CONFIG_NAMES",
+    "config_cube4", "config_batch_instances", "config_concentric_cuboids", "cuboid_radii",
+    "CONFIG_NAMES",
 ]

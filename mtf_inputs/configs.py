@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .meshes import icosphere, split_sphere, cube_partition, cut_sphere, random_rotation
+from .meshes import icosphere, split_sphere, cube_partition, cut_sphere, random_rotation, concentric_cuboids
 from .waves import plane_wave_batch
 
 CONFIG_NAMES = ("sphere", "split_sphere", "cube2", "batch_instances", "cube4")
@@ -84,3 +84,24 @@ def config_batch_instances(n_inst: int = 32, seed: int = 0, tri_range=(500, 5000
         out.append(dict(name=f"inst{q}", mesh=mesh, k0=k0, eps_r=eps,
                         mu_r=np.ones(mesh.n_domains), dirs=dirs, pols=pols))
     return out
+
+
+def cuboid_radii(M: int):
+    """Radius vector [0, r_1, ..., r_M = 1.7] of the M concentric cuboids:
+    r_1 = 0.5 and the outer radii equally spaced up to 1.7 (M = 2 gives
+    [0, 0.5, 1.7]); M = 1 is the undivided scatterer [0, 1.7]."""
+    if M == 1:
+        return [0.0, 1.7]
+    return [0.0] + [float(v) for v in np.linspace(0.5, 1.7, M)]
+
+
+def config_concentric_cuboids(M: int = 1, h: float = 0.18, k0: float = 3.0, eps: float = 2.0):
+    """The scatterer (-1.7, 1.7)^2 x (0, 1) divided into M concentric cuboids
+    (square rings), every ring with eps_r = eps and mu_r = 1 (k_i = k0
+    sqrt(eps) = 4.24 at the defaults), structured grid of spacing <= h
+    (h = 0.18 gives 2,356 skeleton triangles, 14,136 unknowns at M = 1); one
+    z-polarised plane wave travelling along +x."""
+    mesh = concentric_cuboids(cuboid_radii(M), h)
+    return dict(name=f"cuboids_M{M}_h{h:g}", mesh=mesh, k0=k0,
+                eps_r=np.array([1.0] + [eps] * M), mu_r=np.ones(M + 1),
+                dirs=np.array([[1.0, 0.0, 0.0]]), pols=np.array([[0.0, 0.0, 1.0]], dtype=np.complex128))

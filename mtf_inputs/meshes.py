@@ -423,6 +423,87 @@ def cube_partition(P=(2, 2, 2), n: int = 9, size=(1.0, 1.0, 1.0), origin=(0.0, 0
                 name or f"cube{P[0]}x{P[1]}x{P[2]}n{n}")
 
 
+def grid_partition(xs, ys, zs, cell_labels, name: str = "") -> Mesh:
+    """Box [xs[0], xs[-1]] x [ys[0], ys[-1]] x [zs[0], zs[-1]] on the grid of
+    the given (increasing) coordinates; cell_labels[i, j, k] is the subdomain
+    of cell (xs[i]..xs[i+1]) x (ys[j]..ys[j+1]) x (zs[k]..zs[k+1]), and the
+    space outside the box is subdomain 0.  Every grid face between cells of
+    different subdomains becomes two triangles (the rectangle cut along its
+    diagonal), so the skeleton is conforming by construction."""
+    coords = [np.asarray(xs, dtype=np.float64), np.asarray(ys, dtype=np.float64), np.asarray(zs, dtype=np.float64)]
+    cell_labels = np.asarray(cell_labels)
+    L = [len(c) - 1 for c in coords]
+    assert cell_labels.shape == tuple(L)
+    pool = _VertexPool()
+
+    def vid(ijk):
+        return pool.get(tuple(ijk), [coords[d][ijk[d]] for d in range(3)])
+
+    tris, labs, want = [], [], []
+    for d in range(3):
+        e1, e2 = (d + 1) % 3, (d + 2) % 3
+        for k in range(L[d] + 1):
+            for i in range(L[e1]):
+                for j in range(L[e2]):
+                    def lab(c):
+                        if c < 0 or c >= L[d]:
+                            return 0
+                        idx = [0, 0, 0]
+                        idx[d], idx[e1], idx[e2] = c, i, j
+                        return int(cell_labels[tuple(idx)])
+
+                    lb, la = lab(k - 1), lab(k)
+                    if lb == la:
+                        continue
+                    corners = []
+                    for (di, dj) in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        ijk = [0, 0, 0]
+                        ijk[d], ijk[e1], ijk[e2] = k, i + di, j + dj
+                        corners.append(vid(ijk))
+                    a, b = min(lb, la), max(lb, la)
+                    nd = np.zeros(3)
+                    nd[d] = 1.0 if lb == a else -1.0  # from subdomain a into b
+                    for t in ((corners[0], corners[1], corners[2]), (corners[0], corners[2], corners[3])):
+                        tris.append(t)
+                        labs.append((a, b))
+                        want.append(nd)
+    V = pool.array()
+    F = _orient(V, np.array(tris, dtype=np.int64), np.array(want))
+    return Mesh(V, F.astype(np.int32), np.array(labs, dtype=np.int32), int(cell_labels.max()) + 1, name)
+
+
+def _graded(breaks, h):
+    """Grid coordinates through the given breakpoints, each interval split
+    into ceil(length / h) equal pieces."""
+    out = [float(breaks[0])]
+    for a, b in zip(breaks[:-1], breaks[1:]):
+        n = max(1, int(math.ceil((b - a) / h - 1e-9)))
+        out.extend(float(a + (b - a) * q / n) for q in range(1, n + 1))
+    return np.array(out)
+
+
+def concentric_cuboids(radii, h: float, half_width: float = 1.7, height: float = 1.0) -> Mesh:
+    """The scatterer (-w, w)^2 x (0, height), w = half_width, divided into
+    M = len(radii) - 1 concentric cuboids: subdomain i (1..M) is the square
+    ring r_{i-1} < max(|x|, |y|) < r_i, 0 < z < height, for the radius vector
+    radii = [0, r_1, ..., r_M = w].  Structured grid with breakpoints at +-r_i
+    and spacing at most h."""
+    r = [float(v) for v in radii]
+    assert r[0] == 0.0 and abs(r[-1] - half_width) < 1e-12 and all(b > a for a, b in zip(r[:-1], r[1:]))
+    M = len(r) - 1
+    breaks = sorted({-v for v in r[1:]} | {v for v in r[1:]})
+    xs = _graded(breaks, h)
+    zs = _graded([0.0, height], h)
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    lab = np.zeros((len(xc), len(xc), len(zs) - 1), dtype=np.int64)
+    for i, x in enumerate(xc):
+        for j, y in enumerate(xc):
+            m = max(abs(x), abs(y))
+            lab[i, j, :] = 1 + int(np.searchsorted(np.array(r[1:-1]), m))
+    assert lab.max() == M
+    return grid_partition(xs, xs, zs, lab, name=f"cuboids_M{M}_h{h:g}")
+
+
 def two_disjoint_cubes(n: int = 2, gap: float = 1.0) -> Mesh:
     """Two unit cubes separated by ``gap`` along x (Table 2, 'dielectric')."""
     A = cube_partition((1, 1, 1), n, origin=(0.0, 0.0, 0.0), cell_labels=np.array([[[1]]]))

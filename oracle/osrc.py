@@ -27,14 +27,19 @@ the design notes; the CUDA library implements the same operator):
       B_j = e^{-i theta} b_j / (1 + b_j (e^{-i theta} - 1)).
 * Damping eps = c k^{1/3} R^{-2/3} (c = 0.39, R the radius of the sphere with
   the area of Gamma_i), the curvature-based choice of the OSRC literature.
-* Discretisation on RWG_i (closed, genus-0 Gamma_i): the RWG space splits
-  G-orthogonally into the irrotational part (generalised eigenpairs
-  D v = lambda G v with lambda > 0, D the div-div and G the mass matrix;
-  |xi|^2 = lambda) and the loop part, the RWG images u = L phi of nodal P1
-  functions (u = n x grad phi exactly, L[e, lo] = 1/l_e, L[e, hi] = -1/l_e),
-  whose eigenpairs S phi = mu M phi (P1 stiffness S, mass M; |xi|^2 = mu)
-  give G-orthonormal loop modes L phi / sqrt(mu) (L^T G L = S).  With W the
-  G-orthonormal basis of both parts and f the matching symbols,
+* Discretisation on RWG_i (closed, connected Gamma_i of genus g): the RWG
+  space splits G-orthogonally into the irrotational part (generalised
+  eigenpairs D v = lambda G v with lambda > 0, D the div-div and G the mass
+  matrix; |xi|^2 = lambda), the loop part, the RWG images u = L phi of nodal
+  P1 functions (u = n x grad phi exactly, L[e, lo] = 1/l_e,
+  L[e, hi] = -1/l_e), whose eigenpairs S phi = mu M phi (P1 stiffness S,
+  mass M; |xi|^2 = mu) give G-orthonormal loop modes L phi / sqrt(mu)
+  (L^T G L = S), and, when g > 0, the 2 g discrete harmonic fields: the part
+  of the kernel of D that is G-orthogonal to the loops (by Euler's formula
+  its dimension is N - (T - 1) - (V - 1) = 2 g).  Harmonic fields are both
+  divergence- and curl-free, so their symbol is the loop symbol at
+  |xi|^2 = 0; T~ does not depend on the basis chosen for them.  With W the
+  G-orthonormal basis of all parts and f the matching symbols,
       T~ = W diag(f) W^T,
   which maps tested vectors to coefficients (W W^T = G^{-1}); the Pade
   approximant is applied exactly on every mode instead of through auxiliary
@@ -124,6 +129,7 @@ class BlockOSRC:
         self.sk = sk
         self.rho = np.asarray(rho)
         self.Ttil = []
+        self.nh, self.W = [], []
         for i in range(sk.n_domains):
             G = mass_matrix(sk, i)
             D = divdiv_matrix(sk, i)
@@ -131,15 +137,25 @@ class BlockOSRC:
             nirr = len(sk.tris[i]) - 1                 # rank of div on RWG_i
             verts, pos, S, M = p1_matrices(sk, i)
             mu, Phi = scipy.linalg.eigh(S, M)
-            if nirr + len(verts) - 1 != sk.N[i]:
-                raise ValueError("block-OSRC needs genus-0 subdomain boundaries")
+            nh = sk.N[i] - nirr - (len(verts) - 1)      # 2 g harmonic fields
+            if nh < 0 or nh % 2:
+                raise ValueError("block-OSRC needs connected subdomain boundaries")
             U = loop_map(sk, i, pos) @ Phi[:, 1:] / np.sqrt(mu[1:])[None, :]
+            if nh:
+                K = V[:, :sk.N[i] - nirr]                # kernel of D (G-orthonormal)
+                R = K - U @ (U.T @ G @ K)                # its part G-orthogonal to the loops
+                s2, Q = scipy.linalg.eigh(R.T @ G @ R)   # nh eigenvalues 1, the rest 0
+                H = R @ Q[:, -nh:] / np.sqrt(s2[-nh:])[None, :]
+                U = np.concatenate([U, H], axis=1)
+                mu = np.concatenate([mu, np.zeros(nh)])
             area = float(np.sum(sk.area[sk.tris[i]]))
             keps = k[i] + 1j * damping(k[i], area, eps_scale)
             f_irr = 2 * k[i] / (keps * pade_sqrt(-lam[-nirr:] / keps ** 2, Np, theta))
             f_sol = (2 * keps / k[i]) * pade_sqrt(-mu[1:] / keps ** 2, Np, theta)
             W = np.concatenate([V[:, -nirr:], U], axis=1)
             f = np.concatenate([f_irr, f_sol])
+            self.nh.append(nh)
+            self.W.append(W)
             self.Ttil.append((W * f[None, :]) @ W.T)
 
     def apply(self, r):
