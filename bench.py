@@ -234,6 +234,71 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_cuboid_study(args):
+    """The concentric-cuboid workload of the paper's Sec. 5.4 (Table 3) on one
+    GPU: for M = 1..args.study_m square rings on the grid of spacing
+    args.study_h, one JSON line each with the sizes, GMRES iterations, the
+    times of the paper's columns (one-time setup, assembly of M and P, solve,
+    100 applies of M and of P) and the relative L2([0, pi]) error of RCS_z
+    against M = 1 on the finer grid args.study_href (the first line)."""
+    import torch
+    from paper_2502_10907_gb300.build import build
+    build()
+    from paper_2502_10907_gb300 import api, _lib as L
+    torch.cuda.set_device(0)
+    th = np.linspace(0.0, np.pi, 181)
+    obs = np.stack([np.cos(th), np.sin(th), 0 * th], axis=1)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0
+
+    def rcs_z(s, x):
+        f = s.farfield(x, obs).cpu().numpy()
+        return np.abs(f[0, :, 2]) ** 2
+
+    def run(M, h, tol):
+        cfg = mi.config_concentric_cuboids(M, h=h)
+        t0 = time.perf_counter()
+        mesh = api.Mesh.from_inputs(cfg["mesh"])
+        t_mesh = time.perf_counter() - t0
+        sysg, _, t_setup = timed(lambda: api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1,
+                                                     precond=L.MTF_PRECOND_OSRC, tol=tol, restart=args.restart,
+                                                     max_iter=args.study_max_iter, osrc_np=args.osrc_np))
+        _, t_asm, _ = timed(lambda: sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"]))
+        sysg.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)  # warm-up (scratch allocation)
+        (x, st), t_solve, _ = timed(lambda: sysg.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False))
+        xr = torch.randn(1, mesh.n_total, dtype=torch.complex64, device="cuda")
+        _, t_mv, _ = timed(lambda: sysg.matvec_f32(xr), 100)
+        _, t_pc, _ = timed(lambda: sysg.precond_f32(xr), 100)
+        Ns = [int(v) for v in mesh.n_dofs]
+        out = dict(M=M, h=h, triangles=int(cfg["mesh"].nt), N=int(mesh.n_total), n_gmres=int(st.iterations),
+                   refinements=int(st.refinements), converged=bool(st.converged), rel_residual=float(st.rel_residual),
+                   t_setup_s=round(t_setup, 4), t_assembly_s=round(t_asm, 4), t_solver_s=round(t_solve, 4),
+                   t_matvec_M_100_s=round(t_mv, 4), t_matvec_P_100_s=round(t_pc, 4),
+                   dense_entries_M=int(sum(n * n for n in Ns)), t_mesh_host_s=round(t_mesh, 3))
+        rc = rcs_z(sysg, x)
+        del sysg, mesh
+        torch.cuda.empty_cache()
+        return out, rc
+
+    ref, rc_ref = run(1, args.study_href, 1e-7)
+    ref["role"] = "reference (M = 1, fine grid)"
+    print(json.dumps(ref), flush=True)
+    for M in range(1, args.study_m + 1):
+        out, rc = run(M, args.study_h, args.study_tol)
+        out["rcs_z_rel_l2_err"] = float(np.linalg.norm(rc - rc_ref) / np.linalg.norm(rc_ref))
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,7 +320,16 @@ def main():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-accuracy-gate", action="store_true",
                     help="skip the tight-tolerance FP64 reference solve (profiling runs)")
+    ap.add_argument("--study", default="", choices=["", "cuboids"],
+                    help="instead of the benchmark: the concentric-cuboid study (one JSON line per M)")
+    ap.add_argument("--study-m", type=int, default=6)
+    ap.add_argument("--study-h", type=float, default=0.18)
+    ap.add_argument("--study-href", type=float, default=0.09)
+    ap.add_argument("--study-tol", type=float, default=1e-5)
+    ap.add_argument("--study-max-iter", type=int, default=8000)
     args = ap.parse_args()
+    if args.study == "cuboids":
+        return run_cuboid_study(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)

@@ -102,9 +102,11 @@ __global__ void k_p1_matrices(const double* __restrict__ bt_v, const double* __r
 }
 
 // W (column-major, N x N per block): columns j < nirr the irrotational
-// eigenvectors V[:, N - nirr + j]; columns nirr + k the loop modes
-// L Phi[:, k+1] / sqrt(mu_{k+1}), L[e, lo] = 1/l_e, L[e, hi] = -1/l_e.
-// eig[row_off + j] receives the matching |xi|^2.
+// eigenvectors V[:, N - nirr + j]; columns nirr + k (k < nv - 1) the loop
+// modes L Phi[:, k+1] / sqrt(mu_{k+1}), L[e, lo] = 1/l_e, L[e, hi] = -1/l_e;
+// the remaining 2 g columns (harmonic fields of a genus-g boundary) are
+// zeroed here and filled by osrc_harmonic.  eig[row_off + j] receives the
+// matching |xi|^2 (0 for the harmonic fields).
 __global__ void k_build_w(const float* __restrict__ V, const float* __restrict__ lam, const float* __restrict__ Phi,
                           const float* __restrict__ mu, const int32_t* __restrict__ edge_lohi,
                           const double* __restrict__ edge_len, int N, int nirr, int nv, float* __restrict__ W,
@@ -116,6 +118,9 @@ __global__ void k_build_w(const float* __restrict__ V, const float* __restrict__
   if (j < nirr) {
     v = V[int64_t(N - nirr + j) * N + e];
     if (e == 0) eig[j] = lam[N - nirr + j];
+  } else if (j >= nirr + nv - 1) {
+    v = 0.f;
+    if (e == 0) eig[j] = 0.f;
   } else {
     const int k = j - nirr + 1;
     const float* ph = Phi + int64_t(k) * nv;
@@ -301,6 +306,72 @@ static cusolverDnHandle_t solver_handle() {
   return h;
 }
 
+// The 2 g harmonic fields of a genus-g boundary (the part of the kernel of
+// the div-div pencil that is G-orthogonal to the loop modes): with K the
+// first m = N - nirr (G-orthonormal) eigenvectors of (D, G), U the nloop
+// loop modes (columns nirr .. nirr + nloop - 1 of W) and R = K - U (U^T G K),
+// the m x m matrix R^T G R has eigenvalue 1 on the nh harmonic directions
+// and 0 on the loop ones; its top nh eigenvectors Y give the G-orthonormal
+// harmonic fields R Y / sqrt(sigma), written into the last nh columns of W.
+// G is a copy of the mass matrix (the div-div eigensolver overwrites its
+// own).  cuBLAS / cuSOLVER on the stream, FP32 like the rest of the setup.
+static void osrc_harmonic(int N, int nirr, int nloop, int nh, const float* K, const float* G, float* W,
+                          cusolverDnHandle_t sh, cudaStream_t s) {
+  const int m = N - nirr;
+  cublasHandle_t bh = blas_handle();
+  MTF_REQUIRE(cublasSetStream(bh, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
+  DevBuf<float> GK, X, R, Q, w;
+  GK.alloc(size_t(N) * m);
+  X.alloc(size_t(std::max(nloop, 1)) * m);
+  R.alloc(size_t(N) * m);
+  Q.alloc(size_t(m) * m);
+  w.alloc(size_t(m));
+  const float one = 1.f, zero = 0.f, mone = -1.f;
+  const float* U = W + size_t(nirr) * N;
+  auto gemm = [&](cublasOperation_t ta, int rows, int cols, int inner, float alpha, const float* Ap, int lda,
+                  const float* Bp, int ldb, float beta, float* Cp, int ldc) {
+    MTF_REQUIRE(cublasSgemm(bh, ta, CUBLAS_OP_N, rows, cols, inner, &alpha, Ap, lda, Bp, ldb, &beta, Cp, ldc) ==
+                    CUBLAS_STATUS_SUCCESS,
+                MTF_ERR_CUDA, "cublasSgemm failed (harmonic fields)");
+  };
+  gemm(CUBLAS_OP_N, N, m, N, one, G, N, K, N, zero, GK.p, N);  // G K
+  MTF_CUDA(cudaMemcpyAsync(R.p, K, size_t(N) * m * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (nloop > 0) {
+    gemm(CUBLAS_OP_T, nloop, m, N, one, U, N, GK.p, N, zero, X.p, nloop);  // U^T G K
+    gemm(CUBLAS_OP_N, N, m, nloop, mone, U, N, X.p, nloop, one, R.p, N);   // R = K - U X
+  }
+  gemm(CUBLAS_OP_N, N, m, N, one, G, N, R.p, N, zero, GK.p, N);       // G R
+  gemm(CUBLAS_OP_T, m, m, N, one, R.p, N, GK.p, N, zero, Q.p, m);     // R^T G R
+  int lwork = 0;
+  MTF_REQUIRE(cusolverDnSsyevd_bufferSize(sh, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, Q.p, m, w.p,
+                                          &lwork) == CUSOLVER_STATUS_SUCCESS,
+              MTF_ERR_CUDA, "cusolverDnSsyevd_bufferSize failed");
+  DevBuf<float> work;
+  work.alloc(size_t(std::max(lwork, 1)));
+  DevBuf<int> info;
+  info.alloc(1);
+  MTF_REQUIRE(cusolverDnSsyevd(sh, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, Q.p, m, w.p, work.p, lwork,
+                               info.p) == CUSOLVER_STATUS_SUCCESS,
+              MTF_ERR_CUDA, "cusolverDnSsyevd failed");
+  std::vector<float> wh(static_cast<size_t>(m));
+  int hinfo = 0;
+  MTF_CUDA(cudaMemcpyAsync(wh.data(), w.p, size_t(m) * sizeof(float), cudaMemcpyDeviceToHost, s));
+  MTF_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MTF_CUDA(cudaStreamSynchronize(s));
+  MTF_REQUIRE(hinfo == 0, MTF_ERR_CUDA, "harmonic-field eigensolver failed (info " + std::to_string(hinfo) + ")");
+  // nh eigenvalues near 1 above m - nh near 0: the dimension count holds
+  MTF_REQUIRE(wh[size_t(m - nh)] > 0.5f && (m == nh || wh[size_t(m - nh - 1)] < 0.5f), MTF_ERR_MESH,
+              "harmonic fields of a subdomain boundary not separated from its loop modes");
+  float* H = W + size_t(nirr + nloop) * N;
+  gemm(CUBLAS_OP_N, N, nh, m, one, R.p, N, Q.p + size_t(m - nh) * m, m, zero, H, N);  // R Y
+  for (int k = 0; k < nh; ++k) {
+    const float sc = 1.f / std::sqrt(wh[size_t(m - nh + k)]);
+    MTF_REQUIRE(cublasSscal(bh, N, &sc, H + size_t(k) * N, 1) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
+                "cublasSscal failed");
+  }
+  MTF_CUDA(cudaStreamSynchronize(s));  // scratch is freed on return
+}
+
 // mesh-level eigenpairs of (D, G) for every block (once per mesh)
 static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   if (m->osrc_ready) return;
@@ -359,10 +430,18 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   DevBuf<float> Wtmp;
   for (int i = 0; i < m->nd; ++i) {
     const int N = m->blk[i].N, nv = m->p1_n[i];
-    const int nirr = m->blk[i].T - 1;
-    MTF_REQUIRE(nirr + nv - 1 == N, MTF_ERR_MESH,
-                "block-OSRC needs genus-0 subdomain boundaries (Gamma_" + std::to_string(i) + ")");
+    const int nirr = m->blk[i].T - 1, nloop = nv - 1;
+    // a connected boundary of genus g: N = nirr + nloop + 2 g (Euler)
+    const int nh = N - nirr - nloop;
+    MTF_REQUIRE(nh >= 0 && nh % 2 == 0, MTF_ERR_MESH,
+                "block-OSRC needs connected subdomain boundaries (Gamma_" + std::to_string(i) + ")");
     float* A = Dd.p + m->blk[i].mat_off;
+    DevBuf<float> Gc;  // the mass matrix, kept for the harmonic fields
+    if (nh > 0) {
+      Gc.alloc(size_t(N) * N);
+      MTF_CUDA(cudaMemcpyAsync(Gc.p, G.p + m->blk[i].mat_off, size_t(N) * N * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s));
+    }
     sygvd(N, A, G.p + m->blk[i].mat_off, lam_tmp.p + m->blk[i].row_off, "the div-div pencil of block " + std::to_string(i));
     sygvd(nv, S1.p + m->p1_off_h[i], M1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
           "the Laplace-Beltrami pencil of block " + std::to_string(i));
@@ -372,6 +451,7 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
         A, lam_tmp.p + m->blk[i].row_off, S1.p + m->p1_off_h[i], mu.p + m->p1_row_h[i],
         m->d_edge_lohi.p + 2 * m->blk[i].row_off, m->d_edge_len.p + m->blk[i].row_off, N, nirr, nv, Wtmp.p,
         m->d_osrc_lam.p + m->blk[i].row_off));
+    if (nh > 0) osrc_harmonic(N, nirr, nloop, nh, A, Gc.p, Wtmp.p, h, s);
     // padded row-major W^T (rows = modes), ld = N rounded up to 4: the
     // column-major W (rows = RWG dofs) with leading dimension ld
     const int ld = (N + 3) & ~3;
