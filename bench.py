@@ -271,7 +271,7 @@ def run_cuboid_study(args):
         mesh = api.Mesh.from_inputs(cfg["mesh"])
         t_mesh = time.perf_counter() - t0
         sysg, _, t_setup = timed(lambda: api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1,
-                                                     precond=L.MTF_PRECOND_OSRC, tol=tol, restart=args.restart,
+                                                     precond=L.MTF_PRECOND_OSRC, tol=tol, restart=args.study_restart,
                                                      max_iter=args.study_max_iter, osrc_np=args.osrc_np))
         _, t_asm, _ = timed(lambda: sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"]))
         sysg.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)  # warm-up (scratch allocation)
@@ -326,7 +326,10 @@ def main():
     ap.add_argument("--study-h", type=float, default=0.18)
     ap.add_argument("--study-href", type=float, default=0.09)
     ap.add_argument("--study-tol", type=float, default=1e-5)
-    ap.add_argument("--study-max-iter", type=int, default=8000)
+    ap.add_argument("--study-max-iter", type=int, default=12000)
+    # restarted at 500 the M >= 4 solves stall; a 4,000-column FP32 basis
+    # (2.8 GB at M = 6) lets them converge
+    ap.add_argument("--study-restart", type=int, default=4000)
     args = ap.parse_args()
     if args.study == "cuboids":
         return run_cuboid_study(args)
