@@ -9,8 +9,7 @@ import mtf_inputs as mi
 from oracle.mie import mie_farfield, mie_coefficients, _riccati_bessel, _riccati_hankel
 from oracle.mtf import MTFSystem
 from oracle.quadrature import gauss_legendre
-from oracle.operators import triangle_points, _rwg_data
-from tests.oracle_helpers import skeleton_of, sphere_system, rcs_plane
+from tests.oracle_helpers import skeleton_of, sphere_system, rcs_plane, jump_l2
 
 
 def _sphere_dirs(nt=16, nph=32):
@@ -93,29 +92,6 @@ def _split_system(cache, rings, eps2=2.0):
     return cache[key]
 
 
-def _jump_l2(sk, x, i, j):
-    """Relative L2 norm over Gamma_ij of the Dirichlet and Neumann jumps
-    u_i + u_j (the transmission conditions make the fields opposite)."""
-    lo, hi = min(i, j), max(i, j)
-    tris = np.where((sk.L[:, 0] == lo) & (sk.L[:, 1] == hi))[0]
-    X, W = triangle_points(sk, tris)
-    out = []
-    for slot in (0, 1):
-        fields = []
-        for dom in (i, j):
-            pos = {t: p for p, t in enumerate(sk.tris[dom])}
-            loc = np.array([pos[t] for t in tris])
-            c, v = _rwg_data(sk, dom, loc)
-            sl = sk.block_slices(dom)[slot]
-            coef = x[sl, 0][sk.dof[dom][loc]]
-            f = c[:, :, None, None] * (X[:, None] - v[:, :, None, :])
-            fields.append(np.einsum("ta,taqn->tqn", coef, f))
-        jump = fields[0] + fields[1]
-        nrm = lambda u: np.sqrt(np.sum(W * np.sum(np.abs(u) ** 2, axis=-1)))
-        out.append(nrm(jump) / nrm(fields[0]))
-    return out
-
-
 def test_mtf2_triple_junction_matches_mie_and_jumps_converge(oracle_cache):
     """MTF(2): the sphere split in two halves with the same material (the
     paper's Sec. 5.2 experiment) must reproduce the Mie far field, and the
@@ -126,7 +102,7 @@ def test_mtf2_triple_junction_matches_mie_and_jumps_converge(oracle_cache):
         obs = rcs_plane()
         F = sysm.farfield(x, obs)[:, :, 0]
         Fm = mie_farfield(1.0, 1.0, 2.0, d[0], p[0], obs)
-        res.append((np.linalg.norm(F - Fm) / np.linalg.norm(Fm),) + tuple(_jump_l2(sk, x, 1, 2)))
+        res.append((np.linalg.norm(F - Fm) / np.linalg.norm(Fm),) + tuple(jump_l2(sk, x, 1, 2)))
     (e3, jd3, jn3), (e5, jd5, jn5) = res
     assert e3 < 0.15 and e5 < 0.06, res
     assert e5 < 0.5 * e3 and jd5 < 0.7 * jd3 and jn5 < 0.7 * jn3, res
