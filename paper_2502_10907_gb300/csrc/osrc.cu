@@ -29,6 +29,13 @@
 #include <mutex>
 
 #include "stream.cuh"
+#include "stream_tc.cuh"
+
+// FP16 T~ applies on the tensor cores (stream_tc.cuh); 0 keeps the FMA
+// stream of stream.cuh for them
+#ifndef MTF_OSRC_TC
+#define MTF_OSRC_TC 1
+#endif
 
 namespace mtf {
 
@@ -481,7 +488,10 @@ static void osrc_half_copy(mtf_system sys, cudaStream_t s) {
     m->os16_off_h[i] = off;
     off += int64_t(m->blk[i].N) * st_row_stride<3>(m->blk[i].N);
   }
-  sys->d_osrc_T16.alloc(size_t(off));
+  // 8 zeroed entries of slack: the tensor-core stream copies whole k16
+  // chunks, up to 4 entries past the last row
+  sys->d_osrc_T16.alloc(size_t(off) + 8);
+  MTF_CUDA(cudaMemsetAsync(sys->d_osrc_T16.p + off, 0, 8 * sizeof(uint32_t), s));
   DevBuf<unsigned> mx;
   mx.alloc(size_t(m->nd));
   MTF_CUDA(cudaMemsetAsync(mx.p, 0, size_t(m->nd) * sizeof(unsigned), s));
@@ -607,7 +617,10 @@ static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int6
   const StreamUnits& su = ENT == 3 ? m->os16_units : m->os_units;
   const void* ent = ENT == 3 ? static_cast<const void*>(sys->d_osrc_T16.p) : static_cast<const void*>(sys->d_osrc_T.p);
   const float* cf = ENT == 3 ? sys->d_os_coef16.p : sys->d_rho32.p;
-  launch_stream_tiles<NC, ENT>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
+  if (ENT == 3 && MTF_OSRC_TC)
+    launch_stream_tc<NC>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
+  else
+    launch_stream_tiles<NC, ENT>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
   MTF_LAUNCH(KID_OSCOMBINE, s,
              launch_pdl(k_os_combine<NC, ZT, ADJ, ENT>, dim3(unsigned((m->n_rows * 32 + 255) / 256)), dim3(256), 0,
                         s, sys->d_os_part.p, su.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p,

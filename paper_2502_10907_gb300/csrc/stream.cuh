@@ -49,7 +49,7 @@ namespace mtf {
 #define MTF_ST_PIECE_BYTES1 4096
 #endif
 #ifndef MTF_ST_PIECE_BYTES3
-#define MTF_ST_PIECE_BYTES3 3072
+#define MTF_ST_PIECE_BYTES3 2560
 #endif
 // consumer warps and rows per consumer warp for the 8- and 4-byte entry
 // types (the 16-byte {T, K} entries use 8 warps of two rows).  Measured on
