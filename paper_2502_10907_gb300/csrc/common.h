@@ -116,7 +116,21 @@ struct StreamUnits {
   int32_t pmax = 1;
   DevBuf<int4> d_units;
   DevBuf<int64_t> d_src;
+  // tiled copy of the operator (one contiguous run per unit): byte offset of
+  // every unit and the total size
+  DevBuf<int64_t> d_toff;
+  int64_t tiled_bytes = 0;
 };
+
+// row pitch (bytes) of a unit in the tiled copy of a streamed operator with
+// eb-byte entries: 4-byte entries (the tensor-core stream) in whole 8-entry
+// chunks, padded to 16 bytes past a 128-byte multiple so that the rows an
+// ldmatrix phase reads fall in distinct shared-memory banks; others in
+// 16-byte words
+__host__ __device__ inline int st_tile_pitch(int eb, int len) {
+  if (eb == 4) return ((len + 7) / 8 * 32 + 127) / 128 * 128 + 16;
+  return (len * eb + 15) / 16 * 16;
+}
 
 }  // namespace mtf
 
@@ -197,6 +211,7 @@ struct mtf_system_s {
   mtf::DevBuf<float> d_osrc_f, d_osrc_r32;   // OSRC symbol (complex) and apply scratch
   mtf::DevBuf<float> d_osrc_T;               // complex T~ of every block (rows of N_i, at the blocks' mat_off)
   mtf::DevBuf<uint32_t> d_osrc_T16;          // FP16 (__half2) copy of T~, scaled per block (osrc_half)
+  mtf::DevBuf<uint32_t> d_osrc_T16t;         // the same, tiled per stream unit (tensor-core stream)
   mtf::DevBuf<float> d_os_coef16;            // per block: s_i (rho, 1/rho) for the FP16 copy
   mtf::DevBuf<float> d_os_part;              // per-row piece sums of the OSRC apply
   mtf::DevBuf<double> d_cen;
@@ -295,6 +310,8 @@ void stream_prepare(mtf_system sys, cudaStream_t s);
 // copy of the units is 16-byte aligned.
 void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, const std::vector<int64_t>& blk_entry_off,
                         const std::vector<int64_t>& row_stride, StreamUnits& u, cudaStream_t s);
+// tiled copy (su.tiled_bytes) of a streamed operator with eb-byte entries
+void tile_stream_operator(const StreamUnits& su, const void* dense, int eb, void* tiled, cudaStream_t s);
 // One FGMRES cycle of the mixed path on M d = r from d = 0 (FP32 Krylov
 // basis, FP64 reductions), then x += d.  Stops when every right-hand side's
 // estimate reaches tol relative to ||r|| (reached = true), after the restart

@@ -149,7 +149,8 @@ void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, co
   MTF_REQUIRE(rows >= 1 && rows <= 64, MTF_ERR_ARG, "rows per stream unit out of range");
   const int q = 16 / entry_bytes;  // entries per 16 bytes
   std::vector<int4> u;
-  std::vector<int64_t> src;
+  std::vector<int64_t> src, toff;
+  int64_t tiled = 0;
   int pmax = 1;
   for (int i = 0; i < m->nd; ++i) {
     const int N = m->blk[i].N;
@@ -169,6 +170,8 @@ void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, co
         u.push_back(make_int4(N, int(m->blk[i].row_off + r0), int(m->blk[i].dof_off + c),
                               len | (p << 12) | (nr << 24)));
         src.push_back(blk_entry_off[i] + int64_t(r0) * ld + c);
+        toff.push_back(tiled);
+        tiled += int64_t(nr) * st_tile_pitch(entry_bytes, len);
       }
     }
   }
@@ -176,14 +179,47 @@ void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, co
               "mesh too large for the streaming tables");
   su.n_units = int64_t(u.size());
   su.pmax = pmax;
+  su.tiled_bytes = tiled;
   su.d_units.alloc(u.size());
   su.d_src.alloc(src.size());
+  su.d_toff.alloc(toff.size());
   if (!u.empty()) {
     MTF_CUDA(cudaMemcpyAsync(su.d_units.p, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     MTF_CUDA(cudaMemcpyAsync(su.d_src.p, src.data(), src.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(su.d_toff.p, toff.data(), toff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     MTF_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
   }
   su.ready = true;
+}
+
+// Tiled copy of a streamed operator: unit u's nrows rows at byte offset
+// toff[u] with the pitch st_tile_pitch(eb, len), each row the unit's entries
+// (whole 16-byte words of the dense row, which stay inside it: the units
+// table checks that) followed by zeros up to the pitch.  One CTA per unit.
+__global__ void k_tile_units(const unsigned char* __restrict__ dense, const int4* __restrict__ units,
+                             const int64_t* __restrict__ usrc, const int64_t* __restrict__ toff, int eb,
+                             unsigned char* __restrict__ tiled) {
+  const int u = blockIdx.x;
+  const int4 rec = units[u];
+  const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0xff;
+  const int pitch = st_tile_pitch(eb, len), words = pitch / 16, used = len * eb;
+  const int64_t ld = eb == 16 ? N : (eb == 8 ? N + (N & 1) : (N + 3) & ~3);
+  const int64_t src = usrc[u] * eb, dst = toff[u];
+  for (int t = threadIdx.x; t < nrows * words; t += blockDim.x) {
+    const int r = t / words, w = t - r * words;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (w * 16 < used) v = *reinterpret_cast<const uint4*>(dense + src + int64_t(r) * ld * eb + w * 16);
+    *reinterpret_cast<uint4*>(tiled + dst + int64_t(r) * pitch + w * 16) = v;
+  }
+}
+
+void tile_stream_operator(const StreamUnits& su, const void* dense, int eb, void* tiled, cudaStream_t s) {
+  MTF_REQUIRE(su.ready && (reinterpret_cast<uintptr_t>(dense) & 15) == 0 && (reinterpret_cast<uintptr_t>(tiled) & 15) == 0,
+              MTF_ERR_ARG, "tiled operator copy needs built units and 16-byte aligned buffers");
+  if (su.n_units == 0) return;
+  MTF_LAUNCH(KID_MISC, s, k_tile_units<<<unsigned(su.n_units), 256, 0, s>>>(
+      static_cast<const unsigned char*>(dense), su.d_units.p, su.d_src.p, su.d_toff.p, eb,
+      static_cast<unsigned char*>(tiled)));
 }
 
 void stream_prepare(mtf_system sys, cudaStream_t s) {

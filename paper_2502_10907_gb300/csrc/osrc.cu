@@ -476,6 +476,20 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   m->osrc_ready = true;
 }
 
+// stream units of T~ (entry type 1: FP32, 3: FP16), built once per mesh
+template <int ENT>
+static const StreamUnits& ensure_os_units(mtf_system sys, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  StreamUnits& su = ENT == 3 ? m->os16_units : m->os_units;
+  if (!su.ready) {
+    std::vector<int64_t> ld(m->nd);
+    for (int i = 0; i < m->nd; ++i) ld[i] = st_row_stride<ENT>(m->blk[i].N);
+    build_stream_units(m, st_unit_rows<ENT>(), st_piece_len<ENT>(), st_eb<ENT>(),
+                       ENT == 3 ? m->os16_off_h : m->os_T_off_h, ld, su, s);
+  }
+  return su;
+}
+
 // FP16 copy of T~ for the FP32 applies: block i is stored as T~_i / s_i
 // (s_i = largest |re| or |im| of its entries, so every entry lies in
 // [-1, 1] where FP16 keeps 11 significant bits), rows padded to a multiple
@@ -488,10 +502,7 @@ static void osrc_half_copy(mtf_system sys, cudaStream_t s) {
     m->os16_off_h[i] = off;
     off += int64_t(m->blk[i].N) * st_row_stride<3>(m->blk[i].N);
   }
-  // 8 zeroed entries of slack: the tensor-core stream copies whole k16
-  // chunks, up to 4 entries past the last row
-  sys->d_osrc_T16.alloc(size_t(off) + 8);
-  MTF_CUDA(cudaMemsetAsync(sys->d_osrc_T16.p + off, 0, 8 * sizeof(uint32_t), s));
+  sys->d_osrc_T16.alloc(size_t(off));
   DevBuf<unsigned> mx;
   mx.alloc(size_t(m->nd));
   MTF_CUDA(cudaMemsetAsync(mx.p, 0, size_t(m->nd) * sizeof(unsigned), s));
@@ -523,6 +534,12 @@ static void osrc_half_copy(mtf_system sys, cudaStream_t s) {
     cf[size_t(4 * i + 3)] = float(-sc * ri / rn);
   }
   sys->d_os_coef16.upload(cf, s);
+  if (MTF_OSRC_TC) {
+    // the tensor-core stream reads one contiguous run per unit
+    const StreamUnits& su = ensure_os_units<3>(sys, s);
+    sys->d_osrc_T16t.alloc(size_t(su.tiled_bytes / 4));
+    tile_stream_operator(su, sys->d_osrc_T16.p, 4, sys->d_osrc_T16t.p, s);
+  }
   MTF_CUDA(cudaStreamSynchronize(s));  // mx and the host tables go out of scope
 }
 
@@ -618,7 +635,7 @@ static void os_launch(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int6
   const void* ent = ENT == 3 ? static_cast<const void*>(sys->d_osrc_T16.p) : static_cast<const void*>(sys->d_osrc_T.p);
   const float* cf = ENT == 3 ? sys->d_os_coef16.p : sys->d_rho32.p;
   if (ENT == 3 && MTF_OSRC_TC)
-    launch_stream_tc<NC>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
+    launch_stream_tc<NC>(sys, sys->d_osrc_T16t.p, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
   else
     launch_stream_tiles<NC, ENT>(sys, ent, su, r32, ldr, c0, sys->d_os_part.p, KID_OSRC, s);
   MTF_LAUNCH(KID_OSCOMBINE, s,
@@ -631,13 +648,7 @@ template <class ZT, bool ADJ, int ENT>
 static void osrc_stream_ent(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs,
                             cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  StreamUnits& su = ENT == 3 ? m->os16_units : m->os_units;
-  if (!su.ready) {
-    std::vector<int64_t> ld(m->nd);
-    for (int i = 0; i < m->nd; ++i) ld[i] = st_row_stride<ENT>(m->blk[i].N);
-    build_stream_units(m, st_unit_rows<ENT>(), st_piece_len<ENT>(), st_eb<ENT>(), ENT == 3 ? m->os16_off_h : m->os_T_off_h, ld, su,
-                       s);
-  }
+  const StreamUnits& su = ensure_os_units<ENT>(sys, s);
   const size_t npart = size_t(m->n_rows) * su.pmax * 16;
   if (sys->d_os_part.n < npart) sys->d_os_part.alloc(npart);
   for (int c0 = 0; c0 < nrhs; c0 += 4) {

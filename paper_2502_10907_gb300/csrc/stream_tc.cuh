@@ -13,12 +13,14 @@
 // much as the FP16 copy of T~ changes it, and flexible GMRES takes the
 // vectors it applied.
 //
-// The producer warp is the one of stream.cuh (bulk copies into a ring of
-// stages, bounded waits), except that each row slot is padded by 16 bytes so
-// that the eight rows an ldmatrix phase reads fall in distinct banks, and
-// that each row copy is rounded up to whole k16 chunks (8 complex entries);
-// the entries copied past the piece meet zero inputs (the FP16 operator
-// buffer has 32 bytes of zeroed slack after its last row).  The 8 consumer
+// The producer warp works as in stream.cuh (bulk copies into a ring of
+// stages, bounded waits), but streams a tiled copy of the FP16 T~ in which
+// every unit is one contiguous run: its rows at a pitch of whole k16 chunks
+// (8 complex entries, zero past the piece) padded to 16 bytes past a
+// 128-byte multiple, so that the eight rows an ldmatrix phase reads fall in
+// distinct banks.  One bulk copy per unit instead of one per row: the copy
+// count, not DRAM, bounded the row-by-row version (about 90 ns per copy and
+// SM, measured).  The 8 consumer
 // warps take the piece's k16 chunks in turn, add their 16 x 8 partial tiles
 // in shared memory (double-buffered, one named barrier per unit) and store
 // the row piece sums in the layout the combine kernel reads.  A consumer warp
@@ -38,7 +40,7 @@ struct StreamTC {
   static constexpr int K = StreamK<NC, 3>::K;        // partial sums per row piece, as in stream.cuh
   static constexpr int L = st_piece_len<3>();        // complex entries per piece
   static constexpr int LC = (L + 7) / 8 * 8;         // entries copied per row slot
-  static constexpr int RBP = LC * 4 + 16;            // padded row slot
+  static constexpr int RBP = (LC * 4 + 127) / 128 * 128 + 16;  // row slot: the largest tiled pitch
   static constexpr int XB = (L + 2) * 8 + 16;        // input slice slot (padded: slices 8 banks apart)
   static constexpr int ROWS = 16;
   static constexpr int SB = ((ROWS * RBP + 2 * NC * XB) + 127) / 128 * 128;
@@ -57,9 +59,9 @@ __device__ __forceinline__ uint32_t tc_pack(float lo, float hi) {
 }
 
 template <int NC>
-__global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict__ entries,
+__global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict__ tiled,
                                                         const int4* __restrict__ units,
-                                                        const int64_t* __restrict__ usrc, int n_units, int pmax,
+                                                        const int64_t* __restrict__ toff, int n_units, int pmax,
                                                         const float* __restrict__ x32, int64_t ld32, int c0,
                                                         float* __restrict__ part, unsigned* __restrict__ err) {
   using TC = StreamTC<NC>;
@@ -84,21 +86,20 @@ __global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict_
   if (warp == 8) {
     // producer: one lane issues every copy
     if (lane != 0) return;
-    const unsigned char* ent = static_cast<const unsigned char*>(entries);
+    const unsigned char* ent = static_cast<const unsigned char*>(tiled);
     const uint64_t stream_pol = l2_policy_evict_first();
     int k = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++k) {
       const int4 rec = units[u];
-      const int64_t src = usrc[u];
+      const int64_t src = toff[u];
       const int s = k % S;
       if (!mbar_wait_bounded(&empty[s], (uint32_t(k / S) & 1u) ^ 1u, kStWaitNs)) {
         atomicExch(err, 1u);
         return;
       }
       const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0xff;
-      const int64_t stride = st_row_stride<3>(N);
-      const uint32_t rb = uint32_t((len + 7) / 8 * 8) * 4;  // whole k16 chunks
-      uint32_t total = uint32_t(nrows) * rb;
+      const uint32_t rows_bytes = uint32_t(nrows * st_tile_pitch(4, len));  // the unit's contiguous run
+      uint32_t total = rows_bytes;
       int64_t xa[2 * NC];
       uint32_t xbytes[2 * NC];
 #pragma unroll
@@ -111,8 +112,7 @@ __global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict_
       meta[s] = rec;
       mbar_arrive_expect_tx(&full[s], total);
       unsigned char* st = smem + size_t(s) * SB;
-      for (int r = 0; r < nrows; ++r)
-        bulk_g2s_hint(st + r * RBP, ent + (src + r * stride) * 4, rb, &full[s], stream_pol);
+      bulk_g2s_hint(st, ent + src, rows_bytes, &full[s], stream_pol);
 #pragma unroll
       for (int q = 0; q < 2 * NC; ++q) bulk_g2s(st + ROWS * RBP + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
     }
@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict_
       const unsigned char* st = smem + size_t(s) * SB;
       // ldmatrix x4: lanes 0-7 rows 0-7 (k 0-7), 8-15 rows 8-15 (k 0-7),
       // 16-23 rows 0-7 (k 8-15), 24-31 rows 8-15 (k 8-15)
-      const uint32_t abase = smem_u32(st) + uint32_t(((lane & 7) + ((lane >> 3) & 1) * 8) * RBP + (lane >> 4) * 16);
+      const int pitch = st_tile_pitch(4, len);
+      const uint32_t abase = smem_u32(st) + uint32_t(((lane & 7) + ((lane >> 3) & 1) * 8) * pitch + (lane >> 4) * 16);
       const int n = lane >> 2, tig = lane & 3, p = n & 1;
       // this lane's input column per tile: slice q = 4 t + n / 2 (the slice
       // starts one entry early when its first entry is odd; ld32 is even)
@@ -202,11 +203,11 @@ __global__ void __launch_bounds__(9 * 32, 1) k_stream_tc(const void* __restrict_
 
 // one launch of the tensor-core stream for right-hand sides c0 .. c0+NC-1
 template <int NC>
-void launch_stream_tc(mtf_system sys, const void* entries, const StreamUnits& su, const float* x32, int64_t ld32,
+void launch_stream_tc(mtf_system sys, const void* tiled, const StreamUnits& su, const float* x32, int64_t ld32,
                       int c0, float* part, int kid, cudaStream_t s) {
   using TC = StreamTC<NC>;
   MTF_REQUIRE(ld32 % 2 == 0 && (reinterpret_cast<uintptr_t>(x32) & 15) == 0 &&
-                  (reinterpret_cast<uintptr_t>(entries) & 15) == 0,
+                  (reinterpret_cast<uintptr_t>(tiled) & 15) == 0,
               MTF_ERR_ARG, "streamed vectors and operators must be 16-byte aligned with an even column stride");
   auto kfn = k_stream_tc<NC>;
   static std::atomic<uint64_t> opted{0};
@@ -218,8 +219,8 @@ void launch_stream_tc(mtf_system sys, const void* entries, const StreamUnits& su
     opted.fetch_or(bit);
   }
   MTF_LAUNCH(kid, s,
-             launch_pdl(kfn, dim3(unsigned(sys->mv_grid)), dim3(9 * 32), TC::smem, s, entries, su.d_units.p,
-                        su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
+             launch_pdl(kfn, dim3(unsigned(sys->mv_grid)), dim3(9 * 32), TC::smem, s, tiled, su.d_units.p,
+                        su.d_toff.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
 }
 
 }  // namespace mtf
