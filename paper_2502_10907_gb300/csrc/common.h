@@ -200,6 +200,7 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_k, d_rho;            // (re, im) per block
   mtf::DevBuf<double> d_TK64;                // FP64: 4 doubles per dense entry
   mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
+  mtf::DevBuf<float> d_TK32t;                // the same, tiled per stream unit (streaming matvec)
   mtf::DevBuf<double> d_xval;                // exchange values (6 per row)
   mtf::DevBuf<float> d_xval32;               // FP32 copy of the exchange values
   mtf::DevBuf<float> d_rho32;                // per block: rho (re, im), 1 / rho (re, im)
@@ -312,6 +313,7 @@ void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, co
                         const std::vector<int64_t>& row_stride, StreamUnits& u, cudaStream_t s);
 // tiled copy (su.tiled_bytes) of a streamed operator with eb-byte entries
 void tile_stream_operator(const StreamUnits& su, const void* dense, int eb, void* tiled, cudaStream_t s);
+void tile_matvec_operator(mtf_system sys, cudaStream_t s);
 // One FGMRES cycle of the mixed path on M d = r from d = 0 (FP32 Krylov
 // basis, FP64 reductions), then x += d.  Stops when every right-hand side's
 // estimate reaches tol relative to ||r|| (reached = true), after the restart

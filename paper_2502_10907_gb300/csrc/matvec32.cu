@@ -250,11 +250,26 @@ static void ensure_mv_scratch(mtf_system sys, cudaStream_t s) {
   if (sys->d_mv_part.n < npart) sys->d_mv_part.alloc(npart);
 }
 
+// tiled copy of the FP32 {T, K} entries for the streaming matvec, rebuilt
+// after every mixed-precision assembly (MTF_MV_TILED = 0 streams the dense rows)
+#ifndef MTF_MV_TILED
+#define MTF_MV_TILED 1
+#endif
+void tile_matvec_operator(mtf_system sys, cudaStream_t s) {
+  if (!MTF_MV_TILED) return;
+  ensure_mv_scratch(sys, s);
+  const StreamUnits& su = sys->mesh->mv_units;
+  sys->d_TK32t.alloc(size_t(su.tiled_bytes / 4));
+  tile_stream_operator(su, sys->d_TK32.p, 16, sys->d_TK32t.p, s);
+}
+
 template <int NC, class XT, class YT>
 static void mv_launch(mtf_system sys, const XT* x, int64_t ldx, const float* x32, int64_t ld32, YT* y, int64_t ldy,
                       int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  launch_stream_tiles<NC, 2>(sys, sys->d_TK32.p, m->mv_units, x32, ld32, c0, sys->d_mv_part.p, KID_MATVEC32, s);
+  const bool tiled = sys->d_TK32t.p != nullptr;
+  launch_stream_tiles<NC, 2>(sys, tiled ? static_cast<const float*>(sys->d_TK32t.p) : sys->d_TK32.p, m->mv_units, x32, ld32, c0,
+                             sys->d_mv_part.p, KID_MATVEC32, s, tiled);
   MTF_LAUNCH(KID_MVCOMBINE, s,
              launch_pdl(k_mv_combine<NC, XT, YT>, dim3(unsigned((m->n_rows * 32 + 255) / 256)), dim3(256), 0, s,
                         sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p,
@@ -289,7 +304,9 @@ template <int NC>
 static void mv_adj_launch(mtf_system sys, const float* v, int64_t ldv, const float* a32, int64_t lda, float* y,
                           int64_t ldy, int c0, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
-  launch_stream_tiles<NC, 2>(sys, sys->d_TK32.p, m->mv_units, a32, lda, c0, sys->d_mv_part.p, KID_MATVEC32, s);
+  const bool tiled = sys->d_TK32t.p != nullptr;
+  launch_stream_tiles<NC, 2>(sys, tiled ? static_cast<const float*>(sys->d_TK32t.p) : sys->d_TK32.p, m->mv_units, a32, lda, c0,
+                             sys->d_mv_part.p, KID_MATVEC32, s, tiled);
   MTF_LAUNCH(KID_MVCOMBINE, s, k_mv_combine_adj<NC><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
       sys->d_mv_part.p, m->mv_units.pmax, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p,
       m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, v, ldv, y, ldy, c0, m->n_rows));

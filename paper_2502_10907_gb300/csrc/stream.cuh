@@ -2,6 +2,11 @@
 // matvec (entries {T, K}: two complex FP32 values, ENT = 2) and the
 // block-OSRC apply (entries T~: one complex FP32 value, ENT = 1).
 //
+// An operator is streamed either from its dense rows (one bulk copy per row
+// of a unit) or from a tiled copy in which each unit is one contiguous run
+// (toff[u] its byte offset, rows at st_tile_pitch; one bulk copy per unit):
+// the bulk-copy count per byte bounds the row-by-row form.
+//
 // A dense block is cut into work units of st_unit_rows<ENT>() consecutive
 // rows x one column piece of at most st_piece_len<ENT>() entries (every row
 // of block i in P_i pieces of near-equal length).  One persistent CTA per SM
@@ -183,7 +188,7 @@ template <int NC, int ENT>
 __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
     const void* __restrict__ entries, const int4* __restrict__ units, const int64_t* __restrict__ usrc, int n_units,
     int pmax, const float* __restrict__ x32, int64_t ld32, int c0, float* __restrict__ part,
-    unsigned* __restrict__ err) {
+    unsigned* __restrict__ err, const int64_t* __restrict__ toff) {
   using SK = StreamK<NC, ENT>;
   constexpr int RW = st_rpw<ENT>(), ROWS = SK::ROWS;
   constexpr int EB = st_eb<ENT>(), Q = 16 / EB, K = SK::K, SH = SK::SH, RB = SK::RB, XB = SK::XB, SB = SK::SB, S = SK::S;
@@ -234,7 +239,9 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
       const int N = rec.x, len = rec.w & 0xfff, nrows = (rec.w >> 24) & 0xff;
       const int64_t stride = st_row_stride<ENT>(N);
       const uint32_t rb = uint32_t((len + Q - 1) / Q * Q) * EB;
-      uint32_t total = uint32_t(nrows) * rb;
+      // tiled operator: the unit's rows are one contiguous run at the tiled pitch
+      const uint32_t pitch = toff ? uint32_t(st_tile_pitch(EB, len)) : uint32_t(RB);
+      uint32_t total = toff ? uint32_t(nrows) * pitch : uint32_t(nrows) * rb;
       int64_t xa[2 * NC];
       uint32_t xbytes[2 * NC];
 #pragma unroll
@@ -247,8 +254,11 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
       meta[s] = rec;
       mbar_arrive_expect_tx(&full[s], total);
       unsigned char* st = smem + size_t(s) * SB;
-      for (int r = 0; r < nrows; ++r)
-        bulk_g2s_hint(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s], stream_pol);
+      if (toff)
+        bulk_g2s_hint(st, ent + toff[u], uint32_t(nrows) * pitch, &full[s], stream_pol);
+      else
+        for (int r = 0; r < nrows; ++r)
+          bulk_g2s_hint(st + r * RB, ent + (src + r * stride) * EB, rb, &full[s], stream_pol);
 #pragma unroll
       for (int q = 0; q < 2 * NC; ++q)
         bulk_g2s(st + ROWS * RB + q * XB, x32 + 2 * xa[q], xbytes[q], &full[s]);
@@ -267,6 +277,7 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
     }
     const int4 rec = meta[s];
     const int N = rec.x, len = rec.w & 0xfff, p = (rec.w >> 12) & 0xfff, nrows = (rec.w >> 24) & 0xff;
+    const int pitch = toff ? st_tile_pitch(EB, len) : RB;
     const unsigned char* st = smem + size_t(s) * SB;
     const int r0 = RW * warp;
     if (r0 < nrows) {
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
       for (int r = 0; r < RW; ++r) {
 #pragma unroll
         for (int q = 0; q < K; ++q) v[r][q] = 0.f;
-        rowp[r] = st + min(r0 + r, nrows - 1) * RB;  // repeats of the unit's last row are discarded
+        rowp[r] = st + min(r0 + r, nrows - 1) * pitch;  // repeats of the unit's last row are discarded
       }
 #pragma unroll st_unroll<ENT>()
       for (int e = lane; e < len; e += 32) {
@@ -307,7 +318,7 @@ __global__ void __launch_bounds__(st_threads<ENT>(), 1) k_stream_tiles(
 // one launch of the tiled streaming kernel for right-hand sides c0 .. c0+NC-1
 template <int NC, int ENT>
 void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits& su, const float* x32, int64_t ld32,
-                         int c0, float* part, int kid, cudaStream_t s) {
+                         int c0, float* part, int kid, cudaStream_t s, bool tiled = false) {
   using SK = StreamK<NC, ENT>;
   MTF_REQUIRE(ld32 % 2 == 0 && (reinterpret_cast<uintptr_t>(x32) & 15) == 0 &&
                   (reinterpret_cast<uintptr_t>(entries) & 15) == 0,
@@ -324,7 +335,8 @@ void launch_stream_tiles(mtf_system sys, const void* entries, const StreamUnits&
   }
   MTF_LAUNCH(kid, s,
              launch_pdl(kfn, dim3(unsigned(sys->mv_grid)), dim3(st_threads<ENT>()), SK::smem, s, entries,
-                        su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2));
+                        su.d_units.p, su.d_src.p, int(su.n_units), su.pmax, x32, ld32, c0, part, sys->d_mv_ctl.p + 2,
+                        tiled ? su.d_toff.p : static_cast<const int64_t*>(nullptr)));
 }
 
 // Sum of the P piece partials of one row (stored contiguously, K per piece)
