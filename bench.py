@@ -45,10 +45,11 @@ FLOPS_PER_EVAL = 57                                    # moment-form inner loop,
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of the current streaming kernels (--set full, launches around Arnoldi column
-# 330 of the split-sphere workload, n_total 13,068, 2 right-hand sides; the
-# block-OSRC figure is the FP16 copy of T~); keyed by (kernel, n_total, nrhs),
-# absent for other workloads
-NCU_TRAFFIC = {("matvec32", 13068, 2): 231.85e6, ("osrc_apply", 13068, 2): 57.25e6}
+# 100 of the split-sphere workload, n_total 13,068, 2 right-hand sides; both
+# stream tiled operator copies, the block-OSRC one the FP16 T~ on the tensor
+# cores, whose tiled rows carry up to 144 bytes of padding each); keyed by
+# (kernel, n_total, nrhs), absent for other workloads
+NCU_TRAFFIC = {("matvec32", 13068, 2): 232.30e6, ("osrc_apply", 13068, 2): 60.09e6}
 
 
 def _stream_bytes(name, Ns, n_total, nrhs):
