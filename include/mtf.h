@@ -99,6 +99,12 @@ typedef struct {
                            it and new basis vectors are orthogonalised
                            against it) instead of restarting from scratch;
                            0: plain restart.  Default 1                      */
+  int32_t residual_df;  /* mixed mode: 1: the outer refinement residuals
+                           b - M x apply the FP32-stored operator to the FP64
+                           iterate in double-float arithmetic (iterate split
+                           into FP32 pairs, error-free products and sums;
+                           about 2^-46 relative, on the FP32 pipes);
+                           0: FP64 products and sums.  Default 1             */
 } mtf_options;
 
 typedef struct {

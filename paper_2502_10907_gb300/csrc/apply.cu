@@ -12,11 +12,6 @@
 
 #include "common.h"
 
-// refinement residuals of the mixed path in double-float (1) or FP64 (0)
-#ifndef MTF_MV_DF
-#define MTF_MV_DF 1
-#endif
-
 namespace mtf {
 
 template <class MatT>
@@ -325,7 +320,7 @@ void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, 
     if (sys->d_x32.n < size_t(n2) * nrhs) sys->d_x32.alloc(size_t(n2) * nrhs);
     MTF_LAUNCH(KID_MISC, s, k_to_f32<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(x, ldx, n2, nrhs, sys->d_x32.p));
     launch_matvec_stream64(sys, x, ldx, sys->d_x32.p, m->n_total, y, ldy, nrhs, s);
-  } else if (MTF_MV_DF) {
+  } else if (sys->opt.residual_df) {
     // FP32 storage, double-float sums of the split input
     const int64_t n2 = 2 * m->n_total;
     if (sys->d_x32.n < 2 * size_t(n2) * nrhs) sys->d_x32.alloc(2 * size_t(n2) * nrhs);

@@ -84,3 +84,15 @@ def test_invalid_meshes_are_rejected(lib):
     with pytest.raises(lib.MtfError) as e:
         lib.mtf_mesh_create(m.vertices, m.triangles, m.labels, 1)
     assert e.value.status == 1
+
+
+def test_default_options(lib):
+    """Defaults of the solver options as include/mtf.h documents them; the
+    ctypes mirror of mtf_options reads every field of the C struct."""
+    from paper_2502_10907_gb300 import _lib as L
+    o = L.mtf_default_options()
+    assert (o.precision, o.n_ss, o.precond) == (0, 4, 0)
+    assert (o.osrc_np, o.max_refine, o.learned) == (4, 4, 0)
+    assert (o.osrc_half, o.recycle, o.residual_df) == (1, 1, 1)
+    assert o.tol > 0 and o.restart > 0 and o.max_iter > 0
+    assert abs(o.osrc_theta - np.pi / 2) < 1e-12 and abs(o.osrc_eps_scale - 0.39) < 1e-12

@@ -385,9 +385,11 @@ def test_mixed_residual_matvec_is_exact_for_the_stored_operator(api, oracle_cach
     cfg, sk, ref = _case(oracle_cache, name)
     mesh = api.Mesh.from_inputs(cfg["mesh"])
     s32 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    s32f = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, residual_df=0)
     rng = np.random.default_rng(31)
     x = rng.standard_normal((3, sk.n_total)) + 1j * rng.standard_normal((3, sk.n_total))
     y = s32.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    y64 = s32f.matvec(torch.from_numpy(x).cuda()).cpu().numpy()   # FP64 sums
     yr = ref.matvec(x.T).T                              # FP64 blocks + exchange
     for i in range(sk.n_domains):                       # swap in the stored FP32 blocks
         T, K = (t.cpu().numpy() for t in s32.block(i))
@@ -396,4 +398,5 @@ def test_mixed_residual_matvec_is_exact_for_the_stored_operator(api, oracle_cach
         yr[:, Di] += (2.0 * (dK @ x[:, Di].T + (dT @ x[:, Ni].T) / r)).T
         yr[:, Ni] += (2.0 * (-r * (dT @ x[:, Di].T) + dK @ x[:, Ni].T)).T
     assert rel(y, yr) < 1e-12, rel(y, yr)
+    assert rel(y64, yr) < 1e-13, rel(y64, yr)
     assert rel(y, ref.matvec(x.T).T) > 1e-9          # the FP32 storage error is visible
