@@ -55,22 +55,27 @@ NCU_TRAFFIC = {("matvec32", 13068, 2): 232.30e6, ("osrc_apply", 13068, 2): 60.09
 def _stream_bytes(name, Ns, n_total, nrhs):
     """Algorithmic bytes of one launch of an operator-apply kernel.
     matvec64: FP64 {T, K} entries (32 B per dense entry) + FP64 x reads and y
-    writes + the exchange rows (6 entries of 24 B per row).  matvec32 /
-    osrc_apply (the streaming kernels): every stored entry once ({T, K}: 16 B,
-    T~: 8 B on rows padded to an even length), the FP32 input once
-    (8 B per complex unknown and right-hand side) and the per-row piece sums
-    (K floats per piece of 256 / 512 entries, K = 4 ENT NC rounded up to a
-    power of two)."""
+    writes + the exchange rows (6 entries of 24 B per row), for up to four
+    right-hand sides.  matvec32 / osrc_apply (the streaming kernels, one
+    launch per group of up to four right-hand sides): every stored entry once
+    ({T, K}: 16 B; T~ in the default FP16 copy: 4 B on rows padded to a
+    multiple of 4), the FP32 input of the group once (8 B per complex unknown
+    and right-hand side) and the per-row piece sums (K floats per piece of
+    256 {T, K} or 640 T~ entries, K = 4 or 8 values per right-hand side
+    rounded up to a power of two)."""
+    nl = min(nrhs, 4)
     if name == "matvec64":
         n_mat = sum(N * N for N in Ns)
-        return n_mat * 32 + 2 * n_total * 16 * nrhs + (n_total // 2) * 6 * 24
-    ent = 2 if name == "matvec32" else 1
-    L = 4096 // (8 * ent)
-    K = 4 * ent * min(nrhs, 4)
-    K = 4 if K <= 4 else 8 if K <= 8 else 16 if K <= 16 else 32
-    mat = sum(N * (N if ent == 2 else N + (N & 1)) * 8 * ent for N in Ns)
-    parts = sum(N * -(-N // L) for N in Ns) * K * 4 * -(-nrhs // 4)
-    return mat * -(-nrhs // 4) + n_total * 8 * nrhs + parts
+        return n_mat * 32 + 2 * n_total * 16 * nl + (n_total // 2) * 6 * 24
+    if name == "matvec32":
+        mat = sum(N * N * 16 for N in Ns)
+        L, raw = 256, 8 * nl
+    else:
+        mat = sum(N * ((N + 3) & ~3) * 4 for N in Ns)
+        L, raw = 640, 4 * nl
+    K = 4 if raw <= 4 else 8 if raw <= 8 else 16 if raw <= 16 else 32
+    parts = sum(N * -(-N // L) for N in Ns) * K * 4
+    return mat + n_total * 8 * nl + parts
 
 
 def _peaks():
@@ -92,6 +97,9 @@ def workload(name):
     elif name == "cube2":
         cfg = mi.config_cube2()
         desc = "unit cube 2x2x2 subcubes eps U[1.5,4] k0=3, 5832 triangles, 64 plane waves"
+    elif name == "cube4":
+        cfg = mi.config_cube4()
+        desc = "unit cube 4x4x4 subcubes eps U[1.5,6] k0=4, 12000 triangles, 16 plane waves"
     else:
         raise ValueError(name)
     obs_t = np.linspace(0.0, np.pi, 181)
