@@ -39,8 +39,10 @@ import mtf_inputs as mi  # noqa: E402
 METRIC = "solved RHS/sec at 1e-5 rel. err vs FP64 oracle; assembly triangle-pairs/sec"
 UNIT = "RHS/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12      # 152 SMs x 128 lanes x FMA x 2.07 GHz
-FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (recipe table)
-FLOPS_PER_EVAL = 57                                    # moment-form inner loop, see the design doc
+FP64_PEAK_TFLOPS = 1.25                                # GB300 nominal dense FP64
+# FP32 operations per kernel evaluation of the regular-pair kernel's
+# moment-form inner loop (distance, G and grad G, the moment updates)
+FLOPS_PER_EVAL = 57
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
@@ -514,7 +516,8 @@ def main():
     e2e_setup = world * nrhs / min(setup_times)
 
     # ---- the same workload on the plain FP64 path and with the learned ------
-    # correction (rank 0 at N = 1): the comparisons the method is judged by
+    # correction (rank 0 at N = 1): the comparisons that put the mixed path's
+    # number in context
     fp64_line, learned_line = None, None
     if rank == 0 and world == 1 and not args.no_comparisons and prec == L.MTF_PREC_MIXED:
         s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
