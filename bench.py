@@ -80,6 +80,25 @@ def _stream_bytes(name, Ns, n_total, nrhs):
     return mat + n_total * 8 * nl + parts
 
 
+def max_over_ranks(seconds, world, device="cuda"):
+    """Longest per-rank duration of a phase that all ranks ran concurrently
+    (replicas: each rank solves its own instance); the job's throughput is the
+    units of all ranks over it.  A single rank returns its own value."""
+    if world <= 1:
+        return float(seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world, device="cuda"):
+    """Whole-job throughput of N replicas: world x units_per_rank over the
+    slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds, world, device)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -419,11 +438,8 @@ def main():
     torch.cuda.synchronize()
     L.mtf_profile_enable(False)
     prof = L.mtf_profile_read()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     nrhs = len(cfg["dirs"])
+    ms = 1e3 * max_over_ranks(ms / 1e3, world)
     value = world * nrhs / (ms / 1e3)
     err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
     # assembly alone (device-timed)
@@ -496,7 +512,7 @@ def main():
         if it > 0:                                   # the first pass is a warm-up
             e2e_times.append(time.perf_counter() - t0)
     del sh, mh
-    e2e = world * nrhs / statistics.median(e2e_times)
+    e2e = job_throughput(nrhs, statistics.median(e2e_times), world)
     # the same with the mesh and system created from host arrays every step
     # (mesh tables, block-OSRC eigenpairs, assembly), for reference
     setup_times = []
@@ -513,7 +529,7 @@ def main():
         torch.cuda.synchronize()
         setup_times.append(time.perf_counter() - t0)
         del sh, mh
-    e2e_setup = world * nrhs / min(setup_times)
+    e2e_setup = job_throughput(nrhs, min(setup_times), world)
 
     # ---- the same workload on the plain FP64 path and with the learned ------
     # correction (rank 0 at N = 1): the comparisons that put the mixed path's
