@@ -49,3 +49,15 @@ def test_single_rank_is_its_own_time():
     import bench
     assert bench.max_over_ranks(0.3, 1) == 0.3
     assert bench.job_throughput(2, 0.5, 1) == pytest.approx(4.0)
+
+
+def test_algorithmic_bytes_are_per_launch():
+    """The streaming kernels process at most 4 right-hand sides per launch:
+    the roofline's algorithmic bytes count one launch, so they stop growing
+    past 4 right-hand sides; the split-sphere figures are the stored entries
+    plus inputs and piece sums."""
+    import bench
+    Ns, n = [2178] * 3, 13068
+    assert bench._stream_bytes("matvec32", Ns, n, 2) == 3 * 2178 ** 2 * 16 + n * 8 * 2 + 3 * 2178 * 9 * 16 * 4
+    assert bench._stream_bytes("matvec32", Ns, n, 64) == bench._stream_bytes("matvec32", Ns, n, 4)
+    assert bench._stream_bytes("osrc_apply", Ns, n, 2) == 3 * 2178 * 2180 * 4 + n * 8 * 2 + 3 * 2178 * 4 * 8 * 4
