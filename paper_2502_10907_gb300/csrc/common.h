@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mtf.h"
+#include "stream_plan.h"
 
 namespace mtf {
 
@@ -122,15 +123,7 @@ struct StreamUnits {
   int64_t tiled_bytes = 0;
 };
 
-// row pitch (bytes) of a unit in the tiled copy of a streamed operator with
-// eb-byte entries: 4-byte entries (the tensor-core stream) in whole 8-entry
-// chunks, padded to 16 bytes past a 128-byte multiple so that the rows an
-// ldmatrix phase reads fall in distinct shared-memory banks; others in
-// 16-byte words
-__host__ __device__ inline int st_tile_pitch(int eb, int len) {
-  if (eb == 4) return ((len + 7) / 8 * 32 + 127) / 128 * 128 + 16;
-  return (len * eb + 15) / 16 * 16;
-}
+
 
 }  // namespace mtf
 

@@ -144,49 +144,30 @@ __global__ void k_conj32(const float* __restrict__ v, int64_t ldv, int64_t n, fl
 // ---------------------------------------------------------------------------
 void build_stream_units(mtf_mesh m, int rows, int piece_len, int entry_bytes, const std::vector<int64_t>& blk_entry_off,
                         const std::vector<int64_t>& row_stride, StreamUnits& su, cudaStream_t s) {
-  MTF_REQUIRE(entry_bytes == 4 || entry_bytes == 8 || entry_bytes == 16, MTF_ERR_ARG,
-              "stream entries are 4, 8 or 16 bytes");
-  MTF_REQUIRE(rows >= 1 && rows <= 64, MTF_ERR_ARG, "rows per stream unit out of range");
-  const int q = 16 / entry_bytes;  // entries per 16 bytes
-  std::vector<int4> u;
-  std::vector<int64_t> src, toff;
-  int64_t tiled = 0;
-  int pmax = 1;
+  std::vector<StreamBlock> blocks(static_cast<size_t>(m->nd));
   for (int i = 0; i < m->nd; ++i) {
-    const int N = m->blk[i].N;
-    const int64_t ld = row_stride[i];
-    const int P = std::max(1, (N + piece_len - 1) / piece_len);
-    const int ps = ((N + P - 1) / P + q - 1) / q * q;
-    MTF_REQUIRE(ps <= piece_len && P < 4096 && N < (1 << 30), MTF_ERR_MESH, "stream piece longer than a slot");
-    MTF_REQUIRE((ld * entry_bytes) % 16 == 0 && (blk_entry_off[i] * entry_bytes) % 16 == 0 && ld >= N,
-                MTF_ERR_ARG, "stream operator rows are not 16-byte aligned");
-    pmax = std::max(pmax, P);
-    for (int p = 0; p < P; ++p) {
-      const int c = p * ps, len = std::min(ps, N - c);
-      const int clen = (len + q - 1) / q * q;  // entries the copy moves
-      MTF_REQUIRE(len > 0 && len < 4096 && c + clen <= ld, MTF_ERR_MESH, "stream piece out of its row");
-      for (int r0 = 0; r0 < N; r0 += rows) {
-        const int nr = std::min(rows, N - r0);
-        u.push_back(make_int4(N, int(m->blk[i].row_off + r0), int(m->blk[i].dof_off + c),
-                              len | (p << 12) | (nr << 24)));
-        src.push_back(blk_entry_off[i] + int64_t(r0) * ld + c);
-        toff.push_back(tiled);
-        tiled += int64_t(nr) * st_tile_pitch(entry_bytes, len);
-      }
-    }
+    blocks[size_t(i)].N = m->blk[i].N;
+    blocks[size_t(i)].row_off = m->blk[i].row_off;
+    blocks[size_t(i)].dof_off = m->blk[i].dof_off;
+    blocks[size_t(i)].entry_off = blk_entry_off[i];
+    blocks[size_t(i)].ld = row_stride[i];
   }
-  MTF_REQUIRE(m->n_total < (int64_t(1) << 31) && int64_t(u.size()) < (int64_t(1) << 31), MTF_ERR_MESH,
-              "mesh too large for the streaming tables");
-  su.n_units = int64_t(u.size());
-  su.pmax = pmax;
-  su.tiled_bytes = tiled;
-  su.d_units.alloc(u.size());
-  su.d_src.alloc(src.size());
-  su.d_toff.alloc(toff.size());
-  if (!u.empty()) {
-    MTF_CUDA(cudaMemcpyAsync(su.d_units.p, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-    MTF_CUDA(cudaMemcpyAsync(su.d_src.p, src.data(), src.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MTF_CUDA(cudaMemcpyAsync(su.d_toff.p, toff.data(), toff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  StreamPlan plan;
+  const std::string why = plan_stream_units(blocks, rows, piece_len, entry_bytes, plan);
+  MTF_REQUIRE(why.empty(), MTF_ERR_MESH, why);
+  MTF_REQUIRE(m->n_total < (int64_t(1) << 31), MTF_ERR_MESH, "mesh too large for the streaming tables");
+  const size_t nu = size_t(plan.n_units());
+  su.n_units = plan.n_units();
+  su.pmax = plan.pmax;
+  su.tiled_bytes = plan.tiled_bytes;
+  su.d_units.alloc(nu);
+  su.d_src.alloc(nu);
+  su.d_toff.alloc(nu);
+  if (nu > 0) {
+    static_assert(sizeof(int4) == 4 * sizeof(int32_t), "unit records are four int32");
+    MTF_CUDA(cudaMemcpyAsync(su.d_units.p, plan.rec.data(), nu * sizeof(int4), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(su.d_src.p, plan.src.data(), nu * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MTF_CUDA(cudaMemcpyAsync(su.d_toff.p, plan.toff.data(), nu * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     MTF_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
   }
   su.ready = true;
