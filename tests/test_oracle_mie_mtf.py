@@ -129,3 +129,27 @@ def test_reciprocity_and_energy_balance(oracle_cache):
     sca = np.sum(w * np.sum(np.abs(F) ** 2, axis=1))
     ext = 4 * np.pi / sysm.k0 * np.imag(p1 @ sysm.farfield(x[:, :1], d1[None])[0, :, 0])
     assert abs(sca - ext) < 0.05 * ext
+
+
+def test_artificial_interfaces_leave_the_far_field():
+    """Concentric cuboids of one material (Sec. 5.4: the domain-decomposition
+    test of the paper): splitting the scatterer into 2 square rings adds
+    interfaces between equal media, so MTF(2) must reproduce the far field of
+    the undivided scatterer MTF(1) meshed on the same grid, to discretisation
+    accuracy (the rings' boundaries are tori, their walls meet the top and
+    bottom faces in junction lines)."""
+    import mtf_inputs.meshes as mm
+    h = 0.45
+    cfg = mi.config_concentric_cuboids(2, h=h)
+    r = mi.cuboid_radii(2)
+    xs = mm._graded(sorted({-v for v in r[1:]} | {v for v in r[1:]}), h)
+    zs = mm._graded([0.0, 1.0], h)
+    one = mm.grid_partition(xs, xs, zs, np.ones((len(xs) - 1, len(xs) - 1, len(zs) - 1), dtype=int))
+    far = []
+    for mesh, eps in ((cfg["mesh"], cfg["eps_r"]), (one, np.array([1.0, 2.0]))):
+        sk = skeleton_of(mesh)
+        sysm = MTFSystem(sk, cfg["k0"], eps, np.ones(len(eps)))
+        x = sysm.solve_lu(sysm.rhs(cfg["dirs"], cfg["pols"]))
+        far.append(sysm.farfield(x, rcs_plane(91))[:, :, 0])
+    d = np.linalg.norm(far[0] - far[1]) / np.linalg.norm(far[1])
+    assert d < 0.02, d
