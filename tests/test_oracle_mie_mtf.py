@@ -153,3 +153,40 @@ def test_artificial_interfaces_leave_the_far_field():
         far.append(sysm.farfield(x, rcs_plane(91))[:, :, 0])
     d = np.linalg.norm(far[0] - far[1]) / np.linalg.norm(far[1])
     assert d < 0.02, d
+
+
+def test_mtf1_agrees_with_pmchwt(oracle_cache):
+    """MTF(1) and PMCHWT (Sec. 3.1, the PMCHWT remark): summing the two block
+    rows of Problem 2 with u_1 = -u_0 gives (A_0 - A_1) u_0 = u_inc.  The RWG
+    functions of block 1 are the negatives of block 0's on the shared surface,
+    so in coefficients u_1 = +u_0 and the system reads (2 A_0 + 2 A_1) u = b_0.
+    Solving it from the same blocks gives a far field that agrees with
+    MTF(1)'s far below both formulations' distance to the Mie series, and the
+    gap closes under refinement; the opposite sign gives a wrong field."""
+    gaps = []
+    for lvl in (1, 2):
+        cfg, sk, ref = sphere_system(oracle_cache, lvl)
+        b = ref.rhs(cfg["dirs"], cfg["pols"])[:, 0]
+        x = ref.solve_lu(b[:, None])[:, 0]
+        D0, N0 = sk.block_slices(0)
+
+        def A2(i):
+            T, K, r = ref.T[i], ref.K[i], ref.rho[i]
+            return 2.0 * np.block([[K, T / r], [-r * T, K]])
+
+        obs = rcs_plane()
+        F = ref.farfield(x[:, None], obs)[:, :, 0]
+        Fm = mie_farfield(cfg["k0"], 1.0, cfg["eps_r"][1], cfg["dirs"][0], cfg["pols"][0], obs)
+        for sign in (1.0, -1.0):
+            u = np.linalg.solve(A2(0) + sign * A2(1), np.concatenate([b[D0], b[N0]]))
+            xp = np.zeros_like(x)
+            xp[D0], xp[N0] = u[: len(u) // 2], u[len(u) // 2:]
+            Fp = ref.farfield(xp[:, None], obs)[:, :, 0]
+            gap = np.linalg.norm(Fp - F) / np.linalg.norm(F)
+            if sign > 0:
+                gaps.append(gap)
+                mie = np.linalg.norm(F - Fm) / np.linalg.norm(Fm)
+                assert gap < 1e-3 * mie, (lvl, gap, mie)
+            else:
+                assert gap > 0.5, (lvl, gap)
+    assert gaps[1] < gaps[0] / 4, gaps
