@@ -58,7 +58,9 @@ typedef enum {
 typedef enum {
   MTF_PREC_FP64 = 0,    /* FP64 assembly, storage, matvec and solver         */
   MTF_PREC_MIXED = 1    /* FP32 regular pairs + FP32 storage / matvec, FP64
-                           singular pairs, Arnoldi and refinement residuals   */
+                           singular pairs, FP64 Hessenberg sums, FP64
+                           iterate with double-float (or, with
+                           residual_df = 0, FP64) refinement residuals       */
 } mtf_precision;
 
 typedef enum {
@@ -185,7 +187,9 @@ mtf_status mtf_get_block(mtf_system sys, int32_t i, void* t_out, void* k_out, vo
 
 /* y = M x (Problem 2): block-dense 2 A_i u_i plus the skeleton exchange
  * sum_j G^{ij} u_j in both trace slots (Remark 2).  x, y: device complex128,
- * n_total x nrhs, must not overlap. */
+ * n_total x nrhs, must not overlap.  Mixed-precision systems apply their
+ * FP32-stored blocks with double-float sums (opt.residual_df, default) or
+ * FP64 sums: the refinement residual. */
 mtf_status mtf_matvec(mtf_system sys, const void* x, void* y, int32_t nrhs, void* stream);
 
 /* z = A~ r: the block-OSRC preconditioner of Sec. 4.4 (Eq. 19),
