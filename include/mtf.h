@@ -107,6 +107,14 @@ typedef struct {
                            into FP32 pairs, error-free products and sums;
                            about 2^-46 relative, on the FP32 pipes);
                            0: FP64 products and sums.  Default 1             */
+  int32_t block_krylov; /* mixed mode with nrhs > 1 (and no learned
+                           correction initialised): 1: the inner FGMRES cycles build one
+                           block Krylov space shared by all right-hand sides
+                           (block flexible GMRES, block classical
+                           Gram-Schmidt twice, deflating Cholesky
+                           normalisation); restart then counts block steps of
+                           nrhs vectors.  0: one Krylov space per right-hand
+                           side.  Default 1                                  */
 } mtf_options;
 
 typedef struct {
@@ -245,15 +253,20 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
  * call cudaMalloc while they run: code working inside a fixed, pre-reserved
  * memory budget that a late allocation could exhaust, or a serving loop /
  * host callback where cudaMalloc may implicitly synchronise the device and
- * stall other work.  This entry point computes exactly what mtf_solve
- * computes (same kernels, same arithmetic) but takes every device buffer it
- * needs -- right-hand sides, Krylov basis, work vectors, Hessenberg columns,
- * wave parameters -- from one static device array of 16 MiB that every GPU
- * loading the library holds until the process exits.  The caller still
- * provides x_out.
- *   Limit: 2 n_total nrhs (restart + 4) + 6 nrhs (restart + 2) + 9 nrhs + 64
- *   doubles must fit in 2^21 doubles; larger requests fail with MTF_ERR_ARG
- *   and a message giving both numbers.
+ * stall other work.  This entry point runs the algorithm of mtf_solve's FP64
+ * path -- restarted flexible GMRES, right-preconditioned by block-OSRC when
+ * the system was assembled with MTF_PRECOND_OSRC, CGS2 orthogonalisation,
+ * Givens rotations on the host -- with its own simpler reduction kernels, so
+ * its results agree with mtf_solve to rounding (1e-10 relative), not bit for
+ * bit.  It takes every device buffer it needs -- right-hand sides, Krylov
+ * basis, preconditioned directions, work vectors, Hessenberg columns, wave
+ * parameters -- from one static device array of 16 MiB that every GPU
+ * loading the library holds until the process exits (block-OSRC systems
+ * prepare their apply tables at assembly).  The caller still provides x_out.
+ *   Limit, in doubles, with n = n_total and m = opt.restart:
+ *     2 n nrhs (m + 4) + (6 m + 8) nrhs + 9 nrhs + 64
+ *   plus 2 n nrhs m + n nrhs with block-OSRC, must fit in 2^21; larger
+ *   requests fail with MTF_ERR_ARG and a message giving both numbers.
  *   Set-up: the first call on each device (with that device current) looks
  *   up the array's device address; make that first call before any stream
  *   capture.

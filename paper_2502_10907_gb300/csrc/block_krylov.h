@@ -1,0 +1,243 @@
+// Host side of block flexible GMRES (one Krylov space shared by all s
+// right-hand sides of a solve): the deflating Cholesky factorisation that
+// normalises a block of s new vectors, and the progressive Householder QR of
+// the block upper-Hessenberg matrix with the residual estimates of every
+// right-hand side and the final triangular solve.  Pure host C++ (no CUDA),
+// so that it can be tested on its own.
+//
+// Notation.  Block step j produces W = M Z_j (n x s) orthogonalised against
+// the basis V_0 .. V_j, with coefficients h = [V_0 .. V_j]^H W ((j+1) s x s),
+// and W = V_{j+1} R_{j+1} with V_{j+1} orthonormal (deflated columns are zero)
+// and R_{j+1} upper triangular.  Column block j of the Hessenberg matrix is
+// [h; R_{j+1}] ((j+2) s x s).  Each column block is reduced to triangular
+// form by s Householder reflectors acting on rows js .. (j+2)s - 1; reflector
+// k of block j has support {js + k .. js + s - 1} (top) and
+// {(j+1)s .. (j+1)s + k} (bottom, R_{j+1} being upper triangular), s + 1 rows.
+// The right-hand side of the least-squares problem is E_1 S_0, S_0 the
+// factor of the start block; after the reflectors of block j, rows
+// (j+1)s .. (j+2)s - 1 of its column c hold the residual of right-hand side c.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <functional>
+#include <thread>
+#include <vector>
+
+namespace mtf {
+
+using cdouble = std::complex<double>;
+
+// Cholesky factor of the Hermitian s x s Gram matrix G (column-major) of a
+// block W, G = R^H R, skipping directions whose squared norm d_k after
+// removing the earlier directions is at most tau^2 * ref[k] (ref[k] = a
+// reference squared norm of column k, e.g. before orthogonalisation against
+// the basis) or not positive: row k of R is then zero and column k of the
+// normalised block is dropped (deflated).  T (s x s, column-major) receives
+// the transform with V = W T: T[K, K] = R[K, K]^-1 on the kept index set K,
+// zero elsewhere.  Returns the number of kept directions.
+inline int deflating_cholesky(int s, const cdouble* G, const double* ref, double tau, cdouble* R, cdouble* T,
+                              std::vector<int>& kept) {
+  std::fill(R, R + size_t(s) * s, cdouble(0));
+  std::fill(T, T + size_t(s) * s, cdouble(0));
+  kept.assign(s, 0);
+  for (int k = 0; k < s; ++k) {
+    // R[i, k] for kept i < k
+    for (int i = 0; i < k; ++i) {
+      if (!kept[i]) continue;
+      cdouble a = G[size_t(k) * s + i];
+      for (int p = 0; p < i; ++p)
+        if (kept[p]) a -= std::conj(R[size_t(i) * s + p]) * R[size_t(k) * s + p];
+      R[size_t(k) * s + i] = a / R[size_t(i) * s + i];
+    }
+    double d = G[size_t(k) * s + k].real();
+    for (int i = 0; i < k; ++i)
+      if (kept[i]) d -= std::norm(R[size_t(k) * s + i]);
+    const double lim = tau * tau * std::max(ref[k], 0.0);
+    if (!(d > lim) || !(d > 0.0)) continue;  // deflated: column k keeps its projection R[i < k, k]
+    kept[k] = 1;
+    R[size_t(k) * s + k] = std::sqrt(d);
+  }
+  // rows of deflated indices are zero (their entries were never written)
+  // T = R_KK^-1 by back substitution, column by column
+  int nk = 0;
+  for (int q = 0; q < s; ++q) {
+    if (!kept[q]) continue;
+    ++nk;
+    T[size_t(q) * s + q] = 1.0 / R[size_t(q) * s + q];
+    for (int i = q - 1; i >= 0; --i) {
+      if (!kept[i]) continue;
+      cdouble a = 0;
+      for (int p = i + 1; p <= q; ++p)
+        if (kept[p]) a += R[size_t(p) * s + i] * T[size_t(q) * s + p];
+      T[size_t(q) * s + i] = -a / R[size_t(i) * s + i];
+    }
+  }
+  return nk;
+}
+
+// run f(c) for c in [0, n), on up to `threads` host threads
+inline void parallel_for(int n, int threads, const std::function<void(int)>& f) {
+  threads = std::max(1, std::min(threads, n));
+  if (threads == 1) {
+    for (int c = 0; c < n; ++c) f(c);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(size_t(threads));
+  for (int t = 0; t < threads; ++t)
+    pool.emplace_back([&, t] {
+      for (int c = t; c < n; c += threads) f(c);
+    });
+  for (auto& th : pool) th.join();
+}
+
+struct BlockLSQ {
+  int s = 0, m = 0;          // block size, maximum number of block steps
+  int k = 0;                 // block columns added
+  // reduced block columns: column block j holds rows 0 .. (j+1) s - 1 of its
+  // s columns (column-major, leading dimension (j+1) s), at offset off[j]
+  std::vector<cdouble> Rt;
+  std::vector<size_t> off;
+  // reflectors: block j, reflector kk: s + 1 entries (top rows kk .. s-1,
+  // bottom rows 0 .. kk) and the scalar beta (v v^H scaled: I - beta v v^H)
+  std::vector<cdouble> refl;
+  std::vector<double> beta;
+  std::vector<cdouble> g;    // (m + 1) s x s, column-major (ld (m+1) s)
+  std::vector<double> bnorm; // per right-hand side: reference norm of the estimates
+  int threads = 1;
+
+  void init(int s_, int m_, const cdouble* S0, const double* base_norm) {
+    s = s_;
+    m = m_;
+    k = 0;
+    Rt.clear();
+    off.assign(size_t(m) + 1, 0);
+    refl.assign(size_t(m) * s * (s + 1), cdouble(0));
+    beta.assign(size_t(m) * s, 0.0);
+    g.assign(size_t(m + 1) * s * s, cdouble(0));
+    const size_t ldg = size_t(m + 1) * s;
+    for (int c = 0; c < s; ++c)
+      for (int i = 0; i < s; ++i) g[size_t(c) * ldg + i] = S0[size_t(c) * s + i];
+    bnorm.assign(s, 1.0);
+    for (int c = 0; c < s; ++c) bnorm[c] = base_norm[c] > 0 ? base_norm[c] : 1.0;
+    const unsigned hw = std::thread::hardware_concurrency();
+    threads = int(std::max(1u, std::min(hw, 16u)));
+  }
+
+  // apply reflector (j, kk) to one column x of length >= (j+2) s (rows js ..)
+  inline void apply_reflector(int j, int kk, cdouble* x) const {
+    const double b = beta[size_t(j) * s + kk];
+    if (b == 0.0) return;
+    const cdouble* v = &refl[(size_t(j) * s + kk) * (s + 1)];
+    cdouble* top = x + size_t(j) * s;
+    cdouble* bot = x + size_t(j + 1) * s;
+    cdouble a = 0;
+    const int nt = s - kk;
+    for (int t = 0; t < nt; ++t) a += std::conj(v[t]) * top[kk + t];
+    for (int t = 0; t <= kk; ++t) a += std::conj(v[nt + t]) * bot[t];
+    a *= b;
+    for (int t = 0; t < nt; ++t) top[kk + t] -= v[t] * a;
+    for (int t = 0; t <= kk; ++t) bot[t] -= v[nt + t] * a;
+  }
+
+  // Add column block j = k: h ((k+1) s x s, column-major, ld (k+1) s) and the
+  // upper-triangular R ((s x s) column-major).  est[c] receives the relative
+  // residual estimate of right-hand side c.  Returns false when m blocks are
+  // already stored.
+  bool add_block(const cdouble* h, const cdouble* R, double* est) {
+    if (k >= m) return false;
+    const int j = k;
+    const size_t rows = size_t(j + 2) * s;
+    std::vector<cdouble> col(rows * s);
+    for (int c = 0; c < s; ++c) {
+      cdouble* x = &col[size_t(c) * rows];
+      for (size_t i = 0; i < size_t(j + 1) * s; ++i) x[i] = h[size_t(c) * (j + 1) * s + i];
+      for (int i = 0; i < s; ++i) x[size_t(j + 1) * s + i] = R[size_t(c) * s + i];
+    }
+    // earlier reflectors, column by column (independent columns)
+    const long work = long(j) * s * (s + 1) * s;
+    parallel_for(s, work > 200000 ? threads : 1, [&](int c) {
+      cdouble* x = &col[size_t(c) * rows];
+      for (int q = 0; q < j; ++q)
+        for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, x);
+    });
+    // reflectors of this block: column kk, support top rows kk..s-1 and bottom rows 0..kk
+    for (int kk = 0; kk < s; ++kk) {
+      cdouble* x = &col[size_t(kk) * rows];
+      cdouble* v = &refl[(size_t(j) * s + kk) * (s + 1)];
+      const int nt = s - kk;
+      double nrm2 = 0;
+      for (int t = 0; t < nt; ++t) nrm2 += std::norm(x[size_t(j) * s + kk + t]);
+      for (int t = 0; t <= kk; ++t) nrm2 += std::norm(x[size_t(j + 1) * s + t]);
+      const double nrm = std::sqrt(nrm2);
+      const cdouble x0 = x[size_t(j) * s + kk];
+      if (nrm == 0.0) {
+        beta[size_t(j) * s + kk] = 0.0;
+        continue;
+      }
+      const double ax0 = std::abs(x0);
+      const cdouble ph = ax0 > 0 ? x0 / ax0 : cdouble(1.0);
+      const cdouble alpha = -ph * nrm;  // x -> alpha e_0
+      for (int t = 0; t < nt; ++t) v[t] = x[size_t(j) * s + kk + t];
+      for (int t = 0; t <= kk; ++t) v[nt + t] = x[size_t(j + 1) * s + t];
+      v[0] -= alpha;
+      double vn2 = 0;
+      for (int t = 0; t <= s; ++t) vn2 += std::norm(v[t]);
+      beta[size_t(j) * s + kk] = vn2 > 0 ? 2.0 / vn2 : 0.0;
+      for (int c = kk; c < s; ++c) apply_reflector(j, kk, &col[size_t(c) * rows]);
+    }
+    // store the reduced block (rows 0 .. (j+1) s - 1)
+    off[size_t(j)] = Rt.size();
+    Rt.resize(Rt.size() + size_t(j + 1) * s * s);
+    for (int c = 0; c < s; ++c)
+      for (size_t i = 0; i < size_t(j + 1) * s; ++i) Rt[off[size_t(j)] + size_t(c) * (j + 1) * s + i] = col[size_t(c) * rows + i];
+    // the least-squares right-hand side
+    const size_t ldg = size_t(m + 1) * s;
+    for (int c = 0; c < s; ++c)
+      for (int kk = 0; kk < s; ++kk) apply_reflector(j, kk, &g[size_t(c) * ldg]);
+    ++k;
+    for (int c = 0; c < s; ++c) {
+      double r2 = 0;
+      for (int i = 0; i < s; ++i) r2 += std::norm(g[size_t(c) * ldg + size_t(k) * s + i]);
+      est[c] = std::sqrt(r2) / bnorm[c];
+    }
+    return true;
+  }
+
+  // Y (k s x s, column-major, ld k s): the block coefficients minimising the
+  // residual of every right-hand side.  Diagonal entries below eps times the
+  // largest one (deflated or breakdown directions) give zero coefficients.
+  void solve(std::vector<cdouble>& Y) const {
+    const size_t n = size_t(k) * s;
+    Y.assign(n * s, cdouble(0));
+    double dmax = 0;
+    for (size_t i = 0; i < n; ++i) dmax = std::max(dmax, std::abs(diag(i)));
+    const double eps = 1e-13 * dmax;
+    const size_t ldg = size_t(m + 1) * s;
+    parallel_for(s, n * n * s > 4000000 ? threads : 1, [&](int c) {
+      cdouble* y = &Y[size_t(c) * n];
+      for (size_t i = 0; i < n; ++i) y[i] = g[size_t(c) * ldg + i];
+      for (size_t ii = n; ii-- > 0;) {
+        const cdouble d = diag(ii);
+        if (std::abs(d) <= eps) {
+          y[ii] = 0;
+          continue;
+        }
+        y[ii] /= d;
+        // subtract column ii's entries above the diagonal
+        const int jb = int(ii / s), cc = int(ii % s);
+        const cdouble* colp = &Rt[off[size_t(jb)] + size_t(cc) * (jb + 1) * s];
+        for (size_t t = 0; t < ii; ++t) y[t] -= colp[t] * y[ii];
+      }
+    });
+  }
+
+  cdouble diag(size_t i) const {
+    const int jb = int(i / s), cc = int(i % s);
+    return Rt[off[size_t(jb)] + size_t(cc) * (jb + 1) * s + i];
+  }
+};
+
+}  // namespace mtf

@@ -102,6 +102,7 @@ void mtf_default_options(mtf_options* o) {
   o->osrc_half = 1;
   o->recycle = 1;
   o->residual_df = 1;
+  o->block_krylov = 1;
 }
 
 mtf_status mtf_mesh_create(const double* vertices, int32_t nv, const int32_t* tris, int32_t nt,
@@ -156,6 +157,8 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
       MTF_REQUIRE(sys->opt.recycle == 0 || sys->opt.recycle == 1, MTF_ERR_ARG, "recycle must be 0 or 1");
       MTF_REQUIRE(sys->opt.residual_df == 0 || sys->opt.residual_df == 1, MTF_ERR_ARG,
                   "residual_df must be 0 or 1");
+      MTF_REQUIRE(sys->opt.block_krylov == 0 || sys->opt.block_krylov == 1, MTF_ERR_ARG,
+                  "block_krylov must be 0 or 1");
       MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {
@@ -514,6 +517,7 @@ void mtf_system_destroy(mtf_system sys) {
   if (!sys) return;
   destroy_gmres(sys->gw);
   destroy_gmres32(sys->gw32);
+  destroy_block32(sys->bw);
   destroy_learned(sys->learned);
   delete sys;
 }

@@ -182,6 +182,7 @@ struct mtf_mesh_s {
 namespace mtf {
 struct GmresWork;
 struct Gmres32Work;
+struct BlockWork;
 struct LearnedState;
 }
 
@@ -217,6 +218,7 @@ struct mtf_system_s {
   int32_t mv_grid = 0;
   mtf::GmresWork* gw = nullptr;
   mtf::Gmres32Work* gw32 = nullptr;
+  mtf::BlockWork* bw = nullptr;          // block FGMRES workspace (block32.cu)
   mtf::LearnedState* learned = nullptr;  // learned OSRC correction (learned.cu)
   bool learned_active = false;           // used by the current solve (cleared by its fallback)
 };
@@ -278,6 +280,12 @@ void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, 
                        cudaStream_t s);
 void launch_osrc_apply_f32(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
                            cudaStream_t s);
+// set-up of the FP64-output apply done at every block-OSRC assembly, and the
+// apply itself with the FP32 copy of r in the caller's r32 (2 n_total nrhs
+// floats): allocates nothing
+void osrc_prepare_fp64_apply(mtf_system sys, cudaStream_t s);
+void launch_osrc_apply_prepared(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
+                                float* r32, cudaStream_t s);
 // Streaming matvec of the FP32-stored operator (matvec32.cu).  The dense
 // part reads the FP32 vector x32 (column stride ld32, complex units); the
 // exchange rows read x.  f32: FP32 in and out.
@@ -340,6 +348,15 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
                  cudaStream_t s);
 void destroy_gmres(GmresWork* w);
 void destroy_gmres32(Gmres32Work* w);
+void destroy_block32(BlockWork* w);
+// One block flexible GMRES cycle of the mixed path on M D = R from D = 0 for
+// the s right-hand sides together (block32.cu): one Krylov space of blocks of
+// s vectors, FP32 basis, FP64 Hessenberg sums; x += D.  Stops when every
+// right-hand side's estimate reaches tol relative to its ||r|| (reached =
+// true), after opt.restart block steps, after max_iter block steps or when
+// every direction is deflated; iters[c] += block steps.
+mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,
+                          std::vector<int>& iters, bool& reached, cudaStream_t st);
 void destroy_learned(LearnedState* l);
 // learned OSRC correction (learned.cu)
 int64_t learned_param_count(mtf_system sys);

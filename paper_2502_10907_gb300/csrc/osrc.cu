@@ -625,6 +625,7 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
         Cre.p, Cim.p, N, ldt, reinterpret_cast<float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i]));
   }
   if (sys->opt.osrc_half) osrc_half_copy(sys, s);
+  osrc_prepare_fp64_apply(sys, s);
   MTF_CUDA(cudaStreamSynchronize(s));  // scratch and d_pd / d_keps are freed on return
 }
 
@@ -681,6 +682,32 @@ void launch_osrc_apply(mtf_system sys, const double* r, int64_t ldr, double* z, 
   if (sys->d_osrc_r32.n < size_t(n2) * nrhs) sys->d_osrc_r32.alloc(size_t(n2) * nrhs);
   MTF_LAUNCH(KID_OSRC, s, k_to_f32_cols<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(r, ldr, n2, nrhs, sys->d_osrc_r32.p));
   osrc_stream<double>(sys, sys->d_osrc_r32.p, m->n_total, z, ldz, nrhs, s);
+}
+
+// Everything the FP64-output apply keeps per system or mesh (the error word
+// and grid size of the streaming kernels, the FP32 T~ stream units, the
+// per-row piece sums), set up at assembly so that
+// launch_osrc_apply_prepared allocates nothing.
+void osrc_prepare_fp64_apply(mtf_system sys, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  stream_prepare(sys, s);
+  const StreamUnits& su = ensure_os_units<1>(sys, s);
+  const size_t npart = size_t(m->n_rows) * su.pmax * 16;
+  if (sys->d_os_part.n < npart) sys->d_os_part.alloc(npart);
+}
+
+// launch_osrc_apply with the FP32 copy of r written to the caller's r32
+// (2 n_total nrhs floats); needs osrc_prepare_fp64_apply (done by every
+// block-OSRC assembly) and allocates nothing.
+void launch_osrc_apply_prepared(mtf_system sys, const double* r, int64_t ldr, double* z, int64_t ldz, int nrhs,
+                                float* r32, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  MTF_REQUIRE(m->os_units.ready && sys->d_mv_ctl.p && sys->mv_grid > 0 &&
+                  sys->d_os_part.n >= size_t(m->n_rows) * m->os_units.pmax * 16,
+              MTF_ERR_ARG, "block-OSRC apply tables are not prepared (system not assembled with block-OSRC)");
+  const int64_t n2 = 2 * m->n_total;
+  MTF_LAUNCH(KID_OSRC, s, k_to_f32_cols<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(r, ldr, n2, nrhs, r32));
+  osrc_stream<double>(sys, r32, m->n_total, z, ldz, nrhs, s);
 }
 
 // FP32 in, FP32 out (the FP32-basis inner solver)

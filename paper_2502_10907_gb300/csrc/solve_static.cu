@@ -1,11 +1,15 @@
 // mtf_solve_static: the GMRES solve of mtf_solve with every device buffer it
-// needs (right-hand sides, Krylov basis, work vectors, Hessenberg columns,
-// wave parameters) carved out of one fixed, file-scope device array instead
-// of cudaMalloc.  It exists for callers that must not allocate device memory
-// while they run -- code that executes under a custom or pre-reserved memory
-// budget, or inside a host callback / service loop where a cudaMalloc could
-// block on device synchronisation -- and who are willing to trade the size
-// limit below for that.  Same algorithm and kernels as mtf_solve.
+// needs (right-hand sides, Krylov basis, preconditioned directions, work
+// vectors, Hessenberg columns, wave parameters) carved out of one fixed,
+// file-scope device array instead of cudaMalloc.  It exists for callers that
+// must not allocate device memory while they run -- code that executes under
+// a custom or pre-reserved memory budget, or inside a host callback / service
+// loop where a cudaMalloc could block on device synchronisation -- and who
+// are willing to trade the size limit below for that.  Same algorithm as the
+// FP64 path of mtf_solve (restarted flexible GMRES, right-preconditioned by
+// block-OSRC when the system was assembled with it, CGS2, host Givens
+// rotations) with its own simpler reduction kernels, so the two agree to
+// rounding, not bit for bit.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -52,11 +56,15 @@ static double* scratch_address() {
 
 size_t static_solve_capacity() { return kStaticScratchDoubles; }
 
-// doubles of workspace a solve of nrhs right-hand sides with restart m needs
-size_t static_solve_need(int64_t n, int nrhs, int m) {
+// doubles of workspace a solve of nrhs right-hand sides with restart m needs:
+//   2 n nrhs (m + 4) + (6 m + 8) nrhs + 9 nrhs + 64, and with block-OSRC
+//   another 2 n nrhs m (Z) + n nrhs (FP32 copy of the preconditioner input)
+size_t static_solve_need(int64_t n, int nrhs, int m, bool pre) {
   const size_t n2 = size_t(n) * nrhs * 2;
-  return n2 * size_t(m + 1) /*V*/ + 3 * n2 /*w, r, b*/ + size_t(2 * (m + 1) + 1) * nrhs * 2 /*h*/ +
-         size_t(m + 1) * nrhs * 2 /*y*/ + size_t(nrhs) * 9 /*dirs, pols*/ + 64 /*alignment slack*/;
+  size_t need = n2 * size_t(m + 1) /*V*/ + 3 * n2 /*w, r, b*/ + size_t(2 * (m + 1) + 1) * nrhs * 2 /*h*/ +
+                size_t(m + 1) * nrhs * 2 /*y*/ + size_t(nrhs) * 9 /*dirs, pols*/ + 64 /*alignment slack*/;
+  if (pre) need += n2 * size_t(m) /*Z*/ + n2 / 2 /*r32*/;
+  return need;
 }
 
 static inline unsigned nb(int64_t n, int t) { return unsigned((n + t - 1) / t); }
@@ -68,7 +76,8 @@ mtf_status solve_static(mtf_system sys, int nrhs, const double* dirs, const doub
   const int m = std::max(1, sys->opt.restart);
   MTF_REQUIRE(sys->opt.precision == MTF_PREC_FP64, MTF_ERR_ARG,
               "mtf_solve_static supports systems assembled with MTF_PREC_FP64 only");
-  const size_t need = static_solve_need(n, nrhs, m);
+  const bool pre = sys->opt.precond == MTF_PRECOND_OSRC;
+  const size_t need = static_solve_need(n, nrhs, m, pre);
   MTF_REQUIRE(need <= kStaticScratchDoubles, MTF_ERR_ARG,
               "mtf_solve_static: the solve needs " + std::to_string(need) +
                   " doubles of workspace but the static workspace holds " +
@@ -91,6 +100,9 @@ mtf_status solve_static(mtf_system sys, int nrhs, const double* dirs, const doub
   double* yd = take(size_t(m + 1) * nrhs * 2);
   double* d_dirs = take(size_t(nrhs) * 3);
   double* d_pols = take(size_t(nrhs) * 6);
+  // flexible right preconditioning: z_j = P v_j in Z, the FP32 copy of v_j
+  double* Z = pre ? take(n2 * size_t(m)) : nullptr;
+  float* r32 = pre ? reinterpret_cast<float*>(take(n2 / 2)) : nullptr;
   // every call shares the array: clear the part this call uses
   MTF_CUDA(cudaMemsetAsync(base, 0, off * sizeof(double), s));
   MTF_CUDA(cudaMemcpyAsync(d_dirs, dirs, size_t(nrhs) * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -153,7 +165,13 @@ mtf_status solve_static(mtf_system sys, int nrhs, const double* dirs, const doub
     ++restarts;
     for (int c = 0; c < nrhs; ++c) active[c] = !done[c];
     for (int j = 0; j < m && total < max_iter; ++j) {
-      launch_matvec(sys, V + 2 * size_t(j) * n, int64_t(ldv) * n, r, n, nrhs, s);
+      if (pre) {
+        launch_osrc_apply_prepared(sys, V + 2 * size_t(j) * n, int64_t(ldv) * n, Z + 2 * size_t(j) * n,
+                                   int64_t(m) * n, nrhs, r32, s);
+        launch_matvec(sys, Z + 2 * size_t(j) * n, int64_t(m) * n, r, n, nrhs, s);
+      } else {
+        launch_matvec(sys, V + 2 * size_t(j) * n, int64_t(ldv) * n, r, n, nrhs, s);
+      }
       dim3 gd(unsigned(j + 1), unsigned(nrhs));
       MTF_LAUNCH(KID_DOTS, s, k_dots<<<gd, 256, 0, s>>>(V, r, n, ldv, hA, m + 1));
       MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nb(n * nrhs, 256), 256, 0, s>>>(V, hA, j + 1, n, ldv, m + 1, -1.0, r, nrhs));
@@ -229,7 +247,9 @@ mtf_status solve_static(mtf_system sys, int nrhs, const double* dirs, const doub
     }
     if (jmax > 0) {
       MTF_CUDA(cudaMemcpyAsync(yd, yhost.data(), yhost.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nb(n * nrhs, 256), 256, 0, s>>>(V, yd, jmax, n, ldv, m + 1, 1.0, x_dev, nrhs));
+      // x += Z y (flexible) or V y
+      MTF_LAUNCH(KID_AXPY, s, k_axpy_multi<<<nb(n * nrhs, 256), 256, 0, s>>>(pre ? Z : V, yd, jmax, n, pre ? m : ldv,
+                                                                             m + 1, 1.0, x_dev, nrhs));
       MTF_CUDA(cudaStreamSynchronize(s));
     }
   }

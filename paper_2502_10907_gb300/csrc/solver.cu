@@ -598,7 +598,12 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
       bool reached = false;
-      status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
+      // systems with a learned correction keep the per-rhs spaces, so that
+      // their plain and corrected solves compare like for like
+      if (sys->opt.block_krylov && nrhs > 1 && !sys->learned)
+        status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s);
+      else
+        status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
       if (status != MTF_OK) break;
       int mx = 0;
       for (int c = 0; c < nrhs; ++c) {

@@ -261,14 +261,15 @@ def test_osrc_preconditioned_solves(api, oracle_cache, name):
 # of 200 still stagnate in FP64 there, so that case runs one long cycle per
 # refinement step).  Same 1e-5 bound against the oracle LU.
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("block", [0, 1])
 @pytest.mark.parametrize("precond,restart", [(0, 2000), (1, 50)])
-def test_mixed_restarted_six_rhs(api, oracle_cache, precond, restart):
+def test_mixed_restarted_six_rhs(api, oracle_cache, precond, restart, block):
     cfg, sk, ref = _case(oracle_cache, "split")
     mesh = api.Mesh.from_inputs(cfg["mesh"])
     dirs, pols = mi.plane_wave_batch(3)
     xr = ref.solve_lu(ref.rhs(dirs, pols))
     sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, tol=1e-8, restart=restart,
-                      max_iter=8000, max_refine=8, precond=precond)
+                      max_iter=8000, max_refine=8, precond=precond, block_krylov=block)
     x, st = sysg.solve(dirs, pols)
     assert st.converged == 1
     assert st.restarts >= 2, st.restarts
@@ -297,7 +298,7 @@ def test_recycled_second_cycle_matches_oracle_with_fewer_iterations(api, oracle_
     its = {}
     for rec in (0, 1):
         sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, precond=1, tol=1e-8,
-                          restart=400, max_iter=4000, max_refine=6, recycle=rec)
+                          restart=400, max_iter=4000, max_refine=6, recycle=rec, block_krylov=0)
         x, st = sysg.solve(cfg["dirs"], cfg["pols"])
         assert st.converged == 1 and st.restarts >= 2
         errs = np.linalg.norm(x.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
