@@ -115,6 +115,12 @@ typedef struct {
                            normalisation); restart then counts block steps of
                            nrhs vectors.  0: one Krylov space per right-hand
                            side.  Default 1                                  */
+  int32_t mv_tensor;    /* mixed mode: 1: the FP32 matvec of the inner solver
+                           (mtf_matvec_f32) runs on the tensor cores from an
+                           FP16 hi + lo split of the stored blocks (about 22
+                           significant bits, FP32 accumulation), reading
+                           every stored entry once for up to 32 right-hand
+                           sides; 0: the FMA stream, once per 4.  Default 1  */
 } mtf_options;
 
 typedef struct {
@@ -247,6 +253,15 @@ mtf_status mtf_rhs(mtf_system sys, int32_t nrhs, const double* dirs, const doubl
  * x_out holding the last iterate) if some right-hand side misses tol. */
 mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
                      void* x_out, mtf_solve_stats* stats, void* stream);
+
+/* Solve M u = b (Problem 2) for nrhs given right-hand sides with the solver
+ * of mtf_solve (same options, preconditioning, refinement and stopping test
+ * relative to ||b|| per right-hand side).  b: device complex128
+ * n_total x nrhs (read only); x_out: device complex128 n_total x nrhs, must
+ * not overlap b.  Used e.g. for refinement against another system's
+ * residuals.  Errors as mtf_solve. */
+mtf_status mtf_solve_rhs(mtf_system sys, int32_t nrhs, const void* b, void* x_out, mtf_solve_stats* stats,
+                         void* stream);
 
 /* mtf_solve without device allocation (the paper has no counterpart; this
  * is an interface for callers that cannot allocate).  Some callers must not

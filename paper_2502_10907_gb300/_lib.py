@@ -32,7 +32,7 @@ class mtf_options(ctypes.Structure):
                 ("osrc_np", ctypes.c_int32), ("osrc_theta", ctypes.c_double),
                 ("osrc_eps_scale", ctypes.c_double), ("max_refine", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("osrc_half", ctypes.c_int32), ("recycle", ctypes.c_int32), ("residual_df", ctypes.c_int32),
-                ("block_krylov", ctypes.c_int32)]
+                ("block_krylov", ctypes.c_int32), ("mv_tensor", ctypes.c_int32)]
 
 
 class mtf_solve_stats(ctypes.Structure):
@@ -64,6 +64,7 @@ _SIGS = {
     "mtf_rhs": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
+    "mtf_solve_rhs": (_i32, [_vp, _i32, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_farfield": (_i32, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "mtf_system_destroy": (None, [_vp]),
     "mtf_learned_param_count": (_i64, [_vp]),
@@ -230,6 +231,15 @@ def mtf_solve(sys_, dirs, pols, x_out, stream=0, raise_on_noconv=True):
     p = np.ascontiguousarray(pols, dtype=np.complex128)
     st = mtf_solve_stats()
     status = load().mtf_solve(sys_, len(d), _ptr(d), _ptr(p), _ptr(x_out), ctypes.byref(st), stream or None)
+    if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
+        _check(status)
+    return st, status
+
+
+def mtf_solve_rhs(sys_, b, x_out, stream=0, raise_on_noconv=True):
+    """Solve M x = b for device right-hand sides b (nrhs, n_total) complex128."""
+    st = mtf_solve_stats()
+    status = load().mtf_solve_rhs(sys_, int(b.shape[0]), _ptr(b), _ptr(x_out), ctypes.byref(st), stream or None)
     if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
         _check(status)
     return st, status

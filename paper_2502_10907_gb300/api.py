@@ -171,6 +171,13 @@ class System:
         st, status = L.mtf_solve(self.handle, dirs, pols, x, _stream(), raise_on_noconv)
         return x, st
 
+    def solve_rhs(self, b, raise_on_noconv=True):
+        """Solve M x = b for b (nrhs, n_total) complex128 on the GPU."""
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        st, status = L.mtf_solve_rhs(self.handle, b, x, _stream(), raise_on_noconv)
+        return x, st
+
     def nearfield(self, x, points, domains):
         """U at points (P, 3) in subdomains domains (P,) by Eq. 8 -> (nrhs, P, 3) complex128:
         the scattered field in subdomain 0, the total field in the others."""

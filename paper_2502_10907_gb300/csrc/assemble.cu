@@ -583,7 +583,8 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
       MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<float><<<sblocks, 256, 0, s>>>(
           A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
           sys->ss_npts[1], sys->ss_npts[2], sys->d_TK32.p));
-    tile_matvec_operator(sys, s);
+    if (sys->opt.mv_tensor) tc_build_operator(sys, s);
+    else tile_matvec_operator(sys, s);
   }
   launch_exchange_values(sys, s);
 }

@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "block_krylov.h"
@@ -419,8 +421,10 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   BlockLSQ lsq;
   lsq.init(s, m, R.data(), bnorm.data());
 
-  std::vector<cdouble> h;
+  std::vector<cdouble> h, R2(size_t(s) * s), Rn(size_t(s) * s, cdouble(0));
   int kdone = 0;
+  const bool debug = std::getenv("MTF_BLOCK_DEBUG") != nullptr;
+  const double tau = std::getenv("MTF_BLOCK_TAU") ? std::atof(std::getenv("MTF_BLOCK_TAU")) : kDeflateTau;
   const int jend = std::min(m, std::max(1, max_iter));
   for (int j = 0; j < jend; ++j) {
     float* Vj = B.V.p + 2 * int64_t(j) * vstride;
@@ -464,10 +468,36 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     fetch_gram(G, Gh);
     for (int c = 0; c < s; ++c) ref[c] = Gp[size_t(c) * s + c].real();
     if (!finite) return MTF_ERR_NAN;
-    const int nk = deflating_cholesky(s, Gh.data(), ref.data(), kDeflateTau, R.data(), T.data(), kept);
+    const int nk = deflating_cholesky(s, Gh.data(), ref.data(), tau, R.data(), T.data(), kept);
     upload_T(T);
-    bxform(B.W.p, ldn, B.C.p, s, B.V.p + 2 * int64_t(j + 1) * vstride, ldn, ldn, st);
-    lsq.add_block(h.data(), R.data(), est.data());
+    bxform(B.W.p, ldn, B.C.p, s, B.D.p, ldn, ldn, st);
+    // second Cholesky pass (CholQR2): the first leaves V = W R^-1
+    // orthonormal only to about cond(W) times the FP32 rounding;
+    // V_{j+1} = V R2^-1 and R_{j+1} = R2 R
+    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
+    bdots(sys, B.D.p, s, ldn, B.D.p, ldn, s, ldn, G, s, st);
+    MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, size_t(2) * s * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaStreamSynchronize(st));
+    fetch_gram(G, Gh);
+    for (int c = 0; c < s; ++c) ref[c] = kept[c] ? 1.0 : 0.0;
+    std::vector<int> kept2;
+    deflating_cholesky(s, Gh.data(), ref.data(), 1e-3, R2.data(), T.data(), kept2);
+    upload_T(T);
+    bxform(B.D.p, ldn, B.C.p, s, B.V.p + 2 * int64_t(j + 1) * vstride, ldn, ldn, st);
+    for (int c = 0; c < s; ++c)
+      for (int i = 0; i <= c; ++i) {
+        cdouble a = 0;
+        for (int p = i; p <= c; ++p) a += R2[size_t(p) * s + i] * R[size_t(c) * s + p];
+        Rn[size_t(c) * s + i] = a;
+      }
+    lsq.add_block(h.data(), Rn.data(), est.data());
+    if (debug && (j % 25 == 0 || j < 5)) {
+      double emax = 0;
+      for (double e : est) emax = std::max(emax, e);
+      int nk2 = 0;
+      for (int v : kept2) nk2 += v;
+      std::fprintf(stderr, "block j=%d kept=%d/%d est_max=%.3e\n", j, nk, nk2, emax);
+    }
     kdone = j + 1;
     bool all = true;
     for (int c = 0; c < s; ++c) {

@@ -103,6 +103,7 @@ void mtf_default_options(mtf_options* o) {
   o->recycle = 1;
   o->residual_df = 1;
   o->block_krylov = 1;
+  o->mv_tensor = 1;
 }
 
 mtf_status mtf_mesh_create(const double* vertices, int32_t nv, const int32_t* tris, int32_t nt,
@@ -159,6 +160,7 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
                   "residual_df must be 0 or 1");
       MTF_REQUIRE(sys->opt.block_krylov == 0 || sys->opt.block_krylov == 1, MTF_ERR_ARG,
                   "block_krylov must be 0 or 1");
+      MTF_REQUIRE(sys->opt.mv_tensor == 0 || sys->opt.mv_tensor == 1, MTF_ERR_ARG, "mv_tensor must be 0 or 1");
       MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {
@@ -301,6 +303,22 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
     b.alloc(size_t(sys->mesh->n_total) * nrhs * 2);
     launch_rhs(sys, nrhs, dd.p, dp.p, b.p, s);
     st = solve(sys, nrhs, b.p, static_cast<double*>(x_out), stats, s);
+    MTF_CUDA(cudaStreamSynchronize(s));
+    if (st == MTF_ERR_NOCONV) set_last_error("GMRES did not reach the tolerance within max_iter");
+    if (st == MTF_ERR_NAN) set_last_error("non-finite residual in GMRES");
+  });
+  return g != MTF_OK ? g : st;
+}
+
+mtf_status mtf_solve_rhs(mtf_system sys, int32_t nrhs, const void* b, void* x_out, mtf_solve_stats* stats,
+                         void* stream) {
+  mtf_status st = MTF_OK;
+  mtf_status g = guarded([&] {
+    MTF_REQUIRE(sys && b && x_out, MTF_ERR_ARG, "null argument");
+    MTF_REQUIRE(nrhs >= 1, MTF_ERR_ARG, "nrhs must be >= 1");
+    MTF_REQUIRE(b != x_out, MTF_ERR_ARG, "b and x_out must not overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = solve(sys, nrhs, static_cast<const double*>(b), static_cast<double*>(x_out), stats, s);
     MTF_CUDA(cudaStreamSynchronize(s));
     if (st == MTF_ERR_NOCONV) set_last_error("GMRES did not reach the tolerance within max_iter");
     if (st == MTF_ERR_NAN) set_last_error("non-finite residual in GMRES");
@@ -518,6 +536,7 @@ void mtf_system_destroy(mtf_system sys) {
   destroy_gmres(sys->gw);
   destroy_gmres32(sys->gw32);
   destroy_block32(sys->bw);
+  destroy_tc(sys->tc);
   destroy_learned(sys->learned);
   delete sys;
 }

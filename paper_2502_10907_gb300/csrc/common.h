@@ -183,6 +183,7 @@ namespace mtf {
 struct GmresWork;
 struct Gmres32Work;
 struct BlockWork;
+struct TcMatvec;
 struct LearnedState;
 }
 
@@ -219,6 +220,7 @@ struct mtf_system_s {
   mtf::GmresWork* gw = nullptr;
   mtf::Gmres32Work* gw32 = nullptr;
   mtf::BlockWork* bw = nullptr;          // block FGMRES workspace (block32.cu)
+  mtf::TcMatvec* tc = nullptr;           // tensor-core matvec tables and operator copy (mv_tc.cu)
   mtf::LearnedState* learned = nullptr;  // learned OSRC correction (learned.cu)
   bool learned_active = false;           // used by the current solve (cleared by its fallback)
 };
@@ -228,7 +230,7 @@ namespace mtf {
 enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
-  KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_COUNT
+  KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_MVTC, KID_MVTC_PREP, KID_MVTC_COMBINE, KID_TC_TILE, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
@@ -349,6 +351,12 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
 void destroy_gmres(GmresWork* w);
 void destroy_gmres32(Gmres32Work* w);
 void destroy_block32(BlockWork* w);
+void destroy_tc(TcMatvec* t);
+// tensor-core matvec (mv_tc.cu): the FP16 hi / lo tiled operator copy built
+// after every mixed assembly (opt.mv_tensor), and y = M x from it
+void tc_build_operator(mtf_system sys, cudaStream_t s);
+bool tc_matvec_enabled(mtf_system sys);
+void launch_matvec_tc(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs, cudaStream_t s);
 // One block flexible GMRES cycle of the mixed path on M D = R from D = 0 for
 // the s right-hand sides together (block32.cu): one Krylov space of blocks of
 // s vectors, FP32 basis, FP64 Hessenberg sums; x += D.  Stops when every

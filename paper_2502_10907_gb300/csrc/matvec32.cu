@@ -278,6 +278,10 @@ void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const 
 
 void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
                        cudaStream_t s) {
+  if (tc_matvec_enabled(sys)) {
+    launch_matvec_tc(sys, x, ldx, y, ldy, nrhs, s);
+    return;
+  }
   mv_all<float, float>(sys, x, ldx, x, ldx, y, ldy, nrhs, s);
 }
 

@@ -1,0 +1,565 @@
+// Block matvec of the mixed inner solver on the fifth-generation tensor cores
+// (Eq. 16 applied as y = 2 A x + X x, block by block): every stored entry of
+// the dense {T_i, K_i} is read ONCE per apply for up to 32 right-hand sides,
+// instead of once per group of 4 in the FMA stream.
+//
+// Formulation and layout: tc_plan.h (interleaved complex rows, two real
+// input columns per complex input, FP16 hi + lo split of both operands after
+// power-of-two scaling, three products with FP32 accumulation).
+//
+// Kernel k_mv_tc (one persistent CTA per SM, 6 warps):
+//  - warp 0, one lane: producer.  For every chunk of the CTA's units it
+//    loads the 64 KB operator tile (4 parts) and the input chunk (hi, lo)
+//    with two cp.async.bulk.tensor.4d copies (128-byte swizzle) into a ring
+//    of S stages, completing on the stage's "full" mbarrier;
+//  - warp 1: allocates TMEM (two accumulator buffers of 2 NB columns:
+//    T products, K products); one lane issues per K = 16 step the six
+//    tcgen05.mma of the split products and commits each stage back to its
+//    "empty" barrier, and each finished unit to the buffer's "full" barrier;
+//  - warps 2-5: epilogue.  Each reads its 32 TMEM lanes (rows) of the
+//    finished buffer with tcgen05.ld and writes the unit's raw row sums to a
+//    partial buffer, then frees the TMEM buffer.
+// k_mv_tc_combine then adds the pieces of each row in order, undoes the
+// scalings and applies 2 (K u_D + rho^-1 T u_N), 2 (-rho T u_D + K u_N) and
+// the exchange rows, as the FMA stream's combine does.  Every wait is
+// bounded (0.5 s) and ends in the error word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "common.h"
+#include "tc.cuh"
+#include "tc_plan.h"
+
+namespace mtf {
+
+struct TcMatvec {
+  TcPlan plan;
+  int n_cta = 0;
+  bool planned = false, built = false;
+  DevBuf<__half> A;                    // tiled hi / lo operator
+  DevBuf<unsigned> amax;               // per block: largest |re|, |im| of T and K (float bits)
+  DevBuf<int4> units, tile_info;       // unit {blk, mt, kc0, kc1}; tile {blk, mt, kc, 0}
+  DevBuf<int2> chunk_info;             // chunk {blk, kc}
+  DevBuf<int> sched, sched_off, blk_unit_base, blk_pieces, blk_nkc;
+  DevBuf<int64_t> blk_tile_base, blk_chunk_base;
+  DevBuf<__half> B;                    // input chunks for up to 32 right-hand sides
+  DevBuf<float> part;                  // per unit: 128 rows x 2 NB raw sums
+  DevBuf<unsigned> colmax;             // per right-hand side of a pass (float bits)
+  CUtensorMap amap{}, bmap{};
+  const void* amap_ptr = nullptr;
+  const void* bmap_ptr = nullptr;
+  int bmap_nb = 0;
+};
+
+void destroy_tc(TcMatvec* t) { delete t; }
+
+// power-of-two scale s with amax * s < 2^14 (1 for amax = 0), and 1 / s
+__device__ __forceinline__ float tc_scale(unsigned bits) {
+  const float a = __uint_as_float(bits);
+  if (!(a > 0.f)) return 1.f;
+  int ex;
+  frexpf(a, &ex);
+  return ldexpf(1.f, 14 - ex);
+}
+__device__ __forceinline__ float tc_inv_scale(unsigned bits) {
+  const float a = __uint_as_float(bits);
+  if (!(a > 0.f)) return 1.f;
+  int ex;
+  frexpf(a, &ex);
+  return ldexpf(1.f, ex - 14);
+}
+
+// hi = fp16(v), lo = fp16(v - hi)
+__device__ __forceinline__ void tc_split(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+// amax[i] = max over block i's stored T and K entries of |re|, |im|
+__global__ void k_tc_blkmax(const float4* __restrict__ TK, const int64_t* __restrict__ blk_mat_off,
+                            const int32_t* __restrict__ blk_N, unsigned* __restrict__ amax) {
+  const int i = blockIdx.y;
+  const int64_t N = blk_N[i];
+  const float4* e = TK + blk_mat_off[i];
+  float m = 0.f;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < N * N; t += int64_t(gridDim.x) * blockDim.x) {
+    const float4 v = e[t];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax + i, __float_as_uint(m));
+}
+
+// Tiled hi / lo copy: thread = (tile, row, group g of 4 complex columns);
+// writes 8 halves (16 bytes) into each of the 4 parts.
+__global__ void __launch_bounds__(256) k_tc_tile_a(const float4* __restrict__ TK, const int4* __restrict__ tile_info,
+                                                   const int64_t* __restrict__ blk_mat_off,
+                                                   const int32_t* __restrict__ blk_N, const unsigned* __restrict__ amax,
+                                                   int64_t n_tiles, __half* __restrict__ A) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_tiles * kTcRows * 8) return;
+  const int64_t tile = t / (kTcRows * 8);
+  const int row = int((t / 8) % kTcRows), g = int(t % 8);
+  const int4 info = tile_info[tile];
+  const int i = info.x, N = blk_N[i];
+  const int r = info.y * kTcRows + row;
+  const float s = tc_scale(amax[i]);
+  __half h[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int n = info.z * kTcCols + 4 * g + q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < N && n < N) v = TK[blk_mat_off[i] + int64_t(r) * N + n];
+    tc_split(v.x * s, h[0][2 * q], h[1][2 * q]);          // T re
+    tc_split(v.y * s, h[0][2 * q + 1], h[1][2 * q + 1]);  // T im
+    tc_split(v.z * s, h[2][2 * q], h[3][2 * q]);          // K re
+    tc_split(v.w * s, h[2][2 * q + 1], h[3][2 * q + 1]);  // K im
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    *reinterpret_cast<uint4*>(A + tc_a_index(tile, p, row, 8 * g)) = *reinterpret_cast<const uint4*>(h[p]);
+}
+
+// colmax[c] = max |re|, |im| of input column c0 + c (n complex entries)
+__global__ void k_tc_colmax(const float* __restrict__ x, int64_t ldx, int64_t n, int c0, unsigned* __restrict__ colmax) {
+  const int c = blockIdx.y;
+  const float2* xc = reinterpret_cast<const float2*>(x + 2 * int64_t(c0 + c) * ldx);
+  float m = 0.f;
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const float2 v = xc[k];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + c, __float_as_uint(m));
+}
+
+// Input chunks: thread = (chunk, column col, group g of 4 complex entries);
+// column 4 c + 2 t + f holds form f of u_t of right-hand side c0 + c.
+__global__ void __launch_bounds__(256) k_tc_build_b(const float* __restrict__ x, int64_t ldx, int c0, int nc, int nb,
+                                                    const int2* __restrict__ chunk_info, int64_t n_chunks,
+                                                    const int32_t* __restrict__ blk_N,
+                                                    const int64_t* __restrict__ blk_dof_off,
+                                                    const unsigned* __restrict__ colmax, __half* __restrict__ B) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_chunks * nb * 8) return;
+  const int64_t chunk = t / (int64_t(nb) * 8);
+  const int col = int((t / 8) % nb), g = int(t % 8);
+  const int c = col >> 2, slot = (col >> 1) & 1, form = col & 1;
+  __half hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hi[q] = lo[q] = __float2half_rn(0.f);
+  if (c < nc) {
+    const int2 info = chunk_info[chunk];
+    const int N = blk_N[info.x];
+    const float s = tc_scale(colmax[c]);
+    const float2* xc = reinterpret_cast<const float2*>(x + 2 * (int64_t(c0 + c) * ldx + blk_dof_off[info.x] +
+                                                                 int64_t(slot) * N));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = info.y * kTcCols + 4 * g + q;
+      float2 v = make_float2(0.f, 0.f);
+      if (n < N) v = xc[n];
+      const float a = form == 0 ? v.x : v.y, b = form == 0 ? -v.y : v.x;
+      tc_split(a * s, hi[2 * q], lo[2 * q]);
+      tc_split(b * s, hi[2 * q + 1], lo[2 * q + 1]);
+    }
+  }
+  *reinterpret_cast<uint4*>(B + tc_b_index(chunk, 0, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(hi);
+  *reinterpret_cast<uint4*>(B + tc_b_index(chunk, 1, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(lo);
+}
+
+template <int NB>
+struct TcCfg {
+  static constexpr int SA = kTcParts * kTcRows * 128;      // operator tile bytes (64 KB)
+  static constexpr int SBB = 2 * NB * 128;                  // input chunk bytes (hi + lo)
+  static constexpr int SB = SA + SBB;                       // stage bytes (a multiple of 1024)
+  static constexpr int S0 = (220 * 1024) / SB;
+  static constexpr int S = S0 > 4 ? 4 : S0;
+  static constexpr uint32_t TMEM = 4 * NB < 32 ? 32 : 4 * NB;  // two buffers of 2 NB columns
+  static constexpr size_t smem = size_t(S) * SB + 1024 + 256;
+  static_assert(S >= 2, "the stage ring needs two stages");
+  static_assert(smem <= 232448, "shared memory above the per-CTA limit");
+  static_assert(SB % 1024 == 0, "stages must keep the 1024-byte alignment of the swizzled tiles");
+};
+
+constexpr uint64_t kTcWaitNs = 500000000ull;
+
+template <int NB>
+__global__ void __launch_bounds__(192, 1) k_mv_tc(const __grid_constant__ CUtensorMap amap,
+                                                  const __grid_constant__ CUtensorMap bmap,
+                                                  const int4* __restrict__ units, const int* __restrict__ sched,
+                                                  const int* __restrict__ sched_off,
+                                                  const int64_t* __restrict__ blk_tile_base,
+                                                  const int* __restrict__ blk_nkc,
+                                                  const int64_t* __restrict__ blk_chunk_base, float* __restrict__ part,
+                                                  unsigned* __restrict__ err) {
+  using C = TcCfg<NB>;
+  constexpr int S = C::S, SB = C::SB, SA = C::SA;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(S) * SB);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q_begin = sched_off[blockIdx.x], q_end = sched_off[blockIdx.x + 1];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, C::TMEM);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch_map(&amap);
+      tma_prefetch_map(&bmap);
+      const uint64_t pol_a = l2_policy_evict_first(), pol_b = l2_policy_evict_last();
+      int k = 0;
+      bool ok = true;
+      for (int q = q_begin; q < q_end && ok; ++q) {
+        const int4 U = units[sched[q]];
+        const int64_t tb = blk_tile_base[U.x] + int64_t(U.y) * blk_nkc[U.x];
+        const int64_t cb = blk_chunk_base[U.x];
+        for (int kc = U.z; kc < U.w; ++kc, ++k) {
+          const int st = k % S;
+          if (!mbar_wait_bounded(&empty[st], (uint32_t(k / S) & 1u) ^ 1u, kTcWaitNs)) {
+            atomicExch(err, 1u);
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + size_t(st) * SB;
+          mbar_arrive_expect_tx(&full[st], uint32_t(SB));
+          tma_load_4d(sa, &amap, 0, 0, 0, int(tb + kc), &full[st], pol_a);
+          tma_load_4d(sa + SA, &bmap, 0, 0, 0, int(cb + kc), &full[st], pol_b);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16_m128(NB);
+      int k = 0, ub = 0;
+      bool ok = true;
+      for (int q = q_begin; q < q_end && ok; ++q, ++ub) {
+        const int4 U = units[sched[q]];
+        const int buf = ub & 1;
+        if (!mbar_wait_bounded(&tempty[buf], (uint32_t(ub >> 1) & 1u) ^ 1u, kTcWaitNs)) {
+          atomicExch(err, 1u);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dT = tmem + uint32_t(buf * 2 * NB), dK = dT + uint32_t(NB);
+        for (int kc = U.z; kc < U.w; ++kc, ++k) {
+          const int st = k % S;
+          if (!mbar_wait_bounded(&full[st], uint32_t(k / S) & 1u, kTcWaitNs)) {
+            atomicExch(err, 1u);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + size_t(st) * SB), sb = sa + SA;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t th = sw128_desc(sa + kk * 32), tl = sw128_desc(sa + 16384 + kk * 32);
+            const uint64_t kh = sw128_desc(sa + 32768 + kk * 32), kl = sw128_desc(sa + 49152 + kk * 32);
+            const uint64_t bh = sw128_desc(sb + kk * 32), bl = sw128_desc(sb + NB * 128 + kk * 32);
+            const uint32_t acc = (kc != U.z || kk != 0) ? 1u : 0u;
+            tc_mma_f16(dT, th, bh, idesc, acc);
+            tc_mma_f16(dT, th, bl, idesc, 1u);
+            tc_mma_f16(dT, tl, bh, idesc, 1u);
+            tc_mma_f16(dK, kh, bh, idesc, acc);
+            tc_mma_f16(dK, kh, bl, idesc, 1u);
+            tc_mma_f16(dK, kl, bh, idesc, 1u);
+          }
+          tc_commit(&empty[st]);  // the stage is free once these MMAs have read it
+        }
+        if (ok) tc_commit(&tfull[buf]);
+      }
+    }
+  } else {
+    // epilogue: warps 2..5 cover the four TMEM lane quarters
+    const int quarter = warp & 3;
+    const int row = 32 * quarter + lane;
+    int ub = 0;
+    for (int q = q_begin; q < q_end; ++q, ++ub) {
+      const int buf = ub & 1;
+      if (!mbar_wait_bounded(&tfull[buf], uint32_t(ub >> 1) & 1u, kTcWaitNs)) {
+        if (lane == 0) atomicExch(err, 1u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ta = tmem + (uint32_t(32 * quarter) << 16) + uint32_t(buf * 2 * NB);
+      float* dst = part + (size_t(sched[q]) * kTcRows + row) * (2 * NB);
+#pragma unroll
+      for (int c0 = 0; c0 < 2 * NB; c0 += 16) {
+        float v[16];
+        tmem_ld16(ta + uint32_t(c0), v);
+        float4* d4 = reinterpret_cast<float4*>(dst + c0);
+        d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+        d4[2] = make_float4(v[8], v[9], v[10], v[11]);
+        d4[3] = make_float4(v[12], v[13], v[14], v[15]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM);
+  }
+}
+
+// y rows (one warp per global row, lane = right-hand side c < nc): the row's
+// unit pieces summed in order, unscaled, then the epilogue of Eq. 16 with
+// the exchange rows (FP32), as in the FMA stream's combine
+template <int NB>
+__global__ void __launch_bounds__(256) k_mv_tc_combine(
+    const float* __restrict__ part, const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_N,
+    const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const int* __restrict__ blk_unit_base,
+    const int* __restrict__ blk_pieces, const unsigned* __restrict__ amax, const unsigned* __restrict__ colmax,
+    const XEntry* __restrict__ xe, const float* __restrict__ xval32, const float* __restrict__ rho32,
+    const float* __restrict__ x, int64_t ldx, float* __restrict__ y, int64_t ldy, int c0, int nc, int64_t n_rows) {
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows || lane >= nc) return;
+  const int i = row_blk[row];
+  const int N = blk_N[i];
+  const int64_t m = row - blk_row_off[i];
+  const int P = blk_pieces[i];
+  const int64_t u0 = blk_unit_base[i] + (m >> 7) * P;
+  const int lr = int(m & 127);
+  float4 t = make_float4(0.f, 0.f, 0.f, 0.f), k = t;
+  for (int p = 0; p < P; ++p) {
+    const float* pr = part + (size_t(u0 + p) * kTcRows + lr) * (2 * NB);
+    const float4 a = *reinterpret_cast<const float4*>(pr + 4 * lane);
+    const float4 b = *reinterpret_cast<const float4*>(pr + NB + 4 * lane);
+    t.x += a.x;
+    t.y += a.y;
+    t.z += a.z;
+    t.w += a.w;
+    k.x += b.x;
+    k.y += b.y;
+    k.z += b.z;
+    k.w += b.w;
+  }
+  const float sc = tc_inv_scale(amax[i]) * tc_inv_scale(colmax[lane]);
+  // T u_D, T u_N, K u_D, K u_N
+  const float tDr = t.x * sc, tDi = t.y * sc, tNr = t.z * sc, tNi = t.w * sc;
+  const float kDr = k.x * sc, kDi = k.y * sc, kNr = k.z * sc, kNi = k.w * sc;
+  const float rr = rho32[4 * i], ri = rho32[4 * i + 1], ir = rho32[4 * i + 2], ii = rho32[4 * i + 3];
+  const int col = c0 + lane;
+  const float* xc = x + 2 * int64_t(col) * ldx;
+  float yDr = 2.f * (kDr + (tNr * ir - tNi * ii));
+  float yDi = 2.f * (kDi + (tNr * ii + tNi * ir));
+  float yNr = 2.f * (kNr - (tDr * rr - tDi * ri));
+  float yNi = 2.f * (kNi - (tDr * ri + tDi * rr));
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const XEntry X = xe[6 * row + e];
+    const float xv = xval32[6 * row + e];
+    const int Nj = X.ab >> 4;
+    yDr += xv * xc[2 * int64_t(X.col)];
+    yDi += xv * xc[2 * int64_t(X.col) + 1];
+    yNr += xv * xc[2 * (int64_t(X.col) + Nj)];
+    yNi += xv * xc[2 * (int64_t(X.col) + Nj) + 1];
+  }
+  float* yc = y + 2 * (int64_t(col) * ldy + blk_dof_off[i]);
+  yc[2 * m] = yDr;
+  yc[2 * m + 1] = yDi;
+  yc[2 * (N + m)] = yNr;
+  yc[2 * (N + m) + 1] = yNi;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q{};
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  MTF_REQUIRE(fn != nullptr, MTF_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  return fn;
+}
+
+// 4-D FP16 map {64, rows, parts, count} over contiguous boxes of
+// rows x parts x 128 bytes, loaded whole with the 128-byte swizzle
+static void encode_map(CUtensorMap* m, const void* base, int rows, int parts, int64_t count) {
+  MTF_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && count > 0 && count < (int64_t(1) << 31), MTF_ERR_ARG,
+              "tensor map base must be 16-byte aligned");
+  const cuuint64_t dims[4] = {64, cuuint64_t(rows), cuuint64_t(parts), cuuint64_t(count)};
+  const cuuint64_t strides[3] = {128, cuuint64_t(rows) * 128, cuuint64_t(rows) * parts * 128};
+  const cuuint32_t box[4] = {64, cuuint32_t(rows), cuuint32_t(parts), 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void*>(base), dims, strides,
+                                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  MTF_REQUIRE(r == CUDA_SUCCESS, MTF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+}
+
+template <class T>
+static void upload_vec(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+  d.alloc(std::max<size_t>(h.size(), 1));
+  if (!h.empty()) MTF_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+static void tc_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
+  if (t.planned) return;
+  mtf_mesh m = sys->mesh;
+  int dev = 0, sms = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  MTF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  t.n_cta = std::max(1, sms);
+  std::vector<int> Ns(m->nd);
+  for (int i = 0; i < m->nd; ++i) Ns[i] = m->blk[i].N;
+  const std::string why = plan_tc(Ns, t.n_cta, t.plan);
+  MTF_REQUIRE(why.empty(), MTF_ERR_MESH, why);
+  const TcPlan& p = t.plan;
+  std::vector<int4> units(p.units.size()), tinfo(size_t(p.n_tiles));
+  std::vector<int2> cinfo(size_t(p.n_chunks));
+  std::vector<int> ubase(m->nd), pieces(m->nd), nkc(m->nd);
+  std::vector<int64_t> tbase(m->nd), cbase(m->nd);
+  for (size_t u = 0; u < p.units.size(); ++u)
+    units[u] = make_int4(p.units[u].blk, p.units[u].mt, p.units[u].kc0, p.units[u].kc1);
+  for (int i = 0; i < m->nd; ++i) {
+    const TcBlock& b = p.blocks[size_t(i)];
+    ubase[i] = b.unit_base;
+    pieces[i] = b.pieces;
+    nkc[i] = b.n_kc;
+    tbase[i] = b.tile_base;
+    cbase[i] = b.chunk_base;
+    for (int mt = 0; mt < b.n_mt; ++mt)
+      for (int kc = 0; kc < b.n_kc; ++kc) tinfo[size_t(b.tile_base + int64_t(mt) * b.n_kc + kc)] = make_int4(i, mt, kc, 0);
+    for (int kc = 0; kc < b.n_kc; ++kc) cinfo[size_t(b.chunk_base + kc)] = make_int2(i, kc);
+  }
+  upload_vec(t.units, units, s);
+  upload_vec(t.tile_info, tinfo, s);
+  upload_vec(t.chunk_info, cinfo, s);
+  upload_vec(t.sched, p.sched, s);
+  upload_vec(t.sched_off, p.sched_off, s);
+  upload_vec(t.blk_unit_base, ubase, s);
+  upload_vec(t.blk_pieces, pieces, s);
+  upload_vec(t.blk_nkc, nkc, s);
+  upload_vec(t.blk_tile_base, tbase, s);
+  upload_vec(t.blk_chunk_base, cbase, s);
+  t.amax.alloc(size_t(m->nd));
+  t.colmax.alloc(32);
+  MTF_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+  t.planned = true;
+}
+
+bool tc_matvec_enabled(mtf_system sys) {
+  return sys->opt.precision == MTF_PREC_MIXED && sys->opt.mv_tensor && sys->tc && sys->tc->built;
+}
+
+// FP16 hi / lo tiled copy of the FP32-stored {T, K}, rebuilt after every
+// mixed-precision assembly
+void tc_build_operator(mtf_system sys, cudaStream_t s) {
+  if (!sys->opt.mv_tensor) return;
+  if (!sys->tc) sys->tc = new TcMatvec();
+  TcMatvec& t = *sys->tc;
+  mtf_mesh m = sys->mesh;
+  tc_plan_tables(sys, t, s);
+  const size_t nh = size_t(t.plan.n_tiles) * size_t(kTcTileHalves);
+  if (t.A.n != nh) {
+    t.A.alloc(nh);
+    t.amap_ptr = nullptr;
+  }
+  MTF_CUDA(cudaMemsetAsync(t.amax.p, 0, size_t(m->nd) * sizeof(unsigned), s));
+  MTF_LAUNCH(KID_TC_TILE, s, k_tc_blkmax<<<dim3(256, unsigned(m->nd)), 256, 0, s>>>(
+      reinterpret_cast<const float4*>(sys->d_TK32.p), m->d_blk_mat_off.p, m->d_blk_N.p, t.amax.p));
+  const int64_t nthr = t.plan.n_tiles * kTcRows * 8;
+  MTF_LAUNCH(KID_TC_TILE, s, k_tc_tile_a<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const float4*>(sys->d_TK32.p), t.tile_info.p, m->d_blk_mat_off.p, m->d_blk_N.p, t.amax.p,
+      t.plan.n_tiles, t.A.p));
+  if (t.amap_ptr != t.A.p) {
+    encode_map(&t.amap, t.A.p, kTcRows, kTcParts, t.plan.n_tiles);
+    t.amap_ptr = t.A.p;
+  }
+  t.built = true;
+}
+
+template <int NB>
+static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx, float* y, int64_t ldy, int c0, int nc,
+                       cudaStream_t s) {
+  using Cfg = TcCfg<NB>;
+  mtf_mesh m = sys->mesh;
+  const TcPlan& p = t.plan;
+  const size_t bh = size_t(p.n_chunks) * 2 * NB * 64;
+  if (t.B.n < bh) {
+    t.B.alloc(size_t(p.n_chunks) * 2 * 128 * 64);  // room for the widest pass
+    t.bmap_ptr = nullptr;
+  }
+  if (t.bmap_ptr != t.B.p || t.bmap_nb != NB) {
+    encode_map(&t.bmap, t.B.p, NB, 2, p.n_chunks);
+    t.bmap_ptr = t.B.p;
+    t.bmap_nb = NB;
+  }
+  const size_t np = p.units.size() * kTcRows * 2 * NB;
+  if (t.part.n < np) t.part.alloc(size_t(p.units.size()) * kTcRows * 2 * 128);
+  MTF_CUDA(cudaMemsetAsync(t.colmax.p, 0, 32 * sizeof(unsigned), s));
+  MTF_LAUNCH(KID_MVTC_PREP, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(x, ldx, m->n_total, c0, t.colmax.p));
+  const int64_t nthr = p.n_chunks * NB * 8;
+  MTF_LAUNCH(KID_MVTC_PREP, s, k_tc_build_b<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+      x, ldx, c0, nc, NB, t.chunk_info.p, p.n_chunks, m->d_blk_N.p, m->d_blk_dof_off.p, t.colmax.p, t.B.p));
+  static std::atomic<uint64_t> opted{0};
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(opted.load() & bit)) {
+    MTF_CUDA(cudaFuncSetAttribute(k_mv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem)));
+    opted.fetch_or(bit);
+  }
+  stream_prepare(sys, s);
+  MTF_LAUNCH(KID_MVTC, s, k_mv_tc<NB><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
+      t.amap, t.bmap, t.units.p, t.sched.p, t.sched_off.p, t.blk_tile_base.p, t.blk_nkc.p, t.blk_chunk_base.p,
+      t.part.p, sys->d_mv_ctl.p + 2));
+  MTF_LAUNCH(KID_MVTC_COMBINE, s, k_mv_tc_combine<NB><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+      t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
+      t.blk_pieces.p, t.amax.p, t.colmax.p, m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, x, ldx, y, ldy, c0, nc,
+      m->n_rows));
+}
+
+// y = M x (FP32 in and out) on the tensor cores, in passes of up to 32
+// right-hand sides; x and y need 16-byte aligned columns
+void launch_matvec_tc(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs, cudaStream_t s) {
+  MTF_REQUIRE(tc_matvec_enabled(sys), MTF_ERR_ARG, "tensor-core matvec not built for this system");
+  TcMatvec& t = *sys->tc;
+  MTF_REQUIRE((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 1) == 0, MTF_ERR_ARG,
+              "tensor-core matvec input columns must be 16-byte aligned");
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int nc = std::min(32, nrhs - c0);
+    const int nb = tc_nb(nc);
+    if (nb == 16) mv_tc_pass<16>(sys, t, x, ldx, y, ldy, c0, nc, s);
+    else if (nb == 32) mv_tc_pass<32>(sys, t, x, ldx, y, ldy, c0, nc, s);
+    else if (nb == 64) mv_tc_pass<64>(sys, t, x, ldx, y, ldy, c0, nc, s);
+    else mv_tc_pass<128>(sys, t, x, ldx, y, ldy, c0, nc, s);
+  }
+}
+
+}  // namespace mtf

@@ -8,8 +8,8 @@
 // columns of the same length,
 //   form 0: (v_re, -v_im) per entry -> Re(T v),   form 1: (v_im, v_re) -> Im(T v).
 // Column 4 c + 2 t + f of the B operand holds form f of u_t (t = 0: D slot,
-// t = 1: N slot) of right-hand side c; NB = 4 nc rounded up to a multiple of
-// 16 columns.  Both operands are FP16 after a power-of-two scaling (per block
+// t = 1: N slot) of right-hand side c; NB = 4 nc rounded up to 16, 32, 64 or
+// 128 columns (up to 32 right-hand sides per pass).  Both operands are FP16 after a power-of-two scaling (per block
 // for T and K, per right-hand side for the inputs) and are split into an FP16
 // value and the FP16 rounding of its remainder (hi + lo, about 22 significant
 // bits); a product is hi*hi + hi*lo + lo*hi with FP32 accumulation.
@@ -39,15 +39,17 @@ constexpr int kTcParts = 4;   // T hi, T lo, K hi, K lo
 constexpr int64_t kTcPartHalves = int64_t(kTcRows) * 64;
 constexpr int64_t kTcTileHalves = kTcParts * kTcPartHalves;
 
-// columns of the B operand for nc right-hand sides
-inline int tc_nb(int nc) { return std::max(16, (4 * nc + 15) / 16 * 16); }
+// columns of the B operand for nc (<= 32) right-hand sides: 4 nc rounded up
+// to one of the kernel's widths 16, 32, 64, 128
+inline int tc_nb(int nc) { return nc <= 4 ? 16 : nc <= 8 ? 32 : nc <= 16 ? 64 : 128; }
 
 // half index of (tile, part, row, e) in the tiled operator, e in 0..63
-inline int64_t tc_a_index(int64_t tile, int part, int row, int e) {
+// (constexpr: usable in device code)
+constexpr int64_t tc_a_index(int64_t tile, int part, int row, int e) {
   return ((tile * kTcParts + part) * kTcRows + row) * 64 + e;
 }
 // half index of (chunk, part 0 hi / 1 lo, column, e) in the input chunks
-inline int64_t tc_b_index(int64_t chunk, int part, int col, int e, int nb) {
+constexpr int64_t tc_b_index(int64_t chunk, int part, int col, int e, int nb) {
   return ((chunk * 2 + part) * nb + col) * 64 + e;
 }
 
@@ -117,7 +119,7 @@ inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int
   using Item = std::pair<int64_t, int>;
   std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
   for (int b = 0; b < n_cta; ++b) pq.push({0, b});
-  std::vector<std::vector<int>> per(size_t(n_cta));
+  std::vector<std::vector<int>> per(static_cast<size_t>(n_cta));
   for (int u : order) {
     Item it = pq.top();
     pq.pop();

@@ -1,0 +1,150 @@
+// Host checks of the tensor-core matvec plan and formulation (tc_plan.h):
+//  1. plan_tc: every (block, row tile, chunk) lies in exactly one unit, the
+//     units of (block, row tile) are consecutive from unit_base, the schedule
+//     is a permutation of the units and its busiest CTA carries at most the
+//     average plus one longest unit;
+//  2. the formulation: T and K of a ragged block (N = 45, not a multiple of
+//     the tile sizes) packed into the tiled FP16 hi / lo layout after
+//     power-of-two scaling, the inputs packed into chunks in the two real
+//     column forms, the products emulated as the tensor cores form them
+//     (FP16 operands, hi*hi + hi*lo + lo*hi per chunk) and unscaled give
+//     T u and K u to about 2^-22 of the exact complex products.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <random>
+#include "tc_plan.h"
+using cd = std::complex<double>;
+
+static int check_plan(const std::vector<int>& Ns, int ncta) {
+  mtf::TcPlan p;
+  const std::string why = mtf::plan_tc(Ns, ncta, p);
+  if (!why.empty()) return std::printf("plan: %s\n", why.c_str()), 1;
+  // coverage
+  std::vector<int> seen(size_t(p.n_tiles), 0);
+  int64_t longest = 0;
+  for (size_t u = 0; u < p.units.size(); ++u) {
+    const auto& U = p.units[u];
+    const auto& b = p.blocks[size_t(U.blk)];
+    longest = std::max<int64_t>(longest, U.kc1 - U.kc0);
+    const int q = int(u) - b.unit_base - U.mt * b.pieces;
+    if (q < 0 || q >= b.pieces || U.kc0 != q * b.piece_len) return std::printf("plan: unit order\n"), 1;
+    for (int kc = U.kc0; kc < U.kc1; ++kc) ++seen[size_t(b.tile_base + int64_t(U.mt) * b.n_kc + kc)];
+  }
+  for (int v : seen)
+    if (v != 1) return std::printf("plan: coverage\n"), 1;
+  std::vector<int> cnt(p.units.size(), 0);
+  for (int u : p.sched) ++cnt[size_t(u)];
+  for (int v : cnt)
+    if (v != 1) return std::printf("plan: schedule\n"), 1;
+  const double avg = double(p.total_load) / ncta;
+  std::printf("plan: %zu blocks, %zu units, max load %lld chunks (avg %.1f, longest unit %lld)\n", Ns.size(),
+              p.units.size(), (long long)p.max_load, avg, (long long)longest);
+  return p.max_load <= avg + longest ? 0 : 1;
+}
+
+static float f16(float v) { return float(_Float16(v)); }
+
+static int check_formulation() {
+  const int N = 45, nc = 3;
+  std::mt19937 rng(5);
+  std::normal_distribution<double> G(0, 1);
+  std::vector<std::complex<float>> T(size_t(N) * N), K(size_t(N) * N), u(size_t(2 * N) * nc);
+  for (auto& v : T) v = {float(G(rng) * 3e-3), float(G(rng) * 3e-3)};
+  for (auto& v : K) v = {float(G(rng) * 1e-2), float(G(rng) * 1e-2)};
+  for (auto& v : u) v = {float(G(rng)), float(G(rng))};
+  mtf::TcPlan p;
+  mtf::plan_tc({N}, 4, p);
+  const auto& b = p.blocks[0];
+  const int nb = mtf::tc_nb(nc);
+  // scales (largest |re|, |im| mapped below 2^14)
+  auto scale = [](double amax) { int ex; std::frexp(amax, &ex); return std::ldexp(1.0, 14 - ex); };
+  double am = 0;
+  for (int t = 0; t < N * N; ++t)
+    am = std::max({am, double(std::fabs(T[t].real())), double(std::fabs(T[t].imag())), double(std::fabs(K[t].real())),
+                   double(std::fabs(K[t].imag()))});
+  const float sA = float(scale(am));
+  std::vector<float> sB(nc);
+  for (int c = 0; c < nc; ++c) {
+    double m = 0;
+    for (int k = 0; k < 2 * N; ++k) m = std::max({m, double(std::fabs(u[size_t(c) * 2 * N + k].real())),
+                                                  double(std::fabs(u[size_t(c) * 2 * N + k].imag()))});
+    sB[c] = float(scale(m));
+  }
+  std::vector<float> A(size_t(p.n_tiles * mtf::kTcTileHalves), 0.f), B(size_t(p.n_chunks) * 2 * nb * 64, 0.f);
+  for (int mt = 0; mt < b.n_mt; ++mt)
+    for (int kc = 0; kc < b.n_kc; ++kc)
+      for (int row = 0; row < mtf::kTcRows; ++row)
+        for (int q = 0; q < mtf::kTcCols; ++q) {
+          const int r = mt * mtf::kTcRows + row, n = kc * mtf::kTcCols + q;
+          if (r >= N || n >= N) continue;
+          const int64_t tile = b.tile_base + int64_t(mt) * b.n_kc + kc;
+          const float vals[4] = {T[size_t(r) * N + n].real() * sA, T[size_t(r) * N + n].imag() * sA,
+                                 K[size_t(r) * N + n].real() * sA, K[size_t(r) * N + n].imag() * sA};
+          for (int op = 0; op < 2; ++op)
+            for (int ri = 0; ri < 2; ++ri) {
+              const float v = vals[2 * op + ri], hi = f16(v), lo = f16(v - hi);
+              A[size_t(mtf::tc_a_index(tile, 2 * op, row, 2 * q + ri))] = hi;
+              A[size_t(mtf::tc_a_index(tile, 2 * op + 1, row, 2 * q + ri))] = lo;
+            }
+        }
+  for (int kc = 0; kc < b.n_kc; ++kc)
+    for (int col = 0; col < 4 * nc; ++col)
+      for (int q = 0; q < mtf::kTcCols; ++q) {
+        const int n = kc * mtf::kTcCols + q;
+        if (n >= N) continue;
+        const int c = col >> 2, slot = (col >> 1) & 1, form = col & 1;
+        const std::complex<float> v = u[size_t(c) * 2 * N + size_t(slot) * N + n];
+        const float pair[2] = {form == 0 ? v.real() : v.imag(), form == 0 ? -v.imag() : v.real()};
+        for (int t = 0; t < 2; ++t) {
+          const float x = pair[t] * sB[c], hi = f16(x), lo = f16(x - hi);
+          B[size_t(mtf::tc_b_index(b.chunk_base + kc, 0, col, 2 * q + t, nb))] = hi;
+          B[size_t(mtf::tc_b_index(b.chunk_base + kc, 1, col, 2 * q + t, nb))] = lo;
+        }
+      }
+  // emulated products: D_op[row][col] += sum_e Ahi Bhi + Ahi Blo + Alo Bhi (FP32 sums)
+  double err = 0, ref = 0;
+  for (int mt = 0; mt < b.n_mt; ++mt)
+    for (int row = 0; row < mtf::kTcRows; ++row) {
+      const int r = mt * mtf::kTcRows + row;
+      if (r >= N) continue;
+      for (int op = 0; op < 2; ++op)
+        for (int col = 0; col < 4 * nc; ++col) {
+          float acc = 0.f;
+          for (int kc = 0; kc < b.n_kc; ++kc) {
+            const int64_t tile = b.tile_base + int64_t(mt) * b.n_kc + kc, ch = b.chunk_base + kc;
+            for (int e = 0; e < 64; ++e) {
+              const float ah = A[size_t(mtf::tc_a_index(tile, 2 * op, row, e))];
+              const float al = A[size_t(mtf::tc_a_index(tile, 2 * op + 1, row, e))];
+              const float bh = B[size_t(mtf::tc_b_index(ch, 0, col, e, nb))];
+              const float bl = B[size_t(mtf::tc_b_index(ch, 1, col, e, nb))];
+              acc += ah * bh + ah * bl + al * bh;
+            }
+          }
+          const int c = col >> 2, slot = (col >> 1) & 1, form = col & 1;
+          cd exact = 0;
+          for (int n = 0; n < N; ++n) {
+            const auto& M = op == 0 ? T : K;
+            exact += cd(M[size_t(r) * N + n]) * cd(u[size_t(c) * 2 * N + size_t(slot) * N + n]);
+          }
+          const double want = form == 0 ? exact.real() : exact.imag();
+          const double got = double(acc) / (double(sA) * sB[c]);
+          err += (got - want) * (got - want);
+          ref += want * want;
+        }
+    }
+  const double rel = std::sqrt(err / ref);
+  std::printf("formulation: ||emulated - exact|| / ||exact|| = %.2e\n", rel);
+  return rel < 1e-6 ? 0 : 1;
+}
+
+int main() {
+  int f = 0;
+  std::vector<int> cube4(65, 450);
+  cube4[0] = 7200;
+  f += check_plan(cube4, 152);
+  f += check_plan({2178, 2178, 2178}, 152);
+  f += check_plan({567, 45, 3}, 152);
+  f += check_formulation();
+  return f;
+}

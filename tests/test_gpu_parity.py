@@ -278,11 +278,14 @@ def test_mixed_restarted_six_rhs(api, oracle_cache, precond, restart, block):
 
 
 # ---------------------------------------------------------------------------
-# FP32 entry points of the mixed inner solver: the streaming matvec (rows cut
-# into pieces of <= 512 columns, handed out dynamically) and the FP32 OSRC
-# apply.  Bound: 1e-5 norm-wise against the FP64 oracle for the matvec (FP32
-# storage and sums), 1e-4 for the OSRC apply as for its FP64-vector entry.
-# nrhs 1, 3 and 6 cover every column-chunk width (1..4) of the kernels.
+# FP32 entry points of the mixed inner solver: the matvec on the tensor cores
+# (FP16 hi + lo split, up to 32 right-hand sides per pass) and the FMA stream
+# (rows cut into pieces of <= 512 columns, 4 right-hand sides per pass), and
+# the FP32 OSRC apply.  Bound: 1e-5 norm-wise and entry by entry (relative to
+# the largest entry) against the FP64 oracle for the matvec, 1e-4 for the
+# OSRC apply as for its FP64-vector entry.  nrhs 1, 3, 6, 16 and 40 cover
+# every column-chunk width of the FMA stream (1..4) and every input width of
+# the tensor-core kernel (16, 32, 64, 128 columns, two passes for 40).
 # ---------------------------------------------------------------------------
 def _rand_c64(rng, shape):
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
@@ -307,16 +310,19 @@ def test_recycled_second_cycle_matches_oracle_with_fewer_iterations(api, oracle_
     assert its[1] < 0.8 * its[0], its
 
 
+@pytest.mark.parametrize("tensor", [1, 0])
 @pytest.mark.parametrize("name", ["sphere", "split", "cubes", "uvodd"])
-@pytest.mark.parametrize("nrhs", [1, 3, 6])
-def test_matvec_f32_matches_oracle(api, oracle_cache, name, nrhs):
+@pytest.mark.parametrize("nrhs", [1, 3, 6, 16, 40])
+def test_matvec_f32_matches_oracle(api, oracle_cache, name, nrhs, tensor):
     cfg, sk, ref = _case(oracle_cache, name)
     mesh = api.Mesh.from_inputs(cfg["mesh"])
-    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, mv_tensor=tensor)
     x = _rand_c64(np.random.default_rng(nrhs), (nrhs, sk.n_total))
     y = sysg.matvec_f32(torch.from_numpy(x).cuda()).cpu().numpy()
     yr = np.stack([ref.matvec(xx.astype(np.complex128)) for xx in x])
     assert rel(y, yr) < 1e-5, rel(y, yr)
+    # entry by entry: no entry is off by more than 1e-5 of the largest
+    assert np.abs(y - yr).max() < 1e-5 * np.abs(yr).max(), np.abs(y - yr).max() / np.abs(yr).max()
     # repeated launches give identical results (schedule-independent sums)
     y2 = sysg.matvec_f32(torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.array_equal(y, y2)
