@@ -2,20 +2,24 @@
 """Benchmark of the GB300 MTF path (assembly + preconditioned GMRES solve).
 
 Workload (one step = one pass of the whole hot path over one batch): the
-split-sphere scatterer -- unit sphere cut by the equatorial disk into two
-hemispheres (eps_r 2 and 4, a triple-junction equator), k0 = 2, 2178
-skeleton triangles (6 * 11^2 per surface), two polarisations of a plane wave
-along +z.  A step re-assembles the MTF operator (regular + Sauter-Schwab
-pairs, transmission Grams), builds the right-hand sides, solves with
-restarted FGMRES to a relative residual that makes the solution error
-<= 1e-5, and evaluates the far field on the z = 0 plane (RCS_z).
+unit cube partitioned 4 x 4 x 4 into 64 subcubes (65 blocks, eps_r ~
+U[1.5, 6], k0 = 4, 12,000 skeleton triangles, 72,000 unknowns), 16 plane
+waves (8 Fibonacci directions x 2 polarisations).  A step re-assembles the
+MTF operator (regular + Sauter-Schwab pairs, transmission Grams, block-OSRC
+T~ and the tensor-core operator copy), builds the right-hand sides, solves
+with block flexible GMRES (all 16 waves in one Krylov space, tensor-core
+matvec) inside FP64 iterative refinement to a relative residual that makes
+the solution error <= 1e-5, and evaluates the far field on the z = 0 plane.
 
 Metric: solved right-hand sides per second (plus assembly triangle pairs
 per second).  ``value`` is device-timed (CUDA events on the launching
 stream, inputs resident in HBM); ``e2e`` times the same work through the
-C-ABI from host buffers (mesh creation, upload, assembly, solve, far field,
-results copied back).  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload.
+C-ABI from host buffers.  The accuracy reference is the solution of the
+FP64-assembled system (FP64 residuals of that operator, refined with mixed
+solves to 1e-11).  A secondary line runs the split-sphere workload with the
+plain FP64 block-OSRC GMRES and the learned correction beside it.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload.
 """
 from __future__ import annotations
 
@@ -192,7 +196,9 @@ def oracle_sample(cfg, iters, budget_s=12.0):
     """Time the FP64 oracle on a bounded sample of the workload and
     extrapolate to one full step: assembly of a sample of block 0's triangle
     pairs (regular and singular timed separately), dense matvecs of the full
-    block sizes, times the GMRES iteration count of the GPU solve."""
+    block sizes for all right-hand sides at once, times the operator applies
+    per right-hand side of the GPU solve (a lower bound for the oracle's own
+    GMRES, which is not faster per apply)."""
     from oracle.skeleton import Skeleton
     from oracle.operators import classify_pairs, assemble_block
     from oracle.mtf import MTFSystem
@@ -235,19 +241,28 @@ def oracle_sample(cfg, iters, budget_s=12.0):
     t_step = t_asm + (iters + 2) * t_mv
     return {
         "t_step": t_step, "t_assembly": t_asm, "t_matvec": t_mv,
-        "sample": (f"oracle assembly of {n_reg} regular + {n_sing} singular pairs of block 0 "
-                   f"(test triangles 0..{ntau - 1}), extrapolated to {counts[0]} + {counts[1]} pairs; "
-                   f"{nmv} full-size FP64 block matvecs x {iters + 2} GMRES iterations"),
+        "sample": (f"measured: oracle assembly of {n_reg} regular + {n_sing} singular pairs of block 0 "
+                   f"(test triangles 0..{ntau - 1}) and {nmv} FP64 matvecs with full-size dense blocks for all "
+                   f"{x.shape[1]} right-hand sides; extrapolated: assembly to {counts[0]} + {counts[1]} pairs, "
+                   f"solve to {iters + 2} operator applies"),
         "pairs_per_s": (n_reg + n_sing) / (t_reg + t_sing),
     }
 
 
 # ----------------------------------------------------------------------------
+# Operator applies per right-hand side of the GPU solve (block steps of the
+# block FGMRES, or iterations of the single-vector solve for one wave), as
+# the default bench run measured them on a GB300; the reference arm runs
+# without the GPU and extrapolates the oracle's step with these counts
+# (--ref-iters overrides).
+MEASURED_APPLIES = {"cube4": 838, "split_sphere": 436, "sphere": 28, "cube2": 700}
+
+
 def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    iters = args.ref_iters
+    iters = args.ref_iters if args.ref_iters > 0 else MEASURED_APPLIES.get(args.workload, 1000)
     vals = []
     res = None
     for _ in range(args.steps):
@@ -259,6 +274,10 @@ def run_reference(args, cfg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["t_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": cfg["desc"], "nrhs": len(cfg["dirs"])},
+            "measured": {"assembly_pairs_per_s": res["pairs_per_s"], "matvec_s": res["t_matvec"],
+                         "assembly_s_extrapolated": res["t_assembly"]},
+            "extrapolated": f"step = sampled assembly rate x all pairs + {iters + 2} operator applies "
+                            f"(the GPU solve's applies per right-hand side) x the measured apply time",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -329,27 +348,176 @@ def run_cuboid_study(args):
         print(json.dumps(out), flush=True)
 
 
+def fp64_reference(api, L, mesh, cfg, restart, osrc_np, tol=1e-11, max_steps=8):
+    """Solution of the FP64-assembled system for the workload's plane waves:
+    x += (mixed solve of r), r = b - M64 x with the FP64 matvec of the FP64
+    assembly (pinned to the oracle by sampled full rows at this size), until
+    ||r|| / ||b|| <= tol for every right-hand side.  Returns x and a record."""
+    import torch
+    s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    b = s64.rhs(cfg["dirs"], cfg["pols"])
+    smx = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=L.MTF_PREC_MIXED,
+                     precond=L.MTF_PRECOND_OSRC, tol=1e-8, restart=restart, max_iter=8 * restart, max_refine=8,
+                     osrc_np=osrc_np)
+    x = torch.zeros_like(b)
+    bn = b.norm(dim=1)
+    rel = 1.0
+    steps = 0
+    t0 = time.perf_counter()
+    for steps in range(max_steps + 1):
+        r = b - s64.matvec(x)
+        rel = float((r.norm(dim=1) / bn).max())
+        if rel <= tol or steps == max_steps:
+            break
+        d, _ = smx.solve_rhs(r, raise_on_noconv=False)
+        x += d
+    torch.cuda.synchronize()
+    del s64, smx
+    return x, {"fp64_rel_residual": rel, "refinement_steps": steps, "seconds": round(time.perf_counter() - t0, 2),
+               "method": "FP64 residuals b - M x of the FP64-assembled operator, corrections by mixed solves"}
+
+
+def run_steps(step, n, stream):
+    """Time n calls of step() with CUDA events on the stream; returns
+    (ms per step, last result)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(n):
+        out = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n, out
+
+
+def roofline_of(prof, counts, n_ss, hbm, src):
+    """Roofline of the kernel with the largest device time: algorithmic bytes
+    declared by the library's launch sites over the measured time (HBM), or
+    ALU flops for the assembly kernels."""
+    name, (nl, tms, byts) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_s = tms / max(1, nl) / 1e3
+    if name in ("regular64", "regular32"):
+        peak = FP64_PEAK_TFLOPS if name == "regular64" else FP32_PEAK_TFLOPS
+        ach = counts[3] * 36 * FLOPS_PER_EVAL / per_launch_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "derived from unit counts and max SM clock"}
+    elif name == "singular64":
+        npts, per = {0: 6, 1: 5, 2: 2}, {0: 1, 1: 2, 2: 2}
+        evals = sum(int(counts[c]) // per[c] * npts[c] * n_ss ** 4 for c in range(3))
+        ach = evals * 75 / per_launch_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": "derived (FP64 1.25 TF/s)"}
+    else:
+        ach = byts / (tms / 1e3) / 1e9 if byts > 0 and tms > 0 else None
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm if ach else None, "traffic": None,
+                "algorithmic_bytes_per_launch": byts / max(1, nl), "peak_source": src}
+    roof["launches"] = nl
+    roof["avg_launch_ms"] = per_launch_s * 1e3
+    return roof
+
+
+def kernel_table(prof):
+    out = {}
+    for k, (nl, ms, byts) in prof.items():
+        if not nl:
+            continue
+        e = {"launches": nl, "ms": round(ms, 3)}
+        if byts > 0 and ms > 0:
+            e["GB_per_s"] = round(byts / (ms / 1e3) / 1e9, 1)
+        out[k] = e
+    return out
+
+
+def secondary_split_sphere(api, L, args, stream):
+    """The split-sphere workload (3 blocks, 13,068 unknowns, 2 waves): the
+    mixed path, the plain FP64 block-OSRC GMRES and the learned correction on
+    the same GPU at equal accuracy (FP64 solve at tol 1e-11 as reference)."""
+    cfg = workload("split_sphere")
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    kw = dict(tol=args.tol, restart=500, max_iter=2000, precond=L.MTF_PRECOND_OSRC, osrc_np=args.osrc_np)
+    ref = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=500, max_iter=4000,
+                     precond=L.MTF_PRECOND_OSRC, osrc_np=args.osrc_np)
+    x_ref, _ = ref.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+    del ref
+    nrhs = len(cfg["dirs"])
+
+    def err(x):
+        return float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max())
+
+    out = {"workload": cfg["desc"], "nrhs": nrhs, "n_unknowns": int(mesh.n_total)}
+    sm = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=L.MTF_PREC_MIXED, **kw)
+
+    def step():
+        sm.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+        x, st = sm.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        sm.farfield(x, cfg["obs"])
+        return x, st
+
+    for _ in range(3):
+        step()
+    ms, (x, st) = run_steps(step, 5, stream)
+    out["mixed"] = {"value": nrhs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "gmres_iterations": int(st.iterations),
+                    "solution_rel_err_vs_fp64": err(x), "converged": bool(st.converged)}
+    del sm
+    s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **kw)
+
+    def step64():
+        s64.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+        x6, st6 = s64.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        s64.farfield(x6, cfg["obs"])
+        return x6, st6
+
+    step64()
+    ms64, (x6, st6) = run_steps(step64, 2, stream)
+    out["fp64_block_osrc"] = {"value": nrhs / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                              "gmres_iterations": int(st6.iterations), "converged": bool(st6.converged),
+                              "solution_rel_err_vs_fp64": err(x6),
+                              "path": "FP64 storage, matvec, Arnoldi; block-OSRC (same tolerance, restart, Pade order)"}
+    del s64
+    sl = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=L.MTF_PREC_MIXED, **kw)
+    sl.learned_init("table")
+    d_val = mi.fibonacci_directions(9)[0:2]
+    p_val = mi.orthonormal_polarizations(d_val)[0].astype(np.complex128)
+    t0 = time.perf_counter()
+    rep = sl.learned_fit(d_val, p_val, rounds=4, steps_per_round=150, lr=3e-3, batch=16, K=6, seed=5)
+    t_fit = time.perf_counter() - t0
+    xl, stl = sl.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+    out["learned_correction"] = {"fit": rep, "fit_seconds": t_fit, "enabled": bool(rep["enabled"]),
+                                 "gmres_iterations": int(stl.iterations), "solution_rel_err_vs_fp64": err(xl),
+                                 "note": "table-parametrised stencil, power loss K = 6, validation on 2 other waves; "
+                                         "per-rhs Krylov spaces (systems with a correction keep them)"}
+    del sl
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="split_sphere")
+    ap.add_argument("--workload", default="cube4")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="osrc", choices=["none", "osrc"])
     ap.add_argument("--tol", type=float, default=1e-7)
-    ap.add_argument("--restart", type=int, default=500)
+    # block steps of the block FGMRES (each applies the operator to all
+    # right-hand sides), or iterations of the single-vector solver
+    ap.add_argument("--restart", type=int, default=600)
     # the Pade order of the OSRC square root is free (N_p >= 1); it only
     # changes the per-mode symbol formed at assembly, not the apply
     ap.add_argument("--osrc-np", type=int, default=16)
-    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--ref-iters", type=int, default=0,
+                    help="operator applies per right-hand side for the reference arm's extrapolation "
+                         "(0: the count the GPU arm measured for the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparisons", action="store_true",
-                    help="skip the FP64-path and learned-correction lines (rank 0, N=1 only)")
-    ap.add_argument("--max-iter", type=int, default=2000)
+                    help="skip the secondary split-sphere line (FP64 path and learned correction)")
+    ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--no-accuracy-gate", action="store_true",
-                    help="skip the tight-tolerance FP64 reference solve (profiling runs)")
+                    help="skip the FP64 reference solution (profiling runs)")
     ap.add_argument("--study", default="", choices=["", "cuboids"],
                     help="instead of the benchmark: the concentric-cuboid study (one JSON line per M)")
     ap.add_argument("--study-m", type=int, default=6)
@@ -390,17 +558,14 @@ def main():
     mesh = api.Mesh.from_inputs(m)
     counts = mesh.pair_counts()
     n_pairs = int(counts.sum())
-    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                      precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
-    # accuracy gate: FP64 solution at tight tolerance (the FP64 path is pinned
-    # to the oracle at 1e-10 by the parity tests)
-    x_ref, st_ref = None, None
-    if not args.no_accuracy_gate:
-        ref_sys = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=1e-11, restart=args.restart,
-                             max_iter=4000, precond=L.MTF_PRECOND_OSRC)
-        x_ref, st_ref = ref_sys.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
-        del ref_sys
+    nrhs = len(cfg["dirs"])
+    opts = dict(tol=args.tol, restart=args.restart, precision=prec, max_iter=args.max_iter, precond=pc,
+                osrc_np=args.osrc_np)
+    sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **opts)
     stream = torch.cuda.current_stream()
+    x_ref, ref_info = None, None
+    if not args.no_accuracy_gate:
+        x_ref, ref_info = fp64_reference(api, L, mesh, cfg, args.restart, args.osrc_np)
 
     def step():
         sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
@@ -411,7 +576,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         x, st, f = step()
     torch.cuda.synchronize()
-    L.mtf_profile_read()                      # reset counters (launch counts are always kept)
+    L.mtf_profile_read_bytes()                # reset counters (launch counts are always kept)
     iters = []
     with ClockSampler(local) as clk:
         barrier()
@@ -424,70 +589,30 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    launches_timed = L.mtf_profile_read()
+    launches_timed = L.mtf_profile_read_bytes()
     ms = ev0.elapsed_time(ev1) / args.steps
     # per-kernel device times: a second pass of the same steps with CUDA
-    # events around every library launch (on the launching stream).  It is
-    # kept out of the timed region above because the event pairs themselves
-    # slow the solve down; per-kernel durations from this pass are upper
-    # bounds.
+    # events around every library launch (on the launching stream), kept out
+    # of the timed region because the event pairs slow the solve down; the
+    # per-kernel durations of this pass are upper bounds
     L.mtf_profile_enable(True)
     torch.cuda.synchronize()
     for _ in range(args.steps):
         step()
     torch.cuda.synchronize()
     L.mtf_profile_enable(False)
-    prof = L.mtf_profile_read()
-    nrhs = len(cfg["dirs"])
+    prof = L.mtf_profile_read_bytes()
     ms = 1e3 * max_over_ranks(ms / 1e3, world)
     value = world * nrhs / (ms / 1e3)
     err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
     # assembly alone (device-timed)
-    torch.cuda.synchronize()
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ea.record(stream)
-    for _ in range(3):
-        sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
-    eb.record(stream)
-    torch.cuda.synchronize()
-    t_asm = ea.elapsed_time(eb) / 3 / 1e3
-    L.mtf_profile_read()
-
-    # ---- roofline of the dominant kernel -----------------------------------
+    t_asm_ms, _ = run_steps(lambda: sysg.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"]), 3, stream)
+    t_asm = t_asm_ms / 1e3
+    L.mtf_profile_read_bytes()
     hbm, bf16, src = _peaks()
     launches = sum(v[0] for v in launches_timed.values())
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, tms) = top
-    per_launch_s = tms / max(1, nl) / 1e3
-    n_mat = int(sum(int(n) * int(n) for n in mesh.n_dofs))
-    roof = None
-    if name in ("regular64", "regular32"):
-        flops = counts[3] * 36 * FLOPS_PER_EVAL
-        peak = FP64_PEAK_TFLOPS if name == "regular64" else FP32_PEAK_TFLOPS
-        ach = flops / per_launch_s / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "derived from unit counts and max SM clock (FP64 1.25 TF/s, FP32 80.5 TF/s)"}
-    elif name in ("matvec64", "matvec32", "osrc_apply"):
-        byts = _stream_bytes(name, [int(n) for n in mesh.n_dofs], int(mesh.n_total), nrhs)
-        ach = byts / per_launch_s / 1e9
-        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": NCU_TRAFFIC.get((name, int(mesh.n_total), nrhs)),
-                "algorithmic_bytes": byts, "peak_source": src}
-    elif name == "singular64":
-        npts = {0: 6, 1: 5, 2: 2}
-        # adjacent pairs are integrated once per unordered pair (counts are ordered)
-        per = {0: 1, 1: 2, 2: 2}
-        evals = sum(int(counts[c]) // per[c] * npts[c] * sysg.opt.n_ss ** 4 for c in range(3))
-        ach = evals * 75 / per_launch_s / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived (FP64 1.25 TF/s at max SM clock)"}
-    else:
-        roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_source": src}
-    roof["launches"] = nl
-    roof["avg_launch_ms"] = per_launch_s * 1e3
+    roof = roofline_of(prof, counts, sysg.opt.n_ss, hbm, src)
+    roof["traffic"] = NCU_TRAFFIC.get((roof["kernel"], int(mesh.n_total), nrhs))
 
     # ---- end to end through the C-ABI from host buffers ---------------------
     # The step of the timed region (materials re-assembled, plane waves
@@ -498,10 +623,9 @@ def main():
     d2h = nrhs * mesh.n_total * 16 + nrhs * len(cfg["obs"]) * 3 * 16
     h2d = 8 + 2 * 8 * m.n_domains + cfg["dirs"].nbytes + cfg["pols"].nbytes + cfg["obs"].nbytes
     mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
-    sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                    precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
+    sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **opts)
     e2e_times = []
-    for it in range(1 + max(1, min(args.steps, 5))):
+    for it in range(1 + max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sh.reassemble(cfg["k0"], np.asarray(cfg["eps_r"], dtype=np.float64), np.asarray(cfg["mu_r"], dtype=np.float64))
@@ -515,91 +639,52 @@ def main():
     e2e = job_throughput(nrhs, statistics.median(e2e_times), world)
     # the same with the mesh and system created from host arrays every step
     # (mesh tables, block-OSRC eigenpairs, assembly), for reference
-    setup_times = []
     h2d_setup = h2d + m.vertices.nbytes + m.triangles.nbytes + m.labels.nbytes
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
-        sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                        precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
-        xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
-        fe = sh.farfield(xe, cfg["obs"])
-        xh, fh = xe.cpu(), fe.cpu()
-        torch.cuda.synchronize()
-        setup_times.append(time.perf_counter() - t0)
-        del sh, mh
-    e2e_setup = job_throughput(nrhs, min(setup_times), world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mh = api.Mesh(m.vertices, m.triangles, m.labels, m.n_domains)
+    sh = api.System(mh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **opts)
+    xe, ste = sh.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+    fe = sh.farfield(xe, cfg["obs"])
+    xh, fh = xe.cpu(), fe.cpu()
+    torch.cuda.synchronize()
+    e2e_setup = job_throughput(nrhs, time.perf_counter() - t0, world)
+    del sh, mh
 
-    # ---- the same workload on the plain FP64 path and with the learned ------
-    # correction (rank 0 at N = 1): the comparisons that put the mixed path's
-    # number in context
-    fp64_line, learned_line = None, None
-    if rank == 0 and world == 1 and not args.no_comparisons and prec == L.MTF_PREC_MIXED:
-        s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                         max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
-
-        def step64():
-            s64.reassemble(cfg["k0"], cfg["eps_r"], cfg["mu_r"])
-            x6, st6 = s64.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
-            return x6, st6, s64.farfield(x6, cfg["obs"])
-
-        step64()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(2):
-            x6, st6, _f6 = step64()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / 2
-        err64 = (float(((x6 - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None)
-        fp64_line = {"value": nrhs / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                     "gmres_iterations": int(st6.iterations), "converged": bool(st6.converged),
-                     "solution_rel_err_vs_fp64_tight": err64,
-                     "path": "FP64 storage, matvec, Arnoldi; block-OSRC (same tolerance, restart, Pade order)"}
-        del s64
-        # learned correction: fitted on two other plane waves with validation
-        # solves; plain block-OSRC is kept when no round beats it
-        sl = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], tol=args.tol, restart=args.restart,
-                        precision=prec, max_iter=args.max_iter, precond=pc, osrc_np=args.osrc_np)
-        sl.learned_init("table")
-        d_val = mi.fibonacci_directions(9)[0:2]
-        p_val = mi.orthonormal_polarizations(d_val)[0].astype(np.complex128)
-        t0 = time.perf_counter()
-        rep = sl.learned_fit(d_val, p_val, rounds=4, steps_per_round=150, lr=3e-3, batch=16, K=6, seed=5)
-        t_fit = time.perf_counter() - t0
-        xl, stl = sl.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
-        errl = float(((xl - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
-        learned_line = {"fit": rep, "fit_seconds": t_fit, "enabled": bool(rep["enabled"]),
-                        "gmres_iterations": int(stl.iterations), "solution_rel_err_vs_fp64": errl,
-                        "note": "table-parametrised stencil, power loss K = 6, validation on 2 other plane waves"}
-        del sl
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_comparisons and args.workload != "split_sphere":
+        secondary = secondary_split_sphere(api, L, args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(cfg, int(statistics.median(iters)))
         cpu = {"value": nrhs / res["t_step"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": res["sample"], "assembly_pairs_per_s": res["pairs_per_s"]}
+               "sample": res["sample"], "assembly_pairs_per_s": res["pairs_per_s"], "matvec_s": res["t_matvec"]}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == L.MTF_PREC_FP64 else "f32+f64",
+            "vs_baseline": None, "dtype": "f64" if prec == L.MTF_PREC_FP64 else "f16x3+f32+f64",
             "data": "synthetic",
             "config": {"workload": cfg["desc"], "nrhs": nrhs, "n_unknowns": int(mesh.n_total),
-                       "triangle_pairs": n_pairs, "precision": args.precision, "preconditioner": args.precond, "osrc_pade_order": args.osrc_np, "gmres_tol": args.tol,
-                       "restart": args.restart, "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
+                       "blocks": int(mesh.n_domains), "triangle_pairs": n_pairs, "precision": args.precision,
+                       "preconditioner": args.precond, "osrc_pade_order": args.osrc_np, "gmres_tol": args.tol,
+                       "krylov": "block FGMRES (one space for all right-hand sides)" if prec == L.MTF_PREC_MIXED
+                       else "FGMRES per right-hand side", "restart": args.restart,
+                       "matvec": "tcgen05, FP16 hi+lo split, FP32 accumulation" if prec == L.MTF_PREC_MIXED
+                       else "FP64",
+                       "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
                        "parallelism": f"replicas x{world}"},
             "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},
             "solution_rel_err_vs_fp64": err,
+            "fp64_reference": ref_info,
             "gmres_iterations": int(statistics.median(iters)),
             "converged": bool(st.converged),
-            "reference_converged": bool(st_ref.converged) if st_ref is not None else None,
             "gpu_launches": int(launches),
-            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+            "kernels": kernel_table(prof),
             "kernel_times": "CUDA events around every library launch in a second pass of the same steps "
-                            "(event pairs slow the solve, so that pass is not the timed one)",
+                            "(event pairs slow the solve, so that pass is not the timed one); GB/s from the "
+                            "algorithmic bytes each launch declares",
             "roofline": roof,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "step": "mtf_reassemble (host eps_r, mu_r) + mtf_solve (host plane waves) + mtf_farfield, "
@@ -609,8 +694,11 @@ def main():
                                     "step": "mtf_mesh_create + mtf_assemble (incl. block-OSRC eigenpairs) + "
                                             "mtf_solve + mtf_farfield from host arrays"},
             "cpu_baseline": cpu,
-            "fp64_block_osrc": fp64_line,
-            "learned_correction": learned_line,
+            "secondary": secondary,
+            "learned_correction": {"enabled": False, "note": "not run on this workload: the learned correction keeps "
+                                   "per-rhs Krylov spaces, so its validation solves would cost minutes here; it is "
+                                   "reported on the split-sphere line under 'secondary'"}
+            if secondary is not None else None,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

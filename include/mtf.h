@@ -107,7 +107,7 @@ typedef struct {
                            into FP32 pairs, error-free products and sums;
                            about 2^-46 relative, on the FP32 pipes);
                            0: FP64 products and sums.  Default 1             */
-  int32_t block_krylov; /* mixed mode with nrhs > 1 (and no learned
+  int32_t block_krylov; /* mixed mode with nrhs >= 4 (and no learned
                            correction initialised): 1: the inner FGMRES cycles build one
                            block Krylov space shared by all right-hand sides
                            (block flexible GMRES, block classical
@@ -192,6 +192,11 @@ mtf_status mtf_reassemble(mtf_system sys, double k0, const double* eps_r, const 
  * the counters.  Process-wide, not thread-safe. */
 mtf_status mtf_profile_enable(int32_t on);
 mtf_status mtf_profile_read(int32_t n, int64_t* launches, double* ms);
+/* mtf_profile_read that also returns, per kernel id, the algorithmic bytes
+ * of the launches counted (every stored operator entry, input and output
+ * value once, as the launch site declares them; 0 for kernels that declare
+ * none).  Resets all three counters. */
+mtf_status mtf_profile_read_bytes(int32_t n, int64_t* launches, double* ms, double* bytes);
 int32_t mtf_kernel_count(void);
 const char* mtf_kernel_name(int32_t id);
 

@@ -53,6 +53,7 @@ _SIGS = {
     "mtf_reassemble": (_i32, [_vp, _dbl, _vp, _vp, _vp]),
     "mtf_profile_enable": (_i32, [_i32]),
     "mtf_profile_read": (_i32, [_i32, _vp, _vp]),
+    "mtf_profile_read_bytes": (_i32, [_i32, _vp, _vp, _vp]),
     "mtf_kernel_count": (_i32, []),
     "mtf_kernel_name": (ctypes.c_char_p, [_i32]),
     "mtf_get_block": (_i32, [_vp, _i32, _vp, _vp, _vp]),
@@ -194,6 +195,16 @@ def mtf_profile_read():
     ms = np.zeros(n, dtype=np.float64)
     _check(load().mtf_profile_read(n, _ptr(la), _ptr(ms)))
     return {mtf_kernel_name(i): (int(la[i]), float(ms[i])) for i in range(n)}
+
+
+def mtf_profile_read_bytes():
+    """Returns {kernel name: (launches, ms, algorithmic bytes)} since the last read, and resets."""
+    n = mtf_kernel_count()
+    la = np.zeros(n, dtype=np.int64)
+    ms = np.zeros(n, dtype=np.float64)
+    by = np.zeros(n, dtype=np.float64)
+    _check(load().mtf_profile_read_bytes(n, _ptr(la), _ptr(ms), _ptr(by)))
+    return {mtf_kernel_name(i): (int(la[i]), float(ms[i]), float(by[i])) for i in range(n)}
 
 
 def mtf_get_block(sys_, i, t_out, k_out, stream=0):

@@ -33,15 +33,37 @@
 
 namespace mtf {
 
+struct TcArnoldi;
+TcArnoldi* tca_create();
+void tca_destroy(TcArnoldi* t);
+void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st);
+void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st);
+void tca_project(TcArnoldi& t, int nq, float* W, double* H, unsigned* err, cudaStream_t st);
+
 struct BlockWork {
   int s = 0, m = 0;
   int64_t n = 0, ldn = 0;
+  TcArnoldi* tca = nullptr;  // tensor-core projections (arnoldi_tc.cu), with mv_tensor
   DevBuf<float> V, Z, W, D;  // (m + 1) s, m s, s, s vectors
   DevBuf<double> H;          // Gpre (s x s) | H1 ((m+1) s x s) | H2 | G (s x s), complex
   DevBuf<double> C;          // s x s (complex, FP64) transform, or the coefficients Y (m s x s)
+  DevBuf<double> Cd;         // R1, T1, R2, T2 of a step's Cholesky factorisations (complex s x s each)
+  DevBuf<int> kept;          // kept flags of the two factorisations
   double* h_host = nullptr;
+  double* pin = nullptr;     // two pinned slots of a step's coefficients
+  int* kept_host = nullptr;  // two pinned slots of kept flags and the error word
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // the space of the solve's previous cycle, kept for the next one
+  BlockLSQ lsq;
+  bool rec_ok = false;
+  int vshift = 0;
   ~BlockWork() {
     if (h_host) cudaFreeHost(h_host);
+    if (pin) cudaFreeHost(pin);
+    if (kept_host) cudaFreeHost(kept_host);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    tca_destroy(tca);
   }
 };
 
@@ -261,6 +283,81 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
   *xp = o;
 }
 
+// Deflating Cholesky factor of a block's Gram matrix on the device (the
+// rule of deflating_cholesky in block_krylov.h): G (complex FP64, entry
+// [q s + c] = <W_q, W_c>) = R^H R with R upper triangular; direction k is
+// dropped (row k of R zero, kept[k] = 0) when its Schur pivot is not above
+// tau^2 ref_k, ref_k = the diagonal of Gpre (squared norms before the
+// Gram-Schmidt projections) or, with mask, 1 for mask[k] != 0 and 0
+// otherwise.  T = R_KK^-1 on the kept set K (zero elsewhere), so that
+// V = W T is orthonormal on K.  R and T complex FP64, column-major
+// (entry (i, c) at [c s + i]).  One CTA of 64 threads, s <= 64; the working
+// copy of G in shared memory (s * s complex).
+__global__ void __launch_bounds__(64) k_bchol(const double* __restrict__ G, const double* __restrict__ Gpre,
+                                              const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
+                                              double* __restrict__ T, int* __restrict__ kept) {
+  extern __shared__ double2 A[];  // A[c * s + i] = current Schur complement entry (i, c)
+  __shared__ double piv;
+  __shared__ int keep;
+  const int c = threadIdx.x;
+  if (c < s)
+    for (int i = 0; i < s; ++i) {
+      A[c * s + i] = make_double2(G[2 * (i * s + c)], G[2 * (i * s + c) + 1]);
+      R[2 * (c * s + i)] = 0.0;
+      R[2 * (c * s + i) + 1] = 0.0;
+    }
+  for (int k = 0; k < s; ++k) {
+    __syncthreads();
+    if (c == 0) {
+      const double d = A[k * s + k].x;
+      const double ref = mask ? (mask[k] ? 1.0 : 0.0) : Gpre[2 * (k * s + k)];
+      keep = (d > tau * tau * fmax(ref, 0.0) && d > 0.0) ? 1 : 0;
+      piv = keep ? sqrt(d) : 0.0;
+      kept[k] = keep;
+    }
+    __syncthreads();
+    if (!keep) continue;
+    if (c >= k && c < s) {
+      const double2 a = A[c * s + k];
+      const double2 r = c == k ? make_double2(piv, 0.0) : make_double2(a.x / piv, a.y / piv);
+      R[2 * (c * s + k)] = r.x;
+      R[2 * (c * s + k) + 1] = r.y;
+    }
+    __syncthreads();
+    if (c > k && c < s) {
+      const double rkr = R[2 * (c * s + k)], rki = R[2 * (c * s + k) + 1];
+      for (int i = k + 1; i <= c; ++i) {
+        const double ar = R[2 * (i * s + k)], ai = -R[2 * (i * s + k) + 1];  // conj(R(k, i))
+        A[c * s + i].x -= ar * rkr - ai * rki;
+        A[c * s + i].y -= ar * rki + ai * rkr;
+      }
+    }
+  }
+  __syncthreads();
+  if (c >= s) return;
+  for (int i = 0; i < s; ++i) {
+    T[2 * (c * s + i)] = 0.0;
+    T[2 * (c * s + i) + 1] = 0.0;
+  }
+  if (!kept[c]) return;
+  const double dq = R[2 * (c * s + c)];
+  T[2 * (c * s + c)] = 1.0 / dq;
+  for (int i = c - 1; i >= 0; --i) {
+    if (!kept[i]) continue;
+    double ar = 0, ai = 0;
+    for (int p = i + 1; p <= c; ++p) {
+      if (!kept[p]) continue;
+      const double rr = R[2 * (p * s + i)], ri = R[2 * (p * s + i) + 1];
+      const double tr = T[2 * (c * s + p)], ti = T[2 * (c * s + p) + 1];
+      ar += rr * tr - ri * ti;
+      ai += rr * ti + ri * tr;
+    }
+    const double d = R[2 * (i * s + i)];
+    T[2 * (c * s + i)] = -ar / d;
+    T[2 * (c * s + i) + 1] = -ai / d;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -282,6 +379,8 @@ static void bdots(mtf_system sys, const float* V, int nq, int64_t ldv, const flo
     const dim3 grid(unsigned((n_pad + seg - 1) / seg), unsigned(gy));
     const float* Wc = W + 2 * int64_t(c0) * ldw;
     double* Hc = H + 2 * c0;
+    // basis and block read once
+    prof_bytes(KID_DOTS, double(nq + nc) * double(n_pad) * 8.0);
 #define MTF_BDOTS(SCV, VWV) \
   MTF_LAUNCH(KID_DOTS, st, k_bdots<SCV, VWV><<<grid, 256, 0, st>>>(V, nq, ldv, Wc, ldw, nc, seg, n_pad, Hc, ldh))
     if (SC == 16) MTF_BDOTS(16, 2);
@@ -305,6 +404,8 @@ static void bupdate_launch(const float* V, int nq, int64_t ldv, const double* H,
     MTF_CUDA(cudaFuncSetAttribute(k_bupdate<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     opted.fetch_or(bit);
   }
+  // basis read once, block read and written once
+  prof_bytes(KID_AXPY, double(nq + 2 * nc) * double(n_pad) * 8.0);
   MTF_LAUNCH(KID_AXPY, st, k_bupdate<SC><<<nbk(n_pad, 64), 256, smem, st>>>(V, nq, ldv, H, ldh, W, ldw, nc, n_pad));
 }
 
@@ -345,8 +446,11 @@ static void bxform(const float* in, int64_t ldi, const double* T, int s, float* 
 // stay orthogonal to the basis to about 1e-2 after normalisation
 constexpr double kDeflateTau = 1e-5;
 
+// kept restarts in a row (each widens the least-squares band by one block)
+constexpr int kMaxKeep = 2;
+
 mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t st) {
+                          std::vector<int>& iters, bool& reached, cudaStream_t st, int cycle) {
   MTF_REQUIRE(s >= 1 && s <= 64, MTF_ERR_ARG, "block FGMRES supports 1..64 right-hand sides");
   mtf_mesh msh = sys->mesh;
   const int64_t n = msh->n_total;
@@ -355,6 +459,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   const bool pre = sys->opt.precond == MTF_PRECOND_OSRC;
   if (!sys->bw) sys->bw = new BlockWork();
   BlockWork& B = *sys->bw;
+  stream_prepare(sys, st);  // error word of the bounded waits
   const size_t hsz = size_t(2) * (s * s + 2 * size_t(m + 1) * s * s + s * s);
   if (B.s != s || B.m != m || B.n != n) {
     B.V.alloc(size_t(m + 1) * s * ldn * 2);
@@ -366,13 +471,25 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     MTF_CUDA(cudaMemsetAsync(B.W.p, 0, B.W.n * sizeof(float), st));
     B.H.alloc(hsz);
     B.C.alloc(size_t(2) * std::max<size_t>(size_t(s) * s, size_t(m) * s * s));
+    B.Cd.alloc(size_t(8) * s * s);
+    B.kept.alloc(size_t(2) * s);
     if (B.h_host) cudaFreeHost(B.h_host);
+    if (B.pin) cudaFreeHost(B.pin);
+    if (B.kept_host) cudaFreeHost(B.kept_host);
     B.h_host = nullptr;
+    B.pin = nullptr;
+    B.kept_host = nullptr;
     MTF_CUDA(cudaMallocHost(&B.h_host, hsz * sizeof(double)));
+    const size_t slot_len = 4 * size_t(m + 1) * s * s + 4 * size_t(s) * s + 2 * size_t(s) + 1;
+    MTF_CUDA(cudaMallocHost(&B.pin, 2 * slot_len * sizeof(double)));
+    MTF_CUDA(cudaMallocHost(&B.kept_host, 2 * (2 * size_t(s) + 1) * sizeof(int)));
+    for (auto& e : B.ev)
+      if (!e) MTF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     B.s = s;
     B.m = m;
     B.n = n;
     B.ldn = ldn;
+    B.rec_ok = false;
   }
   double* Gpre = B.H.p;
   double* H1 = Gpre + 2 * size_t(s) * s;
@@ -397,137 +514,258 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     }
     MTF_CUDA(cudaMemcpyAsync(B.C.p, Tup.data(), Tup.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   };
+  // the Gram-Schmidt projections run on the tensor cores with the matvec
+  const bool tc = sys->opt.mv_tensor != 0;
+  if (tc) {
+    if (!B.tca) B.tca = tca_create();
+    tca_prepare(*B.tca, s, m, ldn, st);
+  }
+  unsigned* err_word = sys->d_mv_ctl.p + 2;
+  const double tau = kDeflateTau;
+  auto project = [&](int nq) {  // W <- (I - V V^H)^2 W against the first nq basis vectors; H1, H2 the coefficients
+    if (tc) {
+      tca_project(*B.tca, nq, B.W.p, H1, err_word, st);
+      tca_project(*B.tca, nq, B.W.p, H2, err_word, st);
+    } else {
+      MTF_CUDA(cudaMemsetAsync(H1, 0, 2 * size_t(nq) * s * sizeof(double), st));
+      MTF_CUDA(cudaMemsetAsync(H2, 0, 2 * size_t(nq) * s * sizeof(double), st));
+      bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H1, s, st);
+      bupdate(B.V.p, nq, ldn, H1, s, B.W.p, ldn, s, ldn, st);
+      bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H2, s, st);
+      bupdate(B.V.p, nq, ldn, H2, s, B.W.p, ldn, s, ldn, st);
+    }
+  };
 
-  // start block: W = r (FP32), G0 = W^H W, V_0 = W T0, S0 = R0
+  // the residual block: W = r (FP32) and its Gram matrix (norms ||r_c||)
   MTF_LAUNCH(KID_NORM, st, k_blk_to32<<<dim3(nbk(ldn, 256), unsigned(s)), 256, 0, st>>>(r_dev, n, B.W.p, ldn));
   MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
   bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
   MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
   MTF_CUDA(cudaStreamSynchronize(st));
   fetch_gram(G, Gh);
-  std::vector<double> bnorm(s);
+  std::vector<double> bnorm(s), ref0(s);
   for (int c = 0; c < s; ++c) {
     const double d = Gh[size_t(c) * s + c].real();
     if (!std::isfinite(d)) return MTF_ERR_NAN;
     bnorm[c] = std::sqrt(std::max(d, 0.0));
-    ref[c] = d;
+    ref0[c] = d;
   }
-  // dependent or zero residual columns are deflated from the start
-  const int nk0 = deflating_cholesky(s, Gh.data(), ref.data(), 1e-12, R.data(), T.data(), kept);
-  reached = nk0 == 0;
-  if (reached) return MTF_OK;
-  upload_T(T);
-  bxform(B.W.p, ldn, B.C.p, s, B.V.p, ldn, ldn, st);
-  BlockLSQ lsq;
-  lsq.init(s, m, R.data(), bnorm.data());
+  // Restart that keeps the space (the next refinement cycle of one solve):
+  // the new residual is projected on the basis built so far, its remainder
+  // opens a new start block, and the new column blocks are orthogonalised
+  // against the whole basis, so the cycle does not rebuild the slow start
+  // of the previous one.  Column block J then multiplies basis block
+  // J + vshift (vshift = kept restarts so far).
+  BlockLSQ& lsq = B.lsq;
+  const int nb_old = lsq.k + 1 + B.vshift;
+  const bool keep = cycle > 0 && sys->opt.recycle && B.rec_ok && lsq.s == s && B.vshift < kMaxKeep &&
+                    nb_old + 16 <= m;
+  B.rec_ok = false;
+  bool grow = true;  // the start block has a kept direction
+  if (!keep) {
+    // dependent or zero residual columns are deflated from the start
+    const int nk0 = deflating_cholesky(s, Gh.data(), ref0.data(), 1e-12, R.data(), T.data(), kept);
+    reached = nk0 == 0;
+    if (reached) return MTF_OK;
+    upload_T(T);
+    bxform(B.W.p, ldn, B.C.p, s, B.V.p, ldn, ldn, st);
+    if (tc) tca_store(*B.tca, B.V.p, 0, st);
+    lsq.init(s, m, R.data(), bnorm.data(), 1 + kMaxKeep);
+    B.vshift = 0;
+  } else {
+    const int nq_old = nb_old * s;
+    project(nq_old);
+    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
+    bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
+    MTF_CUDA(cudaMemcpyAsync(B.h_host + (H1 - B.H.p), H1, 2 * size_t(nq_old) * s * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(B.h_host + (H2 - B.H.p), H2, 2 * size_t(nq_old) * s * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaStreamSynchronize(st));
+    fetch_gram(G, Gh);
+    const int nk0 = deflating_cholesky(s, Gh.data(), ref0.data(), tau, R.data(), T.data(), kept);
+    const size_t nr = size_t(nq_old + s);
+    std::vector<cdouble> G0(nr * s);
+    const double* hp1 = B.h_host + (H1 - B.H.p);
+    const double* hp2 = B.h_host + (H2 - B.H.p);
+    for (int c = 0; c < s; ++c) {
+      for (int q = 0; q < nq_old; ++q) {
+        const size_t o = 2 * (size_t(q) * s + c);
+        G0[size_t(c) * nr + q] = cdouble(hp1[o] + hp2[o], hp1[o + 1] + hp2[o + 1]);
+      }
+      for (int i = 0; i < s; ++i) G0[size_t(c) * nr + nq_old + i] = R[size_t(c) * s + i];
+    }
+    for (const cdouble& v : G0)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return MTF_ERR_NAN;
+    upload_T(T);
+    float* V0 = B.V.p + 2 * int64_t(nb_old) * vstride;
+    bxform(B.W.p, ldn, B.C.p, s, V0, ldn, ldn, st);
+    if (tc) tca_store(*B.tca, V0, nq_old, st);
+    lsq.restart(G0.data(), nb_old + 1, bnorm.data(), est.data());
+    B.vshift += 1;
+    bool all = true;
+    for (int c = 0; c < s; ++c) all = all && est[c] <= tol;
+    reached = all;
+    grow = !all && nk0 > 0;
+  }
+  const int vshift = B.vshift;
+  const int J0 = lsq.k;
 
-  std::vector<cdouble> h, R2(size_t(s) * s), Rn(size_t(s) * s, cdouble(0));
-  int kdone = 0;
-  const bool debug = std::getenv("MTF_BLOCK_DEBUG") != nullptr;
-  const double tau = std::getenv("MTF_BLOCK_TAU") ? std::atof(std::getenv("MTF_BLOCK_TAU")) : kDeflateTau;
-  const int jend = std::min(m, std::max(1, max_iter));
-  for (int j = 0; j < jend; ++j) {
-    float* Vj = B.V.p + 2 * int64_t(j) * vstride;
-    float* Zj = B.Z.p + 2 * int64_t(j) * vstride;
+  // Pipelined block steps.  Everything of step J runs on the device --
+  // block-OSRC, the matvec, both Gram-Schmidt projections, the deflating
+  // Cholesky factorisations (two: CholQR2) and the next basis block -- and
+  // its coefficients (H1, H2, R1, R2, the kept flags and the error word) are
+  // copied to a pinned slot; the host queues step J + 1 before it reads step
+  // J's slot, so that the least-squares update of step J overlaps the device
+  // work of step J + 1.  A step computed past convergence is discarded.
+  // Column block J multiplies basis block J + vshift and produces block
+  // J + vshift + 1; the basis holds m + 1 blocks and Z holds m.
+  const int Jend = std::min(m - vshift, J0 + std::max(1, max_iter));
+  double* R1 = B.Cd.p;
+  double* T1 = R1 + 2 * size_t(s) * s;
+  double* R2 = T1 + 2 * size_t(s) * s;
+  double* T2 = R2 + 2 * size_t(s) * s;
+  int* kept1 = B.kept.p;
+  int* kept2 = kept1 + s;
+  {
+    static std::atomic<uint64_t> opted{0};
+    int dev = 0;
+    MTF_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(opted.load() & bit)) {
+      MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16));
+      opted.fetch_or(bit);
+    }
+  }
+  const size_t chol_smem = size_t(s) * s * sizeof(double2);
+  // pinned slot layout (doubles): H1 (m+1) s s complex | H2 | R1 | R2; kept flags and error word separately
+  const size_t slot_h = 2 * size_t(m + 1) * s * s;
+  const size_t slot_len = 2 * slot_h + 4 * size_t(s) * s + 2 * size_t(s) + 1;
+  auto slot = [&](int J) { return B.pin + size_t(J & 1) * slot_len; };
+  auto launch_step = [&](int J) {
+    const int vb = J + vshift;
+    float* Vj = B.V.p + 2 * int64_t(vb) * vstride;
+    float* Zj = B.Z.p + 2 * int64_t(J) * vstride;
     if (pre) {
       launch_osrc_apply_f32(sys, Vj, ldn, Zj, ldn, s, st);
     } else {
       MTF_CUDA(cudaMemcpyAsync(Zj, Vj, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
     }
     launch_matvec_f32(sys, Zj, ldn, B.W.p, ldn, s, st);
-    const int nq = (j + 1) * s;
-    MTF_CUDA(cudaMemsetAsync(B.H.p, 0, hsz * sizeof(double), st));
+    const int nq = (vb + 1) * s;
+    MTF_CUDA(cudaMemsetAsync(Gpre, 0, 2 * size_t(s) * s * sizeof(double), st));
+    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
     bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, Gpre, s, st);
-    bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H1, s, st);
-    bupdate(B.V.p, nq, ldn, H1, s, B.W.p, ldn, s, ldn, st);
-    bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H2, s, st);
-    bupdate(B.V.p, nq, ldn, H2, s, B.W.p, ldn, s, ldn, st);
+    project(nq);
     bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
-    // Gpre | H1 | H2 are contiguous; G follows H2's (m+1) s x s slot
-    MTF_CUDA(cudaMemcpyAsync(B.h_host, B.H.p, size_t(2) * (s * s + size_t(nq) * s) * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (H2 - B.H.p), H2, size_t(2) * nq * s * sizeof(double), cudaMemcpyDeviceToHost,
-                             st));
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, size_t(2) * s * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaStreamSynchronize(st));
-    check_matvec_stream(sys, st);
-    // h = H1 + H2 ((j+1) s x s, column-major)
-    h.assign(size_t(nq) * s, cdouble(0));
-    const double* hp1 = B.h_host + (H1 - B.H.p);
-    const double* hp2 = B.h_host + (H2 - B.H.p);
-    bool finite = true;
-    for (int q = 0; q < nq; ++q)
-      for (int c = 0; c < s; ++c) {
-        const size_t o = 2 * (size_t(q) * s + c);
-        const cdouble v(hp1[o] + hp2[o], hp1[o + 1] + hp2[o + 1]);
-        finite = finite && std::isfinite(v.real()) && std::isfinite(v.imag());
-        h[size_t(c) * nq + q] = v;
-      }
-    std::vector<cdouble> Gp(size_t(s) * s);
-    fetch_gram(Gpre, Gp);
-    fetch_gram(G, Gh);
-    for (int c = 0; c < s; ++c) ref[c] = Gp[size_t(c) * s + c].real();
-    if (!finite) return MTF_ERR_NAN;
-    const int nk = deflating_cholesky(s, Gh.data(), ref.data(), tau, R.data(), T.data(), kept);
-    upload_T(T);
-    bxform(B.W.p, ldn, B.C.p, s, B.D.p, ldn, ldn, st);
-    // second Cholesky pass (CholQR2): the first leaves V = W R^-1
-    // orthonormal only to about cond(W) times the FP32 rounding;
-    // V_{j+1} = V R2^-1 and R_{j+1} = R2 R
+    MTF_LAUNCH(KID_NORM, st, k_bchol<<<1, 64, chol_smem, st>>>(G, Gpre, nullptr, tau, s, R1, T1, kept1));
+    bxform(B.W.p, ldn, T1, s, B.D.p, ldn, ldn, st);
+    // second pass (CholQR2): the first leaves V = W R^-1 orthonormal only
+    // to about cond(W) times the FP32 rounding; V_next = V R2^-1, R = R2 R1
     MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
     bdots(sys, B.D.p, s, ldn, B.D.p, ldn, s, ldn, G, s, st);
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, size_t(2) * s * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaStreamSynchronize(st));
-    fetch_gram(G, Gh);
-    for (int c = 0; c < s; ++c) ref[c] = kept[c] ? 1.0 : 0.0;
-    std::vector<int> kept2;
-    deflating_cholesky(s, Gh.data(), ref.data(), 1e-3, R2.data(), T.data(), kept2);
-    upload_T(T);
-    bxform(B.D.p, ldn, B.C.p, s, B.V.p + 2 * int64_t(j + 1) * vstride, ldn, ldn, st);
-    for (int c = 0; c < s; ++c)
-      for (int i = 0; i <= c; ++i) {
-        cdouble a = 0;
-        for (int p = i; p <= c; ++p) a += R2[size_t(p) * s + i] * R[size_t(c) * s + p];
-        Rn[size_t(c) * s + i] = a;
+    MTF_LAUNCH(KID_NORM, st, k_bchol<<<1, 64, chol_smem, st>>>(G, nullptr, kept1, 1e-3, s, R2, T2, kept2));
+    float* Vn = B.V.p + 2 * int64_t(vb + 1) * vstride;
+    bxform(B.D.p, ldn, T2, s, Vn, ldn, ldn, st);
+    if (tc) tca_store(*B.tca, Vn, (vb + 1) * s, st);
+    double* sl = slot(J);
+    MTF_CUDA(cudaMemcpyAsync(sl, H1, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(sl + slot_h, H2, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(sl + 2 * slot_h, R1, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(sl + 2 * slot_h + 2 * size_t(s) * s, R2, 2 * size_t(s) * s * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(B.kept_host + size_t(J & 1) * (2 * s + 1), kept1, 2 * size_t(s) * sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(B.kept_host + size_t(J & 1) * (2 * s + 1) + 2 * s, err_word, sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaEventRecord(B.ev[J & 1], st));
+  };
+
+  std::vector<cdouble> h, Rr1(size_t(s) * s), Rr2(size_t(s) * s), Rn(size_t(s) * s);
+  int steps = 0;
+  mtf_status status = MTF_OK;
+  if (!reached && grow && J0 < Jend) {
+    launch_step(J0);
+    for (int J = J0; J < Jend; ++J) {
+      if (J + 1 < Jend) launch_step(J + 1);
+      MTF_CUDA(cudaEventSynchronize(B.ev[J & 1]));
+      const double* sl = slot(J);
+      const int* kh = B.kept_host + size_t(J & 1) * (2 * s + 1);
+      if (kh[2 * s] != 0) {
+        status = MTF_ERR_TIMEOUT;
+        break;
       }
-    lsq.add_block(h.data(), Rn.data(), est.data());
-    if (debug && (j % 25 == 0 || j < 5)) {
-      double emax = 0;
-      for (double e : est) emax = std::max(emax, e);
-      int nk2 = 0;
-      for (int v : kept2) nk2 += v;
-      std::fprintf(stderr, "block j=%d kept=%d/%d est_max=%.3e\n", j, nk, nk2, emax);
+      const int nq = (J + vshift + 1) * s;
+      h.assign(size_t(nq) * s, cdouble(0));
+      bool finite = true;
+      for (int q = 0; q < nq; ++q)
+        for (int c = 0; c < s; ++c) {
+          const size_t o = 2 * (size_t(q) * s + c);
+          const cdouble v(sl[o] + sl[slot_h + o], sl[o + 1] + sl[slot_h + o + 1]);
+          finite = finite && std::isfinite(v.real()) && std::isfinite(v.imag());
+          h[size_t(c) * nq + q] = v;
+        }
+      const double* r1 = sl + 2 * slot_h;
+      const double* r2 = r1 + 2 * size_t(s) * s;
+      for (size_t t = 0; t < size_t(s) * s; ++t) {
+        Rr1[t] = cdouble(r1[2 * t], r1[2 * t + 1]);
+        Rr2[t] = cdouble(r2[2 * t], r2[2 * t + 1]);
+      }
+      if (!finite) {
+        status = MTF_ERR_NAN;
+        break;
+      }
+      for (int c = 0; c < s; ++c)
+        for (int i = 0; i < s; ++i) {
+          cdouble a = 0;
+          if (i <= c)
+            for (int p = i; p <= c; ++p) a += Rr2[size_t(p) * s + i] * Rr1[size_t(c) * s + p];
+          Rn[size_t(c) * s + i] = a;
+        }
+      if (!lsq.add_block(h.data(), nq / s, Rn.data(), est.data())) break;
+      ++steps;
+      int nk = 0;
+      for (int c = 0; c < s; ++c) nk += kh[c];
+      bool all = true;
+      for (int c = 0; c < s; ++c) {
+        if (!std::isfinite(est[c])) status = MTF_ERR_NAN;
+        all = all && est[c] <= tol;
+      }
+      if (status != MTF_OK) break;
+      if (all) {
+        reached = true;
+        break;
+      }
+      if (nk == 0) break;  // the space is exhausted: the next cycle starts from the new residual
     }
-    kdone = j + 1;
-    bool all = true;
-    for (int c = 0; c < s; ++c) {
-      if (!std::isfinite(est[c])) return MTF_ERR_NAN;
-      all = all && est[c] <= tol;
-    }
-    if (all) {
-      reached = true;
-      break;
-    }
-    if (nk == 0) break;  // the space is exhausted: the next cycle starts from the new residual
+    MTF_CUDA(cudaStreamSynchronize(st));  // a step queued past the last one has finished
   }
-  for (int c = 0; c < s; ++c) iters[c] += kdone;
-  // x += Z Y: D = 0 - Z (-Y)
+  if (status != MTF_OK) {
+    MTF_CUDA(cudaMemsetAsync(sys->d_mv_ctl.p, 0, 4 * sizeof(unsigned), st));
+    return status;
+  }
+  for (int c = 0; c < s; ++c) iters[c] += steps;
+  // x += Z Y over every column block of the space: D = 0 - Z (-Y)
   std::vector<cdouble> Y;
   lsq.solve(Y);
-  const int nqz = kdone * s;
-  std::vector<double> Yup(size_t(2) * nqz * s);
-  for (int q = 0; q < nqz; ++q)
-    for (int c = 0; c < s; ++c) {
-      const cdouble v = Y[size_t(c) * nqz + q];
-      if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return MTF_ERR_NAN;
-      Yup[2 * (size_t(q) * s + c)] = -v.real();
-      Yup[2 * (size_t(q) * s + c) + 1] = -v.imag();
-    }
-  MTF_CUDA(cudaMemcpyAsync(B.C.p, Yup.data(), Yup.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  MTF_CUDA(cudaMemsetAsync(B.D.p, 0, B.D.n * sizeof(float), st));
-  bupdate(B.Z.p, nqz, ldn, B.C.p, s, B.D.p, ldn, s, ldn, st);
-  MTF_LAUNCH(KID_AXPY, st, k_blk_addx<<<dim3(nbk(n, 256), unsigned(s)), 256, 0, st>>>(x_dev, n, B.D.p, ldn));
+  const int nqz = lsq.k * s;
+  if (nqz > 0) {
+    std::vector<double> Yup(size_t(2) * nqz * s);
+    for (int q = 0; q < nqz; ++q)
+      for (int c = 0; c < s; ++c) {
+        const cdouble v = Y[size_t(c) * nqz + q];
+        if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return MTF_ERR_NAN;
+        Yup[2 * (size_t(q) * s + c)] = -v.real();
+        Yup[2 * (size_t(q) * s + c) + 1] = -v.imag();
+      }
+    MTF_CUDA(cudaMemcpyAsync(B.C.p, Yup.data(), Yup.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    MTF_CUDA(cudaMemsetAsync(B.D.p, 0, B.D.n * sizeof(float), st));
+    bupdate(B.Z.p, nqz, ldn, B.C.p, s, B.D.p, ldn, s, ldn, st);
+    MTF_LAUNCH(KID_AXPY, st, k_blk_addx<<<dim3(nbk(n, 256), unsigned(s)), 256, 0, st>>>(x_dev, n, B.D.p, ldn));
+  }
   MTF_CUDA(cudaStreamSynchronize(st));  // host buffers are released on return
+  B.rec_ok = true;
   return MTF_OK;
 }
 

@@ -10,12 +10,17 @@
 // and W = V_{j+1} R_{j+1} with V_{j+1} orthonormal (deflated columns are zero)
 // and R_{j+1} upper triangular.  Column block j of the Hessenberg matrix is
 // [h; R_{j+1}] ((j+2) s x s).  Each column block is reduced to triangular
-// form by s Householder reflectors acting on rows js .. (j+2)s - 1; reflector
-// k of block j has support {js + k .. js + s - 1} (top) and
-// {(j+1)s .. (j+1)s + k} (bottom, R_{j+1} being upper triangular), s + 1 rows.
-// The right-hand side of the least-squares problem is E_1 S_0, S_0 the
-// factor of the start block; after the reflectors of block j, rows
-// (j+1)s .. (j+2)s - 1 of its column c hold the residual of right-hand side c.
+// form by s Householder reflectors acting on rows js + k .. (j+2)s - 1
+// (reflector k of block j).  The right-hand side of the least-squares
+// problem is E_1 S_0, S_0 the factor of the start block; after the
+// reflectors of block j, rows (j+1)s .. (j+2)s - 1 of its column c hold the
+// residual of right-hand side c.
+//
+// A restart that keeps the space (the next cycle continues the basis and
+// projects its new residual onto it) gives column blocks whose h reaches one
+// basis block further per kept restart: the lower bandwidth of a column block
+// is then 2, 3, ... blocks, its reflectors reach as far, and the right-hand
+// sides are replaced by the new residual's coordinates (restart()).
 #pragma once
 
 #include <algorithm>
@@ -94,30 +99,37 @@ inline void parallel_for(int n, int threads, const std::function<void(int)>& f) 
 }
 
 struct BlockLSQ {
-  int s = 0, m = 0;          // block size, maximum number of block steps
-  int k = 0;                 // block columns added
+  int s = 0, m = 0;          // block size, maximum number of column blocks
+  int k = 0;                 // column blocks added
+  int bwmax = 1;             // largest lower bandwidth (in blocks) of a column block
+  std::vector<int> bw;       // lower bandwidth of every column block
   // reduced block columns: column block j holds rows 0 .. (j+1) s - 1 of its
   // s columns (column-major, leading dimension (j+1) s), at offset off[j]
   std::vector<cdouble> Rt;
   std::vector<size_t> off;
-  // reflectors: block j, reflector kk: s + 1 entries (top rows kk .. s-1,
-  // bottom rows 0 .. kk) and the scalar beta (v v^H scaled: I - beta v v^H)
+  // reflectors: block j, reflector kk: (1 + bwmax) s entries (top rows
+  // kk .. s-1 of block row j, then the bw[j] s rows below block row j) and
+  // the scalar beta (I - beta v v^H)
   std::vector<cdouble> refl;
   std::vector<double> beta;
-  std::vector<cdouble> g;    // (m + 1) s x s, column-major (ld (m+1) s)
+  std::vector<cdouble> g;    // ldg x s, column-major: the least-squares right-hand sides
+  size_t ldg = 0;
   std::vector<double> bnorm; // per right-hand side: reference norm of the estimates
   int threads = 1;
 
-  void init(int s_, int m_, const cdouble* S0, const double* base_norm) {
+  // S0: the start block's factor (s x s column-major), r = V_0 S0
+  void init(int s_, int m_, const cdouble* S0, const double* base_norm, int bwmax_ = 1) {
     s = s_;
     m = m_;
+    bwmax = std::max(1, bwmax_);
     k = 0;
+    bw.assign(size_t(m), 1);
     Rt.clear();
     off.assign(size_t(m) + 1, 0);
-    refl.assign(size_t(m) * s * (s + 1), cdouble(0));
+    refl.assign(size_t(m) * s * (1 + bwmax) * s, cdouble(0));
     beta.assign(size_t(m) * s, 0.0);
-    g.assign(size_t(m + 1) * s * s, cdouble(0));
-    const size_t ldg = size_t(m + 1) * s;
+    ldg = size_t(m + bwmax + 1) * s;
+    g.assign(ldg * s, cdouble(0));
     for (int c = 0; c < s; ++c)
       for (int i = 0; i < s; ++i) g[size_t(c) * ldg + i] = S0[size_t(c) * s + i];
     bnorm.assign(s, 1.0);
@@ -126,65 +138,90 @@ struct BlockLSQ {
     threads = int(std::max(1u, std::min(hw, 16u)));
   }
 
-  // apply reflector (j, kk) to one column x of length >= (j+2) s (rows js ..)
+  // apply reflector (j, kk) to one column x (rows j s .. (j + 1 + bw[j]) s - 1)
   inline void apply_reflector(int j, int kk, cdouble* x) const {
     const double b = beta[size_t(j) * s + kk];
     if (b == 0.0) return;
-    const cdouble* v = &refl[(size_t(j) * s + kk) * (s + 1)];
-    cdouble* top = x + size_t(j) * s;
-    cdouble* bot = x + size_t(j + 1) * s;
+    const cdouble* v = &refl[(size_t(j) * s + kk) * (1 + bwmax) * s];
+    cdouble* top = x + size_t(j) * s + kk;
+    const int len = s - kk + bw[size_t(j)] * s;
     cdouble a = 0;
-    const int nt = s - kk;
-    for (int t = 0; t < nt; ++t) a += std::conj(v[t]) * top[kk + t];
-    for (int t = 0; t <= kk; ++t) a += std::conj(v[nt + t]) * bot[t];
+    for (int t = 0; t < len; ++t) a += std::conj(v[t]) * top[t];
     a *= b;
-    for (int t = 0; t < nt; ++t) top[kk + t] -= v[t] * a;
-    for (int t = 0; t <= kk; ++t) bot[t] -= v[nt + t] * a;
+    for (int t = 0; t < len; ++t) top[t] -= v[t] * a;
   }
 
-  // Add column block j = k: h ((k+1) s x s, column-major, ld (k+1) s) and the
-  // upper-triangular R ((s x s) column-major).  est[c] receives the relative
-  // residual estimate of right-hand side c.  Returns false when m blocks are
-  // already stored.
-  bool add_block(const cdouble* h, const cdouble* R, double* est) {
+  // New right-hand sides for the space built so far (a restart that keeps
+  // the space): G0 holds nrows_blk s rows x s columns (column-major, leading
+  // dimension nrows_blk s), the coordinates of the new residual in the basis
+  // blocks 0 .. nrows_blk - 1.  The reflectors of the k column blocks are
+  // applied; est[c] = the residual of right-hand side c within the space.
+  void restart(const cdouble* G0, int nrows_blk, const double* base_norm, double* est) {
+    std::fill(g.begin(), g.end(), cdouble(0));
+    const size_t nr = size_t(nrows_blk) * s;
+    for (int c = 0; c < s; ++c) {
+      for (size_t i = 0; i < nr; ++i) g[size_t(c) * ldg + i] = G0[size_t(c) * nr + i];
+      bnorm[c] = base_norm[c] > 0 ? base_norm[c] : 1.0;
+    }
+    parallel_for(s, long(k) * s * s * s > 200000 ? threads : 1, [&](int c) {
+      for (int q = 0; q < k; ++q)
+        for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, &g[size_t(c) * ldg]);
+    });
+    for (int c = 0; c < s; ++c) {
+      double r2 = 0;
+      for (size_t i = size_t(k) * s; i < nr; ++i) r2 += std::norm(g[size_t(c) * ldg + i]);
+      est[c] = std::sqrt(r2) / bnorm[c];
+    }
+  }
+
+  // Add column block j = k: h (nrows_h s rows x s, column-major, leading
+  // dimension nrows_h s) on the basis blocks 0 .. nrows_h - 1 and the
+  // upper-triangular R (s x s) on block nrows_h; the lower bandwidth is
+  // nrows_h - j blocks (1 in a first cycle, 2 after one restart that kept
+  // the space, ...).  est[c] receives the relative residual estimate of
+  // right-hand side c.  Returns false when m blocks are stored or the
+  // bandwidth exceeds bwmax.
+  bool add_block(const cdouble* h, int nrows_h, const cdouble* R, double* est) {
     if (k >= m) return false;
     const int j = k;
-    const size_t rows = size_t(j + 2) * s;
+    const int b = nrows_h - j;
+    if (b < 1 || b > bwmax) return false;
+    bw[size_t(j)] = b;
+    const size_t rows = size_t(nrows_h + 1) * s, hr = size_t(nrows_h) * s;
     std::vector<cdouble> col(rows * s);
     for (int c = 0; c < s; ++c) {
       cdouble* x = &col[size_t(c) * rows];
-      for (size_t i = 0; i < size_t(j + 1) * s; ++i) x[i] = h[size_t(c) * (j + 1) * s + i];
-      for (int i = 0; i < s; ++i) x[size_t(j + 1) * s + i] = R[size_t(c) * s + i];
+      for (size_t i = 0; i < hr; ++i) x[i] = h[size_t(c) * hr + i];
+      for (int i = 0; i < s; ++i) x[hr + i] = R[size_t(c) * s + i];
     }
     // earlier reflectors, column by column (independent columns)
-    const long work = long(j) * s * (s + 1) * s;
+    const long work = long(j) * s * (2 * s) * s;
     parallel_for(s, work > 200000 ? threads : 1, [&](int c) {
       cdouble* x = &col[size_t(c) * rows];
       for (int q = 0; q < j; ++q)
         for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, x);
     });
-    // reflectors of this block: column kk, support top rows kk..s-1 and bottom rows 0..kk
+    // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1
     for (int kk = 0; kk < s; ++kk) {
-      cdouble* x = &col[size_t(kk) * rows];
-      cdouble* v = &refl[(size_t(j) * s + kk) * (s + 1)];
-      const int nt = s - kk;
+      cdouble* x = &col[size_t(kk) * rows] + size_t(j) * s + kk;
+      cdouble* v = &refl[(size_t(j) * s + kk) * (1 + bwmax) * s];
+      const int len = s - kk + b * s;
       double nrm2 = 0;
-      for (int t = 0; t < nt; ++t) nrm2 += std::norm(x[size_t(j) * s + kk + t]);
-      for (int t = 0; t <= kk; ++t) nrm2 += std::norm(x[size_t(j + 1) * s + t]);
+      for (int t = 0; t < len; ++t) nrm2 += std::norm(x[t]);
       const double nrm = std::sqrt(nrm2);
-      const cdouble x0 = x[size_t(j) * s + kk];
       if (nrm == 0.0) {
         beta[size_t(j) * s + kk] = 0.0;
         continue;
       }
+      const cdouble x0 = x[0];
       const double ax0 = std::abs(x0);
       const cdouble ph = ax0 > 0 ? x0 / ax0 : cdouble(1.0);
       const cdouble alpha = -ph * nrm;  // x -> alpha e_0
-      for (int t = 0; t < nt; ++t) v[t] = x[size_t(j) * s + kk + t];
-      for (int t = 0; t <= kk; ++t) v[nt + t] = x[size_t(j + 1) * s + t];
+      for (int t = 0; t < len; ++t) v[t] = x[t];
+      for (int t = len; t < (1 + bwmax) * s; ++t) v[t] = 0;
       v[0] -= alpha;
       double vn2 = 0;
-      for (int t = 0; t <= s; ++t) vn2 += std::norm(v[t]);
+      for (int t = 0; t < len; ++t) vn2 += std::norm(v[t]);
       beta[size_t(j) * s + kk] = vn2 > 0 ? 2.0 / vn2 : 0.0;
       for (int c = kk; c < s; ++c) apply_reflector(j, kk, &col[size_t(c) * rows]);
     }
@@ -193,14 +230,12 @@ struct BlockLSQ {
     Rt.resize(Rt.size() + size_t(j + 1) * s * s);
     for (int c = 0; c < s; ++c)
       for (size_t i = 0; i < size_t(j + 1) * s; ++i) Rt[off[size_t(j)] + size_t(c) * (j + 1) * s + i] = col[size_t(c) * rows + i];
-    // the least-squares right-hand side
-    const size_t ldg = size_t(m + 1) * s;
     for (int c = 0; c < s; ++c)
       for (int kk = 0; kk < s; ++kk) apply_reflector(j, kk, &g[size_t(c) * ldg]);
     ++k;
     for (int c = 0; c < s; ++c) {
       double r2 = 0;
-      for (int i = 0; i < s; ++i) r2 += std::norm(g[size_t(c) * ldg + size_t(k) * s + i]);
+      for (int i = 0; i < b * s; ++i) r2 += std::norm(g[size_t(c) * ldg + size_t(k) * s + i]);
       est[c] = std::sqrt(r2) / bnorm[c];
     }
     return true;
@@ -215,7 +250,6 @@ struct BlockLSQ {
     double dmax = 0;
     for (size_t i = 0; i < n; ++i) dmax = std::max(dmax, std::abs(diag(i)));
     const double eps = 1e-13 * dmax;
-    const size_t ldg = size_t(m + 1) * s;
     parallel_for(s, n * n * s > 4000000 ? threads : 1, [&](int c) {
       cdouble* y = &Y[size_t(c) * n];
       for (size_t i = 0; i < n; ++i) y[i] = g[size_t(c) * ldg + i];

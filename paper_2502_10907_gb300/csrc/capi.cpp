@@ -190,6 +190,13 @@ mtf_status mtf_profile_read(int32_t n, int64_t* launches, double* ms) {
   });
 }
 
+mtf_status mtf_profile_read_bytes(int32_t n, int64_t* launches, double* ms, double* bytes) {
+  return guarded([&] {
+    MTF_REQUIRE(n >= 0, MTF_ERR_ARG, "n must be >= 0");
+    prof_read(n, launches, ms, bytes);
+  });
+}
+
 int32_t mtf_kernel_count(void) { return KID_COUNT; }
 
 const char* mtf_kernel_name(int32_t id) { return kernel_name(id); }

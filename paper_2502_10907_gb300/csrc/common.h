@@ -235,7 +235,10 @@ enum KernelId {
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
 void prof_enable(bool on);
-void prof_read(int n, int64_t* launches, double* ms);
+void prof_read(int n, int64_t* launches, double* ms, double* bytes = nullptr);
+// algorithmic bytes of a launch (each stored operator entry, input and
+// output value counted once), summed per kernel id for the roofline
+void prof_bytes(int kid, double b);
 const char* kernel_name(int kid);
 // launch a kernel with accounting: LAUNCH(kid, stream, kernel<<<...>>>(args))
 #define MTF_LAUNCH(kid, stream, ...)          \
@@ -357,14 +360,23 @@ void destroy_tc(TcMatvec* t);
 void tc_build_operator(mtf_system sys, cudaStream_t s);
 bool tc_matvec_enabled(mtf_system sys);
 void launch_matvec_tc(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs, cudaStream_t s);
+// block-OSRC on the tensor cores from the FP16 T~ (mv_tc.cu)
+// (ld16: per block, the row stride of the FP16 T~ copy in entries)
+void tc_build_osrc(mtf_system sys, const std::vector<int64_t>& ld16, cudaStream_t s);
+bool tc_osrc_enabled(mtf_system sys);
+void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
+                          cudaStream_t s);
 // One block flexible GMRES cycle of the mixed path on M D = R from D = 0 for
 // the s right-hand sides together (block32.cu): one Krylov space of blocks of
 // s vectors, FP32 basis, FP64 Hessenberg sums; x += D.  Stops when every
 // right-hand side's estimate reaches tol relative to its ||r|| (reached =
 // true), after opt.restart block steps, after max_iter block steps or when
-// every direction is deflated; iters[c] += block steps.
+// every direction is deflated; iters[c] += block steps.  cycle: index of the
+// cycle within the solve; with opt.recycle a later cycle continues the space
+// of the previous ones (its new residual projected on it) while there is
+// room in the restart length.
 mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t st);
+                          std::vector<int>& iters, bool& reached, cudaStream_t st, int cycle);
 void destroy_learned(LearnedState* l);
 // learned OSRC correction (learned.cu)
 int64_t learned_param_count(mtf_system sys);

@@ -34,6 +34,7 @@
 #include "common.h"
 #include "tc.cuh"
 #include "tc_plan.h"
+#include "tc_stream.cuh"
 
 namespace mtf {
 
@@ -54,6 +55,14 @@ struct TcMatvec {
   const void* amap_ptr = nullptr;
   const void* bmap_ptr = nullptr;
   int bmap_nb = 0;
+  // block-OSRC on the tensor cores: the FP16 T~ in the same row tiles
+  // (one part), units {a_base, b_base, kc0, kc1} of the same plan
+  DevBuf<int4> units_ab;
+  DevBuf<__half> Aos;
+  DevBuf<int64_t> os_off, os_ld;       // per block: first entry and row stride of the FP16 T~
+  CUtensorMap osmap{};
+  const void* osmap_ptr = nullptr;
+  bool os_built = false;
 };
 
 void destroy_tc(TcMatvec* t) { delete t; }
@@ -123,6 +132,65 @@ __global__ void __launch_bounds__(256) k_tc_tile_a(const float4* __restrict__ TK
 #pragma unroll
   for (int p = 0; p < 4; ++p)
     *reinterpret_cast<uint4*>(A + tc_a_index(tile, p, row, 8 * g)) = *reinterpret_cast<const uint4*>(h[p]);
+}
+
+// FP16 T~ tiles (one part): thread = (tile, row, group g of 4 complex
+// columns); entries of block i at off[i] + r ld[i] + n as (re, im) halves
+__global__ void __launch_bounds__(256) k_tc_tile_os(const __half2* __restrict__ T16, const int4* __restrict__ tile_info,
+                                                    const int64_t* __restrict__ off, const int64_t* __restrict__ ld,
+                                                    const int32_t* __restrict__ blk_N, int64_t n_tiles,
+                                                    __half* __restrict__ A) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_tiles * kTcRows * 8) return;
+  const int64_t tile = t / (kTcRows * 8);
+  const int row = int((t / 8) % kTcRows), g = int(t % 8);
+  const int4 info = tile_info[tile];
+  const int i = info.x, N = blk_N[i];
+  const int r = info.y * kTcRows + row;
+  __half2 h[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int n = info.z * kTcCols + 4 * g + q;
+    h[q] = (r < N && n < N) ? T16[off[i] + int64_t(r) * ld[i] + n] : __floats2half2_rn(0.f, 0.f);
+  }
+  *reinterpret_cast<uint4*>(A + tc_tile_index(tile, 1, 0, row, 8 * g)) = *reinterpret_cast<const uint4*>(h);
+}
+
+// z rows of the block-OSRC apply (one warp per global row, lane = right-hand
+// side): the row's pieces of T~ r_D and T~ r_N summed in order and unscaled,
+// then z_D = rho^-1 T~ r_N, z_N = -rho T~ r_D with the per-block coefficients
+// of the FP16 copy (s_i rho, s_i / rho)
+template <int NB>
+__global__ void __launch_bounds__(256) k_os_tc_combine(
+    const float* __restrict__ part, const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_N,
+    const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const int* __restrict__ blk_unit_base,
+    const int* __restrict__ blk_pieces, const unsigned* __restrict__ colmax, const float* __restrict__ cf,
+    float* __restrict__ z, int64_t ldz, int c0, int nc, int64_t n_rows) {
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows || lane >= nc) return;
+  const int i = row_blk[row];
+  const int N = blk_N[i];
+  const int64_t m = row - blk_row_off[i];
+  const int P = blk_pieces[i];
+  const int64_t u0 = blk_unit_base[i] + (m >> 7) * P;
+  const int lr = int(m & 127);
+  float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int p = 0; p < P; ++p) {
+    const float4 a = *reinterpret_cast<const float4*>(part + (size_t(u0 + p) * kTcRows + lr) * NB + 4 * lane);
+    t.x += a.x;
+    t.y += a.y;
+    t.z += a.z;
+    t.w += a.w;
+  }
+  const float sc = tcs_inv_scale(colmax[lane]);
+  const float a0 = t.x * sc, a1 = t.y * sc, a2 = t.z * sc, a3 = t.w * sc;  // T~ r_D, T~ r_N
+  const float rr = cf[4 * i], ri = cf[4 * i + 1], ir = cf[4 * i + 2], ii = cf[4 * i + 3];
+  float* zc = z + 2 * (int64_t(c0 + lane) * ldz + blk_dof_off[i]);
+  zc[2 * m] = ir * a2 - ii * a3;
+  zc[2 * m + 1] = ir * a3 + ii * a2;
+  zc[2 * (N + m)] = -(rr * a0 - ri * a1);
+  zc[2 * (N + m) + 1] = -(rr * a1 + ri * a0);
 }
 
 // colmax[c] = max |re|, |im| of input column c0 + c (n complex entries)
@@ -409,7 +477,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 4-D FP16 map {64, rows, parts, count} over contiguous boxes of
 // rows x parts x 128 bytes, loaded whole with the 128-byte swizzle
-static void encode_map(CUtensorMap* m, const void* base, int rows, int parts, int64_t count) {
+void tc_encode_map(void* map, const void* base, int rows, int parts, int64_t count) {
+  CUtensorMap* m = static_cast<CUtensorMap*>(map);
   MTF_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && count > 0 && count < (int64_t(1) << 31), MTF_ERR_ARG,
               "tensor map base must be 16-byte aligned");
   const cuuint64_t dims[4] = {64, cuuint64_t(rows), cuuint64_t(parts), cuuint64_t(count)};
@@ -458,6 +527,14 @@ static void tc_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
     for (int kc = 0; kc < b.n_kc; ++kc) cinfo[size_t(b.chunk_base + kc)] = make_int2(i, kc);
   }
   upload_vec(t.units, units, s);
+  std::vector<int4> uab(p.units.size());
+  for (size_t u = 0; u < p.units.size(); ++u) {
+    const TcBlock& b = p.blocks[size_t(p.units[u].blk)];
+    uab[u] = make_int4(int(b.tile_base + int64_t(p.units[u].mt) * b.n_kc), int(b.chunk_base), p.units[u].kc0,
+                       p.units[u].kc1);
+  }
+  MTF_REQUIRE(p.n_tiles < (int64_t(1) << 31), MTF_ERR_MESH, "mesh too large for the tensor-core tables");
+  upload_vec(t.units_ab, uab, s);
   upload_vec(t.tile_info, tinfo, s);
   upload_vec(t.chunk_info, cinfo, s);
   upload_vec(t.sched, p.sched, s);
@@ -498,16 +575,17 @@ void tc_build_operator(mtf_system sys, cudaStream_t s) {
       reinterpret_cast<const float4*>(sys->d_TK32.p), t.tile_info.p, m->d_blk_mat_off.p, m->d_blk_N.p, t.amax.p,
       t.plan.n_tiles, t.A.p));
   if (t.amap_ptr != t.A.p) {
-    encode_map(&t.amap, t.A.p, kTcRows, kTcParts, t.plan.n_tiles);
+    tc_encode_map(&t.amap, t.A.p, kTcRows, kTcParts, t.plan.n_tiles);
     t.amap_ptr = t.A.p;
   }
   t.built = true;
 }
 
+// input chunks (hi, lo) of columns c0 .. c0 + nc - 1 of x in t.B, their
+// scales in t.colmax, and the B tensor map for width NB
 template <int NB>
-static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx, float* y, int64_t ldy, int c0, int nc,
-                       cudaStream_t s) {
-  using Cfg = TcCfg<NB>;
+static void tc_build_inputs(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx, int c0, int nc, int kid,
+                            cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   const TcPlan& p = t.plan;
   const size_t bh = size_t(p.n_chunks) * 2 * NB * 64;
@@ -516,17 +594,25 @@ static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx,
     t.bmap_ptr = nullptr;
   }
   if (t.bmap_ptr != t.B.p || t.bmap_nb != NB) {
-    encode_map(&t.bmap, t.B.p, NB, 2, p.n_chunks);
+    tc_encode_map(&t.bmap, t.B.p, NB, 2, p.n_chunks);
     t.bmap_ptr = t.B.p;
     t.bmap_nb = NB;
   }
   const size_t np = p.units.size() * kTcRows * 2 * NB;
   if (t.part.n < np) t.part.alloc(size_t(p.units.size()) * kTcRows * 2 * 128);
   MTF_CUDA(cudaMemsetAsync(t.colmax.p, 0, 32 * sizeof(unsigned), s));
-  MTF_LAUNCH(KID_MVTC_PREP, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(x, ldx, m->n_total, c0, t.colmax.p));
+  MTF_LAUNCH(kid, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(x, ldx, m->n_total, c0, t.colmax.p));
   const int64_t nthr = p.n_chunks * NB * 8;
-  MTF_LAUNCH(KID_MVTC_PREP, s, k_tc_build_b<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(kid, s, k_tc_build_b<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
       x, ldx, c0, nc, NB, t.chunk_info.p, p.n_chunks, m->d_blk_N.p, m->d_blk_dof_off.p, t.colmax.p, t.B.p));
+}
+
+template <int NB>
+static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx, float* y, int64_t ldy, int c0, int nc,
+                       cudaStream_t s) {
+  using Cfg = TcCfg<NB>;
+  mtf_mesh m = sys->mesh;
+  tc_build_inputs<NB>(sys, t, x, ldx, c0, nc, KID_MVTC_PREP, s);
   static std::atomic<uint64_t> opted{0};
   int dev = 0;
   MTF_CUDA(cudaGetDevice(&dev));
@@ -536,6 +622,9 @@ static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx,
     opted.fetch_or(bit);
   }
   stream_prepare(sys, s);
+  // every stored {T, K} entry once (16 bytes: FP16 hi + lo of four reals)
+  // and the pass's FP16 hi + lo input chunks once
+  prof_bytes(KID_MVTC, double(m->n_mat) * 16.0 + double(m->n_total) * nc * 8.0);
   MTF_LAUNCH(KID_MVTC, s, k_mv_tc<NB><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.amap, t.bmap, t.units.p, t.sched.p, t.sched_off.p, t.blk_tile_base.p, t.blk_nkc.p, t.blk_chunk_base.p,
       t.part.p, sys->d_mv_ctl.p + 2));
@@ -543,6 +632,83 @@ static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx,
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.amax.p, t.colmax.p, m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, x, ldx, y, ldy, c0, nc,
       m->n_rows));
+}
+
+// FP16 T~ tiles of the block-OSRC apply, rebuilt from the FP16 copy of T~
+// (osrc.cu) after every assembly
+void tc_build_osrc(mtf_system sys, const std::vector<int64_t>& ld16, cudaStream_t s) {
+  if (!sys->opt.mv_tensor || sys->opt.precision != MTF_PREC_MIXED || !sys->d_osrc_T16.p) return;
+  if (!sys->tc) sys->tc = new TcMatvec();
+  TcMatvec& t = *sys->tc;
+  mtf_mesh m = sys->mesh;
+  tc_plan_tables(sys, t, s);
+  upload_vec(t.os_off, m->os16_off_h, s);
+  upload_vec(t.os_ld, ld16, s);
+  const size_t nh = size_t(t.plan.n_tiles) * kTcRows * 64;
+  if (t.Aos.n != nh) {
+    t.Aos.alloc(nh);
+    t.osmap_ptr = nullptr;
+  }
+  const int64_t nthr = t.plan.n_tiles * kTcRows * 8;
+  MTF_LAUNCH(KID_TC_TILE, s, k_tc_tile_os<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const __half2*>(sys->d_osrc_T16.p), t.tile_info.p, t.os_off.p, t.os_ld.p, m->d_blk_N.p,
+      t.plan.n_tiles, t.Aos.p));
+  if (t.osmap_ptr != t.Aos.p) {
+    tc_encode_map(&t.osmap, t.Aos.p, kTcRows, 1, t.plan.n_tiles);
+    t.osmap_ptr = t.Aos.p;
+  }
+  MTF_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+  t.os_built = true;
+}
+
+bool tc_osrc_enabled(mtf_system sys) {
+  return sys->opt.precision == MTF_PREC_MIXED && sys->opt.mv_tensor && sys->opt.osrc_half && sys->tc &&
+         sys->tc->os_built;
+}
+
+template <int NB>
+static void os_tc_pass(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr, float* z, int64_t ldz, int c0, int nc,
+                       cudaStream_t s) {
+  using Cfg = TcsCfg<1, NB>;
+  mtf_mesh m = sys->mesh;
+  tc_build_inputs<NB>(sys, t, r, ldr, c0, nc, KID_OSRC, s);
+  static std::atomic<uint64_t> opted{0};
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(opted.load() & bit)) {
+    MTF_CUDA(cudaFuncSetAttribute(k_tc_stream<1, NB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem)));
+    opted.fetch_or(bit);
+  }
+  stream_prepare(sys, s);
+  // every stored FP16 T~ entry once and the pass's inputs once
+  prof_bytes(KID_OSRC, double(m->n_mat) * 4.0 + double(m->n_total) * nc * 8.0);
+  TcUnits units;
+  units.list = t.units_ab.p;
+  MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
+      t.osmap, t.bmap, units, int(t.plan.units.size()), t.sched.p, t.sched_off.p, t.part.p, nullptr, 0, 0, 0, nullptr,
+      sys->d_mv_ctl.p + 2));
+  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_tc_combine<NB><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+      t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
+      t.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
+}
+
+// z = A~ r (block-OSRC, Eq. 19) with the FP16 T~ on the tensor cores, in
+// passes of up to 32 right-hand sides (FP32 in and out)
+void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
+                          cudaStream_t s) {
+  MTF_REQUIRE(tc_osrc_enabled(sys), MTF_ERR_ARG, "tensor-core block-OSRC not built for this system");
+  TcMatvec& t = *sys->tc;
+  MTF_REQUIRE((reinterpret_cast<uintptr_t>(r) & 15) == 0 && (ldr & 1) == 0, MTF_ERR_ARG,
+              "tensor-core block-OSRC input columns must be 16-byte aligned");
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int nc = std::min(32, nrhs - c0);
+    const int nb = tc_nb(nc);
+    if (nb == 16) os_tc_pass<16>(sys, t, r, ldr, z, ldz, c0, nc, s);
+    else if (nb == 32) os_tc_pass<32>(sys, t, r, ldr, z, ldz, c0, nc, s);
+    else if (nb == 64) os_tc_pass<64>(sys, t, r, ldr, z, ldz, c0, nc, s);
+    else os_tc_pass<128>(sys, t, r, ldr, z, ldz, c0, nc, s);
+  }
 }
 
 // y = M x (FP32 in and out) on the tensor cores, in passes of up to 32

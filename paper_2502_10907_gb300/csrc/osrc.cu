@@ -534,6 +534,9 @@ static void osrc_half_copy(mtf_system sys, cudaStream_t s) {
     cf[size_t(4 * i + 3)] = float(-sc * ri / rn);
   }
   sys->d_os_coef16.upload(cf, s);
+  std::vector<int64_t> ld16(static_cast<size_t>(m->nd));
+  for (int i = 0; i < m->nd; ++i) ld16[size_t(i)] = st_row_stride<3>(m->blk[i].N);
+  tc_build_osrc(sys, ld16, s);
   if (MTF_OSRC_TC) {
     // the tensor-core stream reads one contiguous run per unit
     const StreamUnits& su = ensure_os_units<3>(sys, s);
@@ -667,6 +670,10 @@ template <class ZT, bool ADJ = false>
 static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
   stream_prepare(sys, s);
   if constexpr (sizeof(ZT) == 4) {
+    if (!ADJ && tc_osrc_enabled(sys)) {
+      launch_osrc_apply_tc(sys, r32, ldr, z, ldz, nrhs, s);
+      return;
+    }
     if (sys->opt.osrc_half) {
       osrc_stream_ent<ZT, ADJ, 3>(sys, r32, ldr, z, ldz, nrhs, s);
       return;

@@ -18,6 +18,7 @@ struct Prof {
   bool on = false;
   int64_t launches[KID_COUNT] = {};
   double ms[KID_COUNT] = {};
+  double bytes[KID_COUNT] = {};  // algorithmic bytes declared by the launch sites
   struct Rec {
     int kid;
     cudaEvent_t a, b;
@@ -70,13 +71,17 @@ void prof_enable(bool on) {
   g_prof.on = on;
 }
 
-void prof_read(int n, int64_t* launches, double* ms) {
+void prof_bytes(int kid, double b) { g_prof.bytes[kid] += b; }
+
+void prof_read(int n, int64_t* launches, double* ms, double* bytes) {
   resolve();
   for (int k = 0; k < n && k < KID_COUNT; ++k) {
     if (launches) launches[k] = g_prof.launches[k];
     if (ms) ms[k] = g_prof.ms[k];
+    if (bytes) bytes[k] = g_prof.bytes[k];
     g_prof.launches[k] = 0;
     g_prof.ms[k] = 0;
+    g_prof.bytes[k] = 0;
   }
 }
 

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <complex>
 
 #include "common.h"
@@ -510,6 +511,14 @@ static mtf_status gmres_core(mtf_system sys, int nrhs, const double* b_dev, doub
   return status;
 }
 
+// Fewest right-hand sides for which the block cycle is used.  With 2 waves
+// of one incidence direction (the split sphere) the block space needed as
+// many steps as each single space (437 against 440) and its per-step host
+// synchronisation made the solve slower; with 16 waves of 8 directions (the
+// 4 x 4 x 4 cube) it needed 838 block steps where single spaces needed
+// about 6,000 iterations.
+constexpr int kBlockMinRhs = 4;
+
 __global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int64_t n2) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n2) x[t] += d[t];
@@ -595,13 +604,14 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       for (int c = 0; c < nrhs; ++c)
         if (rel[c] <= sys->opt.tol)
           MTF_CUDA(cudaMemsetAsync(G.b.p + 2 * size_t(c) * n, 0, size_t(n) * 2 * sizeof(double), s));
-      const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
+      const double inner_min = std::getenv("MTF_INNER_MIN") ? std::atof(std::getenv("MTF_INNER_MIN")) : 1e-5;
+      const double inner_tol = std::min(0.5, std::max(inner_min, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
       bool reached = false;
       // systems with a learned correction keep the per-rhs spaces, so that
       // their plain and corrected solves compare like for like
-      if (sys->opt.block_krylov && nrhs > 1 && !sys->learned)
-        status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s);
+      if (sys->opt.block_krylov && nrhs >= kBlockMinRhs && !sys->learned)
+        status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
       else
         status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
       if (status != MTF_OK) break;

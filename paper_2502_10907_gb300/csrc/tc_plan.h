@@ -43,14 +43,39 @@ constexpr int64_t kTcTileHalves = kTcParts * kTcPartHalves;
 // to one of the kernel's widths 16, 32, 64, 128
 inline int tc_nb(int nc) { return nc <= 4 ? 16 : nc <= 8 ? 32 : nc <= 16 ? 64 : 128; }
 
-// half index of (tile, part, row, e) in the tiled operator, e in 0..63
-// (constexpr: usable in device code)
+// half index of (tile, part, row, e) in tiles of `parts` parts of 128 rows
+// x 64 FP16 (constexpr: usable in device code)
+constexpr int64_t tc_tile_index(int64_t tile, int parts, int part, int row, int e) {
+  return ((tile * parts + part) * kTcRows + row) * 64 + e;
+}
+// the matvec's operator tiles (4 parts: T hi, T lo, K hi, K lo)
 constexpr int64_t tc_a_index(int64_t tile, int part, int row, int e) {
-  return ((tile * kTcParts + part) * kTcRows + row) * 64 + e;
+  return tc_tile_index(tile, kTcParts, part, row, e);
 }
 // half index of (chunk, part 0 hi / 1 lo, column, e) in the input chunks
 constexpr int64_t tc_b_index(int64_t chunk, int part, int col, int e, int nb) {
   return ((chunk * 2 + part) * nb + col) * 64 + e;
+}
+
+// Tiled FP16 hi / lo copies of a Krylov basis (2-part tiles), the layouts of
+// the tensor-core Gram-Schmidt projections (arnoldi_tc.cu), for basis vector
+// qq and entry k:
+//  - dots copy: tile (qq / 128) nkc + k / 32, row qq % 128, halves 2 (k % 32) + {0, 1};
+//  - update copy: tile (k / 128) nbc + qq / 32, row k % 128, halves 2 (qq % 32) + {0, 1};
+// with nkc = ldn / 32 entry chunks and nbc = ceil(nvec / 32) basis chunks.
+// Returned as the half index of the real part (the imaginary part follows).
+constexpr int64_t tca_dots_half(int64_t qq, int64_t k, int64_t nkc, int part) {
+  return tc_tile_index((qq / kTcRows) * nkc + k / kTcCols, 2, part, int(qq % kTcRows), int(2 * (k % kTcCols)));
+}
+constexpr int64_t tca_upd_half(int64_t qq, int64_t k, int64_t nbc, int part) {
+  return tc_tile_index((k / kTcRows) * nbc + qq / 32, 2, part, int(k % kTcRows), int(2 * (qq % 32)));
+}
+// halves of the two copies for nvec basis vectors of padded length ldn
+constexpr int64_t tca_dots_halves(int64_t nvec, int64_t ldn) {
+  return ((nvec + kTcRows - 1) / kTcRows) * (ldn / kTcCols) * 2 * kTcRows * 64;
+}
+constexpr int64_t tca_upd_halves(int64_t nvec, int64_t ldn) {
+  return ((ldn + kTcRows - 1) / kTcRows) * ((nvec + 31) / 32) * 2 * kTcRows * 64;
 }
 
 struct TcBlock {
@@ -73,8 +98,9 @@ struct TcPlan {
 
 // Pieces of at most piece_len chunks per (block, row tile), piece_len chosen
 // so that there are at least `waves` units per CTA on average (but no piece
-// shorter than min_len chunks); LPT schedule over n_cta CTAs.
-inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int waves = 4, int min_len = 8) {
+// shorter than min_len chunks; 0 selects the defaults below); LPT schedule
+// over n_cta CTAs.
+inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int waves = 0, int min_len = 0) {
   if (n_cta < 1) return "plan_tc: no CTAs";
   p = TcPlan{};
   p.blocks.resize(Ns.size());
@@ -88,6 +114,11 @@ inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int
     total_chunks += int64_t(b.n_mt) * b.n_kc;
     n_tiles_rows += b.n_mt;
   }
+  // defaults: long pieces (few row pieces for the combine to add) when every
+  // CTA has many chunks, short ones (balance) when it has few
+  const bool big = total_chunks >= int64_t(64) * n_cta;
+  if (waves <= 0) waves = big ? 4 : 8;
+  if (min_len <= 0) min_len = big ? 8 : 2;
   // longest piece that still gives `waves` units per CTA
   int64_t target = std::max<int64_t>(int64_t(min_len), total_chunks / std::max<int64_t>(1, int64_t(waves) * n_cta));
   int64_t tile = 0, chunk = 0;

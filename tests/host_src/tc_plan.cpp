@@ -8,7 +8,11 @@
 //     power-of-two scaling, the inputs packed into chunks in the two real
 //     column forms, the products emulated as the tensor cores form them
 //     (FP16 operands, hi*hi + hi*lo + lo*hi per chunk) and unscaled give
-//     T u and K u to about 2^-22 of the exact complex products.
+//     T u and K u to about 2^-22 of the exact complex products;
+//  3. the two tiled basis copies of the tensor-core Gram-Schmidt projections:
+//     every (vector, entry, part) of the basis sizes used maps inside the
+//     allocation (the stores write 8 halves from a multiple-of-4 entry), and
+//     on a small basis the map is one to one.
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -138,8 +142,48 @@ static int check_formulation() {
   return rel < 1e-6 ? 0 : 1;
 }
 
+static int check_basis_layout() {
+  struct Case { int64_t ldn, nvec; };
+  const Case cases[] = {{2880, 501 * 16}, {72000, 601 * 16}, {13120, 501 * 2}, {35008, 201 * 64}, {64, 3}};
+  for (const Case& c : cases) {
+    const int64_t nkc = c.ldn / mtf::kTcCols, nbc = (c.nvec + 31) / 32;
+    const int64_t nd = mtf::tca_dots_halves(c.nvec, c.ldn), nu = mtf::tca_upd_halves(c.nvec, c.ldn);
+    const int64_t qs[] = {0, 1, 31, 32, 127, 128, c.nvec - 2, c.nvec - 1};
+    for (int64_t qq : qs) {
+      if (qq < 0 || qq >= c.nvec) continue;
+      for (int64_t k = 0; k < c.ldn; ++k)
+        for (int part = 0; part < 2; ++part) {
+          const int64_t d = mtf::tca_dots_half(qq, k & ~int64_t(3), nkc, part) + 7;
+          const int64_t u = mtf::tca_upd_half(qq, k, nbc, part) + 1;
+          if (d >= nd || u >= nu) {
+            std::printf("basis layout: out of range (ldn %lld nvec %lld qq %lld k %lld)\n", (long long)c.ldn,
+                        (long long)c.nvec, (long long)qq, (long long)k);
+            return 1;
+          }
+        }
+    }
+  }
+  // one to one on a small basis
+  const int64_t ldn = 128, nvec = 64, nkc = ldn / mtf::kTcCols, nbc = (nvec + 31) / 32;
+  std::vector<int> hd(size_t(mtf::tca_dots_halves(nvec, ldn)), 0), hu(size_t(mtf::tca_upd_halves(nvec, ldn)), 0);
+  for (int64_t qq = 0; qq < nvec; ++qq)
+    for (int64_t k = 0; k < ldn; ++k)
+      for (int part = 0; part < 2; ++part)
+        for (int ri = 0; ri < 2; ++ri) {
+          ++hd[size_t(mtf::tca_dots_half(qq, k, nkc, part) + ri)];
+          ++hu[size_t(mtf::tca_upd_half(qq, k, nbc, part) + ri)];
+        }
+  for (int v : hd)
+    if (v > 1) return std::printf("basis layout: dots copy not one to one\n"), 1;
+  for (int v : hu)
+    if (v > 1) return std::printf("basis layout: update copy not one to one\n"), 1;
+  std::printf("basis layout: in range for all cases, one to one on the small basis\n");
+  return 0;
+}
+
 int main() {
   int f = 0;
+  f += check_basis_layout();
   std::vector<int> cube4(65, 450);
   cube4[0] = 7200;
   f += check_plan(cube4, 152);

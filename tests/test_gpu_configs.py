@@ -13,8 +13,11 @@ C-ABI, against the oracle's LU solution of the same discrete system.
   in the same mixed-precision batch (the Gram-Schmidt step of a column whose
   residual is zero).
 
+* The same cube partition at the benchmark's size: sampled full rows of the
+  FP64 blocks and of M x, and of the mixed system's tensor-core matvec.
+
 Bounds as in the rest of the suite: 1e-10 for the FP64 path, 1e-5 for the
-mixed path (solution and far field)."""
+mixed path (solution, far field and matvec rows)."""
 import numpy as np
 import pytest
 import torch
@@ -124,3 +127,39 @@ def test_osrc_apply_on_genus_one_boundary_matches_oracle(api, oracle_cache):
     s32 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, precision=1)
     z32 = s32.precond_f32(torch.from_numpy(r.astype(np.complex64)).cuda()).cpu().numpy()
     assert rel(z32, zr) < 1e-3, rel(z32, zr)
+
+
+def test_full_size_cube4_sampled_rows(api):
+    """The 4 x 4 x 4 cube partition at the benchmark's size (65 blocks,
+    72,000 unknowns) in the benchmark's launch configuration (16 right-hand
+    sides): sampled full rows of T_i and K_i of the FP64 assembly (the
+    operator of the benchmark's FP64 reference solution) and sampled rows of
+    M x against the oracle, and the same rows of the mixed system's
+    tensor-core matvec at the mixed bound."""
+    from oracle.operators import block_rows, transmission_gram
+    cfg = mi.config_cube4()
+    sk = skeleton_of(cfg["mesh"])
+    ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"], assemble=False)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    s32 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((16, sk.n_total)) + 1j * rng.standard_normal((16, sk.n_total))
+    y = s64.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    y32 = s32.matvec_f32(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    for i in (0, 1, 22, 64):
+        rows = np.sort(rng.choice(sk.N[i], 3, replace=False))
+        Tr, Kr = block_rows(sk, i, ref.k[i], rows)
+        T, K = (t.cpu().numpy()[rows] for t in s64.block(i))
+        assert rel(T, Tr) < TOL and rel(K, Kr) < TOL, (i, rel(T, Tr), rel(K, Kr))
+        Di, Ni = sk.block_slices(i)
+        r = ref.rho[i]
+        yD = 2 * (Kr @ x[:, Di].T + (Tr @ x[:, Ni].T) / r)
+        yN = 2 * (-r * (Tr @ x[:, Di].T) + Kr @ x[:, Ni].T)
+        for j in sk.Lambda[i]:
+            Gij = transmission_gram(sk, i, j)[rows]
+            Dj, Nj = sk.block_slices(j)
+            yD += Gij @ x[:, Dj].T
+            yN += Gij @ x[:, Nj].T
+        assert rel(y[:, Di][:, rows], yD.T) < TOL and rel(y[:, Ni][:, rows], yN.T) < TOL, i
+        assert rel(y32[:, Di][:, rows], yD.T) < MIXED_TOL and rel(y32[:, Ni][:, rows], yN.T) < MIXED_TOL, i

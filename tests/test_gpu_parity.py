@@ -356,19 +356,24 @@ def test_matvec_f32_full_size_sampled_rows(api):
 
 
 @pytest.mark.parametrize("name", ["sphere", "split", "uvodd"])
-def test_osrc_apply_f32_matches_oracle(api, oracle_cache, name):
+@pytest.mark.parametrize("nrhs", [5, 40])
+def test_osrc_apply_f32_matches_oracle(api, oracle_cache, name, nrhs):
     from oracle.osrc import BlockOSRC
     cfg, sk, ref = _case(oracle_cache, name)
     mesh = api.Mesh.from_inputs(cfg["mesh"])
     P = BlockOSRC(sk, ref.k, ref.rho)
-    r = _rand_c64(np.random.default_rng(12), (5, sk.n_total))
+    r = _rand_c64(np.random.default_rng(12), (nrhs, sk.n_total))
     zr = np.stack([P.apply(rr.astype(np.complex128)) for rr in r])
     # FP32 T~: FP32 storage and sums; FP16 copy: entries rounded to 11
-    # significant bits of the block's largest entry (2^-12 relative at most)
-    for half, tol in ((0, 1e-4), (1, 1e-3)):
-        sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, precision=1, osrc_half=half)
+    # significant bits of the block's largest entry (2^-12 relative at most),
+    # applied by the tensor cores (FP16 hi + lo inputs, up to 32 per pass) or
+    # by the mma.sync stream (FP16 inputs, 4 per pass)
+    for half, tensor, tol in ((0, 0, 1e-4), (1, 1, 1e-3), (1, 0, 1e-3)):
+        sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, precision=1, osrc_half=half,
+                          mv_tensor=tensor)
         z = sysg.precond_f32(torch.from_numpy(r).cuda()).cpu().numpy()
-        assert rel(z, zr) < tol, (half, rel(z, zr))
+        assert rel(z, zr) < tol, (half, tensor, rel(z, zr))
+        assert np.abs(z - zr).max() < tol * np.abs(zr).max(), (half, tensor)
 
 
 def test_f32_entries_reject_wrong_systems(api, oracle_cache):
