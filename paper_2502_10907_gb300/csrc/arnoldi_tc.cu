@@ -252,9 +252,9 @@ void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st) {
 // basis vectors q0 .. q0 + s - 1 (FP32 columns of stride ldn) into both copies
 void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st) {
   const int64_t n1 = t.ldn / 4 * t.s, n2 = t.ldn * t.s;
-  MTF_LAUNCH(KID_NORM, st, k_tca_store_dots<<<unsigned((n1 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nkc,
+  MTF_LAUNCH(KID_BSTORE, st, k_tca_store_dots<<<unsigned((n1 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nkc,
                                                                                         t.Vd.p));
-  MTF_LAUNCH(KID_NORM, st, k_tca_store_upd<<<unsigned((n2 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nbc,
+  MTF_LAUNCH(KID_BSTORE, st, k_tca_store_upd<<<unsigned((n2 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nbc,
                                                                                        t.Vu.p));
 }
 

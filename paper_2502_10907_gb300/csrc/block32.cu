@@ -289,26 +289,27 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
 // dropped (row k of R zero, kept[k] = 0) when its Schur pivot is not above
 // tau^2 ref_k, ref_k = the diagonal of Gpre (squared norms before the
 // Gram-Schmidt projections) or, with mask, 1 for mask[k] != 0 and 0
-// otherwise.  T = R_KK^-1 on the kept set K (zero elsewhere), so that
-// V = W T is orthonormal on K.  R and T complex FP64, column-major
-// (entry (i, c) at [c s + i]).  One CTA of 64 threads, s <= 64; the working
-// copy of G in shared memory (s * s complex).
-__global__ void __launch_bounds__(64) k_bchol(const double* __restrict__ G, const double* __restrict__ Gpre,
-                                              const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
-                                              double* __restrict__ T, int* __restrict__ kept) {
-  extern __shared__ double2 A[];  // A[c * s + i] = current Schur complement entry (i, c)
+// otherwise.  R complex FP64, column-major (entry (i, c) at [c s + i]).
+// One CTA of 256 threads, s <= 64: per pivot the row of R is formed in
+// parallel and the trailing upper triangle is updated by all threads (the
+// Schur complement and R in shared memory, s * s complex each).
+__global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, const double* __restrict__ Gpre,
+                                               const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
+                                               int* __restrict__ kept) {
+  extern __shared__ double2 sh[];
+  double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c
+  double2* Rs = sh + s * s;  // Rs[c * s + i] = R(i, c)
   __shared__ double piv;
   __shared__ int keep;
-  const int c = threadIdx.x;
-  if (c < s)
-    for (int i = 0; i < s; ++i) {
-      A[c * s + i] = make_double2(G[2 * (i * s + c)], G[2 * (i * s + c) + 1]);
-      R[2 * (c * s + i)] = 0.0;
-      R[2 * (c * s + i) + 1] = 0.0;
-    }
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < s * s; t += nt) {
+    const int c = t / s, i = t % s;
+    A[t] = make_double2(G[2 * (i * s + c)], G[2 * (i * s + c) + 1]);
+    Rs[t] = make_double2(0.0, 0.0);
+  }
   for (int k = 0; k < s; ++k) {
     __syncthreads();
-    if (c == 0) {
+    if (tid == 0) {
       const double d = A[k * s + k].x;
       const double ref = mask ? (mask[k] ? 1.0 : 0.0) : Gpre[2 * (k * s + k)];
       keep = (d > tau * tau * fmax(ref, 0.0) && d > 0.0) ? 1 : 0;
@@ -317,44 +318,67 @@ __global__ void __launch_bounds__(64) k_bchol(const double* __restrict__ G, cons
     }
     __syncthreads();
     if (!keep) continue;
-    if (c >= k && c < s) {
+    const double ip = 1.0 / piv;
+    for (int c = k + tid; c < s; c += nt) {
       const double2 a = A[c * s + k];
-      const double2 r = c == k ? make_double2(piv, 0.0) : make_double2(a.x / piv, a.y / piv);
-      R[2 * (c * s + k)] = r.x;
-      R[2 * (c * s + k) + 1] = r.y;
+      Rs[c * s + k] = c == k ? make_double2(piv, 0.0) : make_double2(a.x * ip, a.y * ip);
     }
     __syncthreads();
-    if (c > k && c < s) {
-      const double rkr = R[2 * (c * s + k)], rki = R[2 * (c * s + k) + 1];
-      for (int i = k + 1; i <= c; ++i) {
-        const double ar = R[2 * (i * s + k)], ai = -R[2 * (i * s + k) + 1];  // conj(R(k, i))
-        A[c * s + i].x -= ar * rkr - ai * rki;
-        A[c * s + i].y -= ar * rki + ai * rkr;
-      }
+    const int w = s - k - 1;
+    for (int t = tid; t < w * w; t += nt) {
+      const int i = k + 1 + t % w, c = k + 1 + t / w;
+      if (i > c) continue;
+      const double2 ri = Rs[i * s + k], rc = Rs[c * s + k];  // R(k, i), R(k, c)
+      A[c * s + i].x -= ri.x * rc.x + ri.y * rc.y;            // conj(R(k, i)) R(k, c)
+      A[c * s + i].y -= ri.x * rc.y - ri.y * rc.x;
     }
   }
   __syncthreads();
-  if (c >= s) return;
-  for (int i = 0; i < s; ++i) {
-    T[2 * (c * s + i)] = 0.0;
-    T[2 * (c * s + i) + 1] = 0.0;
+  for (int t = tid; t < s * s; t += nt) {
+    R[2 * t] = Rs[t].x;
+    R[2 * t + 1] = Rs[t].y;
   }
-  if (!kept[c]) return;
-  const double dq = R[2 * (c * s + c)];
-  T[2 * (c * s + c)] = 1.0 / dq;
-  for (int i = c - 1; i >= 0; --i) {
-    if (!kept[i]) continue;
-    double ar = 0, ai = 0;
-    for (int p = i + 1; p <= c; ++p) {
-      if (!kept[p]) continue;
-      const double rr = R[2 * (p * s + i)], ri = R[2 * (p * s + i) + 1];
-      const double tr = T[2 * (c * s + p)], ti = T[2 * (c * s + p) + 1];
-      ar += rr * tr - ri * ti;
-      ai += rr * ti + ri * tr;
+}
+
+// out_q[k] = (in_q[k] - sum_{p < q} out_p[k] R(p, q)) / R(q, q) for kept q,
+// 0 otherwise: V = W R^-1 on the kept set by forward substitution, entry by
+// entry (R complex FP64, column-major, used in FP32)
+template <int SC>
+__global__ void __launch_bounds__(128) k_btrsm(const float* __restrict__ in, int64_t ldi, const double* __restrict__ R,
+                                               const int* __restrict__ kept, int s, float* __restrict__ out, int64_t ldo,
+                                               int64_t n_pad) {
+  __shared__ float2 rs[SC][SC];  // rs[p][q] = R(p, q)
+  __shared__ float2 inv[SC];     // 1 / R(q, q), 0 for dropped q
+  for (int t = threadIdx.x; t < SC * SC; t += blockDim.x) {
+    const int p = t / SC, q = t % SC;
+    rs[p][q] = (p < s && q < s) ? make_float2(float(R[2 * (q * s + p)]), float(R[2 * (q * s + p) + 1]))
+                                : make_float2(0.f, 0.f);
+  }
+  for (int q = threadIdx.x; q < SC; q += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (q < s && kept[q]) {
+      const double a = R[2 * (q * s + q)], b = R[2 * (q * s + q) + 1], d = a * a + b * b;
+      v = make_float2(float(a / d), float(-b / d));
     }
-    const double d = R[2 * (i * s + i)];
-    T[2 * (c * s + i)] = -ar / d;
-    T[2 * (c * s + i) + 1] = -ai / d;
+    inv[q] = v;
+  }
+  __syncthreads();
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n_pad) return;
+  float2 v[SC];
+#pragma unroll
+  for (int q = 0; q < SC; ++q) {
+    if (q >= s) break;
+    float2 a = reinterpret_cast<const float2*>(in + 2 * int64_t(q) * ldi)[k];
+#pragma unroll
+    for (int p = 0; p < q; ++p) {
+      const float2 r = rs[p][q];
+      a.x -= v[p].x * r.x - v[p].y * r.y;
+      a.y -= v[p].x * r.y + v[p].y * r.x;
+    }
+    const float2 iv = inv[q];
+    v[q] = make_float2(a.x * iv.x - a.y * iv.y, a.x * iv.y + a.y * iv.x);
+    reinterpret_cast<float2*>(out + 2 * int64_t(q) * ldo)[k] = v[q];
   }
 }
 
@@ -429,7 +453,7 @@ static void bupdate(const float* V, int nq, int64_t ldv, const double* H, int ld
 static void bxform(const float* in, int64_t ldi, const double* T, int s, float* out, int64_t ldo, int64_t n_pad,
                    cudaStream_t st) {
   const unsigned g = nbk(n_pad, 128);
-#define MTF_BX(SCV) MTF_LAUNCH(KID_NORM, st, k_bxform<SCV><<<g, 128, 0, st>>>(in, ldi, T, s, out, ldo, n_pad))
+#define MTF_BX(SCV) MTF_LAUNCH(KID_BXFORM, st, k_bxform<SCV><<<g, 128, 0, st>>>(in, ldi, T, s, out, ldo, n_pad))
   if (s <= 1) MTF_BX(1);
   else if (s <= 2) MTF_BX(2);
   else if (s <= 4) MTF_BX(4);
@@ -438,6 +462,21 @@ static void bxform(const float* in, int64_t ldi, const double* T, int s, float* 
   else if (s <= 32) MTF_BX(32);
   else MTF_BX(64);
 #undef MTF_BX
+}
+
+static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept, int s, float* out, int64_t ldo,
+                  int64_t n_pad, cudaStream_t st) {
+  const unsigned g = nbk(n_pad, 128);
+#define MTF_BT(SCV) \
+  MTF_LAUNCH(KID_BXFORM, st, k_btrsm<SCV><<<g, 128, 0, st>>>(in, ldi, R, kept, s, out, ldo, n_pad))
+  if (s <= 1) MTF_BT(1);
+  else if (s <= 2) MTF_BT(2);
+  else if (s <= 4) MTF_BT(4);
+  else if (s <= 8) MTF_BT(8);
+  else if (s <= 16) MTF_BT(16);
+  else if (s <= 32) MTF_BT(32);
+  else MTF_BT(64);
+#undef MTF_BT
 }
 
 // relative size below which a new direction of a block is deflated (its norm
@@ -558,7 +597,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   // J + vshift (vshift = kept restarts so far).
   BlockLSQ& lsq = B.lsq;
   const int nb_old = lsq.k + 1 + B.vshift;
-  const bool keep = cycle > 0 && sys->opt.recycle && B.rec_ok && lsq.s == s && B.vshift < kMaxKeep &&
+  const bool keep = cycle > 0 && sys->opt.recycle >= 2 && B.rec_ok && lsq.s == s && B.vshift < kMaxKeep &&
                     nb_old + 16 <= m;
   B.rec_ok = false;
   bool grow = true;  // the start block has a kept direction
@@ -623,9 +662,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   // J + vshift + 1; the basis holds m + 1 blocks and Z holds m.
   const int Jend = std::min(m - vshift, J0 + std::max(1, max_iter));
   double* R1 = B.Cd.p;
-  double* T1 = R1 + 2 * size_t(s) * s;
-  double* R2 = T1 + 2 * size_t(s) * s;
-  double* T2 = R2 + 2 * size_t(s) * s;
+  double* R2 = R1 + 2 * size_t(s) * s;
   int* kept1 = B.kept.p;
   int* kept2 = kept1 + s;
   {
@@ -634,11 +671,11 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     MTF_CUDA(cudaGetDevice(&dev));
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(opted.load() & bit)) {
-      MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16));
+      MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
       opted.fetch_or(bit);
     }
   }
-  const size_t chol_smem = size_t(s) * s * sizeof(double2);
+  const size_t chol_smem = 2 * size_t(s) * s * sizeof(double2);
   // pinned slot layout (doubles): H1 (m+1) s s complex | H2 | R1 | R2; kept flags and error word separately
   const size_t slot_h = 2 * size_t(m + 1) * s * s;
   const size_t slot_len = 2 * slot_h + 4 * size_t(s) * s + 2 * size_t(s) + 1;
@@ -659,15 +696,15 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, Gpre, s, st);
     project(nq);
     bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
-    MTF_LAUNCH(KID_NORM, st, k_bchol<<<1, 64, chol_smem, st>>>(G, Gpre, nullptr, tau, s, R1, T1, kept1));
-    bxform(B.W.p, ldn, T1, s, B.D.p, ldn, ldn, st);
+    MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, Gpre, nullptr, tau, s, R1, kept1));
+    btrsm(B.W.p, ldn, R1, kept1, s, B.D.p, ldn, ldn, st);
     // second pass (CholQR2): the first leaves V = W R^-1 orthonormal only
     // to about cond(W) times the FP32 rounding; V_next = V R2^-1, R = R2 R1
     MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
     bdots(sys, B.D.p, s, ldn, B.D.p, ldn, s, ldn, G, s, st);
-    MTF_LAUNCH(KID_NORM, st, k_bchol<<<1, 64, chol_smem, st>>>(G, nullptr, kept1, 1e-3, s, R2, T2, kept2));
+    MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, nullptr, kept1, 1e-3, s, R2, kept2));
     float* Vn = B.V.p + 2 * int64_t(vb + 1) * vstride;
-    bxform(B.D.p, ldn, T2, s, Vn, ldn, ldn, st);
+    btrsm(B.D.p, ldn, R2, kept2, s, Vn, ldn, ldn, st);
     if (tc) tca_store(*B.tca, Vn, (vb + 1) * s, st);
     double* sl = slot(J);
     MTF_CUDA(cudaMemcpyAsync(sl, H1, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -230,7 +230,8 @@ namespace mtf {
 enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
-  KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_MVTC, KID_MVTC_PREP, KID_MVTC_COMBINE, KID_TC_TILE, KID_COUNT
+  KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_MVTC, KID_MVTC_PREP, KID_MVTC_COMBINE, KID_TC_TILE,
+  KID_BCHOL, KID_BXFORM, KID_BSTORE, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
@@ -372,7 +373,7 @@ void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z,
 // right-hand side's estimate reaches tol relative to its ||r|| (reached =
 // true), after opt.restart block steps, after max_iter block steps or when
 // every direction is deflated; iters[c] += block steps.  cycle: index of the
-// cycle within the solve; with opt.recycle a later cycle continues the space
+// cycle within the solve; with opt.recycle == 2 a later cycle continues the space
 // of the previous ones (its new residual projected on it) while there is
 // room in the restart length.
 mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,

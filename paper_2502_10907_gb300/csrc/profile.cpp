@@ -12,7 +12,8 @@ static const char* kNames[KID_COUNT] = {
     "regular64", "singular64", "exchange_values", "rhs", "matvec64", "gmres_dots",
     "gmres_axpy", "gmres_norm_scale", "gmres_sub", "farfield", "split_block",
     "regular32", "matvec32", "osrc_apply", "mlp", "misc", "matvec32_combine", "osrc_combine",
-    "matvec_tc", "matvec_tc_prep", "matvec_tc_combine", "tc_tile"};
+    "matvec_tc", "matvec_tc_prep", "matvec_tc_combine", "tc_tile", "block_cholesky", "block_xform",
+    "basis_store"};
 
 struct Prof {
   bool on = false;

@@ -604,8 +604,7 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       for (int c = 0; c < nrhs; ++c)
         if (rel[c] <= sys->opt.tol)
           MTF_CUDA(cudaMemsetAsync(G.b.p + 2 * size_t(c) * n, 0, size_t(n) * 2 * sizeof(double), s));
-      const double inner_min = std::getenv("MTF_INNER_MIN") ? std::atof(std::getenv("MTF_INNER_MIN")) : 1e-5;
-      const double inner_tol = std::min(0.5, std::max(inner_min, 0.3 * sys->opt.tol / rmax));
+      const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
       bool reached = false;
       // systems with a learned correction keep the per-rhs spaces, so that
