@@ -120,12 +120,16 @@ typedef struct {
                            normalisation); restart then counts block steps of
                            nrhs vectors.  0: one Krylov space per right-hand
                            side.  Default 1                                  */
-  int32_t mv_tensor;    /* mixed mode: 1: the FP32 matvec of the inner solver
-                           (mtf_matvec_f32) runs on the tensor cores from an
-                           FP16 hi + lo split of the stored blocks (about 22
-                           significant bits, FP32 accumulation), reading
+  int32_t mv_tensor;    /* mixed mode: 1: applies to more than 4 right-hand
+                           sides at once run on the tensor cores: the FP32
+                           matvec of the inner solver (mtf_matvec_f32) from
+                           an FP16 hi + lo split of the stored blocks (about
+                           22 significant bits, FP32 accumulation), reading
                            every stored entry once for up to 32 right-hand
-                           sides; 0: the FMA stream, once per 4.  Default 1  */
+                           sides, and the FP16 block-OSRC apply; applies to
+                           at most 4 (one pass of the FMA streams, which are
+                           faster there) and mv_tensor = 0 use the FMA
+                           streams, one pass per 4.  Default 1               */
 } mtf_options;
 
 typedef struct {

@@ -274,7 +274,7 @@ static void tca_launch(TcArnoldi& t, const CUtensorMap& amap, const CUtensorMap&
   const unsigned grid = unsigned(std::min(n_units, t.n_cta));
   MTF_LAUNCH(kid, st, k_tc_stream<2, NB, EPI><<<grid, 192, Cfg::smem, st>>>(amap, bmap, units, n_units, nullptr,
                                                                             nullptr, t.part.p, W, t.ldn, t.s, n_limit,
-                                                                            cm, err));
+                                                                            cm, err, TcTtOut{}));
 }
 
 template <int NB>

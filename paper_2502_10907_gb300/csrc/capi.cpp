@@ -544,6 +544,7 @@ void mtf_system_destroy(mtf_system sys) {
   destroy_gmres32(sys->gw32);
   destroy_block32(sys->bw);
   destroy_tc(sys->tc);
+  destroy_tt(sys->tt);
   destroy_learned(sys->learned);
   delete sys;
 }

@@ -1,9 +1,11 @@
 // Internal declarations of libmtf (not part of the public C-ABI).
 #pragma once
 
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -184,6 +186,7 @@ struct GmresWork;
 struct Gmres32Work;
 struct BlockWork;
 struct TcMatvec;
+struct TtForm;
 struct LearnedState;
 }
 
@@ -221,6 +224,7 @@ struct mtf_system_s {
   mtf::Gmres32Work* gw32 = nullptr;
   mtf::BlockWork* bw = nullptr;          // block FGMRES workspace (block32.cu)
   mtf::TcMatvec* tc = nullptr;           // tensor-core matvec tables and operator copy (mv_tc.cu)
+  mtf::TtForm* tt = nullptr;             // tensor-core block-OSRC formation (osrc_form_tc.cu)
   mtf::LearnedState* learned = nullptr;  // learned OSRC correction (learned.cu)
   bool learned_active = false;           // used by the current solve (cleared by its fallback)
 };
@@ -231,7 +235,7 @@ enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
   KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_MVTC, KID_MVTC_PREP, KID_MVTC_COMBINE, KID_TC_TILE,
-  KID_BCHOL, KID_BXFORM, KID_BSTORE, KID_COUNT
+  KID_BCHOL, KID_BXFORM, KID_BSTORE, KID_TT, KID_TT_MMA, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
@@ -356,6 +360,20 @@ void destroy_gmres(GmresWork* w);
 void destroy_gmres32(Gmres32Work* w);
 void destroy_block32(BlockWork* w);
 void destroy_tc(TcMatvec* t);
+void destroy_tt(TtForm* t);
+// the calling device's cuBLAS handle, bound to stream s, FP32 pedantic math;
+// the device's lock is held while the lease lives
+struct BlasLease {
+  cublasHandle_t h;
+  std::unique_lock<std::mutex> lock;
+};
+BlasLease blas_lease(cudaStream_t s);
+// right-hand sides of one pass of the FMA streaming applies; wider applies
+// go to the tensor cores (mv_tensor)
+constexpr int kFmaPassRhs = 4;
+// T~_i = W_i diag(f_i) W_i^T of every block into sys->d_osrc_T on the tensor
+// cores (osrc_form_tc.cu)
+void osrc_form_tc(mtf_system sys, cudaStream_t s);
 // tensor-core matvec (mv_tc.cu): the FP16 hi / lo tiled operator copy built
 // after every mixed assembly (opt.mv_tensor), and y = M x from it
 void tc_build_operator(mtf_system sys, cudaStream_t s);

@@ -278,7 +278,9 @@ void launch_matvec_stream64(mtf_system sys, const double* x, int64_t ldx, const 
 
 void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, int64_t ldy, int nrhs,
                        cudaStream_t s) {
-  if (tc_matvec_enabled(sys)) {
+  // one FMA pass (up to 4 right-hand sides) beats the tensor-core pass,
+  // whose input packing and combine cost more at that width
+  if (nrhs > kFmaPassRhs && tc_matvec_enabled(sys)) {
     launch_matvec_tc(sys, x, ldx, y, ldy, nrhs, s);
     return;
   }

@@ -687,7 +687,7 @@ static void os_tc_pass(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr,
   units.list = t.units_ab.p;
   MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.osmap, t.bmap, units, int(t.plan.units.size()), t.sched.p, t.sched_off.p, t.part.p, nullptr, 0, 0, 0, nullptr,
-      sys->d_mv_ctl.p + 2));
+      sys->d_mv_ctl.p + 2, TcTtOut{}));
   MTF_LAUNCH(KID_OSCOMBINE, s, k_os_tc_combine<NB><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));

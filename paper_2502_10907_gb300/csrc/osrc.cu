@@ -181,27 +181,6 @@ __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __re
   }
 }
 
-// columns j of W (rows e, leading dimension ld) scaled by Re f_j and Im f_j
-__global__ void k_scale_modes(const float* __restrict__ Wc, int N, int ld, const float2* __restrict__ f,
-                              float* __restrict__ Bre, float* __restrict__ Bim) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= int64_t(N) * ld) return;
-  const int j = int(t / ld);
-  const float w = Wc[t];
-  const float2 fj = f[j];
-  Bre[t] = w * fj.x;
-  Bim[t] = w * fj.y;
-}
-
-// complex rows of stride ldt (>= N, padding zero) from N x N real and imaginary parts
-__global__ void k_interleave(const float* __restrict__ re, const float* __restrict__ im, int N, int ldt,
-                             float2* __restrict__ out) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= int64_t(N) * ldt) return;
-  const int64_t r = t / ldt, c = t % ldt;
-  out[t] = c < N ? make_float2(re[r * N + c], im[r * N + c]) : make_float2(0.f, 0.f);
-}
-
 // z rows of one block row m (one warp per global row): the row's T~ pieces
 // added in order, then z_D = rho^-1 (T~ r_N), z_N = -rho (T~ r_D) per
 // right-hand side (lane c < NC), in the output precision.
@@ -293,24 +272,46 @@ __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t
   out[t] = float(x[2 * c * ldx + k]);
 }
 
-cublasHandle_t blas_handle() {
-  static cublasHandle_t h = nullptr;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!h) {
-    MTF_REQUIRE(cublasCreate(&h) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasCreate failed");
+// cuBLAS / cuSOLVER handles: one per device, each used under its device's
+// lock (a handle is bound to the device it was created on, and its stream
+// setting is shared state), in FP32 pedantic math (no TF32 rounding)
+static constexpr int kMaxDev = 64;
+
+BlasLease blas_lease(cudaStream_t s) {
+  static cublasHandle_t h[kMaxDev] = {};
+  static std::mutex mu[kMaxDev];
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  MTF_REQUIRE(dev >= 0 && dev < kMaxDev, MTF_ERR_CUDA, "device index out of range");
+  BlasLease L{nullptr, std::unique_lock<std::mutex>(mu[dev])};
+  if (!h[dev]) {
+    MTF_REQUIRE(cublasCreate(&h[dev]) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasCreate failed");
+    MTF_REQUIRE(cublasSetMathMode(h[dev], CUBLAS_PEDANTIC_MATH) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
+                "cublasSetMathMode failed");
   }
-  return h;
+  MTF_REQUIRE(cublasSetStream(h[dev], s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
+  L.h = h[dev];
+  return L;
 }
 
-static cusolverDnHandle_t solver_handle() {
-  static cusolverDnHandle_t h = nullptr;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!h) {
-    MTF_REQUIRE(cusolverDnCreate(&h) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnCreate failed");
+struct SolverLease {
+  cusolverDnHandle_t h;
+  std::unique_lock<std::mutex> lock;
+};
+
+static SolverLease solver_lease(cudaStream_t s) {
+  static cusolverDnHandle_t h[kMaxDev] = {};
+  static std::mutex mu[kMaxDev];
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  MTF_REQUIRE(dev >= 0 && dev < kMaxDev, MTF_ERR_CUDA, "device index out of range");
+  SolverLease L{nullptr, std::unique_lock<std::mutex>(mu[dev])};
+  if (!h[dev]) {
+    MTF_REQUIRE(cusolverDnCreate(&h[dev]) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnCreate failed");
   }
-  return h;
+  MTF_REQUIRE(cusolverDnSetStream(h[dev], s) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnSetStream failed");
+  L.h = h[dev];
+  return L;
 }
 
 // The 2 g harmonic fields of a genus-g boundary (the part of the kernel of
@@ -325,8 +326,8 @@ static cusolverDnHandle_t solver_handle() {
 static void osrc_harmonic(int N, int nirr, int nloop, int nh, const float* K, const float* G, float* W,
                           cusolverDnHandle_t sh, cudaStream_t s) {
   const int m = N - nirr;
-  cublasHandle_t bh = blas_handle();
-  MTF_REQUIRE(cublasSetStream(bh, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
+  BlasLease bl = blas_lease(s);
+  cublasHandle_t bh = bl.h;
   DevBuf<float> GK, X, R, Q, w;
   GK.alloc(size_t(N) * m);
   X.alloc(size_t(std::max(nloop, 1)) * m);
@@ -405,8 +406,8 @@ static void osrc_mesh_setup(mtf_mesh m, cudaStream_t s) {
   MTF_LAUNCH(KID_MISC, s, k_gram_divdiv<<<unsigned((m->n_bt + 127) / 128), 128, 0, s>>>(
       m->d_bt_v.p, m->d_bt_c.p, m->d_bt_area.p, m->d_bt_dof.p, m->d_bt_blk.p, m->d_blk_mat_off.p, m->d_blk_N.p,
       m->n_bt, G.p, Dd.p));
-  cusolverDnHandle_t h = solver_handle();
-  MTF_REQUIRE(cusolverDnSetStream(h, s) == CUSOLVER_STATUS_SUCCESS, MTF_ERR_CUDA, "cusolverDnSetStream failed");
+  SolverLease sl = solver_lease(s);  // held for the whole setup (osrc_harmonic takes the cuBLAS lock inside it)
+  cusolverDnHandle_t h = sl.h;
   DevBuf<int> info;
   info.alloc(1);
   auto sygvd = [&](int N, float* A, float* B, float* W, const std::string& what) {
@@ -588,20 +589,6 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   MTF_LAUNCH(KID_MISC, s, k_osrc_symbol<<<unsigned((m->n_rows + 127) / 128), 128, 0, s>>>(
       m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, m->d_blk_row_off.p, m->d_osrc_nirr.p, sys->d_k.p, d_keps.p,
       d_pd.p, np, reinterpret_cast<float2*>(sys->d_osrc_f.p)));
-  // T~_i = W diag(f) W^T (column-major GEMMs; T~ is symmetric, so the
-  // column-major result read row by row is T~ itself)
-  cublasHandle_t bh = blas_handle();
-  MTF_REQUIRE(cublasSetStream(bh, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
-  MTF_REQUIRE(cublasSetMathMode(bh, CUBLAS_PEDANTIC_MATH) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
-              "cublasSetMathMode failed");
-  int nmax = 0;
-  for (int i = 0; i < m->nd; ++i) nmax = std::max(nmax, m->blk[i].N);
-  const int ldmax = (nmax + 3) & ~3;
-  DevBuf<float> Bre, Bim, Cre, Cim;
-  Bre.alloc(size_t(nmax) * ldmax);
-  Bim.alloc(size_t(nmax) * ldmax);
-  Cre.alloc(size_t(nmax) * nmax);
-  Cim.alloc(size_t(nmax) * nmax);
   // T~ rows padded to an even length (8-byte entries: 16-byte aligned rows)
   m->os_T_off_h.assign(m->nd, 0);
   int64_t toff = 0;
@@ -610,23 +597,8 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
     toff += int64_t(m->blk[i].N) * (m->blk[i].N + (m->blk[i].N & 1));
   }
   sys->d_osrc_T.alloc(size_t(toff) * 2);
-  const float one = 1.f, zero = 0.f;
-  for (int i = 0; i < m->nd; ++i) {
-    const int N = m->blk[i].N, ld = (N + 3) & ~3;
-    const float* Wc = m->d_osrc_Vt.p + m->osrc_off_h[i];
-    MTF_LAUNCH(KID_MISC, s, k_scale_modes<<<unsigned((int64_t(N) * ld + 255) / 256), 256, 0, s>>>(
-        Wc, N, ld, reinterpret_cast<const float2*>(sys->d_osrc_f.p) + m->blk[i].row_off, Bre.p, Bim.p));
-    MTF_REQUIRE(cublasSgemm(bh, CUBLAS_OP_N, CUBLAS_OP_T, N, N, N, &one, Bre.p, ld, Wc, ld, &zero, Cre.p, N) ==
-                    CUBLAS_STATUS_SUCCESS,
-                MTF_ERR_CUDA, "cublasSgemm failed");
-    MTF_REQUIRE(cublasSgemm(bh, CUBLAS_OP_N, CUBLAS_OP_T, N, N, N, &one, Bim.p, ld, Wc, ld, &zero, Cim.p, N) ==
-                    CUBLAS_STATUS_SUCCESS,
-                MTF_ERR_CUDA, "cublasSgemm failed");
-    const int ldt = N + (N & 1);
-    const int64_t nn = int64_t(N) * ldt;
-    MTF_LAUNCH(KID_MISC, s, k_interleave<<<unsigned((nn + 255) / 256), 256, 0, s>>>(
-        Cre.p, Cim.p, N, ldt, reinterpret_cast<float2*>(sys->d_osrc_T.p) + m->os_T_off_h[i]));
-  }
+  // T~_i = W_i diag(f_i) W_i^T on the tensor cores
+  osrc_form_tc(sys, s);
   if (sys->opt.osrc_half) osrc_half_copy(sys, s);
   osrc_prepare_fp64_apply(sys, s);
   MTF_CUDA(cudaStreamSynchronize(s));  // scratch and d_pd / d_keps are freed on return
@@ -670,7 +642,7 @@ template <class ZT, bool ADJ = false>
 static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
   stream_prepare(sys, s);
   if constexpr (sizeof(ZT) == 4) {
-    if (!ADJ && tc_osrc_enabled(sys)) {
+    if (!ADJ && nrhs > kFmaPassRhs && tc_osrc_enabled(sys)) {
       launch_osrc_apply_tc(sys, r32, ldr, z, ldz, nrhs, s);
       return;
     }

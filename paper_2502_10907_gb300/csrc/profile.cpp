@@ -13,7 +13,7 @@ static const char* kNames[KID_COUNT] = {
     "gmres_axpy", "gmres_norm_scale", "gmres_sub", "farfield", "split_block",
     "regular32", "matvec32", "osrc_apply", "mlp", "misc", "matvec32_combine", "osrc_combine",
     "matvec_tc", "matvec_tc_prep", "matvec_tc_combine", "tc_tile", "block_cholesky", "block_xform",
-    "basis_store"};
+    "basis_store", "osrc_form_prep", "osrc_form_mma"};
 
 struct Prof {
   bool on = false;

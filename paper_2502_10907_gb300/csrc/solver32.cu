@@ -580,7 +580,6 @@ constexpr int kBatch = 8;
 // doubles of the Hessenberg slot of column j
 static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 8) * nrhs; }
 
-cublasHandle_t blas_handle();  // shared cuBLAS handle (osrc.cu)
 
 // Build the recycled space of a finished cycle for the next cycle of the same
 // solve: per rhs c with k_c finished columns, H_c = Q_c R_c (host Givens
@@ -617,10 +616,8 @@ static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_
   if (G.RU.n < ncols) G.RU.alloc(ncols);
   if (G.RQ.n < qr32.size()) G.RQ.alloc(qr32.size());
   MTF_CUDA(cudaMemcpyAsync(G.RQ.p, qr32.data(), qr32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-  cublasHandle_t h = blas_handle();
-  MTF_REQUIRE(cublasSetStream(h, s) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA, "cublasSetStream failed");
-  MTF_REQUIRE(cublasSetMathMode(h, CUBLAS_PEDANTIC_MATH) == CUBLAS_STATUS_SUCCESS, MTF_ERR_CUDA,
-              "cublasSetMathMode failed");
+  BlasLease bl = blas_lease(s);
+  cublasHandle_t h = bl.h;
   const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
   for (int c = 0; c < nrhs; ++c) {
     const int kc = ha.jc[c];

@@ -170,4 +170,66 @@ inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int
   return "";
 }
 
+// Tensor-core formation of the block-OSRC operators T~_i = W_i diag(f_i) W_i^T
+// (osrc_form_tc.cu).  W_i is real (N_i x N_i, rows = RWG dofs r, columns =
+// modes j) and f_i complex, so with
+//   A[r][j] = W(r, j),   B[2 c + t][j] = f_j^(t) W(c, j)   (t = 0: Re, 1: Im)
+// the product D = A B^T gives D[r][2 c + t] = (T~_i)^(t)(r, c): the interleaved
+// complex rows of T~ directly.  A tile is (block, row tile mt of 128 dofs,
+// chunk kc of 64 modes), two parts (hi, lo) of 128 rows x 64 FP16; a B chunk
+// is (block, column tile nt of 64 dofs = 128 B rows, chunk kc), two parts of
+// 128 rows x 64 FP16.  T~ is symmetric, so only the units (mt, nt) whose
+// tile holds an entry with c >= r are formed: a unit writes its entries with
+// c >= r in place and those with c > r transposed, so every entry of T~ is
+// written exactly once.
+constexpr int kTtCols = 64;  // complex output columns per unit (128 B rows)
+
+struct TtBlock {
+  int N = 0, n_mt = 0, n_nt = 0, n_kc = 0;
+  int64_t a_base = 0, b_base = 0;  // first A tile, first B chunk
+};
+
+struct TtUnit {
+  int blk, mt, nt;
+};
+
+struct TtPlan {
+  std::vector<TtBlock> blocks;
+  std::vector<TtUnit> units;  // longest blocks first (round-robin over the CTAs)
+  int64_t n_a = 0, n_b = 0;   // A tiles, B chunks
+};
+
+// does the 128 x 64 output tile (mt, nt) hold an entry with c >= r?
+constexpr bool tt_upper(int mt, int nt) { return int64_t(nt) * kTtCols + kTtCols - 1 >= int64_t(mt) * kTcRows; }
+
+inline std::string plan_tt(const std::vector<int>& Ns, TtPlan& p) {
+  p = TtPlan{};
+  p.blocks.resize(Ns.size());
+  int64_t a = 0, b = 0;
+  for (size_t i = 0; i < Ns.size(); ++i) {
+    TtBlock& q = p.blocks[i];
+    if (Ns[i] <= 0) return "plan_tt: empty block";
+    q.N = Ns[i];
+    q.n_mt = (q.N + kTcRows - 1) / kTcRows;
+    q.n_nt = (q.N + kTtCols - 1) / kTtCols;
+    q.n_kc = (q.N + 63) / 64;
+    q.a_base = a;
+    q.b_base = b;
+    a += int64_t(q.n_mt) * q.n_kc;
+    b += int64_t(q.n_nt) * q.n_kc;
+  }
+  p.n_a = a;
+  p.n_b = b;
+  std::vector<int> order(Ns.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return Ns[size_t(x)] > Ns[size_t(y)]; });
+  for (int i : order) {
+    const TtBlock& q = p.blocks[size_t(i)];
+    for (int mt = 0; mt < q.n_mt; ++mt)
+      for (int nt = 0; nt < q.n_nt; ++nt)
+        if (tt_upper(mt, nt)) p.units.push_back(TtUnit{i, mt, nt});
+  }
+  return "";
+}
+
 }  // namespace mtf

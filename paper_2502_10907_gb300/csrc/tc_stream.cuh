@@ -17,6 +17,10 @@
 //   EPI 1: W_c[128 u + row] -= (D[row][2c] + i D[row][2c + 1]) * s_c,
 //          s_c = inv_scale(colmax[c]) / 2^14, for c < ncols, rows < n_limit
 //          (the Gram-Schmidt update of W against a basis stored x 2^14).
+//   EPI 2: the block-OSRC formation (tc_plan.h, plan_tt): unit u covers rows
+//          r = info.y + row and complex columns c = info.z + col / 2 of the
+//          symmetric T~ of block info.x; (D[row][2j], D[row][2j + 1]) * inv
+//          goes to T~(r, c) when c >= r and to T~(c, r) when c > r.
 // Every wait is bounded (0.5 s) and ends in the error word.
 #pragma once
 
@@ -64,6 +68,16 @@ struct TcUnits {
   }
 };
 
+// outputs of the block-OSRC formation (EPI 2)
+struct TcTtOut {
+  const int4* info = nullptr;    // per unit {block, first row, first complex column, 0}
+  const int* N = nullptr;        // per block: order of T~
+  const int* ldt = nullptr;      // per block: row stride of T~ (complex entries)
+  const int64_t* off = nullptr;  // per block: first complex entry of T~
+  const float* inv = nullptr;    // per block: 1 / (operand scales)
+  float2* T = nullptr;
+};
+
 __device__ __forceinline__ float tcs_inv_scale(unsigned bits) {
   const float a = __uint_as_float(bits);
   if (!(a > 0.f)) return 1.f;
@@ -78,7 +92,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_stream(const __grid_constant__ CU
                                                       int n_units, const int* __restrict__ sched,
                                                       const int* __restrict__ sched_off, float* __restrict__ part,
                                                       float* __restrict__ W, int64_t ldw, int ncols, int64_t n_limit,
-                                                      const unsigned* __restrict__ colmax, unsigned* __restrict__ err) {
+                                                      const unsigned* __restrict__ colmax, unsigned* __restrict__ err,
+                                                      const TcTtOut tt) {
   using C = TcsCfg<NPA, NB>;
   constexpr int S = C::S, SB = C::SB, SA = C::SA;
   extern __shared__ unsigned char smem_raw[];
@@ -195,6 +210,26 @@ __global__ void __launch_bounds__(192, 1) k_tc_stream(const __grid_constant__ CU
           d4[1] = make_float4(v[4], v[5], v[6], v[7]);
           d4[2] = make_float4(v[8], v[9], v[10], v[11]);
           d4[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+      } else if constexpr (EPI == 2) {
+        const int4 I = tt.info[u];
+        const int n = tt.N[I.x], ld = tt.ldt[I.x];
+        const int64_t off = tt.off[I.x];
+        const float inv = tt.inv[I.x];
+        const int r = I.y + row;
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+          float v[16];
+          tmem_ld16(ta + uint32_t(c0), v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int c = I.z + c0 / 2 + i;
+            if (r < n && c < n && c >= r) {
+              const float2 o = make_float2(v[2 * i] * inv, v[2 * i + 1] * inv);
+              tt.T[off + int64_t(r) * ld + c] = o;
+              if (c > r) tt.T[off + int64_t(c) * ld + r] = o;
+            }
+          }
         }
       } else {
         const int64_t kk = int64_t(u) * kTcRows + row;

@@ -9,6 +9,11 @@
 //     column forms, the products emulated as the tensor cores form them
 //     (FP16 operands, hi*hi + hi*lo + lo*hi per chunk) and unscaled give
 //     T u and K u to about 2^-22 of the exact complex products;
+//  4. the block-OSRC formation plan (plan_tt): the formed units with the
+//     in-place / mirror rule write every entry of every T~_i exactly once,
+//     tile and chunk indices stay inside the allocations, and the formation
+//     emulated in that layout (W and f^(t) W scaled, split into FP16 hi + lo,
+//     three products, FP32 sums) gives W diag(f) W^T to about 2^-21;
 //  3. the two tiled basis copies of the tensor-core Gram-Schmidt projections:
 //     every (vector, entry, part) of the basis sizes used maps inside the
 //     allocation (the stores write 8 halves from a multiple-of-4 entry), and
@@ -181,6 +186,124 @@ static int check_basis_layout() {
   return 0;
 }
 
+static float p2scale(double a) {
+  if (!(a > 0)) return 1.f;
+  int ex;
+  std::frexp(a, &ex);
+  return std::ldexp(1.f, 14 - ex);
+}
+
+// plan_tt coverage and index bounds; with emulate, the formation itself
+static int check_tt(const std::vector<int>& Ns, bool emulate) {
+  mtf::TtPlan p;
+  const std::string why = mtf::plan_tt(Ns, p);
+  if (!why.empty()) return std::printf("tt: %s\n", why.c_str()), 1;
+  std::mt19937 rng(11);
+  std::normal_distribution<double> G(0, 1);
+  const int64_t na = p.n_a * 2 * mtf::kTcRows * 64, nb = p.n_b * 2 * 128 * 64;
+  std::vector<float> A, B;
+  std::vector<std::vector<double>> W(Ns.size());
+  std::vector<std::vector<cd>> F(Ns.size());
+  std::vector<float> inv(Ns.size());
+  if (emulate) {
+    A.assign(size_t(na), 0.f);
+    B.assign(size_t(nb), 0.f);
+    for (size_t i = 0; i < Ns.size(); ++i) {
+      const int N = Ns[i];
+      const mtf::TtBlock& q = p.blocks[i];
+      W[i].resize(size_t(N) * N);  // W(r, j) at r * N + j
+      F[i].resize(size_t(N));
+      double wm = 0, bm = 0;
+      for (auto& v : W[i]) v = float(G(rng) / std::sqrt(double(N))), wm = std::max(wm, std::fabs(v));
+      for (int j = 0; j < N; ++j) F[i][size_t(j)] = cd(float(3 * G(rng)), float(G(rng)));
+      for (int r = 0; r < N; ++r)
+        for (int j = 0; j < N; ++j) {
+          const double w = W[i][size_t(r) * N + j];
+          bm = std::max(bm, std::fabs(w) * std::max(std::fabs(F[i][size_t(j)].real()), std::fabs(F[i][size_t(j)].imag())));
+        }
+      const float sa = p2scale(wm), sb = p2scale(bm);
+      inv[i] = 1.f / (sa * sb);
+      for (int r = 0; r < q.n_mt * mtf::kTcRows; ++r)
+        for (int j = 0; j < q.n_kc * 64; ++j) {
+          const float x = (r < N && j < N) ? float(W[i][size_t(r) * N + j]) * sa : 0.f;
+          const float h = f16(x), l = f16(x - h);
+          const int64_t tile = q.a_base + int64_t(r / mtf::kTcRows) * q.n_kc + j / 64;
+          A[size_t(mtf::tc_tile_index(tile, 2, 0, r % mtf::kTcRows, j % 64))] = h;
+          A[size_t(mtf::tc_tile_index(tile, 2, 1, r % mtf::kTcRows, j % 64))] = l;
+        }
+      for (int gr = 0; gr < q.n_nt * 128; ++gr)
+        for (int j = 0; j < q.n_kc * 64; ++j) {
+          const int c = gr / 2;
+          float x = 0.f;
+          if (c < N && j < N) {
+            const cd fj = F[i][size_t(j)];
+            x = float(W[i][size_t(c) * N + j]) * float((gr & 1) ? fj.imag() : fj.real()) * sb;
+          }
+          const float h = f16(x), l = f16(x - h);
+          const int64_t chunk = q.b_base + int64_t(gr / 128) * q.n_kc + j / 64;
+          B[size_t(mtf::tc_b_index(chunk, 0, gr % 128, j % 64, 128))] = h;
+          B[size_t(mtf::tc_b_index(chunk, 1, gr % 128, j % 64, 128))] = l;
+        }
+    }
+  }
+  std::vector<std::vector<int>> cnt(Ns.size());
+  std::vector<std::vector<cd>> T(Ns.size());
+  for (size_t i = 0; i < Ns.size(); ++i) {
+    cnt[i].assign(size_t(Ns[i]) * Ns[i], 0);
+    T[i].assign(size_t(Ns[i]) * Ns[i], 0.0);
+  }
+  for (const mtf::TtUnit& u : p.units) {
+    const mtf::TtBlock& q = p.blocks[size_t(u.blk)];
+    const int64_t a0 = q.a_base + int64_t(u.mt) * q.n_kc, b0 = q.b_base + int64_t(u.nt) * q.n_kc;
+    if (a0 + q.n_kc > p.n_a || b0 + q.n_kc > p.n_b) return std::printf("tt: index out of range\n"), 1;
+    const int N = q.N;
+    for (int rho = 0; rho < mtf::kTcRows; ++rho) {
+      const int r = u.mt * mtf::kTcRows + rho;
+      for (int cc = 0; cc < mtf::kTtCols; ++cc) {
+        const int c = u.nt * mtf::kTtCols + cc;
+        if (!(r < N && c < N && c >= r)) continue;
+        float d[2] = {0.f, 0.f};
+        if (emulate)
+          for (int kc = 0; kc < q.n_kc; ++kc)
+            for (int t = 0; t < 2; ++t)
+              for (int e = 0; e < 64; ++e) {
+                const float ah = A[size_t(mtf::tc_tile_index(a0 + kc, 2, 0, rho, e))];
+                const float al = A[size_t(mtf::tc_tile_index(a0 + kc, 2, 1, rho, e))];
+                const float bh = B[size_t(mtf::tc_b_index(b0 + kc, 0, 2 * cc + t, e, 128))];
+                const float bl = B[size_t(mtf::tc_b_index(b0 + kc, 1, 2 * cc + t, e, 128))];
+                d[t] += ah * bh + ah * bl + al * bh;
+              }
+        const cd o(d[0] * inv[size_t(u.blk)], d[1] * inv[size_t(u.blk)]);
+        ++cnt[size_t(u.blk)][size_t(r) * N + c];
+        T[size_t(u.blk)][size_t(r) * N + c] = o;
+        if (c > r) {
+          ++cnt[size_t(u.blk)][size_t(c) * N + r];
+          T[size_t(u.blk)][size_t(c) * N + r] = o;
+        }
+      }
+    }
+  }
+  for (auto& v : cnt)
+    for (int x : v)
+      if (x != 1) return std::printf("tt: an entry written %d times\n", x), 1;
+  if (!emulate) return std::printf("tt: %zu blocks, %zu units, coverage ok\n", Ns.size(), p.units.size()), 0;
+  double emax = 0;
+  for (size_t i = 0; i < Ns.size(); ++i) {
+    const int N = Ns[i];
+    double tmax = 0, err = 0;
+    for (int r = 0; r < N; ++r)
+      for (int c = 0; c < N; ++c) {
+        cd ex = 0;
+        for (int j = 0; j < N; ++j) ex += W[i][size_t(r) * N + j] * F[i][size_t(j)] * W[i][size_t(c) * N + j];
+        tmax = std::max(tmax, std::abs(ex));
+        err = std::max(err, std::abs(ex - T[i][size_t(r) * N + c]));
+      }
+    emax = std::max(emax, err / tmax);
+  }
+  std::printf("tt: formation emulated, max entry error %.2e of the largest entry\n", emax);
+  return emax < 4e-6 ? 0 : 1;
+}
+
 int main() {
   int f = 0;
   f += check_basis_layout();
@@ -190,5 +313,8 @@ int main() {
   f += check_plan({2178, 2178, 2178}, 152);
   f += check_plan({567, 45, 3}, 152);
   f += check_formulation();
+  f += check_tt({2178, 2178, 2178}, false);
+  f += check_tt(cube4, false);
+  f += check_tt({200, 64, 129, 1}, true);
   return f;
 }
