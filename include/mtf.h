@@ -100,12 +100,9 @@ typedef struct {
                            space (GCRO-style: the new residual is projected
                            out of it and new basis vectors are orthogonalised
                            against it) instead of restarting from scratch;
-                           2: also in the block solver (block_krylov), where
-                           the next cycle keeps the basis and its least-
-                           squares factor (on the 72,000-unknown cube with
-                           16 right-hand sides this took 1003 block steps
-                           against 839 for a fresh start, so it is opt-in);
-                           0: plain restart.  Default 1                      */
+                           0: plain restart.  The block solver
+                           (block_krylov) always starts a cycle afresh.
+                           Default 1                                         */
   int32_t residual_df;  /* mixed mode: 1: the outer refinement residuals
                            b - M x apply the FP32-stored operator to the FP64
                            iterate in double-float arithmetic (iterate split

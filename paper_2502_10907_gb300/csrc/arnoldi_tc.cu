@@ -108,12 +108,12 @@ __global__ void k_tca_colmax32(const float* __restrict__ W, int64_t ld, int64_t 
   if ((threadIdx.x & 31) == 0) atomicMax(colmax + c, __float_as_uint(m));
 }
 
-// colmax[c] = max over q < nq of |re|, |im| of H[q, c] (FP64, leading dim s)
-__global__ void k_tca_colmax64(const double* __restrict__ H, int nq, int s, unsigned* __restrict__ colmax) {
+// colmax[c] = max over q < nq of |re|, |im| of H[q, c] (FP64, leading dim ldh)
+__global__ void k_tca_colmax64(const double* __restrict__ H, int nq, int ldh, unsigned* __restrict__ colmax) {
   const int c = blockIdx.y;
   float m = 0.f;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-    const double* h = H + 2 * (int64_t(q) * s + c);
+    const double* h = H + 2 * (int64_t(q) * ldh + c);
     m = fmaxf(m, fmaxf(fabsf(float(h[0])), fabsf(float(h[1]))));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -147,9 +147,10 @@ __global__ void k_tca_w_to_b(const float* __restrict__ W, int64_t ldw, int s, in
   *reinterpret_cast<uint4*>(Bd + tc_b_index(kc, 1, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(lo);
 }
 
-// update input chunks from H (FP64, q < nq): column 2 c + f, form 0
-// (H_re, -H_im), form 1 (H_im, H_re); thread = (chunk, column, group of 4 vectors)
-__global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int nbc, int nb,
+// update input chunks from H (FP64, q < nq, leading dim ldh): column 2 c + f,
+// form 0 (H_re, -H_im), form 1 (H_im, H_re); thread = (chunk, column, group
+// of 4 vectors)
+__global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int ldh, int nbc, int nb,
                              const unsigned* __restrict__ colmax, __half* __restrict__ Bu) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(nbc) * nb * 8) return;
@@ -165,7 +166,7 @@ __global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int nb
     for (int i = 0; i < 4; ++i) {
       const int q = b * 32 + 4 * g + i;
       if (q < nq) {
-        const double* h = H + 2 * (int64_t(q) * s + c);
+        const double* h = H + 2 * (int64_t(q) * ldh + c);
         const float re = float(h[0]), im = float(h[1]);
         const float x = form == 0 ? re : im, y = form == 0 ? -im : re;
         tca_split(x * sc, hi[2 * i], lo[2 * i]);
@@ -177,10 +178,10 @@ __global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int nb
   *reinterpret_cast<uint4*>(Bu + tc_b_index(b, 1, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(lo);
 }
 
-// H[q, c] = (sum over the P pieces of basis group q / 128 of the raw sums) x
-// the inverse scales, in FP64; thread = (q, c)
+// H[q, c] (at H + 2 (q ldh + c)) = (sum over the P pieces of basis group
+// q / 128 of the raw sums) x the inverse scales, in FP64; thread = (q, c)
 __global__ void k_tca_dots_reduce(const float* __restrict__ part, int nb, int P, int nq, int s,
-                                  const unsigned* __restrict__ colmax, double* __restrict__ H) {
+                                  const unsigned* __restrict__ colmax, double* __restrict__ H, int ldh) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(nq) * s) return;
   const int q = int(t / s), c = int(t % s);
@@ -192,22 +193,25 @@ __global__ void k_tca_dots_reduce(const float* __restrict__ part, int nb, int P,
     im += double(pr[1]);
   }
   const double sc = double(tca_inv_scale(colmax[c])) / double(kBasisScale);
-  H[2 * t] = re * sc;
-  H[2 * t + 1] = im * sc;
+  const int64_t o = 2 * (int64_t(q) * ldh + c);
+  H[o] = re * sc;
+  H[o + 1] = im * sc;
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+constexpr int kTcaMaxCols = 64;  // columns of one projection pass (NB = 128)
+
 struct TcArnoldi {
-  int s = 0, m = 0, nb = 0;
+  int s = 0, m = 0;
   int64_t ldn = 0;
   int G = 0, nkc = 0, E = 0, nbc = 0;  // basis groups, entry chunks, entry groups, basis chunks
   DevBuf<__half> Vd, Vu, Bd, Bu;
   DevBuf<float> part;
   DevBuf<unsigned> cm;                 // colmax of W (s) and of H (s)
   size_t h_cap = 0;                    // units the partial buffer holds
-  int n_cta = 0;
+  int n_cta = 0, b_nb = 0;
   CUtensorMap vd_map{}, vu_map{}, bd_map{}, bu_map{};
 
 };
@@ -215,7 +219,7 @@ struct TcArnoldi {
 TcArnoldi* tca_create() { return new TcArnoldi(); }
 void tca_destroy(TcArnoldi* t) { delete t; }
 
-static int tca_nb(int s) { return 2 * s <= 16 ? 16 : 2 * s <= 32 ? 32 : 2 * s <= 64 ? 64 : 128; }
+static int tca_nb(int nc) { return 2 * nc <= 16 ? 16 : 2 * nc <= 32 ? 32 : 2 * nc <= 64 ? 64 : 128; }
 
 void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st) {
   MTF_REQUIRE(s >= 1 && s <= 64 && ldn % 64 == 0, MTF_ERR_ARG, "tensor-core Arnoldi: 1..64 columns, padded length");
@@ -223,7 +227,6 @@ void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st) {
   t.s = s;
   t.m = m;
   t.ldn = ldn;
-  t.nb = tca_nb(s);
   const int64_t nvec = int64_t(m + 1) * s;
   t.G = int((nvec + kTcRows - 1) / kTcRows);
   t.nkc = int(ldn / kTcCols);
@@ -233,20 +236,27 @@ void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st) {
   t.Vu.alloc(size_t(tca_upd_halves(nvec, ldn)));
   MTF_CUDA(cudaMemsetAsync(t.Vd.p, 0, t.Vd.n * sizeof(__half), st));
   MTF_CUDA(cudaMemsetAsync(t.Vu.p, 0, t.Vu.n * sizeof(__half), st));
-  t.Bd.alloc(size_t(t.nkc) * 2 * t.nb * 64);
-  t.Bu.alloc(size_t(t.nbc) * 2 * t.nb * 64);
-  t.cm.alloc(size_t(2) * s);
+  t.Bd.alloc(size_t(t.nkc) * 2 * 128 * 64);
+  t.Bu.alloc(size_t(t.nbc) * 2 * 128 * 64);
+  t.cm.alloc(size_t(2) * kTcaMaxCols);
   int dev = 0;
   MTF_CUDA(cudaGetDevice(&dev));
   MTF_CUDA(cudaDeviceGetAttribute(&t.n_cta, cudaDevAttrMultiProcessorCount, dev));
   // dots units: up to 4 per CTA over the basis groups in use; update units: one per entry group
   const size_t cap = size_t(4 * t.n_cta + t.G) + 16;
-  t.part.alloc(cap * kTcRows * t.nb);
+  t.part.alloc(cap * kTcRows * 128);
   t.h_cap = cap;
   tc_encode_map(&t.vd_map, t.Vd.p, kTcRows, 2, int64_t(t.G) * t.nkc);
   tc_encode_map(&t.vu_map, t.Vu.p, kTcRows, 2, int64_t(t.E) * t.nbc);
-  tc_encode_map(&t.bd_map, t.Bd.p, t.nb, 2, t.nkc);
-  tc_encode_map(&t.bu_map, t.Bu.p, t.nb, 2, t.nbc);
+  t.b_nb = 0;
+}
+
+// B maps for width nb (the chunk buffers hold the widest)
+static void tca_bmaps(TcArnoldi& t, int nb) {
+  if (t.b_nb == nb) return;
+  tc_encode_map(&t.bd_map, t.Bd.p, nb, 2, t.nkc);
+  tc_encode_map(&t.bu_map, t.Bu.p, nb, 2, t.nbc);
+  t.b_nb = nb;
 }
 
 // basis vectors q0 .. q0 + s - 1 (FP32 columns of stride ldn) into both copies
@@ -260,7 +270,7 @@ void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st) {
 
 template <int NB, int EPI>
 static void tca_launch(TcArnoldi& t, const CUtensorMap& amap, const CUtensorMap& bmap, const TcUnits& units,
-                       int n_units, float* W, int64_t n_limit, const unsigned* cm, unsigned* err, int kid,
+                       int n_units, float* W, int nc, int64_t n_limit, const unsigned* cm, unsigned* err, int kid,
                        cudaStream_t st) {
   using Cfg = TcsCfg<2, NB>;
   static std::atomic<uint64_t> opted{0};
@@ -273,20 +283,20 @@ static void tca_launch(TcArnoldi& t, const CUtensorMap& amap, const CUtensorMap&
   }
   const unsigned grid = unsigned(std::min(n_units, t.n_cta));
   MTF_LAUNCH(kid, st, k_tc_stream<2, NB, EPI><<<grid, 192, Cfg::smem, st>>>(amap, bmap, units, n_units, nullptr,
-                                                                            nullptr, t.part.p, W, t.ldn, t.s, n_limit,
+                                                                            nullptr, t.part.p, W, t.ldn, nc, n_limit,
                                                                             cm, err, TcTtOut{}));
 }
 
 template <int NB>
-static void tca_project_nb(TcArnoldi& t, int nq, float* W, double* H, unsigned* err, cudaStream_t st) {
-  const int s = t.s;
+static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, int ldh, unsigned* err, cudaStream_t st) {
+  tca_bmaps(t, NB);
   unsigned* cmw = t.cm.p;
-  unsigned* cmh = t.cm.p + s;
-  MTF_CUDA(cudaMemsetAsync(t.cm.p, 0, size_t(2) * s * sizeof(unsigned), st));
+  unsigned* cmh = t.cm.p + kTcaMaxCols;
+  MTF_CUDA(cudaMemsetAsync(t.cm.p, 0, size_t(2) * kTcaMaxCols * sizeof(unsigned), st));
   // H = V^H W: units (basis group g, a piece of the entry chunks)
-  MTF_LAUNCH(KID_DOTS, st, k_tca_colmax32<<<dim3(64, unsigned(s)), 256, 0, st>>>(W, t.ldn, t.ldn, cmw));
+  MTF_LAUNCH(KID_DOTS, st, k_tca_colmax32<<<dim3(64, unsigned(nc)), 256, 0, st>>>(W, t.ldn, t.ldn, cmw));
   const int64_t nthr = int64_t(t.nkc) * NB * 8;
-  MTF_LAUNCH(KID_DOTS, st, k_tca_w_to_b<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(W, t.ldn, s, t.nkc, NB, cmw,
+  MTF_LAUNCH(KID_DOTS, st, k_tca_w_to_b<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(W, t.ldn, nc, t.nkc, NB, cmw,
                                                                                       t.Bd.p));
   const int g_used = (nq + kTcRows - 1) / kTcRows;
   const int P = std::max(1, std::min(t.nkc, (4 * t.n_cta + g_used - 1) / g_used));
@@ -299,32 +309,40 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, double* H, unsigned* 
   ud.a = t.nkc;
   ud.b = L;
   ud.c = Pn;
-  prof_bytes(KID_DOTS, double(nq + s) * double(t.ldn) * 8.0);
-  tca_launch<NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, 0, cmw, err, KID_DOTS, st);
-  MTF_LAUNCH(KID_DOTS, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * s + 255) / 256), 256, 0, st>>>(
-      t.part.p, NB, Pn, nq, s, cmw, H));
+  prof_bytes(KID_DOTS, double(nq + nc) * double(t.ldn) * 8.0);
+  tca_launch<NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
+  MTF_LAUNCH(KID_DOTS, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * nc + 255) / 256), 256, 0, st>>>(
+      t.part.p, NB, Pn, nq, nc, cmw, H, ldh));
   // W -= V H: one unit per entry group, over the basis chunks in use
-  MTF_LAUNCH(KID_AXPY, st, k_tca_colmax64<<<dim3(8, unsigned(s)), 256, 0, st>>>(H, nq, s, cmh));
+  MTF_LAUNCH(KID_AXPY, st, k_tca_colmax64<<<dim3(8, unsigned(nc)), 256, 0, st>>>(H, nq, ldh, cmh));
   const int nbc_used = (nq + 31) / 32;
   const int64_t nthu = int64_t(nbc_used) * NB * 8;
-  MTF_LAUNCH(KID_AXPY, st, k_tca_h_to_b<<<unsigned((nthu + 255) / 256), 256, 0, st>>>(H, nq, s, nbc_used, NB, cmh,
-                                                                                      t.Bu.p));
+  MTF_LAUNCH(KID_AXPY, st, k_tca_h_to_b<<<unsigned((nthu + 255) / 256), 256, 0, st>>>(H, nq, nc, ldh, nbc_used, NB,
+                                                                                      cmh, t.Bu.p));
   TcUnits uu;
   uu.kind = 2;
   uu.a = t.nbc;
   uu.b = nbc_used;
-  prof_bytes(KID_AXPY, double(nq + 2 * s) * double(t.ldn) * 8.0);
-  tca_launch<NB, 1>(t, t.vu_map, t.bu_map, uu, t.E, W, t.ldn, cmh, err, KID_AXPY, st);
+  prof_bytes(KID_AXPY, double(nq + 2 * nc) * double(t.ldn) * 8.0);
+  tca_launch<NB, 1>(t, t.vu_map, t.bu_map, uu, t.E, W, nc, t.ldn, cmh, err, KID_AXPY, st);
 }
 
-// H (nq x s, FP64, leading dimension s) = V^H W, then W -= V H, for the
-// first nq basis vectors stored by tca_store
-void tca_project(TcArnoldi& t, int nq, float* W, double* H, unsigned* err, cudaStream_t st) {
-  MTF_REQUIRE(nq >= 1 && int64_t(nq) <= int64_t(t.m + 1) * t.s, MTF_ERR_ARG, "tensor-core Arnoldi: basis size");
-  if (t.nb == 16) tca_project_nb<16>(t, nq, W, H, err, st);
-  else if (t.nb == 32) tca_project_nb<32>(t, nq, W, H, err, st);
-  else if (t.nb == 64) tca_project_nb<64>(t, nq, W, H, err, st);
-  else tca_project_nb<128>(t, nq, W, H, err, st);
+// H[q, c] (q < nq, c < nc; complex FP64 at H + 2 (q ldh + c)) = V^H W, then
+// W -= V H, for the first nq basis vectors stored by tca_store and the nc
+// columns of W (stride ldn), in passes of up to 64 columns
+void tca_project(TcArnoldi& t, int nq, float* W, int nc, double* H, int ldh, unsigned* err, cudaStream_t st) {
+  MTF_REQUIRE(nq >= 1 && int64_t(nq) <= int64_t(t.m + 1) * t.s && nc >= 1, MTF_ERR_ARG,
+              "tensor-core Arnoldi: basis size");
+  for (int c0 = 0; c0 < nc; c0 += kTcaMaxCols) {
+    const int w = std::min(kTcaMaxCols, nc - c0);
+    float* Wg = W + 2 * int64_t(c0) * t.ldn;
+    double* Hg = H + 2 * c0;
+    const int nb = tca_nb(w);
+    if (nb == 16) tca_project_nb<16>(t, nq, Wg, w, Hg, ldh, err, st);
+    else if (nb == 32) tca_project_nb<32>(t, nq, Wg, w, Hg, ldh, err, st);
+    else if (nb == 64) tca_project_nb<64>(t, nq, Wg, w, Hg, ldh, err, st);
+    else tca_project_nb<128>(t, nq, Wg, w, Hg, ldh, err, st);
+  }
 }
 
 }  // namespace mtf

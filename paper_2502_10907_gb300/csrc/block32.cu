@@ -1,14 +1,18 @@
 // Block flexible GMRES cycle of the mixed-precision inner solver: the nrhs
 // right-hand sides of a solve share ONE Krylov space.  Block step j applies
-// block-OSRC and the operator to the s = nrhs basis vectors V_j together
-// (Z_j = P V_j, W = M Z_j), orthogonalises W against all earlier basis
+// block-OSRC and the operator to the s = nrhs basis vectors together
+// (Z_j = P V~_j, W = M Z_j), orthogonalises W against all earlier basis
 // vectors by block classical Gram-Schmidt applied twice (BCGS2: the
-// projections are skinny matrix products H = V^H W and W -= V H), and
-// normalises it by a deflating Cholesky factorisation of its Gram matrix
-// (host, block_krylov.h), W = V_{j+1} R_{j+1}.  The block Hessenberg matrix
-// is reduced by a progressive Householder QR on the host, which gives every
-// right-hand side's residual estimate after each step; the update is
-// x += Z Y with the least-squares coefficients Y.
+// projections are skinny matrix products S = V^H X and X -= V S, on the
+// tensor cores) and normalises it by a deflating Cholesky factorisation of
+// its Gram matrix on the device.  The second Gram-Schmidt pass of a block is
+// lagged by one step and shares the pass over the basis with the next
+// block's first, so each step reads the basis twice (dots, update) instead
+// of four times; the Hessenberg column block of step j is completed by step
+// j + 1.  The block Hessenberg matrix is reduced by a progressive
+// Householder QR on the host (block_krylov.h), which gives every right-hand
+// side's residual estimate after each step; the update is x += Z Y with the
+// least-squares coefficients Y.
 //
 // Why: at the same iteration count the block space is s times larger than
 // each single-vector space, so a block step does the work of s single steps
@@ -38,25 +42,22 @@ TcArnoldi* tca_create();
 void tca_destroy(TcArnoldi* t);
 void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st);
 void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st);
-void tca_project(TcArnoldi& t, int nq, float* W, double* H, unsigned* err, cudaStream_t st);
+void tca_project(TcArnoldi& t, int nq, float* W, int nc, double* H, int ldh, unsigned* err, cudaStream_t st);
 
 struct BlockWork {
   int s = 0, m = 0;
   int64_t n = 0, ldn = 0;
   TcArnoldi* tca = nullptr;  // tensor-core projections (arnoldi_tc.cu), with mv_tensor
-  DevBuf<float> V, Z, W, D;  // (m + 1) s, m s, s, s vectors
-  DevBuf<double> H;          // Gpre (s x s) | H1 ((m+1) s x s) | H2 | G (s x s), complex
+  DevBuf<float> V, Z, X, D;  // (m + 1) s, m s, 2 s ([V~_J | W]), s vectors
+  DevBuf<double> S[2];       // projection coefficients of two steps: (m + 1) s x 2 s, complex
+  DevBuf<double> Gs;         // Gpre (s x s) | G2 (2s x 2s) | G (s x s) | Hc ((m + 1) s x s) | Rn | R | Rv | Cc
   DevBuf<double> C;          // s x s (complex, FP64) transform, or the coefficients Y (m s x s)
-  DevBuf<double> Cd;         // R1, T1, R2, T2 of a step's Cholesky factorisations (complex s x s each)
-  DevBuf<int> kept;          // kept flags of the two factorisations
+  DevBuf<int> kept;          // keptR (s) | keptV (s)
   double* h_host = nullptr;
   double* pin = nullptr;     // two pinned slots of a step's coefficients
   int* kept_host = nullptr;  // two pinned slots of kept flags and the error word
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  // the space of the solve's previous cycle, kept for the next one
   BlockLSQ lsq;
-  bool rec_ok = false;
-  int vshift = 0;
   ~BlockWork() {
     if (h_host) cudaFreeHost(h_host);
     if (pin) cudaFreeHost(pin);
@@ -285,7 +286,7 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
 
 // Deflating Cholesky factor of a block's Gram matrix on the device (the
 // rule of deflating_cholesky in block_krylov.h): G (complex FP64, entry
-// [q s + c] = <W_q, W_c>) = R^H R with R upper triangular; direction k is
+// [q ldg + c] = <W_q, W_c>) = R^H R with R upper triangular; direction k is
 // dropped (row k of R zero, kept[k] = 0) when its Schur pivot is not above
 // tau^2 ref_k, ref_k = the diagonal of Gpre (squared norms before the
 // Gram-Schmidt projections) or, with mask, 1 for mask[k] != 0 and 0
@@ -293,28 +294,28 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
 // One CTA of 256 threads, s <= 64: per pivot the row of R is formed in
 // parallel and the trailing upper triangle is updated by all threads (the
 // Schur complement and R in shared memory, s * s complex each).
-__global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, const double* __restrict__ Gpre,
+__global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int ldg, const double* __restrict__ Gpre,
                                                const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
                                                int* __restrict__ kept) {
   extern __shared__ double2 sh[];
   double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c
   double2* Rs = sh + s * s;  // Rs[c * s + i] = R(i, c)
-  __shared__ double piv;
-  __shared__ int keep;
+  __shared__ double piv, refs[64];
+  __shared__ int keep, keeps[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < s * s; t += nt) {
     const int c = t / s, i = t % s;
-    A[t] = make_double2(G[2 * (i * s + c)], G[2 * (i * s + c) + 1]);
+    A[t] = make_double2(G[2 * (i * ldg + c)], G[2 * (i * ldg + c) + 1]);
     Rs[t] = make_double2(0.0, 0.0);
   }
+  for (int k = tid; k < s; k += nt) refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : Gpre[2 * (k * s + k)];
   for (int k = 0; k < s; ++k) {
     __syncthreads();
     if (tid == 0) {
       const double d = A[k * s + k].x;
-      const double ref = mask ? (mask[k] ? 1.0 : 0.0) : Gpre[2 * (k * s + k)];
-      keep = (d > tau * tau * fmax(ref, 0.0) && d > 0.0) ? 1 : 0;
+      keep = (d > tau * tau * fmax(refs[k], 0.0) && d > 0.0) ? 1 : 0;
       piv = keep ? sqrt(d) : 0.0;
-      kept[k] = keep;
+      keeps[k] = keep;
     }
     __syncthreads();
     if (!keep) continue;
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, con
     R[2 * t] = Rs[t].x;
     R[2 * t + 1] = Rs[t].y;
   }
+  for (int k = tid; k < s; k += nt) kept[k] = keeps[k];
 }
 
 // out_q[k] = (in_q[k] - sum_{p < q} out_p[k] R(p, q)) / R(q, q) for kept q,
@@ -379,6 +381,111 @@ __global__ void __launch_bounds__(128) k_btrsm(const float* __restrict__ in, int
     const float2 iv = inv[q];
     v[q] = make_float2(a.x * iv.x - a.y * iv.y, a.x * iv.y + a.y * iv.x);
     reinterpret_cast<float2*>(out + 2 * int64_t(q) * ldo)[k] = v[q];
+  }
+}
+
+// R = the identity on the kept set (zero rows elsewhere), kept_out = kept_in:
+// the start block of a cycle is already orthonormal (no lagged second pass)
+__global__ void k_beye(const int* __restrict__ kept_in, int s, double* __restrict__ R, int* __restrict__ kept_out) {
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    const int c = t / s, i = t % s;
+    R[2 * t] = (c == i && kept_in[i]) ? 1.0 : 0.0;
+    R[2 * t + 1] = 0.0;
+  }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) kept_out[i] = kept_in[i];
+}
+
+// C = R^-H G_vw on the kept set (rows of dropped directions zero): the
+// coordinates of W' along V_J = V~' R^-1, from the Gram matrix of [V~', W']
+// (G_vw entry (i, c) at G + 2 (i ldg + s + c)).  C complex FP64 at
+// C + 2 (i s + c), the layout of the update's coefficients.  R, G_vw and C
+// are staged in shared memory (3 s^2 complex); thread c solves column c.
+__global__ void k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
+                        const int* __restrict__ kept, int s, double* __restrict__ C) {
+  extern __shared__ double2 sh[];
+  double2* Rs = sh;              // Rs[i * s + p] = R(p, i)
+  double2* Gs = sh + s * s;      // Gs[i * s + c] = G_vw(i, c)
+  double2* Cs = Gs + s * s;      // Cs[i * s + c]
+  __shared__ int ks[64];
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    const int i = t / s, c = t % s;
+    Rs[t] = make_double2(R[2 * t], R[2 * t + 1]);
+    Gs[t] = make_double2(G[2 * (i * ldg + s + c)], G[2 * (i * ldg + s + c) + 1]);
+  }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) ks[i] = kept[i];
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < s) {
+    for (int i = 0; i < s; ++i) {
+      double re = 0.0, im = 0.0;
+      if (ks[i]) {
+        re = Gs[i * s + c].x;
+        im = Gs[i * s + c].y;
+        for (int p = 0; p < i; ++p) {  // - conj(R(p, i)) C[p, c]
+          const double2 r = Rs[i * s + p], x = Cs[p * s + c];
+          re -= r.x * x.x + r.y * x.y;
+          im -= r.x * x.y - r.y * x.x;
+        }
+        const double2 d = Rs[i * s + i];  // divide by conj(R(i, i))
+        const double dn = d.x * d.x + d.y * d.y;
+        const double nr = (re * d.x - im * d.y) / dn, ni = (re * d.y + im * d.x) / dn;
+        re = nr;
+        im = ni;
+      }
+      Cs[i * s + c] = make_double2(re, im);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    C[2 * t] = Cs[t].x;
+    C[2 * t + 1] = Cs[t].y;
+  }
+}
+
+// Column block J - 1 of the block Hessenberg matrix, completed by step J
+// (the second Gram-Schmidt pass of block J - 1's successor is lagged one
+// step): with Sw = columns s .. 2s-1 of step J-1's coefficients, Sv =
+// columns 0 .. s-1 of step J's (leading dimension 2 s both), C and R of
+// step J - 1 and Rv of step J,
+//   h[q, c] = Sw[q, c] + (Sv R)[q, c]            for q < nq0 = (J - 1) s,
+//   h[q, c] = C[q - nq0, c] + (Sv R)[q, c]       for nq0 <= q < nq0 + s,
+//   Rn = Rv R                                     (the subdiagonal block).
+// h complex FP64 at h + 2 (q s + c); R, Rv, Rn column-major.  Thread (q, c).
+__global__ void k_bhcol(const double* __restrict__ Sprev, const double* __restrict__ Scur,
+                        const double* __restrict__ Cp, const double* __restrict__ Rp, const double* __restrict__ Rv,
+                        int nq0, int s, double* __restrict__ h, double* __restrict__ Rn) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nh = int64_t(nq0 + s) * s;
+  const int ls = 2 * s;
+  if (t < nh) {
+    const int q = int(t / s), c = int(t % s);
+    double re, im;
+    if (q < nq0) {
+      re = Sprev[2 * (int64_t(q) * ls + s + c)];
+      im = Sprev[2 * (int64_t(q) * ls + s + c) + 1];
+    } else {
+      re = Cp[2 * ((q - nq0) * s + c)];
+      im = Cp[2 * ((q - nq0) * s + c) + 1];
+    }
+    for (int p = 0; p <= c; ++p) {  // R upper triangular: R(p, c) at [c s + p]
+      const double ar = Scur[2 * (int64_t(q) * ls + p)], ai = Scur[2 * (int64_t(q) * ls + p) + 1];
+      const double br = Rp[2 * (c * s + p)], bi = Rp[2 * (c * s + p) + 1];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+    h[2 * t] = re;
+    h[2 * t + 1] = im;
+  } else if (t < nh + int64_t(s) * s) {
+    const int u = int(t - nh), c = u / s, i = u % s;
+    double re = 0.0, im = 0.0;
+    for (int p = i; p <= c; ++p) {  // Rv(i, p) R(p, c)
+      const double ar = Rv[2 * (p * s + i)], ai = Rv[2 * (p * s + i) + 1];
+      const double br = Rp[2 * (c * s + p)], bi = Rp[2 * (c * s + p) + 1];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+    Rn[2 * (c * s + i)] = re;
+    Rn[2 * (c * s + i) + 1] = im;
   }
 }
 
@@ -485,11 +592,8 @@ static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept
 // stay orthogonal to the basis to about 1e-2 after normalisation
 constexpr double kDeflateTau = 1e-5;
 
-// kept restarts in a row (each widens the least-squares band by one block)
-constexpr int kMaxKeep = 2;
-
 mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t st, int cycle) {
+                          std::vector<int>& iters, bool& reached, cudaStream_t st) {
   MTF_REQUIRE(s >= 1 && s <= 64, MTF_ERR_ARG, "block FGMRES supports 1..64 right-hand sides");
   mtf_mesh msh = sys->mesh;
   const int64_t n = msh->n_total;
@@ -499,18 +603,21 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   if (!sys->bw) sys->bw = new BlockWork();
   BlockWork& B = *sys->bw;
   stream_prepare(sys, st);  // error word of the bounded waits
-  const size_t hsz = size_t(2) * (s * s + 2 * size_t(m + 1) * s * s + s * s);
+  const size_t nhc = size_t(m + 1) * s * s;  // complex entries of a Hessenberg column block
+  const size_t gsz = size_t(2) * (size_t(s) * s + 4 * size_t(s) * s + size_t(s) * s + nhc + 4 * size_t(s) * s);
+  // pinned slot of a step (doubles): column block (nhc complex) | Rn (s x s complex)
+  const size_t slot_len = 2 * nhc + 2 * size_t(s) * s;
   if (B.s != s || B.m != m || B.n != n) {
     B.V.alloc(size_t(m + 1) * s * ldn * 2);
     B.Z.alloc(size_t(m) * s * ldn * 2);
-    B.W.alloc(size_t(s) * ldn * 2);
+    B.X.alloc(size_t(2) * s * ldn * 2);
     B.D.alloc(size_t(s) * ldn * 2);
     MTF_CUDA(cudaMemsetAsync(B.V.p, 0, B.V.n * sizeof(float), st));
     MTF_CUDA(cudaMemsetAsync(B.Z.p, 0, B.Z.n * sizeof(float), st));
-    MTF_CUDA(cudaMemsetAsync(B.W.p, 0, B.W.n * sizeof(float), st));
-    B.H.alloc(hsz);
+    MTF_CUDA(cudaMemsetAsync(B.X.p, 0, B.X.n * sizeof(float), st));
+    for (auto& b : B.S) b.alloc(size_t(2) * (m + 1) * s * 2 * s);
+    B.Gs.alloc(gsz);
     B.C.alloc(size_t(2) * std::max<size_t>(size_t(s) * s, size_t(m) * s * s));
-    B.Cd.alloc(size_t(8) * s * s);
     B.kept.alloc(size_t(2) * s);
     if (B.h_host) cudaFreeHost(B.h_host);
     if (B.pin) cudaFreeHost(B.pin);
@@ -518,8 +625,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     B.h_host = nullptr;
     B.pin = nullptr;
     B.kept_host = nullptr;
-    MTF_CUDA(cudaMallocHost(&B.h_host, hsz * sizeof(double)));
-    const size_t slot_len = 4 * size_t(m + 1) * s * s + 4 * size_t(s) * s + 2 * size_t(s) + 1;
+    MTF_CUDA(cudaMallocHost(&B.h_host, 2 * size_t(s) * s * sizeof(double)));
     MTF_CUDA(cudaMallocHost(&B.pin, 2 * slot_len * sizeof(double)));
     MTF_CUDA(cudaMallocHost(&B.kept_host, 2 * (2 * size_t(s) + 1) * sizeof(int)));
     for (auto& e : B.ev)
@@ -528,31 +634,23 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     B.m = m;
     B.n = n;
     B.ldn = ldn;
-    B.rec_ok = false;
   }
-  double* Gpre = B.H.p;
-  double* H1 = Gpre + 2 * size_t(s) * s;
-  double* H2 = H1 + 2 * size_t(m + 1) * s * s;
-  double* G = H2 + 2 * size_t(m + 1) * s * s;
+  double* Gpre = B.Gs.p;                       // s x s: Gram of W before the projections
+  double* G2 = Gpre + 2 * size_t(s) * s;       // 2s x 2s: Gram of [V~', W']
+  double* G = G2 + 8 * size_t(s) * s;          // s x s: Gram of W''
+  double* Hc = G + 2 * size_t(s) * s;          // completed column block ((m + 1) s x s)
+  double* Rn = Hc + 2 * nhc;                   // its subdiagonal block
+  double* R = Rn + 2 * size_t(s) * s;          // W'' = V~_{J+1} R
+  double* Rv = R + 2 * size_t(s) * s;          // V~' = V_J Rv
+  double* Cc = Rv + 2 * size_t(s) * s;         // W' = V_J Cc + W''
+  int* keptR = B.kept.p;
+  int* keptV = keptR + s;
   const int64_t vstride = int64_t(s) * ldn;  // complex entries per block of s vectors
-  std::vector<cdouble> Gh(size_t(s) * s), R(size_t(s) * s), T(size_t(s) * s);
-  std::vector<double> ref(s), Tup(size_t(2) * s * s), est(s, 0.0);
+  float* X0 = B.X.p;                          // V~_J (then V~')
+  float* X1 = B.X.p + 2 * vstride;            // W (then W', W'')
+  std::vector<cdouble> Gh(size_t(s) * s), R0(size_t(s) * s), T(size_t(s) * s);
+  std::vector<double> Tup(size_t(2) * s * s), est(s, 0.0);
   std::vector<int> kept;
-  auto fetch_gram = [&](const double* dev, std::vector<cdouble>& out) {
-    // device layout [q * s + c] = <W_q, W_c>; column-major G[c * s + q] equals it
-    for (int q = 0; q < s; ++q)
-      for (int c = 0; c < s; ++c) {
-        const double* p = B.h_host + (dev - B.H.p) + 2 * (size_t(q) * s + c);
-        out[size_t(c) * s + q] = cdouble(p[0], p[1]);
-      }
-  };
-  auto upload_T = [&](const std::vector<cdouble>& Tm) {
-    for (size_t t = 0; t < Tm.size(); ++t) {
-      Tup[2 * t] = Tm[t].real();
-      Tup[2 * t + 1] = Tm[t].imag();
-    }
-    MTF_CUDA(cudaMemcpyAsync(B.C.p, Tup.data(), Tup.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  };
   // the Gram-Schmidt projections run on the tensor cores with the matvec
   const bool tc = sys->opt.mv_tensor != 0;
   if (tc) {
@@ -560,28 +658,28 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     tca_prepare(*B.tca, s, m, ldn, st);
   }
   unsigned* err_word = sys->d_mv_ctl.p + 2;
-  const double tau = kDeflateTau;
-  auto project = [&](int nq) {  // W <- (I - V V^H)^2 W against the first nq basis vectors; H1, H2 the coefficients
+  // X[:, 0 .. nc) -= V S and S = V^H X against the first nq basis vectors (S leading dimension 2 s)
+  auto project = [&](int nq, int nc, double* S) {
     if (tc) {
-      tca_project(*B.tca, nq, B.W.p, H1, err_word, st);
-      tca_project(*B.tca, nq, B.W.p, H2, err_word, st);
+      tca_project(*B.tca, nq, B.X.p, nc, S, 2 * s, err_word, st);
     } else {
-      MTF_CUDA(cudaMemsetAsync(H1, 0, 2 * size_t(nq) * s * sizeof(double), st));
-      MTF_CUDA(cudaMemsetAsync(H2, 0, 2 * size_t(nq) * s * sizeof(double), st));
-      bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H1, s, st);
-      bupdate(B.V.p, nq, ldn, H1, s, B.W.p, ldn, s, ldn, st);
-      bdots(sys, B.V.p, nq, ldn, B.W.p, ldn, s, ldn, H2, s, st);
-      bupdate(B.V.p, nq, ldn, H2, s, B.W.p, ldn, s, ldn, st);
+      MTF_CUDA(cudaMemsetAsync(S, 0, 2 * size_t(nq) * 2 * s * sizeof(double), st));
+      bdots(sys, B.V.p, nq, ldn, B.X.p, ldn, nc, ldn, S, 2 * s, st);
+      bupdate(B.V.p, nq, ldn, S, 2 * s, B.X.p, ldn, nc, ldn, st);
     }
   };
 
-  // the residual block: W = r (FP32) and its Gram matrix (norms ||r_c||)
-  MTF_LAUNCH(KID_NORM, st, k_blk_to32<<<dim3(nbk(ldn, 256), unsigned(s)), 256, 0, st>>>(r_dev, n, B.W.p, ldn));
+  // the residual block: X1 = r (FP32), its Gram matrix (norms ||r_c||) and
+  // the start block V_0 = r T by the host's deflating Cholesky factor
+  MTF_LAUNCH(KID_NORM, st, k_blk_to32<<<dim3(nbk(ldn, 256), unsigned(s)), 256, 0, st>>>(r_dev, n, X1, ldn));
   MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
-  bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
-  MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+  bdots(sys, X1, s, ldn, X1, ldn, s, ldn, G, s, st);
+  MTF_CUDA(cudaMemcpyAsync(B.h_host, G, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
   MTF_CUDA(cudaStreamSynchronize(st));
-  fetch_gram(G, Gh);
+  // device layout [q * s + c] = <W_q, W_c>; column-major G[c * s + q] equals it
+  for (int q = 0; q < s; ++q)
+    for (int c = 0; c < s; ++c)
+      Gh[size_t(c) * s + q] = cdouble(B.h_host[2 * (size_t(q) * s + c)], B.h_host[2 * (size_t(q) * s + c) + 1]);
   std::vector<double> bnorm(s), ref0(s);
   for (int c = 0; c < s; ++c) {
     const double d = Gh[size_t(c) * s + c].real();
@@ -589,82 +687,42 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     bnorm[c] = std::sqrt(std::max(d, 0.0));
     ref0[c] = d;
   }
-  // Restart that keeps the space (the next refinement cycle of one solve):
-  // the new residual is projected on the basis built so far, its remainder
-  // opens a new start block, and the new column blocks are orthogonalised
-  // against the whole basis, so the cycle does not rebuild the slow start
-  // of the previous one.  Column block J then multiplies basis block
-  // J + vshift (vshift = kept restarts so far).
   BlockLSQ& lsq = B.lsq;
-  const int nb_old = lsq.k + 1 + B.vshift;
-  const bool keep = cycle > 0 && sys->opt.recycle >= 2 && B.rec_ok && lsq.s == s && B.vshift < kMaxKeep &&
-                    nb_old + 16 <= m;
-  B.rec_ok = false;
-  bool grow = true;  // the start block has a kept direction
-  if (!keep) {
+  {
     // dependent or zero residual columns are deflated from the start
-    const int nk0 = deflating_cholesky(s, Gh.data(), ref0.data(), 1e-12, R.data(), T.data(), kept);
+    const int nk0 = deflating_cholesky(s, Gh.data(), ref0.data(), 1e-12, R0.data(), T.data(), kept);
     reached = nk0 == 0;
     if (reached) return MTF_OK;
-    upload_T(T);
-    bxform(B.W.p, ldn, B.C.p, s, B.V.p, ldn, ldn, st);
-    if (tc) tca_store(*B.tca, B.V.p, 0, st);
-    lsq.init(s, m, R.data(), bnorm.data(), 1 + kMaxKeep);
-    B.vshift = 0;
-  } else {
-    const int nq_old = nb_old * s;
-    project(nq_old);
-    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
-    bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (H1 - B.H.p), H1, 2 * size_t(nq_old) * s * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (H2 - B.H.p), H2, 2 * size_t(nq_old) * s * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(B.h_host + (G - B.H.p), G, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaStreamSynchronize(st));
-    fetch_gram(G, Gh);
-    const int nk0 = deflating_cholesky(s, Gh.data(), ref0.data(), tau, R.data(), T.data(), kept);
-    const size_t nr = size_t(nq_old + s);
-    std::vector<cdouble> G0(nr * s);
-    const double* hp1 = B.h_host + (H1 - B.H.p);
-    const double* hp2 = B.h_host + (H2 - B.H.p);
-    for (int c = 0; c < s; ++c) {
-      for (int q = 0; q < nq_old; ++q) {
-        const size_t o = 2 * (size_t(q) * s + c);
-        G0[size_t(c) * nr + q] = cdouble(hp1[o] + hp2[o], hp1[o + 1] + hp2[o + 1]);
-      }
-      for (int i = 0; i < s; ++i) G0[size_t(c) * nr + nq_old + i] = R[size_t(c) * s + i];
+    for (size_t t = 0; t < T.size(); ++t) {
+      Tup[2 * t] = T[t].real();
+      Tup[2 * t + 1] = T[t].imag();
     }
-    for (const cdouble& v : G0)
-      if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return MTF_ERR_NAN;
-    upload_T(T);
-    float* V0 = B.V.p + 2 * int64_t(nb_old) * vstride;
-    bxform(B.W.p, ldn, B.C.p, s, V0, ldn, ldn, st);
-    if (tc) tca_store(*B.tca, V0, nq_old, st);
-    lsq.restart(G0.data(), nb_old + 1, bnorm.data(), est.data());
-    B.vshift += 1;
-    bool all = true;
-    for (int c = 0; c < s; ++c) all = all && est[c] <= tol;
-    reached = all;
-    grow = !all && nk0 > 0;
+    MTF_CUDA(cudaMemcpyAsync(B.C.p, Tup.data(), Tup.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    bxform(X1, ldn, B.C.p, s, B.V.p, ldn, ldn, st);
+    if (tc) tca_store(*B.tca, B.V.p, 0, st);
+    MTF_CUDA(cudaMemcpyAsync(keptR, kept.data(), size_t(s) * sizeof(int), cudaMemcpyHostToDevice, st));
+    MTF_CUDA(cudaStreamSynchronize(st));  // T and kept are host memory
+    lsq.init(s, m, R0.data(), bnorm.data());
   }
-  const int vshift = B.vshift;
-  const int J0 = lsq.k;
 
-  // Pipelined block steps.  Everything of step J runs on the device --
-  // block-OSRC, the matvec, both Gram-Schmidt projections, the deflating
-  // Cholesky factorisations (two: CholQR2) and the next basis block -- and
-  // its coefficients (H1, H2, R1, R2, the kept flags and the error word) are
-  // copied to a pinned slot; the host queues step J + 1 before it reads step
-  // J's slot, so that the least-squares update of step J overlaps the device
-  // work of step J + 1.  A step computed past convergence is discarded.
-  // Column block J multiplies basis block J + vshift and produces block
-  // J + vshift + 1; the basis holds m + 1 blocks and Z holds m.
-  const int Jend = std::min(m - vshift, J0 + std::max(1, max_iter));
-  double* R1 = B.Cd.p;
-  double* R2 = R1 + 2 * size_t(s) * s;
-  int* kept1 = B.kept.p;
-  int* kept2 = kept1 + s;
+  // Pipelined block steps with the second Gram-Schmidt pass lagged by one
+  // step.  Step J applies block-OSRC and the operator to V~_J, the block
+  // orthogonalised once against the basis and normalised (Z_J = P V~_J,
+  // W = M Z_J), and then, in ONE pass over the basis blocks 0 .. J - 1,
+  // projects both V~_J (its second pass) and W (its first):
+  //   [V~', W'] = [V~_J, W] - V [Sv, Sw].
+  // V~' = V_J Rv (Cholesky of its Gram, the second CholQR pass) gives the
+  // final block V_J; W' = V_J Cc + W'' (Cc = Rv^-H V~'^H W') and
+  // W'' = V~_{J+1} R (Cholesky) the next lagged block.  Since
+  // V~_J = V Sv + V_J Rv, column block J - 1 of the Hessenberg matrix,
+  // M Z_{J-1} = V [Sw; Cc] + V~_J R, is completed by step J (k_bhcol).
+  // Every kernel of a step runs on the device; its column block and kept
+  // flags go to a pinned slot, and the host queues step J + 1 before it
+  // reads step J's slot, so the least-squares update overlaps the device.
+  // The last step of a cycle only finishes V~ (no operator apply).  A step
+  // computed past convergence is discarded.  The basis holds m + 1 blocks
+  // and Z holds m.
+  const int Jend = std::min(m, std::max(1, max_iter));  // column blocks of this cycle
   {
     static std::atomic<uint64_t> opted{0};
     int dev = 0;
@@ -672,112 +730,113 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(opted.load() & bit)) {
       MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
+      MTF_CUDA(cudaFuncSetAttribute(k_bcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 64 * 64 * 16));
       opted.fetch_or(bit);
     }
   }
   const size_t chol_smem = 2 * size_t(s) * s * sizeof(double2);
-  // pinned slot layout (doubles): H1 (m+1) s s complex | H2 | R1 | R2; kept flags and error word separately
-  const size_t slot_h = 2 * size_t(m + 1) * s * s;
-  const size_t slot_len = 2 * slot_h + 4 * size_t(s) * s + 2 * size_t(s) + 1;
   auto slot = [&](int J) { return B.pin + size_t(J & 1) * slot_len; };
   auto launch_step = [&](int J) {
-    const int vb = J + vshift;
-    float* Vj = B.V.p + 2 * int64_t(vb) * vstride;
-    float* Zj = B.Z.p + 2 * int64_t(J) * vstride;
-    if (pre) {
-      launch_osrc_apply_f32(sys, Vj, ldn, Zj, ldn, s, st);
-    } else {
-      MTF_CUDA(cudaMemcpyAsync(Zj, Vj, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
+    const bool finish = J == Jend;
+    double* Scur = B.S[J & 1].p;
+    const double* Sprev = B.S[(J + 1) & 1].p;
+    float* Vt = B.V.p + 2 * int64_t(J) * vstride;  // V~_J; V_J after the step
+    const int nq = J * s;
+    const int nc = finish ? s : 2 * s;
+    if (!finish) {
+      float* Zj = B.Z.p + 2 * int64_t(J) * vstride;
+      if (pre) {
+        launch_osrc_apply_f32(sys, Vt, ldn, Zj, ldn, s, st);
+      } else {
+        MTF_CUDA(cudaMemcpyAsync(Zj, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
+      }
+      launch_matvec_f32(sys, Zj, ldn, X1, ldn, s, st);
+      MTF_CUDA(cudaMemsetAsync(Gpre, 0, 2 * size_t(s) * s * sizeof(double), st));
+      bdots(sys, X1, s, ldn, X1, ldn, s, ldn, Gpre, s, st);
     }
-    launch_matvec_f32(sys, Zj, ldn, B.W.p, ldn, s, st);
-    const int nq = (vb + 1) * s;
-    MTF_CUDA(cudaMemsetAsync(Gpre, 0, 2 * size_t(s) * s * sizeof(double), st));
-    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
-    bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, Gpre, s, st);
-    project(nq);
-    bdots(sys, B.W.p, s, ldn, B.W.p, ldn, s, ldn, G, s, st);
-    MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, Gpre, nullptr, tau, s, R1, kept1));
-    btrsm(B.W.p, ldn, R1, kept1, s, B.D.p, ldn, ldn, st);
-    // second pass (CholQR2): the first leaves V = W R^-1 orthonormal only
-    // to about cond(W) times the FP32 rounding; V_next = V R2^-1, R = R2 R1
-    MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
-    bdots(sys, B.D.p, s, ldn, B.D.p, ldn, s, ldn, G, s, st);
-    MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, nullptr, kept1, 1e-3, s, R2, kept2));
-    float* Vn = B.V.p + 2 * int64_t(vb + 1) * vstride;
-    btrsm(B.D.p, ldn, R2, kept2, s, Vn, ldn, ldn, st);
-    if (tc) tca_store(*B.tca, Vn, (vb + 1) * s, st);
+    MTF_CUDA(cudaMemcpyAsync(X0, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
+    if (nq > 0) project(nq, nc, Scur);
+    MTF_CUDA(cudaMemsetAsync(G2, 0, 8 * size_t(s) * s * sizeof(double), st));
+    bdots(sys, B.X.p, nc, ldn, B.X.p, ldn, nc, ldn, G2, 2 * s, st);
+    if (J == 0) {
+      MTF_LAUNCH(KID_BCHOL, st, k_beye<<<1, 256, 0, st>>>(keptR, s, Rv, keptV));
+    } else {
+      // second CholQR pass of V~_J: directions that the first kept
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G2, 2 * s, nullptr, keptR, 1e-3, s, Rv, keptV));
+      MTF_LAUNCH(KID_BXFORM, st, k_bhcol<<<nbk(int64_t(nq + s) * s, 256), 256, 0, st>>>(
+          Sprev, Scur, Cc, R, Rv, nq - s, s, Hc, Rn));
+    }
+    if (!finish) {
+      if (J > 0) btrsm(X0, ldn, Rv, keptV, s, Vt, ldn, ldn, st);
+      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 3 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
+      bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
+      MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
+      bdots(sys, X1, s, ldn, X1, ldn, s, ldn, G, s, st);
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R, keptR));
+      btrsm(X1, ldn, R, keptR, s, Vt + 2 * vstride, ldn, ldn, st);
+      if (tc && J > 0) tca_store(*B.tca, Vt, J * s, st);
+    }
     double* sl = slot(J);
-    MTF_CUDA(cudaMemcpyAsync(sl, H1, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(sl + slot_h, H2, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(sl + 2 * slot_h, R1, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(sl + 2 * slot_h + 2 * size_t(s) * s, R2, 2 * size_t(s) * s * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(B.kept_host + size_t(J & 1) * (2 * s + 1), kept1, 2 * size_t(s) * sizeof(int),
-                             cudaMemcpyDeviceToHost, st));
-    MTF_CUDA(cudaMemcpyAsync(B.kept_host + size_t(J & 1) * (2 * s + 1) + 2 * s, err_word, sizeof(int),
-                             cudaMemcpyDeviceToHost, st));
+    if (J > 0) {
+      MTF_CUDA(cudaMemcpyAsync(sl, Hc, 2 * size_t(nq) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+      MTF_CUDA(cudaMemcpyAsync(sl + 2 * nhc, Rn, 2 * size_t(s) * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    int* kh = B.kept_host + size_t(J & 1) * (2 * s + 1);
+    MTF_CUDA(cudaMemcpyAsync(kh, keptR, 2 * size_t(s) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MTF_CUDA(cudaMemcpyAsync(kh + 2 * s, err_word, sizeof(int), cudaMemcpyDeviceToHost, st));
     MTF_CUDA(cudaEventRecord(B.ev[J & 1], st));
   };
 
-  std::vector<cdouble> h, Rr1(size_t(s) * s), Rr2(size_t(s) * s), Rn(size_t(s) * s);
+  std::vector<cdouble> h, Rnh(size_t(s) * s);
   int steps = 0;
   mtf_status status = MTF_OK;
-  if (!reached && grow && J0 < Jend) {
-    launch_step(J0);
-    for (int J = J0; J < Jend; ++J) {
-      if (J + 1 < Jend) launch_step(J + 1);
-      MTF_CUDA(cudaEventSynchronize(B.ev[J & 1]));
-      const double* sl = slot(J);
-      const int* kh = B.kept_host + size_t(J & 1) * (2 * s + 1);
-      if (kh[2 * s] != 0) {
-        status = MTF_ERR_TIMEOUT;
-        break;
-      }
-      const int nq = (J + vshift + 1) * s;
-      h.assign(size_t(nq) * s, cdouble(0));
-      bool finite = true;
-      for (int q = 0; q < nq; ++q)
-        for (int c = 0; c < s; ++c) {
-          const size_t o = 2 * (size_t(q) * s + c);
-          const cdouble v(sl[o] + sl[slot_h + o], sl[o + 1] + sl[slot_h + o + 1]);
-          finite = finite && std::isfinite(v.real()) && std::isfinite(v.imag());
-          h[size_t(c) * nq + q] = v;
-        }
-      const double* r1 = sl + 2 * slot_h;
-      const double* r2 = r1 + 2 * size_t(s) * s;
-      for (size_t t = 0; t < size_t(s) * s; ++t) {
-        Rr1[t] = cdouble(r1[2 * t], r1[2 * t + 1]);
-        Rr2[t] = cdouble(r2[2 * t], r2[2 * t + 1]);
-      }
-      if (!finite) {
-        status = MTF_ERR_NAN;
-        break;
-      }
-      for (int c = 0; c < s; ++c)
-        for (int i = 0; i < s; ++i) {
-          cdouble a = 0;
-          if (i <= c)
-            for (int p = i; p <= c; ++p) a += Rr2[size_t(p) * s + i] * Rr1[size_t(c) * s + p];
-          Rn[size_t(c) * s + i] = a;
-        }
-      if (!lsq.add_block(h.data(), nq / s, Rn.data(), est.data())) break;
-      ++steps;
-      int nk = 0;
-      for (int c = 0; c < s; ++c) nk += kh[c];
-      bool all = true;
-      for (int c = 0; c < s; ++c) {
-        if (!std::isfinite(est[c])) status = MTF_ERR_NAN;
-        all = all && est[c] <= tol;
-      }
-      if (status != MTF_OK) break;
-      if (all) {
-        reached = true;
-        break;
-      }
-      if (nk == 0) break;  // the space is exhausted: the next cycle starts from the new residual
+  launch_step(0);
+  for (int J = 0; J <= Jend; ++J) {
+    if (J + 1 <= Jend) launch_step(J + 1);
+    MTF_CUDA(cudaEventSynchronize(B.ev[J & 1]));
+    const int* kh = B.kept_host + size_t(J & 1) * (2 * s + 1);
+    if (kh[2 * s] != 0) {
+      status = MTF_ERR_TIMEOUT;
+      break;
     }
-    MTF_CUDA(cudaStreamSynchronize(st));  // a step queued past the last one has finished
+    if (J == 0) continue;
+    // column block J - 1: rows of blocks 0 .. J - 1 and the subdiagonal block
+    const double* sl = slot(J);
+    const int nq = J * s;
+    h.assign(size_t(nq) * s, cdouble(0));
+    bool finite = true;
+    for (int q = 0; q < nq; ++q)
+      for (int c = 0; c < s; ++c) {
+        const size_t o = 2 * (size_t(q) * s + c);
+        const cdouble v(sl[o], sl[o + 1]);
+        finite = finite && std::isfinite(v.real()) && std::isfinite(v.imag());
+        h[size_t(c) * nq + q] = v;
+      }
+    for (size_t t = 0; t < size_t(s) * s; ++t) {
+      Rnh[t] = cdouble(sl[2 * nhc + 2 * t], sl[2 * nhc + 2 * t + 1]);
+      finite = finite && std::isfinite(Rnh[t].real()) && std::isfinite(Rnh[t].imag());
+    }
+    if (!finite) {
+      status = MTF_ERR_NAN;
+      break;
+    }
+    if (!lsq.add_block(h.data(), J, Rnh.data(), est.data())) break;
+    ++steps;
+    bool all = true;
+    for (int c = 0; c < s; ++c) {
+      if (!std::isfinite(est[c])) status = MTF_ERR_NAN;
+      all = all && est[c] <= tol;
+    }
+    if (status != MTF_OK) break;
+    if (all) {
+      reached = true;
+      break;
+    }
+    int nk = 0;  // directions of V_J
+    for (int c = 0; c < s; ++c) nk += kh[s + c];
+    if (nk == 0) break;  // the space is exhausted: the next cycle starts from the new residual
   }
+  MTF_CUDA(cudaStreamSynchronize(st));  // a step queued past the last one has finished
   if (status != MTF_OK) {
     MTF_CUDA(cudaMemsetAsync(sys->d_mv_ctl.p, 0, 4 * sizeof(unsigned), st));
     return status;
@@ -802,7 +861,6 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     MTF_LAUNCH(KID_AXPY, st, k_blk_addx<<<dim3(nbk(n, 256), unsigned(s)), 256, 0, st>>>(x_dev, n, B.D.p, ldn));
   }
   MTF_CUDA(cudaStreamSynchronize(st));  // host buffers are released on return
-  B.rec_ok = true;
   return MTF_OK;
 }
 

@@ -15,12 +15,7 @@
 // problem is E_1 S_0, S_0 the factor of the start block; after the
 // reflectors of block j, rows (j+1)s .. (j+2)s - 1 of its column c hold the
 // residual of right-hand side c.
-//
-// A restart that keeps the space (the next cycle continues the basis and
-// projects its new residual onto it) gives column blocks whose h reaches one
-// basis block further per kept restart: the lower bandwidth of a column block
-// is then 2, 3, ... blocks, its reflectors reach as far, and the right-hand
-// sides are replaced by the new residual's coordinates (restart()).
+
 #pragma once
 
 #include <algorithm>
@@ -101,15 +96,13 @@ inline void parallel_for(int n, int threads, const std::function<void(int)>& f) 
 struct BlockLSQ {
   int s = 0, m = 0;          // block size, maximum number of column blocks
   int k = 0;                 // column blocks added
-  int bwmax = 1;             // largest lower bandwidth (in blocks) of a column block
-  std::vector<int> bw;       // lower bandwidth of every column block
   // reduced block columns: column block j holds rows 0 .. (j+1) s - 1 of its
   // s columns (column-major, leading dimension (j+1) s), at offset off[j]
   std::vector<cdouble> Rt;
   std::vector<size_t> off;
-  // reflectors: block j, reflector kk: (1 + bwmax) s entries (top rows
-  // kk .. s-1 of block row j, then the bw[j] s rows below block row j) and
-  // the scalar beta (I - beta v v^H)
+  // reflectors: block j, reflector kk: 2 s entries (top rows kk .. s-1 of
+  // block row j, then the s rows of block row j + 1) and the scalar beta
+  // (I - beta v v^H)
   std::vector<cdouble> refl;
   std::vector<double> beta;
   std::vector<cdouble> g;    // ldg x s, column-major: the least-squares right-hand sides
@@ -118,17 +111,15 @@ struct BlockLSQ {
   int threads = 1;
 
   // S0: the start block's factor (s x s column-major), r = V_0 S0
-  void init(int s_, int m_, const cdouble* S0, const double* base_norm, int bwmax_ = 1) {
+  void init(int s_, int m_, const cdouble* S0, const double* base_norm) {
     s = s_;
     m = m_;
-    bwmax = std::max(1, bwmax_);
     k = 0;
-    bw.assign(size_t(m), 1);
     Rt.clear();
     off.assign(size_t(m) + 1, 0);
-    refl.assign(size_t(m) * s * (1 + bwmax) * s, cdouble(0));
+    refl.assign(size_t(m) * s * 2 * s, cdouble(0));
     beta.assign(size_t(m) * s, 0.0);
-    ldg = size_t(m + bwmax + 1) * s;
+    ldg = size_t(m + 2) * s;
     g.assign(ldg * s, cdouble(0));
     for (int c = 0; c < s; ++c)
       for (int i = 0; i < s; ++i) g[size_t(c) * ldg + i] = S0[size_t(c) * s + i];
@@ -138,55 +129,29 @@ struct BlockLSQ {
     threads = int(std::max(1u, std::min(hw, 16u)));
   }
 
-  // apply reflector (j, kk) to one column x (rows j s .. (j + 1 + bw[j]) s - 1)
+  // apply reflector (j, kk) to one column x (rows j s + kk .. (j + 2) s - 1)
   inline void apply_reflector(int j, int kk, cdouble* x) const {
     const double b = beta[size_t(j) * s + kk];
     if (b == 0.0) return;
-    const cdouble* v = &refl[(size_t(j) * s + kk) * (1 + bwmax) * s];
+    const cdouble* v = &refl[(size_t(j) * s + kk) * 2 * s];
     cdouble* top = x + size_t(j) * s + kk;
-    const int len = s - kk + bw[size_t(j)] * s;
+    const int len = 2 * s - kk;
     cdouble a = 0;
     for (int t = 0; t < len; ++t) a += std::conj(v[t]) * top[t];
     a *= b;
     for (int t = 0; t < len; ++t) top[t] -= v[t] * a;
   }
 
-  // New right-hand sides for the space built so far (a restart that keeps
-  // the space): G0 holds nrows_blk s rows x s columns (column-major, leading
-  // dimension nrows_blk s), the coordinates of the new residual in the basis
-  // blocks 0 .. nrows_blk - 1.  The reflectors of the k column blocks are
-  // applied; est[c] = the residual of right-hand side c within the space.
-  void restart(const cdouble* G0, int nrows_blk, const double* base_norm, double* est) {
-    std::fill(g.begin(), g.end(), cdouble(0));
-    const size_t nr = size_t(nrows_blk) * s;
-    for (int c = 0; c < s; ++c) {
-      for (size_t i = 0; i < nr; ++i) g[size_t(c) * ldg + i] = G0[size_t(c) * nr + i];
-      bnorm[c] = base_norm[c] > 0 ? base_norm[c] : 1.0;
-    }
-    parallel_for(s, long(k) * s * s * s > 200000 ? threads : 1, [&](int c) {
-      for (int q = 0; q < k; ++q)
-        for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, &g[size_t(c) * ldg]);
-    });
-    for (int c = 0; c < s; ++c) {
-      double r2 = 0;
-      for (size_t i = size_t(k) * s; i < nr; ++i) r2 += std::norm(g[size_t(c) * ldg + i]);
-      est[c] = std::sqrt(r2) / bnorm[c];
-    }
-  }
-
-  // Add column block j = k: h (nrows_h s rows x s, column-major, leading
-  // dimension nrows_h s) on the basis blocks 0 .. nrows_h - 1 and the
-  // upper-triangular R (s x s) on block nrows_h; the lower bandwidth is
-  // nrows_h - j blocks (1 in a first cycle, 2 after one restart that kept
-  // the space, ...).  est[c] receives the relative residual estimate of
-  // right-hand side c.  Returns false when m blocks are stored or the
-  // bandwidth exceeds bwmax.
+  // Add column block j = k: h (nrows_h = j + 1 blocks of s rows x s,
+  // column-major, leading dimension nrows_h s) on the basis blocks
+  // 0 .. j and the upper-triangular R (s x s) on block j + 1.  est[c]
+  // receives the relative residual estimate of right-hand side c.  Returns
+  // false when m blocks are stored or nrows_h != j + 1.
   bool add_block(const cdouble* h, int nrows_h, const cdouble* R, double* est) {
     if (k >= m) return false;
     const int j = k;
     const int b = nrows_h - j;
-    if (b < 1 || b > bwmax) return false;
-    bw[size_t(j)] = b;
+    if (b != 1) return false;
     const size_t rows = size_t(nrows_h + 1) * s, hr = size_t(nrows_h) * s;
     std::vector<cdouble> col(rows * s);
     for (int c = 0; c < s; ++c) {
@@ -204,8 +169,8 @@ struct BlockLSQ {
     // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1
     for (int kk = 0; kk < s; ++kk) {
       cdouble* x = &col[size_t(kk) * rows] + size_t(j) * s + kk;
-      cdouble* v = &refl[(size_t(j) * s + kk) * (1 + bwmax) * s];
-      const int len = s - kk + b * s;
+      cdouble* v = &refl[(size_t(j) * s + kk) * 2 * s];
+      const int len = 2 * s - kk;
       double nrm2 = 0;
       for (int t = 0; t < len; ++t) nrm2 += std::norm(x[t]);
       const double nrm = std::sqrt(nrm2);
@@ -218,7 +183,7 @@ struct BlockLSQ {
       const cdouble ph = ax0 > 0 ? x0 / ax0 : cdouble(1.0);
       const cdouble alpha = -ph * nrm;  // x -> alpha e_0
       for (int t = 0; t < len; ++t) v[t] = x[t];
-      for (int t = len; t < (1 + bwmax) * s; ++t) v[t] = 0;
+      for (int t = len; t < 2 * s; ++t) v[t] = 0;
       v[0] -= alpha;
       double vn2 = 0;
       for (int t = 0; t < len; ++t) vn2 += std::norm(v[t]);
@@ -235,7 +200,7 @@ struct BlockLSQ {
     ++k;
     for (int c = 0; c < s; ++c) {
       double r2 = 0;
-      for (int i = 0; i < b * s; ++i) r2 += std::norm(g[size_t(c) * ldg + size_t(k) * s + i]);
+      for (int i = 0; i < s; ++i) r2 += std::norm(g[size_t(c) * ldg + size_t(k) * s + i]);
       est[c] = std::sqrt(r2) / bnorm[c];
     }
     return true;

@@ -155,7 +155,7 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
       MTF_REQUIRE(sys->opt.precond == MTF_PRECOND_NONE || sys->opt.precond == MTF_PRECOND_OSRC, MTF_ERR_ARG,
                   "unknown preconditioner");
       MTF_REQUIRE(sys->opt.osrc_half == 0 || sys->opt.osrc_half == 1, MTF_ERR_ARG, "osrc_half must be 0 or 1");
-      MTF_REQUIRE(sys->opt.recycle >= 0 && sys->opt.recycle <= 2, MTF_ERR_ARG, "recycle must be 0, 1 or 2");
+      MTF_REQUIRE(sys->opt.recycle == 0 || sys->opt.recycle == 1, MTF_ERR_ARG, "recycle must be 0 or 1");
       MTF_REQUIRE(sys->opt.residual_df == 0 || sys->opt.residual_df == 1, MTF_ERR_ARG,
                   "residual_df must be 0 or 1");
       MTF_REQUIRE(sys->opt.block_krylov == 0 || sys->opt.block_krylov == 1, MTF_ERR_ARG,

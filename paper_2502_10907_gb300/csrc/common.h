@@ -390,12 +390,9 @@ void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z,
 // s vectors, FP32 basis, FP64 Hessenberg sums; x += D.  Stops when every
 // right-hand side's estimate reaches tol relative to its ||r|| (reached =
 // true), after opt.restart block steps, after max_iter block steps or when
-// every direction is deflated; iters[c] += block steps.  cycle: index of the
-// cycle within the solve; with opt.recycle == 2 a later cycle continues the space
-// of the previous ones (its new residual projected on it) while there is
-// room in the restart length.
+// every direction is deflated; iters[c] += block steps.
 mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_dev, double tol, int max_iter,
-                          std::vector<int>& iters, bool& reached, cudaStream_t st, int cycle);
+                          std::vector<int>& iters, bool& reached, cudaStream_t st);
 void destroy_learned(LearnedState* l);
 // learned OSRC correction (learned.cu)
 int64_t learned_param_count(mtf_system sys);

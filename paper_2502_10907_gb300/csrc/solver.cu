@@ -610,7 +610,7 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       // systems with a learned correction keep the per-rhs spaces, so that
       // their plain and corrected solves compare like for like
       if (sys->opt.block_krylov && nrhs >= kBlockMinRhs && !sys->learned)
-        status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
+        status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s);
       else
         status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);
       if (status != MTF_OK) break;
