@@ -186,12 +186,20 @@ __global__ void k_tca_dots_reduce(const float* __restrict__ part, int nb, int P,
   if (t >= int64_t(nq) * s) return;
   const int q = int(t / s), c = int(t % s);
   const int g = q / kTcRows, row = q % kTcRows;
-  double re = 0, im = 0;
+  // FP32 partials added in double-float (two-sum: Knuth's error-free
+  // transformation) on the FP32 pipes, rounded to FP64 once
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (int p = 0; p < P; ++p) {
-    const float* pr = part + (size_t(g * P + p) * kTcRows + row) * nb + 2 * c;
-    re += double(pr[0]);
-    im += double(pr[1]);
+    const float2 v = *reinterpret_cast<const float2*>(part + (size_t(g * P + p) * kTcRows + row) * nb + 2 * c);
+    float s1 = rh + v.x, bb = s1 - rh;
+    rl += (rh - (s1 - bb)) + (v.x - bb);
+    rh = s1;
+    s1 = ih + v.y;
+    bb = s1 - ih;
+    il += (ih - (s1 - bb)) + (v.y - bb);
+    ih = s1;
   }
+  const double re = double(rh) + double(rl), im = double(ih) + double(il);
   const double sc = double(tca_inv_scale(colmax[c])) / double(kBasisScale);
   const int64_t o = 2 * (int64_t(q) * ldh + c);
   H[o] = re * sc;
@@ -294,12 +302,12 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
   unsigned* cmh = t.cm.p + kTcaMaxCols;
   MTF_CUDA(cudaMemsetAsync(t.cm.p, 0, size_t(2) * kTcaMaxCols * sizeof(unsigned), st));
   // H = V^H W: units (basis group g, a piece of the entry chunks)
-  MTF_LAUNCH(KID_DOTS, st, k_tca_colmax32<<<dim3(64, unsigned(nc)), 256, 0, st>>>(W, t.ldn, t.ldn, cmw));
+  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_colmax32<<<dim3(64, unsigned(nc)), 256, 0, st>>>(W, t.ldn, t.ldn, cmw));
   const int64_t nthr = int64_t(t.nkc) * NB * 8;
-  MTF_LAUNCH(KID_DOTS, st, k_tca_w_to_b<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(W, t.ldn, nc, t.nkc, NB, cmw,
+  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_w_to_b<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(W, t.ldn, nc, t.nkc, NB, cmw,
                                                                                       t.Bd.p));
   const int g_used = (nq + kTcRows - 1) / kTcRows;
-  const int P = std::max(1, std::min(t.nkc, (4 * t.n_cta + g_used - 1) / g_used));
+  const int P = std::max(1, std::min({t.nkc, 32, (4 * t.n_cta + g_used - 1) / g_used}));
   const int L = (t.nkc + P - 1) / P;
   const int Pn = (t.nkc + L - 1) / L;
   const int nu = g_used * Pn;
@@ -311,13 +319,13 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
   ud.c = Pn;
   prof_bytes(KID_DOTS, double(nq + nc) * double(t.ldn) * 8.0);
   tca_launch<NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
-  MTF_LAUNCH(KID_DOTS, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * nc + 255) / 256), 256, 0, st>>>(
+  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * nc + 255) / 256), 256, 0, st>>>(
       t.part.p, NB, Pn, nq, nc, cmw, H, ldh));
   // W -= V H: one unit per entry group, over the basis chunks in use
-  MTF_LAUNCH(KID_AXPY, st, k_tca_colmax64<<<dim3(8, unsigned(nc)), 256, 0, st>>>(H, nq, ldh, cmh));
+  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_colmax64<<<dim3(8, unsigned(nc)), 256, 0, st>>>(H, nq, ldh, cmh));
   const int nbc_used = (nq + 31) / 32;
   const int64_t nthu = int64_t(nbc_used) * NB * 8;
-  MTF_LAUNCH(KID_AXPY, st, k_tca_h_to_b<<<unsigned((nthu + 255) / 256), 256, 0, st>>>(H, nq, nc, ldh, nbc_used, NB,
+  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_h_to_b<<<unsigned((nthu + 255) / 256), 256, 0, st>>>(H, nq, nc, ldh, nbc_used, NB,
                                                                                       cmh, t.Bu.p));
   TcUnits uu;
   uu.kind = 2;

@@ -284,6 +284,18 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
   *xp = o;
 }
 
+// 1 / sqrt(d) for d > 0 in FP64: an FP32 seed refined by two Newton steps
+// y <- y (3 - d y^2) / 2 (quadratic convergence: 2^-22 -> 2^-43 -> rounding);
+// the narrow FP64 pipe makes this several times faster than sqrt and a
+// division.  Outside the FP32 range the FP64 library functions are used.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = double(rsqrtf(float(d)));
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  return y;
+}
+
 // Deflating Cholesky factor of a block's Gram matrix on the device (the
 // rule of deflating_cholesky in block_krylov.h): G (complex FP64, entry
 // [q ldg + c] = <W_q, W_c>) = R^H R with R upper triangular; direction k is
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
   extern __shared__ double2 sh[];
   double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c
   double2* Rs = sh + s * s;  // Rs[c * s + i] = R(i, c)
-  __shared__ double piv, refs[64];
+  __shared__ double piv, ipiv, refs[64];
   __shared__ int keep, keeps[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < s * s; t += nt) {
@@ -314,12 +326,16 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
     if (tid == 0) {
       const double d = A[k * s + k].x;
       keep = (d > tau * tau * fmax(refs[k], 0.0) && d > 0.0) ? 1 : 0;
-      piv = keep ? sqrt(d) : 0.0;
+      if (keep) {
+        const double y = rsqrt_newton(d);
+        piv = d * y;
+        ipiv = y;
+      }
       keeps[k] = keep;
     }
     __syncthreads();
     if (!keep) continue;
-    const double ip = 1.0 / piv;
+    const double ip = ipiv;
     for (int c = k + tid; c < s; c += nt) {
       const double2 a = A[c * s + k];
       Rs[c * s + k] = c == k ? make_double2(piv, 0.0) : make_double2(a.x * ip, a.y * ip);
@@ -399,40 +415,51 @@ __global__ void k_beye(const int* __restrict__ kept_in, int s, double* __restric
 // coordinates of W' along V_J = V~' R^-1, from the Gram matrix of [V~', W']
 // (G_vw entry (i, c) at G + 2 (i ldg + s + c)).  C complex FP64 at
 // C + 2 (i s + c), the layout of the update's coefficients.  R, G_vw and C
-// are staged in shared memory (3 s^2 complex); thread c solves column c.
-__global__ void k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
-                        const int* __restrict__ kept, int s, double* __restrict__ C) {
+// are staged in shared memory (3 s^2 complex) and the reciprocals of the
+// diagonal of R^H are formed first, in parallel; then one warp per column c
+// runs the forward substitution, its lanes splitting the sum over p.
+__global__ void __launch_bounds__(256) k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
+                                               const int* __restrict__ kept, int s, double* __restrict__ C) {
   extern __shared__ double2 sh[];
   double2* Rs = sh;              // Rs[i * s + p] = R(p, i)
   double2* Gs = sh + s * s;      // Gs[i * s + c] = G_vw(i, c)
   double2* Cs = Gs + s * s;      // Cs[i * s + c]
-  __shared__ int ks[64];
+  __shared__ double2 rinv[64];   // 1 / conj(R(i, i)), 0 for dropped i
   for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
     const int i = t / s, c = t % s;
     Rs[t] = make_double2(R[2 * t], R[2 * t + 1]);
     Gs[t] = make_double2(G[2 * (i * ldg + s + c)], G[2 * (i * ldg + s + c) + 1]);
   }
-  for (int i = threadIdx.x; i < s; i += blockDim.x) ks[i] = kept[i];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (kept[i]) {
+      const double dr = R[2 * (i * s + i)], di = R[2 * (i * s + i) + 1];
+      const double dn = dr * dr + di * di;  // 1 / (dr - i di) = (dr + i di) / |d|^2
+      v = make_double2(dr / dn, di / dn);
+    }
+    rinv[i] = v;
+  }
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < s; c += nw) {
     for (int i = 0; i < s; ++i) {
-      double re = 0.0, im = 0.0;
-      if (ks[i]) {
-        re = Gs[i * s + c].x;
-        im = Gs[i * s + c].y;
-        for (int p = 0; p < i; ++p) {  // - conj(R(p, i)) C[p, c]
-          const double2 r = Rs[i * s + p], x = Cs[p * s + c];
-          re -= r.x * x.x + r.y * x.y;
-          im -= r.x * x.y - r.y * x.x;
-        }
-        const double2 d = Rs[i * s + i];  // divide by conj(R(i, i))
-        const double dn = d.x * d.x + d.y * d.y;
-        const double nr = (re * d.x - im * d.y) / dn, ni = (re * d.y + im * d.x) / dn;
-        re = nr;
-        im = ni;
+      double re = 0.0, im = 0.0;  // sum over p < i of conj(R(p, i)) C[p, c]
+      for (int p = lane; p < i; p += 32) {
+        const double2 r = Rs[i * s + p], x = Cs[p * s + c];
+        re += r.x * x.x + r.y * x.y;
+        im += r.x * x.y - r.y * x.x;
       }
-      Cs[i * s + c] = make_double2(re, im);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) {
+        const double2 g = Gs[i * s + c], ri = rinv[i];
+        const double ar = g.x - re, ai = g.y - im;
+        Cs[i * s + c] = make_double2(ar * ri.x - ai * ri.y, ar * ri.y + ai * ri.x);
+      }
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -467,14 +494,18 @@ __global__ void k_bhcol(const double* __restrict__ Sprev, const double* __restri
       re = Cp[2 * ((q - nq0) * s + c)];
       im = Cp[2 * ((q - nq0) * s + c) + 1];
     }
+    // Sv holds the components V~_J kept along the earlier blocks after one
+    // projection (about the FP32 rounding times the block's condition), so
+    // its product with R is formed in FP32 and added to the FP64 part
+    float cr = 0.f, ci = 0.f;
     for (int p = 0; p <= c; ++p) {  // R upper triangular: R(p, c) at [c s + p]
-      const double ar = Scur[2 * (int64_t(q) * ls + p)], ai = Scur[2 * (int64_t(q) * ls + p) + 1];
-      const double br = Rp[2 * (c * s + p)], bi = Rp[2 * (c * s + p) + 1];
-      re += ar * br - ai * bi;
-      im += ar * bi + ai * br;
+      const float ar = float(Scur[2 * (int64_t(q) * ls + p)]), ai = float(Scur[2 * (int64_t(q) * ls + p) + 1]);
+      const float br = float(Rp[2 * (c * s + p)]), bi = float(Rp[2 * (c * s + p) + 1]);
+      cr = fmaf(ar, br, fmaf(-ai, bi, cr));
+      ci = fmaf(ar, bi, fmaf(ai, br, ci));
     }
-    h[2 * t] = re;
-    h[2 * t + 1] = im;
+    h[2 * t] = re + double(cr);
+    h[2 * t + 1] = im + double(ci);
   } else if (t < nh + int64_t(s) * s) {
     const int u = int(t - nh), c = u / s, i = u % s;
     double re = 0.0, im = 0.0;
@@ -496,7 +527,7 @@ static int col_tier(int s) { return s <= 1 ? 1 : s <= 2 ? 2 : s <= 4 ? 4 : s <= 
 
 // H[q, c0 + c] += V_q^H W_{c0 + c} over all column groups of 16
 static void bdots(mtf_system sys, const float* V, int nq, int64_t ldv, const float* W, int64_t ldw, int s, int64_t n_pad,
-                  double* H, int ldh, cudaStream_t st) {
+                  double* H, int ldh, cudaStream_t st, int kid = KID_BGRAM) {
   (void)sys;
   if (nq <= 0) return;
   for (int c0 = 0; c0 < s; c0 += 16) {
@@ -504,16 +535,17 @@ static void bdots(mtf_system sys, const float* V, int nq, int64_t ldv, const flo
     const int SC = col_tier(nc);
     const int VW = SC >= 16 ? 2 : 4;
     const int gy = (nq + 8 * VW - 1) / (8 * VW);
-    // segments so that about 600 CTAs run
-    const int64_t nseg0 = std::max<int64_t>(1, std::min<int64_t>((n_pad + 127) / 128, (600 + gy - 1) / gy));
+    // segments so that about two CTAs per SM run, each over at least 8
+    // chunks of 128 entries (fewer FP64 atomics per coefficient)
+    const int64_t nseg0 = std::max<int64_t>(1, std::min<int64_t>((n_pad + 1023) / 1024, (304 + gy - 1) / gy));
     const int64_t seg = ((n_pad + nseg0 - 1) / nseg0 + 127) / 128 * 128;
     const dim3 grid(unsigned((n_pad + seg - 1) / seg), unsigned(gy));
     const float* Wc = W + 2 * int64_t(c0) * ldw;
     double* Hc = H + 2 * c0;
     // basis and block read once
-    prof_bytes(KID_DOTS, double(nq + nc) * double(n_pad) * 8.0);
+    prof_bytes(kid, double(nq + nc) * double(n_pad) * 8.0);
 #define MTF_BDOTS(SCV, VWV) \
-  MTF_LAUNCH(KID_DOTS, st, k_bdots<SCV, VWV><<<grid, 256, 0, st>>>(V, nq, ldv, Wc, ldw, nc, seg, n_pad, Hc, ldh))
+  MTF_LAUNCH(kid, st, k_bdots<SCV, VWV><<<grid, 256, 0, st>>>(V, nq, ldv, Wc, ldw, nc, seg, n_pad, Hc, ldh))
     if (SC == 16) MTF_BDOTS(16, 2);
     else if (SC == 8) MTF_BDOTS(8, 4);
     else if (SC == 4) MTF_BDOTS(4, 4);
@@ -664,7 +696,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
       tca_project(*B.tca, nq, B.X.p, nc, S, 2 * s, err_word, st);
     } else {
       MTF_CUDA(cudaMemsetAsync(S, 0, 2 * size_t(nq) * 2 * s * sizeof(double), st));
-      bdots(sys, B.V.p, nq, ldn, B.X.p, ldn, nc, ldn, S, 2 * s, st);
+      bdots(sys, B.V.p, nq, ldn, B.X.p, ldn, nc, ldn, S, 2 * s, st, KID_DOTS);
       bupdate(B.V.p, nq, ldn, S, 2 * s, B.X.p, ldn, nc, ldn, st);
     }
   };
@@ -768,7 +800,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     }
     if (!finish) {
       if (J > 0) btrsm(X0, ldn, Rv, keptV, s, Vt, ldn, ldn, st);
-      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 3 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
+      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 256, 3 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
       bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
       MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
       bdots(sys, X1, s, ldn, X1, ldn, s, ldn, G, s, st);

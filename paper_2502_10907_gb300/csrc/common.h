@@ -235,7 +235,7 @@ enum KernelId {
   KID_REGULAR64 = 0, KID_SINGULAR64, KID_XVALUES, KID_RHS, KID_MATVEC64, KID_DOTS, KID_AXPY,
   KID_NORM, KID_SUB, KID_FARFIELD, KID_SPLIT, KID_REGULAR32, KID_MATVEC32, KID_OSRC, KID_MLP,
   KID_MISC, KID_MVCOMBINE, KID_OSCOMBINE, KID_MVTC, KID_MVTC_PREP, KID_MVTC_COMBINE, KID_TC_TILE,
-  KID_BCHOL, KID_BXFORM, KID_BSTORE, KID_TT, KID_TT_MMA, KID_COUNT
+  KID_BCHOL, KID_BXFORM, KID_BSTORE, KID_TT, KID_TT_MMA, KID_TCA_PREP, KID_BGRAM, KID_COUNT
 };
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);

@@ -4,6 +4,9 @@
 // for the number of library kernels launched in a timed region.
 #include <vector>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.h"
 
 namespace mtf {
@@ -13,11 +16,15 @@ static const char* kNames[KID_COUNT] = {
     "gmres_axpy", "gmres_norm_scale", "gmres_sub", "farfield", "split_block",
     "regular32", "matvec32", "osrc_apply", "mlp", "misc", "matvec32_combine", "osrc_combine",
     "matvec_tc", "matvec_tc_prep", "matvec_tc_combine", "tc_tile", "block_cholesky", "block_xform",
-    "basis_store", "osrc_form_prep", "osrc_form_mma"};
+    "basis_store", "osrc_form_prep", "osrc_form_mma", "gs_prep", "block_gram"};
 
+// Counters shared by every host thread that launches library kernels (the
+// batched solve drives its instances from several threads): launch counts are
+// atomic, the rest is guarded by mu.
 struct Prof {
-  bool on = false;
-  int64_t launches[KID_COUNT] = {};
+  std::mutex mu;
+  std::atomic<bool> on{false};
+  std::atomic<int64_t> launches[KID_COUNT] = {};
   double ms[KID_COUNT] = {};
   double bytes[KID_COUNT] = {};  // algorithmic bytes declared by the launch sites
   struct Rec {
@@ -41,14 +48,19 @@ static Prof g_prof;
 static thread_local cudaEvent_t t_begin = nullptr;
 
 void prof_begin(int kid, cudaStream_t s) {
-  if (!g_prof.on) return;
-  t_begin = g_prof.get();
+  (void)kid;
+  if (!g_prof.on.load(std::memory_order_relaxed)) return;
+  {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    t_begin = g_prof.get();
+  }
   MTF_CUDA(cudaEventRecord(t_begin, s));
 }
 
 void prof_end(int kid, cudaStream_t s) {
-  g_prof.launches[kid] += 1;
-  if (!g_prof.on || !t_begin) return;
+  g_prof.launches[kid].fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof.on.load(std::memory_order_relaxed) || !t_begin) return;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
   cudaEvent_t e = g_prof.get();
   MTF_CUDA(cudaEventRecord(e, s));
   g_prof.pending.push_back({kid, t_begin, e});
@@ -68,16 +80,21 @@ static void resolve() {
 }
 
 void prof_enable(bool on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!on) resolve();
   g_prof.on = on;
 }
 
-void prof_bytes(int kid, double b) { g_prof.bytes[kid] += b; }
+void prof_bytes(int kid, double b) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.bytes[kid] += b;
+}
 
 void prof_read(int n, int64_t* launches, double* ms, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
   resolve();
   for (int k = 0; k < n && k < KID_COUNT; ++k) {
-    if (launches) launches[k] = g_prof.launches[k];
+    if (launches) launches[k] = g_prof.launches[k].load();
     if (ms) ms[k] = g_prof.ms[k];
     if (bytes) bytes[k] = g_prof.bytes[k];
     g_prof.launches[k] = 0;
