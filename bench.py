@@ -56,6 +56,11 @@ FLOPS_PER_EVAL = 57
 # cores, whose tiled rows carry up to 144 bytes of padding each); keyed by
 # (kernel, n_total, nrhs), absent for other workloads
 NCU_TRAFFIC = {("matvec32", 13068, 2): 232.30e6, ("osrc_apply", 13068, 2): 60.09e6}
+# DRAM traffic over algorithmic bytes of the tensor-core Gram-Schmidt streams
+# (ncu --set full, one launch each at block step 61 of the 25,920-unknown
+# cube, 16 right-hand sides; both read the basis once, so their traffic grows
+# with the basis vectors read and is scaled to the launch by this ratio)
+NCU_TRAFFIC_RATIO = {("gmres_dots", 16): 232.91e6 / 209.00e6, ("gmres_axpy", 16): 216.31e6 / 215.65e6}
 
 
 def _stream_bytes(name, Ns, n_total, nrhs):
@@ -431,6 +436,66 @@ def kernel_table(prof):
     return out
 
 
+def batch_instances(api, L, args):
+    """The batched workload: 32 uneven instances (spheres cut by 1..15
+    parallel planes into slab subdomains, rotated, 500-5,000 skeleton
+    triangles, k0 U[1, 4], eps_r U[1.5, 6]), 8 plane waves each, mixed path
+    with block-OSRC at tol 1e-8 (the error of these thin-slab instances is
+    up to about 600 times the residual).  Every system is autotuned for 8
+    right-hand sides once; then the batch (mtf_solve_batch, instances
+    concurrent) is timed against a loop of mtf_solve over the same systems.
+    Accuracy: the largest relative residual over all instances, and the
+    solution error of the three largest instances against the FP64 solution
+    of fp64_reference (FP64 residuals of the FP64 assembly, refined to
+    1e-11; a plain FP64 GMRES stagnates on them at 3e-4 to 3e-2 after 6,000
+    iterations)."""
+    import torch
+    cfgs = mi.config_batch_instances(n_inst=32, seed=0, tri_range=(500, 5000), nrhs=8)
+    t0 = time.perf_counter()
+    meshes = [api.Mesh.from_inputs(c["mesh"]) for c in cfgs]
+    opts = dict(precision=L.MTF_PREC_MIXED, precond=L.MTF_PRECOND_OSRC, tol=1e-8, restart=500, max_iter=4000,
+                osrc_np=args.osrc_np)
+    systems = [api.System(m, c["k0"], c["eps_r"], c["mu_r"], **opts) for m, c in zip(meshes, cfgs)]
+    t_setup = time.perf_counter() - t0
+    chosen = {}
+    for s in systems:
+        plan = s.autotune(8, reps=3)[-1].replace("chosen ", "")
+        chosen[plan] = chosen.get(plan, 0) + 1
+    dirs = [c["dirs"] for c in cfgs]
+    pols = [c["pols"] for c in cfgs]
+    nrhs_tot = sum(len(d) for d in dirs)
+    api.solve_batch(systems, dirs, pols, raise_on_noconv=False)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xs, st = api.solve_batch(systems, dirs, pols, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for s, d, p in zip(systems, dirs, pols):
+        s.solve(d, p, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    big = sorted(range(len(cfgs)), key=lambda i: -int(meshes[i].n_total))[:3]
+    errs = []
+    for i in big:
+        xr, _ = fp64_reference(api, L, meshes[i], cfgs[i], 500, args.osrc_np)
+        errs.append(float(((xs[i] - xr).norm(dim=1) / xr.norm(dim=1)).max()))
+    n_tot = [int(m.n_total) for m in meshes]
+    return {"workload": "32 cut spheres, 500-5000 skeleton triangles, 2-16 slab subdomains, 8 plane waves each",
+            "instances": len(cfgs), "nrhs_total": nrhs_tot, "unknowns_min_max": [min(n_tot), max(n_tot)],
+            "unknowns_total": sum(n_tot), "setup_seconds": round(t_setup, 2),
+            "batch": {"value": nrhs_tot / t_batch, "unit": UNIT, "seconds": t_batch,
+                      "how": "mtf_solve_batch: instances on their own streams, 8 host worker threads"},
+            "loop": {"value": nrhs_tot / t_loop, "unit": UNIT, "seconds": t_loop, "how": "mtf_solve per instance"},
+            "batch_over_loop": t_loop / t_batch,
+            "autotune_choices": chosen,
+            "converged": all(bool(x.converged) for x in st),
+            "max_rel_residual": max(float(x.rel_residual) for x in st),
+            "gmres_tol": 1e-8,
+            "solution_rel_err_vs_fp64_three_largest": errs,
+            "timing": "host wall clock around each synchronous call (the batch synchronises its streams)"}
+
+
 def secondary_split_sphere(api, L, args, stream):
     """The split-sphere workload (3 blocks, 13,068 unknowns, 2 waves): the
     mixed path, the plain FP64 block-OSRC GMRES and the learned correction on
@@ -612,7 +677,30 @@ def main():
     hbm, bf16, src = _peaks()
     launches = sum(v[0] for v in launches_timed.values())
     roof = roofline_of(prof, counts, sysg.opt.n_ss, hbm, src)
+    # ALU rooflines of the assembly kernels against the device's measured
+    # FP32 / FP64 rates (the library's own FMA-chain probes)
+    peaks = L.mtf_probe_peaks()
+    asm_roof = []
+    for name in ("regular32", "regular64", "singular64"):
+        nl, tms, _ = prof.get(name, (0, 0.0, 0.0))
+        if not nl or tms <= 0:
+            continue
+        per = tms / nl / 1e3
+        if name.startswith("regular"):
+            fl, pk = counts[3] * 36 * FLOPS_PER_EVAL, peaks[0 if name == "regular32" else 1]
+        else:
+            npts, per_pair = {0: 6, 1: 5, 2: 2}, {0: 1, 1: 2, 2: 2}
+            fl = sum(int(counts[c]) // per_pair[c] * npts[c] * sysg.opt.n_ss ** 4 for c in range(3)) * 75
+            pk = peaks[1]
+        asm_roof.append({"kernel": name, "bound": "alu", "achieved": fl / per / 1e12, "peak": pk / 1e12,
+                         "unit": "TFLOP/s", "frac": fl / per / pk, "ms_per_launch": per * 1e3,
+                         "peak_source": "measured (mtf_probe_peaks: FP32 / FP64 FMA chains)"})
     roof["traffic"] = NCU_TRAFFIC.get((roof["kernel"], int(mesh.n_total), nrhs))
+    ratio = NCU_TRAFFIC_RATIO.get((roof["kernel"], nrhs))
+    if roof["traffic"] is None and ratio is not None and roof.get("algorithmic_bytes_per_launch"):
+        roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
+        roof["traffic_source"] = ("ncu DRAM bytes / algorithmic bytes of one launch of the 25,920-unknown cube "
+                                  "(16 rhs), times this launch's algorithmic bytes")
 
     # ---- end to end through the C-ABI from host buffers ---------------------
     # The step of the timed region (materials re-assembled, plane waves
@@ -652,8 +740,10 @@ def main():
     del sh, mh
 
     secondary = None
+    batch = None
     if rank == 0 and world == 1 and not args.no_comparisons and args.workload != "split_sphere":
         secondary = secondary_split_sphere(api, L, args, stream)
+        batch = batch_instances(api, L, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -675,7 +765,10 @@ def main():
                        else "FP64",
                        "l2": "inputs larger than L2 (dense blocks re-assembled each step)",
                        "parallelism": f"replicas x{world}"},
-            "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3},
+            "assembly": {"value": n_pairs / t_asm, "unit": "triangle-pairs/s", "ms": t_asm * 1e3,
+                         "roofline": asm_roof},
+            "alu_peaks_measured": {"fp32_tflops": peaks[0] / 1e12, "fp64_tflops": peaks[1] / 1e12,
+                                   "sfu_gresults_per_s": peaks[2] / 1e9},
             "solution_rel_err_vs_fp64": err,
             "fp64_reference": ref_info,
             "gmres_iterations": int(statistics.median(iters)),
@@ -695,6 +788,7 @@ def main():
                                             "mtf_solve + mtf_farfield from host arrays"},
             "cpu_baseline": cpu,
             "secondary": secondary,
+            "batched_instances": batch,
             "learned_correction": {"enabled": False, "note": "not run on this workload: the learned correction keeps "
                                    "per-rhs Krylov spaces, so its validation solves would cost minutes here; it is "
                                    "reported on the split-sphere line under 'secondary'"}

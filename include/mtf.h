@@ -305,6 +305,51 @@ mtf_status mtf_solve_rhs(mtf_system sys, int32_t nrhs, const void* b, void* x_ou
 mtf_status mtf_solve_static(mtf_system sys, int32_t nrhs, const double* dirs, const double* pols,
                             void* x_out, mtf_solve_stats* stats, void* stream);
 
+/* Batched solve of independent problems: each instance is Problem 2 on its
+ * own system, solved as mtf_solve solves it (Sec. 5.3 stopping rule per
+ * right-hand side).  The paper solves one scatterer at a time; the batch is
+ * this library's, for workloads of many small, uneven instances whose single
+ * solves leave most of the GPU idle (their kernels are short and their
+ * steps wait on each other).  Instance i solves the nrhs[i] plane waves
+ * dirs[i], pols[i] (host, laid out as for mtf_solve) on systems[i] into
+ * x_out[i] (device complex128 n_total_i x nrhs[i]).  The instances run
+ * concurrently: each on its own CUDA stream, driven by a pool of host worker
+ * threads (at most `threads`; threads <= 0 selects min(n, 8)), largest
+ * instance (n_total x nrhs) first.  They start after the work queued on
+ * `stream` before the call, and the call returns when every instance has
+ * finished.  systems: n distinct handles, all on the current device (a
+ * system must not be used by two calls at once).  stats: host array of n
+ * entries, may be NULL.  Returns MTF_OK, or the status of the
+ * lowest-indexed failing instance (every instance runs to its end);
+ * MTF_ERR_ARG for n < 1, null arrays or a repeated system. */
+mtf_status mtf_solve_batch(int32_t n, const mtf_system* systems, const int32_t* nrhs, const double* const* dirs,
+                           const double* const* pols, void* const* x_out, mtf_solve_stats* stats, int32_t threads,
+                           void* stream);
+
+/* Arithmetic-peak probes of the current device (a measurement utility of
+ * this library; no counterpart in the paper): rates[0] = FP32 FLOP/s (fused
+ * multiply-add chains, an FMA counts 2), rates[1] = FP64 FLOP/s, rates[2] =
+ * special-function results per second (single-precision sine on the SFU).
+ * Independent chains per thread over 8 CTAs of 256 threads per SM, timed
+ * with CUDA events on `stream` after one warm-up launch; about 2 ms.
+ * rates: host, 3 doubles. */
+mtf_status mtf_probe_peaks(double* rates, void* stream);
+
+/* Autotuner of the mixed inner solver's operator applies (this library's;
+ * no counterpart in the paper).  For nrhs right-hand sides per apply it times
+ * the candidate launch plans of mtf_matvec_f32 on the system -- the FMA
+ * stream (one pass per 4 right-hand sides) and the tensor-core kernel with
+ * work units of {2, 8}-chunk minimum pieces at {2, 4, 8} units per CTA on
+ * all SMs or half of them -- with CUDA events on `stream` (one warm-up and
+ * `reps` timed applies each, on a fixed input), and keeps the fastest for
+ * every later apply of the system (matvec and block-OSRC, which share the
+ * plan).  Applies to at most 4 right-hand sides always use the FMA stream,
+ * so for nrhs <= 4 only that candidate exists.  report: host, may be NULL:
+ * one line per candidate ("<plan> <mean ms>") and a last line "chosen
+ * <plan>", NUL-terminated within report_len bytes.  Mixed-precision systems
+ * with mv_tensor only (MTF_ERR_ARG otherwise); reps in 1..100. */
+mtf_status mtf_autotune(mtf_system sys, int32_t nrhs, int32_t reps, char* report, int32_t report_len, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned correction of the block-OSRC preconditioner (no counterpart in the
  * paper).  The preconditioner stays linear: z = P r + C r, P the block-OSRC

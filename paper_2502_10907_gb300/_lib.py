@@ -66,6 +66,9 @@ _SIGS = {
     "mtf_solve": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_static": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
     "mtf_solve_rhs": (_i32, [_vp, _i32, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _vp]),
+    "mtf_solve_batch": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(mtf_solve_stats), _i32, _vp]),
+    "mtf_autotune": (_i32, [_vp, _i32, _i32, ctypes.c_char_p, _i32, _vp]),
+    "mtf_probe_peaks": (_i32, [_vp, _vp]),
     "mtf_farfield": (_i32, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "mtf_system_destroy": (None, [_vp]),
     "mtf_learned_param_count": (_i64, [_vp]),
@@ -254,6 +257,37 @@ def mtf_solve_rhs(sys_, b, x_out, stream=0, raise_on_noconv=True):
     if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
         _check(status)
     return st, status
+
+
+def mtf_solve_batch(systems, dirs_list, pols_list, x_outs, threads=0, stream=0, raise_on_noconv=True):
+    """Instances solved concurrently: systems[i] with waves dirs_list[i], pols_list[i] into x_outs[i]."""
+    n = len(systems)
+    ds = [np.ascontiguousarray(d, dtype=np.float64) for d in dirs_list]
+    ps = [np.ascontiguousarray(p, dtype=np.complex128) for p in pols_list]
+    sysv = (ctypes.c_void_p * n)(*systems)
+    nr = (ctypes.c_int32 * n)(*[len(d) for d in ds])
+    dv = (ctypes.c_void_p * n)(*[_ptr(d) for d in ds])
+    pv = (ctypes.c_void_p * n)(*[_ptr(p) for p in ps])
+    xv = (ctypes.c_void_p * n)(*[_ptr(x) for x in x_outs])
+    st = (mtf_solve_stats * n)()
+    status = load().mtf_solve_batch(n, sysv, nr, dv, pv, xv, st, int(threads), stream or None)
+    if status != MTF_OK and (raise_on_noconv or status != MTF_ERR_NOCONV):
+        _check(status)
+    return list(st), status
+
+
+def mtf_probe_peaks(stream=0):
+    """Measured (FP32 FLOP/s, FP64 FLOP/s, SFU results/s) of the current device."""
+    r = np.zeros(3, dtype=np.float64)
+    _check(load().mtf_probe_peaks(_ptr(r), stream or None))
+    return tuple(float(v) for v in r)
+
+
+def mtf_autotune(sys_, nrhs, reps=5, stream=0):
+    """Times the apply plans for nrhs right-hand sides, keeps the fastest; returns the report lines."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().mtf_autotune(sys_, int(nrhs), int(reps), buf, len(buf), stream or None))
+    return buf.value.decode().strip().split("\n")
 
 
 def mtf_solve_static(sys_, dirs, pols, x_out, stream=0, raise_on_noconv=True):

@@ -171,6 +171,10 @@ class System:
         st, status = L.mtf_solve(self.handle, dirs, pols, x, _stream(), raise_on_noconv)
         return x, st
 
+    def autotune(self, nrhs, reps=5):
+        """Time the operator-apply plans for nrhs right-hand sides and keep the fastest (report lines)."""
+        return L.mtf_autotune(self.handle, nrhs, reps, _stream())
+
     def solve_rhs(self, b, raise_on_noconv=True):
         """Solve M x = b for b (nrhs, n_total) complex128 on the GPU."""
         b = b.contiguous()
@@ -197,3 +201,13 @@ class System:
         if getattr(self, "handle", None):
             L.mtf_system_destroy(self.handle)
             self.handle = None
+
+
+def solve_batch(systems, dirs_list, pols_list, threads=0, raise_on_noconv=True):
+    """Solve independent instances together (mtf_solve_batch): one (nrhs_i, n_total_i)
+    complex128 solution per system, and the per-instance stats."""
+    xs = [torch.empty((len(d), s.mesh.n_total), dtype=torch.complex128, device="cuda")
+          for s, d in zip(systems, dirs_list)]
+    st, status = L.mtf_solve_batch([s.handle for s in systems], dirs_list, pols_list, xs, threads, _stream(),
+                                   raise_on_noconv)
+    return xs, st

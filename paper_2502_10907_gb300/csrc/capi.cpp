@@ -5,6 +5,10 @@
 #include <complex>
 #include <cstring>
 #include <string>
+#include <thread>
+#include <vector>
+#include <algorithm>
+#include <atomic>
 
 #include "common.h"
 
@@ -33,7 +37,7 @@ static mtf_status guarded(Fn&& fn) {
 }
 
 static void upload_small(DevBuf<double>& buf, const double* h, size_t n, cudaStream_t s) {
-  buf.alloc(n);
+  if (buf.n < n) buf.alloc(n);
   MTF_CUDA(cudaMemcpyAsync(buf.p, h, n * sizeof(double), cudaMemcpyHostToDevice, s));
   MTF_CUDA(cudaStreamSynchronize(s));
 }
@@ -305,11 +309,13 @@ mtf_status mtf_solve(mtf_system sys, int32_t nrhs, const double* dirs, const dou
   mtf_status g = guarded([&] {
     MTF_REQUIRE(sys && x_out, MTF_ERR_ARG, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    DevBuf<double> dd, dp, b;
-    upload_waves(dd, dp, nrhs, dirs, pols, s);
-    b.alloc(size_t(sys->mesh->n_total) * nrhs * 2);
-    launch_rhs(sys, nrhs, dd.p, dp.p, b.p, s);
-    st = solve(sys, nrhs, b.p, static_cast<double*>(x_out), stats, s);
+    // the buffers stay with the system (no allocation, and no implicit
+    // device synchronisation, in repeated solves)
+    upload_waves(sys->d_wdir, sys->d_wpol, nrhs, dirs, pols, s);
+    const size_t nb = size_t(sys->mesh->n_total) * nrhs * 2;
+    if (sys->d_brhs.n < nb) sys->d_brhs.alloc(nb);
+    launch_rhs(sys, nrhs, sys->d_wdir.p, sys->d_wpol.p, sys->d_brhs.p, s);
+    st = solve(sys, nrhs, sys->d_brhs.p, static_cast<double*>(x_out), stats, s);
     MTF_CUDA(cudaStreamSynchronize(s));
     if (st == MTF_ERR_NOCONV) set_last_error("GMRES did not reach the tolerance within max_iter");
     if (st == MTF_ERR_NAN) set_last_error("non-finite residual in GMRES");
@@ -331,6 +337,142 @@ mtf_status mtf_solve_rhs(mtf_system sys, int32_t nrhs, const void* b, void* x_ou
     if (st == MTF_ERR_NAN) set_last_error("non-finite residual in GMRES");
   });
   return g != MTF_OK ? g : st;
+}
+
+// ---------------------------------------------------------------------------
+// batched solve and autotuner
+// ---------------------------------------------------------------------------
+mtf_status mtf_solve_batch(int32_t n, const mtf_system* systems, const int32_t* nrhs, const double* const* dirs,
+                           const double* const* pols, void* const* x_out, mtf_solve_stats* stats, int32_t threads,
+                           void* stream) {
+  std::vector<mtf_status> status;
+  std::vector<std::string> msg;
+  mtf_status g = guarded([&] {
+    MTF_REQUIRE(n >= 1 && systems && nrhs && dirs && pols && x_out, MTF_ERR_ARG, "batch: null arrays or n < 1");
+    for (int i = 0; i < n; ++i) {
+      MTF_REQUIRE(systems[i] && x_out[i] && nrhs[i] >= 1, MTF_ERR_ARG, "batch: instance " + std::to_string(i));
+      for (int j = 0; j < i; ++j) MTF_REQUIRE(systems[j] != systems[i], MTF_ERR_ARG, "batch: repeated system");
+    }
+    int dev = 0;
+    MTF_CUDA(cudaGetDevice(&dev));
+    // instances largest first, so that the long ones start early
+    std::vector<int> order(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) order[size_t(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return double(systems[a]->mesh->n_total) * nrhs[a] > double(systems[b]->mesh->n_total) * nrhs[b];
+    });
+    const int nt = std::max(1, std::min<int>(n, threads > 0 ? threads : 8));
+    // every instance starts after the work queued on the caller's stream
+    cudaEvent_t start = nullptr;
+    MTF_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    MTF_CUDA(cudaEventRecord(start, static_cast<cudaStream_t>(stream)));
+    status.assign(size_t(n), MTF_OK);
+    msg.assign(size_t(n), std::string());
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      cudaSetDevice(dev);
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+          status[size_t(order[size_t(q)])] = MTF_ERR_CUDA;
+          msg[size_t(order[size_t(q)])] = "batch: stream creation failed";
+        }
+        return;
+      }
+      cudaStreamWaitEvent(s, start, 0);
+      for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+        const int i = order[size_t(q)];
+        mtf_solve_stats* st = stats ? stats + i : nullptr;
+        const mtf_status r = mtf_solve(systems[i], nrhs[i], dirs[i], pols[i], x_out[i], st, s);
+        status[size_t(i)] = r;
+        if (r != MTF_OK) msg[size_t(i)] = mtf_last_error();
+      }
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    cudaEventDestroy(start);
+  });
+  if (g != MTF_OK) return g;
+  for (int i = 0; i < n; ++i)
+    if (status[size_t(i)] != MTF_OK) {
+      set_last_error("instance " + std::to_string(i) + ": " + msg[size_t(i)]);
+      return status[size_t(i)];
+    }
+  return MTF_OK;
+}
+
+mtf_status mtf_probe_peaks(double* rates, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(rates, MTF_ERR_ARG, "null argument");
+    probe_peaks(rates, static_cast<cudaStream_t>(stream));
+  });
+}
+
+mtf_status mtf_autotune(mtf_system sys, int32_t nrhs, int32_t reps, char* report, int32_t report_len, void* stream) {
+  return guarded([&] {
+    MTF_REQUIRE(sys && nrhs >= 1 && reps >= 1 && reps <= 100, MTF_ERR_ARG, "autotune: arguments");
+    MTF_REQUIRE(tc_matvec_enabled(sys), MTF_ERR_ARG, "autotune: needs a mixed-precision system with mv_tensor");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t ldn = (sys->mesh->n_total + 63) & ~int64_t(63);  // the solvers' padded column length
+    DevBuf<float> x, y;
+    x.alloc(size_t(ldn) * nrhs * 2);
+    y.alloc(size_t(ldn) * nrhs * 2);
+    MTF_CUDA(cudaMemsetAsync(x.p, 0x3c, x.n * sizeof(float), s));  // every float 0.0115
+    int dev = 0, sms = 0;
+    MTF_CUDA(cudaGetDevice(&dev));
+    MTF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    struct Cand {
+      int waves, min_len, grid;
+      bool fma;
+      std::string name;
+    };
+    std::vector<Cand> cands{{0, 0, 0, true, "fma_stream"}};
+    if (nrhs > kFmaPassRhs)
+      for (int grid : {0, sms / 2})
+        for (int waves : {2, 4, 8})
+          for (int ml : {2, 8})
+            cands.push_back({waves, ml, grid, false,
+                             "tc waves=" + std::to_string(waves) + " min_len=" + std::to_string(ml) +
+                                 " grid=" + std::to_string(grid > 0 ? grid : sms)});
+    cudaEvent_t e0, e1;
+    MTF_CUDA(cudaEventCreate(&e0));
+    MTF_CUDA(cudaEventCreate(&e1));
+    std::string rep;
+    size_t best = 0;
+    float best_ms = 0.f;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const Cand& k = cands[c];
+      tc_set_plan(sys, k.waves, k.min_len, k.grid, k.fma, s);
+      launch_matvec_f32(sys, x.p, ldn, y.p, ldn, nrhs, s);  // warm-up
+      MTF_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r) launch_matvec_f32(sys, x.p, ldn, y.p, ldn, nrhs, s);
+      MTF_CUDA(cudaEventRecord(e1, s));
+      MTF_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MTF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= float(reps);
+      rep += k.name + " " + std::to_string(ms) + "\n";
+      if (c == 0 || ms < best_ms) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    check_matvec_stream(sys, s);
+    const Cand& k = cands[best];
+    tc_set_plan(sys, k.waves, k.min_len, k.grid, k.fma, s);
+    rep += "chosen " + k.name + "\n";
+    if (report && report_len > 0) {
+      const size_t len = std::min(rep.size(), size_t(report_len - 1));
+      std::memcpy(report, rep.data(), len);
+      report[len] = '\0';
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------

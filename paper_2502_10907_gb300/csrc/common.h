@@ -196,6 +196,7 @@ struct mtf_system_s {
   double k0 = 0;
   std::vector<double> k_re, k_im, rho_re, rho_im;
   mtf::DevBuf<double> d_k, d_rho;            // (re, im) per block
+  mtf::DevBuf<double> d_wdir, d_wpol, d_brhs;  // mtf_solve: wave parameters and right-hand sides (kept)
   mtf::DevBuf<double> d_TK64;                // FP64: 4 doubles per dense entry
   mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
   mtf::DevBuf<float> d_TK32t;                // the same, tiled per stream unit (streaming matvec)
@@ -371,6 +372,13 @@ BlasLease blas_lease(cudaStream_t s);
 // right-hand sides of one pass of the FMA streaming applies; wider applies
 // go to the tensor cores (mv_tensor)
 constexpr int kFmaPassRhs = 4;
+// whether an apply to nrhs right-hand sides runs on the tensor cores (more
+// than one FMA pass, tensor-core tables built, not overridden by the
+// autotuner), and the autotuner's plan setter (mv_tc.cu)
+bool tc_wide_apply(mtf_system sys, int nrhs);
+void tc_set_plan(mtf_system sys, int waves, int min_len, int grid, bool prefer_fma, cudaStream_t s);
+// FP32, FP64 FLOP/s and SFU results per second of the device (probe.cu)
+void probe_peaks(double* rates, cudaStream_t s);
 // T~_i = W_i diag(f_i) W_i^T of every block into sys->d_osrc_T on the tensor
 // cores (osrc_form_tc.cu)
 void osrc_form_tc(mtf_system sys, cudaStream_t s);

@@ -280,7 +280,7 @@ void launch_matvec_f32(mtf_system sys, const float* x, int64_t ldx, float* y, in
                        cudaStream_t s) {
   // one FMA pass (up to 4 right-hand sides) beats the tensor-core pass,
   // whose input packing and combine cost more at that width
-  if (nrhs > kFmaPassRhs && tc_matvec_enabled(sys)) {
+  if (tc_wide_apply(sys, nrhs)) {
     launch_matvec_tc(sys, x, ldx, y, ldy, nrhs, s);
     return;
   }

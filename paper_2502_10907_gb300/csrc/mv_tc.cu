@@ -42,6 +42,9 @@ struct TcMatvec {
   TcPlan plan;
   int n_cta = 0;
   bool planned = false, built = false;
+  // launch plan (the autotuner's choice; 0 = plan_tc's defaults, one CTA per SM)
+  int waves = 0, min_len = 0, grid = 0;
+  bool prefer_fma = false;             // wide applies on the FMA streams instead
   DevBuf<__half> A;                    // tiled hi / lo operator
   DevBuf<unsigned> amax;               // per block: largest |re|, |im| of T and K (float bits)
   DevBuf<int4> units, tile_info;       // unit {blk, mt, kc0, kc1}; tile {blk, mt, kc, 0}
@@ -503,10 +506,10 @@ static void tc_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
   int dev = 0, sms = 0;
   MTF_CUDA(cudaGetDevice(&dev));
   MTF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  t.n_cta = std::max(1, sms);
+  t.n_cta = std::max(1, t.grid > 0 ? std::min(t.grid, sms) : sms);
   std::vector<int> Ns(m->nd);
   for (int i = 0; i < m->nd; ++i) Ns[i] = m->blk[i].N;
-  const std::string why = plan_tc(Ns, t.n_cta, t.plan);
+  const std::string why = plan_tc(Ns, t.n_cta, t.plan, t.waves, t.min_len);
   MTF_REQUIRE(why.empty(), MTF_ERR_MESH, why);
   const TcPlan& p = t.plan;
   std::vector<int4> units(p.units.size()), tinfo(size_t(p.n_tiles));
@@ -552,6 +555,23 @@ static void tc_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
 
 bool tc_matvec_enabled(mtf_system sys) {
   return sys->opt.precision == MTF_PREC_MIXED && sys->opt.mv_tensor && sys->tc && sys->tc->built;
+}
+
+bool tc_wide_apply(mtf_system sys, int nrhs) {
+  return nrhs > kFmaPassRhs && tc_matvec_enabled(sys) && !sys->tc->prefer_fma;
+}
+
+void tc_set_plan(mtf_system sys, int waves, int min_len, int grid, bool prefer_fma, cudaStream_t s) {
+  MTF_REQUIRE(tc_matvec_enabled(sys), MTF_ERR_ARG, "tensor-core matvec not built for this system");
+  TcMatvec& t = *sys->tc;
+  t.prefer_fma = prefer_fma;
+  if (t.waves == waves && t.min_len == min_len && t.grid == grid && t.planned) return;
+  MTF_CUDA(cudaStreamSynchronize(s));  // launches queued with the old tables have finished
+  t.waves = waves;
+  t.min_len = min_len;
+  t.grid = grid;
+  t.planned = false;
+  tc_plan_tables(sys, t, s);
 }
 
 // FP16 hi / lo tiled copy of the FP32-stored {T, K}, rebuilt after every

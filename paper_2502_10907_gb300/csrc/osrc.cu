@@ -642,7 +642,7 @@ template <class ZT, bool ADJ = false>
 static void osrc_stream(mtf_system sys, const float* r32, int64_t ldr, ZT* z, int64_t ldz, int nrhs, cudaStream_t s) {
   stream_prepare(sys, s);
   if constexpr (sizeof(ZT) == 4) {
-    if (!ADJ && nrhs > kFmaPassRhs && tc_osrc_enabled(sys)) {
+    if (!ADJ && tc_wide_apply(sys, nrhs) && tc_osrc_enabled(sys)) {
       launch_osrc_apply_tc(sys, r32, ldr, z, ldz, nrhs, s);
       return;
     }
