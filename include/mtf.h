@@ -127,6 +127,16 @@ typedef struct {
                            at most 4 (one pass of the FMA streams, which are
                            faster there) and mv_tensor = 0 use the FMA
                            streams, one pass per 4.  Default 1               */
+  int32_t residual_fp64;/* mixed mode: 1: the assembly also forms the FP64
+                           blocks (FP64 regular and singular pairs, 32 B per
+                           entry more) and the outer refinement residuals
+                           b - M x apply them in FP64, so the solution
+                           converges to the FP64-assembled system's rather
+                           than to the FP32-stored one's (whose difference
+                           is the FP32 entry error, about 1e-7, times the
+                           conditioning); mtf_matvec then applies the FP64
+                           blocks.  0: residuals of the FP32-stored blocks
+                           (residual_df).  Default 0                         */
 } mtf_options;
 
 typedef struct {

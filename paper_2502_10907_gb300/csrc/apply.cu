@@ -338,12 +338,13 @@ void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, 
 }
 
 // y = M x with the operator as stored: FP64 storage and arithmetic on the FP64
-// path; FP32 storage with double-float accumulation of the FP64 input (the
-// refinement residual) on the mixed path.
+// path and on the mixed path with residual_fp64; FP32 storage with
+// double-float accumulation of the FP64 input (the refinement residual) on
+// the mixed path otherwise.
 void launch_matvec(mtf_system sys, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs,
                    cudaStream_t s) {
-  launch_matvec_kind(sys, sys->opt.precision == MTF_PREC_FP64 ? MV_FP64 : MV_FP32_ACC64, x, ldx, y, ldy,
-                     nrhs, s);
+  const bool fp64 = sys->opt.precision == MTF_PREC_FP64 || sys->opt.residual_fp64;
+  launch_matvec_kind(sys, fp64 ? MV_FP64 : MV_FP32_ACC64, x, ldx, y, ldy, nrhs, s);
 }
 
 }  // namespace mtf

@@ -564,7 +564,8 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
   BlockArgs A = block_args(sys);
   const int64_t np = int64_t(m->sing.size());
   const unsigned sblocks = unsigned((np * 32 + 255) / 256);
-  if (sys->opt.precision == MTF_PREC_FP64) {
+  const bool fp64_blocks = sys->opt.precision == MTF_PREC_FP64 || sys->opt.residual_fp64;
+  if (fp64_blocks) {
     sys->d_TK64.alloc(size_t(m->n_mat) * 4);
     MTF_CUDA(cudaMemsetAsync(sys->d_TK64.p, 0, size_t(m->n_mat) * 4 * sizeof(double), s));
     const int64_t nct = m->reg_cta_prefix.back();
@@ -574,7 +575,8 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
       MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<double><<<sblocks, 256, 0, s>>>(
           A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
           sys->ss_npts[1], sys->ss_npts[2], sys->d_TK64.p));
-  } else {
+  }
+  if (sys->opt.precision != MTF_PREC_FP64) {
     // mixed: FP32 storage; regular pairs in FP32, singular pairs in FP64
     sys->d_TK32.alloc(size_t(m->n_mat) * 4);
     MTF_CUDA(cudaMemsetAsync(sys->d_TK32.p, 0, size_t(m->n_mat) * 4 * sizeof(float), s));

@@ -580,7 +580,8 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       if (it == 0) {
         MTF_CUDA(cudaMemcpyAsync(G.b.p, b_dev, vec_bytes, cudaMemcpyDeviceToDevice, s));
       } else {
-        launch_matvec_kind(sys, MV_FP32_ACC64, x_dev, n, G.w.p, n, nrhs, s);
+        // b - M x with the FP64 blocks (residual_fp64) or the FP32-stored ones
+        launch_matvec_kind(sys, sys->opt.residual_fp64 ? MV_FP64 : MV_FP32_ACC64, x_dev, n, G.w.p, n, nrhs, s);
         MTF_LAUNCH(KID_SUB, s, k_sub<<<nblk(n * nrhs * 2, 256), 256, 0, s>>>(b_dev, G.w.p, G.b.p, n * nrhs * 2));
       }
       MTF_LAUNCH(KID_NORM, s, k_norm_scale<<<nrhs, 1024, 0, s>>>(G.b.p, n, hN, G.w.p, n));

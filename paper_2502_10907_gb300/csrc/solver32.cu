@@ -17,9 +17,9 @@
 #include <atomic>
 #include <cmath>
 
-#include <cublas_v2.h>
 
 #include "bulk.h"
+#include "block_krylov.h"
 #include "common.h"
 #include "krylov_host.h"
 
@@ -581,6 +581,67 @@ constexpr int kBatch = 8;
 static inline size_t slot_len(int j, int nrhs) { return size_t(4 * (j + 1) + 8) * nrhs; }
 
 
+// Out[:, j] = sum_{k < K} In[:, k] M[k, j] for j < ncol over n rows: In and Out
+// complex FP32 columns of stride ldi / ldo, M complex FP32 column-major with
+// leading dimension ldm.  CTA tile 128 rows x 32 columns, K in chunks of 32
+// staged in shared memory; thread (row group, column group) holds 4 x 4
+// complex sums.  (The recycling products C = V Q and U = Z R^-1.)
+__global__ void __launch_bounds__(256) k_cgemm_nn(const float* __restrict__ In, int64_t ldi, const float* __restrict__ M,
+                                                  int ldm, int K, int ncol, int64_t n, float* __restrict__ Out,
+                                                  int64_t ldo) {
+  __shared__ float2 a[32][128 + 1];  // a[k][row]
+  __shared__ float2 b[32][32 + 1];   // b[k][col]
+  const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;  // rows tr + 32 i, columns tc + 8 j
+  const int64_t r0 = int64_t(blockIdx.x) * 128;
+  const int c0 = blockIdx.y * 32;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 128; t += 256) {
+      const int kk = t / 128, rr = t % 128;
+      const int64_t row = r0 + rr;
+      a[kk][rr] = (k0 + kk < K && row < n) ? reinterpret_cast<const float2*>(In + 2 * int64_t(k0 + kk) * ldi)[row]
+                                           : make_float2(0.f, 0.f);
+    }
+    for (int t = threadIdx.x; t < 32 * 32; t += 256) {
+      const int kk = t / 32, cc = t % 32;
+      b[kk][cc] = (k0 + kk < K && c0 + cc < ncol)
+                      ? reinterpret_cast<const float2*>(M)[int64_t(c0 + cc) * ldm + k0 + kk]
+                      : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      float2 x[4], y[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = a[kk][tr + 32 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) y[j] = b[kk][tc + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(x[i].x, y[j].x, fmaf(-x[i].y, y[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(x[i].x, y[j].y, fmaf(x[i].y, y[j].x, acc[i][j].y));
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = r0 + tr + 32 * i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tc + 8 * j;
+      if (col < ncol) reinterpret_cast<float2*>(Out + 2 * int64_t(col) * ldo)[row] = acc[i][j];
+    }
+  }
+}
+
 // Build the recycled space of a finished cycle for the next cycle of the same
 // solve: per rhs c with k_c finished columns, H_c = Q_c R_c (host Givens
 // data), C_c = V_c Q_c (orthonormal, M U_c = C_c) and U_c = Z_c R_c^{-1}, stored
@@ -594,7 +655,10 @@ static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_
   using cd = std::complex<double>;
   const size_t qsz = size_t(kr + 1) * kr, rsz = size_t(kr) * kr;
   std::vector<cd> Q(qsz), R(rsz);
-  std::vector<float> qr32(size_t(nrhs) * (qsz + rsz) * 2);
+  // per rhs: Q (column-major, leading dimension kr + 1) and R^-1 (upper
+  // triangular, leading dimension kr; columns by back substitution on the
+  // host in FP64, in parallel)
+  std::vector<float> qr32(size_t(nrhs) * (qsz + rsz) * 2, 0.f);
   for (int c = 0; c < nrhs; ++c) {
     const int kc = ha.jc[c];
     if (kc <= 0) continue;
@@ -606,37 +670,38 @@ static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_
         qc[2 * (size_t(p) * (kr + 1) + q) + 1] = float(Q[size_t(p) * (kc + 1) + q].imag());
       }
     float* rc = qc + qsz * 2;
-    for (size_t t = 0; t < rsz; ++t) {
-      rc[2 * t] = float(R[t].real());
-      rc[2 * t + 1] = float(R[t].imag());
-    }
+    parallel_for(kc, long(kc) * kc * kc > 4000000 ? 16 : 1, [&](int j) {
+      std::vector<cd> xj(size_t(j) + 1);
+      xj[size_t(j)] = 1.0 / R[size_t(j) * kr + j];
+      for (int q = j - 1; q >= 0; --q) {
+        cd acc = 0;
+        for (int p = q + 1; p <= j; ++p) acc += R[size_t(p) * kr + q] * xj[size_t(p)];
+        xj[size_t(q)] = -acc / R[size_t(q) * kr + q];
+      }
+      for (int q = 0; q <= j; ++q) {
+        rc[2 * (size_t(j) * kr + q)] = float(xj[size_t(q)].real());
+        rc[2 * (size_t(j) * kr + q) + 1] = float(xj[size_t(q)].imag());
+      }
+    });
   }
   const size_t ncols = size_t(kr) * ldn * nrhs * 2;
   if (G.RC.n < ncols) G.RC.alloc(ncols);
   if (G.RU.n < ncols) G.RU.alloc(ncols);
   if (G.RQ.n < qr32.size()) G.RQ.alloc(qr32.size());
   MTF_CUDA(cudaMemcpyAsync(G.RQ.p, qr32.data(), qr32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-  BlasLease bl = blas_lease(s);
-  cublasHandle_t h = bl.h;
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
   for (int c = 0; c < nrhs; ++c) {
     const int kc = ha.jc[c];
     float* Vc = G.V.p + 2 * size_t(c) * ldv;
     float* Zc = G.Z.p + 2 * size_t(c) * ldz;
     float* Cc = G.RC.p + 2 * size_t(c) * kr * ldn;
     float* Uc = G.RU.p + 2 * size_t(c) * kr * ldn;
-    const cuComplex* Qd = reinterpret_cast<const cuComplex*>(G.RQ.p + size_t(c) * (qsz + rsz) * 2);
-    const cuComplex* Rd = Qd + qsz;
+    const float* Qd = G.RQ.p + size_t(c) * (qsz + rsz) * 2;
+    const float* Rid = Qd + qsz * 2;
     if (kc > 0) {
-      MTF_REQUIRE(cublasCgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, int(ldn), kc, kc + 1, &one,
-                              reinterpret_cast<const cuComplex*>(Vc), int(ldn), Qd, kr + 1, &zero,
-                              reinterpret_cast<cuComplex*>(Cc), int(ldn)) == CUBLAS_STATUS_SUCCESS,
-                  MTF_ERR_CUDA, "cublasCgemm failed");
-      MTF_CUDA(cudaMemcpyAsync(Uc, Zc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
-      MTF_REQUIRE(cublasCtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT,
-                              int(ldn), kc, &one, Rd, kr, reinterpret_cast<cuComplex*>(Uc), int(ldn)) ==
-                      CUBLAS_STATUS_SUCCESS,
-                  MTF_ERR_CUDA, "cublasCtrsm failed");
+      const dim3 grid(unsigned((ldn + 127) / 128), unsigned((kc + 31) / 32));
+      // C = V Q (the first kc + 1 basis vectors), U = Z R^-1
+      MTF_LAUNCH(KID_MISC, s, k_cgemm_nn<<<grid, 256, 0, s>>>(Vc, ldn, Qd, kr + 1, kc + 1, kc, ldn, Cc, ldn));
+      MTF_LAUNCH(KID_MISC, s, k_cgemm_nn<<<grid, 256, 0, s>>>(Zc, ldn, Rid, kr, kc, kc, ldn, Uc, ldn));
       MTF_CUDA(cudaMemcpyAsync(Vc, Cc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
       MTF_CUDA(cudaMemcpyAsync(Zc, Uc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
     }

@@ -9,6 +9,8 @@ unknowns), 8 plane waves each, solved together:
 * mixed path with block-OSRC (block FGMRES and tensor-core applies for the
   8 waves): every instance within 1e-5, and the same iterate as a single
   solve of that instance to rounding;
+* the mixed path with FP64 refinement residuals (residual_fp64): within 1e-7
+  at tol 1e-10, beyond what the FP32-stored operator allows;
 * the autotuner times its candidate apply plans, keeps one, and the tuned
   system still matches the oracle (matvec at 1e-5, solve at 1e-5)."""
 import numpy as np
@@ -69,6 +71,14 @@ def test_batch_fp64_and_mixed_match_oracle_lu(api, instances):
     x0, _ = s32[0].solve(dirs[0], pols[0])
     d = (x0 - xs[0]).abs().max().item() / xs[0].abs().max().item()
     assert d < 1e-9, d
+    # residual_fp64: refinement residuals of the FP64 blocks, so the mixed
+    # solve converges to the FP64 system's solution, past the FP32 floor
+    sdf = [api.System(m, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, precond=1, tol=1e-10, restart=500,
+                      max_iter=8000, max_refine=10, residual_fp64=1) for m, (cfg, _, _, _) in zip(meshes, instances)]
+    xs, st = api.solve_batch(sdf, dirs, pols)
+    for x, s, (_, _, _, xr) in zip(xs, st, instances):
+        assert s.converged == 1
+        assert _errs(x, xr).max() < 1e-7, _errs(x, xr)
 
 
 def test_batch_rejects_a_repeated_system(api, instances):
