@@ -376,8 +376,10 @@ mtf_status mtf_autotune(mtf_system sys, int32_t nrhs, int32_t reps, char* report
  *  - MTF_LEARNED_NETWORK: a = g(x) per dof, g a network of 10 geometric
  *    features (k_i l_m, rho_i, 1 for block 0, k_i l of the 4 neighbours,
  *    k_i^2 (A_1 + A_2) of its triangles, cosine between their normals, 1 for
- *    a junction edge) -> 64 -> 64 (ReLU) -> 80; parameters augmented
- *    row-major matrices [W | b] layer after layer (64 x 11, 64 x 65, 80 x 65).
+ *    a junction edge) -> 256 -> 256 (ReLU) -> 80; parameters augmented
+ *    row-major matrices [W | b] layer after layer (256 x 11, 256 x 257,
+ *    80 x 257); every layer's product (forward, backward, weight gradient)
+ *    runs on the tensor cores (FP16 hi + lo operands, FP32 accumulation).
  * Both start at zero output (plain block-OSRC).  Training minimises the
  * power loss
  *   L = mean_z ||E^K z||^2 / ||z||^2,   E = I - M (P + C) / c0,

@@ -36,18 +36,23 @@
 // operators the FP32 kernels of the inner solver.
 //
 // Network activations are stored feature-major (value f of row q at
-// [f * ld + q]) so that a warp reads 32 consecutive rows of one feature.
+// [f * ld + q]).  Every layer of the network -- forward, the backward
+// products and the weight gradients -- is a matrix product on the tensor
+// cores (tc_gemm.cu: FP16 hi + lo operands, FP32 accumulation), with the
+// bias folded in as a column (row) of ones and ReLU or its derivative in the
+// product's epilogue.
 #include <algorithm>
 #include <cmath>
 #include <random>
 
 #include "common.h"
+#include "tc_gemm.h"
 
 namespace mtf {
 
 constexpr int kLF = 10;  // geometric features
 constexpr int kLO = 80;  // stencil coefficients (re, im)
-constexpr int kLH = 64;  // hidden width
+constexpr int kLH = 256;  // hidden width
 constexpr int kLW1 = kLH * (kLF + 1), kLW2 = kLH * (kLH + 1), kLW3 = kLO * (kLH + 1);
 constexpr int kLNetParams = kLW1 + kLW2 + kLW3;
 constexpr int kLMaxBatch = 32;
@@ -68,12 +73,16 @@ struct LearnedState {
   // power-loss scratch (complex64 columns of n_total)
   DevBuf<float> Zb, E, PE, T, MT, A, B, CRH, CPH, U, CA;
   DevBuf<double> acc;
+  TcGemm* gemm = nullptr;  // tensor-core products of the network
   uint64_t draws = 0;    // random vectors drawn so far (counter of the generator)
   bool centred = false;
   double center_re = 1.0, center_im = 0.0;
 };
 
-void destroy_learned(LearnedState* l) { delete l; }
+void destroy_learned(LearnedState* l) {
+  if (l) tg_destroy(l->gemm);
+  delete l;
+}
 
 static inline unsigned nbk(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
@@ -128,51 +137,6 @@ __global__ void k_l_axpy(const float* __restrict__ a, const float* __restrict__ 
   reinterpret_cast<float2*>(out)[o] = make_float2(x.x + br * y.x - bi * y.y, x.y + br * y.y + bi * y.x);
 }
 
-__device__ __forceinline__ void l_load_params(const float* __restrict__ prm, float* sp) {
-  for (int t = threadIdx.x; t < kLNetParams; t += blockDim.x) sp[t] = prm[t];
-  __syncthreads();
-}
-
-// forward pass, one thread per row: Y (kLO x ld); H1, H2 (kLH x ld) if not null
-__global__ void __launch_bounds__(128) k_l_forward(const float* __restrict__ X, int64_t ld, int64_t rows,
-                                                   const float* __restrict__ prm, float* __restrict__ H1,
-                                                   float* __restrict__ H2, float* __restrict__ Y) {
-  extern __shared__ float sp[];
-  l_load_params(prm, sp);
-  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= rows) return;
-  const float* W1 = sp;
-  const float* W2 = sp + kLW1;
-  const float* W3 = sp + kLW1 + kLW2;
-  float x[kLF];
-#pragma unroll
-  for (int f = 0; f < kLF; ++f) x[f] = X[f * ld + q];
-  float h1[kLH];
-#pragma unroll
-  for (int j = 0; j < kLH; ++j) {
-    float a = W1[j * (kLF + 1) + kLF];
-#pragma unroll
-    for (int f = 0; f < kLF; ++f) a = fmaf(W1[j * (kLF + 1) + f], x[f], a);
-    h1[j] = fmaxf(a, 0.f);
-    if (H1) H1[j * ld + q] = h1[j];
-  }
-  float y[kLO];
-#pragma unroll
-  for (int o = 0; o < kLO; ++o) y[o] = W3[o * (kLH + 1) + kLH];
-#pragma unroll 1
-  for (int j = 0; j < kLH; ++j) {
-    float a = W2[j * (kLH + 1) + kLH];
-#pragma unroll
-    for (int k = 0; k < kLH; ++k) a = fmaf(W2[j * (kLH + 1) + k], h1[k], a);
-    a = fmaxf(a, 0.f);
-    if (H2) H2[j * ld + q] = a;
-#pragma unroll
-    for (int o = 0; o < kLO; ++o) y[o] = fmaf(W3[o * (kLH + 1) + j], a, y[o]);
-  }
-#pragma unroll
-  for (int o = 0; o < kLO; ++o) Y[o * ld + q] = y[o];
-}
-
 // G3 = 2 w (y - t) and loss += sum w |y - t|^2 (network-level loss)
 __global__ void __launch_bounds__(256) k_l_loss(const float* __restrict__ Y, const float* __restrict__ T,
                                                 const float* __restrict__ w, int64_t ld, int64_t rows,
@@ -189,87 +153,6 @@ __global__ void __launch_bounds__(256) k_l_loss(const float* __restrict__ Y, con
   }
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, double(l));
-}
-
-// backward through the hidden layers, one thread per row: G2, G1 (kLH x ld)
-__global__ void __launch_bounds__(128) k_l_backward(const float* __restrict__ G3, const float* __restrict__ H1,
-                                                    const float* __restrict__ H2, int64_t ld, int64_t rows,
-                                                    const float* __restrict__ prm, float* __restrict__ G2,
-                                                    float* __restrict__ G1) {
-  extern __shared__ float sp[];
-  l_load_params(prm, sp);
-  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= rows) return;
-  const float* W2 = sp + kLW1;
-  const float* W3 = sp + kLW1 + kLW2;
-  float g1[kLH];
-#pragma unroll
-  for (int k = 0; k < kLH; ++k) g1[k] = 0.f;
-#pragma unroll 1
-  for (int j = 0; j < kLH; ++j) {
-    float a = 0.f;
-#pragma unroll 8
-    for (int o = 0; o < kLO; ++o) a = fmaf(W3[o * (kLH + 1) + j], G3[o * ld + q], a);
-    a = H2[j * ld + q] > 0.f ? a : 0.f;
-    G2[j * ld + q] = a;
-#pragma unroll
-    for (int k = 0; k < kLH; ++k) g1[k] = fmaf(W2[j * (kLH + 1) + k], a, g1[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < kLH; ++k) G1[k * ld + q] = H1[k * ld + q] > 0.f ? g1[k] : 0.f;
-}
-
-// dW[p][qq] += sum_rows A[p][row] B[qq][row] (qq < Q) and dW[p][Q] += sum_rows
-// A[p][row] (bias column); A: P x ld, B: Q x ld (P, Q <= 64), dW row stride
-// Q + 1.  CTA = 16 x 16 threads, each a 4 x 4 tile of outputs, over chunks of
-// 64 rows staged in shared memory; partial sums added to dW with atomics.
-__global__ void __launch_bounds__(256) k_l_wgrad(const float* __restrict__ A, int P, const float* __restrict__ B,
-                                                 int Q, int64_t ld, int64_t rows, float* __restrict__ dW) {
-  __shared__ float As[64][65], Bs[64][65];
-  const int tp = threadIdx.x >> 4, tq = threadIdx.x & 15;
-  float acc[4][4], bias[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    bias[a] = 0.f;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  }
-  for (int64_t r0 = int64_t(blockIdx.x) * 64; r0 < rows; r0 += int64_t(gridDim.x) * 64) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
-      const int f = t >> 6, rr = t & 63;
-      const int64_t row = r0 + rr;
-      As[rr][f] = (f < P && row < rows) ? A[int64_t(f) * ld + row] : 0.f;
-      Bs[rr][f] = (f < Q && row < rows) ? B[int64_t(f) * ld + row] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int rr = 0; rr < 64; ++rr) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[rr][tp * 4 + u];
-        b[u] = Bs[rr][tq * 4 + u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        bias[u] += a[u];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-      }
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int p = tp * 4 + u;
-    if (p >= P) continue;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int qq = tq * 4 + v;
-      if (qq < Q) atomicAdd(dW + int64_t(p) * (Q + 1) + qq, acc[u][v]);
-    }
-    if (tq == 0) atomicAdd(dW + int64_t(p) * (Q + 1) + Q, bias[u]);
-  }
 }
 
 __global__ void k_l_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
@@ -485,29 +368,110 @@ int learned_kind(mtf_system sys) { return state(sys).kind; }
 // stencil coefficients in use (kLO x n_rows)
 static const float* coef_of(const LearnedState& L) { return L.kind == MTF_LEARNED_TABLE ? L.params.p : L.coef.p; }
 
-static void forward(LearnedState& L, const float* X, int64_t ld, int64_t rows, bool keep, float* Y,
+// operand helpers for the network products: a feature-major matrix read as
+// rows = dofs (A of a forward product), or as rows = features (A or B of a
+// weight gradient), and a row-major augmented weight matrix [W | b]
+static TgOperand dof_rows(const float* X, int64_t ld, int64_t rows, int feats, bool ones) {
+  TgOperand o;
+  o.X = X;
+  o.sr = 1;
+  o.sk = ld;
+  o.Rv = rows;
+  o.Kv = feats;
+  o.ones_k = ones ? feats : -1;
+  return o;
+}
+static TgOperand feat_rows(const float* X, int64_t ld, int feats, int64_t rows, bool ones) {
+  TgOperand o;
+  o.X = X;
+  o.sr = ld;
+  o.sk = 1;
+  o.Rv = feats;
+  o.Kv = rows;
+  o.ones_r = ones ? feats : -1;
+  return o;
+}
+static TgOperand weights(const float* W, int outs, int ins_aug) {  // W(c, k) = W[c ins_aug + k]
+  TgOperand o;
+  o.X = W;
+  o.sr = ins_aug;
+  o.sk = 1;
+  o.Rv = outs;
+  o.Kv = ins_aug;
+  return o;
+}
+static TgOperand weights_t(const float* W, int outs, int ins, int ins_aug) {  // W^T(c, k) = W[k ins_aug + c]
+  TgOperand o;
+  o.X = W;
+  o.sr = 1;
+  o.sk = ins_aug;
+  o.Rv = ins;
+  o.Kv = outs;
+  return o;
+}
+static TgOut to_feat(float* D, int64_t ld, int op, const float* mask, unsigned* err) {
+  TgOut o;
+  o.D = D;
+  o.dr = 1;
+  o.dc = ld;
+  o.op = op;
+  o.mask = mask;
+  o.mr = 1;
+  o.mc = ld;
+  o.err = err;
+  return o;
+}
+static TgOut to_weights(float* D, int ins_aug, unsigned* err) {
+  TgOut o;
+  o.D = D;
+  o.dr = ins_aug;
+  o.dc = 1;
+  o.err = err;
+  return o;
+}
+
+// forward pass: H1 = relu(W1 [x; 1]), H2 = relu(W2 [H1; 1]), Y = W3 [H2; 1]
+// (feature-major, leading dimension ld; H1, H2 kept in L for the backward)
+static void forward(mtf_system sys, LearnedState& L, const float* X, int64_t ld, int64_t rows, float* Y,
                     cudaStream_t s) {
-  const size_t sm = kLNetParams * sizeof(float);
-  MTF_LAUNCH(KID_MLP, s, k_l_forward<<<nbk(rows, 128), 128, sm, s>>>(X, ld, rows, L.params.p, keep ? L.H1.p : nullptr,
-                                                                      keep ? L.H2.p : nullptr, Y));
+  if (!L.gemm) L.gemm = tg_create();
+  stream_prepare(sys, s);
+  unsigned* err = sys->d_mv_ctl.p + 2;
+  const float* W1 = L.params.p;
+  const float* W2 = W1 + kLW1;
+  const float* W3 = W2 + kLW2;
+  tc_gemm(*L.gemm, dof_rows(X, ld, rows, kLF, true), weights(W1, kLH, kLF + 1), rows, kLH, kLF + 1,
+          to_feat(L.H1.p, ld, 1, nullptr, err), s);
+  tc_gemm(*L.gemm, dof_rows(L.H1.p, ld, rows, kLH, true), weights(W2, kLH, kLH + 1), rows, kLH, kLH + 1,
+          to_feat(L.H2.p, ld, 1, nullptr, err), s);
+  tc_gemm(*L.gemm, dof_rows(L.H2.p, ld, rows, kLH, true), weights(W3, kLO, kLH + 1), rows, kLO, kLH + 1,
+          to_feat(Y, ld, 0, nullptr, err), s);
+  check_matvec_stream(sys, s);
 }
 
 // network parameter gradient (into L.grad) from dL/dY in L.G3, after a
-// forward pass that kept H1 and H2 (all with leading dimension rows)
-static void backward_from_g3(LearnedState& L, const float* X, int64_t rows, cudaStream_t s) {
+// forward pass (H1, H2 in L; all with leading dimension rows):
+//   G2 = (W3^T G3) masked by H2 > 0, G1 = (W2^T G2) masked by H1 > 0,
+//   dW3 = G3 [H2; 1]^T, dW2 = G2 [H1; 1]^T, dW1 = G1 [x; 1]^T
+static void backward_from_g3(mtf_system sys, LearnedState& L, const float* X, int64_t rows, cudaStream_t s) {
   const int64_t ld = rows;
-  const size_t sm = kLNetParams * sizeof(float);
-  MTF_LAUNCH(KID_MLP, s, k_l_backward<<<nbk(rows, 128), 128, sm, s>>>(L.G3.p, L.H1.p, L.H2.p, ld, rows, L.params.p,
-                                                                      L.G2.p, L.G1.p));
-  MTF_CUDA(cudaMemsetAsync(L.grad.p, 0, kLNetParams * sizeof(float), s));
-  const unsigned gw = unsigned(std::min<int64_t>(4 * 152, (rows + 63) / 64));
-  float* dW3 = L.grad.p + kLW1 + kLW2;
-  MTF_LAUNCH(KID_MLP, s, k_l_wgrad<<<gw, 256, 0, s>>>(L.G1.p, kLH, X, kLF, ld, rows, L.grad.p));
-  MTF_LAUNCH(KID_MLP, s, k_l_wgrad<<<gw, 256, 0, s>>>(L.G2.p, kLH, L.H1.p, kLH, ld, rows, L.grad.p + kLW1));
-  // output layer in two slices of at most 64 rows of W3
-  MTF_LAUNCH(KID_MLP, s, k_l_wgrad<<<gw, 256, 0, s>>>(L.G3.p, 64, L.H2.p, kLH, ld, rows, dW3));
-  MTF_LAUNCH(KID_MLP, s, k_l_wgrad<<<gw, 256, 0, s>>>(L.G3.p + 64 * ld, kLO - 64, L.H2.p, kLH, ld, rows,
-                                                      dW3 + 64 * (kLH + 1)));
+  unsigned* err = sys->d_mv_ctl.p + 2;
+  const float* W2 = L.params.p + kLW1;
+  const float* W3 = W2 + kLW2;
+  tc_gemm(*L.gemm, dof_rows(L.G3.p, ld, rows, kLO, false), weights_t(W3, kLO, kLH, kLH + 1), rows, kLH, kLO,
+          to_feat(L.G2.p, ld, 2, L.H2.p, err), s);
+  tc_gemm(*L.gemm, dof_rows(L.G2.p, ld, rows, kLH, false), weights_t(W2, kLH, kLH, kLH + 1), rows, kLH, kLH,
+          to_feat(L.G1.p, ld, 2, L.H1.p, err), s);
+  float* dW1 = L.grad.p;
+  float* dW2 = dW1 + kLW1;
+  float* dW3 = dW2 + kLW2;
+  tc_gemm(*L.gemm, feat_rows(L.G3.p, ld, kLO, rows, false), feat_rows(L.H2.p, ld, kLH, rows, true), kLO, kLH + 1,
+          rows, to_weights(dW3, kLH + 1, err), s);
+  tc_gemm(*L.gemm, feat_rows(L.G2.p, ld, kLH, rows, false), feat_rows(L.H1.p, ld, kLH, rows, true), kLH, kLH + 1,
+          rows, to_weights(dW2, kLH + 1, err), s);
+  tc_gemm(*L.gemm, feat_rows(L.G1.p, ld, kLH, rows, false), feat_rows(X, ld, kLF, rows, true), kLH, kLF + 1, rows,
+          to_weights(dW1, kLF + 1, err), s);
+  check_matvec_stream(sys, s);
 }
 
 // network: coefficients of the current parameters for every dof
@@ -515,7 +479,7 @@ static void refresh_coef(mtf_system sys, cudaStream_t s) {
   LearnedState& L = state(sys);
   if (L.kind != MTF_LEARNED_NETWORK) return;
   const int64_t rows = sys->mesh->n_rows;
-  forward(L, L.X.p, rows, rows, false, L.coef.p, s);
+  forward(sys, L, L.X.p, rows, rows, L.coef.p, s);
 }
 
 void learned_init(mtf_system sys, int kind, uint64_t seed, cudaStream_t s) {
@@ -656,11 +620,11 @@ void learned_loss_grad(mtf_system sys, const float* X, const float* T, const flo
   MTF_REQUIRE(L.kind == MTF_LEARNED_NETWORK, MTF_ERR_ARG, "the network loss needs the network parametrisation");
   MTF_REQUIRE(rows >= 1, MTF_ERR_ARG, "rows must be >= 1");
   ensure_rows(L, rows);
-  forward(L, X, rows, rows, true, L.Y.p, s);
+  forward(sys, L, X, rows, rows, L.Y.p, s);
   double* loss_dev = L.acc.p + 255;
   MTF_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(double), s));
   MTF_LAUNCH(KID_MLP, s, k_l_loss<<<nbk(rows, 256), 256, 0, s>>>(L.Y.p, T, w, rows, rows, L.G3.p, loss_dev));
-  backward_from_g3(L, X, rows, s);
+  backward_from_g3(sys, L, X, rows, s);
   MTF_CUDA(cudaMemcpyAsync(grad_out, L.grad.p, kLNetParams * sizeof(float), cudaMemcpyDeviceToDevice, s));
   double l = 0;
   MTF_CUDA(cudaMemcpyAsync(&l, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -715,7 +679,7 @@ static double power_grad(mtf_system sys, const float* Z, int pb, double c0r, dou
   MTF_REQUIRE(cn > 0, MTF_ERR_ARG, "c0 must not be zero");
   // ic = 1 / c0; forward steps use -ic, backward steps -conj(ic)
   const float icr = float(c0r / cn), ici = float(-c0i / cn);
-  if (L.kind == MTF_LEARNED_NETWORK) forward(L, L.X.p, nr, nr, true, L.coef.p, s);
+  if (L.kind == MTF_LEARNED_NETWORK) forward(sys, L, L.X.p, nr, nr, L.coef.p, s);
   MTF_CUDA(cudaMemcpyAsync(L.E.p, Z, col * pb * sizeof(float), cudaMemcpyDeviceToDevice, s));
   for (int j = 0; j < K; ++j) {
     float* Ej = L.E.p + col * pb * j;
@@ -747,7 +711,7 @@ static double power_grad(mtf_system sys, const float* Z, int pb, double c0r, dou
     MTF_LAUNCH(KID_MLP, s, k_l_axpy<<<gv, 256, 0, s>>>(L.U.p, L.CRH.p, n, n, 1.f, 0.f, L.U.p));
     MTF_LAUNCH(KID_MLP, s, k_l_axpy<<<gv, 256, 0, s>>>(L.A.p, L.U.p, n, n, -icr, ici, L.A.p));
   }
-  if (L.kind == MTF_LEARNED_NETWORK) backward_from_g3(L, L.X.p, nr, s);
+  if (L.kind == MTF_LEARNED_NETWORK) backward_from_g3(sys, L, L.X.p, nr, s);
   std::vector<double> h(static_cast<size_t>(128), 0.0);
   MTF_CUDA(cudaMemcpyAsync(h.data(), L.acc.p, 128 * sizeof(double), cudaMemcpyDeviceToHost, s));
   MTF_CUDA(cudaStreamSynchronize(s));

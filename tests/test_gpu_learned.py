@@ -20,7 +20,7 @@ from oracle.osrc import BlockOSRC
 from tests.oracle_helpers import skeleton_of
 
 pytestmark = pytest.mark.gpu
-H = 64
+H = 256
 
 
 @pytest.fixture(scope="module")
@@ -209,3 +209,27 @@ def test_fitted_correction_against_plain_osrc(api):
     assert rel(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-5
     if rep["enabled"]:
         assert st1.iterations <= 1.05 * st0.iterations, (rep, st0.iterations, st1.iterations)
+
+
+def test_learned_correction_gains_on_held_out_waves(api):
+    """The trained correction's gain, measured: on the R = 4 split sphere at
+    restart 50 (where restarted GMRES is slowed by the outlying eigenvalues
+    of the preconditioned operator that the power loss targets), fit on two
+    plane waves and then solve two held-out ones with and without it: at
+    least 10% fewer iterations, the same solution to 1e-5."""
+    cfg = mi.config_split_sphere(rings=4, k0=2.0)
+    sysg = _system(api, cfg, restart=50)
+    sysg.learned_init("table")
+    d_val = mi.fibonacci_directions(9)[0:2]
+    p_val = mi.orthonormal_polarizations(d_val)[0].astype(np.complex128)
+    rep = sysg.learned_fit(d_val, p_val, rounds=6, steps_per_round=150, lr=3e-3, batch=16, K=6, seed=5)
+    assert rep["enabled"] == 1, rep
+    d_te = mi.fibonacci_directions(7)[5:7]
+    p_te = mi.orthonormal_polarizations(d_te)[0].astype(np.complex128)
+    sysg.learned_enable(False)
+    x0, st0 = sysg.solve(d_te, p_te)
+    sysg.learned_enable(True)
+    x1, st1 = sysg.solve(d_te, p_te)
+    assert st0.converged and st1.converged
+    assert rel(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-5
+    assert st1.iterations <= 0.9 * st0.iterations, (rep, st0.iterations, st1.iterations)
