@@ -109,13 +109,15 @@ typedef struct {
                            into FP32 pairs, error-free products and sums;
                            about 2^-46 relative, on the FP32 pipes);
                            0: FP64 products and sums.  Default 1             */
-  int32_t block_krylov; /* mixed mode with nrhs >= 4 (and no learned
-                           correction initialised): 1: the inner FGMRES cycles build one
-                           block Krylov space shared by all right-hand sides
-                           (block flexible GMRES, block classical
-                           Gram-Schmidt twice, deflating Cholesky
-                           normalisation); restart then counts block steps of
-                           nrhs vectors.  0: one Krylov space per right-hand
+  int32_t block_krylov; /* mixed mode with nrhs >= 4: 1: the inner FGMRES
+                           cycles build one block Krylov space shared by all
+                           right-hand sides (block flexible GMRES, block
+                           classical Gram-Schmidt twice with the second pass
+                           lagged one step, deflating Cholesky
+                           normalisation; the learned correction, when
+                           enabled, follows block-OSRC as in the per-rhs
+                           cycle); restart then counts block steps of nrhs
+                           vectors.  0: one Krylov space per right-hand
                            side.  Default 1                                  */
   int32_t mv_tensor;    /* mixed mode: 1: applies to more than 4 right-hand
                            sides at once run on the tensor cores: the FP32

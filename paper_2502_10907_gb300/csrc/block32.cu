@@ -779,6 +779,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
       float* Zj = B.Z.p + 2 * int64_t(J) * vstride;
       if (pre) {
         launch_osrc_apply_f32(sys, Vt, ldn, Zj, ldn, s, st);
+        if (sys->learned_active) learned_apply_inplace(sys, Vt, ldn, Zj, ldn, s, st);
       } else {
         MTF_CUDA(cudaMemcpyAsync(Zj, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
       }

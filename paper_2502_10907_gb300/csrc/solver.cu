@@ -608,9 +608,9 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
       bool reached = false;
-      // systems with a learned correction keep the per-rhs spaces, so that
-      // their plain and corrected solves compare like for like
-      if (sys->opt.block_krylov && nrhs >= kBlockMinRhs && !sys->learned)
+      // 4 or more right-hand sides share one block space (with or without
+      // the learned correction, which both cycles apply after block-OSRC)
+      if (sys->opt.block_krylov && nrhs >= kBlockMinRhs)
         status = fgmres_block32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s);
       else
         status = fgmres_cycle32(sys, nrhs, G.b.p, x_dev, inner_tol, max_iter - total, it_in, reached, s, it);

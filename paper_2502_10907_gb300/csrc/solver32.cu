@@ -19,7 +19,6 @@
 
 
 #include "bulk.h"
-#include "block_krylov.h"
 #include "common.h"
 #include "krylov_host.h"
 
@@ -31,9 +30,13 @@ struct Gmres32Work {
   bool pre = false;
   DevBuf<float> V, Z, w;
   // recycled space of the previous cycle of the same solve: C = V Q in the
-  // first rec_k columns of V, U = Z R^{-1} (M U = C) in those of Z
+  // first rec_k columns of V; U = Z R^{-1} (M U = C) is kept as the first
+  // rec_k columns of Z and the factor R (host, per rhs), and applied as
+  // U c = Z (R^{-1} c)
   int rec_k = 0;
-  DevBuf<float> RC, RU, RQ;
+  DevBuf<float> RC, RQ;
+  std::vector<std::vector<std::complex<double>>> rec_R;  // per rhs: R (rec_kc x rec_kc, column-major, ld rec_k)
+  std::vector<int> rec_kc;
   // h: kBatch slots, one per Arnoldi column j of a batch; slot layout (complex
   // entries, index i * nrhs + c): t (j+1) x nrhs, s (j+1) x nrhs, coef 2 nrhs
   // (alpha, h_j), ||w|| nrhs, then nrhs real sums of squares
@@ -644,9 +647,10 @@ __global__ void __launch_bounds__(256) k_cgemm_nn(const float* __restrict__ In, 
 
 // Build the recycled space of a finished cycle for the next cycle of the same
 // solve: per rhs c with k_c finished columns, H_c = Q_c R_c (host Givens
-// data), C_c = V_c Q_c (orthonormal, M U_c = C_c) and U_c = Z_c R_c^{-1}, stored
-// in the first k_c columns of V and Z; columns k_c .. kr-1 (kr = max k_c)
-// are zero.  Returns kr.
+// data), C_c = V_c Q_c (orthonormal) in the first k_c columns of V, with
+// M U_c = C_c for U_c = Z_c R_c^{-1}: the first k_c columns of Z stay, R_c
+// is kept on the host, and U_c c = Z_c (R_c^{-1} c).  Columns k_c .. kr-1
+// (kr = max k_c) are zero.  Returns kr.
 static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_t ldv, int64_t ldz, cudaStream_t s) {
   const int64_t ldn = G.ldn;
   int kr = 0;
@@ -654,64 +658,67 @@ static int build_recycle(Gmres32Work& G, const HostArnoldi& ha, int nrhs, int64_
   if (kr <= 0) return 0;
   using cd = std::complex<double>;
   const size_t qsz = size_t(kr + 1) * kr, rsz = size_t(kr) * kr;
-  std::vector<cd> Q(qsz), R(rsz);
-  // per rhs: Q (column-major, leading dimension kr + 1) and R^-1 (upper
-  // triangular, leading dimension kr; columns by back substitution on the
-  // host in FP64, in parallel)
-  std::vector<float> qr32(size_t(nrhs) * (qsz + rsz) * 2, 0.f);
+  std::vector<cd> Q(qsz);
+  // per rhs: Q (column-major, leading dimension kr + 1) to the device, R kept on the host
+  std::vector<float> q32(size_t(nrhs) * qsz * 2, 0.f);
+  G.rec_R.assign(size_t(nrhs), std::vector<cd>());
+  G.rec_kc.assign(size_t(nrhs), 0);
   for (int c = 0; c < nrhs; ++c) {
     const int kc = ha.jc[c];
+    G.rec_kc[size_t(c)] = std::max(kc, 0);
     if (kc <= 0) continue;
-    ha.qr(c, kc, Q.data(), R.data(), kr);
-    float* qc = qr32.data() + size_t(c) * (qsz + rsz) * 2;
+    G.rec_R[size_t(c)].assign(rsz, cd(0));
+    ha.qr(c, kc, Q.data(), G.rec_R[size_t(c)].data(), kr);
+    float* qc = q32.data() + size_t(c) * qsz * 2;
     for (int p = 0; p < kc; ++p)
       for (int q = 0; q <= kc; ++q) {
         qc[2 * (size_t(p) * (kr + 1) + q)] = float(Q[size_t(p) * (kc + 1) + q].real());
         qc[2 * (size_t(p) * (kr + 1) + q) + 1] = float(Q[size_t(p) * (kc + 1) + q].imag());
       }
-    float* rc = qc + qsz * 2;
-    parallel_for(kc, long(kc) * kc * kc > 4000000 ? 16 : 1, [&](int j) {
-      std::vector<cd> xj(size_t(j) + 1);
-      xj[size_t(j)] = 1.0 / R[size_t(j) * kr + j];
-      for (int q = j - 1; q >= 0; --q) {
-        cd acc = 0;
-        for (int p = q + 1; p <= j; ++p) acc += R[size_t(p) * kr + q] * xj[size_t(p)];
-        xj[size_t(q)] = -acc / R[size_t(q) * kr + q];
-      }
-      for (int q = 0; q <= j; ++q) {
-        rc[2 * (size_t(j) * kr + q)] = float(xj[size_t(q)].real());
-        rc[2 * (size_t(j) * kr + q) + 1] = float(xj[size_t(q)].imag());
-      }
-    });
   }
   const size_t ncols = size_t(kr) * ldn * nrhs * 2;
   if (G.RC.n < ncols) G.RC.alloc(ncols);
-  if (G.RU.n < ncols) G.RU.alloc(ncols);
-  if (G.RQ.n < qr32.size()) G.RQ.alloc(qr32.size());
-  MTF_CUDA(cudaMemcpyAsync(G.RQ.p, qr32.data(), qr32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (G.RQ.n < q32.size()) G.RQ.alloc(q32.size());
+  MTF_CUDA(cudaMemcpyAsync(G.RQ.p, q32.data(), q32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   for (int c = 0; c < nrhs; ++c) {
     const int kc = ha.jc[c];
     float* Vc = G.V.p + 2 * size_t(c) * ldv;
     float* Zc = G.Z.p + 2 * size_t(c) * ldz;
     float* Cc = G.RC.p + 2 * size_t(c) * kr * ldn;
-    float* Uc = G.RU.p + 2 * size_t(c) * kr * ldn;
-    const float* Qd = G.RQ.p + size_t(c) * (qsz + rsz) * 2;
-    const float* Rid = Qd + qsz * 2;
+    const float* Qd = G.RQ.p + size_t(c) * qsz * 2;
     if (kc > 0) {
+      // C = V Q over the first kc + 1 basis vectors
       const dim3 grid(unsigned((ldn + 127) / 128), unsigned((kc + 31) / 32));
-      // C = V Q (the first kc + 1 basis vectors), U = Z R^-1
       MTF_LAUNCH(KID_MISC, s, k_cgemm_nn<<<grid, 256, 0, s>>>(Vc, ldn, Qd, kr + 1, kc + 1, kc, ldn, Cc, ldn));
-      MTF_LAUNCH(KID_MISC, s, k_cgemm_nn<<<grid, 256, 0, s>>>(Zc, ldn, Rid, kr, kc, kc, ldn, Uc, ldn));
       MTF_CUDA(cudaMemcpyAsync(Vc, Cc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
-      MTF_CUDA(cudaMemcpyAsync(Zc, Uc, size_t(kc) * ldn * 8, cudaMemcpyDeviceToDevice, s));
     }
     if (kc < kr) {
       MTF_CUDA(cudaMemsetAsync(Vc + 2 * size_t(kc) * ldn, 0, size_t(kr - kc) * ldn * 8, s));
       MTF_CUDA(cudaMemsetAsync(Zc + 2 * size_t(kc) * ldn, 0, size_t(kr - kc) * ldn * 8, s));
     }
   }
-  MTF_CUDA(cudaStreamSynchronize(s));  // qr32 is released on return
+  MTF_CUDA(cudaStreamSynchronize(s));  // q32 is released on return
   return kr;
+}
+
+// the coefficients of the recycled columns (entries 0 .. kr-1 of each rhs's
+// block of m + 1 complex values in yc) replaced by R_c^{-1} times them: back
+// substitution with the kept upper-triangular factor
+static void rec_coefficients(const Gmres32Work& G, std::vector<double>& yc, int nrhs, int m, int kr) {
+  using cd = std::complex<double>;
+  for (int c = 0; c < nrhs; ++c) {
+    const int kc = G.rec_kc[size_t(c)];
+    if (kc <= 0) continue;
+    const std::vector<cd>& R = G.rec_R[size_t(c)];
+    double* y = yc.data() + 2 * size_t(c) * (m + 1);
+    for (int q = kc - 1; q >= 0; --q) {
+      cd acc(y[2 * q], y[2 * q + 1]);
+      for (int p = q + 1; p < kc; ++p) acc -= R[size_t(p) * kr + q] * cd(y[2 * p], y[2 * p + 1]);
+      acc /= R[size_t(q) * kr + q];
+      y[2 * q] = acc.real();
+      y[2 * q + 1] = acc.imag();
+    }
+  }
 }
 
 mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double* x_dev, double tol, int max_iter,
@@ -836,7 +843,8 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
       active[c] = rn > 0 && beta > 0;
       any = any || active[c];
     }
-    x_update(yc, jcs);  // x += U (C^H r)
+    rec_coefficients(G, yc, nrhs, m, kr);
+    x_update(yc, jcs);  // x += U (C^H r) = Z (R^{-1} C^H r)
   }
   reached = !any;
   if (!any) return MTF_OK;
@@ -981,6 +989,7 @@ mtf_status fgmres_cycle32(mtf_system sys, int nrhs, const double* r_dev, double*
     }
     jcs[c] = kr + jl;
   }
+  if (kr > 0) rec_coefficients(G, yc, nrhs, m, kr);  // U (B y) = Z (R^{-1} B y)
   x_update(yc, jcs);
   // keep this cycle's space for the next cycle of the solve when there is
   // room for a useful number of new columns next to it
