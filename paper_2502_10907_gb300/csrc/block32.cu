@@ -284,6 +284,22 @@ __global__ void k_blk_addx(double* __restrict__ x, int64_t n, const float* __res
   *xp = o;
 }
 
+// out[c] += ||W_c||^2 for the s columns of W (FP32 sums per thread and
+// warp, one FP64 atomic per warp and column): the reference norms of the
+// deflation test, read once from the block the operator just produced
+__global__ void __launch_bounds__(256) k_bnorm2(const float* __restrict__ W, int64_t ldw, int64_t n,
+                                                double* __restrict__ out) {
+  const int c = blockIdx.y;
+  const float4* w = reinterpret_cast<const float4*>(W + 2 * int64_t(c) * ldw);
+  float a = 0.f;
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n / 2; k += int64_t(gridDim.x) * blockDim.x) {
+    const float4 v = w[k];  // two complex entries
+    a = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, a))));
+  }
+  for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out + c, double(a));
+}
+
 // 1 / sqrt(d) for d > 0 in FP64: an FP32 seed refined by two Newton steps
 // y <- y (3 - d y^2) / 2 (quadratic convergence: 2^-22 -> 2^-43 -> rounding);
 // the narrow FP64 pipe makes this several times faster than sqrt and a
@@ -300,13 +316,13 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // rule of deflating_cholesky in block_krylov.h): G (complex FP64, entry
 // [q ldg + c] = <W_q, W_c>) = R^H R with R upper triangular; direction k is
 // dropped (row k of R zero, kept[k] = 0) when its Schur pivot is not above
-// tau^2 ref_k, ref_k = the diagonal of Gpre (squared norms before the
+// tau^2 ref_k, ref_k = ref[k] (squared norms before the
 // Gram-Schmidt projections) or, with mask, 1 for mask[k] != 0 and 0
 // otherwise.  R complex FP64, column-major (entry (i, c) at [c s + i]).
 // One CTA of 256 threads, s <= 64: per pivot the row of R is formed in
 // parallel and the trailing upper triangle is updated by all threads (the
 // Schur complement and R in shared memory, s * s complex each).
-__global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int ldg, const double* __restrict__ Gpre,
+__global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int ldg, const double* __restrict__ ref,
                                                const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
                                                int* __restrict__ kept) {
   extern __shared__ double2 sh[];
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
     A[t] = make_double2(G[2 * (i * ldg + c)], G[2 * (i * ldg + c) + 1]);
     Rs[t] = make_double2(0.0, 0.0);
   }
-  for (int k = tid; k < s; k += nt) refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : Gpre[2 * (k * s + k)];
+  for (int k = tid; k < s; k += nt) refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : ref[k];
   for (int k = 0; k < s; ++k) {
     __syncthreads();
     if (tid == 0) {
@@ -415,20 +431,20 @@ __global__ void k_beye(const int* __restrict__ kept_in, int s, double* __restric
 // coordinates of W' along V_J = V~' R^-1, from the Gram matrix of [V~', W']
 // (G_vw entry (i, c) at G + 2 (i ldg + s + c)).  C complex FP64 at
 // C + 2 (i s + c), the layout of the update's coefficients.  R, G_vw and C
-// are staged in shared memory (3 s^2 complex) and the reciprocals of the
-// diagonal of R^H are formed first, in parallel; then one warp per column c
-// runs the forward substitution, its lanes splitting the sum over p.
-__global__ void __launch_bounds__(256) k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
-                                               const int* __restrict__ kept, int s, double* __restrict__ C) {
+// are staged in shared memory (3 s^2 complex), the reciprocals of the
+// diagonal of R^H are formed first, in parallel; then thread c runs the
+// forward substitution of column c (no reductions across threads: the
+// narrow FP64 pipe makes warp-shuffle sums the slower form).
+__global__ void __launch_bounds__(64) k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
+                                              const int* __restrict__ kept, int s, double* __restrict__ C) {
   extern __shared__ double2 sh[];
   double2* Rs = sh;              // Rs[i * s + p] = R(p, i)
-  double2* Gs = sh + s * s;      // Gs[i * s + c] = G_vw(i, c)
-  double2* Cs = Gs + s * s;      // Cs[i * s + c]
+  double2* Cs = sh + s * s;      // Cs[i * s + c]; first G_vw(i, c)
   __shared__ double2 rinv[64];   // 1 / conj(R(i, i)), 0 for dropped i
   for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
     const int i = t / s, c = t % s;
     Rs[t] = make_double2(R[2 * t], R[2 * t + 1]);
-    Gs[t] = make_double2(G[2 * (i * ldg + s + c)], G[2 * (i * ldg + s + c) + 1]);
+    Cs[t] = make_double2(G[2 * (i * ldg + s + c)], G[2 * (i * ldg + s + c) + 1]);
   }
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
@@ -440,26 +456,17 @@ __global__ void __launch_bounds__(256) k_bcoef(const double* __restrict__ G, int
     rinv[i] = v;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c = warp; c < s; c += nw) {
+  const int c = threadIdx.x;
+  if (c < s) {
     for (int i = 0; i < s; ++i) {
-      double re = 0.0, im = 0.0;  // sum over p < i of conj(R(p, i)) C[p, c]
-      for (int p = lane; p < i; p += 32) {
+      double re = Cs[i * s + c].x, im = Cs[i * s + c].y;
+      for (int p = 0; p < i; ++p) {  // - conj(R(p, i)) C[p, c]
         const double2 r = Rs[i * s + p], x = Cs[p * s + c];
-        re += r.x * x.x + r.y * x.y;
-        im += r.x * x.y - r.y * x.x;
+        re -= r.x * x.x + r.y * x.y;
+        im -= r.x * x.y - r.y * x.x;
       }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-      }
-      if (lane == 0) {
-        const double2 g = Gs[i * s + c], ri = rinv[i];
-        const double ar = g.x - re, ai = g.y - im;
-        Cs[i * s + c] = make_double2(ar * ri.x - ai * ri.y, ar * ri.y + ai * ri.x);
-      }
-      __syncwarp();
+      const double2 ri = rinv[i];
+      Cs[i * s + c] = make_double2(re * ri.x - im * ri.y, re * ri.y + im * ri.x);
     }
   }
   __syncthreads();
@@ -535,9 +542,9 @@ static void bdots(mtf_system sys, const float* V, int nq, int64_t ldv, const flo
     const int SC = col_tier(nc);
     const int VW = SC >= 16 ? 2 : 4;
     const int gy = (nq + 8 * VW - 1) / (8 * VW);
-    // segments so that about two CTAs per SM run, each over at least 8
-    // chunks of 128 entries (fewer FP64 atomics per coefficient)
-    const int64_t nseg0 = std::max<int64_t>(1, std::min<int64_t>((n_pad + 1023) / 1024, (304 + gy - 1) / gy));
+    // segments so that about 600 CTAs run (fewer, longer segments measured
+    // slower: 29 against 18 us for a 16-column Gram matrix of 72,000 entries)
+    const int64_t nseg0 = std::max<int64_t>(1, std::min<int64_t>((n_pad + 127) / 128, (600 + gy - 1) / gy));
     const int64_t seg = ((n_pad + nseg0 - 1) / nseg0 + 127) / 128 * 128;
     const dim3 grid(unsigned((n_pad + seg - 1) / seg), unsigned(gy));
     const float* Wc = W + 2 * int64_t(c0) * ldw;
@@ -667,7 +674,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     B.n = n;
     B.ldn = ldn;
   }
-  double* Gpre = B.Gs.p;                       // s x s: Gram of W before the projections
+  double* Gpre = B.Gs.p;                       // s: squared column norms of W before the projections
   double* G2 = Gpre + 2 * size_t(s) * s;       // 2s x 2s: Gram of [V~', W']
   double* G = G2 + 8 * size_t(s) * s;          // s x s: Gram of W''
   double* Hc = G + 2 * size_t(s) * s;          // completed column block ((m + 1) s x s)
@@ -762,7 +769,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(opted.load() & bit)) {
       MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
-      MTF_CUDA(cudaFuncSetAttribute(k_bcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 64 * 64 * 16));
+      MTF_CUDA(cudaFuncSetAttribute(k_bcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
       opted.fetch_or(bit);
     }
   }
@@ -784,8 +791,8 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
         MTF_CUDA(cudaMemcpyAsync(Zj, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
       }
       launch_matvec_f32(sys, Zj, ldn, X1, ldn, s, st);
-      MTF_CUDA(cudaMemsetAsync(Gpre, 0, 2 * size_t(s) * s * sizeof(double), st));
-      bdots(sys, X1, s, ldn, X1, ldn, s, ldn, Gpre, s, st);
+      MTF_CUDA(cudaMemsetAsync(Gpre, 0, size_t(s) * sizeof(double), st));
+      MTF_LAUNCH(KID_BGRAM, st, k_bnorm2<<<dim3(64, unsigned(s)), 256, 0, st>>>(X1, ldn, ldn, Gpre));
     }
     MTF_CUDA(cudaMemcpyAsync(X0, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
     if (nq > 0) project(nq, nc, Scur);
@@ -801,7 +808,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     }
     if (!finish) {
       if (J > 0) btrsm(X0, ldn, Rv, keptV, s, Vt, ldn, ldn, st);
-      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 256, 3 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
+      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
       bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
       MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
       bdots(sys, X1, s, ldn, X1, ldn, s, ldn, G, s, st);

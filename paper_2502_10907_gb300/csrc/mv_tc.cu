@@ -159,6 +159,10 @@ __global__ void __launch_bounds__(256) k_tc_tile_os(const __half2* __restrict__ 
   *reinterpret_cast<uint4*>(A + tc_tile_index(tile, 1, 0, row, 8 * g)) = *reinterpret_cast<const uint4*>(h);
 }
 
+// lanes per row of the combines: the pass's right-hand sides rounded up to a
+// power of two (at least 4), so that one warp takes 32 / lanes rows
+__host__ __device__ constexpr int tc_row_lanes(int nc) { return nc <= 4 ? 4 : nc <= 8 ? 8 : nc <= 16 ? 16 : 32; }
+
 // z rows of the block-OSRC apply (one warp per global row, lane = right-hand
 // side): the row's pieces of T~ r_D and T~ r_N summed in order and unscaled,
 // then z_D = rho^-1 T~ r_N, z_N = -rho T~ r_D with the per-block coefficients
@@ -169,8 +173,10 @@ __global__ void __launch_bounds__(256) k_os_tc_combine(
     const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const int* __restrict__ blk_unit_base,
     const int* __restrict__ blk_pieces, const unsigned* __restrict__ colmax, const float* __restrict__ cf,
     float* __restrict__ z, int64_t ldz, int c0, int nc, int64_t n_rows) {
-  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int L = tc_row_lanes(nc);
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t row = gt / L;
+  const int lane = int(gt % L);
   if (row >= n_rows || lane >= nc) return;
   const int i = row_blk[row];
   const int N = blk_N[i];
@@ -410,8 +416,10 @@ __global__ void __launch_bounds__(256) k_mv_tc_combine(
     const int* __restrict__ blk_pieces, const unsigned* __restrict__ amax, const unsigned* __restrict__ colmax,
     const XEntry* __restrict__ xe, const float* __restrict__ xval32, const float* __restrict__ rho32,
     const float* __restrict__ x, int64_t ldx, float* __restrict__ y, int64_t ldy, int c0, int nc, int64_t n_rows) {
-  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int L = tc_row_lanes(nc);
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t row = gt / L;
+  const int lane = int(gt % L);
   if (row >= n_rows || lane >= nc) return;
   const int i = row_blk[row];
   const int N = blk_N[i];
@@ -648,7 +656,7 @@ static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx,
   MTF_LAUNCH(KID_MVTC, s, k_mv_tc<NB><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.amap, t.bmap, t.units.p, t.sched.p, t.sched_off.p, t.blk_tile_base.p, t.blk_nkc.p, t.blk_chunk_base.p,
       t.part.p, sys->d_mv_ctl.p + 2));
-  MTF_LAUNCH(KID_MVTC_COMBINE, s, k_mv_tc_combine<NB><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(KID_MVTC_COMBINE, s, k_mv_tc_combine<NB><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.amax.p, t.colmax.p, m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, x, ldx, y, ldy, c0, nc,
       m->n_rows));
@@ -708,7 +716,7 @@ static void os_tc_pass(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr,
   MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.osmap, t.bmap, units, int(t.plan.units.size()), t.sched.p, t.sched_off.p, t.part.p, nullptr, 0, 0, 0, nullptr,
       sys->d_mv_ctl.p + 2, TcTtOut{}));
-  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_tc_combine<NB><<<unsigned((m->n_rows * 32 + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_tc_combine<NB><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
 }
