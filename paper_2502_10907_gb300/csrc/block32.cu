@@ -416,6 +416,48 @@ __global__ void __launch_bounds__(128) k_btrsm(const float* __restrict__ in, int
   }
 }
 
+// k_btrsm for wide blocks (s > 16): the same forward substitution with the
+// solved entries of each thread kept in shared memory instead of registers
+// (SC complex values per thread would spill), R and the reciprocals staged
+// as in k_btrsm.  Dynamic shared memory: SC^2 + SC x 128 complex FP32.
+template <int SC>
+__global__ void __launch_bounds__(128) k_btrsm_wide(const float* __restrict__ in, int64_t ldi,
+                                                    const double* __restrict__ R, const int* __restrict__ kept, int s,
+                                                    float* __restrict__ out, int64_t ldo, int64_t n_pad) {
+  extern __shared__ float2 shw[];
+  float2* rs = shw;             // rs[p * SC + q] = R(p, q)
+  float2* vs = shw + SC * SC;   // vs[q * 128 + thread]
+  __shared__ float2 inv[SC];
+  for (int t = threadIdx.x; t < SC * SC; t += blockDim.x) {
+    const int p = t / SC, q = t % SC;
+    rs[t] = (p < s && q < s) ? make_float2(float(R[2 * (q * s + p)]), float(R[2 * (q * s + p) + 1]))
+                             : make_float2(0.f, 0.f);
+  }
+  for (int q = threadIdx.x; q < SC; q += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (q < s && kept[q]) {
+      const double a = R[2 * (q * s + q)], b = R[2 * (q * s + q) + 1], d = a * a + b * b;
+      v = make_float2(float(a / d), float(-b / d));
+    }
+    inv[q] = v;
+  }
+  __syncthreads();
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n_pad) return;
+  for (int q = 0; q < s; ++q) {
+    float2 a = reinterpret_cast<const float2*>(in + 2 * int64_t(q) * ldi)[k];
+    for (int p = 0; p < q; ++p) {
+      const float2 r = rs[p * SC + q], v = vs[p * 128 + threadIdx.x];
+      a.x -= v.x * r.x - v.y * r.y;
+      a.y -= v.x * r.y + v.y * r.x;
+    }
+    const float2 iv = inv[q];
+    const float2 o = make_float2(a.x * iv.x - a.y * iv.y, a.x * iv.y + a.y * iv.x);
+    vs[q * 128 + threadIdx.x] = o;
+    reinterpret_cast<float2*>(out + 2 * int64_t(q) * ldo)[k] = o;
+  }
+}
+
 // R = the identity on the kept set (zero rows elsewhere), kept_out = kept_in:
 // the start block of a cycle is already orthonormal (no lagged second pass)
 __global__ void k_beye(const int* __restrict__ kept_in, int s, double* __restrict__ R, int* __restrict__ kept_out) {
@@ -620,8 +662,26 @@ static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept
   else if (s <= 4) MTF_BT(4);
   else if (s <= 8) MTF_BT(8);
   else if (s <= 16) MTF_BT(16);
-  else if (s <= 32) MTF_BT(32);
-  else MTF_BT(64);
+  else {
+    // wide blocks: solved entries in shared memory
+    const int SC = s <= 32 ? 32 : 64;
+    const size_t smem = size_t(SC) * SC * sizeof(float2) + size_t(SC) * 128 * sizeof(float2);
+    static std::atomic<uint64_t> opted{0};
+    int dev = 0;
+    MTF_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(opted.load() & bit)) {
+      MTF_CUDA(cudaFuncSetAttribute(k_btrsm_wide<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(32 * 32 * 8 + 32 * 128 * 8)));
+      MTF_CUDA(cudaFuncSetAttribute(k_btrsm_wide<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(64 * 64 * 8 + 64 * 128 * 8)));
+      opted.fetch_or(bit);
+    }
+    if (SC == 32)
+      MTF_LAUNCH(KID_BXFORM, st, k_btrsm_wide<32><<<g, 128, smem, st>>>(in, ldi, R, kept, s, out, ldo, n_pad));
+    else
+      MTF_LAUNCH(KID_BXFORM, st, k_btrsm_wide<64><<<g, 128, smem, st>>>(in, ldi, R, kept, s, out, ldo, n_pad));
+  }
 #undef MTF_BT
 }
 

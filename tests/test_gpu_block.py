@@ -83,3 +83,23 @@ def test_block_solve_deflates_dependent_and_zero_columns(api, cube4):
     assert torch.all(x[~lv] == 0)
     # the repeated wave gets the same solution as its twin
     assert float((x[0] - x[1]).abs().max()) <= 1e-5 * float(x[0].abs().max())
+
+
+@pytest.mark.parametrize("nw", [20, 40])
+def test_wide_block_solve_matches_oracle_lu(api, cube4, nw):
+    """Blocks wider than 16 vectors: the wide triangular solves (solved
+    entries in shared memory), Gram-Schmidt passes of up to 2 x 40 columns in
+    groups of 64, tensor-core applies in passes of up to 32 waves."""
+    cfg, sk, ref = cube4
+    dirs = mi.fibonacci_directions(nw // 2)
+    p1, p2 = mi.orthonormal_polarizations(dirs)
+    dirs = np.concatenate([dirs, dirs])
+    pols = np.concatenate([p1, p2]).astype(np.complex128)
+    xr = ref.solve_lu(ref.rhs(dirs, pols))
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    s = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, precond=1, tol=1e-8, restart=300,
+                   max_iter=6000, max_refine=6, block_krylov=1)
+    x, st = s.solve(dirs, pols)
+    assert st.converged == 1
+    errs = _errs(x, xr)
+    assert errs.max() < MIXED_TOL, errs
