@@ -50,7 +50,7 @@ struct BlockWork {
   TcArnoldi* tca = nullptr;  // tensor-core projections (arnoldi_tc.cu), with mv_tensor
   DevBuf<float> V, Z, X, D;  // (m + 1) s, m s, 2 s ([V~_J | W]), s vectors
   DevBuf<double> S[2];       // projection coefficients of two steps: (m + 1) s x 2 s, complex
-  DevBuf<double> Gs;         // Gpre (s x s) | G2 (2s x 2s) | G (s x s) | Hc ((m + 1) s x s) | Rn | R | Rv | Cc
+  DevBuf<double> Gs;         // Gpre (s) | G2 (2s x 2s) | G (s x s) | Hc ((m + 1) s x s) | Rn | R | Rv | Cc (two)
   DevBuf<double> C;          // s x s (complex, FP64) transform, or the coefficients Y (m s x s)
   DevBuf<int> kept;          // keptR (s) | keptV (s)
   double* h_host = nullptr;
@@ -322,13 +322,19 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // One CTA of 256 threads, s <= 64: per pivot the row of R is formed in
 // parallel and the trailing upper triangle is updated by all threads (the
 // Schur complement and R in shared memory, s * s complex each).
+//
+// With C non-null (the second CholQR pass of V~_J, G the Gram matrix of
+// [V~', W'] with leading dimension ldg = 2 s), the same CTA then forms
+// C = R^-H G_vw (G_vw(i, c) at G + 2 (i ldg + s + c)), the coordinates of W'
+// along V_J = V~' R^-1, rows of dropped directions zero; C complex FP64 at
+// C + 2 (i s + c), thread c solving column c from shared memory.
 __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int ldg, const double* __restrict__ ref,
                                                const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
-                                               int* __restrict__ kept) {
+                                               int* __restrict__ kept, double* __restrict__ C) {
   extern __shared__ double2 sh[];
-  double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c
+  double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c; then C
   double2* Rs = sh + s * s;  // Rs[c * s + i] = R(i, c)
-  __shared__ double piv, ipiv, refs[64];
+  __shared__ double piv, ipiv, refs[64], rinv[64];
   __shared__ int keep, keeps[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < s * s; t += nt) {
@@ -336,7 +342,10 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
     A[t] = make_double2(G[2 * (i * ldg + c)], G[2 * (i * ldg + c) + 1]);
     Rs[t] = make_double2(0.0, 0.0);
   }
-  for (int k = tid; k < s; k += nt) refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : ref[k];
+  for (int k = tid; k < s; k += nt) {
+    refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : ref[k];
+    rinv[k] = 0.0;
+  }
   for (int k = 0; k < s; ++k) {
     __syncthreads();
     if (tid == 0) {
@@ -346,6 +355,7 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
         const double y = rsqrt_newton(d);
         piv = d * y;
         ipiv = y;
+        rinv[k] = y;
       }
       keeps[k] = keep;
     }
@@ -372,6 +382,27 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
     R[2 * t + 1] = Rs[t].y;
   }
   for (int k = tid; k < s; k += nt) kept[k] = keeps[k];
+  if (C != nullptr && tid < s) {
+    const int c = tid;
+    double2* Cs = A;  // the Schur complement is no longer needed
+    for (int i = 0; i < s; ++i) {
+      double re = 0.0, im = 0.0;
+      if (keeps[i]) {
+        re = G[2 * (i * ldg + s + c)];
+        im = G[2 * (i * ldg + s + c) + 1];
+        for (int p = 0; p < i; ++p) {  // - conj(R(p, i)) C[p, c]
+          const double2 r = Rs[i * s + p], x = Cs[p * s + c];
+          re -= r.x * x.x + r.y * x.y;
+          im -= r.x * x.y - r.y * x.x;
+        }
+        re *= rinv[i];  // R(i, i) is real
+        im *= rinv[i];
+      }
+      Cs[i * s + c] = make_double2(re, im);
+      C[2 * (i * s + c)] = re;
+      C[2 * (i * s + c) + 1] = im;
+    }
+  }
 }
 
 // out_q[k] = (in_q[k] - sum_{p < q} out_p[k] R(p, q)) / R(q, q) for kept q,
@@ -685,6 +716,16 @@ static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept
 #undef MTF_BT
 }
 
+// G (nc x nc, complex FP64, G[a ldg + c] = <X_a, X_c>) of nc columns of
+// stride ldx over n_pad entries (bdots: FP32 products per segment, FP64
+// atomics; a two-stage kernel with per-CTA partial matrices measured slower,
+// its shared-memory loads per product outweighing the saved atomics)
+static void bgram(mtf_system sys, const float* X, int64_t ldx, int nc, int64_t n_pad, double* G, int ldg,
+                  cudaStream_t st) {
+  MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(nc) * ldg * sizeof(double), st));
+  bdots(sys, X, nc, ldx, X, ldx, nc, n_pad, G, ldg, st);
+}
+
 // relative size below which a new direction of a block is deflated (its norm
 // after orthogonalisation against the basis over its norm before): about a
 // hundred times the FP32 rounding of the basis, so that the directions kept
@@ -703,7 +744,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   BlockWork& B = *sys->bw;
   stream_prepare(sys, st);  // error word of the bounded waits
   const size_t nhc = size_t(m + 1) * s * s;  // complex entries of a Hessenberg column block
-  const size_t gsz = size_t(2) * (size_t(s) * s + 4 * size_t(s) * s + size_t(s) * s + nhc + 4 * size_t(s) * s);
+  const size_t gsz = size_t(2) * (size_t(s) * s + 4 * size_t(s) * s + size_t(s) * s + nhc + 5 * size_t(s) * s);
   // pinned slot of a step (doubles): column block (nhc complex) | Rn (s x s complex)
   const size_t slot_len = 2 * nhc + 2 * size_t(s) * s;
   if (B.s != s || B.m != m || B.n != n) {
@@ -741,7 +782,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   double* Rn = Hc + 2 * nhc;                   // its subdiagonal block
   double* R = Rn + 2 * size_t(s) * s;          // W'' = V~_{J+1} R
   double* Rv = R + 2 * size_t(s) * s;          // V~' = V_J Rv
-  double* Cc = Rv + 2 * size_t(s) * s;         // W' = V_J Cc + W''
+  double* CcBuf[2] = {Rv + 2 * size_t(s) * s, Rv + 4 * size_t(s) * s};  // W' = V_J Cc + W'' (steps by parity)
   int* keptR = B.kept.p;
   int* keptV = keptR + s;
   const int64_t vstride = int64_t(s) * ldn;  // complex entries per block of s vectors
@@ -838,6 +879,8 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   auto launch_step = [&](int J) {
     const bool finish = J == Jend;
     double* Scur = B.S[J & 1].p;
+    double* Cc = CcBuf[J & 1];
+    const double* Cprev = CcBuf[(J + 1) & 1];
     const double* Sprev = B.S[(J + 1) & 1].p;
     float* Vt = B.V.p + 2 * int64_t(J) * vstride;  // V~_J; V_J after the step
     const int nq = J * s;
@@ -856,23 +899,27 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     }
     MTF_CUDA(cudaMemcpyAsync(X0, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
     if (nq > 0) project(nq, nc, Scur);
-    MTF_CUDA(cudaMemsetAsync(G2, 0, 8 * size_t(s) * s * sizeof(double), st));
-    bdots(sys, B.X.p, nc, ldn, B.X.p, ldn, nc, ldn, G2, 2 * s, st);
+    bgram(sys, B.X.p, ldn, nc, ldn, G2, 2 * s, st);
     if (J == 0) {
       MTF_LAUNCH(KID_BCHOL, st, k_beye<<<1, 256, 0, st>>>(keptR, s, Rv, keptV));
     } else {
       // second CholQR pass of V~_J: directions that the first kept
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G2, 2 * s, nullptr, keptR, 1e-3, s, Rv, keptV));
+      // Rv and, for a step with an operator apply, Cc = Rv^-H G_vw
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G2, 2 * s, nullptr, keptR, 1e-3, s, Rv, keptV,
+                                                                   finish ? nullptr : Cc));
       MTF_LAUNCH(KID_BXFORM, st, k_bhcol<<<nbk(int64_t(nq + s) * s, 256), 256, 0, st>>>(
-          Sprev, Scur, Cc, R, Rv, nq - s, s, Hc, Rn));
+          Sprev, Scur, Cprev, R, Rv, nq - s, s, Hc, Rn));
     }
     if (!finish) {
       if (J > 0) btrsm(X0, ldn, Rv, keptV, s, Vt, ldn, ldn, st);
-      MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s, Cc));
+      // (step 0: V_0 is final, Cc = G_vw on its kept set)
+      if (J == 0)
+        MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s,
+                                                                                               Cc));
       bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
-      MTF_CUDA(cudaMemsetAsync(G, 0, 2 * size_t(s) * s * sizeof(double), st));
-      bdots(sys, X1, s, ldn, X1, ldn, s, ldn, G, s, st);
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R, keptR));
+      bgram(sys, X1, ldn, s, ldn, G, s, st);
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R, keptR,
+                                                                   nullptr));
       btrsm(X1, ldn, R, keptR, s, Vt + 2 * vstride, ldn, ldn, st);
       if (tc && J > 0) tca_store(*B.tca, Vt, J * s, st);
     }
