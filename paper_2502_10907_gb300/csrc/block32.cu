@@ -323,36 +323,63 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // parallel and the trailing upper triangle is updated by all threads (the
 // Schur complement and R in shared memory, s * s complex each).
 //
-// With C non-null (the second CholQR pass of V~_J, G the Gram matrix of
-// [V~', W'] with leading dimension ldg = 2 s), the same CTA then forms
-// C = R^-H G_vw (G_vw(i, c) at G + 2 (i ldg + s + c)), the coordinates of W'
-// along V_J = V~' R^-1, rows of dropped directions zero; C complex FP64 at
-// C + 2 (i s + c), thread c solving column c from shared memory.
+// With C non-null (the second CholQR pass of V~_J), the same CTA then forms
+// C = R^-H G_vw, the coordinates of W' along V_J = V~' R^-1, rows of dropped
+// directions zero, from Gwv (Gwv[2 (c s + i)] = <W'_c, V~'_i>, so G_vw(i, c)
+// = conj of it); C complex FP64 at C + 2 (i s + c), thread c solving
+// column c from shared memory.
+//
+// T: the arithmetic.  FP64 for the first pass, whose pivots decide the
+// deflation down to tau^2 = 1e-10 of a column's norm; FP32 for the second
+// pass, whose Gram matrix is the identity to the FP32 rounding of the
+// once-normalised block (its factor is I + O(2^-24) and FP32 keeps that),
+// on the FP32 pipes instead of the narrow FP64 one.
+template <class T>
+struct CxOf;
+template <>
+struct CxOf<double> {
+  using type = double2;
+};
+template <>
+struct CxOf<float> {
+  using type = float2;
+};
+
+__device__ __forceinline__ double rsqrt_of(double d) { return rsqrt_newton(d); }
+__device__ __forceinline__ float rsqrt_of(float d) {
+  const float y = rsqrtf(d);
+  return y * fmaf(-0.5f * d, y * y, 1.5f);  // one Newton step on the approximate reciprocal square root
+}
+
+template <class T>
 __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int ldg, const double* __restrict__ ref,
                                                const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
-                                               int* __restrict__ kept, double* __restrict__ C) {
-  extern __shared__ double2 sh[];
-  double2* A = sh;           // A[c * s + i] = Schur complement entry (i, c), i <= c; then C
-  double2* Rs = sh + s * s;  // Rs[c * s + i] = R(i, c)
-  __shared__ double piv, ipiv, refs[64], rinv[64];
+                                               int* __restrict__ kept, const double* __restrict__ Gwv,
+                                               double* __restrict__ C) {
+  using T2 = typename CxOf<T>::type;
+  extern __shared__ __align__(16) unsigned char shb[];
+  T2* A = reinterpret_cast<T2*>(shb);  // A[c * s + i] = Schur complement entry (i, c), i <= c; then C
+  T2* Rs = A + s * s;                  // Rs[c * s + i] = R(i, c)
+  __shared__ T piv, ipiv, rinv[64];
+  __shared__ double refs[64];
   __shared__ int keep, keeps[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < s * s; t += nt) {
     const int c = t / s, i = t % s;
-    A[t] = make_double2(G[2 * (i * ldg + c)], G[2 * (i * ldg + c) + 1]);
-    Rs[t] = make_double2(0.0, 0.0);
+    A[t] = T2{T(G[2 * (i * ldg + c)]), T(G[2 * (i * ldg + c) + 1])};
+    Rs[t] = T2{T(0), T(0)};
   }
   for (int k = tid; k < s; k += nt) {
     refs[k] = mask ? (mask[k] ? 1.0 : 0.0) : ref[k];
-    rinv[k] = 0.0;
+    rinv[k] = T(0);
   }
   for (int k = 0; k < s; ++k) {
     __syncthreads();
     if (tid == 0) {
-      const double d = A[k * s + k].x;
-      keep = (d > tau * tau * fmax(refs[k], 0.0) && d > 0.0) ? 1 : 0;
+      const T d = A[k * s + k].x;
+      keep = (double(d) > tau * tau * fmax(refs[k], 0.0) && d > T(0)) ? 1 : 0;
       if (keep) {
-        const double y = rsqrt_newton(d);
+        const T y = rsqrt_of(d);
         piv = d * y;
         ipiv = y;
         rinv[k] = y;
@@ -361,46 +388,46 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
     }
     __syncthreads();
     if (!keep) continue;
-    const double ip = ipiv;
+    const T ip = ipiv;
     for (int c = k + tid; c < s; c += nt) {
-      const double2 a = A[c * s + k];
-      Rs[c * s + k] = c == k ? make_double2(piv, 0.0) : make_double2(a.x * ip, a.y * ip);
+      const T2 a = A[c * s + k];
+      Rs[c * s + k] = c == k ? T2{piv, T(0)} : T2{a.x * ip, a.y * ip};
     }
     __syncthreads();
     const int w = s - k - 1;
     for (int t = tid; t < w * w; t += nt) {
       const int i = k + 1 + t % w, c = k + 1 + t / w;
       if (i > c) continue;
-      const double2 ri = Rs[i * s + k], rc = Rs[c * s + k];  // R(k, i), R(k, c)
-      A[c * s + i].x -= ri.x * rc.x + ri.y * rc.y;            // conj(R(k, i)) R(k, c)
+      const T2 ri = Rs[i * s + k], rc = Rs[c * s + k];  // R(k, i), R(k, c)
+      A[c * s + i].x -= ri.x * rc.x + ri.y * rc.y;      // conj(R(k, i)) R(k, c)
       A[c * s + i].y -= ri.x * rc.y - ri.y * rc.x;
     }
   }
   __syncthreads();
   for (int t = tid; t < s * s; t += nt) {
-    R[2 * t] = Rs[t].x;
-    R[2 * t + 1] = Rs[t].y;
+    R[2 * t] = double(Rs[t].x);
+    R[2 * t + 1] = double(Rs[t].y);
   }
   for (int k = tid; k < s; k += nt) kept[k] = keeps[k];
   if (C != nullptr && tid < s) {
     const int c = tid;
-    double2* Cs = A;  // the Schur complement is no longer needed
+    T2* Cs = A;  // the Schur complement is no longer needed
     for (int i = 0; i < s; ++i) {
-      double re = 0.0, im = 0.0;
+      T re = T(0), im = T(0);
       if (keeps[i]) {
-        re = G[2 * (i * ldg + s + c)];
-        im = G[2 * (i * ldg + s + c) + 1];
+        re = T(Gwv[2 * (c * s + i)]);    // G_vw(i, c) = conj(<W'_c, V~'_i>)
+        im = -T(Gwv[2 * (c * s + i) + 1]);
         for (int p = 0; p < i; ++p) {  // - conj(R(p, i)) C[p, c]
-          const double2 r = Rs[i * s + p], x = Cs[p * s + c];
+          const T2 r = Rs[i * s + p], x = Cs[p * s + c];
           re -= r.x * x.x + r.y * x.y;
           im -= r.x * x.y - r.y * x.x;
         }
         re *= rinv[i];  // R(i, i) is real
         im *= rinv[i];
       }
-      Cs[i * s + c] = make_double2(re, im);
-      C[2 * (i * s + c)] = re;
-      C[2 * (i * s + c) + 1] = im;
+      Cs[i * s + c] = T2{re, im};
+      C[2 * (i * s + c)] = double(re);
+      C[2 * (i * s + c) + 1] = double(im);
     }
   }
 }
@@ -501,14 +528,14 @@ __global__ void k_beye(const int* __restrict__ kept_in, int s, double* __restric
 }
 
 // C = R^-H G_vw on the kept set (rows of dropped directions zero): the
-// coordinates of W' along V_J = V~' R^-1, from the Gram matrix of [V~', W']
-// (G_vw entry (i, c) at G + 2 (i ldg + s + c)).  C complex FP64 at
+// coordinates of W' along V_J = V~' R^-1, from Gwv[2 (c s + i)] =
+// <W'_c, V~'_i> (G_vw(i, c) is its conjugate).  C complex FP64 at
 // C + 2 (i s + c), the layout of the update's coefficients.  R, G_vw and C
 // are staged in shared memory (3 s^2 complex), the reciprocals of the
 // diagonal of R^H are formed first, in parallel; then thread c runs the
 // forward substitution of column c (no reductions across threads: the
 // narrow FP64 pipe makes warp-shuffle sums the slower form).
-__global__ void __launch_bounds__(64) k_bcoef(const double* __restrict__ G, int ldg, const double* __restrict__ R,
+__global__ void __launch_bounds__(64) k_bcoef(const double* __restrict__ Gwv, const double* __restrict__ R,
                                               const int* __restrict__ kept, int s, double* __restrict__ C) {
   extern __shared__ double2 sh[];
   double2* Rs = sh;              // Rs[i * s + p] = R(p, i)
@@ -517,7 +544,7 @@ __global__ void __launch_bounds__(64) k_bcoef(const double* __restrict__ G, int 
   for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
     const int i = t / s, c = t % s;
     Rs[t] = make_double2(R[2 * t], R[2 * t + 1]);
-    Cs[t] = make_double2(G[2 * (i * ldg + s + c)], G[2 * (i * ldg + s + c) + 1]);
+    Cs[t] = make_double2(Gwv[2 * (c * s + i)], -Gwv[2 * (c * s + i) + 1]);  // conj(<W'_c, V~'_i>)
   }
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
@@ -776,7 +803,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     B.ldn = ldn;
   }
   double* Gpre = B.Gs.p;                       // s: squared column norms of W before the projections
-  double* G2 = Gpre + 2 * size_t(s) * s;       // 2s x 2s: Gram of [V~', W']
+  double* G2 = Gpre + 2 * size_t(s) * s;       // 2s x s: <X_q, V~'_c> for the columns q of [V~', W']
   double* G = G2 + 8 * size_t(s) * s;          // s x s: Gram of W''
   double* Hc = G + 2 * size_t(s) * s;          // completed column block ((m + 1) s x s)
   double* Rn = Hc + 2 * nhc;                   // its subdiagonal block
@@ -869,12 +896,13 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     MTF_CUDA(cudaGetDevice(&dev));
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(opted.load() & bit)) {
-      MTF_CUDA(cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
+      MTF_CUDA(cudaFuncSetAttribute(k_bchol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
+      MTF_CUDA(cudaFuncSetAttribute(k_bchol<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
       MTF_CUDA(cudaFuncSetAttribute(k_bcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16));
       opted.fetch_or(bit);
     }
   }
-  const size_t chol_smem = 2 * size_t(s) * s * sizeof(double2);
+  const size_t chol_smem = 2 * size_t(s) * s * sizeof(double2), chol_smem32 = 2 * size_t(s) * s * sizeof(float2);
   auto slot = [&](int J) { return B.pin + size_t(J & 1) * slot_len; };
   auto launch_step = [&](int J) {
     const bool finish = J == Jend;
@@ -899,14 +927,18 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     }
     MTF_CUDA(cudaMemcpyAsync(X0, Vt, size_t(s) * ldn * 8, cudaMemcpyDeviceToDevice, st));
     if (nq > 0) project(nq, nc, Scur);
-    bgram(sys, B.X.p, ldn, nc, ldn, G2, 2 * s, st);
+    // <X_q, V~'_c> for every column q of X = [V~', W'] (G_vv, then the
+    // conjugate of G_vw): one pass with s right-hand columns
+    MTF_CUDA(cudaMemsetAsync(G2, 0, 2 * size_t(nc) * s * sizeof(double), st));
+    bdots(sys, B.X.p, nc, ldn, X0, ldn, s, ldn, G2, s, st);
+    const double* Gwv = G2 + 2 * size_t(s) * s;
     if (J == 0) {
       MTF_LAUNCH(KID_BCHOL, st, k_beye<<<1, 256, 0, st>>>(keptR, s, Rv, keptV));
     } else {
       // second CholQR pass of V~_J: directions that the first kept
       // Rv and, for a step with an operator apply, Cc = Rv^-H G_vw
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G2, 2 * s, nullptr, keptR, 1e-3, s, Rv, keptV,
-                                                                   finish ? nullptr : Cc));
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<float><<<1, 256, chol_smem32, st>>>(G2, s, nullptr, keptR, 1e-3, s, Rv, keptV,
+                                                                          Gwv, finish ? nullptr : Cc));
       MTF_LAUNCH(KID_BXFORM, st, k_bhcol<<<nbk(int64_t(nq + s) * s, 256), 256, 0, st>>>(
           Sprev, Scur, Cprev, R, Rv, nq - s, s, Hc, Rn));
     }
@@ -914,12 +946,11 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
       if (J > 0) btrsm(X0, ldn, Rv, keptV, s, Vt, ldn, ldn, st);
       // (step 0: V_0 is final, Cc = G_vw on its kept set)
       if (J == 0)
-        MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(G2, 2 * s, Rv, keptV, s,
-                                                                                               Cc));
+        MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(Gwv, Rv, keptV, s, Cc));
       bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
       bgram(sys, X1, ldn, s, ldn, G, s, st);
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R, keptR,
-                                                                   nullptr));
+      MTF_LAUNCH(KID_BCHOL, st, k_bchol<double><<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R,
+                                                                           keptR, nullptr, nullptr));
       btrsm(X1, ldn, R, keptR, s, Vt + 2 * vstride, ldn, ldn, st);
       if (tc && J > 0) tca_store(*B.tca, Vt, J * s, st);
     }
