@@ -1,7 +1,6 @@
 // Internal declarations of libmtf (not part of the public C-ABI).
 #pragma once
 
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -362,13 +361,7 @@ void destroy_gmres32(Gmres32Work* w);
 void destroy_block32(BlockWork* w);
 void destroy_tc(TcMatvec* t);
 void destroy_tt(TtForm* t);
-// the calling device's cuBLAS handle, bound to stream s, FP32 pedantic math;
-// the device's lock is held while the lease lives
-struct BlasLease {
-  cublasHandle_t h;
-  std::unique_lock<std::mutex> lock;
-};
-BlasLease blas_lease(cudaStream_t s);
+
 // right-hand sides of one pass of the FMA streaming applies; wider applies
 // go to the tensor cores (mv_tensor)
 constexpr int kFmaPassRhs = 4;

@@ -277,7 +277,14 @@ __global__ void k_to_f32_cols(const double* __restrict__ x, int64_t ldx, int64_t
 // setting is shared state), in FP32 pedantic math (no TF32 rounding)
 static constexpr int kMaxDev = 64;
 
-BlasLease blas_lease(cudaStream_t s) {
+// the calling device's cuBLAS handle, bound to stream s, FP32 pedantic math;
+// the device's lock is held while the lease lives
+struct BlasLease {
+  cublasHandle_t h;
+  std::unique_lock<std::mutex> lock;
+};
+
+static BlasLease blas_lease(cudaStream_t s) {
   static cublasHandle_t h[kMaxDev] = {};
   static std::mutex mu[kMaxDev];
   int dev = 0;

@@ -105,3 +105,26 @@ def test_autotuned_system_matches_oracle(api, instances):
     xt, st = s.solve(cfg["dirs"], np.array(cfg["pols"], dtype=np.complex128))
     assert st.converged == 1
     assert _errs(xt, xr).max() < 1e-5
+
+
+def test_batch_reports_the_failing_instance_and_finishes_the_others(api, instances):
+    """An instance that cannot reach its tolerance within its iteration cap
+    makes the batch return MTF_ERR_NOCONV (with raise_on_noconv off), while
+    every other instance still runs to its own converged solution."""
+    meshes = [api.Mesh.from_inputs(cfg["mesh"]) for cfg, _, _, _ in instances]
+    dirs = [cfg["dirs"] for cfg, _, _, _ in instances]
+    pols = [np.array(cfg["pols"], dtype=np.complex128) for cfg, _, _, _ in instances]
+    systems = []
+    for q, (m, (cfg, _, _, _)) in enumerate(zip(meshes, instances)):
+        cap = 3 if q == 1 else 6000
+        systems.append(api.System(m, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, precond=1, tol=1e-8,
+                                  restart=500, max_iter=cap, max_refine=6))
+    xs, st = api.solve_batch(systems, dirs, pols, raise_on_noconv=False)
+    assert st[1].converged == 0
+    for q, (x, s, (_, _, _, xr)) in enumerate(zip(xs, st, instances)):
+        if q == 1:
+            continue
+        assert s.converged == 1
+        assert _errs(x, xr).max() < 1e-5
+    with pytest.raises(api.L.MtfError):
+        api.solve_batch(systems, dirs, pols)
