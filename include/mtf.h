@@ -130,9 +130,10 @@ typedef struct {
                            faster there) and mv_tensor = 0 use the FMA
                            streams, one pass per 4.  Default 1               */
   int32_t residual_fp64;/* mixed mode: 1: the assembly also forms the FP64
-                           blocks (FP64 regular and singular pairs, 32 B per
-                           entry more) and the outer refinement residuals
-                           b - M x apply them in FP64, so the solution
+                           blocks (FP64 regular and singular pairs, kept as
+                           FP64 and as FP32 pairs, 64 B per entry more) and
+                           the outer refinement residuals b - M x apply them
+                           with double-float sums (about 2^-46), so the solution
                            converges to the FP64-assembled system's rather
                            than to the FP32-stored one's (whose difference
                            is the FP32 entry error, about 1e-7, times the

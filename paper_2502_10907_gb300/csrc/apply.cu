@@ -177,8 +177,14 @@ __device__ __forceinline__ void df_mac(float& hi, float& lo, float a, float xh, 
   lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
+// E64: the operator is the FP64 blocks, given as FP32 pairs (TK = fl(v),
+// TKlo = fl(v - fl(v)), split once per assembly): every product adds the
+// lo part times the input's hi part to the running lo sum, so the residual
+// of the FP64-assembled system costs FP32 work (residual_fp64).
+template <bool E64>
 __global__ void __launch_bounds__(256) k_matvec_df(
-    const float* __restrict__ TK, const XEntry* __restrict__ xe, const double* __restrict__ xval,
+    const float* __restrict__ TK, const float* __restrict__ TKlo, const XEntry* __restrict__ xe,
+    const double* __restrict__ xval,
     const int32_t* __restrict__ row_blk, const int64_t* __restrict__ blk_row_off,
     const int32_t* __restrict__ blk_N, const int64_t* __restrict__ blk_dof_off,
     const int64_t* __restrict__ blk_mat_off, const double* __restrict__ rho, const double* __restrict__ x,
@@ -192,6 +198,7 @@ __global__ void __launch_bounds__(256) k_matvec_df(
   const int N = blk_N[i];
   const int64_t off = blk_dof_off[i];
   const float* row = TK + 4 * (blk_mat_off[i] + m * N);
+  const float* rowlo = E64 ? TKlo + 4 * (blk_mat_off[i] + m * N) : nullptr;
   const double rr = rho[2 * i], ri = rho[2 * i + 1];
   const double rn = rr * rr + ri * ri;
   const double ir = rr / rn, ii = -ri / rn;  // 1 / rho
@@ -204,11 +211,14 @@ __global__ void __launch_bounds__(256) k_matvec_df(
       for (int q = 0; q < 8; ++q) ah[c][q] = al[c][q] = 0.f;
     constexpr int U = 4;
     for (int n0 = lane; n0 < N; n0 += 32 * U) {
-      float4 e[U];
+      float4 e[U], el[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int n = n0 + 32 * u;
-        if (n < N) e[u] = __ldg(reinterpret_cast<const float4*>(row) + n);
+        if (n < N) {
+          e[u] = __ldg(reinterpret_cast<const float4*>(row) + n);
+          if constexpr (E64) el[u] = __ldg(reinterpret_cast<const float4*>(rowlo) + n);
+        }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -242,6 +252,18 @@ __global__ void __launch_bounds__(256) k_matvec_df(
             df_mac(H[6], Lo[6], -Ki, nh.y, nl.y);
             df_mac(H[7], Lo[7], Kr, nh.y, nl.y);
             df_mac(H[7], Lo[7], Ki, nh.x, nl.x);
+            if constexpr (E64) {
+              // the entries' lo parts times the inputs' hi parts
+              const float tr = el[u].x, ti = el[u].y, kr = el[u].z, ki = el[u].w;
+              Lo[0] = fmaf(tr, dh.x, fmaf(-ti, dh.y, Lo[0]));
+              Lo[1] = fmaf(tr, dh.y, fmaf(ti, dh.x, Lo[1]));
+              Lo[2] = fmaf(tr, nh.x, fmaf(-ti, nh.y, Lo[2]));
+              Lo[3] = fmaf(tr, nh.y, fmaf(ti, nh.x, Lo[3]));
+              Lo[4] = fmaf(kr, dh.x, fmaf(-ki, dh.y, Lo[4]));
+              Lo[5] = fmaf(kr, dh.y, fmaf(ki, dh.x, Lo[5]));
+              Lo[6] = fmaf(kr, nh.x, fmaf(-ki, nh.y, Lo[6]));
+              Lo[7] = fmaf(kr, nh.y, fmaf(ki, nh.x, Lo[7]));
+            }
           }
         }
       }
@@ -311,7 +333,18 @@ void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, 
   mtf_mesh m = sys->mesh;
   const unsigned blocks = unsigned((m->n_rows * 32 + 255) / 256);
   if (kind == MV_AUTO) kind = sys->opt.precision == MTF_PREC_FP64 ? MV_FP64 : MV_FP32;
-  if (kind == MV_FP64) {
+  if (kind == MV_FP64 && sys->opt.precision != MTF_PREC_FP64 && sys->d_TK64hl.p) {
+    // mixed path with residual_fp64: the FP64 blocks as FP32 pairs, double-float sums
+    const int64_t n2 = 2 * m->n_total;
+    if (sys->d_x32.n < 2 * size_t(n2) * nrhs) sys->d_x32.alloc(2 * size_t(n2) * nrhs);
+    float* xh = sys->d_x32.p;
+    float* xl = xh + size_t(n2) * nrhs;
+    MTF_LAUNCH(KID_MISC, s, k_split_f32<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(x, ldx, n2, nrhs, xh, xl));
+    MTF_LAUNCH(KID_MATVEC64, s, k_matvec_df<true><<<blocks, 256, 0, s>>>(
+        sys->d_TK64hl.p, sys->d_TK64hl.p + size_t(m->n_mat) * 4, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p,
+        m->d_blk_row_off.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, xh, xl,
+        m->n_total, y, ldy, nrhs, m->n_rows));
+  } else if (kind == MV_FP64) {
     MTF_LAUNCH(KID_MATVEC64, s, k_matvec<double, double, double><<<blocks, 256, 0, s>>>(
         sys->d_TK64.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
         m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, x, ldx, y, ldy, nrhs, m->n_rows));
@@ -327,8 +360,8 @@ void launch_matvec_kind(mtf_system sys, int kind, const double* x, int64_t ldx, 
     float* xh = sys->d_x32.p;
     float* xl = xh + size_t(n2) * nrhs;
     MTF_LAUNCH(KID_MISC, s, k_split_f32<<<unsigned((n2 * nrhs + 255) / 256), 256, 0, s>>>(x, ldx, n2, nrhs, xh, xl));
-    MTF_LAUNCH(KID_MATVEC64, s, k_matvec_df<<<blocks, 256, 0, s>>>(
-        sys->d_TK32.p, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
+    MTF_LAUNCH(KID_MATVEC64, s, k_matvec_df<false><<<blocks, 256, 0, s>>>(
+        sys->d_TK32.p, nullptr, m->d_xent.p, sys->d_xval.p, m->d_row_blk.p, m->d_blk_row_off.p, m->d_blk_N.p,
         m->d_blk_dof_off.p, m->d_blk_mat_off.p, sys->d_rho.p, x, ldx, xh, xl, m->n_total, y, ldy, nrhs, m->n_rows));
   } else {
     MTF_LAUNCH(KID_MATVEC64, s, k_matvec<float, double, double><<<blocks, 256, 0, s>>>(

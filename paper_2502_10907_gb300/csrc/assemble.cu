@@ -548,6 +548,16 @@ static BlockArgs block_args(mtf_system sys) {
   return A;
 }
 
+// v[k] -> out[k] = fl(v[k]), out[n + k] = fl(v[k] - fl(v[k]))
+__global__ void k_split_pairs(const double* __restrict__ v, int64_t n, float* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double a = v[t];
+  const float h = float(a);
+  out[t] = h;
+  out[n + t] = float(a - double(h));
+}
+
 void launch_assemble(mtf_system sys, cudaStream_t s) {
   mtf_mesh m = sys->mesh;
   upload_rule_constants(s);
@@ -575,6 +585,14 @@ void launch_assemble(mtf_system sys, cudaStream_t s) {
       MTF_LAUNCH(KID_SINGULAR64, s, k_singular64<double><<<sblocks, 256, 0, s>>>(
           A, m->d_sing.p, np, sys->d_ss_pts[0].p, sys->d_ss_pts[1].p, sys->d_ss_pts[2].p, sys->ss_npts[0],
           sys->ss_npts[1], sys->ss_npts[2], sys->d_TK64.p));
+  }
+  if (fp64_blocks && sys->opt.precision != MTF_PREC_FP64) {
+    // residual_fp64: the FP64 entries split into FP32 pairs once per assembly,
+    // for the double-float residual matvec
+    const int64_t nv = m->n_mat * 4;
+    sys->d_TK64hl.alloc(size_t(nv) * 2);
+    MTF_LAUNCH(KID_MISC, s, k_split_pairs<<<unsigned((nv + 255) / 256), 256, 0, s>>>(sys->d_TK64.p, nv,
+                                                                                     sys->d_TK64hl.p));
   }
   if (sys->opt.precision != MTF_PREC_FP64) {
     // mixed: FP32 storage; regular pairs in FP32, singular pairs in FP64

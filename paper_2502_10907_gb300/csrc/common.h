@@ -197,6 +197,7 @@ struct mtf_system_s {
   mtf::DevBuf<double> d_k, d_rho;            // (re, im) per block
   mtf::DevBuf<double> d_wdir, d_wpol, d_brhs;  // mtf_solve: wave parameters and right-hand sides (kept)
   mtf::DevBuf<double> d_TK64;                // FP64: 4 doubles per dense entry
+  mtf::DevBuf<float> d_TK64hl;               // residual_fp64: the FP64 entries as FP32 pairs (all hi, then all lo)
   mtf::DevBuf<float> d_TK32;                 // mixed: 4 floats per dense entry
   mtf::DevBuf<float> d_TK32t;                // the same, tiled per stream unit (streaming matvec)
   mtf::DevBuf<double> d_xval;                // exchange values (6 per row)

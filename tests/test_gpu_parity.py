@@ -413,3 +413,22 @@ def test_mixed_residual_matvec_is_exact_for_the_stored_operator(api, oracle_cach
             yr[:, Ni] += (2.0 * (-r * (dT @ x[:, Di].T) + dK @ x[:, Ni].T)).T
         assert rel(y, yr) < tol, (df, rel(y, yr))
         assert rel(y, ref.matvec(x.T).T) > 1e-9      # the FP32 storage error is visible
+
+
+@pytest.mark.parametrize("name", ["split", "cubes"])
+def test_residual_fp64_matvec_matches_the_fp64_blocks(api, oracle_cache, name):
+    """residual_fp64: the mixed system keeps the FP64 blocks as FP32 pairs and
+    applies them with double-float sums (the refinement residual and
+    mtf_matvec); against the FP64 system's FP64 matvec of the same blocks the
+    difference is the double-float rounding, far below the FP32 entry error."""
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"])
+    sdf = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, residual_fp64=1)
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal((5, sk.n_total)) + 1j * rng.standard_normal((5, sk.n_total))
+    xt = torch.from_numpy(x).cuda()
+    y64 = s64.matvec(xt).cpu().numpy()
+    ydf = sdf.matvec(xt).cpu().numpy()
+    assert rel(ydf, y64) < 1e-12, rel(ydf, y64)
+    assert np.abs(ydf - y64).max() < 1e-12 * np.abs(y64).max()
