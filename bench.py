@@ -486,7 +486,7 @@ def batch_instances(api, L, args):
             "instances": len(cfgs), "nrhs_total": nrhs_tot, "unknowns_min_max": [min(n_tot), max(n_tot)],
             "unknowns_total": sum(n_tot), "setup_seconds": round(t_setup, 2),
             "batch": {"value": nrhs_tot / t_batch, "unit": UNIT, "seconds": t_batch,
-                      "how": "mtf_solve_batch: instances on their own streams, 8 host worker threads"},
+                      "how": "mtf_solve_batch: instances on their own streams, 4 host worker threads"},
             "loop": {"value": nrhs_tot / t_loop, "unit": UNIT, "seconds": t_loop, "how": "mtf_solve per instance"},
             "batch_over_loop": t_loop / t_batch,
             "autotune_choices": chosen,

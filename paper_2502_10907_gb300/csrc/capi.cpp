@@ -363,7 +363,7 @@ mtf_status mtf_solve_batch(int32_t n, const mtf_system* systems, const int32_t* 
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return double(systems[a]->mesh->n_total) * nrhs[a] > double(systems[b]->mesh->n_total) * nrhs[b];
     });
-    const int nt = std::max(1, std::min<int>(n, threads > 0 ? threads : 8));
+    const int nt = std::max(1, std::min<int>(n, threads > 0 ? threads : 4));
     // every instance starts after the work queued on the caller's stream
     cudaEvent_t start = nullptr;
     MTF_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
