@@ -260,7 +260,7 @@ def oracle_sample(cfg, iters, budget_s=12.0):
 # the default bench run measured them on a GB300; the reference arm runs
 # without the GPU and extrapolates the oracle's step with these counts
 # (--ref-iters overrides).
-MEASURED_APPLIES = {"cube4": 838, "split_sphere": 436, "sphere": 28, "cube2": 700}
+MEASURED_APPLIES = {"cube4": 840, "split_sphere": 439, "sphere": 28, "cube2": 104}
 
 
 def run_reference(args, cfg):
