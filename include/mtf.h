@@ -140,6 +140,14 @@ typedef struct {
                            conditioning); mtf_matvec then applies the FP64
                            blocks.  0: residuals of the FP32-stored blocks
                            (residual_df).  Default 0                         */
+  double inner_tol_min; /* mixed mode: lower bound of the relative tolerance
+                           given to an inner FP32 FGMRES cycle (the cycle's
+                           target is 0.3 tol / (current FP64 residual),
+                           clamped to [inner_tol_min, 0.5]); a smaller bound
+                           lets the first cycle run further before the FP64
+                           residual is taken, a larger one restarts sooner.
+                           0 selects the default 1e-5; otherwise in
+                           [1e-9, 0.5]                                       */
 } mtf_options;
 
 typedef struct {

@@ -167,6 +167,8 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
       MTF_REQUIRE(sys->opt.mv_tensor == 0 || sys->opt.mv_tensor == 1, MTF_ERR_ARG, "mv_tensor must be 0 or 1");
       MTF_REQUIRE(sys->opt.residual_fp64 == 0 || sys->opt.residual_fp64 == 1, MTF_ERR_ARG,
                   "residual_fp64 must be 0 or 1");
+      MTF_REQUIRE(sys->opt.inner_tol_min == 0.0 || (sys->opt.inner_tol_min >= 1e-9 && sys->opt.inner_tol_min <= 0.5),
+                  MTF_ERR_ARG, "inner_tol_min must be 0 or in [1e-9, 0.5]");
       MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {

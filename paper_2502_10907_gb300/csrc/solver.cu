@@ -605,7 +605,8 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
       for (int c = 0; c < nrhs; ++c)
         if (rel[c] <= sys->opt.tol)
           MTF_CUDA(cudaMemsetAsync(G.b.p + 2 * size_t(c) * n, 0, size_t(n) * 2 * sizeof(double), s));
-      const double inner_tol = std::min(0.5, std::max(1e-5, 0.3 * sys->opt.tol / rmax));
+      const double tol_min = sys->opt.inner_tol_min > 0 ? sys->opt.inner_tol_min : 1e-5;
+      const double inner_tol = std::min(0.5, std::max(tol_min, 0.3 * sys->opt.tol / rmax));
       std::vector<int> it_in(nrhs, 0);
       bool reached = false;
       // 4 or more right-hand sides share one block space (with or without
