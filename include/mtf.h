@@ -148,6 +148,13 @@ typedef struct {
                            residual is taken, a larger one restarts sooner.
                            0 selects the default 1e-5; otherwise in
                            [1e-9, 0.5]                                       */
+  int32_t gs_dots_half; /* mixed mode, block_krylov with mv_tensor: 1: the
+                           Gram-Schmidt dots V^H W read the FP16 high part of
+                           the stored basis only (two tensor-core products
+                           instead of three, half the basis bytes); the
+                           second Gram-Schmidt pass measures what the first
+                           left, and the update W -= V H keeps hi + lo.
+                           0: hi + lo.  Default 1                            */
 } mtf_options;
 
 typedef struct {

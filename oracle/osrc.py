@@ -44,6 +44,19 @@ the design notes; the CUDA library implements the same operator):
   which maps tested vectors to coefficients (W W^T = G^{-1}); the Pade
   approximant is applied exactly on every mode instead of through auxiliary
   sparse solves.
+* Type 2 (Sec. 5.4 uses it and only cites its source, for a twofold saving in
+  memory and solver time at similar iteration counts; no definition is
+  printed).  Reading taken here: a compressed T~ whose modal symbols keep
+  their modulus and take the phase of the principal symbols of the EtM map
+  (the |xi| -> infinity limits -2ik/|xi| on irrotational and 2i|xi|/k on
+  solenoidal currents, i.e. -pi/2 and +pi/2):
+      f2 = -i |f| on irrotational modes,  f2 = +i |f| on loop and harmonic
+      modes,   T~2 = W diag(f2) W^T = i R,  R = W diag(Im f2) W^T real.
+  R is real symmetric, so T~2 needs half the storage of T~ and its apply to
+  a complex vector is two real products.  For the damped symbols used here
+  the irrotational symbols have Im f < 0 and the solenoidal ones Im f > 0,
+  so f2 = i sign(Im f) |f|: Type 2 rounds every symbol's phase to the
+  nearest of +-pi/2.  It changes iteration counts only, never the solution.
 """
 from __future__ import annotations
 
@@ -125,11 +138,14 @@ def loop_map(sk: Skeleton, i: int, pos):
 class BlockOSRC:
     """Block-OSRC preconditioner of an MTF system (Eq. 19)."""
 
-    def __init__(self, sk: Skeleton, k, rho, Np=4, theta=np.pi / 2, eps_scale=0.39):
+    def __init__(self, sk: Skeleton, k, rho, Np=4, theta=np.pi / 2, eps_scale=0.39, osrc_type=1):
+        if osrc_type not in (1, 2):
+            raise ValueError("block-OSRC type must be 1 or 2")
         self.sk = sk
         self.rho = np.asarray(rho)
+        self.osrc_type = osrc_type
         self.Ttil = []
-        self.nh, self.W = [], []
+        self.nh, self.W, self.f, self.n_irr = [], [], [], []
         for i in range(sk.n_domains):
             G = mass_matrix(sk, i)
             D = divdiv_matrix(sk, i)
@@ -154,8 +170,15 @@ class BlockOSRC:
             f_sol = (2 * keps / k[i]) * pade_sqrt(-mu[1:] / keps ** 2, Np, theta)
             W = np.concatenate([V[:, -nirr:], U], axis=1)
             f = np.concatenate([f_irr, f_sol])
+            if osrc_type == 2:
+                # Type 2: modulus kept, phase of the principal symbol
+                # (-pi/2 irrotational, +pi/2 loops and harmonic fields)
+                sigma = np.concatenate([-np.ones(nirr), np.ones(len(f_sol))])
+                f = 1j * sigma * np.abs(f)
             self.nh.append(nh)
+            self.n_irr.append(nirr)
             self.W.append(W)
+            self.f.append(f)
             self.Ttil.append((W * f[None, :]) @ W.T)
 
     def apply(self, r):

@@ -33,7 +33,8 @@ class mtf_options(ctypes.Structure):
                 ("osrc_eps_scale", ctypes.c_double), ("max_refine", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("osrc_half", ctypes.c_int32), ("recycle", ctypes.c_int32), ("residual_df", ctypes.c_int32),
                 ("block_krylov", ctypes.c_int32), ("mv_tensor", ctypes.c_int32),
-                ("residual_fp64", ctypes.c_int32), ("inner_tol_min", ctypes.c_double)]
+                ("residual_fp64", ctypes.c_int32), ("inner_tol_min", ctypes.c_double),
+                ("gs_dots_half", ctypes.c_int32)]
 
 
 class mtf_solve_stats(ctypes.Structure):

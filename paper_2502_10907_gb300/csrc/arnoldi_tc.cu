@@ -13,6 +13,12 @@
 //    32 b .. 32 b + 31, rows = entries, (re, im) interleaved along K = the
 //    basis index: (V H)[k, c] with input columns (H_re, -H_im) and
 //    (H_im, H_re) per complex H[:, c].
+// The dots may read the hi parts of the basis alone (two products, half the
+// basis bytes): a basis entry then enters the dots rounded to FP16.  Classical
+// Gram-Schmidt twice tolerates that error in its coefficients (the second
+// pass measures what the first left, and the rounding errors of the basis
+// entries do not correlate with W), while the update W -= V H, which carries
+// the Arnoldi relation M Z = V H, keeps hi + lo.
 // Dots units (basis group g, a range of entry chunks) write row sums that a
 // reduction adds in FP64 into H; update units (entry group e, all basis
 // chunks) subtract their product from W directly.  Both unit sets follow a
@@ -37,6 +43,7 @@ namespace mtf {
 
 // tensor-map encoder and helpers of the tensor-core matvec (mv_tc.cu)
 void tc_encode_map(void* map, const void* base, int rows, int parts, int64_t count);
+void tc_encode_map_first(void* map, const void* base, int rows, int parts, int64_t count);
 
 constexpr float kBasisScale = 16384.f;  // 2^14: unit-norm basis entries stay below the FP16 range limit
 
@@ -221,11 +228,14 @@ struct TcArnoldi {
   size_t h_cap = 0;                    // units the partial buffer holds
   int n_cta = 0, b_nb = 0;
   CUtensorMap vd_map{}, vu_map{}, bd_map{}, bu_map{};
+  CUtensorMap vd_hi_map{};             // the dots copy's FP16 hi parts alone
+  bool dots_hi = false;                // dots from the basis's hi part (two products)
 
 };
 
 TcArnoldi* tca_create() { return new TcArnoldi(); }
 void tca_destroy(TcArnoldi* t) { delete t; }
+void tca_set_dots_hi(TcArnoldi& t, bool on) { t.dots_hi = on; }
 
 static int tca_nb(int nc) { return 2 * nc <= 16 ? 16 : 2 * nc <= 32 ? 32 : 2 * nc <= 64 ? 64 : 128; }
 
@@ -255,6 +265,7 @@ void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st) {
   t.part.alloc(cap * kTcRows * 128);
   t.h_cap = cap;
   tc_encode_map(&t.vd_map, t.Vd.p, kTcRows, 2, int64_t(t.G) * t.nkc);
+  tc_encode_map_first(&t.vd_hi_map, t.Vd.p, kTcRows, 2, int64_t(t.G) * t.nkc);
   tc_encode_map(&t.vu_map, t.Vu.p, kTcRows, 2, int64_t(t.E) * t.nbc);
   t.b_nb = 0;
 }
@@ -276,23 +287,24 @@ void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st) {
                                                                                        t.Vu.p));
 }
 
-template <int NB, int EPI>
+template <int NPA, int NB, int EPI>
 static void tca_launch(TcArnoldi& t, const CUtensorMap& amap, const CUtensorMap& bmap, const TcUnits& units,
                        int n_units, float* W, int nc, int64_t n_limit, const unsigned* cm, unsigned* err, int kid,
                        cudaStream_t st) {
-  using Cfg = TcsCfg<2, NB>;
+  using Cfg = TcsCfg<NPA, NB>;
   static std::atomic<uint64_t> opted{0};
   int dev = 0;
   MTF_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = uint64_t(1) << (dev & 63);
   if (!(opted.load() & bit)) {
-    MTF_CUDA(cudaFuncSetAttribute(k_tc_stream<2, NB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem)));
+    MTF_CUDA(cudaFuncSetAttribute(k_tc_stream<NPA, NB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(Cfg::smem)));
     opted.fetch_or(bit);
   }
   const unsigned grid = unsigned(std::min(n_units, t.n_cta));
-  MTF_LAUNCH(kid, st, k_tc_stream<2, NB, EPI><<<grid, 192, Cfg::smem, st>>>(amap, bmap, units, n_units, nullptr,
-                                                                            nullptr, t.part.p, W, t.ldn, nc, n_limit,
-                                                                            cm, err, TcTtOut{}));
+  MTF_LAUNCH(kid, st, k_tc_stream<NPA, NB, EPI><<<grid, 192, Cfg::smem, st>>>(amap, bmap, units, n_units, nullptr,
+                                                                              nullptr, t.part.p, W, t.ldn, nc, n_limit,
+                                                                              cm, err, TcTtOut{}));
 }
 
 template <int NB>
@@ -317,8 +329,13 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
   ud.a = t.nkc;
   ud.b = L;
   ud.c = Pn;
-  prof_bytes(KID_DOTS, double(nq + nc) * double(t.ldn) * 8.0);
-  tca_launch<NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
+  if (t.dots_hi) {
+    prof_bytes(KID_DOTS, (double(nq) * 4.0 + double(nc) * 8.0) * double(t.ldn));
+    tca_launch<1, NB, 0>(t, t.vd_hi_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
+  } else {
+    prof_bytes(KID_DOTS, double(nq + nc) * double(t.ldn) * 8.0);
+    tca_launch<2, NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
+  }
   MTF_LAUNCH(KID_TCA_PREP, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * nc + 255) / 256), 256, 0, st>>>(
       t.part.p, NB, Pn, nq, nc, cmw, H, ldh));
   // W -= V H: one unit per entry group, over the basis chunks in use
@@ -332,7 +349,7 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
   uu.a = t.nbc;
   uu.b = nbc_used;
   prof_bytes(KID_AXPY, double(nq + 2 * nc) * double(t.ldn) * 8.0);
-  tca_launch<NB, 1>(t, t.vu_map, t.bu_map, uu, t.E, W, nc, t.ldn, cmh, err, KID_AXPY, st);
+  tca_launch<2, NB, 1>(t, t.vu_map, t.bu_map, uu, t.E, W, nc, t.ldn, cmh, err, KID_AXPY, st);
 }
 
 // H[q, c] (q < nq, c < nc; complex FP64 at H + 2 (q ldh + c)) = V^H W, then

@@ -40,6 +40,7 @@ namespace mtf {
 struct TcArnoldi;
 TcArnoldi* tca_create();
 void tca_destroy(TcArnoldi* t);
+void tca_set_dots_hi(TcArnoldi& t, bool on);
 void tca_prepare(TcArnoldi& t, int s, int m, int64_t ldn, cudaStream_t st);
 void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st);
 void tca_project(TcArnoldi& t, int nq, float* W, int nc, double* H, int ldh, unsigned* err, cudaStream_t st);
@@ -823,6 +824,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   if (tc) {
     if (!B.tca) B.tca = tca_create();
     tca_prepare(*B.tca, s, m, ldn, st);
+    tca_set_dots_hi(*B.tca, sys->opt.gs_dots_half != 0);
   }
   unsigned* err_word = sys->d_mv_ctl.p + 2;
   // X[:, 0 .. nc) -= V S and S = V^H X against the first nq basis vectors (S leading dimension 2 s)

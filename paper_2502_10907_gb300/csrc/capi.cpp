@@ -108,6 +108,7 @@ void mtf_default_options(mtf_options* o) {
   o->residual_df = 1;
   o->block_krylov = 1;
   o->mv_tensor = 1;
+  o->gs_dots_half = 1;
 }
 
 mtf_status mtf_mesh_create(const double* vertices, int32_t nv, const int32_t* tris, int32_t nt,
@@ -169,6 +170,8 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
                   "residual_fp64 must be 0 or 1");
       MTF_REQUIRE(sys->opt.inner_tol_min == 0.0 || (sys->opt.inner_tol_min >= 1e-9 && sys->opt.inner_tol_min <= 0.5),
                   MTF_ERR_ARG, "inner_tol_min must be 0 or in [1e-9, 0.5]");
+      MTF_REQUIRE(sys->opt.gs_dots_half == 0 || sys->opt.gs_dots_half == 1, MTF_ERR_ARG,
+                  "gs_dots_half must be 0 or 1");
       MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {

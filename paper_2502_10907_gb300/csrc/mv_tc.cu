@@ -487,19 +487,26 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 4-D FP16 map {64, rows, parts, count} over contiguous boxes of
-// rows x parts x 128 bytes, loaded whole with the 128-byte swizzle
-void tc_encode_map(void* map, const void* base, int rows, int parts, int64_t count) {
+// rows x parts x 128 bytes, loaded with the 128-byte swizzle: whole boxes, or
+// (box_parts = 1) only the first part of each box
+static void encode_map(void* map, const void* base, int rows, int parts, int box_parts, int64_t count) {
   CUtensorMap* m = static_cast<CUtensorMap*>(map);
   MTF_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && count > 0 && count < (int64_t(1) << 31), MTF_ERR_ARG,
               "tensor map base must be 16-byte aligned");
   const cuuint64_t dims[4] = {64, cuuint64_t(rows), cuuint64_t(parts), cuuint64_t(count)};
   const cuuint64_t strides[3] = {128, cuuint64_t(rows) * 128, cuuint64_t(rows) * parts * 128};
-  const cuuint32_t box[4] = {64, cuuint32_t(rows), cuuint32_t(parts), 1};
+  const cuuint32_t box[4] = {64, cuuint32_t(rows), cuuint32_t(box_parts), 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void*>(base), dims, strides,
                                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   MTF_REQUIRE(r == CUDA_SUCCESS, MTF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+}
+void tc_encode_map(void* map, const void* base, int rows, int parts, int64_t count) {
+  encode_map(map, base, rows, parts, parts, count);
+}
+void tc_encode_map_first(void* map, const void* base, int rows, int parts, int64_t count) {
+  encode_map(map, base, rows, parts, 1, count);
 }
 
 template <class T>

@@ -39,7 +39,7 @@ struct TcsCfg {
   static constexpr int SBB = 2 * NB * 128;
   static constexpr int SB = SA + SBB;
   static constexpr int S0 = (220 * 1024) / SB;
-  static constexpr int S = S0 > 4 ? 4 : S0;
+  static constexpr int S = S0 > 6 ? 6 : S0;  // up to 6 stages (about 100 KB of operator tiles in flight)
   static constexpr uint32_t TMEM = 2 * NB < 32 ? 32 : 2 * NB;  // two buffers of NB columns
   static constexpr size_t smem = size_t(S) * SB + 1024 + 256;
   static_assert(S >= 2 && smem <= 232448 && SB % 1024 == 0, "stage ring");

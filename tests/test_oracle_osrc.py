@@ -98,3 +98,51 @@ def test_block_osrc_on_genus_one_boundaries():
     _, it0, c0 = gmres_iterations(M, b, 1e-5, 100, 600)
     _, it1, c1 = gmres_iterations(M, b, 1e-5, 100, 600, P=P.matrix())
     assert c1 and not c0 and it1 < 300, (it0, it1)
+
+
+def test_block_osrc_type2_modal_structure(oracle_cache):
+    """Type 2 (Sec. 5.4; reading: the Type-1 symbols with their modulus kept
+    and their phase set to that of the EtM principal symbols).  Pinned without
+    the mode basis the oracle builds it from: T~2 is purely imaginary and
+    symmetric; the eigenvalues of T~2 G (G the RWG Gram matrix) are the
+    Type-2 symbols, so they have the moduli of the eigenvalues of T~1 G and
+    are purely imaginary; exactly T_i - 1 of them (the rank of div on RWG_i)
+    lie on the negative imaginary axis; and the eigenvectors on the positive
+    axis are divergence-free (D v = 0: loops and harmonic fields), those on
+    the negative axis are not."""
+    cfg, sk, ref = sphere_system(oracle_cache, 2)
+    P1 = BlockOSRC(sk, ref.k, ref.rho, Np=16)
+    P2 = BlockOSRC(sk, ref.k, ref.rho, Np=16, osrc_type=2)
+    for i in range(sk.n_domains):
+        G, D = mass_matrix(sk, i), divdiv_matrix(sk, i)
+        T1, T2 = P1.Ttil[i], P2.Ttil[i]
+        assert np.abs(T2.real).max() == 0.0
+        assert np.abs(T2 - T2.T).max() < 1e-12 * np.abs(T2).max()
+        l1 = np.linalg.eigvals(T1 @ G)
+        l2, V2 = np.linalg.eig(T2 @ G)
+        assert np.abs(np.sort(np.abs(l2)) - np.sort(np.abs(l1))).max() < 1e-9 * np.abs(l1).max()
+        assert np.abs(l2.real).max() < 1e-9 * np.abs(l2).max()
+        neg = l2.imag < 0
+        assert int(neg.sum()) == len(sk.tris[i]) - 1
+        Dv = np.linalg.norm(D @ V2, axis=0) / (np.linalg.norm(D) * np.linalg.norm(V2, axis=0))
+        assert Dv[~neg].max() < 1e-8 and Dv[neg].min() > 1e-6, (Dv[~neg].max(), Dv[neg].min())
+
+
+def test_block_osrc_type2_keeps_the_solution_and_the_iterations(oracle_cache):
+    """Type 2 changes the preconditioner, not the solution, and keeps the
+    iteration count near Type 1's (the paper reports similar convergence):
+    within 1.25x of Type 1 and more than 3x below plain GMRES on the sphere."""
+    cfg, sk, ref = sphere_system(oracle_cache, 2)
+    M = ref.matrix()
+    b = ref.rhs(cfg["dirs"], cfg["pols"])[:, 0]
+    xs = np.linalg.solve(M, b)
+    its = []
+    for t in (1, 2):
+        P = BlockOSRC(sk, ref.k, ref.rho, Np=16, osrc_type=t)
+        x, it, c = gmres_iterations(M, b, 1e-5, 100, 1500, P=P.matrix())
+        assert c and np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-3
+        its.append(it)
+    _, it0, _ = gmres_iterations(M, b, 1e-5, 100, 1500)
+    assert its[1] <= 1.25 * its[0] and 3 * its[1] < it0, (its, it0)
+    with pytest.raises(ValueError):
+        BlockOSRC(sk, ref.k, ref.rho, osrc_type=3)
