@@ -523,6 +523,45 @@ def learned_on_workload(api, L, mesh, cfg, opts, x_ref, plain_iters):
                     "enabled only if the validation solve beats plain block-OSRC"}
 
 
+def osrc_type2_on_workload(api, L, mesh, cfg, opts, x_ref):
+    """Block-OSRC Type 1 against Type 2 (T~2 = i R, R real symmetric; the
+    wide applies stream R in FP16, 2 bytes per stored entry instead of 4) on
+    the headline workload: one timed solve each (after a warm-up solve),
+    block steps, error against the FP64 solution, and the device time of one
+    16-column apply (CUDA events, 20 applies after 3 warm-ups)."""
+    import torch
+    n_entries = int(sum(int(n) ** 2 for n in mesh.n_dofs))
+    out = {"streamed_bytes_per_apply": {"type1": 4 * n_entries, "type2": 2 * n_entries}}
+    rng = torch.Generator(device="cuda")
+    rng.manual_seed(7)
+    r = torch.randn((16, mesh.n_total), dtype=torch.complex64, device="cuda", generator=rng)
+    for t in (1, 2):
+        s = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], **dict(opts, osrc_type=t))
+        s.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, st = s.solve(cfg["dirs"], cfg["pols"], raise_on_noconv=False)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        err = float(((x - x_ref).norm(dim=1) / x_ref.norm(dim=1)).max()) if x_ref is not None else None
+        for _ in range(3):
+            s.precond_f32(r)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            s.precond_f32(r)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"type{t}"] = {"solve_seconds": round(secs, 3), "gmres_iterations": int(st.iterations),
+                           "converged": bool(st.converged), "solution_rel_err_vs_fp64": err,
+                           "apply_ms_16_columns": round(e0.elapsed_time(e1) / 20, 4)}
+        del s
+    out["note"] = ("Type 2 (reading of Sec. 5.4: symbols with the principal symbols' phase) changes the "
+                   "preconditioner, not the solution")
+    return out
+
+
 def secondary_split_sphere(api, L, args, stream):
     """The split-sphere workload (3 blocks, 13,068 unknowns, 2 waves): the
     mixed path, the plain FP64 block-OSRC GMRES and the learned correction on
@@ -768,11 +807,13 @@ def main():
     secondary = None
     batch = None
     learned = None
+    type2 = None
     if rank == 0 and world == 1 and not args.no_comparisons and args.workload != "split_sphere":
         secondary = secondary_split_sphere(api, L, args, stream)
         batch = batch_instances(api, L, args)
         if prec == L.MTF_PREC_MIXED and pc == L.MTF_PRECOND_OSRC:
             learned = learned_on_workload(api, L, mesh, cfg, opts, x_ref, statistics.median(iters))
+            type2 = osrc_type2_on_workload(api, L, mesh, cfg, opts, x_ref)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -819,6 +860,7 @@ def main():
             "secondary": secondary,
             "batched_instances": batch,
             "learned_correction": learned,
+            "block_osrc_type2": type2,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -155,6 +155,17 @@ typedef struct {
                            second Gram-Schmidt pass measures what the first
                            left, and the update W -= V H keeps hi + lo.
                            0: hi + lo.  Default 1                            */
+  int32_t osrc_type;    /* block-OSRC variant (Sec. 5.4 names Type 1 and Type
+                           2; the paper defines neither beyond Eq. 19):
+                           1: T~ = W diag(f) W^T with the Pade symbols f;
+                           2: the compressed T~2 = W diag(f2) W^T, f2 = the
+                           modulus of f with the phase of the EtM principal
+                           symbol (-i |f| on irrotational, +i |f| on loop and
+                           harmonic modes), so T~2 = i R with R real
+                           symmetric; the wide tensor-core applies (more than
+                           4 right-hand sides, mixed mode) stream R in FP16,
+                           2 bytes per entry instead of 4.  The solution does
+                           not depend on the choice.  0 selects 1.  Default 1 */
 } mtf_options;
 
 typedef struct {

@@ -34,7 +34,7 @@ class mtf_options(ctypes.Structure):
                 ("osrc_half", ctypes.c_int32), ("recycle", ctypes.c_int32), ("residual_df", ctypes.c_int32),
                 ("block_krylov", ctypes.c_int32), ("mv_tensor", ctypes.c_int32),
                 ("residual_fp64", ctypes.c_int32), ("inner_tol_min", ctypes.c_double),
-                ("gs_dots_half", ctypes.c_int32)]
+                ("gs_dots_half", ctypes.c_int32), ("osrc_type", ctypes.c_int32)]
 
 
 class mtf_solve_stats(ctypes.Structure):

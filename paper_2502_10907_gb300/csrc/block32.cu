@@ -665,7 +665,7 @@ static void bdots(mtf_system sys, const float* V, int nq, int64_t ldv, const flo
 
 template <int SC>
 static void bupdate_launch(const float* V, int nq, int64_t ldv, const double* H, int ldh, float* W, int64_t ldw, int nc,
-                           int64_t n_pad, cudaStream_t st) {
+                           int64_t n_pad, int kid, cudaStream_t st) {
   const size_t smem = size_t(8) * SC * 32 * sizeof(float4);
   static std::atomic<uint64_t> opted{0};
   int dev = 0;
@@ -676,24 +676,27 @@ static void bupdate_launch(const float* V, int nq, int64_t ldv, const double* H,
     opted.fetch_or(bit);
   }
   // basis read once, block read and written once
-  prof_bytes(KID_AXPY, double(nq + 2 * nc) * double(n_pad) * 8.0);
-  MTF_LAUNCH(KID_AXPY, st, k_bupdate<SC><<<nbk(n_pad, 64), 256, smem, st>>>(V, nq, ldv, H, ldh, W, ldw, nc, n_pad));
+  prof_bytes(kid, double(nq + 2 * nc) * double(n_pad) * 8.0);
+  MTF_LAUNCH(kid, st, k_bupdate<SC><<<nbk(n_pad, 64), 256, smem, st>>>(V, nq, ldv, H, ldh, W, ldw, nc, n_pad));
 }
 
 // W_{c0 + c} -= sum_q V_q H[q, c0 + c] over all column groups of 16
+// W -= V H over nq basis columns (kid: the profile entry; the Gram-Schmidt
+// update of the FMA path counts as such, the small per-step corrections and
+// the solution update as block transforms)
 static void bupdate(const float* V, int nq, int64_t ldv, const double* H, int ldh, float* W, int64_t ldw, int s,
-                    int64_t n_pad, cudaStream_t st) {
+                    int64_t n_pad, cudaStream_t st, int kid = KID_BXFORM) {
   if (nq <= 0) return;
   for (int c0 = 0; c0 < s; c0 += 16) {
     const int nc = std::min(16, s - c0);
     const int SC = col_tier(nc);
     float* Wc = W + 2 * int64_t(c0) * ldw;
     const double* Hc = H + 2 * c0;
-    if (SC == 16) bupdate_launch<16>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, st);
-    else if (SC == 8) bupdate_launch<8>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, st);
-    else if (SC == 4) bupdate_launch<4>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, st);
-    else if (SC == 2) bupdate_launch<2>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, st);
-    else bupdate_launch<1>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, st);
+    if (SC == 16) bupdate_launch<16>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, kid, st);
+    else if (SC == 8) bupdate_launch<8>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, kid, st);
+    else if (SC == 4) bupdate_launch<4>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, kid, st);
+    else if (SC == 2) bupdate_launch<2>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, kid, st);
+    else bupdate_launch<1>(V, nq, ldv, Hc, ldh, Wc, ldw, nc, n_pad, kid, st);
   }
 }
 
@@ -834,7 +837,7 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     } else {
       MTF_CUDA(cudaMemsetAsync(S, 0, 2 * size_t(nq) * 2 * s * sizeof(double), st));
       bdots(sys, B.V.p, nq, ldn, B.X.p, ldn, nc, ldn, S, 2 * s, st, KID_DOTS);
-      bupdate(B.V.p, nq, ldn, S, 2 * s, B.X.p, ldn, nc, ldn, st);
+      bupdate(B.V.p, nq, ldn, S, 2 * s, B.X.p, ldn, nc, ldn, st, KID_AXPY);
     }
   };
 

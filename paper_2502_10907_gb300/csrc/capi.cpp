@@ -109,6 +109,7 @@ void mtf_default_options(mtf_options* o) {
   o->block_krylov = 1;
   o->mv_tensor = 1;
   o->gs_dots_half = 1;
+  o->osrc_type = 1;
 }
 
 mtf_status mtf_mesh_create(const double* vertices, int32_t nv, const int32_t* tris, int32_t nt,
@@ -172,6 +173,8 @@ mtf_status mtf_assemble(mtf_mesh mesh, double k0, const double* eps_r, const dou
                   MTF_ERR_ARG, "inner_tol_min must be 0 or in [1e-9, 0.5]");
       MTF_REQUIRE(sys->opt.gs_dots_half == 0 || sys->opt.gs_dots_half == 1, MTF_ERR_ARG,
                   "gs_dots_half must be 0 or 1");
+      if (sys->opt.osrc_type == 0) sys->opt.osrc_type = 1;
+      MTF_REQUIRE(sys->opt.osrc_type == 1 || sys->opt.osrc_type == 2, MTF_ERR_ARG, "osrc_type must be 1 or 2");
       MTF_REQUIRE(sys->opt.osrc_np >= 1 && sys->opt.osrc_np <= 16, MTF_ERR_ARG, "osrc_np out of range 1..16");
       assemble_into(sys, k0, eps_r, mu_r, s);
     } catch (...) {

@@ -66,6 +66,22 @@ struct TcMatvec {
   CUtensorMap osmap{};
   const void* osmap_ptr = nullptr;
   bool os_built = false;
+  // block-OSRC Type 2 (T~2 = i R, R real symmetric): R in FP16 row tiles of
+  // 128 rows x 64 real columns (2 bytes per entry), real input chunks of 64
+  // entries, units of its own plan (64 columns per chunk)
+  struct Real {
+    TcPlan plan;
+    DevBuf<int4> units_ab, tile_info;
+    DevBuf<int2> chunk_info;
+    DevBuf<int> sched, sched_off, blk_unit_base, blk_pieces;
+    DevBuf<__half> A, B;
+    DevBuf<float> part;
+    CUtensorMap amap{}, bmap{};
+    const void* amap_ptr = nullptr;
+    const void* bmap_ptr = nullptr;
+    int bmap_nb = 0;
+    bool planned = false;
+  } osr;
 };
 
 void destroy_tc(TcMatvec* t) { delete t; }
@@ -159,6 +175,62 @@ __global__ void __launch_bounds__(256) k_tc_tile_os(const __half2* __restrict__ 
   *reinterpret_cast<uint4*>(A + tc_tile_index(tile, 1, 0, row, 8 * g)) = *reinterpret_cast<const uint4*>(h);
 }
 
+// FP16 tiles of R = Im T~ (block-OSRC Type 2, whose T~ = i R): thread =
+// (tile, row, group g of 8 real columns); R(r, n) is the imaginary half of
+// the FP16 copy's entry (r, n)
+__global__ void __launch_bounds__(256) k_tc_tile_os_im(const __half2* __restrict__ T16,
+                                                       const int4* __restrict__ tile_info,
+                                                       const int64_t* __restrict__ off, const int64_t* __restrict__ ld,
+                                                       const int32_t* __restrict__ blk_N, int64_t n_tiles,
+                                                       __half* __restrict__ A) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_tiles * kTcRows * 8) return;
+  const int64_t tile = t / (kTcRows * 8);
+  const int row = int((t / 8) % kTcRows), g = int(t % 8);
+  const int4 info = tile_info[tile];
+  const int i = info.x, N = blk_N[i];
+  const int r = info.y * kTcRows + row;
+  __half h[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int n = info.z * 2 * kTcCols + 8 * g + q;
+    h[q] = (r < N && n < N) ? __high2half(T16[off[i] + int64_t(r) * ld[i] + n]) : __float2half_rn(0.f);
+  }
+  *reinterpret_cast<uint4*>(A + tc_tile_index(tile, 1, 0, row, 8 * g)) = *reinterpret_cast<const uint4*>(h);
+}
+
+// Real input chunks of the Type-2 apply: thread = (chunk, column col, group g
+// of 8 entries); column 4 c + 2 t + f holds part f (0: re, 1: im) of u_t of
+// right-hand side c0 + c, as FP16 hi / lo after the column's scaling
+__global__ void __launch_bounds__(256) k_tc_build_b_real(const float* __restrict__ x, int64_t ldx, int c0, int nc,
+                                                         int nb, const int2* __restrict__ chunk_info, int64_t n_chunks,
+                                                         const int32_t* __restrict__ blk_N,
+                                                         const int64_t* __restrict__ blk_dof_off,
+                                                         const unsigned* __restrict__ colmax, __half* __restrict__ B) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_chunks * nb * 8) return;
+  const int64_t chunk = t / (int64_t(nb) * 8);
+  const int col = int((t / 8) % nb), g = int(t % 8);
+  const int c = col >> 2, slot = (col >> 1) & 1, part = col & 1;
+  __half hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hi[q] = lo[q] = __float2half_rn(0.f);
+  if (c < nc) {
+    const int2 info = chunk_info[chunk];
+    const int N = blk_N[info.x];
+    const float s = tc_scale(colmax[c]);
+    const float* xc = x + 2 * (int64_t(c0 + c) * ldx + blk_dof_off[info.x] + int64_t(slot) * N) + part;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int n = info.y * 2 * kTcCols + 8 * g + q;
+      const float v = n < N ? xc[2 * int64_t(n)] : 0.f;
+      tc_split(v * s, hi[q], lo[q]);
+    }
+  }
+  *reinterpret_cast<uint4*>(B + tc_b_index(chunk, 0, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(hi);
+  *reinterpret_cast<uint4*>(B + tc_b_index(chunk, 1, col, 8 * g, nb)) = *reinterpret_cast<const uint4*>(lo);
+}
+
 // lanes per row of the combines: the pass's right-hand sides rounded up to a
 // power of two (at least 4), so that one warp takes 32 / lanes rows
 __host__ __device__ constexpr int tc_row_lanes(int nc) { return nc <= 4 ? 4 : nc <= 8 ? 8 : nc <= 16 ? 16 : 32; }
@@ -166,8 +238,9 @@ __host__ __device__ constexpr int tc_row_lanes(int nc) { return nc <= 4 ? 4 : nc
 // z rows of the block-OSRC apply (one warp per global row, lane = right-hand
 // side): the row's pieces of T~ r_D and T~ r_N summed in order and unscaled,
 // then z_D = rho^-1 T~ r_N, z_N = -rho T~ r_D with the per-block coefficients
-// of the FP16 copy (s_i rho, s_i / rho)
-template <int NB>
+// of the FP16 copy (s_i rho, s_i / rho).  IM (Type 2): the pieces hold
+// R r_D and R r_N, and T~ r = i R r.
+template <int NB, bool IM = false>
 __global__ void __launch_bounds__(256) k_os_tc_combine(
     const float* __restrict__ part, const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_N,
     const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const int* __restrict__ blk_unit_base,
@@ -193,7 +266,14 @@ __global__ void __launch_bounds__(256) k_os_tc_combine(
     t.w += a.w;
   }
   const float sc = tcs_inv_scale(colmax[lane]);
-  const float a0 = t.x * sc, a1 = t.y * sc, a2 = t.z * sc, a3 = t.w * sc;  // T~ r_D, T~ r_N
+  float a0 = t.x * sc, a1 = t.y * sc, a2 = t.z * sc, a3 = t.w * sc;  // T~ r_D, T~ r_N
+  if constexpr (IM) {
+    const float d0 = a0, d2 = a2;
+    a0 = -a1;
+    a1 = d0;
+    a2 = -a3;
+    a3 = d2;
+  }
   const float rr = cf[4 * i], ri = cf[4 * i + 1], ir = cf[4 * i + 2], ii = cf[4 * i + 3];
   float* zc = z + 2 * (int64_t(c0 + lane) * ldz + blk_dof_off[i]);
   zc[2 * m] = ir * a2 - ii * a3;
@@ -568,6 +648,48 @@ static void tc_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
   t.planned = true;
 }
 
+// units, tiles and chunks of the Type-2 block-OSRC apply: the matvec's
+// launch plan (CTAs, waves, piece length) over chunks of 64 real columns.
+// With the defaults a real row tile has half the chunks of a complex one, so
+// the plan asks for 2 units per CTA instead of 4: whole row tiles on large
+// systems, which keeps the per-unit epilogue and partial sums from
+// dominating the halved stream.
+static void tc_osr_plan_tables(mtf_system sys, TcMatvec& t, cudaStream_t s) {
+  mtf_mesh m = sys->mesh;
+  TcMatvec::Real& o = t.osr;
+  std::vector<int> Ns(m->nd);
+  for (int i = 0; i < m->nd; ++i) Ns[i] = m->blk[i].N;
+  const std::string why = plan_tc(Ns, t.n_cta, o.plan, t.waves > 0 ? t.waves : 2, t.min_len, 2 * kTcCols);
+  MTF_REQUIRE(why.empty(), MTF_ERR_MESH, why);
+  const TcPlan& p = o.plan;
+  MTF_REQUIRE(p.n_tiles < (int64_t(1) << 31), MTF_ERR_MESH, "mesh too large for the tensor-core tables");
+  std::vector<int4> uab(p.units.size()), tinfo(size_t(p.n_tiles));
+  std::vector<int2> cinfo(size_t(p.n_chunks));
+  std::vector<int> ubase(m->nd), pieces(m->nd);
+  for (size_t u = 0; u < p.units.size(); ++u) {
+    const TcBlock& b = p.blocks[size_t(p.units[u].blk)];
+    uab[u] = make_int4(int(b.tile_base + int64_t(p.units[u].mt) * b.n_kc), int(b.chunk_base), p.units[u].kc0,
+                       p.units[u].kc1);
+  }
+  for (int i = 0; i < m->nd; ++i) {
+    const TcBlock& b = p.blocks[size_t(i)];
+    ubase[i] = b.unit_base;
+    pieces[i] = b.pieces;
+    for (int mt = 0; mt < b.n_mt; ++mt)
+      for (int kc = 0; kc < b.n_kc; ++kc) tinfo[size_t(b.tile_base + int64_t(mt) * b.n_kc + kc)] = make_int4(i, mt, kc, 0);
+    for (int kc = 0; kc < b.n_kc; ++kc) cinfo[size_t(b.chunk_base + kc)] = make_int2(i, kc);
+  }
+  upload_vec(o.units_ab, uab, s);
+  upload_vec(o.tile_info, tinfo, s);
+  upload_vec(o.chunk_info, cinfo, s);
+  upload_vec(o.sched, p.sched, s);
+  upload_vec(o.sched_off, p.sched_off, s);
+  upload_vec(o.blk_unit_base, ubase, s);
+  upload_vec(o.blk_pieces, pieces, s);
+  MTF_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+  o.planned = true;
+}
+
 bool tc_matvec_enabled(mtf_system sys) {
   return sys->opt.precision == MTF_PREC_MIXED && sys->opt.mv_tensor && sys->tc && sys->tc->built;
 }
@@ -587,6 +709,7 @@ void tc_set_plan(mtf_system sys, int waves, int min_len, int grid, bool prefer_f
   t.grid = grid;
   t.planned = false;
   tc_plan_tables(sys, t, s);
+  if (t.osr.planned) tc_osr_plan_tables(sys, t, s);  // same tile order, new units
 }
 
 // FP16 hi / lo tiled copy of the FP32-stored {T, K}, rebuilt after every
@@ -679,6 +802,27 @@ void tc_build_osrc(mtf_system sys, const std::vector<int64_t>& ld16, cudaStream_
   tc_plan_tables(sys, t, s);
   upload_vec(t.os_off, m->os16_off_h, s);
   upload_vec(t.os_ld, ld16, s);
+  if (sys->opt.osrc_type == 2) {
+    // Type 2: tiles of R = Im T~ (64 real columns per tile row)
+    TcMatvec::Real& o = t.osr;
+    if (!o.planned) tc_osr_plan_tables(sys, t, s);
+    const size_t nr = size_t(o.plan.n_tiles) * kTcRows * 64;
+    if (o.A.n != nr) {
+      o.A.alloc(nr);
+      o.amap_ptr = nullptr;
+    }
+    const int64_t nthr = o.plan.n_tiles * kTcRows * 8;
+    MTF_LAUNCH(KID_TC_TILE, s, k_tc_tile_os_im<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const __half2*>(sys->d_osrc_T16.p), o.tile_info.p, t.os_off.p, t.os_ld.p, m->d_blk_N.p,
+        o.plan.n_tiles, o.A.p));
+    if (o.amap_ptr != o.A.p) {
+      tc_encode_map(&o.amap, o.A.p, kTcRows, 1, o.plan.n_tiles);
+      o.amap_ptr = o.A.p;
+    }
+    MTF_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+    t.os_built = true;
+    return;
+  }
   const size_t nh = size_t(t.plan.n_tiles) * kTcRows * 64;
   if (t.Aos.n != nh) {
     t.Aos.alloc(nh);
@@ -728,6 +872,53 @@ static void os_tc_pass(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr,
       t.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
 }
 
+// The Type-2 pass: real input chunks of the pass's columns, one stream over
+// the FP16 tiles of R (2 bytes per stored entry), and the combine with
+// T~ r = i R r
+template <int NB>
+static void os_tc_pass_real(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr, float* z, int64_t ldz, int c0,
+                            int nc, cudaStream_t s) {
+  using Cfg = TcsCfg<1, NB>;
+  mtf_mesh m = sys->mesh;
+  TcMatvec::Real& o = t.osr;
+  const TcPlan& p = o.plan;
+  if (o.B.n < size_t(p.n_chunks) * 2 * NB * 64) {
+    o.B.alloc(size_t(p.n_chunks) * 2 * 128 * 64);  // room for the widest pass
+    o.bmap_ptr = nullptr;
+  }
+  if (o.bmap_ptr != o.B.p || o.bmap_nb != NB) {
+    tc_encode_map(&o.bmap, o.B.p, NB, 2, p.n_chunks);
+    o.bmap_ptr = o.B.p;
+    o.bmap_nb = NB;
+  }
+  if (o.part.n < p.units.size() * kTcRows * NB) o.part.alloc(p.units.size() * kTcRows * 128);
+  MTF_CUDA(cudaMemsetAsync(t.colmax.p, 0, 32 * sizeof(unsigned), s));
+  MTF_LAUNCH(KID_OSRC, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(r, ldr, m->n_total, c0, t.colmax.p));
+  const int64_t nthr = p.n_chunks * NB * 8;
+  MTF_LAUNCH(KID_OSRC, s, k_tc_build_b_real<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+      r, ldr, c0, nc, NB, o.chunk_info.p, p.n_chunks, m->d_blk_N.p, m->d_blk_dof_off.p, t.colmax.p, o.B.p));
+  static std::atomic<uint64_t> opted{0};
+  int dev = 0;
+  MTF_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(opted.load() & bit)) {
+    MTF_CUDA(cudaFuncSetAttribute(k_tc_stream<1, NB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem)));
+    opted.fetch_or(bit);
+  }
+  stream_prepare(sys, s);
+  // every stored FP16 entry of R once and the pass's inputs once
+  prof_bytes(KID_OSRC, double(m->n_mat) * 2.0 + double(m->n_total) * nc * 8.0);
+  TcUnits units;
+  units.list = o.units_ab.p;
+  MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
+      o.amap, o.bmap, units, int(p.units.size()), o.sched.p, o.sched_off.p, o.part.p, nullptr, 0, 0, 0, nullptr,
+      sys->d_mv_ctl.p + 2, TcTtOut{}));
+  MTF_LAUNCH(KID_OSCOMBINE, s,
+             k_os_tc_combine<NB, true><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
+                 o.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, o.blk_unit_base.p,
+                 o.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
+}
+
 // z = A~ r (block-OSRC, Eq. 19) with the FP16 T~ on the tensor cores, in
 // passes of up to 32 right-hand sides (FP32 in and out)
 void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z, int64_t ldz, int nrhs,
@@ -739,6 +930,13 @@ void launch_osrc_apply_tc(mtf_system sys, const float* r, int64_t ldr, float* z,
   for (int c0 = 0; c0 < nrhs; c0 += 32) {
     const int nc = std::min(32, nrhs - c0);
     const int nb = tc_nb(nc);
+    if (sys->opt.osrc_type == 2) {
+      if (nb == 16) os_tc_pass_real<16>(sys, t, r, ldr, z, ldz, c0, nc, s);
+      else if (nb == 32) os_tc_pass_real<32>(sys, t, r, ldr, z, ldz, c0, nc, s);
+      else if (nb == 64) os_tc_pass_real<64>(sys, t, r, ldr, z, ldz, c0, nc, s);
+      else os_tc_pass_real<128>(sys, t, r, ldr, z, ldz, c0, nc, s);
+      continue;
+    }
     if (nb == 16) os_tc_pass<16>(sys, t, r, ldr, z, ldz, c0, nc, s);
     else if (nb == 32) os_tc_pass<32>(sys, t, r, ldr, z, ldz, c0, nc, s);
     else if (nb == 64) os_tc_pass<64>(sys, t, r, ldr, z, ldz, c0, nc, s);

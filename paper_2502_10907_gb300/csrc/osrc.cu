@@ -148,10 +148,13 @@ __global__ void k_pad_copy(const float* __restrict__ W, int N, int ld, float* __
 
 // symbol per (block, mode j) with Z = -|xi|^2 / k_eps^2:
 //   irrotational (j < nirr): f = 2k / (k_eps P(Z)),  loop: f = (2 k_eps / k) P(Z)
+// type2: the modulus of f with the phase of the EtM principal symbols,
+//   -i |f| on irrotational modes, +i |f| on loop and harmonic modes
+// (block-OSRC Type 2: T~2 = W diag(f2) W^T = i R with R real symmetric)
 __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __restrict__ row_blk, int64_t n_rows,
                               const int64_t* __restrict__ blk_row_off, const int32_t* __restrict__ nirr_blk,
                               const double* __restrict__ kk, const double* __restrict__ keps,
-                              const double* __restrict__ pd, int np, float2* __restrict__ f) {
+                              const double* __restrict__ pd, int np, int type2, float2* __restrict__ f) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
   const int i = row_blk[r];
@@ -173,12 +176,21 @@ __global__ void k_osrc_symbol(const float* __restrict__ lam, const int32_t* __re
   }
   const double er = kr * Pr - ki * Pi, ei = kr * Pi + ki * Pr;     // k_eps P
   const double k0 = kk[2 * i];
+  double fr, fi;
   if (irr) {
     const double en = er * er + ei * ei;
-    f[r] = make_float2(float(2.0 * k0 * er / en), float(-2.0 * k0 * ei / en));
+    fr = 2.0 * k0 * er / en;
+    fi = -2.0 * k0 * ei / en;
   } else {
-    f[r] = make_float2(float(2.0 * er / k0), float(2.0 * ei / k0));
+    fr = 2.0 * er / k0;
+    fi = 2.0 * ei / k0;
   }
+  if (type2) {
+    const double a = sqrt(fr * fr + fi * fi);
+    fr = 0.0;
+    fi = irr ? -a : a;
+  }
+  f[r] = make_float2(float(fr), float(fi));
 }
 
 // z rows of one block row m (one warp per global row): the row's T~ pieces
@@ -595,7 +607,7 @@ void osrc_setup(mtf_system sys, cudaStream_t s) {
   sys->d_osrc_f.alloc(size_t(m->n_rows) * 2);
   MTF_LAUNCH(KID_MISC, s, k_osrc_symbol<<<unsigned((m->n_rows + 127) / 128), 128, 0, s>>>(
       m->d_osrc_lam.p, m->d_row_blk.p, m->n_rows, m->d_blk_row_off.p, m->d_osrc_nirr.p, sys->d_k.p, d_keps.p,
-      d_pd.p, np, reinterpret_cast<float2*>(sys->d_osrc_f.p)));
+      d_pd.p, np, sys->opt.osrc_type == 2 ? 1 : 0, reinterpret_cast<float2*>(sys->d_osrc_f.p)));
   // T~ rows padded to an even length (8-byte entries: 16-byte aligned rows)
   m->os_T_off_h.assign(m->nd, 0);
   int64_t toff = 0;

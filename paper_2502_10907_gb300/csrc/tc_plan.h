@@ -99,9 +99,12 @@ struct TcPlan {
 // Pieces of at most piece_len chunks per (block, row tile), piece_len chosen
 // so that there are at least `waves` units per CTA on average (but no piece
 // shorter than min_len chunks; 0 selects the defaults below); LPT schedule
-// over n_cta CTAs.
-inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int waves = 0, int min_len = 0) {
+// over n_cta CTAs.  A chunk covers cols_per_chunk columns of the operator:
+// 32 complex columns (64 FP16) for the complex operators, 64 for a real one.
+inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int waves = 0, int min_len = 0,
+                           int cols_per_chunk = kTcCols) {
   if (n_cta < 1) return "plan_tc: no CTAs";
+  if (cols_per_chunk != kTcCols && cols_per_chunk != 2 * kTcCols) return "plan_tc: 32 or 64 columns per chunk";
   p = TcPlan{};
   p.blocks.resize(Ns.size());
   int64_t total_chunks = 0, n_tiles_rows = 0;
@@ -110,7 +113,7 @@ inline std::string plan_tc(const std::vector<int>& Ns, int n_cta, TcPlan& p, int
     if (Ns[i] <= 0) return "plan_tc: empty block";
     b.N = Ns[i];
     b.n_mt = (b.N + kTcRows - 1) / kTcRows;
-    b.n_kc = (b.N + kTcCols - 1) / kTcCols;
+    b.n_kc = (b.N + cols_per_chunk - 1) / cols_per_chunk;
     total_chunks += int64_t(b.n_mt) * b.n_kc;
     n_tiles_rows += b.n_mt;
   }

@@ -376,6 +376,59 @@ def test_osrc_apply_f32_matches_oracle(api, oracle_cache, name, nrhs):
         assert np.abs(z - zr).max() < tol * np.abs(zr).max(), (half, tensor)
 
 
+
+# ---------------------------------------------------------------------------
+# block-OSRC Type 2 (Sec. 5.4; reading: modal symbols with the phase of the
+# EtM principal symbols, T~2 = i R with R real symmetric).  The wide
+# tensor-core apply streams R alone in FP16 (real input chunks, 64 columns
+# per chunk, odd N padded), the narrow applies the complex copy whose real
+# part is zero; both against the oracle's Type-2 operator.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["split", "uvodd", "cubes"])
+def test_osrc_type2_apply_matches_oracle(api, oracle_cache, name):
+    from oracle.osrc import BlockOSRC
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    P2 = BlockOSRC(sk, ref.k, ref.rho, osrc_type=2)
+    P1 = BlockOSRC(sk, ref.k, ref.rho)
+    rng = np.random.default_rng(13)
+    r = rng.standard_normal((3, sk.n_total)) + 1j * rng.standard_normal((3, sk.n_total))
+    s64 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, osrc_type=2)
+    z = s64.precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    zr = np.stack([P2.apply(rr) for rr in r])
+    assert rel(z, zr) < 1e-4
+    # Type 2 is a different operator from Type 1 (not a relabelling)
+    assert rel(np.stack([P1.apply(rr) for rr in r]), zr) > 1e-2
+    s32 = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, precision=1, osrc_type=2)
+    for nrhs in (3, 9, 36):
+        r32 = _rand_c64(rng, (nrhs, sk.n_total))
+        zr = np.stack([P2.apply(rr.astype(np.complex128)) for rr in r32])
+        z = s32.precond_f32(torch.from_numpy(r32).cuda()).cpu().numpy()
+        assert rel(z, zr) < 1e-3, (nrhs, rel(z, zr))
+        assert np.abs(z - zr).max() < 1e-3 * np.abs(zr).max(), nrhs
+
+
+@pytest.mark.parametrize("name", ["split", "cubes"])
+def test_osrc_type2_solves_to_the_same_solution(api, oracle_cache, name):
+    """Eight plane waves through the mixed block solver (the wide Type-2
+    apply inside): both types reach the oracle's LU solution within 1e-5,
+    and Type 2 needs at most 1.5x Type 1's iterations."""
+    cfg, sk, ref = _case(oracle_cache, name)
+    mesh = api.Mesh.from_inputs(cfg["mesh"])
+    dirs, pols = mi.plane_wave_batch(4)
+    xr = ref.solve_lu(ref.rhs(dirs, pols))
+    its = {}
+    for t in (1, 2):
+        sysg = api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precision=1, precond=1, tol=1e-8, restart=500,
+                          max_iter=4000, max_refine=6, osrc_type=t)
+        x, st = sysg.solve(dirs, pols)
+        errs = np.linalg.norm(x.cpu().numpy().T - xr, axis=0) / np.linalg.norm(xr, axis=0)
+        assert st.converged == 1 and errs.max() < MIXED_TOL, (t, errs)
+        its[t] = st.iterations
+    assert its[2] <= 1.5 * its[1], its
+    with pytest.raises(api.L.MtfError):
+        api.System(mesh, cfg["k0"], cfg["eps_r"], cfg["mu_r"], precond=1, osrc_type=3)
+
 def test_f32_entries_reject_wrong_systems(api, oracle_cache):
     cfg, sk, ref = _case(oracle_cache, "sphere")
     mesh = api.Mesh.from_inputs(cfg["mesh"])
