@@ -57,10 +57,13 @@ FLOPS_PER_EVAL = 57
 # (kernel, n_total, nrhs), absent for other workloads
 NCU_TRAFFIC = {("matvec32", 13068, 2): 232.30e6, ("osrc_apply", 13068, 2): 60.09e6}
 # DRAM traffic over algorithmic bytes of the tensor-core Gram-Schmidt streams
-# (ncu --set full, one launch each at block step 61 of the 25,920-unknown
+# (ncu --set full, one launch each around block step 61 of the 25,920-unknown
 # cube, 16 right-hand sides; both read the basis once, so their traffic grows
-# with the basis vectors read and is scaled to the launch by this ratio)
-NCU_TRAFFIC_RATIO = {("gmres_dots", 16): 232.91e6 / 209.00e6, ("gmres_axpy", 16): 216.31e6 / 215.65e6}
+# with the basis vectors read and is scaled to the launch by this ratio).  The
+# dots read the FP16 high part of the basis (1,088 vectors in the captured
+# launch: 119.46 MB read and 2.75 MB of row sums written for 119.44 MB of
+# algorithmic bytes).
+NCU_TRAFFIC_RATIO = {("gmres_dots", 16): 122.21e6 / 119.44e6, ("gmres_axpy", 16): 216.31e6 / 215.65e6}
 
 
 def _stream_bytes(name, Ns, n_total, nrhs):
