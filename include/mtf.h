@@ -175,6 +175,12 @@ typedef struct {
   int32_t converged;    /* 1 if every right-hand side met tol                   */
   double rel_residual;  /* max over rhs of the final true ||b - M x|| / ||b||  */
   double seconds;       /* wall time of the call                               */
+  double launch_seconds;/* host time spent queueing the kernels of the inner
+                           block FGMRES steps (0 for other paths)            */
+  double lsq_seconds;   /* host time of their block least-squares updates    */
+  double wait_seconds;  /* host time spent waiting for their steps to finish
+                           on the device (small when the host is the
+                           bottleneck)                                       */
 } mtf_solve_stats;
 
 /* Fill *opt with the defaults listed above.  Never fails. */

@@ -39,7 +39,9 @@ class mtf_options(ctypes.Structure):
 
 class mtf_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("refinements", ctypes.c_int32),
-                ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("launch_seconds", ctypes.c_double), ("lsq_seconds", ctypes.c_double),
+                ("wait_seconds", ctypes.c_double)]
 
 
 _lib = None

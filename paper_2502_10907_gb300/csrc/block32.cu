@@ -25,6 +25,7 @@
 // length ldn (a multiple of 64, padding zero), vector-major; the Hessenberg
 // coefficients are reduced in FP64 (FP64 atomics across CTAs).
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -973,10 +974,24 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
   std::vector<cdouble> h, Rnh(size_t(s) * s);
   int steps = 0;
   mtf_status status = MTF_OK;
+  using clk = std::chrono::steady_clock;
+  auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
+  auto tq = clk::now();
   launch_step(0);
+  sys->t_launch += since(tq);
   for (int J = 0; J <= Jend; ++J) {
+    tq = clk::now();
     if (J + 1 <= Jend) launch_step(J + 1);
+    sys->t_launch += since(tq);
+    tq = clk::now();
     MTF_CUDA(cudaEventSynchronize(B.ev[J & 1]));
+    sys->t_wait += since(tq);
+    const auto tl = clk::now();
+    struct LsqClock {  // adds the host time of this step's update on every exit
+      double& acc;
+      clk::time_point t;
+      ~LsqClock() { acc += std::chrono::duration<double>(clk::now() - t).count(); }
+    } lsq_clock{sys->t_lsq, tl};
     const int* kh = B.kept_host + size_t(J & 1) * (2 * s + 1);
     if (kh[2 * s] != 0) {
       status = MTF_ERR_TIMEOUT;

@@ -19,9 +19,15 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
+#include <cstdlib>
 #include <functional>
+#include <memory>
+#include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -77,28 +83,87 @@ inline int deflating_cholesky(int s, const cdouble* G, const double* ref, double
   return nk;
 }
 
-// run f(c) for c in [0, n), on up to `threads` host threads
-inline void parallel_for(int n, int threads, const std::function<void(int)>& f) {
-  threads = std::max(1, std::min(threads, n));
-  if (threads == 1) {
-    for (int c = 0; c < n; ++c) f(c);
-    return;
+// Persistent host workers: run(n, f) calls f(i) for i in [0, n) on the
+// workers and the calling thread and returns when all calls have finished
+// and every worker is done with the task (so none can reach into the next
+// one).  Workers poll for a new task for a short while (a block step's
+// update follows the previous one within about a millisecond), then sleep on
+// a condition variable.  One task at a time per pool.
+class HostPool {
+ public:
+  explicit HostPool(int workers) {
+    for (int t = 0; t < workers; ++t) th_.emplace_back([this] { loop(); });
   }
-  std::vector<std::thread> pool;
-  pool.reserve(size_t(threads));
-  for (int t = 0; t < threads; ++t)
-    pool.emplace_back([&, t] {
-      for (int c = t; c < n; c += threads) f(c);
-    });
-  for (auto& th : pool) th.join();
-}
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  HostPool(const HostPool&) = delete;
+  HostPool& operator=(const HostPool&) = delete;
+
+  void run(int n, const std::function<void(int)>& f) {
+    fn_ = &f;
+    n_ = n;
+    next_.store(0, std::memory_order_relaxed);
+    finished_.store(0, std::memory_order_relaxed);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      gen_.fetch_add(1, std::memory_order_release);  // publishes the task
+    }
+    cv_.notify_all();
+    work();
+    while (finished_.load(std::memory_order_acquire) < int(th_.size())) std::this_thread::yield();
+  }
+
+ private:
+  void work() {
+    for (int i = next_.fetch_add(1, std::memory_order_relaxed); i < n_; i = next_.fetch_add(1, std::memory_order_relaxed))
+      (*fn_)(i);
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      uint64_t g = gen_.load(std::memory_order_acquire);
+      for (int spin = 0; g == seen && spin < 4000; ++spin) {
+        std::this_thread::yield();
+        g = gen_.load(std::memory_order_acquire);
+      }
+      if (g == seen) {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+        g = gen_.load(std::memory_order_acquire);
+      }
+      seen = g;
+      if (stop_) return;
+      work();
+      finished_.fetch_add(1, std::memory_order_release);
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::atomic<uint64_t> gen_{0};
+  std::atomic<int> next_{0}, finished_{0};
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_ = 0;
+  bool stop_ = false;
+};
 
 struct BlockLSQ {
   int s = 0, m = 0;          // block size, maximum number of column blocks
   int k = 0;                 // column blocks added
-  // reduced block columns: column block j holds rows 0 .. (j+1) s - 1 of its
-  // s columns (column-major, leading dimension (j+1) s), at offset off[j]
-  std::vector<cdouble> Rt;
+  // reduced block columns: column block j is reduced in place in its slot of
+  // the arena, (j + 2) s rows of s columns (column-major, leading dimension
+  // (j + 2) s) at offset off[j]; rows 0 .. (j+1) s - 1 hold the triangular
+  // factor.  The arena is allocated for m blocks once and reused by later
+  // cycles (no per-step allocation; its pages are touched once).
+  std::shared_ptr<cdouble> arena;
+  size_t arena_len = 0;
   std::vector<size_t> off;
   // reflectors: block j, reflector kk: 2 s entries (top rows kk .. s-1 of
   // block row j, then the s rows of block row j + 1) and the scalar beta
@@ -109,14 +174,30 @@ struct BlockLSQ {
   size_t ldg = 0;
   std::vector<double> bnorm; // per right-hand side: reference norm of the estimates
   int threads = 1;
+  mutable std::shared_ptr<HostPool> pool;  // threads - 1 workers, created with the first large update
+
+  // f(c) for c in [0, n): on the pool when `big`, else on the calling thread
+  void for_columns(int n, bool big, const std::function<void(int)>& f) const {
+    if (!big || threads <= 1 || n <= 1) {
+      for (int c = 0; c < n; ++c) f(c);
+      return;
+    }
+    if (!pool) pool = std::make_shared<HostPool>(threads - 1);
+    pool->run(n, f);
+  }
 
   // S0: the start block's factor (s x s column-major), r = V_0 S0
   void init(int s_, int m_, const cdouble* S0, const double* base_norm) {
     s = s_;
     m = m_;
     k = 0;
-    Rt.clear();
     off.assign(size_t(m) + 1, 0);
+    for (int j = 0; j < m; ++j) off[size_t(j) + 1] = off[size_t(j)] + size_t(j + 2) * s * s;
+    if (off[size_t(m)] > arena_len) {
+      arena.reset(static_cast<cdouble*>(std::malloc(off[size_t(m)] * sizeof(cdouble))), std::free);
+      if (!arena) throw std::bad_alloc();
+      arena_len = off[size_t(m)];
+    }
     refl.assign(size_t(m) * s * 2 * s, cdouble(0));
     beta.assign(size_t(m) * s, 0.0);
     ldg = size_t(m + 2) * s;
@@ -130,16 +211,64 @@ struct BlockLSQ {
   }
 
   // apply reflector (j, kk) to one column x (rows j s + kk .. (j + 2) s - 1)
+  // (written on the (re, im) doubles of the complex arrays, with two
+  // independent partial sums, which the compiler keeps in registers)
   inline void apply_reflector(int j, int kk, cdouble* x) const {
     const double b = beta[size_t(j) * s + kk];
     if (b == 0.0) return;
-    const cdouble* v = &refl[(size_t(j) * s + kk) * 2 * s];
-    cdouble* top = x + size_t(j) * s + kk;
+    const double* v = reinterpret_cast<const double*>(&refl[(size_t(j) * s + kk) * 2 * s]);
+    double* top = reinterpret_cast<double*>(x + size_t(j) * s + kk);
     const int len = 2 * s - kk;
-    cdouble a = 0;
-    for (int t = 0; t < len; ++t) a += std::conj(v[t]) * top[t];
-    a *= b;
-    for (int t = 0; t < len; ++t) top[t] -= v[t] * a;
+    double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;  // a = sum conj(v_t) x_t
+    int t = 0;
+    for (; t + 1 < len; t += 2) {
+      const double vr0 = v[2 * t], vi0 = v[2 * t + 1], xr0 = top[2 * t], xi0 = top[2 * t + 1];
+      const double vr1 = v[2 * t + 2], vi1 = v[2 * t + 3], xr1 = top[2 * t + 2], xi1 = top[2 * t + 3];
+      ar0 += vr0 * xr0 + vi0 * xi0;
+      ai0 += vr0 * xi0 - vi0 * xr0;
+      ar1 += vr1 * xr1 + vi1 * xi1;
+      ai1 += vr1 * xi1 - vi1 * xr1;
+    }
+    if (t < len) {
+      ar0 += v[2 * t] * top[2 * t] + v[2 * t + 1] * top[2 * t + 1];
+      ai0 += v[2 * t] * top[2 * t + 1] - v[2 * t + 1] * top[2 * t];
+    }
+    const double ar = (ar0 + ar1) * b, ai = (ai0 + ai1) * b;
+    for (t = 0; t < len; ++t) {  // x -= v a
+      const double vr = v[2 * t], vi = v[2 * t + 1];
+      top[2 * t] -= vr * ar - vi * ai;
+      top[2 * t + 1] -= vr * ai + vi * ar;
+    }
+  }
+
+  // apply reflector (j, kk) to two columns x0, x1 at once (one pass over v,
+  // two independent chains)
+  inline void apply_reflector2(int j, int kk, cdouble* x0, cdouble* x1) const {
+    const double b = beta[size_t(j) * s + kk];
+    if (b == 0.0) return;
+    const double* v = reinterpret_cast<const double*>(&refl[(size_t(j) * s + kk) * 2 * s]);
+    double* p0 = reinterpret_cast<double*>(x0 + size_t(j) * s + kk);
+    double* p1 = reinterpret_cast<double*>(x1 + size_t(j) * s + kk);
+    const int len = 2 * s - kk;
+    double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
+    for (int t = 0; t < len; ++t) {
+      const double vr = v[2 * t], vi = v[2 * t + 1];
+      ar0 += vr * p0[2 * t] + vi * p0[2 * t + 1];
+      ai0 += vr * p0[2 * t + 1] - vi * p0[2 * t];
+      ar1 += vr * p1[2 * t] + vi * p1[2 * t + 1];
+      ai1 += vr * p1[2 * t + 1] - vi * p1[2 * t];
+    }
+    ar0 *= b;
+    ai0 *= b;
+    ar1 *= b;
+    ai1 *= b;
+    for (int t = 0; t < len; ++t) {
+      const double vr = v[2 * t], vi = v[2 * t + 1];
+      p0[2 * t] -= vr * ar0 - vi * ai0;
+      p0[2 * t + 1] -= vr * ai0 + vi * ar0;
+      p1[2 * t] -= vr * ar1 - vi * ai1;
+      p1[2 * t + 1] -= vr * ai1 + vi * ar1;
+    }
   }
 
   // Add column block j = k: h (nrows_h = j + 1 blocks of s rows x s,
@@ -153,7 +282,7 @@ struct BlockLSQ {
     const int b = nrows_h - j;
     if (b != 1) return false;
     const size_t rows = size_t(nrows_h + 1) * s, hr = size_t(nrows_h) * s;
-    std::vector<cdouble> col(rows * s);
+    cdouble* col = arena.get() + off[size_t(j)];  // this block's slot, leading dimension rows
     for (int c = 0; c < s; ++c) {
       cdouble* x = &col[size_t(c) * rows];
       for (size_t i = 0; i < hr; ++i) x[i] = h[size_t(c) * hr + i];
@@ -161,10 +290,17 @@ struct BlockLSQ {
     }
     // earlier reflectors, column by column (independent columns)
     const long work = long(j) * s * (2 * s) * s;
-    parallel_for(s, work > 200000 ? threads : 1, [&](int c) {
-      cdouble* x = &col[size_t(c) * rows];
-      for (int q = 0; q < j; ++q)
-        for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, x);
+    // (columns in pairs: one pass over the stored reflectors serves two)
+    for_columns((s + 1) / 2, work > 200000, [&](int cp) {
+      cdouble* x0 = &col[size_t(2 * cp) * rows];
+      if (2 * cp + 1 < s) {
+        cdouble* x1 = &col[size_t(2 * cp + 1) * rows];
+        for (int q = 0; q < j; ++q)
+          for (int kk = 0; kk < s; ++kk) apply_reflector2(q, kk, x0, x1);
+      } else {
+        for (int q = 0; q < j; ++q)
+          for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, x0);
+      }
     });
     // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1
     for (int kk = 0; kk < s; ++kk) {
@@ -190,11 +326,7 @@ struct BlockLSQ {
       beta[size_t(j) * s + kk] = vn2 > 0 ? 2.0 / vn2 : 0.0;
       for (int c = kk; c < s; ++c) apply_reflector(j, kk, &col[size_t(c) * rows]);
     }
-    // store the reduced block (rows 0 .. (j+1) s - 1)
-    off[size_t(j)] = Rt.size();
-    Rt.resize(Rt.size() + size_t(j + 1) * s * s);
-    for (int c = 0; c < s; ++c)
-      for (size_t i = 0; i < size_t(j + 1) * s; ++i) Rt[off[size_t(j)] + size_t(c) * (j + 1) * s + i] = col[size_t(c) * rows + i];
+    // the reduced block stays in its slot (rows 0 .. (j+1) s - 1)
     for (int c = 0; c < s; ++c)
       for (int kk = 0; kk < s; ++kk) apply_reflector(j, kk, &g[size_t(c) * ldg]);
     ++k;
@@ -215,7 +347,7 @@ struct BlockLSQ {
     double dmax = 0;
     for (size_t i = 0; i < n; ++i) dmax = std::max(dmax, std::abs(diag(i)));
     const double eps = 1e-13 * dmax;
-    parallel_for(s, n * n * s > 4000000 ? threads : 1, [&](int c) {
+    for_columns(s, n * n * s > 4000000, [&](int c) {
       cdouble* y = &Y[size_t(c) * n];
       for (size_t i = 0; i < n; ++i) y[i] = g[size_t(c) * ldg + i];
       for (size_t ii = n; ii-- > 0;) {
@@ -227,7 +359,7 @@ struct BlockLSQ {
         y[ii] /= d;
         // subtract column ii's entries above the diagonal
         const int jb = int(ii / s), cc = int(ii % s);
-        const cdouble* colp = &Rt[off[size_t(jb)] + size_t(cc) * (jb + 1) * s];
+        const cdouble* colp = arena.get() + off[size_t(jb)] + size_t(cc) * (jb + 2) * s;
         for (size_t t = 0; t < ii; ++t) y[t] -= colp[t] * y[ii];
       }
     });
@@ -235,7 +367,7 @@ struct BlockLSQ {
 
   cdouble diag(size_t i) const {
     const int jb = int(i / s), cc = int(i % s);
-    return Rt[off[size_t(jb)] + size_t(cc) * (jb + 1) * s + i];
+    return arena.get()[off[size_t(jb)] + size_t(cc) * (jb + 2) * s + i];
   }
 };
 

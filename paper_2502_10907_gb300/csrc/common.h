@@ -192,6 +192,8 @@ struct LearnedState;
 struct mtf_system_s {
   mtf_mesh mesh = nullptr;
   mtf_options opt{};
+  // host time of the inner block FGMRES steps of the current solve (s)
+  double t_launch = 0, t_lsq = 0, t_wait = 0;
   double k0 = 0;
   std::vector<double> k_re, k_im, rho_re, rho_im;
   mtf::DevBuf<double> d_k, d_rho;            // (re, im) per block

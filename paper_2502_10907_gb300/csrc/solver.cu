@@ -527,6 +527,7 @@ __global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int6
 mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, mtf_solve_stats* st,
                  cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
+  sys->t_launch = sys->t_lsq = sys->t_wait = 0;
   mtf_mesh msh = sys->mesh;
   const int64_t n = msh->n_total;
   const int m = std::max(1, sys->opt.restart);
@@ -634,6 +635,9 @@ mtf_status solve(mtf_system sys, int nrhs, const double* b_dev, double* x_dev, m
     st->converged = status == MTF_OK;
     st->rel_residual = *std::max_element(rel.begin(), rel.end());
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    st->launch_seconds = sys->t_launch;
+    st->lsq_seconds = sys->t_lsq;
+    st->wait_seconds = sys->t_wait;
   }
   return status;
 }

@@ -6,7 +6,8 @@
 //     and columns a deflated direction gives): the coefficients Y solve the
 //     least-squares problem min ||E_1 S_0 - Hbar Y|| (compared with the
 //     normal equations solved densely) and the residual estimates equal the
-//     true residual norms.
+//     true residual norms;
+//  3. the worker pool gives the single-thread results (below).
 #include <cstdio>
 #include <random>
 #include "block_krylov.h"
@@ -111,7 +112,51 @@ static double check_lsq() {
   return (worst_est < 1e-10 && worst_ne < 1e-10) ? 0.0 : 1.0;
 }
 
+// 3. the same updates on the host worker pool: 40 column blocks of 16
+//    columns (past the size at which BlockLSQ hands its columns to the pool;
+//    the least-squares solve too), once on 1 thread and once on 4, give
+//    bit-identical estimates and coefficients (every column follows the same
+//    arithmetic on whichever thread runs it)
+static double check_pool() {
+  const int s = 16, kb = 40, m = 44;
+  std::vector<std::vector<cd>> hs, Rs;
+  std::mt19937 rng(13);
+  std::normal_distribution<double> N(0, 1);
+  for (int j = 0; j < kb; ++j) {
+    std::vector<cd> h(size_t(j + 1) * s * s), R(size_t(s) * s, 0.0);
+    for (auto& v : h) v = cd(N(rng), N(rng));
+    for (int c = 0; c < s; ++c)
+      for (int i = 0; i <= c; ++i) R[size_t(c) * s + i] = cd(N(rng), N(rng)) * (i == c ? 4.0 : 1.0);
+    hs.push_back(h);
+    Rs.push_back(R);
+  }
+  std::vector<cd> S0(size_t(s) * s, 0.0);
+  for (int c = 0; c < s; ++c) S0[size_t(c) * s + c] = 1.0 + c;
+  std::vector<double> bn(s, 1.0);
+  std::vector<double> est[2];
+  std::vector<cd> Y[2];
+  int rounds = 0;
+  for (int v = 0; v < 2; ++v) {
+    mtf::BlockLSQ L;
+    L.init(s, m, S0.data(), bn.data());
+    L.threads = v == 0 ? 1 : 4;
+    est[v].assign(s, 0.0);
+    for (int r = 0; r < 3; ++r) {  // the pool serves several solves in a row
+      L.init(s, m, S0.data(), bn.data());
+      L.threads = v == 0 ? 1 : 4;
+      for (int j = 0; j < kb; ++j) L.add_block(hs[j].data(), j + 1, Rs[j].data(), est[v].data());
+      L.solve(Y[v]);
+      rounds += v;
+    }
+  }
+  bool same = Y[0].size() == Y[1].size();
+  for (size_t i = 0; same && i < Y[0].size(); ++i) same = Y[0][i] == Y[1][i];
+  for (int c = 0; same && c < s; ++c) same = est[0][c] == est[1][c];
+  std::printf("pool: %d pooled solves, results %s\n", rounds, same ? "identical" : "DIFFER");
+  return same ? 0.0 : 1.0;
+}
+
 int main() {
-  const double f = check_cholesky() + check_lsq();
+  const double f = check_cholesky() + check_lsq() + check_pool();
   return f == 0.0 ? 0 : 1;
 }
