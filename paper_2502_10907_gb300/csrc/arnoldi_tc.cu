@@ -70,6 +70,8 @@ __device__ __forceinline__ void tca_split(float v, __half& hi, __half& lo) {
 // thread = (vector, group of 4 entries), entries fastest
 __global__ void k_tca_store_dots(const float* __restrict__ Vn, int64_t ldn, int q0, int s, int nkc,
                                  __half* __restrict__ Vd) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t ng = ldn / 4;
   if (t >= ng * s) return;
@@ -89,6 +91,8 @@ __global__ void k_tca_store_dots(const float* __restrict__ Vn, int64_t ldn, int 
 // the same vectors into the update copy: thread = (entry, vector), vectors fastest
 __global__ void k_tca_store_upd(const float* __restrict__ Vn, int64_t ldn, int q0, int s, int nbc,
                                 __half* __restrict__ Vu) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= ldn * s) return;
   const int q = int(t % s);
@@ -117,6 +121,8 @@ __global__ void k_tca_colmax32(const float* __restrict__ W, int64_t ld, int64_t 
 
 // colmax[c] = max over q < nq of |re|, |im| of H[q, c] (FP64, leading dim ldh)
 __global__ void k_tca_colmax64(const double* __restrict__ H, int nq, int ldh, unsigned* __restrict__ colmax) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int c = blockIdx.y;
   float m = 0.f;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -131,6 +137,8 @@ __global__ void k_tca_colmax64(const double* __restrict__ H, int nq, int ldh, un
 // (w_im, -w_re); thread = (chunk, column, group of 4 entries)
 __global__ void k_tca_w_to_b(const float* __restrict__ W, int64_t ldw, int s, int nkc, int nb,
                              const unsigned* __restrict__ colmax, __half* __restrict__ Bd) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(nkc) * nb * 8) return;
   const int64_t kc = t / (int64_t(nb) * 8);
@@ -159,6 +167,8 @@ __global__ void k_tca_w_to_b(const float* __restrict__ W, int64_t ldw, int s, in
 // of 4 vectors)
 __global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int ldh, int nbc, int nb,
                              const unsigned* __restrict__ colmax, __half* __restrict__ Bu) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(nbc) * nb * 8) return;
   const int b = int(t / (int64_t(nb) * 8));
@@ -189,6 +199,8 @@ __global__ void k_tca_h_to_b(const double* __restrict__ H, int nq, int s, int ld
 // q / 128 of the raw sums) x the inverse scales, in FP64; thread = (q, c)
 __global__ void k_tca_dots_reduce(const float* __restrict__ part, int nb, int P, int nq, int s,
                                   const unsigned* __restrict__ colmax, double* __restrict__ H, int ldh) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(nq) * s) return;
   const int q = int(t / s), c = int(t % s);
@@ -281,9 +293,11 @@ static void tca_bmaps(TcArnoldi& t, int nb) {
 // basis vectors q0 .. q0 + s - 1 (FP32 columns of stride ldn) into both copies
 void tca_store(TcArnoldi& t, const float* Vn, int q0, cudaStream_t st) {
   const int64_t n1 = t.ldn / 4 * t.s, n2 = t.ldn * t.s;
-  MTF_LAUNCH(KID_BSTORE, st, k_tca_store_dots<<<unsigned((n1 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nkc,
+  MTF_LAUNCH(KID_BSTORE, st, launch_pdl(k_tca_store_dots, dim3(unsigned((n1 + 255) / 256)), dim3(256), 0, st,
+      Vn, t.ldn, q0, t.s, t.nkc,
                                                                                         t.Vd.p));
-  MTF_LAUNCH(KID_BSTORE, st, k_tca_store_upd<<<unsigned((n2 + 255) / 256), 256, 0, st>>>(Vn, t.ldn, q0, t.s, t.nbc,
+  MTF_LAUNCH(KID_BSTORE, st, launch_pdl(k_tca_store_upd, dim3(unsigned((n2 + 255) / 256)), dim3(256), 0, st,
+      Vn, t.ldn, q0, t.s, t.nbc,
                                                                                        t.Vu.p));
 }
 
@@ -316,7 +330,8 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
   // H = V^H W: units (basis group g, a piece of the entry chunks)
   MTF_LAUNCH(KID_TCA_PREP, st, k_tca_colmax32<<<dim3(64, unsigned(nc)), 256, 0, st>>>(W, t.ldn, t.ldn, cmw));
   const int64_t nthr = int64_t(t.nkc) * NB * 8;
-  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_w_to_b<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(W, t.ldn, nc, t.nkc, NB, cmw,
+  MTF_LAUNCH(KID_TCA_PREP, st, launch_pdl(k_tca_w_to_b, dim3(unsigned((nthr + 255) / 256)), dim3(256), 0, st,
+      W, t.ldn, nc, t.nkc, NB, cmw,
                                                                                       t.Bd.p));
   const int g_used = (nq + kTcRows - 1) / kTcRows;
   const int P = std::max(1, std::min({t.nkc, 32, (4 * t.n_cta + g_used - 1) / g_used}));
@@ -336,13 +351,16 @@ static void tca_project_nb(TcArnoldi& t, int nq, float* W, int nc, double* H, in
     prof_bytes(KID_DOTS, double(nq + nc) * double(t.ldn) * 8.0);
     tca_launch<2, NB, 0>(t, t.vd_map, t.bd_map, ud, nu, nullptr, nc, 0, cmw, err, KID_DOTS, st);
   }
-  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_dots_reduce<<<unsigned((int64_t(nq) * nc + 255) / 256), 256, 0, st>>>(
+  const unsigned gr = unsigned((int64_t(nq) * nc + 255) / 256);
+  MTF_LAUNCH(KID_TCA_PREP, st, launch_pdl(k_tca_dots_reduce, dim3(gr), dim3(256), 0, st,
       t.part.p, NB, Pn, nq, nc, cmw, H, ldh));
   // W -= V H: one unit per entry group, over the basis chunks in use
-  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_colmax64<<<dim3(8, unsigned(nc)), 256, 0, st>>>(H, nq, ldh, cmh));
+  MTF_LAUNCH(KID_TCA_PREP, st, launch_pdl(k_tca_colmax64, dim3(8, unsigned(nc)), dim3(256), 0, st,
+      H, nq, ldh, cmh));
   const int nbc_used = (nq + 31) / 32;
   const int64_t nthu = int64_t(nbc_used) * NB * 8;
-  MTF_LAUNCH(KID_TCA_PREP, st, k_tca_h_to_b<<<unsigned((nthu + 255) / 256), 256, 0, st>>>(H, nq, nc, ldh, nbc_used, NB,
+  MTF_LAUNCH(KID_TCA_PREP, st, launch_pdl(k_tca_h_to_b, dim3(unsigned((nthu + 255) / 256)), dim3(256), 0, st,
+      H, nq, nc, ldh, nbc_used, NB,
                                                                                       cmh, t.Bu.p));
   TcUnits uu;
   uu.kind = 2;

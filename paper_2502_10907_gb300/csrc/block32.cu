@@ -165,6 +165,8 @@ template <int SC>
 __global__ void __launch_bounds__(256) k_bupdate(const float* __restrict__ V, int nq, int64_t ldv,
                                                  const double* __restrict__ H, int ldh, float* __restrict__ W,
                                                  int64_t ldw, int nc, int64_t n_pad) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   constexpr int QC = 128;
   __shared__ __align__(16) float2 hs[QC][SC];
   extern __shared__ __align__(16) float4 red[];  // [8][SC][32] float4 (two complex)
@@ -358,6 +360,8 @@ __global__ void __launch_bounds__(256) k_bchol(const double* __restrict__ G, int
                                                const int* __restrict__ mask, double tau, int s, double* __restrict__ R,
                                                int* __restrict__ kept, const double* __restrict__ Gwv,
                                                double* __restrict__ C) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   using T2 = typename CxOf<T>::type;
   extern __shared__ __align__(16) unsigned char shb[];
   T2* A = reinterpret_cast<T2*>(shb);  // A[c * s + i] = Schur complement entry (i, c), i <= c; then C
@@ -441,6 +445,8 @@ template <int SC>
 __global__ void __launch_bounds__(128) k_btrsm(const float* __restrict__ in, int64_t ldi, const double* __restrict__ R,
                                                const int* __restrict__ kept, int s, float* __restrict__ out, int64_t ldo,
                                                int64_t n_pad) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   __shared__ float2 rs[SC][SC];  // rs[p][q] = R(p, q)
   __shared__ float2 inv[SC];     // 1 / R(q, q), 0 for dropped q
   for (int t = threadIdx.x; t < SC * SC; t += blockDim.x) {
@@ -484,6 +490,8 @@ template <int SC>
 __global__ void __launch_bounds__(128) k_btrsm_wide(const float* __restrict__ in, int64_t ldi,
                                                     const double* __restrict__ R, const int* __restrict__ kept, int s,
                                                     float* __restrict__ out, int64_t ldo, int64_t n_pad) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   extern __shared__ float2 shw[];
   float2* rs = shw;             // rs[p * SC + q] = R(p, q)
   float2* vs = shw + SC * SC;   // vs[q * 128 + thread]
@@ -590,6 +598,8 @@ __global__ void __launch_bounds__(64) k_bcoef(const double* __restrict__ Gwv, co
 __global__ void k_bhcol(const double* __restrict__ Sprev, const double* __restrict__ Scur,
                         const double* __restrict__ Cp, const double* __restrict__ Rp, const double* __restrict__ Rv,
                         int nq0, int s, double* __restrict__ h, double* __restrict__ Rn) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nh = int64_t(nq0 + s) * s;
   const int ls = 2 * s;
@@ -678,7 +688,8 @@ static void bupdate_launch(const float* V, int nq, int64_t ldv, const double* H,
   }
   // basis read once, block read and written once
   prof_bytes(kid, double(nq + 2 * nc) * double(n_pad) * 8.0);
-  MTF_LAUNCH(kid, st, k_bupdate<SC><<<nbk(n_pad, 64), 256, smem, st>>>(V, nq, ldv, H, ldh, W, ldw, nc, n_pad));
+  MTF_LAUNCH(kid, st, launch_pdl(k_bupdate<SC>, dim3(nbk(n_pad, 64)), dim3(256), smem, st,
+      V, nq, ldv, H, ldh, W, ldw, nc, n_pad));
 }
 
 // W_{c0 + c} -= sum_q V_q H[q, c0 + c] over all column groups of 16
@@ -719,7 +730,7 @@ static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept
                   int64_t n_pad, cudaStream_t st) {
   const unsigned g = nbk(n_pad, 128);
 #define MTF_BT(SCV) \
-  MTF_LAUNCH(KID_BXFORM, st, k_btrsm<SCV><<<g, 128, 0, st>>>(in, ldi, R, kept, s, out, ldo, n_pad))
+  MTF_LAUNCH(KID_BXFORM, st, launch_pdl(k_btrsm<SCV>, dim3(g), dim3(128), 0, st, in, ldi, R, kept, s, out, ldo, n_pad))
   if (s <= 1) MTF_BT(1);
   else if (s <= 2) MTF_BT(2);
   else if (s <= 4) MTF_BT(4);
@@ -741,9 +752,11 @@ static void btrsm(const float* in, int64_t ldi, const double* R, const int* kept
       opted.fetch_or(bit);
     }
     if (SC == 32)
-      MTF_LAUNCH(KID_BXFORM, st, k_btrsm_wide<32><<<g, 128, smem, st>>>(in, ldi, R, kept, s, out, ldo, n_pad));
+      MTF_LAUNCH(KID_BXFORM, st, launch_pdl(k_btrsm_wide<32>, dim3(g), dim3(128), smem, st,
+          in, ldi, R, kept, s, out, ldo, n_pad));
     else
-      MTF_LAUNCH(KID_BXFORM, st, k_btrsm_wide<64><<<g, 128, smem, st>>>(in, ldi, R, kept, s, out, ldo, n_pad));
+      MTF_LAUNCH(KID_BXFORM, st, launch_pdl(k_btrsm_wide<64>, dim3(g), dim3(128), smem, st,
+          in, ldi, R, kept, s, out, ldo, n_pad));
   }
 #undef MTF_BT
 }
@@ -943,9 +956,10 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
     } else {
       // second CholQR pass of V~_J: directions that the first kept
       // Rv and, for a step with an operator apply, Cc = Rv^-H G_vw
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<float><<<1, 256, chol_smem32, st>>>(G2, s, nullptr, keptR, 1e-3, s, Rv, keptV,
+      MTF_LAUNCH(KID_BCHOL, st, launch_pdl(k_bchol<float>, dim3(1), dim3(256), chol_smem32, st,
+          G2, s, nullptr, keptR, 1e-3, s, Rv, keptV,
                                                                           Gwv, finish ? nullptr : Cc));
-      MTF_LAUNCH(KID_BXFORM, st, k_bhcol<<<nbk(int64_t(nq + s) * s, 256), 256, 0, st>>>(
+      MTF_LAUNCH(KID_BXFORM, st, launch_pdl(k_bhcol, dim3(nbk(int64_t(nq + s) * s, 256)), dim3(256), 0, st,
           Sprev, Scur, Cprev, R, Rv, nq - s, s, Hc, Rn));
     }
     if (!finish) {
@@ -955,7 +969,8 @@ mtf_status fgmres_block32(mtf_system sys, int s, const double* r_dev, double* x_
         MTF_LAUNCH(KID_BXFORM, st, k_bcoef<<<1, 64, 2 * size_t(s) * s * sizeof(double2), st>>>(Gwv, Rv, keptV, s, Cc));
       bupdate(Vt, s, ldn, Cc, s, X1, ldn, s, ldn, st);
       bgram(sys, X1, ldn, s, ldn, G, s, st);
-      MTF_LAUNCH(KID_BCHOL, st, k_bchol<double><<<1, 256, chol_smem, st>>>(G, s, Gpre, nullptr, kDeflateTau, s, R,
+      MTF_LAUNCH(KID_BCHOL, st, launch_pdl(k_bchol<double>, dim3(1), dim3(256), chol_smem, st,
+          G, s, Gpre, nullptr, kDeflateTau, s, R,
                                                                            keptR, nullptr, nullptr));
       btrsm(X1, ldn, R, keptR, s, Vt + 2 * vstride, ldn, ldn, st);
       if (tc && J > 0) tca_store(*B.tca, Vt, J * s, st);

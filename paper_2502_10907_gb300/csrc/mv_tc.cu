@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(256) k_tc_build_b_real(const float* __restrict
                                                          const int32_t* __restrict__ blk_N,
                                                          const int64_t* __restrict__ blk_dof_off,
                                                          const unsigned* __restrict__ colmax, __half* __restrict__ B) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n_chunks * nb * 8) return;
   const int64_t chunk = t / (int64_t(nb) * 8);
@@ -246,6 +248,8 @@ __global__ void __launch_bounds__(256) k_os_tc_combine(
     const int64_t* __restrict__ blk_dof_off, const int64_t* __restrict__ blk_row_off, const int* __restrict__ blk_unit_base,
     const int* __restrict__ blk_pieces, const unsigned* __restrict__ colmax, const float* __restrict__ cf,
     float* __restrict__ z, int64_t ldz, int c0, int nc, int64_t n_rows) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int L = tc_row_lanes(nc);
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
@@ -302,6 +306,8 @@ __global__ void __launch_bounds__(256) k_tc_build_b(const float* __restrict__ x,
                                                     const int32_t* __restrict__ blk_N,
                                                     const int64_t* __restrict__ blk_dof_off,
                                                     const unsigned* __restrict__ colmax, __half* __restrict__ B) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n_chunks * nb * 8) return;
   const int64_t chunk = t / (int64_t(nb) * 8);
@@ -496,6 +502,8 @@ __global__ void __launch_bounds__(256) k_mv_tc_combine(
     const int* __restrict__ blk_pieces, const unsigned* __restrict__ amax, const unsigned* __restrict__ colmax,
     const XEntry* __restrict__ xe, const float* __restrict__ xval32, const float* __restrict__ rho32,
     const float* __restrict__ x, int64_t ldx, float* __restrict__ y, int64_t ldy, int c0, int nc, int64_t n_rows) {
+  MTF_PDL_WAIT();
+  MTF_PDL_TRIGGER();
   const int L = tc_row_lanes(nc);
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
@@ -761,7 +769,7 @@ static void tc_build_inputs(mtf_system sys, TcMatvec& t, const float* x, int64_t
   MTF_CUDA(cudaMemsetAsync(t.colmax.p, 0, 32 * sizeof(unsigned), s));
   MTF_LAUNCH(kid, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(x, ldx, m->n_total, c0, t.colmax.p));
   const int64_t nthr = p.n_chunks * NB * 8;
-  MTF_LAUNCH(kid, s, k_tc_build_b<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(kid, s, launch_pdl(k_tc_build_b, dim3(unsigned((nthr + 255) / 256)), dim3(256), 0, s,
       x, ldx, c0, nc, NB, t.chunk_info.p, p.n_chunks, m->d_blk_N.p, m->d_blk_dof_off.p, t.colmax.p, t.B.p));
 }
 
@@ -786,7 +794,8 @@ static void mv_tc_pass(mtf_system sys, TcMatvec& t, const float* x, int64_t ldx,
   MTF_LAUNCH(KID_MVTC, s, k_mv_tc<NB><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.amap, t.bmap, t.units.p, t.sched.p, t.sched_off.p, t.blk_tile_base.p, t.blk_nkc.p, t.blk_chunk_base.p,
       t.part.p, sys->d_mv_ctl.p + 2));
-  MTF_LAUNCH(KID_MVTC_COMBINE, s, k_mv_tc_combine<NB><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
+  const unsigned gc = unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256);
+  MTF_LAUNCH(KID_MVTC_COMBINE, s, launch_pdl(k_mv_tc_combine<NB>, dim3(gc), dim3(256), 0, s,
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.amax.p, t.colmax.p, m->d_xent.p, sys->d_xval32.p, sys->d_rho32.p, x, ldx, y, ldy, c0, nc,
       m->n_rows));
@@ -867,7 +876,8 @@ static void os_tc_pass(mtf_system sys, TcMatvec& t, const float* r, int64_t ldr,
   MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       t.osmap, t.bmap, units, int(t.plan.units.size()), t.sched.p, t.sched_off.p, t.part.p, nullptr, 0, 0, 0, nullptr,
       sys->d_mv_ctl.p + 2, TcTtOut{}));
-  MTF_LAUNCH(KID_OSCOMBINE, s, k_os_tc_combine<NB><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
+  const unsigned gc = unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256);
+  MTF_LAUNCH(KID_OSCOMBINE, s, launch_pdl(k_os_tc_combine<NB>, dim3(gc), dim3(256), 0, s,
       t.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, t.blk_unit_base.p,
       t.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
 }
@@ -895,7 +905,7 @@ static void os_tc_pass_real(mtf_system sys, TcMatvec& t, const float* r, int64_t
   MTF_CUDA(cudaMemsetAsync(t.colmax.p, 0, 32 * sizeof(unsigned), s));
   MTF_LAUNCH(KID_OSRC, s, k_tc_colmax<<<dim3(64, unsigned(nc)), 256, 0, s>>>(r, ldr, m->n_total, c0, t.colmax.p));
   const int64_t nthr = p.n_chunks * NB * 8;
-  MTF_LAUNCH(KID_OSRC, s, k_tc_build_b_real<<<unsigned((nthr + 255) / 256), 256, 0, s>>>(
+  MTF_LAUNCH(KID_OSRC, s, launch_pdl(k_tc_build_b_real, dim3(unsigned((nthr + 255) / 256)), dim3(256), 0, s,
       r, ldr, c0, nc, NB, o.chunk_info.p, p.n_chunks, m->d_blk_N.p, m->d_blk_dof_off.p, t.colmax.p, o.B.p));
   static std::atomic<uint64_t> opted{0};
   int dev = 0;
@@ -913,8 +923,9 @@ static void os_tc_pass_real(mtf_system sys, TcMatvec& t, const float* r, int64_t
   MTF_LAUNCH(KID_OSRC, s, k_tc_stream<1, NB, 0><<<unsigned(t.n_cta), 192, Cfg::smem, s>>>(
       o.amap, o.bmap, units, int(p.units.size()), o.sched.p, o.sched_off.p, o.part.p, nullptr, 0, 0, 0, nullptr,
       sys->d_mv_ctl.p + 2, TcTtOut{}));
+  const unsigned gc = unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256);
   MTF_LAUNCH(KID_OSCOMBINE, s,
-             k_os_tc_combine<NB, true><<<unsigned((m->n_rows * tc_row_lanes(nc) + 255) / 256), 256, 0, s>>>(
+             launch_pdl(k_os_tc_combine<NB, true>, dim3(gc), dim3(256), 0, s,
                  o.part.p, m->d_row_blk.p, m->d_blk_N.p, m->d_blk_dof_off.p, m->d_blk_row_off.p, o.blk_unit_base.p,
                  o.blk_pieces.p, t.colmax.p, sys->d_os_coef16.p, z, ldz, c0, nc, m->n_rows));
 }
