@@ -716,9 +716,11 @@ def main():
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
+        host_split = []
         for _ in range(args.steps):
             x, st, f = step()
             iters.append(st.iterations)
+            host_split.append((st.seconds, st.launch_seconds, st.lsq_seconds, st.wait_seconds))
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -846,6 +848,8 @@ def main():
             "fp64_reference": ref_info,
             "gmres_iterations": int(statistics.median(iters)),
             "converged": bool(st.converged),
+            "solve_host_split": {k: round(statistics.median(h[i] for h in host_split), 4) for i, k in
+                                 enumerate(("solve_s", "launch_s", "lsq_s", "wait_s"))},
             "gpu_launches": int(launches),
             "kernels": kernel_table(prof),
             "kernel_times": "CUDA events around every library launch in a second pass of the same steps "
