@@ -241,34 +241,52 @@ struct BlockLSQ {
     }
   }
 
-  // apply reflector (j, kk) to two columns x0, x1 at once (one pass over v,
-  // two independent chains)
-  inline void apply_reflector2(int j, int kk, cdouble* x0, cdouble* x1) const {
+  // apply reflector (j, kk) to NC columns at once (one pass over v, NC
+  // independent chains)
+  template <int NC>
+  inline void apply_reflector_cols(int j, int kk, cdouble* const* xs) const {
     const double b = beta[size_t(j) * s + kk];
     if (b == 0.0) return;
     const double* v = reinterpret_cast<const double*>(&refl[(size_t(j) * s + kk) * 2 * s]);
-    double* p0 = reinterpret_cast<double*>(x0 + size_t(j) * s + kk);
-    double* p1 = reinterpret_cast<double*>(x1 + size_t(j) * s + kk);
+    double* p[NC];
+    for (int c = 0; c < NC; ++c) p[c] = reinterpret_cast<double*>(xs[c] + size_t(j) * s + kk);
     const int len = 2 * s - kk;
-    double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
+    double ar[NC], ai[NC];
+    for (int c = 0; c < NC; ++c) ar[c] = ai[c] = 0.0;
     for (int t = 0; t < len; ++t) {
       const double vr = v[2 * t], vi = v[2 * t + 1];
-      ar0 += vr * p0[2 * t] + vi * p0[2 * t + 1];
-      ai0 += vr * p0[2 * t + 1] - vi * p0[2 * t];
-      ar1 += vr * p1[2 * t] + vi * p1[2 * t + 1];
-      ai1 += vr * p1[2 * t + 1] - vi * p1[2 * t];
+      for (int c = 0; c < NC; ++c) {
+        ar[c] += vr * p[c][2 * t] + vi * p[c][2 * t + 1];
+        ai[c] += vr * p[c][2 * t + 1] - vi * p[c][2 * t];
+      }
     }
-    ar0 *= b;
-    ai0 *= b;
-    ar1 *= b;
-    ai1 *= b;
+    for (int c = 0; c < NC; ++c) {
+      ar[c] *= b;
+      ai[c] *= b;
+    }
     for (int t = 0; t < len; ++t) {
       const double vr = v[2 * t], vi = v[2 * t + 1];
-      p0[2 * t] -= vr * ar0 - vi * ai0;
-      p0[2 * t + 1] -= vr * ai0 + vi * ar0;
-      p1[2 * t] -= vr * ar1 - vi * ai1;
-      p1[2 * t + 1] -= vr * ai1 + vi * ar1;
+      for (int c = 0; c < NC; ++c) {
+        p[c][2 * t] -= vr * ar[c] - vi * ai[c];
+        p[c][2 * t + 1] -= vr * ai[c] + vi * ar[c];
+      }
     }
+  }
+
+  // earlier blocks' reflectors on the columns [c0, c0 + n) of x (column
+  // stride rows), NC at a time
+  template <int NC>
+  void earlier_reflectors(int j, cdouble* col, size_t rows, int c0, int n) const {
+    int c = c0;
+    for (; c + NC <= c0 + n; c += NC) {
+      cdouble* xs[NC];
+      for (int q = 0; q < NC; ++q) xs[q] = col + size_t(c + q) * rows;
+      for (int q = 0; q < j; ++q)
+        for (int kk = 0; kk < s; ++kk) apply_reflector_cols<NC>(q, kk, xs);
+    }
+    for (; c < c0 + n; ++c)
+      for (int q = 0; q < j; ++q)
+        for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, col + size_t(c) * rows);
   }
 
   // Add column block j = k: h (nrows_h = j + 1 blocks of s rows x s,
@@ -290,17 +308,13 @@ struct BlockLSQ {
     }
     // earlier reflectors, column by column (independent columns)
     const long work = long(j) * s * (2 * s) * s;
-    // (columns in pairs: one pass over the stored reflectors serves two)
-    for_columns((s + 1) / 2, work > 200000, [&](int cp) {
-      cdouble* x0 = &col[size_t(2 * cp) * rows];
-      if (2 * cp + 1 < s) {
-        cdouble* x1 = &col[size_t(2 * cp + 1) * rows];
-        for (int q = 0; q < j; ++q)
-          for (int kk = 0; kk < s; ++kk) apply_reflector2(q, kk, x0, x1);
-      } else {
-        for (int q = 0; q < j; ++q)
-          for (int kk = 0; kk < s; ++kk) apply_reflector(q, kk, x0);
-      }
+    // (columns in groups: one pass over the stored reflectors serves 2, or 4
+    // for blocks of 32 columns or more)
+    const int G = s >= 32 ? 4 : 2;
+    for_columns((s + G - 1) / G, work > 200000, [&](int cg) {
+      const int c0 = cg * G, n = std::min(G, s - c0);
+      if (G == 4) earlier_reflectors<4>(j, col, rows, c0, n);
+      else earlier_reflectors<2>(j, col, rows, c0, n);
     });
     // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1
     for (int kk = 0; kk < s; ++kk) {

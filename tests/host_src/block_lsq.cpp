@@ -2,7 +2,8 @@
 //  1. deflating_cholesky on a block with a dependent column: the kept
 //     columns of V = W T are orthonormal, W = V R, the dependent column is
 //     deflated;
-//  2. BlockLSQ on a random block upper-Hessenberg matrix (with the zero rows
+//  2. BlockLSQ on random block upper-Hessenberg matrices, blocks of 4 and of
+//     32 columns (with the zero rows
 //     and columns a deflated direction gives): the coefficients Y solve the
 //     least-squares problem min ||E_1 S_0 - Hbar Y|| (compared with the
 //     normal equations solved densely) and the residual estimates equal the
@@ -55,8 +56,8 @@ static double check_cholesky() {
   return (nk == s - 1 && !kept[3] && orth < 1e-10 && std::sqrt(rec / nw) < 1e-10) ? 0.0 : 1.0;
 }
 
-static double check_lsq() {
-  const int s = 4, kb = 7, m = 10;
+static double check_lsq(int s, int kb) {
+  const int m = kb + 3;
   std::mt19937 rng(11);
   std::normal_distribution<double> N(0, 1);
   const int rows = (kb + 1) * s, cols = kb * s;
@@ -108,7 +109,8 @@ static double check_lsq() {
       worst_ne = std::max(worst_ne, std::abs(acc));
     }
   }
-  std::printf("lsq: max |est - ||r||| / est = %.2e   max |H^H r| = %.2e\n", worst_est, worst_ne);
+  std::printf("lsq (s = %d, %d blocks): max |est - ||r||| / est = %.2e   max |H^H r| = %.2e\n", s, kb, worst_est,
+              worst_ne);
   return (worst_est < 1e-10 && worst_ne < 1e-10) ? 0.0 : 1.0;
 }
 
@@ -157,6 +159,8 @@ static double check_pool() {
 }
 
 int main() {
-  const double f = check_cholesky() + check_lsq() + check_pool();
+  // s = 4: reflectors of earlier blocks applied to column pairs; s = 32:
+  // in groups of 4 columns
+  const double f = check_cholesky() + check_lsq(4, 7) + check_lsq(32, 6) + check_pool();
   return f == 0.0 ? 0 : 1;
 }
