@@ -316,33 +316,49 @@ struct BlockLSQ {
       if (G == 4) earlier_reflectors<4>(j, col, rows, c0, n);
       else earlier_reflectors<2>(j, col, rows, c0, n);
     });
-    // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1
-    for (int kk = 0; kk < s; ++kk) {
-      cdouble* x = &col[size_t(kk) * rows] + size_t(j) * s + kk;
-      cdouble* v = &refl[(size_t(j) * s + kk) * 2 * s];
-      const int len = 2 * s - kk;
-      double nrm2 = 0;
-      for (int t = 0; t < len; ++t) nrm2 += std::norm(x[t]);
-      const double nrm = std::sqrt(nrm2);
-      if (nrm == 0.0) {
-        beta[size_t(j) * s + kk] = 0.0;
-        continue;
+    // reflectors of this block: column kk, rows j s + kk .. (j + 1 + b) s - 1.
+    // Wide blocks (32 columns or more) take them in panels of 8 columns: a
+    // panel's reflectors are formed and applied within the panel, then
+    // applied to the columns to its right on the pool (each column still
+    // sees the reflectors in order)
+    const bool wide = s >= 32 && threads > 1;
+    const int P = wide ? 8 : s;
+    for (int k0 = 0; k0 < s; k0 += P) {
+      const int k1 = std::min(s, k0 + P);
+      for (int kk = k0; kk < k1; ++kk) {
+        cdouble* x = &col[size_t(kk) * rows] + size_t(j) * s + kk;
+        cdouble* v = &refl[(size_t(j) * s + kk) * 2 * s];
+        const int len = 2 * s - kk;
+        double nrm2 = 0;
+        for (int t = 0; t < len; ++t) nrm2 += std::norm(x[t]);
+        const double nrm = std::sqrt(nrm2);
+        if (nrm == 0.0) {
+          beta[size_t(j) * s + kk] = 0.0;
+          continue;
+        }
+        const cdouble x0 = x[0];
+        const double ax0 = std::abs(x0);
+        const cdouble ph = ax0 > 0 ? x0 / ax0 : cdouble(1.0);
+        const cdouble alpha = -ph * nrm;  // x -> alpha e_0
+        for (int t = 0; t < len; ++t) v[t] = x[t];
+        for (int t = len; t < 2 * s; ++t) v[t] = 0;
+        v[0] -= alpha;
+        double vn2 = 0;
+        for (int t = 0; t < len; ++t) vn2 += std::norm(v[t]);
+        beta[size_t(j) * s + kk] = vn2 > 0 ? 2.0 / vn2 : 0.0;
+        for (int c = kk; c < k1; ++c) apply_reflector(j, kk, &col[size_t(c) * rows]);
       }
-      const cdouble x0 = x[0];
-      const double ax0 = std::abs(x0);
-      const cdouble ph = ax0 > 0 ? x0 / ax0 : cdouble(1.0);
-      const cdouble alpha = -ph * nrm;  // x -> alpha e_0
-      for (int t = 0; t < len; ++t) v[t] = x[t];
-      for (int t = len; t < 2 * s; ++t) v[t] = 0;
-      v[0] -= alpha;
-      double vn2 = 0;
-      for (int t = 0; t < len; ++t) vn2 += std::norm(v[t]);
-      beta[size_t(j) * s + kk] = vn2 > 0 ? 2.0 / vn2 : 0.0;
-      for (int c = kk; c < s; ++c) apply_reflector(j, kk, &col[size_t(c) * rows]);
+      if (k1 < s)
+        for_columns(s - k1, wide, [&](int i) {
+          cdouble* x = &col[size_t(k1 + i) * rows];
+          for (int kk = k0; kk < k1; ++kk) apply_reflector(j, kk, x);
+        });
     }
-    // the reduced block stays in its slot (rows 0 .. (j+1) s - 1)
-    for (int c = 0; c < s; ++c)
+    // the reduced block stays in its slot (rows 0 .. (j+1) s - 1); the
+    // least-squares right-hand sides take the block's reflectors
+    for_columns(s, wide, [&](int c) {
       for (int kk = 0; kk < s; ++kk) apply_reflector(j, kk, &g[size_t(c) * ldg]);
+    });
     ++k;
     for (int c = 0; c < s; ++c) {
       double r2 = 0;
