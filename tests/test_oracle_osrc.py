@@ -146,3 +146,28 @@ def test_block_osrc_type2_keeps_the_solution_and_the_iterations(oracle_cache):
     assert its[1] <= 1.25 * its[0] and 3 * its[1] < it0, (its, it0)
     with pytest.raises(ValueError):
         BlockOSRC(sk, ref.k, ref.rho, osrc_type=3)
+
+
+def test_block_osrc_type2_on_genus_one_boundaries():
+    """Type 2 on the concentric cuboids (M = 2; the outer ring is bounded by a
+    torus with 2 discrete harmonic fields): T~2 stays purely imaginary and
+    symmetric, T~2 G has exactly T_i - 1 eigenvalues on the negative
+    imaginary axis (the irrotational modes) and the rest, the harmonic
+    fields among them, on the positive axis, with the moduli of Type 1's."""
+    cfg = mi.config_concentric_cuboids(2, h=0.6)
+    sk = skeleton_of(cfg["mesh"])
+    from oracle.mtf import MTFSystem
+    ref = MTFSystem(sk, cfg["k0"], cfg["eps_r"], cfg["mu_r"], assemble=False)
+    P1 = BlockOSRC(sk, ref.k, ref.rho)
+    P2 = BlockOSRC(sk, ref.k, ref.rho, osrc_type=2)
+    assert P2.nh == [0, 0, 2]
+    for i in range(sk.n_domains):
+        G = mass_matrix(sk, i)
+        T2 = P2.Ttil[i]
+        assert np.abs(T2.real).max() == 0.0
+        assert np.abs(T2 - T2.T).max() < 1e-12 * np.abs(T2).max()
+        l1 = np.linalg.eigvals(P1.Ttil[i] @ G)
+        l2 = np.linalg.eigvals(T2 @ G)
+        assert np.abs(np.sort(np.abs(l2)) - np.sort(np.abs(l1))).max() < 1e-9 * np.abs(l1).max()
+        assert int((l2.imag < 0).sum()) == len(sk.tris[i]) - 1
+        assert int((l2.imag > 0).sum()) == sk.N[i] - (len(sk.tris[i]) - 1)
